@@ -1,0 +1,497 @@
+/*
+ * FP64 CPU oracle for the implicit TDGL step of Sadovskyy, Koshelev, Phillips,
+ * Karpeyev & Glatz, "Stable large-scale solver for Ginzburg-Landau equations
+ * for superconductors" (arXiv:1409.8340).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path links or calls this
+ * file; it exists so that tests, the smoke check and the CPU baseline of the
+ * benchmark can compare the CUDA implementation against a plain, slow,
+ * obviously correct restatement of the paper's discretisation.
+ *
+ * Every routine works site by site in the paper's own notation, in double
+ * precision, with no blocking, fusion or reordering.  Loops over sites may run
+ * in parallel (OpenMP); every reduction is a serial sum in index order.
+ *
+ * Grid: m = i + Nx*(j + Ny*k), x fastest (Sec. 3, discretisation of the
+ * coordinates).  Complex arrays are interleaved (re, im) doubles.
+ *
+ * Field in the yz plane, large-lambda Landau gauge A = xbar [0, Bz, -By]
+ * (Sec. 2.3, Eq. A_yz) with xbar = x - Lx/2, generalised potential
+ * A~ = A - K xhat (Sec. 2.2), link variables U = exp(-i h A~) (Eq. link_variables).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+enum { OR_PERIODIC = 0, OR_OPEN = 1 };
+
+typedef struct {
+    int32_t n[3];      /* Nx, Ny, Nz                                      */
+    int32_t bc[3];     /* OR_PERIODIC or OR_OPEN per axis                  */
+    double h[3];       /* hx, hy, hz                                      */
+    double g;          /* anisotropy: z terms carry 1/g^2 (Sec. 2.1)       */
+    double u;          /* relaxation constant u (Eq. GL_dimensionless)     */
+    double beta;       /* coefficient of |psi|^2 psi (1 in the paper)      */
+    double ht;         /* time step h_t (Eq. GL_numCN)                     */
+    double By, Bz;     /* field components, yz plane (Eq. B_yz)            */
+    double Jext;       /* applied current along x                          */
+} or_grid;
+
+static inline int64_t idx3(const or_grid *G, int i, int j, int k)
+{
+    return (int64_t)i + (int64_t)G->n[0] * ((int64_t)j + (int64_t)G->n[1] * (int64_t)k);
+}
+
+static inline int axis_active(const or_grid *G, int ax) { return G->n[ax] >= 2; }
+
+/* Coefficient 1/h_a^2, with the 1/g^2 of the z axis (Eq. LaplUV_yz). */
+static inline double axis_coef(const or_grid *G, int ax)
+{
+    double c = 1.0 / (G->h[ax] * G->h[ax]);
+    if (ax == 2) c /= G->g * G->g;
+    return c;
+}
+
+static double box_length(const or_grid *G, int ax)
+{
+    /* h = L/N (periodic) or L/(N-1) (open), Sec. 3 */
+    return G->bc[ax] == OR_PERIODIC ? G->n[ax] * G->h[ax] : (G->n[ax] - 1) * G->h[ax];
+}
+
+/*
+ * Forward link U_{ax}(i,j,k) from site (i,j,k) to its +ax neighbour.
+ * theta != NULL: explicit link phases theta[ax*N + m] (gauge-test mode), times
+ * exp(i hx K) on x links.  theta == NULL: Landau gauge of Eq. A_yz:
+ *   U_x = exp(i hx K)                                 (A~_x = -K)
+ *   U_y(i) = exp(-i hy Bz xbar_i)                     (A~_y = xbar Bz)
+ *   U_z(i) = exp(+i hz By xbar_i)                     (A~_z = -xbar By)
+ * and for periodic x the wrap link from i = Nx-1 to i = 0 carries conj(P_{j,k}),
+ * P_{j,k} = exp(i(-j hy Lx Bz + k hz Lx By)) (Sec. 3.3.1, yz-field paragraph).
+ */
+static cplx link(const or_grid *G, const double *theta, double K, int ax, int i, int j, int k)
+{
+    if (theta) {
+        int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+        cplx U = cexp(I * theta[ax * N + idx3(G, i, j, k)]);
+        if (ax == 0) U *= cexp(I * G->h[0] * K);
+        return U;
+    }
+    double Lx = box_length(G, 0);
+    double xbar = i * G->h[0] - 0.5 * Lx;
+    if (ax == 0) {
+        cplx U = cexp(I * G->h[0] * K);
+        if (G->bc[0] == OR_PERIODIC && i == G->n[0] - 1) {
+            double phase = -j * G->h[1] * Lx * G->Bz + k * G->h[2] * Lx * G->By;
+            U *= cexp(-I * phase);
+        }
+        return U;
+    }
+    if (ax == 1) return cexp(-I * G->h[1] * G->Bz * xbar);
+    return cexp(I * G->h[2] * G->By * xbar);
+}
+
+static inline cplx load(const double *a, int64_t m) { return a[2 * m] + I * a[2 * m + 1]; }
+static inline void store(double *a, int64_t m, cplx v) { a[2 * m] = creal(v); a[2 * m + 1] = cimag(v); }
+
+static void step_index(const or_grid *G, int ax, int sgn, int c[3])
+{
+    c[ax] += sgn;
+    if (c[ax] < 0) c[ax] += G->n[ax];
+    if (c[ax] >= G->n[ax]) c[ax] -= G->n[ax];
+}
+
+/*
+ * Neighbour sum NS_m(psi) = sum over axes of c_a (U_a psi_{m+a} + U*_{a,m-a} psi_{m-a}),
+ * where at an open face the missing neighbour is replaced by the Neumann ghost
+ * (Sec. 3.3.2), which gives 2 c_a U psi_1 at index 0 and 2 c_a U* psi_{N-2}
+ * at index N-1.  The gauge Laplacian of Eq. LaplUV_yz is NS_m - 2 S psi_m
+ * with S = sum_a c_a.
+ */
+static cplx neighbour_sum(const or_grid *G, const double *theta, double K, const double *psi,
+                          int i, int j, int k)
+{
+    cplx acc = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!axis_active(G, ax)) continue;
+        int c0[3] = {i, j, k};
+        int idx = c0[ax];
+        int n = G->n[ax];
+        double c = axis_coef(G, ax);
+        int cp[3] = {i, j, k}, cm[3] = {i, j, k};
+        step_index(G, ax, +1, cp);
+        step_index(G, ax, -1, cm);
+        cplx fwd = link(G, theta, K, ax, i, j, k) * load(psi, idx3(G, cp[0], cp[1], cp[2]));
+        cplx bwd = conj(link(G, theta, K, ax, cm[0], cm[1], cm[2])) * load(psi, idx3(G, cm[0], cm[1], cm[2]));
+        if (G->bc[ax] == OR_PERIODIC) {
+            acc += c * (fwd + bwd);
+        } else if (idx == 0) {
+            acc += 2.0 * c * fwd;
+        } else if (idx == n - 1) {
+            acc += 2.0 * c * bwd;
+        } else {
+            acc += c * (fwd + bwd);
+        }
+    }
+    return acc;
+}
+
+static double sum_coef(const or_grid *G)
+{
+    double S = 0.0;
+    for (int ax = 0; ax < 3; ++ax)
+        if (axis_active(G, ax)) S += axis_coef(G, ax);
+    return S;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public: link phase of the Landau gauge, for building gauge-test links.   */
+/* theta_out[ax*N + m] = arg of the Landau link at K = 0 (unwrapped phase).  */
+/* ------------------------------------------------------------------------ */
+void or_landau_link_phases(const or_grid *G, double *theta_out)
+{
+    int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+    double Lx = box_length(G, 0);
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                double xbar = i * G->h[0] - 0.5 * Lx;
+                double tx = 0.0;
+                if (G->bc[0] == OR_PERIODIC && i == G->n[0] - 1)
+                    tx = -(-j * G->h[1] * Lx * G->Bz + k * G->h[2] * Lx * G->By);
+                theta_out[m] = tx;
+                theta_out[N + m] = -G->h[1] * G->Bz * xbar;
+                theta_out[2 * N + m] = G->h[2] * G->By * xbar;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Init: diagonal M_mm and right-hand side b_m (Sec. 3.1, matrix M, Eq. b),  */
+/* with psi_est = psi^- and no noise.                                       */
+/*   M_mm = 1 + (ht/2)[beta|psi^-|^2 + 2S + i u mu - alpha]                  */
+/*   b_m  = psi^- + (ht/2)[(alpha - i u mu) psi^- - beta|psi^-|^2 psi^-      */
+/*                         + Lap_U psi^-]                                    */
+/* ------------------------------------------------------------------------ */
+void or_init(const or_grid *G, const double *theta, double K, const double *psi_prev,
+             const double *mu, const double *alpha, double *b, double *D)
+{
+    double S = sum_coef(G);
+    double ht2 = 0.5 * G->ht;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                cplx p = load(psi_prev, m);
+                double a2 = creal(p) * creal(p) + cimag(p) * cimag(p);
+                cplx lap = neighbour_sum(G, theta, K, psi_prev, i, j, k) - 2.0 * S * p;
+                cplx Dm = 1.0 + ht2 * (G->beta * a2 + 2.0 * S + I * G->u * mu[m] - alpha[m]);
+                cplx bm = p + ht2 * ((alpha[m] - I * G->u * mu[m]) * p - G->beta * a2 * p + lap);
+                store(D, m, Dm);
+                store(b, m, bm);
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One Jacobi sweep (Eq. final) and the residual of its input iterate        */
+/* (Eq. convergence): r^(l) = b - M psi^(l).                                 */
+/* Off-diagonal entries of M are -(ht/2) times the neighbour coefficients.   */
+/* Returns max_m |r_m|^2.                                                    */
+/* ------------------------------------------------------------------------ */
+double or_sweep(const or_grid *G, const double *theta, double K, const double *psi_in,
+                const double *b, const double *D, double *psi_out)
+{
+    int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+    double ht2 = 0.5 * G->ht;
+    double *r2 = (double *)malloc(sizeof(double) * (size_t)N);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                cplx offdiag = -ht2 * neighbour_sum(G, theta, K, psi_in, i, j, k); /* sum_{m'!=m} M psi */
+                cplx Dm = load(D, m);
+                cplx bm = load(b, m);
+                cplx r = bm - (Dm * load(psi_in, m) + offdiag);
+                store(psi_out, m, (bm - offdiag) / Dm);
+                r2[m] = creal(r) * creal(r) + cimag(r) * cimag(r);
+            }
+    double mx = 0.0;
+    for (int64_t m = 0; m < N; ++m)
+        if (r2[m] > mx) mx = r2[m];
+    free(r2);
+    return mx;
+}
+
+/* Residual b - M psi for a given iterate (for tests). */
+void or_residual(const or_grid *G, const double *theta, double K, const double *psi,
+                 const double *b, const double *D, double *r_out)
+{
+    double ht2 = 0.5 * G->ht;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                cplx offdiag = -ht2 * neighbour_sum(G, theta, K, psi, i, j, k);
+                store(r_out, m, load(b, m) - (load(D, m) * load(psi, m) + offdiag));
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Supercurrent mean along x (Sec. 3.1.1, J_av):                             */
+/*   J_av = 1/(2 N hx) sum_m Im[psi*_m (U_x psi_{i+1} - U*_x psi_{i-1})]     */
+/* Defined for periodic x (the paper's current formulation).                 */
+/* ------------------------------------------------------------------------ */
+double or_javg(const or_grid *G, const double *theta, double K, const double *psi)
+{
+    int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+    double s = 0.0;
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int c[3] = {i, j, k};
+                int cp[3] = {i, j, k}, cm[3] = {i, j, k};
+                step_index(G, 0, +1, cp);
+                step_index(G, 0, -1, cm);
+                cplx p = load(psi, idx3(G, c[0], c[1], c[2]));
+                cplx fwd = link(G, theta, K, 0, i, j, k) * load(psi, idx3(G, cp[0], cp[1], cp[2]));
+                cplx bwd = conj(link(G, theta, K, 0, cm[0], cm[1], cm[2])) * load(psi, idx3(G, cm[0], cm[1], cm[2]));
+                s += cimag(conj(p) * (fwd - bwd));
+            }
+    return s / (2.0 * (double)N * G->h[0]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Right-hand side of the Poisson equation (Sec. 3.2, Eq. Poisson):          */
+/*   f_m = sum_a c_a Im[psi*_m (U_a psi_{m+a} + U*_{a,m-a} psi_{m-a})]       */
+/* i.e. Im[psi*_m NS_m(psi)], with the Neumann ghost at open faces.          */
+/* ------------------------------------------------------------------------ */
+void or_poisson_rhs(const or_grid *G, const double *theta, double K, const double *psi, double *f)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                f[m] = cimag(conj(load(psi, m)) * neighbour_sum(G, theta, K, psi, i, j, k));
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Discrete scalar Laplacian of Sec. 3.2 (left-hand side), with periodic     */
+/* wrap or the Neumann ghost mu_{-1} = mu_1 at open faces.  For tests.       */
+/* ------------------------------------------------------------------------ */
+void or_laplacian_mu(const or_grid *G, const double *mu, double *out)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                double acc = 0.0;
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (!axis_active(G, ax)) continue;
+                    int c0[3] = {i, j, k};
+                    int cp[3] = {i, j, k}, cm[3] = {i, j, k};
+                    step_index(G, ax, +1, cp);
+                    step_index(G, ax, -1, cm);
+                    double vp = mu[idx3(G, cp[0], cp[1], cp[2])];
+                    double vm = mu[idx3(G, cm[0], cm[1], cm[2])];
+                    if (G->bc[ax] == OR_OPEN) {
+                        if (c0[ax] == 0) vm = vp;
+                        if (c0[ax] == G->n[ax] - 1) vp = vm;
+                    }
+                    acc += axis_coef(G, ax) * (vp + vm - 2.0 * mu[m]);
+                }
+                out[m] = acc;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Discrete free energy (the paper refers to F_GL, Sec. 2.1, but does not    */
+/* write its discrete form).  Trapezoid weights w = product of 1/2 per open  */
+/* face the site (or link) lies on, so that dF/dpsi*_m = w_m(-alpha psi +    */
+/* beta|psi|^2 psi - Lap_U psi) dV exactly:                                  */
+/*   F = dV { sum_m w_m[-alpha|psi|^2 + beta/2 |psi|^4]                      */
+/*          + sum_links w_l c_a |U psi_{m+a} - psi_m|^2 }                    */
+/* ------------------------------------------------------------------------ */
+static double face_weight(const or_grid *G, int ax, int idx)
+{
+    if (G->bc[ax] == OR_OPEN && axis_active(G, ax) && (idx == 0 || idx == G->n[ax] - 1)) return 0.5;
+    return 1.0;
+}
+
+double or_energy(const or_grid *G, const double *theta, double K, const double *psi, const double *alpha)
+{
+    double dV = 1.0;
+    for (int ax = 0; ax < 3; ++ax)
+        if (axis_active(G, ax)) dV *= G->h[ax];
+    double F = 0.0;
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int c[3] = {i, j, k};
+                int64_t m = idx3(G, i, j, k);
+                cplx p = load(psi, m);
+                double a2 = creal(p) * creal(p) + cimag(p) * cimag(p);
+                double w = face_weight(G, 0, i) * face_weight(G, 1, j) * face_weight(G, 2, k);
+                F += w * (-alpha[m] * a2 + 0.5 * G->beta * a2 * a2);
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (!axis_active(G, ax)) continue;
+                    if (G->bc[ax] == OR_OPEN && c[ax] == G->n[ax] - 1) continue; /* no link beyond the face */
+                    int cp[3] = {i, j, k};
+                    step_index(G, ax, +1, cp);
+                    double wl = 1.0;
+                    for (int o = 0; o < 3; ++o)
+                        if (o != ax) wl *= face_weight(G, o, c[o]);
+                    cplx d = link(G, theta, K, ax, i, j, k) * load(psi, idx3(G, cp[0], cp[1], cp[2])) - p;
+                    F += wl * axis_coef(G, ax) * (creal(d) * creal(d) + cimag(d) * cimag(d));
+                }
+            }
+    return F * dV;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vortex winding of xy plaquettes.  theta_ab = arg(psi*_a U_ab psi_b) in     */
+/* (-pi, pi]; n_p = round((sum of the four theta + hx hy Bz) / 2 pi).        */
+/* Writes per-plaquette integers (Nx*Ny*Nz, zero where no plaquette exists). */
+/* Returns the signed total.                                                 */
+/* ------------------------------------------------------------------------ */
+int64_t or_winding(const or_grid *G, const double *theta, double K, const double *psi, int32_t *n_out)
+{
+    int nx = G->n[0], ny = G->n[1], nz = G->n[2];
+    double flux = G->h[0] * G->h[1] * G->Bz;
+    int64_t total = 0;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                n_out[m] = 0;
+                if (G->bc[0] == OR_OPEN && i == nx - 1) continue;
+                if (G->bc[1] == OR_OPEN && j == ny - 1) continue;
+                int a[3] = {i, j, k};
+                int bb[3] = {i, j, k};
+                step_index(G, 0, +1, bb);
+                int d[3] = {i, j, k};
+                step_index(G, 1, +1, d);
+                int c[3] = {bb[0], bb[1], bb[2]};
+                step_index(G, 1, +1, c);
+                cplx pa = load(psi, idx3(G, a[0], a[1], a[2]));
+                cplx pb = load(psi, idx3(G, bb[0], bb[1], bb[2]));
+                cplx pc = load(psi, idx3(G, c[0], c[1], c[2]));
+                cplx pd = load(psi, idx3(G, d[0], d[1], d[2]));
+                double t_ab = carg(conj(pa) * link(G, theta, K, 0, a[0], a[1], a[2]) * pb);
+                double t_bc = carg(conj(pb) * link(G, theta, K, 1, bb[0], bb[1], bb[2]) * pc);
+                double t_cd = carg(conj(pc) * conj(link(G, theta, K, 0, d[0], d[1], d[2])) * pd);
+                double t_da = carg(conj(pd) * conj(link(G, theta, K, 1, a[0], a[1], a[2])) * pa);
+                double w = (t_ab + t_bc + t_cd + t_da + flux) / (2.0 * M_PI);
+                int32_t np = (int32_t)floor(w + 0.5);
+                n_out[m] = np;
+                total += np;
+            }
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inclusion pattern generator (Sec. 3.4).  Candidates are consumed in      */
+/* order; a site at r = (i hx, j hy, k hz) is inside candidate n when        */
+/*   q = d^T R diag(a^-2) R^T d <= 1,  d = r - c,                             */
+/* with the minimum-image convention d -= L floor(d/L + 1/2) on periodic     */
+/* axes.  R is the rotation of the unit quaternion (q0,q1,q2,q3).  A site is */
+/* marked by the first candidate that contains it; candidates are added      */
+/* until at least `target` sites are marked (target <= 0: use all).          */
+/* alpha = alpha_in on marked sites, alpha_out elsewhere.                    */
+/* Returns the number of candidates used; *marked receives the site count.   */
+/* ------------------------------------------------------------------------ */
+static void quat_to_rot(const double q[4], double R[3][3])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - w * z);
+    R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y);
+    R[2][1] = 2.0 * (y * z + w * x);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static double inside_q(const or_grid *G, const double *inc, int i, int j, int k)
+{
+    double r[3] = {i * G->h[0], j * G->h[1], k * G->h[2]};
+    double d[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        d[ax] = r[ax] - inc[ax];
+        if (G->bc[ax] == OR_PERIODIC) {
+            double L = G->n[ax] * G->h[ax];
+            d[ax] -= L * floor(d[ax] / L + 0.5);
+        }
+    }
+    double R[3][3];
+    quat_to_rot(inc + 6, R);
+    double q = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        /* body-frame coordinate: column a of R dotted with d */
+        double e = R[0][a] * d[0] + R[1][a] * d[1] + R[2][a] * d[2];
+        double s = e / inc[3 + a];
+        q += s * s;
+    }
+    return q;
+}
+
+int64_t or_pattern(const or_grid *G, const double *incl, int64_t n_incl, int64_t target,
+                   double alpha_in, double alpha_out, double *alpha, int64_t *marked_out)
+{
+    int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+    unsigned char *mark = (unsigned char *)calloc((size_t)N, 1);
+    int64_t marked = 0, used = 0;
+    for (int64_t n = 0; n < n_incl; ++n) {
+        if (target > 0 && marked >= target) break;
+        const double *inc = incl + 10 * n;
+        double rmax = inc[3];
+        if (inc[4] > rmax) rmax = inc[4];
+        if (inc[5] > rmax) rmax = inc[5];
+        int lo[3], hi[3];
+        for (int ax = 0; ax < 3; ++ax) {
+            lo[ax] = (int)ceil((inc[ax] - rmax) / G->h[ax]);
+            hi[ax] = (int)floor((inc[ax] + rmax) / G->h[ax]);
+            if (G->bc[ax] == OR_OPEN) {
+                if (lo[ax] < 0) lo[ax] = 0;
+                if (hi[ax] > G->n[ax] - 1) hi[ax] = G->n[ax] - 1;
+            } else if (hi[ax] - lo[ax] + 1 > G->n[ax]) {
+                lo[ax] = 0;
+                hi[ax] = G->n[ax] - 1;
+            }
+        }
+        for (int kk = lo[2]; kk <= hi[2]; ++kk)
+            for (int jj = lo[1]; jj <= hi[1]; ++jj)
+                for (int ii = lo[0]; ii <= hi[0]; ++ii) {
+                    int i = ((ii % G->n[0]) + G->n[0]) % G->n[0];
+                    int j = ((jj % G->n[1]) + G->n[1]) % G->n[1];
+                    int k = ((kk % G->n[2]) + G->n[2]) % G->n[2];
+                    int64_t m = idx3(G, i, j, k);
+                    if (mark[m]) continue;
+                    if (inside_q(G, inc, i, j, k) <= 1.0) {
+                        mark[m] = 1;
+                        ++marked;
+                    }
+                }
+        used = n + 1;
+    }
+    for (int64_t m = 0; m < N; ++m) alpha[m] = mark[m] ? alpha_in : alpha_out;
+    free(mark);
+    if (marked_out) *marked_out = marked;
+    return used;
+}
+
+/* Plain inside test value q for one site and one inclusion (for tests). */
+double or_inside_q(const or_grid *G, const double *inc, int i, int j, int k)
+{
+    return inside_q(G, inc, i, j, k);
+}
