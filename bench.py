@@ -1,0 +1,346 @@
+"""Benchmark of the implicit TDGL time step on GB300.
+
+Workload (default): the 512 x 512 x 256 mesoscopic sample -- open x, periodic
+y and z, Bz = 0.2, random ellipsoidal inclusions (semi-axes U[1.5, 5] xi,
+random orientation) to 10 % volume, alpha = +1 / -1, one increment of the
+current sweep (J = 0.025), h = 0.5, h_t = 0.1, eps = 1e-6.  Synthetic seeded
+inputs; the state is relaxed for a number of untimed steps before timing.
+
+A step is one full time step: fused init + Jacobi sweeps to convergence
+(residual reductions included), voltage, Poisson right-hand side, multigrid
+V-cycles and zero-mode projection.  `value` is Jacobi site-updates per second
+over whole steps (Gsite-iter/s), inputs resident in HBM; each array (512 MiB
+per complex64 field) is far larger than the 129 MB L2, so no flush is needed.
+
+Multi-GPU: every rank advances its own replica (weak scaling, no collective on
+the data path); value = all ranks' site-updates / max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, each
+step being one oracle time step on a bounded slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsite-iter/s"
+BYTES_PER_SITE_ITER = 32          # read psi 8 + b 8 + D 8, write psi 8
+SLAB_NZ = 8                       # CPU sample: full x-y extent, 8 z planes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--relax", type=int, default=150, help="untimed steps from the random start")
+    ap.add_argument("--J", type=float, default=0.025)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    src = os.path.join(ROOT, "paper_1409_8340_gb300", "csrc", "k_jacobi.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def traffic_from_profile():
+    """dram bytes per sweep launch from the committed ncu summary, if it was taken
+    on the current sweep kernel source; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        for line in open(self.file.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[6:10]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        pw = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# workload construction
+# ---------------------------------------------------------------------------
+def workload(J: float, nz_override: int | None = None):
+    from paper_1409_8340_gb300 import inputs
+    from paper_1409_8340_gb300.presets import mesoscopic_512x512x256
+    w = mesoscopic_512x512x256(J)
+    if nz_override is not None:
+        p = w.params
+        p.nz = nz_override
+        box = (p.length(0), p.length(1), p.length(2))
+        count = max(200, int(w.candidates.shape[0] * nz_override / 256))
+        w.candidates = inputs.ellipsoids(count, box, 1.5, 5.0, seed=w.seed)
+        w.target_sites = inputs.target_sites(0.10, p.N)
+    return w
+
+
+def cpu_oracle_run(J: float, budget_s: float, max_steps: int | None = None):
+    """Time the FP64 oracle on the slab sample.  Returns (value, info)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_1409_8340_gb300 import inputs
+    w = workload(J, SLAB_NZ)
+    p = w.params
+    G = O.Grid(p.nx, p.ny, p.nz, hx=p.hx, hy=p.hy, hz=p.hz, bc=tuple(p.bc), Bz=p.Bz, Jext=p.Jext, ht=p.ht)
+    alpha, _, _ = O.pattern(G, w.candidates, w.target_sites, w.alpha_in, w.alpha_out)
+    st = O.State(inputs.random_psi(p.nx, p.ny, p.nz, w.seed), np.zeros(p.shape))
+    O.step(G, st, alpha, eps=p.eps)            # one untimed step (first-touch, build)
+    t0 = time.perf_counter()
+    sweeps = steps = 0
+    while True:
+        s = O.step(G, st, alpha, eps=p.eps)
+        sweeps += s.sweeps
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= budget_s):
+            break
+    value = sweeps * p.N / el / 1e9
+    info = {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{steps} FP64 oracle time steps ({sweeps} Jacobi sweeps) on a {p.nx}x{p.ny}x{p.nz} slab of "
+                      f"the 512x512x256 workload (same h, BCs, field, current, inclusion recipe); "
+                      f"{el:.1f} s wall, OpenMP threads = {O.threads()}"}
+    return value, info, el, steps, sweeps
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    # warmup steps, then K timed steps (each one oracle step on the slab sample)
+    cpu_oracle_run(args.J, 0.0, max_steps=max(1, args.warmup))
+    value, info, el, steps, sweeps = cpu_oracle_run(args.J, 0.0, max_steps=args.steps)
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"mesoscopic_512x512x256 (CPU slab nz={SLAB_NZ})",
+                                            "J": args.J, "grid": [512, 512, SLAB_NZ]},
+            "cpu_baseline": info,
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1409_8340_gb300 import build as B
+    from paper_1409_8340_gb300 import inputs
+    from paper_1409_8340_gb300.solver import Solver, pattern
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workload(args.J)
+    p = w.params
+    alpha, used, marked = pattern(p, w.candidates, w.target_sites, w.alpha_in, w.alpha_out, device=dev)
+    psi0 = inputs.random_psi(p.nx, p.ny, p.nz, w.seed + rank).astype(np.complex64)
+    s = Solver(p, alpha)
+    s.set_state(torch.as_tensor(psi0))
+    s.step(args.relax)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.profile_enable(True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    s.profile_enable(False)
+    clk = clocks.stop()
+    obs = s.observables()
+
+    site_iters = prof["sweeps"] * p.N
+    t = torch.tensor([ms, float(site_iters)], dtype=torch.float64, device=dev)
+    if dist:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_max, total_iters = float(tmax[0]), float(tsum[1])
+    else:
+        ms_max, total_iters = ms, float(site_iters)
+    value = total_iters / (ms_max * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the Jacobi sweep (sweeps 2..n of each step)
+    n_plain = prof["sweeps"] - prof["steps"]
+    avg_sweep_ms = prof["ms_sweeps"] / max(1, n_plain)
+    bytes_per_launch = BYTES_PER_SITE_ITER * p.N
+    achieved = bytes_per_launch / (avg_sweep_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    implicit_ms = prof["ms_init"] + prof["ms_sweeps"]
+
+    # end to end through the C ABI with pinned host buffers: upload, step, download
+    host_psi = torch.empty(p.shape, dtype=torch.complex64).pin_memory()
+    host_mu = torch.empty(p.shape, dtype=torch.float32).pin_memory()
+    _, _, K_now = s.download_state(host_psi, host_mu)
+    e2e_value = None
+    if args.e2e_steps > 0:
+        # each step: H2D of the state from pinned memory, one time step, D2H of the new state
+        s.profile_enable(True)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s.upload_state(host_psi, host_mu, K_now)
+            s.step(1)
+            _, _, K_now = s.download_state(host_psi, host_mu)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        pe = s.profile()
+        s.profile_enable(False)
+        e2e_iters = pe["sweeps"] * p.N
+        e2e_value = e2e_iters * world / e2e_s / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, cpu, _, _, _ = cpu_oracle_run(args.J, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "mesoscopic_512x512x256", "grid": [p.nx, p.ny, p.nz], "sites": p.N,
+                       "bc": "open x, periodic y z", "Bz": p.Bz, "J": p.Jext, "h": p.hx, "ht": p.ht, "eps": p.eps,
+                       "inclusions": {"kind": "ellipsoids", "used": used, "sites": marked,
+                                      "fraction": marked / p.N},
+                       "relax_steps": args.relax, "poisson_cycles": p.poisson_cycles,
+                       "l2": "inputs larger than L2 (512 MiB per complex64 array vs 129 MB L2); no flush",
+                       "parallelism": f"replicas x{world}"},
+            "sweeps_per_step": prof["sweeps"] / max(1, prof["steps"]),
+            "phase_ms_per_step": {"init_sweep": prof["ms_init"] / args.steps,
+                                  "sweeps": prof["ms_sweeps"] / args.steps, "K": prof["ms_K"] / args.steps,
+                                  "poisson": prof["ms_poisson"] / args.steps},
+            "implicit_step_gsite_iter_s": site_iters / (implicit_ms * 1e-3) / 1e9 if implicit_ms > 0 else None,
+            "roofline": {"kernel": "sweep_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                         "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_sweep_ms,
+                         "traffic": traffic_from_profile()},
+            "e2e": {"value": e2e_value, "unit": METRIC, "steps": args.e2e_steps,
+                    "h2d_bytes_per_step": 12 * p.N, "d2h_bytes_per_step": 12 * p.N + 128},
+            "gpu_launches": prof["kernel_launches"],
+            "clocks": clk,
+            "observables": {"Ex": obs["Ex"], "psi2_mean": obs["psi2_mean"],
+                            "vortex_unsigned_per_layer": obs["vortex_unsigned"], "last_sweeps": obs["last_sweeps"]},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_native(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * tdgl.h -- C ABI of the GB300 implicit TDGL solver.
+ *
+ * The solver advances the complex order parameter psi of the dimensionless
+ * time-dependent Ginzburg-Landau equation (arXiv:1409.8340, Sec. 2, Eq.
+ * GL_dimensionless with the external-current gauge of Eq. GL_external_current)
+ * on an Nx x Ny x Nz grid, together with the scalar potential mu (Eq. Poisson)
+ * and the phase-gradient variable K (Eq. K_ODE).  Each time step is the
+ * Crank-Nicolson step of Eq. GL_numCN, linearised with |psi_est|^2 = |psi^-|^2,
+ * solved by Jacobi iteration (Eq. final) to the squared max-norm tolerance of
+ * Eq. convergence; then K (periodic x) and mu are updated (Sec. 3, order psi,
+ * K, mu).
+ *
+ * Conventions for every entry point:
+ *   - Return value: TDGL_OK (0) or a negative TDGL_ERR_* code.  No exception
+ *     crosses the ABI.  tdgl_error_string() names a code.
+ *   - Grid index m = i + Nx*(j + Ny*k), x fastest (Sec. 3).  Complex arrays
+ *     are interleaved float pairs (re, im) = 8 bytes per site.
+ *   - Device memory is owned by the caller.  The library never allocates
+ *     device memory: tdgl_create() carves its arrays out of a caller-provided
+ *     workspace of tdgl_workspace_bytes() bytes, and the caller keeps it alive
+ *     until tdgl_destroy().  The handle itself is a small host object.
+ *   - All work is enqueued on the stream given at creation (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream).  Entry points that return
+ *     host-visible results synchronise that stream; the others are asynchronous.
+ *   - A handle is used by one host thread and one stream at a time.
+ *   - After TDGL_ERR_NOT_CONVERGED or TDGL_ERR_NONFINITE from a step, the
+ *     state (psi, mu, K) is left at the last completed step.
+ */
+#ifndef TDGL_H
+#define TDGL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TDGL_OK 0
+#define TDGL_ERR_INVALID_ARG (-1)
+#define TDGL_ERR_NOT_CONVERGED (-2)
+#define TDGL_ERR_NONFINITE (-3)
+#define TDGL_ERR_TIMEOUT (-4)
+#define TDGL_ERR_CUDA (-5)
+#define TDGL_ERR_WORKSPACE (-6)
+
+#define TDGL_PERIODIC 0
+#define TDGL_OPEN 1
+
+#define TDGL_LINKS_LANDAU 0   /* yz-plane field, Landau gauge A = xbar [0, Bz, -By] (Eq. A_yz) */
+#define TDGL_LINKS_GENERAL 1  /* explicit per-link phases (gauge tests)                         */
+
+/*
+ * Problem description.
+ *   nx, ny, nz      grid points per axis (nx, ny >= 2; nz >= 1, nz = 1 is a film).
+ *   bc[3]           TDGL_PERIODIC or TDGL_OPEN per axis (Sec. 3.3).  Periodic x
+ *                   with a field uses the quasi-periodic wrap phase of Sec. 3.3.1;
+ *                   periodic x and y then require Bz Lx Ly = 2 pi n_z, periodic x
+ *                   and z require By Lx Lz = 2 pi n_y (flux quantisation).
+ *   hx, hy, hz      grid spacings in units of xi_0 (L = N h periodic, (N-1) h open).
+ *   g               anisotropy: z derivatives carry 1/g^2 (Sec. 2.1).
+ *   u, beta         u of Eq. GL_dimensionless (absorbed into ht as in the
+ *                   footnote of Eq. GL_numCN) and the |psi|^2 psi coefficient.
+ *   ht              time step h_t.
+ *   By, Bz          field in the yz plane, units of H_c2(0) (Eq. B_yz).
+ *   Jext            applied current along x.  Periodic x: enters through the K
+ *                   ODE (Eq. K_ODE).  Open x: injected as normal current through
+ *                   the x faces via the Neumann condition d(mu)/dx = -Jext.
+ *   eps             Jacobi tolerance on max_m |r_m|^2 (Eq. convergence).
+ *   max_iter        sweep cap per step; exceeding it is TDGL_ERR_NOT_CONVERGED.
+ *   check_every     convergence is tested after every check_every-th sweep
+ *                   (1 = the paper's per-sweep test).
+ *   fixed_sweeps    > 0: run exactly this many sweeps per step, no test.
+ *   freeze_mu_K     1: keep mu and K fixed (no K ODE, no Poisson solve).
+ *   poisson_cycles  multigrid V-cycles per step (>= 1).
+ *   poisson_tol     > 0: keep cycling (up to poisson_max_cycles) until
+ *                   max|F - Lap mu| <= poisson_tol * max|F|.
+ *   links_mode      TDGL_LINKS_LANDAU or TDGL_LINKS_GENERAL.
+ *   d_alpha         device f32[N], eps(r) of Eq. epsilon (caller-owned, read-only
+ *                   for the handle's lifetime).
+ *   d_link_phase    device f32[3N] link phases theta_{a,m} of the link from m to
+ *                   m+a (general mode only; NULL otherwise).  The x links are
+ *                   further multiplied by exp(i hx K).
+ */
+typedef struct tdgl_config {
+    int32_t nx, ny, nz;
+    int32_t bc[3];
+    double hx, hy, hz;
+    double g, u, beta, ht;
+    double By, Bz;
+    double Jext;
+    double eps;
+    int32_t max_iter;
+    int32_t check_every;
+    int32_t fixed_sweeps;
+    int32_t freeze_mu_K;
+    int32_t poisson_cycles;
+    int32_t poisson_max_cycles;
+    double poisson_tol;
+    int32_t links_mode;
+    int32_t reserved0;
+    const float *d_alpha;
+    const float *d_link_phase;
+} tdgl_config;
+
+typedef struct tdgl_handle tdgl_handle;
+
+/* Observables (Sec. 2.1 Eq. J, Sec. 3.1.1 J_av, Sec. 2.2 K and E_x).  energy is the
+ * discrete GL free energy with trapezoid face weights; vortices come from the
+ * winding of xy plaquettes (arg of psi*_a U_ab psi_b summed with the plaquette
+ * flux hx hy Bz).  FP64 accumulations. */
+typedef struct tdgl_obs {
+    double psi2_mean;        /* (1/N) sum |psi|^2                                     */
+    double energy;           /* free energy                                            */
+    double javg;             /* J_av of the last step (periodic x), else 0             */
+    double K;                /* current K                                              */
+    double Ex;               /* electric field of the last step                        */
+    double vortex_unsigned;  /* sum_p |n_p| per z layer, averaged over layers          */
+    double vortex_signed;    /* sum_p n_p per z layer, averaged over layers            */
+    double last_r2;          /* max |r|^2 at the last convergence test                 */
+    double poisson_res;      /* max|F - Lap mu| / max|F| after the last Poisson solve  */
+    int32_t last_sweeps;     /* Jacobi sweeps of the last step                         */
+    int32_t poisson_cycles;  /* V-cycles of the last step                              */
+    int64_t step;            /* completed time steps                                   */
+} tdgl_obs;
+
+/* Device pointers into the handle's workspace (valid until tdgl_destroy). */
+typedef struct tdgl_state_ptrs {
+    float *psi;   /* complex64[N], current psi^n                  */
+    float *mu;    /* f32[N], current mu^n                         */
+    float *b;     /* complex64[N], b of the last step (Eq. b)     */
+    float *D;     /* complex64[N], diag M of the last step        */
+    float *f;     /* f32[N], Poisson right-hand side, last step   */
+} tdgl_state_ptrs;
+
+/* Per-phase device time (CUDA events on the handle's stream, summed over steps
+ * since tdgl_profile_enable) and host-side launch counters.  ms_sweeps covers
+ * only the batches of Jacobi sweeps (host gaps between batches excluded);
+ * launches that found the solve already converged return immediately and are
+ * counted in sweep_launches but not in sweeps. */
+typedef struct tdgl_profile {
+    double ms_init;          /* fused init + first sweep                        */
+    double ms_sweeps;        /* Jacobi sweeps 2..n                              */
+    double ms_K;             /* J_av and the K ODE                              */
+    double ms_poisson;       /* right-hand side, V-cycles, projection, voltage  */
+    int64_t steps;           /* time steps                                      */
+    int64_t sweeps;          /* Jacobi sweeps that did work, all steps          */
+    int64_t sweep_launches;  /* sweep kernels launched (after the init sweep)   */
+    int64_t kernel_launches; /* every kernel launch of the library              */
+    int64_t vcycles;         /* multigrid V-cycles                              */
+} tdgl_profile;
+
+const char *tdgl_error_string(int code);
+
+/* Bytes of device workspace tdgl_create() needs for cfg (0 if cfg is invalid). */
+size_t tdgl_workspace_bytes(const tdgl_config *cfg);
+
+/* Validate cfg, carve the workspace (d_workspace must be 256-byte aligned and
+ * ws_bytes >= tdgl_workspace_bytes(cfg)), build link tables on the device and
+ * set psi = 0, mu = 0, K = 0.  Synchronises the stream before returning. */
+int tdgl_create(const tdgl_config *cfg, void *d_workspace, size_t ws_bytes, void *stream, tdgl_handle **out);
+
+void tdgl_destroy(tdgl_handle *h);
+
+/* Copy a state in from DEVICE arrays (psi complex64[N], mu f32[N] or NULL = 0). */
+int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double K);
+
+/* Copy a state in from / out to HOST arrays (pinned or pageable). */
+int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_mu, double K);
+int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double *K);
+
+int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out);
+
+/* Advance n_steps full time steps (psi, K, mu).  Synchronises once per step to
+ * read the convergence status; returns the first error met. */
+int tdgl_step(tdgl_handle *h, int n_steps);
+
+/* Only the implicit psi solve of one step (init, Jacobi sweeps, residual
+ * reductions), without the K and mu updates; *sweeps_out may be NULL. */
+int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out);
+
+/* Only the Poisson solve for the current psi and K (right-hand side, V-cycles,
+ * zero-mode projection). */
+int tdgl_solve_mu(tdgl_handle *h);
+
+/* Start (on != 0) or stop collecting tdgl_profile data; enabling resets it. */
+int tdgl_profile_enable(tdgl_handle *h, int on);
+int tdgl_profile_read(tdgl_handle *h, tdgl_profile *out);
+
+/* Compute observables of the current state (synchronises). */
+int tdgl_observables(tdgl_handle *h, tdgl_obs *out);
+
+/*
+ * Inclusion pattern generator (Sec. 3.4), standalone.  Candidates (host array,
+ * 10 doubles each: centre cx cy cz, semi-axes a b c, unit quaternion q0..q3 of
+ * the body rotation) are consumed in order; a site r = (i hx, j hy, k hz) lies
+ * inside candidate n when d^T R diag(a^-2) R^T d <= 1, d = r - c with the
+ * minimum-image convention on periodic axes, evaluated in FP64.  A site belongs
+ * to the first candidate containing it; candidates are added until at least
+ * target_sites sites are inside (target_sites <= 0: all candidates).
+ * d_alpha[m] = alpha_in inside, alpha_out elsewhere.  Only nx..nz, bc and h of
+ * grid are read.  d_scratch: device bytes >= tdgl_pattern_scratch_bytes().
+ * Synchronises; *n_used and *n_marked (may be NULL) receive the counts.
+ */
+size_t tdgl_pattern_scratch_bytes(const tdgl_config *grid, int64_t n_candidates);
+int tdgl_pattern(const tdgl_config *grid, const double *host_candidates, int64_t n_candidates,
+                 int64_t target_sites, float alpha_in, float alpha_out, float *d_alpha,
+                 void *d_scratch, size_t scratch_bytes, void *stream, int64_t *n_used, int64_t *n_marked);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDGL_H */

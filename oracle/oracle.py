@@ -91,6 +91,7 @@ def lib():
         L.or_pattern.restype = ctypes.c_int64
         L.or_inside_q.argtypes = [gp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_inside_q.restype = d
+        L.or_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -154,6 +155,11 @@ def _theta_ptr(theta):
 # --------------------------------------------------------------------------
 # Elementary operations (thin wrappers over the C routines)
 # --------------------------------------------------------------------------
+def threads() -> int:
+    """OpenMP threads used by the C loops."""
+    return int(lib().or_threads())
+
+
 def landau_link_phases(G: Grid) -> np.ndarray:
     th = np.zeros((3,) + G.shape, dtype=np.float64)
     lib().or_landau_link_phases(ctypes.byref(G.c()), _dp(th))

@@ -495,3 +495,16 @@ double or_inside_q(const or_grid *G, const double *inc, int i, int j, int k)
 {
     return inside_q(G, inc, i, j, k);
 }
+
+/* Number of OpenMP threads the oracle's parallel loops use (for reporting). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

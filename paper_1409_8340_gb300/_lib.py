@@ -1,0 +1,124 @@
+"""ctypes binding of libtdgl_gb300.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/tdgl.h.  There
+is no fallback: if the CUDA library is missing or cannot be loaded, loading
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtdgl_gb300.so")
+
+PERIODIC = 0
+OPEN = 1
+LINKS_LANDAU = 0
+LINKS_GENERAL = 1
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "not converged", -3: "non-finite residual", -4: "timeout",
+          -5: "CUDA error", -6: "workspace"}
+
+
+class TdglError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, 'unknown')} ({code})")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("bc", ctypes.c_int32 * 3),
+        ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
+        ("g", ctypes.c_double), ("u", ctypes.c_double), ("beta", ctypes.c_double), ("ht", ctypes.c_double),
+        ("By", ctypes.c_double), ("Bz", ctypes.c_double),
+        ("Jext", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("check_every", ctypes.c_int32),
+        ("fixed_sweeps", ctypes.c_int32),
+        ("freeze_mu_K", ctypes.c_int32),
+        ("poisson_cycles", ctypes.c_int32),
+        ("poisson_max_cycles", ctypes.c_int32),
+        ("poisson_tol", ctypes.c_double),
+        ("links_mode", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("d_alpha", ctypes.c_void_p),
+        ("d_link_phase", ctypes.c_void_p),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("psi2_mean", ctypes.c_double), ("energy", ctypes.c_double), ("javg", ctypes.c_double),
+        ("K", ctypes.c_double), ("Ex", ctypes.c_double),
+        ("vortex_unsigned", ctypes.c_double), ("vortex_signed", ctypes.c_double),
+        ("last_r2", ctypes.c_double), ("poisson_res", ctypes.c_double),
+        ("last_sweeps", ctypes.c_int32), ("poisson_cycles", ctypes.c_int32), ("step", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class StatePtrs(ctypes.Structure):
+    _fields_ = [("psi", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("D", ctypes.c_void_p), ("f", ctypes.c_void_p)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms_init", ctypes.c_double), ("ms_sweeps", ctypes.c_double), ("ms_K", ctypes.c_double),
+                ("ms_poisson", ctypes.c_double), ("steps", ctypes.c_int64), ("sweeps", ctypes.c_int64),
+                ("sweep_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("vcycles", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "tdgl_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tdgl_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config)]),
+    "tdgl_create": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "tdgl_destroy": (None, [_P]),
+    "tdgl_set_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "tdgl_upload_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "tdgl_download_state": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "tdgl_get_state": (ctypes.c_int, [_P, ctypes.POINTER(StatePtrs)]),
+    "tdgl_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tdgl_solve_psi": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "tdgl_solve_mu": (ctypes.c_int, [_P]),
+    "tdgl_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),
+    "tdgl_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tdgl_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "tdgl_pattern_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64]),
+    "tdgl_pattern": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+                                    ctypes.c_float, _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises OSError when it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"CUDA library not built: {path} (run paper_1409_8340_gb300/build.py)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code: int, where: str):
+    if code != 0:
+        raise TdglError(code, where)

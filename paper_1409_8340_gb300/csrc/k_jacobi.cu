@@ -1,0 +1,352 @@
+// Implicit psi step: fused init (b, diag M) + first Jacobi sweep, and the
+// Jacobi sweep with its residual (arXiv:1409.8340, Sec. 3.1: matrix M, Eq. b,
+// Eq. final, Eq. convergence).
+//
+// Layout: psi, b, D are complex64 arrays, x fastest.  A block of 32 x 8 threads
+// owns a 32 x 8 column of the xy plane and marches along z over KZ planes,
+// keeping psi(k-1), psi(k), psi(k+1) in registers; x and y neighbours come
+// from global memory through L1.  Every sweep also forms r = b - M psi for its
+// input iterate and reduces max |r|^2 per block; the last block to finish
+// reduces the block maxima and updates the device control block (sweep count,
+// convergence flag, result buffer).  Sweeps launched after convergence exit at
+// their first instruction, so the host can enqueue several sweeps ahead.
+#include <float.h>
+
+#include "tdgl_internal.cuh"
+
+namespace tdgl {
+
+constexpr int kBX = 32;
+constexpr int kBY = 8;
+
+static int zchunk(const DevGrid &g)
+{
+    long long bxy = (long long)((g.nx + kBX - 1) / kBX) * ((g.ny + kBY - 1) / kBY);
+    long long kz = (bxy * g.nz) / 2432;
+    if (kz < 1) kz = 1;
+    if (kz > 32) kz = 32;
+    return (int)kz;
+}
+
+int sweep_blocks(const DevGrid &g)
+{
+    int kz = zchunk(g);
+    return ((g.nx + kBX - 1) / kBX) * ((g.ny + kBY - 1) / kBY) * ((g.nz + kz - 1) / kz);
+}
+
+__device__ __forceinline__ float2 wrap_phase(const DevGrid &g, int j, int k)
+{
+    return cmul(g.Py[j], g.Pz[k]);
+}
+
+// x and y parts of the neighbour sum NS_m (the off-diagonal part of the gauge
+// Laplacian of Eq. LaplUV_yz, with the Neumann ghosts of Sec. 3.3.2 at open
+// faces and the quasi-periodic wrap phase of Sec. 3.3.1 on the x wrap link).
+template <bool GEN>
+__device__ __forceinline__ float2 ns_xy(const DevGrid &g, const float2 *__restrict__ psi, int i, int j, int k,
+                                        long long m, float2 Ux)
+{
+    float2 fwd = cmk(0.f, 0.f), bwd = cmk(0.f, 0.f);
+    const bool lo = (i == 0), hi = (i == g.nx - 1);
+    const bool per = (g.bcx == kPeriodic);
+    if (!hi || per) {
+        long long mp = hi ? m - (g.nx - 1) : m + 1;
+        float2 U = GEN ? cmul(Ux, g.L[m]) : Ux;
+        if (!GEN && hi) U = cmulc(wrap_phase(g, j, k), U);
+        fwd = cmul(U, psi[mp]);
+    }
+    if (!lo || per) {
+        long long mm = lo ? m + (g.nx - 1) : m - 1;
+        float2 U = GEN ? cmul(Ux, g.L[mm]) : Ux;
+        if (!GEN && lo) U = cmulc(wrap_phase(g, j, k), U);
+        bwd = cmulc(U, psi[mm]);
+    }
+    float2 tx;
+    if (per) tx = cadd(fwd, bwd);
+    else tx = lo ? cscale(2.f, fwd) : (hi ? cscale(2.f, bwd) : cadd(fwd, bwd));
+
+    const long long sy = g.nx;
+    const bool ylo = (j == 0), yhi = (j == g.ny - 1);
+    const bool yper = (g.bcy == kPeriodic);
+    float2 fy = cmk(0.f, 0.f), by = cmk(0.f, 0.f);
+    if (!yhi || yper) {
+        long long mp = yhi ? m - (long long)(g.ny - 1) * sy : m + sy;
+        float2 U = GEN ? g.L[g.N + m] : g.Uy[i];
+        fy = cmul(U, psi[mp]);
+    }
+    if (!ylo || yper) {
+        long long mm = ylo ? m + (long long)(g.ny - 1) * sy : m - sy;
+        float2 U = GEN ? g.L[g.N + mm] : g.Uy[i];
+        by = cmulc(U, psi[mm]);
+    }
+    float2 ty;
+    if (yper) ty = cadd(fy, by);
+    else ty = ylo ? cscale(2.f, fy) : (yhi ? cscale(2.f, by) : cadd(fy, by));
+    return cadd(cscale(g.cx, tx), cscale(g.cy, ty));
+}
+
+// z part from register-held neighbours.
+template <bool GEN>
+__device__ __forceinline__ float2 ns_z(const DevGrid &g, int i, int k, long long m, float2 pzm, float2 pzp)
+{
+    if (g.nz < 2) return cmk(0.f, 0.f);
+    const long long sz = (long long)g.nx * g.ny;
+    const bool lo = (k == 0), hi = (k == g.nz - 1);
+    const bool per = (g.bcz == kPeriodic);
+    float2 Uf, Ub;
+    if (GEN) {
+        Uf = g.L[2 * g.N + m];
+        long long mm = lo ? m + (long long)(g.nz - 1) * sz : m - sz;
+        Ub = g.L[2 * g.N + mm];
+    } else {
+        Uf = g.Uz[i];
+        Ub = Uf;
+    }
+    float2 fwd = cmul(Uf, pzp), bwd = cmulc(Ub, pzm);
+    float2 t;
+    if (per) t = cadd(fwd, bwd);
+    else t = lo ? cscale(2.f, fwd) : (hi ? cscale(2.f, bwd) : cadd(fwd, bwd));
+    return cscale(g.cz, t);
+}
+
+__device__ __forceinline__ void finish_sweep(const SweepArgs &a, float bmax, bool init)
+{
+    __shared__ float shf[32];
+    __shared__ int flag;
+    float m = block_max(bmax, shf);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (tid == 0) a.blockred[bid] = (double)m;
+    if (!last_block(&a.ctl->ticket, nb, &flag)) return;
+    double g = 0.0;
+    for (unsigned int q = tid; q < nb; q += blockDim.x * blockDim.y) {
+        double v = ((volatile double *)a.blockred)[q];
+        g = v > g ? v : g;
+    }
+    float gf = block_max((float)g, shf);
+    if (tid == 0) {
+        DevCtl *c = a.ctl;
+        c->ticket = 0u;
+        int it = init ? 1 : c->iter + 1;
+        if (init) c->status = TDGL_OK;
+        c->iter = it;
+        c->r2 = (double)gf;
+        c->result = a.dst_index;
+        if (!(gf <= FLT_MAX)) {
+            c->status = TDGL_ERR_NONFINITE;
+            c->done = 1;
+        } else if (a.fixed_sweeps > 0) {
+            c->done = (it >= a.fixed_sweeps) ? 1 : 0;
+        } else if ((it % a.check_every) == 0 && (double)gf < a.eps) {
+            c->done = 1;
+        } else if (it >= a.max_iter) {
+            c->status = TDGL_ERR_NOT_CONVERGED;
+            c->done = 1;
+        } else {
+            c->done = 0;
+        }
+    }
+}
+
+// Init (Sec. 3.1, Eq. b and diag M with psi_est = psi^-) fused with the first
+// Jacobi sweep from psi^(0) = psi^-: both need the same neighbour sum of psi^-.
+template <bool GEN>
+__global__ void __launch_bounds__(kBX *kBY) init_sweep_kernel(SweepArgs a, int kz)
+{
+    const DevGrid &g = a.g;
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k0 = blockIdx.z * kz;
+    const int k1 = min(k0 + kz, g.nz);
+    const float2 Ux = a.ctl->Ux;
+    float rmax = 0.f;
+    if (i < g.nx && j < g.ny) {
+        const long long sz = (long long)g.nx * g.ny;
+        const long long base = (long long)i + (long long)g.nx * j;
+        const bool zper = (g.bcz == kPeriodic);
+        float2 pzm = cmk(0.f, 0.f);
+        if (g.nz >= 2) {
+            int kp = (k0 == 0) ? (zper ? g.nz - 1 : 1) : k0 - 1;
+            pzm = a.src[base + kp * sz];
+        }
+        float2 pc = a.src[base + k0 * sz];
+        for (int k = k0; k < k1; ++k) {
+            const long long m = base + k * sz;
+            float2 pzp = cmk(0.f, 0.f);
+            if (g.nz >= 2) {
+                int kn = (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1;
+                pzp = a.src[base + kn * sz];
+            }
+            float2 ns = cadd(ns_xy<GEN>(g, a.src, i, j, k, m, Ux), ns_z<GEN>(g, i, k, m, pzm, pzp));
+            const float a2 = cabs2(pc);
+            const float mu = a.mu[m], al = a.alpha[m];
+            const float2 D = cmk(1.f + g.ht2 * (g.beta * a2 + 2.f * g.S - al), g.ht2 * g.u * mu);
+            // b = p + (ht/2)[(alpha - i u mu) p - beta|p|^2 p + NS - 2 S p]
+            const float cr = al - g.beta * a2 - 2.f * g.S;
+            const float ci = -g.u * mu;
+            const float2 lin = cmk(cr * pc.x - ci * pc.y, cr * pc.y + ci * pc.x);
+            const float2 b = cadd(pc, cscale(g.ht2, cadd(lin, ns)));
+            // first sweep: s = b - sum_{m'!=m} M psi = b + (ht/2) NS
+            const float2 s = cadd(b, cscale(g.ht2, ns));
+            const float2 r = csub(s, cmul(D, pc));
+            const float inv = 1.0f / cabs2(D);
+            const float2 nxt = cscale(inv, cmulc(D, s));
+            a.b[m] = b;
+            a.D[m] = D;
+            a.dst[m] = nxt;
+            float r2 = cabs2(r);
+            r2 = (r2 <= FLT_MAX) ? r2 : INFINITY;
+            rmax = fmaxf(rmax, r2);
+            pzm = pc;
+            pc = pzp;
+        }
+    }
+    finish_sweep(a, rmax, true);
+}
+
+template <bool GEN>
+__global__ void __launch_bounds__(kBX *kBY) sweep_kernel(SweepArgs a, int kz)
+{
+    if (*(volatile int *)&a.ctl->done) return;
+    const DevGrid &g = a.g;
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k0 = blockIdx.z * kz;
+    const int k1 = min(k0 + kz, g.nz);
+    const float2 Ux = a.ctl->Ux;
+    float rmax = 0.f;
+    if (i < g.nx && j < g.ny) {
+        const long long sz = (long long)g.nx * g.ny;
+        const long long base = (long long)i + (long long)g.nx * j;
+        const bool zper = (g.bcz == kPeriodic);
+        float2 pzm = cmk(0.f, 0.f);
+        if (g.nz >= 2) {
+            int kp = (k0 == 0) ? (zper ? g.nz - 1 : 1) : k0 - 1;
+            pzm = a.src[base + kp * sz];
+        }
+        float2 pc = a.src[base + k0 * sz];
+        for (int k = k0; k < k1; ++k) {
+            const long long m = base + k * sz;
+            float2 pzp = cmk(0.f, 0.f);
+            if (g.nz >= 2) {
+                int kn = (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1;
+                pzp = a.src[base + kn * sz];
+            }
+            float2 ns = cadd(ns_xy<GEN>(g, a.src, i, j, k, m, Ux), ns_z<GEN>(g, i, k, m, pzm, pzp));
+            const float2 D = a.D[m];
+            const float2 s = cadd(a.b[m], cscale(g.ht2, ns));
+            const float2 r = csub(s, cmul(D, pc));
+            const float inv = 1.0f / cabs2(D);
+            a.dst[m] = cscale(inv, cmulc(D, s));
+            float r2 = cabs2(r);
+            r2 = (r2 <= FLT_MAX) ? r2 : INFINITY;
+            rmax = fmaxf(rmax, r2);
+            pzm = pc;
+            pc = pzp;
+        }
+    }
+    finish_sweep(a, rmax, false);
+}
+
+// Right-hand side of the Poisson equation (Sec. 3.2): f_m = Im[conj(psi_m) NS_m(psi)],
+// the lattice divergence of the supercurrent, with the open-x injection terms
+// (Neumann ghosts mu_{-1} = mu_1 + 2 hx J, mu_Nx = mu_{Nx-2} - 2 hx J moved to the
+// right-hand side).  Also reduces sum_m w_m f_m in FP64 for the compatibility
+// projection (w: trapezoid weights).
+template <bool GEN>
+__global__ void __launch_bounds__(kBX *kBY) poisson_rhs_kernel(DevGrid g, DevCtl *ctl, double *blockred,
+                                                               const float2 *__restrict__ psi, float *__restrict__ f,
+                                                               float inj, double wsum, int kz)
+{
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k0 = blockIdx.z * kz;
+    const int k1 = min(k0 + kz, g.nz);
+    const float2 Ux = ctl->Ux;
+    float acc = 0.f;
+    if (i < g.nx && j < g.ny) {
+        const long long sz = (long long)g.nx * g.ny;
+        const long long base = (long long)i + (long long)g.nx * j;
+        const bool zper = (g.bcz == kPeriodic);
+        float wxy = 1.f;
+        if (g.bcx == kOpen && (i == 0 || i == g.nx - 1)) wxy *= 0.5f;
+        if (g.bcy == kOpen && (j == 0 || j == g.ny - 1)) wxy *= 0.5f;
+        float2 pzm = cmk(0.f, 0.f);
+        if (g.nz >= 2) {
+            int kp = (k0 == 0) ? (zper ? g.nz - 1 : 1) : k0 - 1;
+            pzm = psi[base + kp * sz];
+        }
+        float2 pc = psi[base + k0 * sz];
+        for (int k = k0; k < k1; ++k) {
+            const long long m = base + k * sz;
+            float2 pzp = cmk(0.f, 0.f);
+            if (g.nz >= 2) {
+                int kn = (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1;
+                pzp = psi[base + kn * sz];
+            }
+            float2 ns = cadd(ns_xy<GEN>(g, psi, i, j, k, m, Ux), ns_z<GEN>(g, i, k, m, pzm, pzp));
+            float v = pc.x * ns.y - pc.y * ns.x;
+            if (g.bcx == kOpen) {
+                if (i == 0) v -= inj;
+                if (i == g.nx - 1) v += inj;
+            }
+            f[m] = v;
+            float w = wxy;
+            if (g.bcz == kOpen && g.nz >= 2 && (k == 0 || k == g.nz - 1)) w *= 0.5f;
+            acc += w * v;
+            pzm = pc;
+            pc = pzp;
+        }
+    }
+    __shared__ double shd[32];
+    __shared__ int flag;
+    double s = block_sum((double)acc, shd);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (tid == 0) blockred[bid] = s;
+    if (!last_block(&ctl->ticket, nb, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = tid; q < nb; q += blockDim.x * blockDim.y) t += ((volatile double *)blockred)[q];
+    t = block_sum(t, shd);
+    if (tid == 0) {
+        ctl->ticket = 0u;
+        ctl->fmean = t / wsum;
+    }
+}
+
+static dim3 sweep_grid(const DevGrid &g, int kz)
+{
+    return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, (g.nz + kz - 1) / kz);
+}
+
+cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s)
+{
+    int kz = zchunk(a.g);
+    dim3 grid = sweep_grid(a.g, kz), block(kBX, kBY);
+    if (a.g.L) init_sweep_kernel<true><<<grid, block, 0, s>>>(a, kz);
+    else init_sweep_kernel<false><<<grid, block, 0, s>>>(a, kz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s)
+{
+    int kz = zchunk(a.g);
+    dim3 grid = sweep_grid(a.g, kz), block(kBX, kBY);
+    if (a.g.L) sweep_kernel<true><<<grid, block, 0, s>>>(a, kz);
+    else sweep_kernel<false><<<grid, block, 0, s>>>(a, kz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStream_t s)
+{
+    int kz = zchunk(a.g);
+    dim3 grid = sweep_grid(a.g, kz), block(kBX, kBY);
+    float inj = a.inject ? (float)(2.0 * a.Jext / a.hx) : 0.f;
+    if (a.g.L) poisson_rhs_kernel<true><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
+    else poisson_rhs_kernel<false><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
+    return cudaGetLastError();
+}
+
+}  // namespace tdgl

@@ -1,0 +1,728 @@
+// C ABI of the solver: configuration checks, workspace layout, link tables,
+// and the order of launches within a time step (arXiv:1409.8340, Sec. 3 and
+// Sec. 4.1: psi first, then K, then mu).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "tdgl_internal.cuh"
+
+using namespace tdgl;
+
+struct tdgl_handle {
+    tdgl_config cfg;
+    DevGrid g;
+    cudaStream_t stream;
+    DevCtl *ctl;
+    double *blockred;
+    float2 *psi[3];
+    int cur;
+    float2 *b, *D;
+    float *mu, *f;
+    float2 *links;
+    PoissonArgs pa;
+    int last_sweeps;
+    int last_cycles;
+    int64_t step;
+    double wsum;
+    double dtK;
+    double last_javg;
+    // profiling
+    int prof_on;
+    cudaEvent_t ev[8];
+    bool ev_made;
+    bool pend_K, pend_P;   // K / Poisson event pairs recorded but not yet read
+    tdgl_profile prof;
+};
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int active(int n) { return n >= 2; }
+
+double box_len(int n, double h, int bc) { return bc == TDGL_PERIODIC ? n * h : (n - 1) * h; }
+
+// flux quantum count n = B L1 L2 / 2 pi; returns false if not an integer
+bool quantised(double B, double L1, double L2, long long *n)
+{
+    double q = B * L1 * L2 / kTwoPi;
+    double r = floor(q + 0.5);
+    *n = (long long)r;
+    return fabs(q - r) <= 1e-9 * (1.0 + fabs(q));
+}
+
+int validate(const tdgl_config *c)
+{
+    if (!c) return TDGL_ERR_INVALID_ARG;
+    if (c->nx < 2 || c->ny < 2 || c->nz < 1) return TDGL_ERR_INVALID_ARG;
+    if ((long long)c->nx * c->ny * c->nz > (1LL << 33)) return TDGL_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (c->bc[a] != TDGL_PERIODIC && c->bc[a] != TDGL_OPEN) return TDGL_ERR_INVALID_ARG;
+    if (!(c->hx > 0) || !(c->hy > 0) || !(c->hz > 0) || !(c->g > 0) || !(c->ht > 0)) return TDGL_ERR_INVALID_ARG;
+    if (!(c->u > 0) || !(c->beta >= 0)) return TDGL_ERR_INVALID_ARG;
+    if (c->max_iter < 1 || c->check_every < 1 || c->fixed_sweeps < 0) return TDGL_ERR_INVALID_ARG;
+    if (c->fixed_sweeps == 0 && !(c->eps > 0)) return TDGL_ERR_INVALID_ARG;
+    if (c->poisson_cycles < 1 || c->poisson_max_cycles < c->poisson_cycles) return TDGL_ERR_INVALID_ARG;
+    if (!c->d_alpha) return TDGL_ERR_INVALID_ARG;
+    if (c->links_mode != TDGL_LINKS_LANDAU && c->links_mode != TDGL_LINKS_GENERAL) return TDGL_ERR_INVALID_ARG;
+    if (c->links_mode == TDGL_LINKS_GENERAL && !c->d_link_phase) return TDGL_ERR_INVALID_ARG;
+    if (c->nx > 1500) return TDGL_ERR_INVALID_ARG;   // x lines of the Poisson smoother live in shared memory
+    if (c->links_mode == TDGL_LINKS_LANDAU && c->bc[0] == TDGL_PERIODIC) {
+        double Lx = box_len(c->nx, c->hx, c->bc[0]);
+        long long n;
+        if (c->bc[1] == TDGL_PERIODIC && !quantised(c->Bz, Lx, box_len(c->ny, c->hy, c->bc[1]), &n))
+            return TDGL_ERR_INVALID_ARG;
+        if (c->bc[2] == TDGL_PERIODIC && c->nz >= 2 && !quantised(c->By, Lx, box_len(c->nz, c->hz, c->bc[2]), &n))
+            return TDGL_ERR_INVALID_ARG;
+    }
+    return TDGL_OK;
+}
+
+struct Layout {
+    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, Uy, Uz, Py, Pz, total;
+    int nlevels;
+    int ny[kMaxLevels], nz[kMaxLevels], fy[kMaxLevels], fz[kMaxLevels];
+    size_t u[kMaxLevels], r[kMaxLevels], tri[kMaxLevels];
+    size_t nblockred;
+};
+
+bool can_coarsen(int n, int bc)
+{
+    if (bc == TDGL_PERIODIC) return (n % 2 == 0) && n >= 8;
+    return (n % 2 == 1) && n >= 5;
+}
+int coarse_n(int n, int bc) { return bc == TDGL_PERIODIC ? n / 2 : (n - 1) / 2 + 1; }
+
+Layout layout(const tdgl_config *c)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    const long long N = (long long)c->nx * c->ny * c->nz;
+    DevGrid g;
+    memset(&g, 0, sizeof(g));
+    g.nx = c->nx;
+    g.ny = c->ny;
+    g.nz = c->nz;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.ctl = take(sizeof(DevCtl));
+    size_t nb = (size_t)sweep_blocks(g);
+    if (nb < 4 * 4096) nb = 4 * 4096;
+    L.nblockred = nb;
+    L.blockred = take(sizeof(double) * nb);
+    for (int q = 0; q < 3; ++q) L.psi[q] = take(8 * (size_t)N);
+    L.b = take(8 * (size_t)N);
+    L.D = take(8 * (size_t)N);
+    L.mu = take(4 * (size_t)N);
+    L.f = take(4 * (size_t)N);
+    L.t = take(4 * (size_t)N);
+    L.links = (c->links_mode == TDGL_LINKS_GENERAL) ? take(8 * 3 * (size_t)N) : 0;
+    L.Uy = take(8 * (size_t)c->nx);
+    L.Uz = take(8 * (size_t)c->nx);
+    L.Py = take(8 * (size_t)c->ny);
+    L.Pz = take(8 * (size_t)c->nz);
+    // multigrid levels
+    int ny = c->ny, nz = c->nz, l = 0;
+    for (;;) {
+        L.ny[l] = ny;
+        L.nz[l] = nz;
+        L.tri[l] = take(4 * (size_t)(4 * c->nx + 2));
+        if (l > 0) {
+            L.u[l] = take(4 * (size_t)c->nx * ny * nz);
+            L.r[l] = take(4 * (size_t)c->nx * ny * nz);
+        }
+        bool cy = can_coarsen(ny, c->bc[1]);
+        bool cz = nz >= 2 && can_coarsen(nz, c->bc[2]);
+        if ((!cy && !cz) || l + 1 >= kMaxLevels) {
+            L.fy[l] = L.fz[l] = 1;
+            break;
+        }
+        L.fy[l] = cy ? 2 : 1;
+        L.fz[l] = cz ? 2 : 1;
+        ny = cy ? coarse_n(ny, c->bc[1]) : ny;
+        nz = cz ? coarse_n(nz, c->bc[2]) : nz;
+        ++l;
+    }
+    L.nlevels = l + 1;
+    L.total = off;
+    return L;
+}
+
+template <class T>
+T *at(void *base, size_t off)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(base) + off);
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? TDGL_OK : TDGL_ERR_CUDA; }
+
+__global__ void phases_to_links(const float *theta, float2 *L, long long n3)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n3; q += (long long)gridDim.x * blockDim.x) {
+        float s, c;
+        sincosf(theta[q], &s, &c);
+        L[q] = make_float2(c, s);
+    }
+}
+
+void ev_collect(tdgl_handle *h);
+
+int read_ctl(tdgl_handle *h, DevCtl *out)
+{
+    cudaError_t e = cudaMemcpyAsync(out, h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return TDGL_ERR_CUDA;
+    int rc = cuda_err(cudaStreamSynchronize(h->stream));
+    ev_collect(h);
+    return rc;
+}
+
+SweepArgs sweep_args(tdgl_handle *h)
+{
+    SweepArgs a;
+    a.g = h->g;
+    a.ctl = h->ctl;
+    a.blockred = h->blockred;
+    a.b = h->b;
+    a.D = h->D;
+    a.mu = h->mu;
+    a.alpha = h->cfg.d_alpha;
+    a.check_every = h->cfg.check_every;
+    a.fixed_sweeps = h->cfg.fixed_sweeps;
+    a.max_iter = h->cfg.max_iter;
+    a.eps = h->cfg.eps;
+    return a;
+}
+
+void ev_rec(tdgl_handle *h, int i)
+{
+    if (h->prof_on) cudaEventRecord(h->ev[i], h->stream);
+}
+
+double ev_ms(tdgl_handle *h, int a, int b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]) != cudaSuccess) return 0.0;
+    return (double)ms;
+}
+
+// Read K / Poisson timings recorded in an earlier step (the stream has been
+// synchronised since, so the events are complete).
+void ev_collect(tdgl_handle *h)
+{
+    if (!h->prof_on) return;
+    if (h->pend_K) h->prof.ms_K += ev_ms(h, 4, 5);
+    if (h->pend_P) h->prof.ms_poisson += ev_ms(h, 6, 7);
+    h->pend_K = h->pend_P = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tdgl_error_string(int code)
+{
+    switch (code) {
+    case TDGL_OK: return "ok";
+    case TDGL_ERR_INVALID_ARG: return "invalid argument";
+    case TDGL_ERR_NOT_CONVERGED: return "Jacobi iteration did not converge within max_iter sweeps";
+    case TDGL_ERR_NONFINITE: return "non-finite residual";
+    case TDGL_ERR_TIMEOUT: return "device wait timed out";
+    case TDGL_ERR_CUDA: return "CUDA runtime error";
+    case TDGL_ERR_WORKSPACE: return "workspace too small or misaligned";
+    default: return "unknown error";
+    }
+}
+
+size_t tdgl_workspace_bytes(const tdgl_config *cfg)
+{
+    if (validate(cfg) != TDGL_OK) return 0;
+    return layout(cfg).total;
+}
+
+int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream, tdgl_handle **out)
+{
+    if (!out) return TDGL_ERR_INVALID_ARG;
+    *out = nullptr;
+    int v = validate(cfg);
+    if (v != TDGL_OK) return v;
+    Layout L = layout(cfg);
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < L.total) return TDGL_ERR_WORKSPACE;
+    tdgl_handle *h = new tdgl_handle();
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)stream;
+    const tdgl_config &c = *cfg;
+    const long long N = (long long)c.nx * c.ny * c.nz;
+    DevGrid &g = h->g;
+    g.nx = c.nx;
+    g.ny = c.ny;
+    g.nz = c.nz;
+    g.N = N;
+    g.bcx = c.bc[0];
+    g.bcy = c.bc[1];
+    g.bcz = c.bc[2];
+    g.cx = (float)(1.0 / (c.hx * c.hx));
+    g.cy = (float)(1.0 / (c.hy * c.hy));
+    g.cz = active(c.nz) ? (float)(1.0 / (c.g * c.g * c.hz * c.hz)) : 0.f;
+    g.S = (float)(1.0 / (c.hx * c.hx) + 1.0 / (c.hy * c.hy) + (active(c.nz) ? 1.0 / (c.g * c.g * c.hz * c.hz) : 0.0));
+    g.ht2 = (float)(0.5 * c.ht);
+    g.u = (float)c.u;
+    g.beta = (float)c.beta;
+    g.Uy = at<float2>(ws, L.Uy);
+    g.Uz = at<float2>(ws, L.Uz);
+    g.Py = at<float2>(ws, L.Py);
+    g.Pz = at<float2>(ws, L.Pz);
+    g.L = (c.links_mode == TDGL_LINKS_GENERAL) ? at<float2>(ws, L.links) : nullptr;
+    h->ctl = at<DevCtl>(ws, L.ctl);
+    h->blockred = at<double>(ws, L.blockred);
+    for (int q = 0; q < 3; ++q) h->psi[q] = at<float2>(ws, L.psi[q]);
+    h->cur = 0;
+    h->b = at<float2>(ws, L.b);
+    h->D = at<float2>(ws, L.D);
+    h->mu = at<float>(ws, L.mu);
+    h->f = at<float>(ws, L.f);
+    h->links = g.L ? at<float2>(ws, L.links) : nullptr;
+    h->last_sweeps = 8;
+    h->last_cycles = c.poisson_cycles;
+    h->step = 0;
+    h->dtK = c.u * c.ht;
+    h->wsum = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        int n = (a == 0) ? c.nx : (a == 1 ? c.ny : c.nz);
+        h->wsum *= (c.bc[a] == TDGL_OPEN && n >= 2) ? (double)(n - 1) : (double)n;
+    }
+
+    // link tables in FP64 (Eq. link_variables with A~ of Eq. A_yz), wrap phase of Sec. 3.3.1
+    const double Lx = box_len(c.nx, c.hx, c.bc[0]);
+    std::vector<float2> Uy(c.nx), Uz(c.nx), Py(c.ny), Pz(c.nz);
+    for (int i = 0; i < c.nx; ++i) {
+        double xbar = i * c.hx - 0.5 * Lx;
+        double ay = fmod(-c.hy * c.Bz * xbar, kTwoPi), az = fmod(c.hz * c.By * xbar, kTwoPi);
+        Uy[i] = make_float2((float)cos(ay), (float)sin(ay));
+        Uz[i] = make_float2((float)cos(az), (float)sin(az));
+    }
+    // P_{j,k} = exp(i(-j hy Lx Bz + k hz Lx By)) = Py[j] Pz[k]
+    long long nzq = 0, nyq = 0;
+    bool qy = c.bc[1] == TDGL_PERIODIC && quantised(c.Bz, Lx, box_len(c.ny, c.hy, c.bc[1]), &nzq);
+    bool qz = c.bc[2] == TDGL_PERIODIC && quantised(c.By, Lx, box_len(c.nz, c.hz, c.bc[2]), &nyq);
+    for (int j = 0; j < c.ny; ++j) {
+        double ph;
+        if (qy) {
+            long long r = ((nzq * j) % c.ny + c.ny) % c.ny;       // j hy Lx Bz = 2 pi nz j / Ny
+            ph = -kTwoPi * (double)r / (double)c.ny;
+        } else {
+            ph = -fmod(j * c.hy * Lx * c.Bz, kTwoPi);
+        }
+        Py[j] = make_float2((float)cos(ph), (float)sin(ph));
+    }
+    for (int k = 0; k < c.nz; ++k) {
+        double ph;
+        if (qz) {
+            long long r = ((nyq * k) % c.nz + c.nz) % c.nz;
+            ph = kTwoPi * (double)r / (double)c.nz;
+        } else {
+            ph = fmod(k * c.hz * Lx * c.By, kTwoPi);
+        }
+        Pz[k] = make_float2((float)cos(ph), (float)sin(ph));
+    }
+    cudaStream_t s = h->stream;
+    int rc = TDGL_OK;
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == TDGL_OK) rc = TDGL_ERR_CUDA;
+    };
+    chk(cudaMemcpyAsync((void *)g.Uy, Uy.data(), 8 * c.nx, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync((void *)g.Uz, Uz.data(), 8 * c.nx, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync((void *)g.Py, Py.data(), 8 * c.ny, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync((void *)g.Pz, Pz.data(), 8 * c.nz, cudaMemcpyHostToDevice, s));
+    if (g.L) {
+        long long n3 = 3 * N;
+        int nb = (int)((n3 + 255) / 256 < 8192 ? (n3 + 255) / 256 : 8192);
+        phases_to_links<<<nb, 256, 0, s>>>(c.d_link_phase, h->links, n3);
+        chk(cudaGetLastError());
+    }
+    DevCtl ctl0;
+    memset(&ctl0, 0, sizeof(ctl0));
+    ctl0.Ux = make_float2(1.f, 0.f);
+    chk(cudaMemcpyAsync(h->ctl, &ctl0, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
+    chk(cudaMemsetAsync(h->psi[0], 0, 8 * (size_t)N, s));
+    chk(cudaMemsetAsync(h->mu, 0, 4 * (size_t)N, s));
+    chk(cudaMemsetAsync(h->f, 0, 4 * (size_t)N, s));
+
+    // multigrid
+    PoissonArgs &pa = h->pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.g = g;
+    pa.ctl = h->ctl;
+    pa.blockred = h->blockred;
+    pa.nlevels = L.nlevels;
+    pa.f = h->f;
+    pa.mu = h->mu;
+    pa.hx = c.hx;
+    pa.Jext = c.Jext;
+    pa.inject = (c.bc[0] == TDGL_OPEN && c.Jext != 0.0) ? 1 : 0;
+    pa.wsum = h->wsum;
+    std::vector<float> tri(4 * c.nx + 2);
+    double hy = c.hy, hz = c.hz;
+    for (int l = 0; l < L.nlevels; ++l) {
+        MGLevel &M = pa.lev[l];
+        M.nx = c.nx;
+        M.ny = L.ny[l];
+        M.nz = L.nz[l];
+        M.N = (long long)c.nx * M.ny * M.nz;
+        M.fy = L.fy[l];
+        M.fz = L.fz[l];
+        M.cx = g.cx;
+        M.cy = (float)(1.0 / (hy * hy));
+        M.cz = active(M.nz) ? (float)(1.0 / (c.g * c.g * hz * hz)) : 0.f;
+        M.u = (l == 0) ? h->mu : at<float>(ws, L.u[l]);
+        M.r = (l == 0) ? h->f : at<float>(ws, L.r[l]);
+        M.t = at<float>(ws, L.t);
+        M.tri = at<float>(ws, L.tri[l]);
+        mg_line_factors(c.nx, c.bc[0], M.cx, M.cy, M.cz, tri.data());
+        chk(cudaMemcpyAsync(M.tri, tri.data(), 4 * tri.size(), cudaMemcpyHostToDevice, s));
+        if (M.fy == 2) hy *= 2.0;
+        if (M.fz == 2) hz *= 2.0;
+        // a synchronous wait keeps `tri` valid for the copy above
+        chk(cudaStreamSynchronize(s));
+    }
+    chk(cudaStreamSynchronize(s));
+    if (rc != TDGL_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return TDGL_OK;
+}
+
+void tdgl_destroy(tdgl_handle *h)
+{
+    if (!h) return;
+    if (h->ev_made)
+        for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
+    delete h;
+}
+
+int tdgl_profile_enable(tdgl_handle *h, int on)
+{
+    if (!h) return TDGL_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (on && !h->ev_made) {
+        for (int i = 0; i < 8; ++i)
+            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return TDGL_ERR_CUDA;
+        h->ev_made = true;
+    }
+    h->prof_on = on ? 1 : 0;
+    h->pend_K = h->pend_P = false;
+    memset(&h->prof, 0, sizeof(h->prof));
+    return TDGL_OK;
+}
+
+int tdgl_profile_read(tdgl_handle *h, tdgl_profile *out)
+{
+    if (!h || !out) return TDGL_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
+    ev_collect(h);
+    *out = h->prof;
+    return TDGL_OK;
+}
+
+int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double K)
+{
+    if (!h || !d_psi) return TDGL_ERR_INVALID_ARG;
+    const size_t N = (size_t)h->g.N;
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->psi[h->cur], d_psi, 8 * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    cudaError_t e = d_mu ? cudaMemcpyAsync(h->mu, d_mu, 4 * N, cudaMemcpyDeviceToDevice, s)
+                         : cudaMemsetAsync(h->mu, 0, 4 * N, s);
+    if (e != cudaSuccess) return TDGL_ERR_CUDA;
+    DevCtl c;
+    memset(&c, 0, sizeof(c));
+    c.K = K;
+    c.Ux = make_float2((float)cos(h->cfg.hx * K), (float)sin(h->cfg.hx * K));
+    if (cudaMemcpyAsync(h->ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (launch_set_Ux(h->ctl, h->cfg.hx, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    return cuda_err(cudaStreamSynchronize(s));
+}
+
+int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_mu, double K)
+{
+    if (!h || !host_psi) return TDGL_ERR_INVALID_ARG;
+    const size_t N = (size_t)h->g.N;
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->psi[h->cur], host_psi, 8 * N, cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    cudaError_t e = host_mu ? cudaMemcpyAsync(h->mu, host_mu, 4 * N, cudaMemcpyHostToDevice, s)
+                            : cudaMemsetAsync(h->mu, 0, 4 * N, s);
+    if (e != cudaSuccess) return TDGL_ERR_CUDA;
+    DevCtl c;
+    memset(&c, 0, sizeof(c));
+    c.K = K;
+    if (cudaMemcpyAsync(h->ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (launch_set_Ux(h->ctl, h->cfg.hx, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    return cuda_err(cudaStreamSynchronize(s));
+}
+
+int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double *K)
+{
+    if (!h) return TDGL_ERR_INVALID_ARG;
+    const size_t N = (size_t)h->g.N;
+    cudaStream_t s = h->stream;
+    if (host_psi && cudaMemcpyAsync(host_psi, h->psi[h->cur], 8 * N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    if (host_mu && cudaMemcpyAsync(host_mu, h->mu, 4 * N, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    DevCtl c;
+    int rc = read_ctl(h, &c);
+    if (rc != TDGL_OK) return rc;
+    if (K) *K = c.K;
+    return TDGL_OK;
+}
+
+int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out)
+{
+    if (!h || !out) return TDGL_ERR_INVALID_ARG;
+    out->psi = reinterpret_cast<float *>(h->psi[h->cur]);
+    out->mu = h->mu;
+    out->b = reinterpret_cast<float *>(h->b);
+    out->D = reinterpret_cast<float *>(h->D);
+    out->f = h->f;
+    return TDGL_OK;
+}
+
+int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
+{
+    if (!h) return TDGL_ERR_INVALID_ARG;
+    const tdgl_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    SweepArgs a = sweep_args(h);
+    const int ia = (h->cur + 1) % 3, ib = (h->cur + 2) % 3;
+    a.src = h->psi[h->cur];
+    a.dst = h->psi[ia];
+    a.dst_index = ia;
+    ev_rec(h, 0);
+    if (launch_init_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    ev_rec(h, 1);
+    h->prof.kernel_launches += 1;
+    int launched = 1;
+    bool first_sync = true;
+    auto collect = [&]() {
+        if (!h->prof_on) return;
+        if (first_sync) h->prof.ms_init += ev_ms(h, 0, 1);
+        first_sync = false;
+        h->prof.ms_sweeps += ev_ms(h, 2, 3);
+    };
+    auto enqueue = [&](int n) -> int {
+        ev_rec(h, 2);
+        h->prof.sweep_launches += n;
+        h->prof.kernel_launches += n;
+        for (int q = 0; q < n; ++q) {
+            // sweep number `launched` (1-based count of sweeps before it) reads the
+            // output of the previous one: odd -> A to B, even -> B to A
+            const bool odd = (launched % 2) == 1;
+            a.src = odd ? h->psi[ia] : h->psi[ib];
+            a.dst = odd ? h->psi[ib] : h->psi[ia];
+            a.dst_index = odd ? ib : ia;
+            if (launch_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+            ++launched;
+        }
+        ev_rec(h, 3);
+        return TDGL_OK;
+    };
+    DevCtl ctl;
+    if (c.fixed_sweeps > 0) {
+        int rc = enqueue(c.fixed_sweeps - 1);
+        if (rc != TDGL_OK) return rc;
+        rc = read_ctl(h, &ctl);
+        if (rc != TDGL_OK) return rc;
+        collect();
+    } else {
+        int batch = h->last_sweeps;
+        for (;;) {
+            int n = batch - launched;
+            if (n < 1) n = 1;
+            if (launched + n > c.max_iter) n = c.max_iter - launched;
+            if (n > 0) {
+                int rc = enqueue(n);
+                if (rc != TDGL_OK) return rc;
+            } else {
+                ev_rec(h, 2);
+                ev_rec(h, 3);
+            }
+            int rc = read_ctl(h, &ctl);
+            if (rc != TDGL_OK) return rc;
+            collect();
+            if (ctl.done || launched >= c.max_iter) break;
+            batch = launched + 4;
+        }
+    }
+    if (ctl.status != TDGL_OK) return ctl.status;
+    if (!ctl.done) return TDGL_ERR_NOT_CONVERGED;
+    h->cur = ctl.result;
+    h->last_sweeps = ctl.iter;
+    h->prof.sweeps += ctl.iter;
+    if (sweeps_out) *sweeps_out = ctl.iter;
+    return TDGL_OK;
+}
+
+int tdgl_solve_mu(tdgl_handle *h)
+{
+    if (!h) return TDGL_ERR_INVALID_ARG;
+    const tdgl_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    if (launch_poisson_rhs(h->pa, h->psi[h->cur], s) != cudaSuccess) return TDGL_ERR_CUDA;
+    long long nl = 1;
+    int cycles = 0;
+    for (int q = 0; q < c.poisson_cycles; ++q, ++cycles)
+        if (launch_vcycle(h->pa, s, &nl) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (c.poisson_tol > 0) {
+        for (;;) {
+            if (launch_poisson_residual(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
+            ++nl;
+            DevCtl ctl;
+            int rc = read_ctl(h, &ctl);
+            if (rc != TDGL_OK) return rc;
+            if (ctl.res <= c.poisson_tol || cycles >= c.poisson_max_cycles) break;
+            if (launch_vcycle(h->pa, s, &nl) != cudaSuccess) return TDGL_ERR_CUDA;
+            ++cycles;
+        }
+    }
+    if (launch_project_mu(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    nl += 2;
+    h->last_cycles = cycles;
+    h->prof.vcycles += cycles;
+    h->prof.kernel_launches += nl;
+    return TDGL_OK;
+}
+
+int tdgl_step(tdgl_handle *h, int n_steps)
+{
+    if (!h || n_steps < 0) return TDGL_ERR_INVALID_ARG;
+    const tdgl_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    for (int n = 0; n < n_steps; ++n) {
+        int rc = tdgl_solve_psi(h, nullptr);
+        if (rc != TDGL_OK) return rc;
+        if (c.bc[0] == TDGL_PERIODIC) {
+            KArgs k;
+            k.g = h->g;
+            k.ctl = h->ctl;
+            k.blockred = h->blockred;
+            k.psi = h->psi[h->cur];
+            k.hx = c.hx;
+            k.dtK = h->dtK;
+            k.Jext = c.Jext;
+            k.update_K = c.freeze_mu_K ? 0 : 1;
+            ev_rec(h, 4);
+            if (launch_javg_K(k, s) != cudaSuccess) return TDGL_ERR_CUDA;
+            ev_rec(h, 5);
+            h->pend_K = h->prof_on;
+            h->prof.kernel_launches += 1;
+        }
+        ev_rec(h, 6);
+        if (!c.freeze_mu_K) {
+            rc = tdgl_solve_mu(h);
+            if (rc != TDGL_OK) return rc;
+        }
+        if (c.bc[0] == TDGL_OPEN) {
+            if (launch_voltage(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
+            h->prof.kernel_launches += 1;
+        }
+        ev_rec(h, 7);
+        h->pend_P = h->prof_on;
+        ++h->step;
+        ++h->prof.steps;
+    }
+    return cuda_err(cudaGetLastError());
+}
+
+int tdgl_observables(tdgl_handle *h, tdgl_obs *out)
+{
+    if (!h || !out) return TDGL_ERR_INVALID_ARG;
+    const tdgl_config &c = h->cfg;
+    double flux = c.hx * c.hy * c.Bz;
+    if (launch_observables(h->g, h->ctl, h->blockred, h->psi[h->cur], c.d_alpha, nullptr, flux, h->stream) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    DevCtl ctl;
+    int rc = read_ctl(h, &ctl);
+    if (rc != TDGL_OK) return rc;
+    double dV = c.hx * c.hy * (c.nz >= 2 ? c.hz : 1.0);
+    memset(out, 0, sizeof(*out));
+    out->psi2_mean = ctl.sums[0] / (double)h->g.N;
+    out->energy = ctl.sums[1] * dV;
+    out->vortex_unsigned = ctl.sums[2] / (double)c.nz;
+    out->vortex_signed = ctl.sums[3] / (double)c.nz;
+    out->javg = ctl.javg;
+    out->K = ctl.K;
+    out->Ex = ctl.Ex;
+    out->last_r2 = ctl.r2;
+    out->poisson_res = ctl.res;
+    out->last_sweeps = h->last_sweeps;
+    out->poisson_cycles = h->last_cycles;
+    out->step = h->step;
+    return TDGL_OK;
+}
+
+size_t tdgl_pattern_scratch_bytes(const tdgl_config *grid, int64_t n_candidates)
+{
+    if (!grid || grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || n_candidates < 0) return 0;
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    return align256(4 * (size_t)N) + align256(8 * (size_t)n_candidates + 8) + align256(16) +
+           align256(80 * (size_t)n_candidates + 8);
+}
+
+int tdgl_pattern(const tdgl_config *grid, const double *host_candidates, int64_t n_candidates, int64_t target_sites,
+                 float alpha_in, float alpha_out, float *d_alpha, void *d_scratch, size_t scratch_bytes, void *stream,
+                 int64_t *n_used, int64_t *n_marked)
+{
+    if (!grid || !d_alpha || n_candidates < 0 || (n_candidates > 0 && !host_candidates)) return TDGL_ERR_INVALID_ARG;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return TDGL_ERR_INVALID_ARG;
+    if (!(grid->hx > 0) || !(grid->hy > 0) || !(grid->hz > 0)) return TDGL_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (grid->bc[a] != TDGL_PERIODIC && grid->bc[a] != TDGL_OPEN) return TDGL_ERR_INVALID_ARG;
+    if (n_candidates > 0x7ffffff0LL) return TDGL_ERR_INVALID_ARG;
+    size_t need = tdgl_pattern_scratch_bytes(grid, n_candidates);
+    if (!d_scratch || ((uintptr_t)d_scratch & 255u) || scratch_bytes < need) return TDGL_ERR_WORKSPACE;
+    for (int64_t n = 0; n < n_candidates; ++n) {
+        const double *q = host_candidates + 10 * n;
+        if (!(q[3] > 0) || !(q[4] > 0) || !(q[5] > 0)) return TDGL_ERR_INVALID_ARG;
+    }
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    size_t off = 0;
+    int *first = at<int>(d_scratch, off);
+    off += align256(4 * (size_t)N);
+    unsigned long long *counts = at<unsigned long long>(d_scratch, off);
+    off += align256(8 * (size_t)n_candidates + 8);
+    long long *result = at<long long>(d_scratch, off);
+    off += align256(16);
+    double *incl = at<double>(d_scratch, off);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_candidates > 0 &&
+        cudaMemcpyAsync(incl, host_candidates, 80 * (size_t)n_candidates, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    DevGrid g;
+    memset(&g, 0, sizeof(g));
+    g.nx = grid->nx;
+    g.ny = grid->ny;
+    g.nz = grid->nz;
+    g.N = N;
+    g.bcx = grid->bc[0];
+    g.bcy = grid->bc[1];
+    g.bcz = grid->bc[2];
+    if (launch_pattern(g, grid->hx, grid->hy, grid->hz, incl, n_candidates, target_sites, alpha_in, alpha_out, d_alpha,
+                       first, counts, result, s) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    long long res[2];
+    if (cudaMemcpyAsync(res, result, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (n_used) *n_used = res[0];
+    if (n_marked) *n_marked = res[1];
+    return TDGL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,222 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tdgl.h"
+
+namespace tdgl {
+
+constexpr int kPeriodic = TDGL_PERIODIC;
+constexpr int kOpen = TDGL_OPEN;
+constexpr int kMaxLevels = 16;
+
+// Grid and coefficients as the kernels see them (passed by value).
+struct DevGrid {
+    int nx, ny, nz;
+    long long N;
+    int bcx, bcy, bcz;
+    float cx, cy, cz;          // 1/hx^2, 1/hy^2, 1/(g^2 hz^2); 0 on an inactive axis
+    float S;                   // cx + cy + cz
+    float ht2, u, beta;        // ht/2, u, beta
+    const float2 *Uy;          // [nx] y links exp(-i hy Bz xbar_i)
+    const float2 *Uz;          // [nx] z links exp(+i hz By xbar_i)
+    const float2 *Py;          // [ny] periodic-x wrap phase, y part
+    const float2 *Pz;          // [nz] periodic-x wrap phase, z part
+    const float2 *L;           // [3N] general links, or nullptr (Landau)
+};
+
+// Device-resident control block.  Written only by single threads at the end of
+// kernels (last-block reductions), read by later launches on the same stream.
+struct DevCtl {
+    double K;                  // current K
+    double K_step_start;       // K at the start of the step
+    double Ex;                 // electric field of the last step
+    double javg;               // J_av of the last step
+    double r2;                 // max |r|^2 of the last tested sweep
+    double fmean;              // weighted mean of the Poisson right-hand side
+    double fmax;               // max |F| (after projection)
+    double res;                // last Poisson residual max-norm
+    double wsum;               // sum of trapezoid weights
+    double mu_mean;            // weighted mean of mu before projection
+    double sums[8];            // scratch results of observable reductions
+    float2 Ux;                 // exp(i hx K), from K in FP64
+    int iter;                  // sweeps done in this step
+    int done;                  // 1: this step's Jacobi solve finished
+    int status;                // TDGL_OK or error
+    int result;                // buffer index holding the solve's result
+    unsigned int ticket;       // last-block ticket (reset by the last block)
+    int pad[3];
+};
+
+// ----------------------------------------------------------------------------
+// complex64 helpers
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cmk(float x, float y) { return make_float2(x, y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+// ----------------------------------------------------------------------------
+// reductions
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide max of a float (all threads get the result).  sh: >= 32 floats.
+__device__ __forceinline__ float block_max(float v, float *sh)
+{
+    int lane = threadIdx.x & 31;
+    int wid = (threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) >> 5;
+    int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    lane = tid & 31;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = (nthreads + 31) >> 5;
+    float r = (tid < nw) ? sh[tid] : 0.0f;
+    if (wid == 0) r = warp_max(r);
+    if (tid == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    return r;
+}
+
+// Block-wide FP64 sum (result valid in thread 0).  sh: >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    int lane = tid & 31, wid = tid >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = (nthreads + 31) >> 5;
+    double r = (tid < nw) ? sh[tid] : 0.0;
+    if (wid == 0) r = warp_sum(r);
+    return r;
+}
+
+// Last-block ticket: returns true in every thread of the block that finishes
+// last.  The caller has already written its per-block partial.
+__device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nblocks, int *sh_flag)
+{
+    int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        *sh_flag = (t == nblocks - 1u);
+    }
+    __syncthreads();
+    bool last = *sh_flag != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// ----------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files)
+// ----------------------------------------------------------------------------
+struct SweepArgs {
+    DevGrid g;
+    DevCtl *ctl;
+    double *blockred;          // per-block partials
+    const float2 *src;         // input iterate (init: psi^-)
+    float2 *dst;               // output iterate
+    float2 *b;
+    float2 *D;
+    const float *mu;           // init only
+    const float *alpha;        // init only
+    int dst_index;             // buffer index of dst
+    int check_every;
+    int fixed_sweeps;
+    int max_iter;
+    double eps;
+};
+
+cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
+cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
+int sweep_blocks(const DevGrid &g);
+
+struct KArgs {
+    DevGrid g;
+    DevCtl *ctl;
+    double *blockred;
+    const float2 *psi;
+    double hx, dtK, Jext;
+    int update_K;              // 1: integrate the K ODE
+};
+cudaError_t launch_javg_K(const KArgs &a, cudaStream_t s);
+cudaError_t launch_set_Ux(DevCtl *ctl, double hx, cudaStream_t s);
+
+// Multigrid Poisson solver
+struct MGLevel {
+    int nx, ny, nz;
+    long long N;
+    int fy, fz;                // coarsening factor from this level to the next (1 or 2)
+    float cx, cy, cz;
+    float *u;                  // solution / correction
+    float *r;                  // right-hand side
+    float *t;                  // residual scratch
+    float *tri;                // x-line factors: [nx] c', [nx] 1/pivot, [nx] SM z, [1] SM factor
+};
+struct PoissonArgs {
+    DevGrid g;
+    DevCtl *ctl;
+    double *blockred;
+    int nlevels;
+    MGLevel lev[kMaxLevels];
+    float *f;                  // level-0 right-hand side (= lev[0].r)
+    float *mu;                 // level-0 solution (= lev[0].u)
+    double hx, Jext;
+    int inject;                // open x with applied current
+    double wsum;
+};
+cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStream_t s);
+cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches);
+cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s);
+cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s);
+cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
+void mg_line_factors(int nx, int bcx, float cx, float cy, float cz, float *host_tri);
+
+// Observables
+cudaError_t launch_observables(const DevGrid &g, DevCtl *ctl, double *blockred, const float2 *psi,
+                               const float *alpha, int32_t *scratch_i, double flux, cudaStream_t s);
+
+// Pattern
+cudaError_t launch_pattern(const DevGrid &g, double hx, double hy, double hz, const double *d_incl,
+                           long long n_incl, long long target, float alpha_in, float alpha_out, float *alpha,
+                           int *first_idx, unsigned long long *counts, long long *result, cudaStream_t s);
+
+}  // namespace tdgl

@@ -1,0 +1,215 @@
+"""Python front end of the GB300 TDGL solver.
+
+PyTorch only provides device memory and the stream: the workspace is one
+uint8 CUDA tensor handed to tdgl_create(), and the state arrays are exposed as
+zero-copy tensor views into it.  All arithmetic runs in libtdgl_gb300.so.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import OPEN, PERIODIC, TdglError, check
+
+
+@dataclasses.dataclass
+class Params:
+    """Problem description (see include/tdgl.h, struct tdgl_config)."""
+    nx: int
+    ny: int
+    nz: int
+    hx: float = 0.5
+    hy: float = 0.5
+    hz: float = 0.5
+    bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
+    g: float = 1.0
+    u: float = 1.0
+    beta: float = 1.0
+    ht: float = 0.1
+    By: float = 0.0
+    Bz: float = 0.0
+    Jext: float = 0.0
+    eps: float = 1e-6
+    max_iter: int = 200
+    check_every: int = 1
+    fixed_sweeps: int = 0
+    freeze_mu_K: bool = False
+    poisson_cycles: int = 2
+    poisson_max_cycles: int = 50
+    poisson_tol: float = 0.0
+    general_links: bool = False
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def N(self):
+        return self.nx * self.ny * self.nz
+
+    def length(self, ax):
+        n = (self.nx, self.ny, self.nz)[ax]
+        h = (self.hx, self.hy, self.hz)[ax]
+        return n * h if self.bc[ax] == PERIODIC else (n - 1) * h
+
+    def quantise_Bz(self, n_quanta: int):
+        """Set Bz to n flux quanta through the xy face (Sec. 3.3.1)."""
+        self.Bz = 2 * math.pi * n_quanta / (self.length(0) * self.length(1))
+        return self
+
+    def to_c(self, d_alpha: int, d_link_phase: int = 0) -> _lib.Config:
+        c = _lib.Config()
+        c.nx, c.ny, c.nz = self.nx, self.ny, self.nz
+        c.bc[:] = list(self.bc)
+        c.hx, c.hy, c.hz = self.hx, self.hy, self.hz
+        c.g, c.u, c.beta, c.ht = self.g, self.u, self.beta, self.ht
+        c.By, c.Bz, c.Jext = self.By, self.Bz, self.Jext
+        c.eps = self.eps
+        c.max_iter = self.max_iter
+        c.check_every = self.check_every
+        c.fixed_sweeps = self.fixed_sweeps
+        c.freeze_mu_K = int(bool(self.freeze_mu_K))
+        c.poisson_cycles = self.poisson_cycles
+        c.poisson_max_cycles = max(self.poisson_max_cycles, self.poisson_cycles)
+        c.poisson_tol = self.poisson_tol
+        c.links_mode = _lib.LINKS_GENERAL if self.general_links else _lib.LINKS_LANDAU
+        c.d_alpha = d_alpha
+        c.d_link_phase = d_link_phase or None
+        return c
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Solver:
+    """One TDGL problem on one GPU.  alpha: CUDA float32 tensor of shape (nz, ny, nx)."""
+
+    def __init__(self, p: Params, alpha: torch.Tensor, link_phase: torch.Tensor | None = None, stream=None,
+                 device=None):
+        L = _lib.load()
+        self.p = p
+        self.device = alpha.device if device is None else torch.device(device)
+        if alpha.dtype != torch.float32 or not alpha.is_cuda or alpha.numel() != p.N:
+            raise ValueError("alpha must be a CUDA float32 tensor with nx*ny*nz elements")
+        self.alpha = alpha.contiguous()
+        self.link_phase = None
+        if p.general_links:
+            if link_phase is None or link_phase.numel() != 3 * p.N:
+                raise ValueError("general links need a float32 phase tensor of 3*N elements")
+            self.link_phase = link_phase.contiguous().to(torch.float32)
+        self._cfg = p.to_c(self.alpha.data_ptr(), self.link_phase.data_ptr() if self.link_phase is not None else 0)
+        nbytes = L.tdgl_workspace_bytes(ctypes.byref(self._cfg))
+        if nbytes == 0:
+            raise TdglError(-1, "tdgl_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        check(L.tdgl_create(ctypes.byref(self._cfg), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                            ctypes.c_void_p(_stream_ptr(self.stream)), ctypes.byref(h)), "tdgl_create")
+        self._h = h
+        self._L = L
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.tdgl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _view(self, ptr: int, dtype, shape):
+        off = ptr - self.workspace.data_ptr()
+        n = int(np.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+        return self.workspace[off:off + n].view(dtype).view(shape)
+
+    def state(self):
+        """(psi complex64, mu float32) zero-copy views of the current state."""
+        sp = _lib.StatePtrs()
+        check(self._L.tdgl_get_state(self._h, ctypes.byref(sp)), "tdgl_get_state")
+        return self._view(sp.psi, torch.complex64, self.p.shape), self._view(sp.mu, torch.float32, self.p.shape)
+
+    def internals(self):
+        """Views of b, diag M and the Poisson right-hand side of the last step."""
+        sp = _lib.StatePtrs()
+        check(self._L.tdgl_get_state(self._h, ctypes.byref(sp)), "tdgl_get_state")
+        return (self._view(sp.b, torch.complex64, self.p.shape), self._view(sp.D, torch.complex64, self.p.shape),
+                self._view(sp.f, torch.float32, self.p.shape))
+
+    def set_state(self, psi: torch.Tensor, mu: torch.Tensor | None = None, K: float = 0.0):
+        psi = psi.to(device=self.device, dtype=torch.complex64).contiguous()
+        mu_ptr = None
+        if mu is not None:
+            mu = mu.to(device=self.device, dtype=torch.float32).contiguous()
+            mu_ptr = ctypes.c_void_p(mu.data_ptr())
+        check(self._L.tdgl_set_state(self._h, ctypes.c_void_p(psi.data_ptr()), mu_ptr, float(K)), "tdgl_set_state")
+
+    def upload_state(self, psi: np.ndarray | torch.Tensor, mu=None, K: float = 0.0):
+        """Copy a state in from host memory (numpy or CPU tensor)."""
+        psi_t = torch.as_tensor(psi).to(torch.complex64).contiguous()
+        mu_t = None if mu is None else torch.as_tensor(mu).to(torch.float32).contiguous()
+        check(self._L.tdgl_upload_state(self._h, ctypes.c_void_p(psi_t.data_ptr()),
+                                        None if mu_t is None else ctypes.c_void_p(mu_t.data_ptr()), float(K)),
+              "tdgl_upload_state")
+
+    def download_state(self, psi_out: torch.Tensor | None = None, mu_out: torch.Tensor | None = None):
+        psi_out = torch.empty(self.p.shape, dtype=torch.complex64) if psi_out is None else psi_out
+        mu_out = torch.empty(self.p.shape, dtype=torch.float32) if mu_out is None else mu_out
+        K = ctypes.c_double()
+        check(self._L.tdgl_download_state(self._h, ctypes.c_void_p(psi_out.data_ptr()),
+                                          ctypes.c_void_p(mu_out.data_ptr()), ctypes.byref(K)), "tdgl_download_state")
+        return psi_out, mu_out, K.value
+
+    def step(self, n: int = 1):
+        check(self._L.tdgl_step(self._h, int(n)), "tdgl_step")
+
+    def solve_psi(self) -> int:
+        n = ctypes.c_int32()
+        check(self._L.tdgl_solve_psi(self._h, ctypes.byref(n)), "tdgl_solve_psi")
+        return n.value
+
+    def solve_mu(self):
+        check(self._L.tdgl_solve_mu(self._h), "tdgl_solve_mu")
+
+    def profile_enable(self, on: bool = True):
+        check(self._L.tdgl_profile_enable(self._h, int(bool(on))), "tdgl_profile_enable")
+
+    def profile(self) -> dict:
+        pr = _lib.Profile()
+        check(self._L.tdgl_profile_read(self._h, ctypes.byref(pr)), "tdgl_profile_read")
+        return pr.as_dict()
+
+    def observables(self) -> dict:
+        o = _lib.Obs()
+        check(self._L.tdgl_observables(self._h, ctypes.byref(o)), "tdgl_observables")
+        return o.as_dict()
+
+
+def pattern(p: Params, candidates: np.ndarray, target_sites: int = 0, alpha_in: float = -1.0,
+            alpha_out: float = 1.0, device="cuda", stream=None):
+    """Inclusion map alpha on the device (tdgl_pattern).  Returns (alpha, n_used, n_marked)."""
+    L = _lib.load()
+    cand = np.ascontiguousarray(candidates, dtype=np.float64).reshape(-1, 10)
+    alpha = torch.empty(p.shape, dtype=torch.float32, device=device)
+    cfg = p.to_c(alpha.data_ptr())
+    nb = L.tdgl_pattern_scratch_bytes(ctypes.byref(cfg), cand.shape[0])
+    scratch = torch.empty(max(nb, 256), dtype=torch.uint8, device=device)
+    used = ctypes.c_int64()
+    marked = ctypes.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream(alpha.device)
+    check(L.tdgl_pattern(ctypes.byref(cfg), cand.ctypes.data_as(ctypes.c_void_p), cand.shape[0], int(target_sites),
+                         float(alpha_in), float(alpha_out), ctypes.c_void_p(alpha.data_ptr()),
+                         ctypes.c_void_p(scratch.data_ptr()), nb, ctypes.c_void_p(st.cuda_stream),
+                         ctypes.byref(used), ctypes.byref(marked)), "tdgl_pattern")
+    return alpha, used.value, marked.value
