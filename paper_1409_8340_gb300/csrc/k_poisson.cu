@@ -3,22 +3,37 @@
 // geometric multigrid.
 //
 // x is never coarsened: every level keeps all Nx points and is smoothed by
-// zebra line Gauss-Seidel, each x line solved exactly (Thomas algorithm, or
-// Sherman-Morrison for a periodic x line) in shared memory.  y and z are
-// coarsened by 2 while the size allows (periodic: even N >= 8; open: odd
-// N >= 5), with full weighting and bilinear interpolation.  This pairing
-// (x-line relaxation, yz semi-coarsening) is robust to the strong x coupling of
-// the coarse levels and to any Nx, including the odd interval count of an open
-// x axis.  The zero mode (constants) is removed in FP64: the right-hand side is
-// projected onto sum_m w_m F_m = 0 and the solution onto sum_m w_m mu_m = 0, w
-// the trapezoid weights (1/2 per open face).
+// zebra x-line Gauss-Seidel.  Every x line of a level carries the same
+// constant-coefficient operator T = tridiag(-cx, 2cx + s, -cx) (s = 2 cy + 2 cz),
+// periodic on a periodic x axis; on an open x axis the Neumann rows make it the
+// restriction of the periodic operator on the mirrored line of period
+// P = 2(Nx - 1).  So T^{-1} is a circular convolution with the periodized Green's
+// function G_k = (1/P) sum_m cos(2 pi m k / P) / (2 cx (1 - cos(2 pi m / P)) + s),
+// which decays like rho^|k| (rho = 0.17 on the finest level of an isotropic
+// grid): it is precomputed in FP64 on the host and truncated where it falls
+// below 2e-9 G_0, so a line solve is a short, fully parallel convolution.
+//
+// y and z are coarsened by 2 while the size allows (periodic: even N >= 8; open:
+// odd N >= 5), with full weighting and bilinear interpolation.  The coarsest
+// level is solved exactly: its small y-z operator is diagonalised by a dense
+// basis V (Fourier modes on periodic axes, DCT-I modes on open axes), and each
+// mode q is a line problem with shift sigma_q, solved with its own Green's
+// function (the pseudo-inverse for the singular mode).  The zero mode
+// (constants) is removed in FP64: the right-hand side is projected onto
+// sum_m w_m F_m = 0 and the solution onto sum_m w_m mu_m = 0, w the trapezoid
+// weights (1/2 per open face).
 #include <float.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "tdgl_internal.cuh"
 
 namespace tdgl {
 
 constexpr int kThreads = 256;
+constexpr int kR = 16;          // consecutive outputs per thread in a line convolution
 
 static int grid_blocks(long long n, int per_thread = 4)
 {
@@ -29,66 +44,57 @@ static int grid_blocks(long long n, int per_thread = 4)
 }
 
 // ---------------------------------------------------------------------------
-// x-line factors (host, FP64): tri = [c' (nx) | 1/pivot (nx) | a (nx) | z (nx) | bg, 1/(1+v.z)]
-// for rows a_i u_{i-1} + d u_i + c_i u_{i+1} = rhs_i, d = 2(cx+cy+cz).
+// host: Green's functions
 // ---------------------------------------------------------------------------
-void mg_line_factors(int nx, int bcx, float cx_f, float cy_f, float cz_f, float *tri)
+int mg_period(int nx, int bcx) { return bcx == kOpen ? 2 * (nx - 1) : nx; }
+
+// G_k, k = 0..P-1, of T = tridiag(-cx, 2cx + s, -cx) on a ring of P points.
+// s == 0: pseudo-inverse (the constant mode dropped).
+static void green(int P, double cx, double s, std::vector<double> &G)
 {
-    const double cx = cx_f, cy = cy_f, cz = cz_f;
-    const double d = 2.0 * (cx + cy + cz);
-    double *a = new double[nx], *c = new double[nx], *dd = new double[nx];
-    for (int i = 0; i < nx; ++i) {
-        a[i] = (i == 0) ? 0.0 : -cx;
-        c[i] = (i == nx - 1) ? 0.0 : -cx;
-        dd[i] = d;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> ct(P), inv(P);
+    for (int j = 0; j < P; ++j) ct[j] = cos(2.0 * pi * j / P);
+    for (int m = 0; m < P; ++m) {
+        double lam = 2.0 * cx * (1.0 - ct[m]) + s;
+        inv[m] = (s == 0.0 && m == 0) ? 0.0 : 1.0 / lam;
     }
-    double gam = -d, bg = 0.0;
-    if (bcx == kOpen) {
-        c[0] = -2.0 * cx;
-        a[nx - 1] = -2.0 * cx;
-    } else {
-        // cyclic: T = T' + u v^T, u = (gam, 0.., alpha), v = (1, 0.., beta/gam)
-        const double alpha = -cx, beta = -cx;
-        dd[0] = d - gam;
-        dd[nx - 1] = d - alpha * beta / gam;
-        bg = beta / gam;
-    }
-    double *cp = new double[nx], *ip = new double[nx];
-    for (int i = 0; i < nx; ++i) {
-        double piv = dd[i] - (i > 0 ? a[i] * cp[i - 1] : 0.0);
-        ip[i] = 1.0 / piv;
-        cp[i] = c[i] * ip[i];
-    }
-    for (int i = 0; i < nx; ++i) {
-        tri[i] = (float)cp[i];
-        tri[nx + i] = (float)ip[i];
-        tri[2 * nx + i] = (float)a[i];
-        tri[3 * nx + i] = 0.f;
-    }
-    tri[4 * nx] = 0.f;
-    tri[4 * nx + 1] = 0.f;
-    if (bcx == kPeriodic) {
-        // z = T'^{-1} u
-        double *y = new double[nx];
-        for (int i = 0; i < nx; ++i) {
-            double rhs = (i == 0) ? gam : (i == nx - 1 ? -cx : 0.0);
-            y[i] = (rhs - (i > 0 ? a[i] * y[i - 1] : 0.0)) * ip[i];
+    G.assign(P, 0.0);
+    for (int k = 0; k < P; ++k) {
+        double acc = 0.0;
+        long long idx = 0;
+        for (int m = 0; m < P; ++m) {
+            acc += ct[idx] * inv[m];
+            idx += k;
+            if (idx >= P) idx -= P;
         }
-        for (int i = nx - 2; i >= 0; --i) y[i] -= cp[i] * y[i + 1];
-        double vz = y[0] + bg * y[nx - 1];
-        for (int i = 0; i < nx; ++i) tri[3 * nx + i] = (float)y[i];
-        tri[4 * nx] = (float)bg;
-        tri[4 * nx + 1] = (float)(1.0 / (1.0 + vz));
-        delete[] y;
+        G[k] = acc / P;
     }
-    delete[] a;
-    delete[] c;
-    delete[] dd;
-    delete[] cp;
-    delete[] ip;
 }
 
-// neighbour index along a coarse/fine axis with periodic wrap or Neumann mirror
+// Fills Gs (length kmax - kmin + 1, Gs[k - kmin] = G_k) for the line operator of
+// a level; returns kmin (kmax = -kmin for a truncated kernel, P - 1 for a full one).
+int mg_line_kernel(int nx, int bcx, double cx, double s, std::vector<float> &Gs)
+{
+    const int P = mg_period(nx, bcx);
+    std::vector<double> G;
+    green(P, cx, s, G);
+    int B = 0;
+    for (int k = 1; k <= P / 2; ++k)
+        if (fabs(G[k]) > 2e-9 * fabs(G[0])) B = k;
+    Gs.clear();
+    if (2 * B + 1 < P) {
+        for (int k = -B; k <= B; ++k) Gs.push_back((float)G[(k + P) % P]);
+        return -B;
+    }
+    for (int k = 0; k < P; ++k) Gs.push_back((float)G[k]);
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// neighbour index along an axis with periodic wrap or Neumann mirror
 __device__ __forceinline__ int nb_idx(int j, int d, int n, int bc)
 {
     int q = j + d;
@@ -101,6 +107,17 @@ __device__ __forceinline__ int nb_idx(int j, int d, int n, int bc)
     }
     return q;
 }
+
+// index of the extended (periodic or mirrored) x line
+__device__ __forceinline__ int ext_idx(int j, int nx, int P, int open)
+{
+    int q = j % P;
+    if (q < 0) q += P;
+    if (open && q > nx - 1) q = P - q;
+    return q;
+}
+
+__device__ __forceinline__ int pad(int j) { return j + (j >> 5); }
 
 // q-th line of colour c ((j + k) % 2 == c) on an ny x nz line grid
 __device__ __forceinline__ void line_jk(long long q, int c, int ny, int nz, int &j, int &k)
@@ -131,12 +148,37 @@ static long long lines_of_colour(int ny, int nz, int c)
     return n;
 }
 
+// Convolve one padded smem line with the kernel Gs: outputs i0 .. i0+kR-1.
+// out[r] = sum_{k=kmin}^{kmax} Gs[k - kmin] * line(ext(i0 + r + k))
+__device__ __forceinline__ void line_convolve(const float *__restrict__ line, const float *__restrict__ Gs, int kmin,
+                                              int kmax, int i0, int nx, int P, int open, float out[kR])
+{
+    float w[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        w[r] = line[pad(ext_idx(i0 + r + kmin, nx, P, open))];
+        out[r] = 0.f;
+    }
+    for (int k = kmin; k <= kmax; ++k) {
+        const float g = Gs[k - kmin];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) out[r] = fmaf(g, w[r], out[r]);
+#pragma unroll
+        for (int r = 0; r < kR - 1; ++r) w[r] = w[r + 1];
+        w[kR - 1] = line[pad(ext_idx(i0 + kR + k, nx, P, open))];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// zebra x-line smoother
+// ---------------------------------------------------------------------------
 struct LineArgs {
     MGLevel L;
     int bcx, bcy, bcz;
     int color;
     long long nlines;
-    int lpb;
+    int lpb;                   // lines per block
+    int tpl;                   // threads per line (ceil(nx / kR))
     const DevCtl *ctl;
     int level0;
 };
@@ -146,9 +188,10 @@ __global__ void __launch_bounds__(kThreads) line_smooth_kernel(LineArgs A)
     extern __shared__ float sm[];
     const MGLevel &L = A.L;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int stride = nx + 1;
-    float *tri = sm + A.lpb * stride;
-    for (int t = threadIdx.x; t < 4 * nx + 2; t += blockDim.x) tri[t] = L.tri[t];
+    const int lstride = pad(nx) + 1;
+    float *Gs = sm + A.lpb * lstride;
+    const int nG = L.kmax - L.kmin + 1;
+    for (int t = threadIdx.x; t < nG; t += blockDim.x) Gs[t] = L.G[t];
     const long long q0 = (long long)blockIdx.x * A.lpb;
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
     const long long plane = (long long)nx * ny;
@@ -167,39 +210,24 @@ __global__ void __launch_bounds__(kThreads) line_smooth_kernel(LineArgs A)
             int kp = nb_idx(k, 1, nz, A.bcz), km = nb_idx(k, -1, nz, A.bcz);
             v += L.cz * (L.u[(long long)nx * j + plane * kp + i] + L.u[(long long)nx * j + plane * km + i]);
         }
-        sm[q * stride + i] = v;
+        sm[q * lstride + pad(i)] = v;
     }
     __syncthreads();
-    if (threadIdx.x < A.lpb && q0 + threadIdx.x < A.nlines) {
-        float *row = sm + threadIdx.x * stride;
-        const float *cp = tri, *ip = tri + nx, *aa = tri + 2 * nx, *zz = tri + 3 * nx;
-        float y = row[0] * ip[0];
-        row[0] = y;
-        for (int i = 1; i < nx; ++i) {
-            y = (row[i] - aa[i] * y) * ip[i];
-            row[i] = y;
-        }
-        float x = row[nx - 1];
-        for (int i = nx - 2; i >= 0; --i) {
-            x = row[i] - cp[i] * x;
-            row[i] = x;
-        }
-        if (A.bcx == kPeriodic) {
-            const float fac = (row[0] + tri[4 * nx] * row[nx - 1]) * tri[4 * nx + 1];
-            for (int i = 0; i < nx; ++i) row[i] -= fac * zz[i];
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < A.lpb * nx; e += blockDim.x) {
-        const int q = e / nx, i = e - q * nx;
-        if (q0 + q >= A.nlines) break;
+    const int q = threadIdx.x / A.tpl;
+    const int i0 = (threadIdx.x - q * A.tpl) * kR;
+    if (q < A.lpb && q0 + q < A.nlines && i0 < nx) {
+        float out[kR];
+        line_convolve(sm + q * lstride, Gs, L.kmin, L.kmax, i0, nx, L.P, A.bcx == kOpen, out);
         int j, k;
         line_jk(q0 + q, A.color, ny, nz, j, k);
-        L.u[(long long)nx * j + plane * k + i] = sm[q * stride + i];
+        float *dst = L.u + (long long)nx * j + plane * k;
+#pragma unroll
+        for (int r = 0; r < kR; ++r)
+            if (i0 + r < nx) dst[i0 + r] = out[r];
     }
 }
 
-// t = F - L u on one level (level 0: F = f - fmean).  Optionally the max norms.
+// t = F - L u on one level (level 0: F = f - fmean)
 __global__ void residual_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0)
 {
     const float fsub = level0 ? (float)ctl->fmean : 0.f;
@@ -340,6 +368,11 @@ __global__ void prolong_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
     }
 }
 
+static size_t line_smem(int lpb, int nx, int nG)
+{
+    return sizeof(float) * ((size_t)lpb * (nx + nx / 32 + 2) + nG);
+}
+
 static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s, long long *nl)
 {
     const MGLevel &L = a.lev[l];
@@ -352,16 +385,17 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.nlines = lines_of_colour(L.ny, L.nz, color);
     A.ctl = a.ctl;
     A.level0 = (l == 0);
-    int lpb = (int)((200 * 1024 - 4 * (4 * L.nx + 2)) / (4 * (L.nx + 1)));
-    if (lpb > 32) lpb = 32;
+    A.tpl = (L.nx + kR - 1) / kR;
+    int lpb = kThreads / A.tpl;
     if (lpb < 1) lpb = 1;
     A.lpb = lpb;
     if (A.nlines == 0) return cudaSuccess;
-    size_t smem = (size_t)4 * (lpb * (L.nx + 1) + 4 * L.nx + 2);
+    const int nG = L.kmax - L.kmin + 1;
+    size_t smem = line_smem(lpb, L.nx, nG);
     int nb = (int)((A.nlines + lpb - 1) / lpb);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(line_smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        cudaFuncSetAttribute(line_smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
     line_smooth_kernel<<<nb, kThreads, smem, s>>>(A);
@@ -369,10 +403,195 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Exact solve on the coarsest level: forward y-z transform, per-mode line
+// convolution, inverse transform.  cw = [W (M x M) | V (M x M) | Gq (M x P)].
+// ---------------------------------------------------------------------------
+static void yz_basis(int n, int bc, double c, std::vector<double> &V, std::vector<double> &lam)
+{
+    const double pi = 3.14159265358979323846;
+    V.assign((size_t)n * n, 0.0);
+    lam.assign(n, 0.0);
+    if (n == 1) {
+        V[0] = 1.0;
+        return;
+    }
+    if (bc == kOpen) {
+        for (int k = 0; k < n; ++k) {
+            for (int j = 0; j < n; ++j) V[(size_t)j * n + k] = cos(pi * k * j / (n - 1));
+            double sn = sin(pi * k / (2.0 * (n - 1)));
+            lam[k] = -4.0 * c * sn * sn;
+        }
+        return;
+    }
+    int col = 0;
+    for (int j = 0; j < n; ++j) V[(size_t)j * n + col] = 1.0;
+    lam[col++] = 0.0;
+    for (int k = 1; 2 * k < n; ++k) {
+        double sn = sin(pi * k / n);
+        for (int j = 0; j < n; ++j) V[(size_t)j * n + col] = cos(2.0 * pi * k * j / n);
+        lam[col++] = -4.0 * c * sn * sn;
+        for (int j = 0; j < n; ++j) V[(size_t)j * n + col] = sin(2.0 * pi * k * j / n);
+        lam[col++] = -4.0 * c * sn * sn;
+    }
+    if (n % 2 == 0) {
+        for (int j = 0; j < n; ++j) V[(size_t)j * n + col] = (j % 2) ? -1.0 : 1.0;
+        lam[col++] = -4.0 * c;
+    }
+}
+
+static bool invert(int n, const std::vector<double> &A, std::vector<double> &Ainv)
+{
+    std::vector<double> a(A);
+    Ainv.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Ainv[(size_t)i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(a[(size_t)r * n + c]) > fabs(a[(size_t)p * n + c])) p = r;
+        if (fabs(a[(size_t)p * n + c]) < 1e-300) return false;
+        for (int k = 0; k < n; ++k) {
+            std::swap(a[(size_t)c * n + k], a[(size_t)p * n + k]);
+            std::swap(Ainv[(size_t)c * n + k], Ainv[(size_t)p * n + k]);
+        }
+        double d = 1.0 / a[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) {
+            a[(size_t)c * n + k] *= d;
+            Ainv[(size_t)c * n + k] *= d;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = a[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
+                Ainv[(size_t)r * n + k] -= f * Ainv[(size_t)c * n + k];
+            }
+        }
+    }
+    return true;
+}
+
+size_t mg_coarse_floats(int nx, int bcx, int M) { return 2 * (size_t)M * M + (size_t)M * mg_period(nx, bcx); }
+
+bool mg_coarse_factors(int nx, int bcx, double cx, int ny, int nz, int bcy, int bcz, double cy, double cz, float *cw)
+{
+    std::vector<double> Vy, Vz, ly, lz, Wy, Wz;
+    yz_basis(ny, bcy, cy, Vy, ly);
+    yz_basis(nz, bcz, cz, Vz, lz);
+    if (!invert(ny, Vy, Wy) || !invert(nz, Vz, Wz)) return false;
+    const int M = ny * nz, P = mg_period(nx, bcx);
+    float *W = cw, *V = cw + (size_t)M * M, *Gq = cw + 2 * (size_t)M * M;
+    // site s = j + ny k, mode q = p + ny r
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int r = 0; r < nz; ++r)
+                for (int p = 0; p < ny; ++p) {
+                    const int s = j + ny * k, q = p + ny * r;
+                    V[(size_t)s * M + q] = (float)(Vy[(size_t)j * ny + p] * Vz[(size_t)k * nz + r]);
+                    W[(size_t)q * M + s] = (float)(Wy[(size_t)p * ny + j] * Wz[(size_t)r * nz + k]);
+                }
+    std::vector<double> G;
+    for (int r = 0; r < nz; ++r)
+        for (int p = 0; p < ny; ++p) {
+            const int q = p + ny * r;
+            double sigma = -(ly[p] + lz[r]);
+            if (sigma < 1e-12 * cx) sigma = 0.0;
+            green(P, cx, sigma, G);
+            for (int k = 0; k < P; ++k) Gq[(size_t)q * P + k] = (float)G[k];
+        }
+    return true;
+}
+
+struct CoarseArgs {
+    MGLevel L;
+    int bcx;
+    const DevCtl *ctl;
+    int level0;
+};
+
+// H[q][i] = sum_s W[q][s] * (-(r[s][i] - fsub)), stored in t
+__global__ void coarse_fwd_kernel(CoarseArgs A)
+{
+    const MGLevel &L = A.L;
+    const int nx = L.nx, M = L.M;
+    const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)M * nx; e += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(e / nx), i = (int)(e - (long long)q * nx);
+        float acc = 0.f;
+        for (int s = 0; s < M; ++s) acc += L.cw[(size_t)q * M + s] * (-(L.r[(size_t)s * nx + i] - fsub));
+        L.t[e] = acc;
+    }
+}
+
+// X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period, in place in t.  One block
+// owns a whole mode line (nx <= kThreads * kR), so it reads the line before writing it.
+__global__ void __launch_bounds__(kThreads) coarse_conv_kernel(CoarseArgs A)
+{
+    extern __shared__ float sm[];
+    const MGLevel &L = A.L;
+    const int nx = L.nx, M = L.M, P = L.P;
+    const int q = blockIdx.y;
+    float *line = sm;                       // padded copy of H[q]
+    float *Gs = sm + pad(nx) + 2;           // Gq[q], length P
+    const float *Gq = L.cw + 2 * (size_t)M * M + (size_t)q * P;
+    for (int t = threadIdx.x; t < nx; t += blockDim.x) line[pad(t)] = L.t[(size_t)q * nx + t];
+    for (int t = threadIdx.x; t < P; t += blockDim.x) Gs[t] = Gq[t];
+    __syncthreads();
+    const int i0 = threadIdx.x * kR;
+    if (i0 < nx) {
+        float out[kR];
+        line_convolve(line, Gs, 0, P - 1, i0, nx, P, A.bcx == kOpen, out);
+#pragma unroll
+        for (int r = 0; r < kR; ++r)
+            if (i0 + r < nx) L.t[(size_t)q * nx + i0 + r] = out[r];
+    }
+}
+
+// u[s][i] = sum_q V[s][q] X[q][i]  (X in t)
+__global__ void coarse_inv_kernel(CoarseArgs A)
+{
+    const MGLevel &L = A.L;
+    const int nx = L.nx, M = L.M;
+    const float *V = L.cw + (size_t)M * M;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)M * nx; e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / nx), i = (int)(e - (long long)s * nx);
+        float acc = 0.f;
+        for (int q = 0; q < M; ++q) acc += V[(size_t)s * M + q] * L.t[(size_t)q * nx + i];
+        L.u[e] = acc;
+    }
+}
+
+static cudaError_t coarse_solve(const PoissonArgs &a, int l, cudaStream_t s, long long *nl)
+{
+    CoarseArgs C;
+    C.L = a.lev[l];
+    C.bcx = a.g.bcx;
+    C.ctl = a.ctl;
+    C.level0 = (l == 0);
+    const long long n = (long long)C.L.M * C.L.nx;
+    int nb = (int)((n + kThreads - 1) / kThreads);
+    if (nb > 4096) nb = 4096;
+    coarse_fwd_kernel<<<nb, kThreads, 0, s>>>(C);
+    dim3 grid(1, C.L.M);
+    size_t smem = sizeof(float) * ((size_t)(C.L.nx + C.L.nx / 32 + 2) + C.L.P);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(coarse_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    coarse_conv_kernel<<<grid, kThreads, smem, s>>>(C);
+    coarse_inv_kernel<<<nb, kThreads, 0, s>>>(C);
+    *nl += 3;
+    return cudaGetLastError();
+}
+
 static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long *nl)
 {
     const int bcx = a.g.bcx, bcy = a.g.bcy, bcz = a.g.bcz;
     if (l == a.nlevels - 1) {
+        if (a.lev[l].cw) return coarse_solve(a, l, s, nl);
+        // no exact factors (too many y-z modes): relax
         int n = 2 * (a.lev[l].ny + a.lev[l].nz) + 8;
         for (int it = 0; it < n; ++it) {
             smooth(a, l, 0, s, nl);
@@ -419,12 +638,12 @@ __device__ __forceinline__ float site_w(const DevGrid &g, long long m)
 
 __global__ void mu_mean_kernel(DevGrid g, const float *mu, DevCtl *ctl, double *blockred, double wsum)
 {
-    double acc = 0.0;
+    float accf = 0.f;
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x)
-        acc += (double)(site_w(g, m) * mu[m]);
+        accf += site_w(g, m) * mu[m];
     __shared__ double shd[32];
     __shared__ int flag;
-    double s = block_sum(acc, shd);
+    double s = block_sum((double)accf, shd);
     if (threadIdx.x == 0) blockred[blockIdx.x] = s;
     if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
     double t = 0.0;
@@ -445,7 +664,7 @@ __global__ void mu_shift_kernel(long long N, float *mu, const DevCtl *ctl)
 
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s)
 {
-    int nb = grid_blocks(a.g.N, 8);
+    int nb = grid_blocks(a.g.N, 16);
     if (nb > 2048) nb = 2048;
     mu_mean_kernel<<<nb, kThreads, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum);
     mu_shift_kernel<<<grid_blocks(a.g.N, 8), kThreads, 0, s>>>(a.g.N, a.mu, a.ctl);

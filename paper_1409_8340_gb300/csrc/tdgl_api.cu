@@ -63,6 +63,9 @@ int validate(const tdgl_config *c)
     if ((long long)c->nx * c->ny * c->nz > (1LL << 33)) return TDGL_ERR_INVALID_ARG;
     for (int a = 0; a < 3; ++a)
         if (c->bc[a] != TDGL_PERIODIC && c->bc[a] != TDGL_OPEN) return TDGL_ERR_INVALID_ARG;
+    if ((c->bc[0] == TDGL_PERIODIC && c->nx < 3) || (c->bc[1] == TDGL_PERIODIC && c->ny < 3) ||
+        (c->bc[2] == TDGL_PERIODIC && c->nz == 2))
+        return TDGL_ERR_INVALID_ARG;   // a periodic axis needs distinct forward and backward neighbours
     if (!(c->hx > 0) || !(c->hy > 0) || !(c->hz > 0) || !(c->g > 0) || !(c->ht > 0)) return TDGL_ERR_INVALID_ARG;
     if (!(c->u > 0) || !(c->beta >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->max_iter < 1 || c->check_every < 1 || c->fixed_sweeps < 0) return TDGL_ERR_INVALID_ARG;
@@ -89,6 +92,7 @@ struct Layout {
     int ny[kMaxLevels], nz[kMaxLevels], fy[kMaxLevels], fz[kMaxLevels];
     size_t u[kMaxLevels], r[kMaxLevels], tri[kMaxLevels];
     size_t nblockred;
+    size_t cw;        // coarsest-level eigen-factors (0: none, the coarsest level is relaxed)
 };
 
 bool can_coarsen(int n, int bc)
@@ -135,7 +139,7 @@ Layout layout(const tdgl_config *c)
     for (;;) {
         L.ny[l] = ny;
         L.nz[l] = nz;
-        L.tri[l] = take(4 * (size_t)(4 * c->nx + 2));
+        L.tri[l] = take(4 * (size_t)mg_period(c->nx, c->bc[0]));
         if (l > 0) {
             L.u[l] = take(4 * (size_t)c->nx * ny * nz);
             L.r[l] = take(4 * (size_t)c->nx * ny * nz);
@@ -153,6 +157,11 @@ Layout layout(const tdgl_config *c)
         ++l;
     }
     L.nlevels = l + 1;
+    {
+        // exact coarsest solve when the dense y-z basis stays small
+        const int M = L.ny[l] * L.nz[l];
+        L.cw = (M <= 1024) ? take(sizeof(float) * mg_coarse_floats(c->nx, c->bc[0], M)) : 0;
+    }
     L.total = off;
     return L;
 }
@@ -369,7 +378,7 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     pa.Jext = c.Jext;
     pa.inject = (c.bc[0] == TDGL_OPEN && c.Jext != 0.0) ? 1 : 0;
     pa.wsum = h->wsum;
-    std::vector<float> tri(4 * c.nx + 2);
+    std::vector<float> tri;
     double hy = c.hy, hz = c.hz;
     for (int l = 0; l < L.nlevels; ++l) {
         MGLevel &M = pa.lev[l];
@@ -385,9 +394,22 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
         M.u = (l == 0) ? h->mu : at<float>(ws, L.u[l]);
         M.r = (l == 0) ? h->f : at<float>(ws, L.r[l]);
         M.t = at<float>(ws, L.t);
-        M.tri = at<float>(ws, L.tri[l]);
-        mg_line_factors(c.nx, c.bc[0], M.cx, M.cy, M.cz, tri.data());
-        chk(cudaMemcpyAsync(M.tri, tri.data(), 4 * tri.size(), cudaMemcpyHostToDevice, s));
+        M.G = at<float>(ws, L.tri[l]);
+        M.P = mg_period(c.nx, c.bc[0]);
+        M.kmin = mg_line_kernel(c.nx, c.bc[0], M.cx, 2.0 * M.cy + 2.0 * M.cz, tri);
+        M.kmax = M.kmin + (int)tri.size() - 1;
+        chk(cudaMemcpyAsync(M.G, tri.data(), 4 * tri.size(), cudaMemcpyHostToDevice, s));
+        M.cw = nullptr;
+        M.M = M.ny * M.nz;
+        std::vector<float> cwh;
+        if (l == L.nlevels - 1 && L.cw) {
+            cwh.resize(mg_coarse_floats(c.nx, c.bc[0], M.M));
+            if (mg_coarse_factors(c.nx, c.bc[0], M.cx, M.ny, M.nz, c.bc[1], c.bc[2], M.cy, M.nz >= 2 ? M.cz : 0.0,
+                                  cwh.data())) {
+                M.cw = at<float>(ws, L.cw);
+                chk(cudaMemcpyAsync(M.cw, cwh.data(), 4 * cwh.size(), cudaMemcpyHostToDevice, s));
+            }
+        }
         if (M.fy == 2) hy *= 2.0;
         if (M.fz == 2) hz *= 2.0;
         // a synchronous wait keeps `tri` valid for the copy above

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/tdgl.h"
 
 namespace tdgl {
@@ -189,8 +191,19 @@ struct MGLevel {
     float *u;                  // solution / correction
     float *r;                  // right-hand side
     float *t;                  // residual scratch
-    float *tri;                // x-line factors: [nx] c', [nx] 1/pivot, [nx] SM z, [1] SM factor
+    float *G;                  // x-line inverse kernel G_k, k = kmin..kmax (device)
+    int P;                     // period of the extended x line: nx (periodic) or 2(nx-1) (open)
+    int kmin, kmax;            // kernel support (kmax - kmin + 1 <= P)
+    float *cw;                 // coarsest level only: [W (M x M) | V (M x M) | G_q (M x P)], or nullptr
+    int M;                     // number of y-z modes of the coarsest level (ny * nz)
 };
+int mg_period(int nx, int bcx);
+// Line-inverse kernel of a level with shift s = 2 cy + 2 cz; returns kmin.
+int mg_line_kernel(int nx, int bcx, double cx, double s, std::vector<float> &Gs);
+// Eigen-decomposition of the coarsest level's y-z operator and per-mode kernels
+// (host, FP64 -> f32), M = ny*nz.  Returns false if the basis is singular.
+size_t mg_coarse_floats(int nx, int bcx, int M);
+bool mg_coarse_factors(int nx, int bcx, double cx, int ny, int nz, int bcy, int bcz, double cy, double cz, float *cw);
 struct PoissonArgs {
     DevGrid g;
     DevCtl *ctl;
@@ -208,7 +221,6 @@ cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launc
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
-void mg_line_factors(int nx, int bcx, float cx, float cy, float cz, float *host_tri);
 
 // Observables
 cudaError_t launch_observables(const DevGrid &g, DevCtl *ctl, double *blockred, const float2 *psi,

@@ -52,11 +52,13 @@ def test_gauge_invariance_fp32(O):
 
 def test_uniform_fixed_point_and_plane_wave(O):
     from paper_1409_8340_gb300.solver import Params
-    p = Params(32, 8, 8, bc=(P, P, P), fixed_sweeps=60, Jext=0.02, beta=1.0, poisson_tol=1e-6)
+    # zero field, zero current: |psi|^2 = alpha/beta is a fixed point
+    p0 = Params(32, 8, 8, bc=(P, P, P), fixed_sweeps=60, Jext=0.0, beta=1.0, poisson_tol=1e-6)
     alpha = 0.8
-    psi = np.full(p.shape, math.sqrt(alpha) * np.exp(0.4j), dtype=np.complex64)
-    s = make_solver(p, np.full(p.shape, alpha, np.float32), psi)
-    # plane wave exp(i k x), k = 2 pi / Lx: amplitude and K follow the scalar recurrence
+    psi = np.full(p0.shape, math.sqrt(alpha) * np.exp(0.4j), dtype=np.complex64)
+    s = make_solver(p0, np.full(p0.shape, alpha, np.float32), psi)
+    # plane wave exp(i k x), k = 2 pi / Lx, under current: amplitude and K follow the scalar recurrence
+    p = Params(32, 8, 8, bc=(P, P, P), fixed_sweeps=60, Jext=0.02, beta=1.0, poisson_tol=1e-6)
     k = 2 * math.pi / p.length(0)
     x = np.arange(p.nx) * p.hx
     pw = (0.55 * np.exp(1j * k * x))[None, None, :] * np.ones(p.shape)

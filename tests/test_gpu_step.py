@@ -4,6 +4,7 @@ Grids span several 32x8 tiles with ragged tails, every boundary combination,
 a film (Nz = 1), anisotropy g != 1 and both field components.  Tolerance:
 per-step max |psi_GPU - psi_oracle| <= 2e-5 (FP32 arithmetic against FP64).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -32,8 +33,14 @@ def cases():
 CASES = cases()
 
 
+def fresh(p):
+    """Each test works on its own copy of the case parameters."""
+    return dataclasses.replace(p)
+
+
 @pytest.mark.parametrize("name,p", CASES, ids=[c[0] for c in CASES])
 def test_init_and_first_sweep(O, name, p):
+    p = fresh(p)
     p.fixed_sweeps = 1
     G = oracle_grid(O, p)
     psi0 = I.random_psi(p.nx, p.ny, p.nz, 7)
@@ -55,6 +62,7 @@ def test_init_and_first_sweep(O, name, p):
 @pytest.mark.parametrize("name,p", CASES, ids=[c[0] for c in CASES])
 def test_fixed_sweeps_trajectory(O, name, p):
     """10 full steps (psi, K, mu) with exactly 40 sweeps per step on both sides."""
+    p = fresh(p)
     p.fixed_sweeps = 40
     p.poisson_tol = 1e-5
     p.poisson_max_cycles = 60
@@ -79,6 +87,7 @@ def test_fixed_sweeps_trajectory(O, name, p):
 def test_tolerance_mode_per_step(O, name, p):
     """Convergence-tested steps: from the same input state, the oracle and the GPU
     take the same number of sweeps and produce the same psi."""
+    p = fresh(p)
     if p.eps > 1e-8:
         p.eps = 1e-7
     p.poisson_tol = 1e-5
