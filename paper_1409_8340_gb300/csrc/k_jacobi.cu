@@ -11,6 +11,7 @@
 // convergence flag, result buffer).  Sweeps launched after convergence exit at
 // their first instruction, so the host can enqueue several sweeps ahead.
 #include <float.h>
+#include <string.h>
 
 #include "tdgl_internal.cuh"
 
@@ -316,26 +317,262 @@ __global__ void __launch_bounds__(kBX *kBY) poisson_rhs_kernel(DevGrid g, DevCtl
     }
 }
 
+// ---------------------------------------------------------------------------
+// Landau-gauge sweep, two sites per thread (even nx): each thread owns the x pair
+// (x, x+1) of one row and marches in z.  16-byte loads of psi, b and D; the x
+// neighbours of the pair come from the adjacent lanes by warp shuffles; the
+// next plane's b, D and psi(k+1) are requested before the current plane is
+// computed, so each thread keeps two planes of loads in flight.
+// INIT: also forms b and diag M from psi^-, mu and alpha (first sweep).
+// ---------------------------------------------------------------------------
+constexpr int kPX = 64;   // x sites per block (32 lanes x 2)
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// Block FP64 sum of w f, finished by the last block into ctl->fmean.
+__device__ __forceinline__ void finish_rhs_sum(DevCtl *ctl, double *blockred, double v, double wsum)
+{
+    __shared__ double shd[32];
+    __shared__ int flag;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    double s = block_sum(v, shd);
+    if (tid == 0) blockred[bid] = s;
+    if (!last_block(&ctl->ticket, nb, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = tid; q < nb; q += blockDim.x * blockDim.y) t += ((volatile double *)blockred)[q];
+    t = block_sum(t, shd);
+    if (tid == 0) {
+        ctl->ticket = 0u;
+        ctl->fmean = t / wsum;
+    }
+}
+
+// MODE 0: Jacobi sweep; 1: init + first sweep; 2: Poisson right-hand side
+template <int MODE>
+__global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
+{
+    constexpr bool INIT = (MODE == 1);
+    constexpr bool RHS = (MODE == 2);
+    if (MODE == 0 && *(volatile int *)&a.ctl->done) return;
+    const DevGrid &g = a.g;
+    const int tx = threadIdx.x;
+    const int x = (blockIdx.x * kBX + tx) * 2;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k0 = blockIdx.z * kz;
+    const int k1 = min(k0 + kz, g.nz);
+    const bool in = (x < g.nx) && (j < g.ny);
+    const float2 Ux = a.ctl->Ux;
+    const float4 *__restrict__ src = reinterpret_cast<const float4 *>(a.src);
+    const float2 *__restrict__ src2 = a.src;
+    const float4 *__restrict__ bq = reinterpret_cast<const float4 *>(a.b);
+    const float4 *__restrict__ Dq = reinterpret_cast<const float4 *>(a.D);
+    const float2 *__restrict__ mu2 = reinterpret_cast<const float2 *>(a.mu);
+    const float2 *__restrict__ al2 = reinterpret_cast<const float2 *>(a.alpha);
+    float4 *__restrict__ dst = reinterpret_cast<float4 *>(a.dst);
+    float4 *__restrict__ bout = reinterpret_cast<float4 *>(a.b);
+    float4 *__restrict__ Dout = reinterpret_cast<float4 *>(a.D);
+
+    const long long rowq = g.nx >> 1;                       // float4 per row
+    const long long plq = rowq * g.ny;                       // float4 per plane
+    const long long sz = (long long)g.nx * g.ny;             // sites per plane
+    const bool xper = (g.bcx == kPeriodic), yper = (g.bcy == kPeriodic), zper = (g.bcz == kPeriodic);
+    const bool xlo = (x == 0), xhi = (x + 2 >= g.nx);
+    const bool ylo = (j == 0), yhi = (j == g.ny - 1);
+    const int jc = min(j, g.ny - 1);
+    const int jp = yhi ? (yper ? 0 : jc) : jc + 1;
+    const int jm = ylo ? (yper ? g.ny - 1 : jc) : jc - 1;
+    const long long q0 = (x >> 1) + rowq * jc;               // float4 index in plane 0
+    // links of the pair
+    float2 Uy0 = cmk(1.f, 0.f), Uy1 = cmk(1.f, 0.f), Uz0 = cmk(1.f, 0.f), Uz1 = cmk(1.f, 0.f);
+    if (in) {
+        const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
+        const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
+        Uy0 = lo2(uy);
+        Uy1 = hi2(uy);
+        Uz0 = lo2(uz);
+        Uz1 = hi2(uz);
+    }
+    const float wy_f = yper ? 1.f : (ylo ? 2.f : (yhi ? 0.f : 1.f));
+    const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
+    const bool zact = g.nz >= 2;
+
+    auto knext = [&](int k) { return (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1; };
+    float4 pzm = make_float4(0.f, 0.f, 0.f, 0.f), pc = pzm, pzp_n = pzm, b_n = pzm, D_n = pzm;
+    float2 mu_n = cmk(0.f, 0.f), al_n = mu_n;
+    if (in) {
+        if (zact) pzm = src[q0 + plq * ((k0 == 0) ? (zper ? g.nz - 1 : 1) : k0 - 1)];
+        pc = src[q0 + plq * k0];
+        if (zact) pzp_n = src[q0 + plq * knext(k0)];
+        if (INIT) {
+            mu_n = mu2[(q0 + plq * k0)];
+            al_n = al2[(q0 + plq * k0)];
+        } else if (!RHS) {
+            b_n = bq[q0 + plq * k0];
+            D_n = Dq[q0 + plq * k0];
+        }
+    }
+    float rmax = 0.f;
+    float facc = 0.f;   // RHS: sum of w f over this thread's sites
+    float wxy0 = 1.f, wxy1 = 1.f;
+    if (RHS) {
+        const float wy = (g.bcy == kOpen && (j == 0 || j == g.ny - 1)) ? 0.5f : 1.f;
+        wxy0 = wy * ((g.bcx == kOpen && x == 0) ? 0.5f : 1.f);
+        wxy1 = wy * ((g.bcx == kOpen && x + 1 == g.nx - 1) ? 0.5f : 1.f);
+    }
+    for (int k = k0; k < k1; ++k) {
+        const float4 pzp = pzp_n;
+        const float4 bc = b_n, Dc = D_n;
+        const float2 muc = mu_n, alc = al_n;
+        const long long q = q0 + plq * k;
+        float4 yf = make_float4(0.f, 0.f, 0.f, 0.f), yb = yf;
+        float2 xl = cmk(0.f, 0.f), xr = xl;
+        if (in) {
+            if (k + 1 < k1) {
+                if (zact) pzp_n = src[q0 + plq * knext(k + 1)];
+                if (INIT) {
+                    mu_n = mu2[q + plq];
+                    al_n = al2[q + plq];
+                } else if (!RHS) {
+                    b_n = bq[q + plq];
+                    D_n = Dq[q + plq];
+                }
+            }
+            yf = src[(x >> 1) + rowq * jp + plq * k];
+            yb = src[(x >> 1) + rowq * jm + plq * k];
+        }
+        // x neighbours: left of x from lane tx-1, right of x+1 from lane tx+1
+        const float2 from_left = make_float2(__shfl_up_sync(0xffffffffu, pc.z, 1), __shfl_up_sync(0xffffffffu, pc.w, 1));
+        const float2 from_right =
+            make_float2(__shfl_down_sync(0xffffffffu, pc.x, 1), __shfl_down_sync(0xffffffffu, pc.y, 1));
+        const long long m = (long long)x + (long long)g.nx * jc + sz * k;   // site index of x
+        if (in) {
+            if (tx > 0) xl = from_left;
+            else if (!xlo) xl = src2[m - 1];
+            else if (xper) xl = src2[m + g.nx - 1];
+            if (!xhi && tx < kBX - 1) xr = from_right;
+            else if (!xhi) xr = src2[m + 2];
+            else if (xper) xr = src2[m + 2 - g.nx];
+        }
+        if (in) {
+            const float2 c0 = lo2(pc), c1 = hi2(pc);
+            // x part, site x: fwd = Ux c1, bwd = conj(Ux or wrap link) xl
+            float2 bwd0 = cmulc(Ux, xl);
+            if (xlo && xper) bwd0 = cmulc(cmulc(cmul(g.Py[jc], g.Pz[k]), Ux), xl);
+            float2 tx0 = cadd(cmul(Ux, c1), bwd0);
+            if (!xper && xlo) tx0 = cscale(2.f, cmul(Ux, c1));
+            // site x+1: fwd = Ux (or wrap link) xr, bwd = conj(Ux) c0
+            float2 fwd1 = cmul(Ux, xr);
+            if (xhi && xper) fwd1 = cmul(cmulc(cmul(g.Py[jc], g.Pz[k]), Ux), xr);
+            float2 tx1 = cadd(fwd1, cmulc(Ux, c0));
+            if (!xper && xhi) tx1 = cscale(2.f, cmulc(Ux, c0));
+            // y part
+            const float2 ty0 = cadd(cscale(wy_f, cmul(Uy0, lo2(yf))), cscale(wy_b, cmulc(Uy0, lo2(yb))));
+            const float2 ty1 = cadd(cscale(wy_f, cmul(Uy1, hi2(yf))), cscale(wy_b, cmulc(Uy1, hi2(yb))));
+            float2 ns0 = cadd(cscale(g.cx, tx0), cscale(g.cy, ty0));
+            float2 ns1 = cadd(cscale(g.cx, tx1), cscale(g.cy, ty1));
+            if (zact) {
+                const bool zlo = (k == 0), zhi = (k == g.nz - 1);
+                const float wz_f = zper ? 1.f : (zlo ? 2.f : (zhi ? 0.f : 1.f));
+                const float wz_b = zper ? 1.f : (zhi ? 2.f : (zlo ? 0.f : 1.f));
+                const float2 tz0 = cadd(cscale(wz_f, cmul(Uz0, lo2(pzp))), cscale(wz_b, cmulc(Uz0, lo2(pzm))));
+                const float2 tz1 = cadd(cscale(wz_f, cmul(Uz1, hi2(pzp))), cscale(wz_b, cmulc(Uz1, hi2(pzm))));
+                ns0 = cadd(ns0, cscale(g.cz, tz0));
+                ns1 = cadd(ns1, cscale(g.cz, tz1));
+            }
+            if (RHS) {
+                // f = Im[conj(psi) NS(psi)] plus the open-x injection terms
+                float f0 = c0.x * ns0.y - c0.y * ns0.x;
+                float f1 = c1.x * ns1.y - c1.y * ns1.x;
+                if (!xper) {
+                    if (xlo) f0 -= a.inj;
+                    if (xhi) f1 += a.inj;
+                }
+                reinterpret_cast<float2 *>(a.f)[q] = make_float2(f0, f1);
+                const float wz = (g.bcz == kOpen && g.nz >= 2 && (k == 0 || k == g.nz - 1)) ? 0.5f : 1.f;
+                facc += wz * (wxy0 * f0 + wxy1 * f1);
+                pzm = pc;
+                pc = pzp;
+                continue;
+            }
+            float2 b0, b1, D0, D1;
+            if (INIT) {
+                const float2 cs[2] = {c0, c1};
+                const float2 nss[2] = {ns0, ns1};
+                const float mus[2] = {muc.x, muc.y}, als[2] = {alc.x, alc.y};
+                float2 bo[2], Do[2];
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const float a2 = cabs2(cs[s2]);
+                    Do[s2] = cmk(1.f + g.ht2 * (g.beta * a2 + 2.f * g.S - als[s2]), g.ht2 * g.u * mus[s2]);
+                    const float cr = als[s2] - g.beta * a2 - 2.f * g.S;
+                    const float ci = -g.u * mus[s2];
+                    const float2 lin = cmk(cr * cs[s2].x - ci * cs[s2].y, cr * cs[s2].y + ci * cs[s2].x);
+                    bo[s2] = cadd(cs[s2], cscale(g.ht2, cadd(lin, nss[s2])));
+                }
+                b0 = bo[0];
+                b1 = bo[1];
+                D0 = Do[0];
+                D1 = Do[1];
+                bout[q] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                Dout[q] = make_float4(D0.x, D0.y, D1.x, D1.y);
+            } else {
+                b0 = lo2(bc);
+                b1 = hi2(bc);
+                D0 = lo2(Dc);
+                D1 = hi2(Dc);
+            }
+            const float2 s0 = cadd(b0, cscale(g.ht2, ns0)), s1 = cadd(b1, cscale(g.ht2, ns1));
+            const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
+            const float2 n0 = cscale(1.0f / cabs2(D0), cmulc(D0, s0));
+            const float2 n1 = cscale(1.0f / cabs2(D1), cmulc(D1, s1));
+            dst[q] = make_float4(n0.x, n0.y, n1.x, n1.y);
+            float r2a = cabs2(r0), r2b = cabs2(r1);
+            r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
+            r2b = (r2b <= FLT_MAX) ? r2b : INFINITY;
+            rmax = fmaxf(rmax, fmaxf(r2a, r2b));
+        }
+        pzm = pc;
+        pc = pzp;
+    }
+    if (RHS) {
+        finish_rhs_sum(a.ctl, a.blockred, (double)facc, a.wsum);
+        return;
+    }
+    finish_sweep(a, rmax, INIT);
+}
+
 static dim3 sweep_grid(const DevGrid &g, int kz)
 {
     return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, (g.nz + kz - 1) / kz);
 }
 
+static dim3 sweep2_grid(const DevGrid &g, int kz)
+{
+    return dim3((g.nx + kPX - 1) / kPX, (g.ny + kBY - 1) / kBY, (g.nz + kz - 1) / kz);
+}
+
+static bool use_sweep2(const DevGrid &g) { return g.L == nullptr && (g.nx % 2) == 0; }
+
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s)
 {
     int kz = zchunk(a.g);
-    dim3 grid = sweep_grid(a.g, kz), block(kBX, kBY);
-    if (a.g.L) init_sweep_kernel<true><<<grid, block, 0, s>>>(a, kz);
-    else init_sweep_kernel<false><<<grid, block, 0, s>>>(a, kz);
+    dim3 block(kBX, kBY);
+    if (use_sweep2(a.g)) sweep2_kernel<1><<<sweep2_grid(a.g, kz), block, 0, s>>>(a, kz);
+    else if (a.g.L) init_sweep_kernel<true><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
+    else init_sweep_kernel<false><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s)
 {
     int kz = zchunk(a.g);
-    dim3 grid = sweep_grid(a.g, kz), block(kBX, kBY);
-    if (a.g.L) sweep_kernel<true><<<grid, block, 0, s>>>(a, kz);
-    else sweep_kernel<false><<<grid, block, 0, s>>>(a, kz);
+    dim3 block(kBX, kBY);
+    if (use_sweep2(a.g)) sweep2_kernel<0><<<sweep2_grid(a.g, kz), block, 0, s>>>(a, kz);
+    else if (a.g.L) sweep_kernel<true><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
+    else sweep_kernel<false><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
     return cudaGetLastError();
 }
 
@@ -344,7 +581,18 @@ cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStre
     int kz = zchunk(a.g);
     dim3 grid = sweep_grid(a.g, kz), block(kBX, kBY);
     float inj = a.inject ? (float)(2.0 * a.Jext / a.hx) : 0.f;
-    if (a.g.L) poisson_rhs_kernel<true><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
+    if (use_sweep2(a.g)) {
+        SweepArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.g = a.g;
+        sa.ctl = a.ctl;
+        sa.blockred = a.blockred;
+        sa.src = psi;
+        sa.f = a.f;
+        sa.inj = inj;
+        sa.wsum = a.wsum;
+        sweep2_kernel<2><<<sweep2_grid(a.g, kz), block, 0, s>>>(sa, kz);
+    } else if (a.g.L) poisson_rhs_kernel<true><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
     else poisson_rhs_kernel<false><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
     return cudaGetLastError();
 }

@@ -111,10 +111,10 @@ __device__ __forceinline__ int nb_idx(int j, int d, int n, int bc)
 // index of the extended (periodic or mirrored) x line
 __device__ __forceinline__ int ext_idx(int j, int nx, int P, int open)
 {
-    int q = j % P;
-    if (q < 0) q += P;
-    if (open && q > nx - 1) q = P - q;
-    return q;
+    while (j < 0) j += P;
+    while (j >= P) j -= P;
+    if (open && j > nx - 1) j = P - j;
+    return j;
 }
 
 __device__ __forceinline__ int pad(int j) { return j + (j >> 5); }
@@ -192,109 +192,124 @@ __global__ void __launch_bounds__(kThreads) line_smooth_kernel(LineArgs A)
     float *Gs = sm + A.lpb * lstride;
     const int nG = L.kmax - L.kmin + 1;
     for (int t = threadIdx.x; t < nG; t += blockDim.x) Gs[t] = L.G[t];
-    const long long q0 = (long long)blockIdx.x * A.lpb;
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
     const long long plane = (long long)nx * ny;
-    for (int e = threadIdx.x; e < A.lpb * nx; e += blockDim.x) {
-        const int q = e / nx, i = e - q * nx;
-        if (q0 + q >= A.nlines) break;
+    // thread (q, r): line q of the block, positions r, r + tpl, ... (load), r*kR .. r*kR + kR-1 (solve)
+    const int q = threadIdx.x / A.tpl;
+    const int r = threadIdx.x - q * A.tpl;
+    const long long line = (long long)blockIdx.x * A.lpb + q;
+    const bool active = (q < A.lpb) && (line < A.nlines);
+    long long base = 0;
+    if (active) {
         int j, k;
-        line_jk(q0 + q, A.color, ny, nz, j, k);
-        const long long base = (long long)nx * j + plane * k;
-        float v = -(L.r[base + i] - fsub);
+        line_jk(line, A.color, ny, nz, j, k);
+        base = (long long)nx * j + plane * k;
+        const float *__restrict__ rr = L.r + base;
+        const float *__restrict__ up = nullptr, *__restrict__ um = nullptr, *__restrict__ zp = nullptr,
+                                     *__restrict__ zm = nullptr;
         if (ny >= 2) {
-            int jp = nb_idx(j, 1, ny, A.bcy), jm = nb_idx(j, -1, ny, A.bcy);
-            v += L.cy * (L.u[(long long)nx * jp + plane * k + i] + L.u[(long long)nx * jm + plane * k + i]);
+            up = L.u + (long long)nx * nb_idx(j, 1, ny, A.bcy) + plane * k;
+            um = L.u + (long long)nx * nb_idx(j, -1, ny, A.bcy) + plane * k;
         }
         if (nz >= 2) {
-            int kp = nb_idx(k, 1, nz, A.bcz), km = nb_idx(k, -1, nz, A.bcz);
-            v += L.cz * (L.u[(long long)nx * j + plane * kp + i] + L.u[(long long)nx * j + plane * km + i]);
+            zp = L.u + (long long)nx * j + plane * nb_idx(k, 1, nz, A.bcz);
+            zm = L.u + (long long)nx * j + plane * nb_idx(k, -1, nz, A.bcz);
         }
-        sm[q * lstride + pad(i)] = v;
+        float *row = sm + q * lstride;
+#pragma unroll 8
+        for (int i = r; i < nx; i += A.tpl) {
+            float v = -(rr[i] - fsub);
+            if (up) v += L.cy * (up[i] + um[i]);
+            if (zp) v += L.cz * (zp[i] + zm[i]);
+            row[pad(i)] = v;
+        }
     }
     __syncthreads();
-    const int q = threadIdx.x / A.tpl;
-    const int i0 = (threadIdx.x - q * A.tpl) * kR;
-    if (q < A.lpb && q0 + q < A.nlines && i0 < nx) {
+    const int i0 = r * kR;
+    if (active && i0 < nx) {
         float out[kR];
         line_convolve(sm + q * lstride, Gs, L.kmin, L.kmax, i0, nx, L.P, A.bcx == kOpen, out);
-        int j, k;
-        line_jk(q0 + q, A.color, ny, nz, j, k);
-        float *dst = L.u + (long long)nx * j + plane * k;
+        float *dst = L.u + base;
 #pragma unroll
-        for (int r = 0; r < kR; ++r)
-            if (i0 + r < nx) dst[i0 + r] = out[r];
+        for (int rr2 = 0; rr2 < kR; ++rr2)
+            if (i0 + rr2 < nx) dst[i0 + rr2] = out[rr2];
     }
 }
 
-// t = F - L u on one level (level 0: F = f - fmean)
-__global__ void residual_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0)
+// 2D launch over (x, y) with a loop over z: thread (i, j) walks its z column.
+constexpr int kGX = 128;
+static dim3 grid_xy(int nx, int ny) { return dim3((nx + kGX - 1) / kGX, ny); }
+// 3D launch: (x, y, z-chunk of kGZ planes), enough independent threads to cover memory latency
+constexpr int kGZ = 4;
+static dim3 grid_xyz(int nx, int ny, int nz) { return dim3((nx + kGX - 1) / kGX, ny, (nz + kGZ - 1) / kGZ); }
+
+__device__ __forceinline__ float lap_at(const MGLevel &L, const float *__restrict__ u, int i, int j, int k, long long m,
+                                        int bcx, int bcy, int bcz)
 {
-    const float fsub = level0 ? (float)ctl->fmean : 0.f;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < L.N; m += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(m % nx);
-        long long t = m / nx;
-        int j = (int)(t % ny), k = (int)(t / ny);
-        const float u0 = L.u[m];
-        float lap = 0.f;
-        {
-            int ip = nb_idx(i, 1, nx, bcx), im = nb_idx(i, -1, nx, bcx);
-            lap += L.cx * (L.u[m - i + ip] + L.u[m - i + im] - 2.f * u0);
-        }
-        if (ny >= 2) {
-            int jp = nb_idx(j, 1, ny, bcy), jm = nb_idx(j, -1, ny, bcy);
-            lap += L.cy * (L.u[m + (long long)nx * (jp - j)] + L.u[m + (long long)nx * (jm - j)] - 2.f * u0);
-        }
-        if (nz >= 2) {
-            int kp = nb_idx(k, 1, nz, bcz), km = nb_idx(k, -1, nz, bcz);
-            const long long pl = (long long)nx * ny;
-            lap += L.cz * (L.u[m + pl * (kp - k)] + L.u[m + pl * (km - k)] - 2.f * u0);
-        }
-        L.t[m] = (L.r[m] - fsub) - lap;
+    const float u0 = u[m];
+    const int ip = nb_idx(i, 1, nx, bcx), im = nb_idx(i, -1, nx, bcx);
+    float lap = L.cx * (u[m - i + ip] + u[m - i + im] - 2.f * u0);
+    if (ny >= 2) {
+        const int jp = nb_idx(j, 1, ny, bcy), jm = nb_idx(j, -1, ny, bcy);
+        lap += L.cy * (u[m + (long long)nx * (jp - j)] + u[m + (long long)nx * (jm - j)] - 2.f * u0);
+    }
+    if (nz >= 2) {
+        const int kp = nb_idx(k, 1, nz, bcz), km = nb_idx(k, -1, nz, bcz);
+        const long long pl = (long long)nx * ny;
+        lap += L.cz * (u[m + pl * (kp - k)] + u[m + pl * (km - k)] - 2.f * u0);
+    }
+    return lap;
+}
+
+// t = F - L u on one level (level 0: F = f - fmean)
+__global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0)
+{
+    const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
+    if (i >= L.nx) return;
+    const float fsub = level0 ? (float)ctl->fmean : 0.f;
+    const long long pl = (long long)L.nx * L.ny;
+    const float *__restrict__ u = L.u;
+    const float *__restrict__ rr = L.r;
+    float *__restrict__ tt = L.t;
+    const int ka = blockIdx.z * kGZ, kb = min(ka + kGZ, L.nz);
+#pragma unroll
+    for (int dk = 0; dk < kGZ; ++dk) {
+        const int k = ka + dk;
+        if (k >= kb) break;
+        const long long m = i + (long long)L.nx * j + pl * k;
+        tt[m] = (rr[m] - fsub) - lap_at(L, u, i, j, k, m, bcx, bcy, bcz);
     }
 }
 
 // max |F - L u| and max |F| on level 0 (ctl->res = ratio)
-__global__ void residual_norm_kernel(MGLevel L, int bcx, int bcy, int bcz, DevCtl *ctl, double *blockred)
+__global__ void __launch_bounds__(kGX) residual_norm_kernel(MGLevel L, int bcx, int bcy, int bcz, DevCtl *ctl,
+                                                            double *blockred)
 {
+    const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
     const float fsub = (float)ctl->fmean;
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
     float rmax = 0.f, fmax = 0.f;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < L.N; m += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(m % nx);
-        long long t = m / nx;
-        int j = (int)(t % ny), k = (int)(t / ny);
-        const float u0 = L.u[m];
-        float lap = 0.f;
-        {
-            int ip = nb_idx(i, 1, nx, bcx), im = nb_idx(i, -1, nx, bcx);
-            lap += L.cx * (L.u[m - i + ip] + L.u[m - i + im] - 2.f * u0);
+    if (i < L.nx) {
+        const long long pl = (long long)L.nx * L.ny;
+        for (int k = 0; k < L.nz; ++k) {
+            const long long m = i + (long long)L.nx * j + pl * k;
+            const float F = L.r[m] - fsub;
+            rmax = fmaxf(rmax, fabsf(F - lap_at(L, L.u, i, j, k, m, bcx, bcy, bcz)));
+            fmax = fmaxf(fmax, fabsf(F));
         }
-        if (ny >= 2) {
-            int jp = nb_idx(j, 1, ny, bcy), jm = nb_idx(j, -1, ny, bcy);
-            lap += L.cy * (L.u[m + (long long)nx * (jp - j)] + L.u[m + (long long)nx * (jm - j)] - 2.f * u0);
-        }
-        if (nz >= 2) {
-            int kp = nb_idx(k, 1, nz, bcz), km = nb_idx(k, -1, nz, bcz);
-            const long long pl = (long long)nx * ny;
-            lap += L.cz * (L.u[m + pl * (kp - k)] + L.u[m + pl * (km - k)] - 2.f * u0);
-        }
-        const float F = L.r[m] - fsub;
-        rmax = fmaxf(rmax, fabsf(F - lap));
-        fmax = fmaxf(fmax, fabsf(F));
     }
     __shared__ float shf[32];
     __shared__ int flag;
+    const unsigned int bid = blockIdx.x + gridDim.x * blockIdx.y, nb = gridDim.x * gridDim.y;
     float a = block_max(rmax, shf);
     float b = block_max(fmax, shf);
     if (threadIdx.x == 0) {
-        blockred[2 * blockIdx.x] = a;
-        blockred[2 * blockIdx.x + 1] = b;
+        blockred[2 * bid] = a;
+        blockred[2 * bid + 1] = b;
     }
-    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
+    if (!last_block(&ctl->ticket, nb, &flag)) return;
     float ra = 0.f, rb = 0.f;
-    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+    for (unsigned int q = threadIdx.x; q < nb; q += blockDim.x) {
         ra = fmaxf(ra, (float)((volatile double *)blockred)[2 * q]);
         rb = fmaxf(rb, (float)((volatile double *)blockred)[2 * q + 1]);
     }
@@ -307,49 +322,59 @@ __global__ void residual_norm_kernel(MGLevel L, int bcx, int bcy, int bcz, DevCt
     }
 }
 
-// r_c = full weighting of t_f (y, z); u_c = 0
-__global__ void restrict_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+// r_c = full weighting of t_f (y, z); u_c = 0.  Grid over the coarse (x, y).
+__global__ void __launch_bounds__(kGX) restrict_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
 {
+    const int i = blockIdx.x * kGX + threadIdx.x, J = blockIdx.y;
+    if (i >= C.nx) return;
     const int nx = C.nx;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < C.N; m += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(m % nx);
-        long long t = m / nx;
-        int J = (int)(t % C.ny), K = (int)(t / C.ny);
+    const int Ka = blockIdx.z * kGZ, Kb = min(Ka + kGZ, C.nz);
+#pragma unroll
+    for (int dK = 0; dK < kGZ; ++dK) {
+        const int K = Ka + dK;
+        if (K >= Kb) break;
         float acc = 0.f;
         for (int dk = -1; dk <= 1; ++dk) {
-            float wk = (F.fz == 2) ? (dk == 0 ? 0.5f : 0.25f) : (dk == 0 ? 1.f : 0.f);
+            const float wk = (F.fz == 2) ? (dk == 0 ? 0.5f : 0.25f) : (dk == 0 ? 1.f : 0.f);
             if (wk == 0.f) continue;
-            int kf = (F.nz >= 2) ? nb_idx(F.fz * K, dk, F.nz, bcz) : 0;
+            const int kf = (F.nz >= 2) ? nb_idx(F.fz * K, dk, F.nz, bcz) : 0;
             for (int dj = -1; dj <= 1; ++dj) {
-                float wj = (F.fy == 2) ? (dj == 0 ? 0.5f : 0.25f) : (dj == 0 ? 1.f : 0.f);
+                const float wj = (F.fy == 2) ? (dj == 0 ? 0.5f : 0.25f) : (dj == 0 ? 1.f : 0.f);
                 if (wj == 0.f) continue;
-                int jf = nb_idx(F.fy * J, dj, F.ny, bcy);
+                const int jf = nb_idx(F.fy * J, dj, F.ny, bcy);
                 acc += wk * wj * F.t[(long long)nx * (jf + (long long)F.ny * kf) + i];
             }
         }
+        const long long m = i + (long long)nx * (J + (long long)C.ny * K);
         C.r[m] = acc;
         C.u[m] = 0.f;
     }
 }
 
-// u_f += bilinear interpolation of u_c
-__global__ void prolong_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+// u_f += bilinear interpolation of u_c.  Grid over the fine (x, y).
+__global__ void __launch_bounds__(kGX) prolong_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
 {
+    const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
+    if (i >= F.nx) return;
     const int nx = F.nx;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < F.N; m += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(m % nx);
-        long long t = m / nx;
-        int j = (int)(t % F.ny), k = (int)(t / F.ny);
-        int j0, j1, k0, k1;
-        float wj1, wk1;
-        if (F.fy == 2) {
-            j0 = j >> 1;
-            j1 = (j & 1) ? ((j0 + 1 < C.ny) ? j0 + 1 : (bcy == kPeriodic ? 0 : j0)) : j0;
-            wj1 = (j & 1) ? 0.5f : 0.f;
-        } else {
-            j0 = j1 = j;
-            wj1 = 0.f;
-        }
+    int j0, j1;
+    float wj1;
+    if (F.fy == 2) {
+        j0 = j >> 1;
+        j1 = (j & 1) ? ((j0 + 1 < C.ny) ? j0 + 1 : (bcy == kPeriodic ? 0 : j0)) : j0;
+        wj1 = (j & 1) ? 0.5f : 0.f;
+    } else {
+        j0 = j1 = j;
+        wj1 = 0.f;
+    }
+    const long long cpl = (long long)nx * C.ny;
+    const int ka = blockIdx.z * kGZ, kb = min(ka + kGZ, F.nz);
+#pragma unroll
+    for (int dk = 0; dk < kGZ; ++dk) {
+        const int k = ka + dk;
+        if (k >= kb) break;
+        int k0, k1;
+        float wk1;
         if (F.fz == 2) {
             k0 = k >> 1;
             k1 = (k & 1) ? ((k0 + 1 < C.nz) ? k0 + 1 : (bcz == kPeriodic ? 0 : k0)) : k0;
@@ -358,13 +383,12 @@ __global__ void prolong_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
             k0 = k1 = k;
             wk1 = 0.f;
         }
-        const long long cpl = (long long)nx * C.ny;
-        float v00 = C.u[(long long)nx * j0 + cpl * k0 + i];
-        float v10 = C.u[(long long)nx * j1 + cpl * k0 + i];
-        float v01 = C.u[(long long)nx * j0 + cpl * k1 + i];
-        float v11 = C.u[(long long)nx * j1 + cpl * k1 + i];
-        float v = (1.f - wk1) * ((1.f - wj1) * v00 + wj1 * v10) + wk1 * ((1.f - wj1) * v01 + wj1 * v11);
-        F.u[m] += v;
+        const float v00 = C.u[(long long)nx * j0 + cpl * k0 + i];
+        const float v10 = C.u[(long long)nx * j1 + cpl * k0 + i];
+        const float v01 = C.u[(long long)nx * j0 + cpl * k1 + i];
+        const float v11 = C.u[(long long)nx * j1 + cpl * k1 + i];
+        const float v = (1.f - wk1) * ((1.f - wj1) * v00 + wj1 * v10) + wk1 * ((1.f - wj1) * v01 + wj1 * v11);
+        F.u[i + (long long)nx * (j + (long long)F.ny * k)] += v;
     }
 }
 
@@ -601,11 +625,13 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     }
     smooth(a, l, 0, s, nl);
     smooth(a, l, 1, s, nl);
-    residual_kernel<<<grid_blocks(a.lev[l].N), kThreads, 0, s>>>(a.lev[l], bcx, bcy, bcz, a.ctl, l == 0);
-    restrict_kernel<<<grid_blocks(a.lev[l + 1].N), kThreads, 0, s>>>(a.lev[l], a.lev[l + 1], bcy, bcz);
+    residual_kernel<<<grid_xyz(a.lev[l].nx, a.lev[l].ny, a.lev[l].nz), kGX, 0, s>>>(a.lev[l], bcx, bcy, bcz, a.ctl,
+                                                                                   l == 0);
+    restrict_kernel<<<grid_xyz(a.lev[l + 1].nx, a.lev[l + 1].ny, a.lev[l + 1].nz), kGX, 0, s>>>(a.lev[l], a.lev[l + 1],
+                                                                                               bcy, bcz);
     *nl += 3;
     vcycle(a, l + 1, s, nl);
-    prolong_kernel<<<grid_blocks(a.lev[l].N), kThreads, 0, s>>>(a.lev[l], a.lev[l + 1], bcy, bcz);
+    prolong_kernel<<<grid_xyz(a.lev[l].nx, a.lev[l].ny, a.lev[l].nz), kGX, 0, s>>>(a.lev[l], a.lev[l + 1], bcy, bcz);
     smooth(a, l, 1, s, nl);
     smooth(a, l, 0, s, nl);
     return cudaGetLastError();
@@ -615,39 +641,38 @@ cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launc
 
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s)
 {
-    int nb = grid_blocks(a.lev[0].N, 8);
-    if (nb > 2048) nb = 2048;
-    residual_norm_kernel<<<nb, kThreads, 0, s>>>(a.lev[0], a.g.bcx, a.g.bcy, a.g.bcz, a.ctl, a.blockred);
+    residual_norm_kernel<<<grid_xy(a.lev[0].nx, a.lev[0].ny), kGX, 0, s>>>(a.lev[0], a.g.bcx, a.g.bcy, a.g.bcz, a.ctl,
+                                                                          a.blockred);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Zero mode of mu: subtract the weighted mean (FP64 sum).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float site_w(const DevGrid &g, long long m)
+__global__ void __launch_bounds__(kGX) mu_mean_kernel(DevGrid g, const float *mu, DevCtl *ctl, double *blockred,
+                                                      double wsum)
 {
-    int i = (int)(m % g.nx);
-    long long t = m / g.nx;
-    int j = (int)(t % g.ny), k = (int)(t / g.ny);
-    float w = 1.f;
-    if (g.bcx == kOpen && (i == 0 || i == g.nx - 1)) w *= 0.5f;
-    if (g.bcy == kOpen && (j == 0 || j == g.ny - 1)) w *= 0.5f;
-    if (g.bcz == kOpen && g.nz >= 2 && (k == 0 || k == g.nz - 1)) w *= 0.5f;
-    return w;
-}
-
-__global__ void mu_mean_kernel(DevGrid g, const float *mu, DevCtl *ctl, double *blockred, double wsum)
-{
+    const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
     float accf = 0.f;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x)
-        accf += site_w(g, m) * mu[m];
+    if (i < g.nx) {
+        float wxy = 1.f;
+        if (g.bcx == kOpen && (i == 0 || i == g.nx - 1)) wxy *= 0.5f;
+        if (g.bcy == kOpen && (j == 0 || j == g.ny - 1)) wxy *= 0.5f;
+        const long long pl = (long long)g.nx * g.ny;
+        for (int k = 0; k < g.nz; ++k) {
+            float w = wxy;
+            if (g.bcz == kOpen && g.nz >= 2 && (k == 0 || k == g.nz - 1)) w *= 0.5f;
+            accf += w * mu[i + (long long)g.nx * j + pl * k];
+        }
+    }
     __shared__ double shd[32];
     __shared__ int flag;
+    const unsigned int bid = blockIdx.x + gridDim.x * blockIdx.y, nb = gridDim.x * gridDim.y;
     double s = block_sum((double)accf, shd);
-    if (threadIdx.x == 0) blockred[blockIdx.x] = s;
-    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
+    if (threadIdx.x == 0) blockred[bid] = s;
+    if (!last_block(&ctl->ticket, nb, &flag)) return;
     double t = 0.0;
-    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += ((volatile double *)blockred)[q];
+    for (unsigned int q = threadIdx.x; q < nb; q += blockDim.x) t += ((volatile double *)blockred)[q];
     t = block_sum(t, shd);
     if (threadIdx.x == 0) {
         ctl->ticket = 0u;
@@ -664,9 +689,7 @@ __global__ void mu_shift_kernel(long long N, float *mu, const DevCtl *ctl)
 
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s)
 {
-    int nb = grid_blocks(a.g.N, 16);
-    if (nb > 2048) nb = 2048;
-    mu_mean_kernel<<<nb, kThreads, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum);
+    mu_mean_kernel<<<grid_xy(a.g.nx, a.g.ny), kGX, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum);
     mu_shift_kernel<<<grid_blocks(a.g.N, 8), kThreads, 0, s>>>(a.g.N, a.mu, a.ctl);
     return cudaGetLastError();
 }

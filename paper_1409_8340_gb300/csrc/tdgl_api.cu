@@ -95,6 +95,8 @@ struct Layout {
     size_t cw;        // coarsest-level eigen-factors (0: none, the coarsest level is relaxed)
 };
 
+constexpr int kCoarseModes = 128;
+
 bool can_coarsen(int n, int bc)
 {
     if (bc == TDGL_PERIODIC) return (n % 2 == 0) && n >= 8;
@@ -121,6 +123,8 @@ Layout layout(const tdgl_config *c)
     L.ctl = take(sizeof(DevCtl));
     size_t nb = (size_t)sweep_blocks(g);
     if (nb < 4 * 4096) nb = 4 * 4096;
+    const size_t nb2d = 2 * (size_t)((c->nx + 127) / 128) * (size_t)c->ny;   // 2-D reduction grids, 2 values each
+    if (nb < nb2d) nb = nb2d;
     L.nblockred = nb;
     L.blockred = take(sizeof(double) * nb);
     for (int q = 0; q < 3; ++q) L.psi[q] = take(8 * (size_t)N);
@@ -146,7 +150,8 @@ Layout layout(const tdgl_config *c)
         }
         bool cy = can_coarsen(ny, c->bc[1]);
         bool cz = nz >= 2 && can_coarsen(nz, c->bc[2]);
-        if ((!cy && !cz) || l + 1 >= kMaxLevels) {
+        // a level with at most kCoarseModes y-z modes is solved exactly (dense basis)
+        if ((!cy && !cz) || ny * nz <= kCoarseModes || l + 1 >= kMaxLevels) {
             L.fy[l] = L.fz[l] = 1;
             break;
         }

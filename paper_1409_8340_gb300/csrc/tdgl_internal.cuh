@@ -165,6 +165,9 @@ struct SweepArgs {
     int fixed_sweeps;
     int max_iter;
     double eps;
+    float *f;                  // Poisson right-hand side (right-hand-side mode)
+    float inj;                 // 2 J / hx at open x faces (right-hand-side mode)
+    double wsum;               // sum of trapezoid weights (right-hand-side mode)
 };
 
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
