@@ -208,6 +208,32 @@ int tdgl_pattern(const tdgl_config *grid, const double *host_candidates, int64_t
                  int64_t target_sites, float alpha_in, float alpha_out, float *d_alpha,
                  void *d_scratch, size_t scratch_bytes, void *stream, int64_t *n_used, int64_t *n_marked);
 
+/*
+ * Allocation-free Jacobi sweep.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code running inside a host
+ * application whose memory manager owns the device heap, or a real-time loop
+ * that must not allocate once it runs -- but that hold device buffers for their
+ * inputs and outputs.  It performs one sweep of Eq. final, exactly as the sweeps
+ * of tdgl_step do, with the Landau links of cfg and exp(i hx K) on x links:
+ *   d_psi_out = D^{-1} (b - R psi_in),   *r2max = max_m |b - M psi_in|^2,
+ * for complex64 arrays d_psi_in, d_b (Eq. b), d_D (diag M) and d_psi_out of
+ * nx*ny*nz sites (d_psi_out must not alias d_psi_in).  Only nx..Bz of cfg are
+ * read; d_alpha may be NULL; links_mode must be TDGL_LINKS_LANDAU.
+ * Its scratch (control block, link tables, per-block maxima) is one static
+ * device array of TDGL_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the
+ * library holds until exit; nothing is allocated.  Grids with an axis longer
+ * than TDGL_NOALLOC_MAX_AXIS, or needing more than TDGL_NOALLOC_MAX_BLOCKS sweep
+ * blocks, are rejected with TDGL_ERR_WORKSPACE.  The first call on a device
+ * looks the array's address up (make it before any stream capture).  All calls
+ * share the array, so calls that overlap on the GPU race; each call rewrites
+ * what it uses before it runs.  Synchronises the stream.
+ */
+#define TDGL_NOALLOC_MAX_AXIS 4096
+#define TDGL_NOALLOC_MAX_BLOCKS 65536
+#define TDGL_NOALLOC_SCRATCH_BYTES (512 + 32 * TDGL_NOALLOC_MAX_AXIS + 8 * TDGL_NOALLOC_MAX_BLOCKS)
+int tdgl_sweep_noalloc(const tdgl_config *cfg, const float *d_psi_in, const float *d_b, const float *d_D, double K,
+                       float *d_psi_out, double *r2max, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,8 @@ _SIGS = {
     "tdgl_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),
     "tdgl_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tdgl_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "tdgl_sweep_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), _P, _P, _P, ctypes.c_double, _P,
+                                          ctypes.POINTER(ctypes.c_double), _P]),
     "tdgl_pattern_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64]),
     "tdgl_pattern": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
                                     ctypes.c_float, _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_int64),
