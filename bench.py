@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # profiling captures only (a number printed with these changed is not a bench value)
+    ap.add_argument("--nz", type=int, default=256, help="z planes of the grid (profiling captures: a smaller case)")
+    ap.add_argument("--fixed-sweeps", type=int, default=0, help="exactly this many sweeps per step (profiling)")
     return ap.parse_args()
 
 
@@ -214,8 +217,9 @@ def run_native(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w = workload(args.J)
+    w = workload(args.J, None if args.nz == 256 else args.nz)
     p = w.params
+    p.fixed_sweeps = args.fixed_sweeps
     alpha, used, marked = pattern(p, w.candidates, w.target_sites, w.alpha_in, w.alpha_out, device=dev)
     psi0 = inputs.random_psi(p.nx, p.ny, p.nz, w.seed + rank).astype(np.complex64)
     s = Solver(p, alpha)
@@ -302,7 +306,9 @@ def run_native(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "mesoscopic_512x512x256", "grid": [p.nx, p.ny, p.nz], "sites": p.N,
+            "config": {"workload": ("mesoscopic_512x512x256" if (args.nz == 256 and args.fixed_sweeps == 0)
+                                    else f"profiling case 512x512x{p.nz}, fixed_sweeps={args.fixed_sweeps}"),
+                       "grid": [p.nx, p.ny, p.nz], "sites": p.N,
                        "bc": "open x, periodic y z", "Bz": p.Bz, "J": p.Jext, "h": p.hx, "ht": p.ht, "eps": p.eps,
                        "inclusions": {"kind": "ellipsoids", "used": used, "sites": marked,
                                       "fraction": marked / p.N},

@@ -385,19 +385,27 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
     const int jp = yhi ? (yper ? 0 : jc) : jc + 1;
     const int jm = ylo ? (yper ? g.ny - 1 : jc) : jc - 1;
     const long long q0 = (x >> 1) + rowq * jc;               // float4 index in plane 0
-    // links of the pair
-    float2 Uy0 = cmk(1.f, 0.f), Uy1 = cmk(1.f, 0.f), Uz0 = cmk(1.f, 0.f), Uz1 = cmk(1.f, 0.f);
+    // Neighbour coefficients of the pair, constant along z: (ht/2) * c_axis *
+    // (open-face weight 2 or 0) * link, so that S = (ht/2) NS is six complex
+    // multiply-adds per site.  Forward neighbours use U, backward ones conj(U).
+    const bool zact = g.nz >= 2;
+    const float wy_f = yper ? 1.f : (ylo ? 2.f : (yhi ? 0.f : 1.f));
+    const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
+    const bool yedge = (wy_f != 1.f) || (wy_b != 1.f);
+    float2 yf0 = cmk(0.f, 0.f), yf1 = yf0, zf0 = yf0, zf1 = yf0;
     if (in) {
         const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
         const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
-        Uy0 = lo2(uy);
-        Uy1 = hi2(uy);
-        Uz0 = lo2(uz);
-        Uz1 = hi2(uz);
+        const float sy = g.ht2 * g.cy, szc = g.ht2 * g.cz;
+        yf0 = cscale(sy, lo2(uy));
+        yf1 = cscale(sy, hi2(uy));
+        zf0 = cscale(szc, lo2(uz));
+        zf1 = cscale(szc, hi2(uz));
     }
-    const float wy_f = yper ? 1.f : (ylo ? 2.f : (yhi ? 0.f : 1.f));
-    const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
-    const bool zact = g.nz >= 2;
+    // x: site x has forward neighbour c1 and backward xl; site x+1 has forward xr and backward c0.
+    // Backward coefficients are the conjugates of the forward ones.
+    const float2 xf = cscale(g.ht2 * g.cx, Ux);
+    const float inv_ht2 = 1.0f / g.ht2;
 
     auto knext = [&](int k) { return (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1; };
     float4 pzm = make_float4(0.f, 0.f, 0.f, 0.f), pc = pzm, pzp_n = pzm, b_n = pzm, D_n = pzm;
@@ -458,34 +466,62 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
         }
         if (in) {
             const float2 c0 = lo2(pc), c1 = hi2(pc);
-            // x part, site x: fwd = Ux c1, bwd = conj(Ux or wrap link) xl
-            float2 bwd0 = cmulc(Ux, xl);
-            if (xlo && xper) bwd0 = cmulc(cmulc(cmul(g.Py[jc], g.Pz[k]), Ux), xl);
-            float2 tx0 = cadd(cmul(Ux, c1), bwd0);
-            if (!xper && xlo) tx0 = cscale(2.f, cmul(Ux, c1));
-            // site x+1: fwd = Ux (or wrap link) xr, bwd = conj(Ux) c0
-            float2 fwd1 = cmul(Ux, xr);
-            if (xhi && xper) fwd1 = cmul(cmulc(cmul(g.Py[jc], g.Pz[k]), Ux), xr);
-            float2 tx1 = cadd(fwd1, cmulc(Ux, c0));
-            if (!xper && xhi) tx1 = cscale(2.f, cmulc(Ux, c0));
-            // y part
-            const float2 ty0 = cadd(cscale(wy_f, cmul(Uy0, lo2(yf))), cscale(wy_b, cmulc(Uy0, lo2(yb))));
-            const float2 ty1 = cadd(cscale(wy_f, cmul(Uy1, hi2(yf))), cscale(wy_b, cmulc(Uy1, hi2(yb))));
-            float2 ns0 = cadd(cscale(g.cx, tx0), cscale(g.cy, ty0));
-            float2 ns1 = cadd(cscale(g.cx, tx1), cscale(g.cy, ty1));
+            // x neighbours with the boundary rules: open faces double the inner
+            // neighbour; the periodic wrap link (i = nx-1 -> 0) carries conj(P_jk).
+            float2 xl0 = xl, xr1 = xr, c1x = c1, c0x = c0;
+            if (xlo || xhi) {
+                if (xper) {
+                    const float2 P = cmul(g.Py[jc], g.Pz[k]);
+                    if (xlo) xl0 = cmul(P, xl);      // conj(Ux conj(P)) xl = conj(Ux) (P xl)
+                    if (xhi) xr1 = cmulc(P, xr);     // Ux conj(P) xr = Ux (conj(P) xr)
+                } else {
+                    if (xlo) {
+                        c1x = cscale(2.f, c1);
+                        xl0 = cmk(0.f, 0.f);
+                    }
+                    if (xhi) {
+                        c0x = cscale(2.f, c0);
+                        xr1 = cmk(0.f, 0.f);
+                    }
+                }
+            }
+            float2 yf_0 = lo2(yf), yf_1 = hi2(yf), yb_0 = lo2(yb), yb_1 = hi2(yb);
+            if (yedge) {
+                yf_0 = cscale(wy_f, yf_0);
+                yf_1 = cscale(wy_f, yf_1);
+                yb_0 = cscale(wy_b, yb_0);
+                yb_1 = cscale(wy_b, yb_1);
+            }
+            // S = (ht/2) NS for both sites
+            float2 ns0 = cmul(xf, c1x), ns1 = cmulc(xf, c0x);
+            cfmac(ns0, xf, xl0);
+            cfma(ns1, xf, xr1);
+            cfma(ns0, yf0, yf_0);
+            cfmac(ns0, yf0, yb_0);
+            cfma(ns1, yf1, yf_1);
+            cfmac(ns1, yf1, yb_1);
             if (zact) {
-                const bool zlo = (k == 0), zhi = (k == g.nz - 1);
-                const float wz_f = zper ? 1.f : (zlo ? 2.f : (zhi ? 0.f : 1.f));
-                const float wz_b = zper ? 1.f : (zhi ? 2.f : (zlo ? 0.f : 1.f));
-                const float2 tz0 = cadd(cscale(wz_f, cmul(Uz0, lo2(pzp))), cscale(wz_b, cmulc(Uz0, lo2(pzm))));
-                const float2 tz1 = cadd(cscale(wz_f, cmul(Uz1, hi2(pzp))), cscale(wz_b, cmulc(Uz1, hi2(pzm))));
-                ns0 = cadd(ns0, cscale(g.cz, tz0));
-                ns1 = cadd(ns1, cscale(g.cz, tz1));
+                float wz_f = 1.f, wz_b = 1.f;
+                if (!zper) {
+                    if (k == 0) {
+                        wz_f = 2.f;
+                        wz_b = 0.f;
+                    } else if (k == g.nz - 1) {
+                        wz_f = 0.f;
+                        wz_b = 2.f;
+                    }
+                }
+                const float4 zpp = (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
+                const float4 zmm = (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
+                cfma(ns0, zf0, lo2(zpp));
+                cfmac(ns0, zf0, lo2(zmm));
+                cfma(ns1, zf1, hi2(zpp));
+                cfmac(ns1, zf1, hi2(zmm));
             }
             if (RHS) {
                 // f = Im[conj(psi) NS(psi)] plus the open-x injection terms
-                float f0 = c0.x * ns0.y - c0.y * ns0.x;
-                float f1 = c1.x * ns1.y - c1.y * ns1.x;
+                float f0 = (c0.x * ns0.y - c0.y * ns0.x) * inv_ht2;
+                float f1 = (c1.x * ns1.y - c1.y * ns1.x) * inv_ht2;
                 if (!xper) {
                     if (xlo) f0 -= a.inj;
                     if (xhi) f1 += a.inj;
@@ -510,7 +546,7 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
                     const float cr = als[s2] - g.beta * a2 - 2.f * g.S;
                     const float ci = -g.u * mus[s2];
                     const float2 lin = cmk(cr * cs[s2].x - ci * cs[s2].y, cr * cs[s2].y + ci * cs[s2].x);
-                    bo[s2] = cadd(cs[s2], cscale(g.ht2, cadd(lin, nss[s2])));
+                    bo[s2] = cadd(cadd(cs[s2], cscale(g.ht2, lin)), nss[s2]);   // nss = (ht/2) NS
                 }
                 b0 = bo[0];
                 b1 = bo[1];
@@ -524,7 +560,7 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
                 D0 = lo2(Dc);
                 D1 = hi2(Dc);
             }
-            const float2 s0 = cadd(b0, cscale(g.ht2, ns0)), s1 = cadd(b1, cscale(g.ht2, ns1));
+            const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
             const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
             const float2 n0 = cscale(1.0f / cabs2(D0), cmulc(D0, s0));
             const float2 n1 = cscale(1.0f / cabs2(D1), cmulc(D1, s1));

@@ -70,6 +70,18 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
     return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 __host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b)
+{
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+// acc += conj(a) * b
+__host__ __device__ __forceinline__ void cfmac(float2 &acc, float2 a, float2 b)
+{
+    acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
 
 // ----------------------------------------------------------------------------
 // reductions
