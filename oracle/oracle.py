@@ -386,3 +386,35 @@ def run(G: Grid, st: State, alpha, nsteps, **kw):
     for _ in range(nsteps):
         stats.append(step(G, st, alpha, **kw))
     return stats
+
+
+# --------------------------------------------------------------------------
+# Pieces used by the adjoint
+# --------------------------------------------------------------------------
+def ns(G: Grid, psi, K=0.0, theta=None):
+    """Neighbour sum NS_m(psi): the off-diagonal part of the gauge Laplacian."""
+    out = np.empty(G.shape, dtype=np.complex128)
+    L = lib()
+    L.or_ns.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.or_ns(ctypes.byref(G.c()), _theta_ptr(theta), K, _dp(_cplx(psi)), _dp(out))
+    return out
+
+
+def ns_adj(G: Grid, lam, K=0.0, theta=None):
+    """Conjugate transpose of the neighbour-sum operator applied to lam."""
+    out = np.empty(G.shape, dtype=np.complex128)
+    L = lib()
+    L.or_ns_adj.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.or_ns_adj(ctypes.byref(G.c()), _theta_ptr(theta), K, _dp(_cplx(lam)), _dp(out))
+    return out
+
+
+def voltage_weights(G: Grid):
+    """v with E_x = sum(v * mu) for open x (the face-mean voltage)."""
+    v = np.zeros(G.shape)
+    s = 1.0 / (G.ny * G.nz * (G.nx - 1) * G.hx)
+    v[:, :, 0] = s
+    v[:, :, -1] -= s
+    return v

@@ -508,3 +508,51 @@ int or_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour sum NS_m(psi) (complex) and its conjugate transpose, for the    */
+/* adjoint of the step.  NS^H has entries conj(NS_{m',m}): the open-face      */
+/* factor 2 moves from the face row to the row next to the face.             */
+/* ------------------------------------------------------------------------ */
+void or_ns(const or_grid *G, const double *theta, double K, const double *psi, double *out)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i)
+                store(out, idx3(G, i, j, k), neighbour_sum(G, theta, K, psi, i, j, k));
+}
+
+void or_ns_adj(const or_grid *G, const double *theta, double K, const double *lam, double *out)
+{
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int c0[3] = {i, j, k};
+                cplx acc = 0.0;
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (!axis_active(G, ax)) continue;
+                    int n = G->n[ax], idx = c0[ax];
+                    double c = axis_coef(G, ax);
+                    int cp[3] = {i, j, k}, cm[3] = {i, j, k};
+                    step_index(G, ax, +1, cp);
+                    step_index(G, ax, -1, cm);
+                    int open = (G->bc[ax] == OR_OPEN);
+                    /* row m+a holds U*_{a,m} lam_m as its backward term (times 2 if m+a is the
+                       high open face); its conjugate transpose gives U_{a,m} lam_{m+a} here */
+                    if (!open || idx < n - 1) {
+                        double wgt = (open && idx + 1 == n - 1) ? 2.0 : 1.0;
+                        acc += wgt * c * link(G, theta, K, ax, i, j, k) * load(lam, idx3(G, cp[0], cp[1], cp[2]));
+                    }
+                    /* row m-a holds U_{a,m-a} lam_m as its forward term (times 2 if m-a is the
+                       low open face); its conjugate transpose gives conj(U_{a,m-a}) lam_{m-a} */
+                    if (!open || idx > 0) {
+                        double wgt = (open && idx - 1 == 0) ? 2.0 : 1.0;
+                        acc += wgt * c * conj(link(G, theta, K, ax, cm[0], cm[1], cm[2])) *
+                               load(lam, idx3(G, cm[0], cm[1], cm[2]));
+                    }
+                }
+                store(out, idx3(G, i, j, k), acc);
+            }
+}
