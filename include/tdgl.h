@@ -209,6 +209,48 @@ int tdgl_pattern(const tdgl_config *grid, const double *host_candidates, int64_t
                  void *d_scratch, size_t scratch_bytes, void *stream, int64_t *n_used, int64_t *n_marked);
 
 /*
+ * Adjoint of the time loop: gradient of the time-averaged electric field with
+ * respect to the pinning map alpha (inverse design of inclusions).  The paper
+ * has no adjoint; this differentiates its discrete step (Sec. 3.1, Crank-
+ * Nicolson residual R = psi' - psi + (ht/2) H (psi' + psi), H = diag(beta|psi|^2
+ * + i u mu - alpha) - Lap_U; Sec. 3.2 Poisson solve), taking every linear solve
+ * as exact.  Starting from the handle's current state, tdgl_adjoint runs
+ * n_steps forward steps exactly as tdgl_step (the handle ends in the state
+ * after them), storing (psi, mu) every checkpoint_every steps in d_ws; then,
+ * segment by segment from the end, recomputes the segment's states from its
+ * checkpoint and runs the reverse steps: adjoint Poisson, adjoint of the
+ * right-hand side Im[psi* NS psi], adjoint implicit solve M^H lam = g by
+ * Jacobi to a relative tolerance, and accumulation of dJ/dalpha.
+ *   J = (1/(n_steps - window_start)) sum_{n > window_start} E_x^n
+ * Requires open x (E_x from the face potentials), Landau links and even nx.
+ * d_grad_alpha: device f32[N], overwritten.  *objective: J.  d_ws: device bytes
+ * >= tdgl_adjoint_workspace_bytes(), 256-byte aligned, caller-owned.
+ * Synchronises the stream once per step.
+ */
+typedef struct tdgl_adjoint_config {
+    int32_t n_steps;           /* forward steps                                   */
+    int32_t checkpoint_every;  /* steps between stored states (>= 1)              */
+    int32_t window_start;      /* J averages E_x over steps window_start+1..n     */
+    int32_t adj_max_iter;      /* sweep cap of each adjoint solve                 */
+    double adj_eps;            /* adjoint Jacobi stops when max |r|^2 <= adj_eps  */
+                               /* times max |r|^2 of its first sweep (relative)   */
+    int32_t poisson_cycles;    /* V-cycles of each adjoint Poisson solve (>= 1)   */
+    int32_t reserved;
+    double poisson_tol;        /* > 0: more cycles until the relative residual    */
+} tdgl_adjoint_config;         /*      is below it (up to poisson_max_cycles)     */
+
+typedef struct tdgl_adjoint_stats {
+    double ms_forward;         /* first forward pass (device time)                */
+    double ms_recompute;       /* recomputed segments                             */
+    double ms_reverse;         /* reverse steps                                   */
+    int64_t adjoint_sweeps;    /* adjoint Jacobi sweeps, all steps                */
+} tdgl_adjoint_stats;
+
+size_t tdgl_adjoint_workspace_bytes(const tdgl_handle *h, const tdgl_adjoint_config *acfg);
+int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, void *d_ws, size_t ws_bytes, float *d_grad_alpha,
+                 double *objective, tdgl_adjoint_stats *stats);
+
+/*
  * Allocation-free Jacobi sweep.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- code running inside a host
  * application whose memory manager owns the device heap, or a real-time loop

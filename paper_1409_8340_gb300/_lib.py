@@ -78,6 +78,20 @@ class Profile(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class AdjointConfig(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32), ("window_start", ctypes.c_int32),
+                ("adj_max_iter", ctypes.c_int32), ("adj_eps", ctypes.c_double), ("poisson_cycles", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("poisson_tol", ctypes.c_double)]
+
+
+class AdjointStats(ctypes.Structure):
+    _fields_ = [("ms_forward", ctypes.c_double), ("ms_recompute", ctypes.c_double), ("ms_reverse", ctypes.c_double),
+                ("adjoint_sweeps", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _SIGS = {
@@ -93,6 +107,9 @@ _SIGS = {
     "tdgl_solve_psi": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "tdgl_solve_mu": (ctypes.c_int, [_P]),
     "tdgl_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),
+    "tdgl_adjoint_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.POINTER(AdjointConfig)]),
+    "tdgl_adjoint": (ctypes.c_int, [_P, ctypes.POINTER(AdjointConfig), _P, ctypes.c_size_t, _P,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(AdjointStats)]),
     "tdgl_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tdgl_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "tdgl_sweep_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), _P, _P, _P, ctypes.c_double, _P,

@@ -139,7 +139,9 @@ __device__ __forceinline__ void finish_sweep(const SweepArgs &a, float bmax, boo
             c->done = 1;
         } else if (a.fixed_sweeps > 0) {
             c->done = (it >= a.fixed_sweeps) ? 1 : 0;
-        } else if ((it % a.check_every) == 0 && (double)gf < a.eps) {
+        } else if (a.rel_eps && (it == 1 ? (c->r2ref = (double)gf, gf == 0.f) : (double)gf <= a.eps * c->r2ref)) {
+            c->done = 1;
+        } else if (!a.rel_eps && (it % a.check_every) == 0 && (double)gf < a.eps) {
             c->done = 1;
         } else if (it >= a.max_iter) {
             c->status = TDGL_ERR_NOT_CONVERGED;
@@ -356,7 +358,8 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
 {
     constexpr bool INIT = (MODE == 1);
     constexpr bool RHS = (MODE == 2);
-    if (MODE == 0 && *(volatile int *)&a.ctl->done) return;
+    constexpr bool ADJ = (MODE == 3);   // adjoint solve M^H lam = g: conj(D), transposed open-face rows
+    if ((MODE == 0 || ADJ) && *(volatile int *)&a.ctl->done) return;
     const DevGrid &g = a.g;
     const int tx = threadIdx.x;
     const int x = (blockIdx.x * kBX + tx) * 2;
@@ -389,8 +392,12 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
     // (open-face weight 2 or 0) * link, so that S = (ht/2) NS is six complex
     // multiply-adds per site.  Forward neighbours use U, backward ones conj(U).
     const bool zact = g.nz >= 2;
-    const float wy_f = yper ? 1.f : (ylo ? 2.f : (yhi ? 0.f : 1.f));
-    const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
+    // open-face weights of the y neighbours: the forward operator doubles the inner
+    // neighbour on a face row; its transpose doubles the face value on the next row
+    const float wy_f = yper ? 1.f
+                            : (ADJ ? (yhi ? 0.f : (j + 1 == g.ny - 1 ? 2.f : 1.f)) : (ylo ? 2.f : (yhi ? 0.f : 1.f)));
+    const float wy_b = yper ? 1.f
+                            : (ADJ ? (ylo ? 0.f : (j - 1 == 0 ? 2.f : 1.f)) : (yhi ? 2.f : (ylo ? 0.f : 1.f)));
     const bool yedge = (wy_f != 1.f) || (wy_b != 1.f);
     float2 yf0 = cmk(0.f, 0.f), yf1 = yf0, zf0 = yf0, zf1 = yf0;
     if (in) {
@@ -474,13 +481,23 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
                     const float2 P = cmul(g.Py[jc], g.Pz[k]);
                     if (xlo) xl0 = cmul(P, xl);      // conj(Ux conj(P)) xl = conj(Ux) (P xl)
                     if (xhi) xr1 = cmulc(P, xr);     // Ux conj(P) xr = Ux (conj(P) xr)
-                } else {
+                } else if (!ADJ) {
                     if (xlo) {
                         c1x = cscale(2.f, c1);
                         xl0 = cmk(0.f, 0.f);
                     }
                     if (xhi) {
                         c0x = cscale(2.f, c0);
+                        xr1 = cmk(0.f, 0.f);
+                    }
+                } else {
+                    // transpose: site 1 sees the low face value twice, site nx-2 the high one
+                    if (xlo) {
+                        c0x = cscale(2.f, c0);
+                        xl0 = cmk(0.f, 0.f);
+                    }
+                    if (xhi) {
+                        c1x = cscale(2.f, c1);
                         xr1 = cmk(0.f, 0.f);
                     }
                 }
@@ -502,7 +519,10 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
             cfmac(ns1, yf1, yb_1);
             if (zact) {
                 float wz_f = 1.f, wz_b = 1.f;
-                if (!zper) {
+                if (!zper && ADJ) {
+                    wz_f = (k == g.nz - 1) ? 0.f : (k + 1 == g.nz - 1 ? 2.f : 1.f);
+                    wz_b = (k == 0) ? 0.f : (k - 1 == 0 ? 2.f : 1.f);
+                } else if (!zper) {
                     if (k == 0) {
                         wz_f = 2.f;
                         wz_b = 0.f;
@@ -557,8 +577,8 @@ __global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
             } else {
                 b0 = lo2(bc);
                 b1 = hi2(bc);
-                D0 = lo2(Dc);
-                D1 = hi2(Dc);
+                D0 = ADJ ? cconj(lo2(Dc)) : lo2(Dc);
+                D1 = ADJ ? cconj(hi2(Dc)) : hi2(Dc);
             }
             const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
             const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
@@ -632,5 +652,21 @@ cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStre
     else poisson_rhs_kernel<false><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
     return cudaGetLastError();
 }
+
+}  // namespace tdgl
+
+namespace tdgl {
+
+// Adjoint Jacobi sweep for M^H lam = g (b = g, D = diag M of the forward step).
+cudaError_t launch_adj_sweep(const SweepArgs &a, cudaStream_t s)
+{
+    if (!use_sweep2(a.g)) return cudaErrorInvalidValue;
+    int kz = zchunk(a.g);
+    dim3 block(kBX, kBY);
+    sweep2_kernel<3><<<sweep2_grid(a.g, kz), block, 0, s>>>(a, kz);
+    return cudaGetLastError();
+}
+
+bool adj_supported(const DevGrid &g) { return use_sweep2(g); }
 
 }  // namespace tdgl

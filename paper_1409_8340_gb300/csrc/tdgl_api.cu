@@ -11,32 +11,6 @@
 
 using namespace tdgl;
 
-struct tdgl_handle {
-    tdgl_config cfg;
-    DevGrid g;
-    cudaStream_t stream;
-    DevCtl *ctl;
-    double *blockred;
-    float2 *psi[3];
-    int cur;
-    float2 *b, *D;
-    float *mu, *f;
-    float2 *links;
-    PoissonArgs pa;
-    int last_sweeps;
-    int last_cycles;
-    int64_t step;
-    double wsum;
-    double dtK;
-    double last_javg;
-    // profiling
-    int prof_on;
-    cudaEvent_t ev[8];
-    bool ev_made;
-    bool pend_K, pend_P;   // K / Poisson event pairs recorded but not yet read
-    tdgl_profile prof;
-};
-
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -202,6 +176,7 @@ int read_ctl(tdgl_handle *h, DevCtl *out)
 SweepArgs sweep_args(tdgl_handle *h)
 {
     SweepArgs a;
+    memset(&a, 0, sizeof(a));
     a.g = h->g;
     a.ctl = h->ctl;
     a.blockred = h->blockred;

@@ -33,7 +33,7 @@ struct DevGrid {
 // kernels (last-block reductions), read by later launches on the same stream.
 struct DevCtl {
     double K;                  // current K
-    double K_step_start;       // K at the start of the step
+    double r2ref;              // max |r|^2 of the first sweep (relative tolerance)
     double Ex;                 // electric field of the last step
     double javg;               // J_av of the last step
     double r2;                 // max |r|^2 of the last tested sweep
@@ -177,6 +177,7 @@ struct SweepArgs {
     int fixed_sweeps;
     int max_iter;
     double eps;
+    int rel_eps;               // 1: converge when max|r|^2 <= eps * (max|r|^2 of the first sweep)
     float *f;                  // Poisson right-hand side (right-hand-side mode)
     float inj;                 // 2 J / hx at open x faces (right-hand-side mode)
     double wsum;               // sum of trapezoid weights (right-hand-side mode)
@@ -246,4 +247,44 @@ cudaError_t launch_pattern(const DevGrid &g, double hx, double hy, double hz, co
                            long long n_incl, long long target, float alpha_in, float alpha_out, float *alpha,
                            int *first_idx, unsigned long long *counts, long long *result, cudaStream_t s);
 
+// Adjoint kernels (k_adjoint.cu) and the adjoint sweep (k_jacobi.cu)
+cudaError_t launch_adj_sweep(const SweepArgs &a, cudaStream_t s);
+bool adj_supported(const DevGrid &g);
+cudaError_t launch_adj_fterm(const DevGrid &g, float2 Ux, const float2 *psi, const float *u, const float2 *psibar,
+                             float2 *gout, cudaStream_t s);
+cudaError_t launch_adj_diag(const DevGrid &g, const float2 *psi_p, const float *mu_p, const float *alpha,
+                            const float2 *gv, float2 *D, float2 *lam0, cudaStream_t s);
+cudaError_t launch_adj_update(const DevGrid &g, const float2 *lam, const float2 *psi_n, const float2 *psi_p,
+                              const float2 *gv, float *grad, float *mubar, float2 *psibar, cudaStream_t s);
+cudaError_t launch_adj_voltage_source(const DevGrid &g, float *mubar, float s_val, cudaStream_t s);
+cudaError_t launch_adj_rhs(const DevGrid &g, const float *mubar, float *r, DevCtl *ctl, double *blockred, double wsum,
+                           cudaStream_t s);
+
 }  // namespace tdgl
+
+// Host-side solver handle (shared by the C ABI translation units).
+struct tdgl_handle {
+    tdgl_config cfg;
+    tdgl::DevGrid g;
+    cudaStream_t stream;
+    tdgl::DevCtl *ctl;
+    double *blockred;
+    float2 *psi[3];
+    int cur;
+    float2 *b, *D;
+    float *mu, *f;
+    float2 *links;
+    tdgl::PoissonArgs pa;
+    int last_sweeps;
+    int last_cycles;
+    int64_t step;
+    double wsum;
+    double dtK;
+    double last_javg;
+    // profiling
+    int prof_on;
+    cudaEvent_t ev[8];
+    bool ev_made;
+    bool pend_K, pend_P;   // K / Poisson event pairs recorded but not yet read
+    tdgl_profile prof;
+};

@@ -182,6 +182,25 @@ class Solver:
     def solve_mu(self):
         check(self._L.tdgl_solve_mu(self._h), "tdgl_solve_mu")
 
+    def adjoint(self, n_steps: int, checkpoint_every: int = 20, window_start: int | None = None,
+                adj_eps: float = 1e-8, adj_max_iter: int = 500, poisson_cycles: int = 2, poisson_tol: float = 0.0):
+        """Run n_steps forward from the current state and return (J, dJ/dalpha, stats),
+        J = mean E_x over steps window_start+1..n_steps (default: the second half)."""
+        ws_start = n_steps // 2 if window_start is None else window_start
+        ac = _lib.AdjointConfig(n_steps, checkpoint_every, ws_start, adj_max_iter, adj_eps, poisson_cycles, 0,
+                                poisson_tol)
+        nbytes = self._L.tdgl_adjoint_workspace_bytes(self._h, ctypes.byref(ac))
+        if nbytes == 0:
+            raise TdglError(-1, "tdgl_adjoint_workspace_bytes")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        grad = torch.empty(self.p.shape, dtype=torch.float32, device=self.device)
+        J = ctypes.c_double()
+        st = _lib.AdjointStats()
+        check(self._L.tdgl_adjoint(self._h, ctypes.byref(ac), ctypes.c_void_p(ws.data_ptr()), nbytes,
+                                   ctypes.c_void_p(grad.data_ptr()), ctypes.byref(J), ctypes.byref(st)),
+              "tdgl_adjoint")
+        return J.value, grad, st.as_dict()
+
     def profile_enable(self, on: bool = True):
         check(self._L.tdgl_profile_enable(self._h, int(bool(on))), "tdgl_profile_enable")
 
@@ -213,3 +232,35 @@ def pattern(p: Params, candidates: np.ndarray, target_sites: int = 0, alpha_in: 
                          ctypes.c_void_p(scratch.data_ptr()), nb, ctypes.c_void_p(st.cuda_stream),
                          ctypes.byref(used), ctypes.byref(marked)), "tdgl_pattern")
     return alpha, used.value, marked.value
+
+
+class TimeAveragedVoltage(torch.autograd.Function):
+    """J(alpha) = time-averaged E_x of a run of n_steps from (psi0, mu0), differentiable
+    in the pinning map alpha through the hand-written adjoint (tdgl_adjoint).
+
+    The forward pass runs the checkpointed forward and, when alpha requires a
+    gradient, the reverse pass too (checkpoint-and-recompute inside the library);
+    backward scales the stored dJ/dalpha by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, alpha, params: Params, psi0, mu0=None, n_steps: int = 400, checkpoint_every: int = 20,
+                window_start: int | None = None, adj_eps: float = 1e-8):
+        s = Solver(params, alpha.detach().contiguous())
+        s.set_state(psi0, mu0, 0.0)
+        if alpha.requires_grad:
+            J, grad, _ = s.adjoint(n_steps, checkpoint_every, window_start, adj_eps)
+            ctx.save_for_backward(grad)
+        else:
+            ws = n_steps // 2 if window_start is None else window_start
+            ex = []
+            for _ in range(n_steps):
+                s.step(1)
+                ex.append(s.observables()["Ex"])
+            J = float(np.mean(ex[ws:]))
+        s.close()
+        return torch.tensor(J, dtype=torch.float64, device=alpha.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (grad,) = ctx.saved_tensors
+        return (grad * gJ.to(grad.dtype), None, None, None, None, None, None, None)
