@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the batched and adjoint measurements")
+    ap.add_argument("--batch-steps", type=int, default=30)
     # profiling captures only (a number printed with these changed is not a bench value)
     ap.add_argument("--nz", type=int, default=256, help="z planes of the grid (profiling captures: a smaller case)")
     ap.add_argument("--fixed-sweeps", type=int, default=0, help="exactly this many sweeps per step (profiling)")
@@ -182,6 +184,114 @@ def cpu_oracle_run(J: float, budget_s: float, max_steps: int | None = None):
 
 
 # ---------------------------------------------------------------------------
+# batched and adjoint modes, reported against the plain single-instance step
+# ---------------------------------------------------------------------------
+def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5):
+    """The 64-member ensemble of uneven sizes in one persistent launch per step,
+    replayed from a CUDA graph, after the autotuner; then the same members
+    stepped one after another through plain handles from the same states."""
+    import numpy as np
+    import torch
+
+    from paper_1409_8340_gb300 import inputs, presets
+    from paper_1409_8340_gb300.solver import Batch, Solver, pattern
+    members = presets.ensemble_64()
+    ps = [w.params for w in members]
+    alphas = [pattern(w.params, w.candidates, w.target_sites, w.alpha_in, w.alpha_out, device=dev)[0]
+              for w in members]
+    b = Batch(ps, alphas)
+    for i, s in enumerate(b.instances):
+        s.set_state(torch.as_tensor(inputs.random_psi(ps[i].nx, ps[i].ny, ps[i].nz, members[i].seed)
+                                    .astype(np.complex64)))
+    b.step(relax)
+    b.check()
+    rep = b.autotune(trial_steps=3)
+    b.step(3)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st0 = b.stats()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st1 = b.stats()
+    rc, _ = b.status()
+    site_iters = st1["site_iters"] - st0["site_iters"]
+    value = site_iters / (ms * 1e-3) / 1e9
+    # the same members, one after another, through plain handles from the batch's states
+    plain = []
+    for i, s in enumerate(b.instances):
+        psi, mu = s.state()
+        h = Solver(ps[i], alphas[i])
+        h.set_state(psi.clone(), mu.clone(), s.observables()["K"])
+        plain.append(h)
+    for h in plain:
+        h.step(1)
+        h.profile_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h in plain:
+        h.step(seq_steps)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    seq_iters = sum(h.profile()["sweeps"] * h.p.N for h in plain)
+    launches = sum(h.profile()["kernel_launches"] for h in plain)
+    sizes = {}
+    for p in ps:
+        sizes[f"{p.nx}x{p.ny}x{p.nz}"] = sizes.get(f"{p.nx}x{p.ny}x{p.nz}", 0) + 1
+    return {
+        "workload": "ensemble_64: 64 instances from {32^3, 64^3, 96x96x48, 128x128x64}, own seed, Bz in "
+                    "[0.05,0.5], alpha scale in [0.5,1], J in [0,0.03], 3-8 % spheres; open x, periodic y z",
+        "sizes": sizes, "sites": sum(p.N for p in ps), "steps": steps, "ms_per_step": ms / steps,
+        "value": value, "unit": METRIC, "status": rc,
+        "sweep_bytes_gbs": BYTES_PER_SITE_ITER * site_iters / (ms * 1e-3) / 1e9,
+        "launches_per_step": 1, "graph": st1["graph"], "grid_blocks": st1["grid_blocks"],
+        "blocks_per_sm": st1["blocks_per_sm"], "autotune": rep,
+        "sequential_plain": {"value": seq_iters / seq_s / 1e9, "unit": METRIC, "steps": seq_steps,
+                             "ms_per_batch_step": 1e3 * seq_s / seq_steps,
+                             "launches_per_batch_step": launches / seq_steps},
+        "speedup_vs_sequential": value / (seq_iters / seq_s / 1e9),
+    }
+
+
+def adjoint_mode(dev, n_steps: int = 400, every: int = 20, relax: int = 50):
+    """Gradient of the time-averaged E_x with respect to alpha on the 64x64x32
+    transport case: 400 steps, checkpoints every 20, recompute; against 400 plain
+    forward steps from the same state."""
+    import numpy as np
+    import torch
+
+    from paper_1409_8340_gb300 import inputs, presets
+    from paper_1409_8340_gb300.solver import Solver
+    w = presets.adjoint_64x64x32()
+    p = w.params
+    s = Solver(p, torch.as_tensor(w.alpha_field).to(dev))
+    s.set_state(torch.as_tensor(inputs.random_psi(p.nx, p.ny, p.nz, w.seed).astype(np.complex64)))
+    s.step(relax)
+    psi, mu = s.state()
+    psi0, mu0, K0 = psi.clone(), mu.clone(), s.observables()["K"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(n_steps)
+    torch.cuda.synchronize()
+    fwd_s = time.perf_counter() - t0
+    s.set_state(psi0, mu0, K0)
+    t0 = time.perf_counter()
+    J, grad, st = s.adjoint(n_steps, checkpoint_every=every)
+    torch.cuda.synchronize()
+    adj_s = time.perf_counter() - t0
+    return {"workload": "adjoint_64x64x32: open x, periodic y z, Bz 0.1, J 0.01, smoothed random alpha in [-1,1]",
+            "steps": n_steps, "checkpoint_every": every, "objective_mean_Ex": J,
+            "grad_norm": float(grad.norm()), "forward_ms": 1e3 * fwd_s, "adjoint_total_ms": 1e3 * adj_s,
+            "phases_ms": {"forward": st["ms_forward"], "recompute": st["ms_recompute"], "reverse": st["ms_reverse"]},
+            "adjoint_sweeps_per_step": st["adjoint_sweeps"] / n_steps,
+            "cost_vs_forward": adj_s / fwd_s,
+            "reverse_step_vs_forward_step": (st["ms_reverse"] / n_steps) / (1e3 * fwd_s / n_steps)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -297,6 +407,12 @@ def run_native(args, rank, world, local_rank):
         e2e_iters = pe["sweeps"] * p.N
         e2e_value = e2e_iters * world / e2e_s / 1e9
 
+    modes = {}
+    if rank == 0 and world == 1 and not args.no_modes:
+        modes["batched"] = batched_mode(dev, args.batch_steps)
+        modes["batched"]["vs_plain_step"] = modes["batched"]["value"] / value
+        modes["adjoint"] = adjoint_mode(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, cpu, _, _, _ = cpu_oracle_run(args.J, args.cpu_seconds)
@@ -332,6 +448,7 @@ def run_native(args, rank, world, local_rank):
                             "vortex_unsigned_per_layer": obs["vortex_unsigned"], "last_sweeps": obs["last_sweeps"]},
             "cpu_baseline": cpu,
         }
+        line.update(modes)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

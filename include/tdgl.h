@@ -276,6 +276,89 @@ int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, void *d_ws, si
 int tdgl_sweep_noalloc(const tdgl_config *cfg, const float *d_psi_in, const float *d_b, const float *d_D, double K,
                        float *d_psi_out, double *r2max, void *stream);
 
+/*
+ * Batched ensembles.  The paper steps one sample at a time; a batch advances up
+ * to TDGL_BATCH_MAX independent instances (own grid size, boundary conditions,
+ * field, current, time step, tolerance and alpha map) with one persistent,
+ * cooperative kernel launch per time step.  That launch runs, for every
+ * instance, the whole step of tdgl_step: init and Jacobi sweeps of the implicit
+ * psi solve (Sec. 3.1, Eq. b, Eq. final) with the convergence test of each
+ * instance applied after every sweep (Eq. convergence; an instance that has
+ * converged stops while the others go on), J_av and the K ODE on periodic x
+ * (Sec. 2.2), the Poisson right-hand side and poisson_cycles multigrid V-cycles
+ * (Sec. 3.2), the zero-mode projection of mu and the open-x voltage.  Phases
+ * are separated by a grid barrier whose waits end after timeout_ms; a timeout
+ * sets a sticky error that tdgl_batch_status reports, and every later launch
+ * returns at once.  Launches are replayed from a CUDA graph of graph_steps
+ * steps.  Work items are (instance, tile) pairs, distributed over the
+ * persistent blocks phase by phase.
+ *
+ * Requirements per instance: links_mode TDGL_LINKS_LANDAU, nx even, nx*ny*nz <
+ * 2^31, poisson_tol == 0 (a fixed number of V-cycles), and a coarsest multigrid
+ * level of at most 1024 y-z modes.  Violations return TDGL_ERR_INVALID_ARG.
+ * The instances' handles (tdgl_batch_instance) serve tdgl_set_state,
+ * tdgl_upload_state, tdgl_download_state, tdgl_get_state and tdgl_observables;
+ * tdgl_step, tdgl_solve_psi, tdgl_solve_mu and tdgl_adjoint refuse them
+ * (TDGL_ERR_INVALID_ARG).  After an instance fails (no convergence within
+ * max_iter, or a non-finite residual) its state stays at its last good step
+ * and later steps skip it.
+ */
+#define TDGL_BATCH_MAX 256
+
+typedef struct tdgl_batch tdgl_batch;
+
+typedef struct tdgl_batch_tuning {
+    int32_t blocks_per_sm;        /* persistent blocks per SM (<= the occupancy limit; 0 = that limit) */
+    int32_t graph_steps;          /* steps per CUDA graph replay (0: plain launches)                   */
+    int32_t timeout_ms;           /* bound of every grid-barrier wait                                  */
+    int32_t test_extra_arrivals;  /* 0.  > 0 makes every barrier wait for blocks that do not exist,    */
+                                  /* so that the timeout path can be tested                            */
+    int32_t kz[TDGL_BATCH_MAX];   /* z planes per sweep tile, per instance (0: default rule)           */
+} tdgl_batch_tuning;
+
+typedef struct tdgl_batch_stats {
+    int64_t steps;                /* batch steps enqueued since creation                               */
+    int64_t sweeps;               /* Jacobi sweeps, summed over instances                              */
+    double site_iters;            /* sum over instances of sites x sweeps                              */
+    int32_t grid_blocks;          /* persistent blocks of the launch                                   */
+    int32_t blocks_per_sm;
+    int32_t graph;                /* 1: steps are replayed from a captured CUDA graph                  */
+    int32_t smem_bytes;           /* dynamic shared memory per block                                   */
+} tdgl_batch_stats;
+
+typedef struct tdgl_batch_tune_report {
+    double ms_default;            /* ms per step of the starting configuration                        */
+    double ms_best;               /* ms per step of the chosen configuration                          */
+    int32_t candidates;           /* configurations timed                                              */
+    int32_t classes;              /* distinct instance grid sizes tuned separately                     */
+} tdgl_batch_tune_report;
+
+/* Device bytes for the instances' workspaces, the instance table and the batch
+ * scratch (0 if any cfg is invalid for a batch). */
+size_t tdgl_batch_workspace_bytes(const tdgl_config *cfgs, int32_t n);
+/* Create n instances in d_workspace (256-byte aligned); states start at psi = 0,
+ * mu = 0, K = 0.  Synchronises the stream. */
+int tdgl_batch_create(const tdgl_config *cfgs, int32_t n, void *d_workspace, size_t ws_bytes, void *stream,
+                      tdgl_batch **out);
+void tdgl_batch_destroy(tdgl_batch *b);
+int tdgl_batch_instance(tdgl_batch *b, int32_t i, tdgl_handle **out);
+/* Enqueue n_steps batch steps on the stream (asynchronous). */
+int tdgl_batch_step(tdgl_batch *b, int32_t n_steps);
+/* Synchronise; status[i] (may be NULL) = 0 or the error that stopped instance i.
+ * Returns TDGL_ERR_TIMEOUT after a barrier timeout, else the first nonzero
+ * instance status, else TDGL_OK. */
+int tdgl_batch_status(tdgl_batch *b, int32_t *status);
+/* Synchronise and compute every instance's observables into out[n]. */
+int tdgl_batch_observables(tdgl_batch *b, tdgl_obs *out);
+/* Synchronise; sweeps (may be NULL) receives each instance's cumulative sweeps. */
+int tdgl_batch_stats_read(tdgl_batch *b, tdgl_batch_stats *out, int64_t *sweeps);
+int tdgl_batch_get_tuning(tdgl_batch *b, tdgl_batch_tuning *out);
+int tdgl_batch_set_tuning(tdgl_batch *b, const tdgl_batch_tuning *in);
+/* Time trial_steps steps (after one warm-up step) for each candidate launch
+ * shape and per-size-class sweep tile depth, restoring the states before every
+ * trial and at the end; keeps the fastest.  The states are left unchanged. */
+int tdgl_batch_autotune(tdgl_batch *b, int32_t trial_steps, tdgl_batch_tune_report *report);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,14 @@ OPEN = 1
 LINKS_LANDAU = 0
 LINKS_GENERAL = 1
 
+TDGL_OK = 0
+TDGL_ERR_INVALID_ARG = -1
+TDGL_ERR_NOT_CONVERGED = -2
+TDGL_ERR_NONFINITE = -3
+TDGL_ERR_TIMEOUT = -4
+TDGL_ERR_CUDA = -5
+TDGL_ERR_WORKSPACE = -6
+
 ERRORS = {0: "ok", -1: "invalid argument", -2: "not converged", -3: "non-finite residual", -4: "timeout",
           -5: "CUDA error", -6: "workspace"}
 
@@ -92,6 +100,31 @@ class AdjointStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+BATCH_MAX = 256
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
+                ("test_extra_arrivals", ctypes.c_int32), ("kz", ctypes.c_int32 * BATCH_MAX)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("site_iters", ctypes.c_double),
+                ("grid_blocks", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchTuneReport(ctypes.Structure):
+    _fields_ = [("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("classes", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _SIGS = {
@@ -114,6 +147,18 @@ _SIGS = {
     "tdgl_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "tdgl_sweep_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), _P, _P, _P, ctypes.c_double, _P,
                                           ctypes.POINTER(ctypes.c_double), _P]),
+    "tdgl_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int32]),
+    "tdgl_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int32, _P, ctypes.c_size_t, _P,
+                                         ctypes.POINTER(_P)]),
+    "tdgl_batch_destroy": (None, [_P]),
+    "tdgl_batch_instance": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "tdgl_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "tdgl_batch_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "tdgl_batch_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),
+    "tdgl_batch_stats_read": (ctypes.c_int, [_P, ctypes.POINTER(BatchStats), ctypes.POINTER(ctypes.c_int64)]),
+    "tdgl_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
+    "tdgl_batch_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
+    "tdgl_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BatchTuneReport)]),
     "tdgl_pattern_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64]),
     "tdgl_pattern": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
                                     ctypes.c_float, _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_int64),

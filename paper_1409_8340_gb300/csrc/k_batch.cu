@@ -1,0 +1,576 @@
+// Batched persistent step: one cooperative launch advances every instance of a
+// batch by one full time step (Sec. 3.1 implicit psi solve with its per-sweep
+// convergence test, Sec. 2.2 K ODE, Sec. 3.2 Poisson solve).  The launch walks
+// a fixed sequence of phases; in each phase the blocks share out the work items
+// (instance, tile) of the instances taking part, and a grid barrier ends the
+// phase.  The Jacobi phases repeat while any instance is still iterating: the
+// last tile of an instance to finish a sweep reduces that instance's residual
+// maxima and decides (the same decision as the per-instance kernels), so
+// converged instances drop out while the others go on.
+//
+// All loads of arrays written earlier in the same launch go through L2
+// (ld.global.cg): the non-coherent path is never used for them.
+#include <float.h>
+#include <stddef.h>
+#include <string.h>
+
+#include "mg_tile.cuh"
+#include "sweep_tile.cuh"
+
+namespace tdgl {
+
+constexpr int kBT = kBX * kBY;   // threads per block
+constexpr int kFlat = 1024;      // sites per flat work item (4 per thread)
+
+enum BatchOp {
+    OP_INIT,
+    OP_SWEEP,
+    OP_JAVG,
+    OP_RHS,
+    OP_SMOOTH,
+    OP_RESID,
+    OP_RESTRICT,
+    OP_CFWD,
+    OP_CCONV,
+    OP_CINV,
+    OP_PROLONG,
+    OP_MEAN,
+    OP_SHIFT
+};
+
+struct BatchSmem {
+    int start[kBatchMax + 1];   // exclusive prefix of the phase's item counts
+    int cnt[kBatchMax];
+    int active[kBatchMax];      // instance takes part in the current Jacobi phase
+    int ok[kBatchMax];          // instance finished its Jacobi solve without error
+    int alive[kBatchMax];       // instance not stopped by an earlier error
+    BatchHead H;
+    MGLevel L0, L1;
+    int cached;                 // instance whose head is in H (-1: none)
+    int flag;
+};
+
+__device__ __forceinline__ int btid() { return threadIdx.x + kBX * threadIdx.y; }
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes)
+{
+    int *d = reinterpret_cast<int *>(dst);
+    const int *s = reinterpret_cast<const int *>(src);
+    for (int w = btid(); w < bytes / 4; w += kBT) d[w] = s[w];
+}
+
+// Grid barrier with a bounded wait.  Arrivals accumulate in bar[0] over the
+// launch (zeroed before it); barrier number nb completes at nb * (grid + extra)
+// arrivals.  A wait that passes timeout_ns, or sees the error flag, sets the
+// flag and returns false in every thread of the block.
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int extra, unsigned long long timeout_ns,
+                                             unsigned int nb, int *flag)
+{
+    __syncthreads();
+    if (btid() == 0) {
+        const unsigned int target = nb * (gridDim.x + extra);
+        volatile unsigned int *cnt = bar;
+        volatile unsigned int *err = bar + 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned long long t0 = gtimer();
+        int good = 1;
+        unsigned int back = 32;
+        for (;;) {
+            if (*cnt >= target) break;
+            if (*err != 0u) {
+                good = 0;
+                break;
+            }
+            if (gtimer() - t0 > timeout_ns) {
+                atomicCAS(bar + 1, 0u, 1u);
+                good = 0;
+                break;
+            }
+            __nanosleep(back);
+            if (back < 256) back <<= 1;
+        }
+        __threadfence();
+        *flag = good;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// Work items of instance t in a phase (0: not taking part).
+__device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op, int l)
+{
+    const BatchInst &I = P.inst[t];
+    switch (op) {
+    case OP_INIT: return S.alive[t] ? I.h.tiles : 0;
+    case OP_SWEEP: return S.active[t] ? I.h.tiles : 0;
+    case OP_JAVG: return (S.ok[t] && I.h.periodic_x) ? I.h.red_items : 0;
+    case OP_RHS: return S.ok[t] ? I.h.tiles : 0;
+    case OP_MEAN: return (S.ok[t] && (!I.h.freeze || I.h.open_x)) ? I.h.red_items : 0;
+    case OP_SHIFT: return (S.ok[t] && !I.h.freeze) ? (int)((I.h.a.g.N + kFlat - 1) / kFlat) : 0;
+    default: break;
+    }
+    // multigrid phases: l is the level, or the cycle for the coarsest-level ops
+    if (!S.ok[t] || I.h.freeze) return 0;
+    const int top = I.h.nlev - 1;
+    switch (op) {
+    case OP_SMOOTH: {
+        const int lev = l >> 1, c = l & 1;
+        if (lev >= top) return 0;
+        return (int)((I.h.nlines[lev][c] + I.h.lpb[lev] - 1) / I.h.lpb[lev]);
+    }
+    case OP_RESID:
+    case OP_PROLONG: return (l < top) ? (int)((I.pa.lev[l].N + kFlat - 1) / kFlat) : 0;
+    case OP_RESTRICT: return (l < top) ? (int)((I.pa.lev[l + 1].N + kFlat - 1) / kFlat) : 0;
+    case OP_CFWD:
+    case OP_CINV: return (int)(((long long)I.pa.lev[top].M * I.pa.lev[top].nx + kFlat - 1) / kFlat);
+    case OP_CCONV: return I.pa.lev[top].M;
+    default: return 0;
+    }
+}
+
+// Item counts and their exclusive prefix for a phase; returns the total.
+__device__ int build_phase(const BatchParams &P, BatchSmem &S, int op, int l)
+{
+    __syncthreads();
+    for (int t = btid(); t < P.n; t += kBT) S.cnt[t] = items_of(P, S, t, op, l);
+    __syncthreads();
+    if (btid() < 32) {
+        const int lane = btid();
+        const int per = (P.n + 31) / 32;
+        int sum = 0;
+        for (int q = 0; q < per; ++q) {
+            const int t = lane * per + q;
+            if (t < P.n) sum += S.cnt[t];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int run = incl - sum;
+        for (int q = 0; q < per; ++q) {
+            const int t = lane * per + q;
+            if (t < P.n) {
+                S.start[t] = run;
+                run += S.cnt[t];
+            }
+        }
+        if (lane == 31) S.start[P.n] = incl;
+    }
+    if (btid() == 0) S.cached = -1;
+    __syncthreads();
+    return S.start[P.n];
+}
+
+// Instance holding item `it` (the last t with start[t] <= it; it < total).
+__device__ __forceinline__ int find_instance(const BatchSmem &S, int n, int it)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.start[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Stage instance m's head (and the levels op needs) in shared memory and point
+// the sweep arguments at the phase's buffers.
+__device__ void stage(const BatchParams &P, BatchSmem &S, int m, int op, int l, int parity)
+{
+    if (S.cached == m) return;
+    __syncthreads();
+    const BatchInst &I = P.inst[m];
+    copy_words(&S.H, &I.h, sizeof(BatchHead));
+    int la = -1, lb = -1;
+    const int top = I.h.nlev - 1;
+    if (op == OP_SMOOTH) la = l >> 1;
+    else if (op == OP_RESID) la = l;
+    else if (op == OP_RESTRICT || op == OP_PROLONG) {
+        la = l;
+        lb = l + 1;
+    } else if (op == OP_CFWD || op == OP_CCONV || op == OP_CINV) la = top;
+    if (la >= 0) copy_words(&S.L0, &I.pa.lev[la], sizeof(MGLevel));
+    if (lb >= 0) copy_words(&S.L1, &I.pa.lev[lb], sizeof(MGLevel));
+    __syncthreads();
+    if (btid() == 0) {
+        SweepArgs &a = S.H.a;
+        if (op == OP_INIT) {
+            a.src = S.H.psi[S.H.iS];
+            a.dst = S.H.psi[S.H.iA];
+            a.dst_index = S.H.iA;
+        } else if (op == OP_SWEEP) {
+            // sweep p reads the output of sweep p-1: odd p A -> B, even p B -> A
+            const int ia = parity ? S.H.iA : S.H.iB, ib = parity ? S.H.iB : S.H.iA;
+            a.src = S.H.psi[ia];
+            a.dst = S.H.psi[ib];
+            a.dst_index = ib;
+        } else if (op == OP_RHS || op == OP_JAVG) {
+            a.src = S.H.psi[ldx<true>(&a.ctl->result)];
+            a.dst = S.H.psi[S.H.iS];
+        }
+        S.cached = m;
+    }
+    __syncthreads();
+}
+
+// site (i, j, k) of flat index m on an nx x ny x nz grid
+__device__ __forceinline__ void flat_ijk(unsigned int m, int nx, int ny, int &i, int &j, int &k)
+{
+    const unsigned int r = m / (unsigned int)nx;
+    i = (int)(m - r * (unsigned int)nx);
+    k = (int)(r / (unsigned int)ny);
+    j = (int)(r - (unsigned int)k * (unsigned int)ny);
+}
+
+// Im[conj(psi_m) (Ux' psi_{m+x} - conj(Ux'') psi_{m-x})]: the x-link current at
+// site m (Sec. 3.1.1, J_av), Landau links with the periodic-x wrap phase.
+__device__ __forceinline__ double javg_site(const DevGrid &g, float2 Ux, const float2 *psi, long long m)
+{
+    const int i = (int)(m % g.nx);
+    const long long t = m / g.nx;
+    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    const float2 p = ldx<true>(psi + m);
+    const long long mp = (i == g.nx - 1) ? m - (g.nx - 1) : m + 1;
+    const long long mm = (i == 0) ? m + (g.nx - 1) : m - 1;
+    const float2 lf = (i == g.nx - 1) ? cmulc(cmul(g.Py[j], g.Pz[k]), Ux) : Ux;
+    const float2 lb = (i == 0) ? cmulc(cmul(g.Py[j], g.Pz[k]), Ux) : Ux;
+    const float2 d = csub(cmul(lf, ldx<true>(psi + mp)), cmulc(lb, ldx<true>(psi + mm)));
+    return (double)(p.x * d.y - p.y * d.x);
+}
+
+__device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op, int l, int parity, int m, int li)
+{
+    BatchHead &H = S.H;
+    const int tid = btid();
+    switch (op) {
+    case OP_INIT:
+    case OP_SWEEP: {
+        const int bx = li % H.gx, r = li / H.gx;
+        const int by = r % H.gy, bz = r / H.gy;
+        float rmax = 0.f, facc = 0.f;
+        if (op == OP_INIT) sweep2_body<1, true>(H.a, H.kz, bx, by, bz, rmax, facc);
+        else sweep2_body<0, true>(H.a, H.kz, bx, by, bz, rmax, facc);
+        if (finish_sweep_at(H.a, rmax, op == OP_INIT, li, H.tiles) && tid == 0)
+            P.act[(parity & 1) * P.n + m] = H.a.ctl->done ? 0 : 1;
+        break;
+    }
+    case OP_RHS: {
+        const int bx = li % H.gx, r = li / H.gx;
+        const int by = r % H.gy, bz = r / H.gy;
+        float rmax = 0.f, facc = 0.f;
+        sweep2_body<4, true>(H.a, H.kz, bx, by, bz, rmax, facc);
+        finish_rhs_sum_at(H.a.ctl, H.a.blockred, (double)facc, H.a.wsum, li, H.tiles);
+        break;
+    }
+    case OP_JAVG: {
+        const DevGrid &g = H.a.g;
+        const float2 Ux = ldx<true>(&H.a.ctl->Ux);
+        const long long m0 = (long long)li * H.red_chunk;
+        const long long m1 = min(m0 + H.red_chunk, g.N);
+        double acc = 0.0;
+        for (long long q = m0 + tid; q < m1; q += kBT) acc += javg_site(g, Ux, H.a.src, q);
+        __shared__ double shd[32];
+        double s = block_sum(acc, shd);
+        if (tid == 0) H.a.blockred[li] = s;
+        if (!last_block(&H.a.ctl->ticket, H.red_items, &S.flag)) break;
+        double t = 0.0;
+        for (int q = tid; q < H.red_items; q += kBT) t += ((volatile double *)H.a.blockred)[q];
+        t = block_sum(t, shd);
+        if (tid == 0) {
+            H.a.ctl->ticket = 0u;
+            k_ode_update(H.a.ctl, t / (2.0 * (double)g.N * H.hx), H.hx, H.dtK, H.Jext, H.freeze ? 0 : 1);
+        }
+        break;
+    }
+    case OP_SMOOTH: {
+        const int lev = l >> 1, c = l & 1;
+        const float fsub = (lev == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
+        const DevGrid &g = H.a.g;
+        line_smooth_lines<true>(S.L0, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], H.lpb[lev], H.tpl[lev], fsub, li, tid,
+                                kBT, dsm);
+        break;
+    }
+    case OP_RESID: {
+        const MGLevel &L = S.L0;
+        const DevGrid &g = H.a.g;
+        const float fsub = (l == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
+#pragma unroll
+        for (int r = 0; r < kFlat / kBT; ++r) {
+            const long long mm = (long long)li * kFlat + r * kBT + tid;
+            if (mm >= L.N) break;
+            int i, j, k;
+            flat_ijk((unsigned int)mm, L.nx, L.ny, i, j, k);
+            L.t[mm] = residual_at<true>(L, g.bcx, g.bcy, g.bcz, fsub, i, j, k, mm);
+        }
+        break;
+    }
+    case OP_RESTRICT: {
+        const MGLevel &F = S.L0, &C = S.L1;
+        const DevGrid &g = H.a.g;
+#pragma unroll
+        for (int r = 0; r < kFlat / kBT; ++r) {
+            const long long mm = (long long)li * kFlat + r * kBT + tid;
+            if (mm >= C.N) break;
+            int i, J, K;
+            flat_ijk((unsigned int)mm, C.nx, C.ny, i, J, K);
+            C.r[mm] = restrict_at<true>(F, g.bcy, g.bcz, i, J, K);
+            C.u[mm] = 0.f;
+        }
+        break;
+    }
+    case OP_PROLONG: {
+        const MGLevel &F = S.L0, &C = S.L1;
+        const DevGrid &g = H.a.g;
+#pragma unroll
+        for (int r = 0; r < kFlat / kBT; ++r) {
+            const long long mm = (long long)li * kFlat + r * kBT + tid;
+            if (mm >= F.N) break;
+            int i, j, k;
+            flat_ijk((unsigned int)mm, F.nx, F.ny, i, j, k);
+            const float v = prolong_at<true>(F, C, g.bcy, g.bcz, i, j, k);
+            F.u[mm] = ldx<true>(F.u + mm) + v;
+        }
+        break;
+    }
+    case OP_CFWD:
+    case OP_CINV: {
+        const MGLevel &L = S.L0;
+        const float fsub = (H.nlev == 1) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
+        const long long ne = (long long)L.M * L.nx;
+#pragma unroll
+        for (int r = 0; r < kFlat / kBT; ++r) {
+            const long long e = (long long)li * kFlat + r * kBT + tid;
+            if (e >= ne) break;
+            if (op == OP_CFWD) L.t[e] = coarse_fwd_at<true>(L, fsub, e);
+            else L.u[e] = coarse_inv_at<true>(L, e);
+        }
+        break;
+    }
+    case OP_CCONV: coarse_conv_line<true>(S.L0, H.a.g.bcx, li, tid, kBT, dsm); break;
+    case OP_MEAN: {
+        // sum w mu (zero mode) and the x-face difference of mu (open-x voltage)
+        const DevGrid &g = H.a.g;
+        const float *mu = H.a.mu;
+        const long long m0 = (long long)li * H.red_chunk;
+        const long long m1 = min(m0 + H.red_chunk, g.N);
+        float accf = 0.f;
+        double accv = 0.0;
+        for (long long q = m0 + tid; q < m1; q += kBT) {
+            const int i = (int)(q % g.nx);
+            const long long t = q / g.nx;
+            const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+            float w = 1.f;
+            if (g.bcx == kOpen && (i == 0 || i == g.nx - 1)) w *= 0.5f;
+            if (g.bcy == kOpen && (j == 0 || j == g.ny - 1)) w *= 0.5f;
+            if (g.bcz == kOpen && g.nz >= 2 && (k == 0 || k == g.nz - 1)) w *= 0.5f;
+            const float v = ldx<true>(mu + q);
+            accf += w * v;
+            if (H.open_x) {
+                if (i == 0) accv += (double)v;
+                if (i == g.nx - 1) accv -= (double)v;
+            }
+        }
+        __shared__ double shd[32];
+        const double s0 = block_sum((double)accf, shd);
+        const double s1 = block_sum(accv, shd);
+        if (tid == 0) {
+            H.a.blockred[2 * li] = s0;
+            H.a.blockred[2 * li + 1] = s1;
+        }
+        if (!last_block(&H.a.ctl->ticket, H.red_items, &S.flag)) break;
+        double t0 = 0.0, t1 = 0.0;
+        for (int q = tid; q < H.red_items; q += kBT) {
+            t0 += ((volatile double *)H.a.blockred)[2 * q];
+            t1 += ((volatile double *)H.a.blockred)[2 * q + 1];
+        }
+        t0 = block_sum(t0, shd);
+        t1 = block_sum(t1, shd);
+        if (tid == 0) {
+            DevCtl *c = H.a.ctl;
+            c->ticket = 0u;
+            if (!H.freeze) c->mu_mean = t0 / H.a.wsum;
+            if (H.open_x) c->Ex = t1 / (double)((long long)g.ny * g.nz) / ((g.nx - 1) * H.hx);
+        }
+        break;
+    }
+    case OP_SHIFT: {
+        const float c = (float)ldx<true>(&H.a.ctl->mu_mean);
+        float *mu = const_cast<float *>(H.a.mu);
+#pragma unroll
+        for (int r = 0; r < kFlat / kBT; ++r) {
+            const long long q = (long long)li * kFlat + r * kBT + tid;
+            if (q >= H.a.g.N) break;
+            mu[q] = ldx<true>(mu + q) - c;
+        }
+        break;
+    }
+    default: break;
+    }
+}
+
+// This block's share of a phase's items (total from build_phase).
+__device__ void run_items(const BatchParams &P, BatchSmem &S, float *dsm, int op, int l, int parity, int total)
+{
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int m = find_instance(S, P.n, it);
+        stage(P, S, m, op, l, parity);
+        run_item(P, S, dsm, op, l, parity, m, it - S.start[m]);
+    }
+}
+
+// One phase: item table, this block's items, then the grid barrier.
+__device__ __forceinline__ bool phase(const BatchParams &P, BatchSmem &S, float *dsm, unsigned int &nbar, int op,
+                                      int l, int parity)
+{
+    run_items(P, S, dsm, op, l, parity, build_phase(P, S, op, l));
+    return grid_barrier(P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag);
+}
+
+// MINB: resident blocks per SM the register budget is sized for (2: no spills;
+// 3: a few spilled registers, more warps to cover memory latency).
+template <int MINB>
+__global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
+{
+    extern __shared__ float dsm[];
+    __shared__ BatchSmem S;
+    if (*(volatile unsigned int *)(P.bar + 1) != 0u) return;   // sticky error from an earlier launch
+    const int tid = btid();
+    unsigned int nbar = 0;
+    for (int t = tid; t < P.n; t += kBT) {
+        S.alive[t] = (ldx<true>(P.bst + t) == 0) ? 1 : 0;
+        S.active[t] = S.alive[t];
+        S.ok[t] = 0;
+    }
+    // implicit psi solve: init + first sweep, then sweeps while any instance iterates
+    if (!phase(P, S, dsm, nbar, OP_INIT, 0, 0)) return;
+    for (int p = 1;; ++p) {
+        __syncthreads();
+        for (int t = tid; t < P.n; t += kBT)
+            S.active[t] = S.active[t] && ldx<true>(P.act + ((p - 1) & 1) * P.n + t);
+        if (p > P.max_phases) {
+            // every instance stops at its own max_iter; this bound is never reached
+            if (blockIdx.x == 0 && tid == 0) atomicCAS(P.bar + 1, 0u, 2u);
+            return;
+        }
+        const int total = build_phase(P, S, OP_SWEEP, 0);
+        if (total == 0) break;
+        run_items(P, S, dsm, OP_SWEEP, 0, p & 1, total);
+        if (!grid_barrier(P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag)) return;
+    }
+    __syncthreads();
+    for (int t = tid; t < P.n; t += kBT) {
+        const DevCtl *c = P.inst[t].h.a.ctl;
+        const int st = ldx<true>(&c->status);
+        S.ok[t] = S.alive[t] && st == TDGL_OK;
+        if (blockIdx.x == 0 && S.alive[t]) {
+            P.sweeps[t] += ldx<true>(&c->iter);
+            if (st != TDGL_OK) P.bst[t] = st;
+        }
+    }
+    if (P.any_px && !phase(P, S, dsm, nbar, OP_JAVG, 0, 0)) return;
+    if (!phase(P, S, dsm, nbar, OP_RHS, 0, 0)) return;
+    for (int cyc = 0; cyc < P.cycles_max; ++cyc) {
+        for (int l = 0; l < P.lmax; ++l) {
+            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l, 0)) return;
+            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l + 1, 0)) return;
+            if (!phase(P, S, dsm, nbar, OP_RESID, l, 0)) return;
+            if (!phase(P, S, dsm, nbar, OP_RESTRICT, l, 0)) return;
+        }
+        if (!phase(P, S, dsm, nbar, OP_CFWD, 0, 0)) return;
+        if (!phase(P, S, dsm, nbar, OP_CCONV, 0, 0)) return;
+        if (!phase(P, S, dsm, nbar, OP_CINV, 0, 0)) return;
+        for (int l = P.lmax - 1; l >= 0; --l) {
+            if (!phase(P, S, dsm, nbar, OP_PROLONG, l, 0)) return;
+            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l + 1, 0)) return;
+            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l, 0)) return;
+        }
+    }
+    if (!phase(P, S, dsm, nbar, OP_MEAN, 0, 0)) return;
+    run_items(P, S, dsm, OP_SHIFT, 0, 0, build_phase(P, S, OP_SHIFT, 0));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int batch_default_kz(const DevGrid &g)
+{
+    // enough tiles for the instance to spread over the GPU, planes deep enough to
+    // amortise the two halo planes
+    const int gx = (g.nx + kPX - 1) / kPX, gy = (g.ny + kBY - 1) / kBY;
+    int kz = 8;
+    while (kz > 1 && (long long)gx * gy * ((g.nz + kz - 1) / kz) < 64) kz >>= 1;
+    return kz > g.nz ? g.nz : kz;
+}
+
+void batch_tiling(BatchInst &I, int kz)
+{
+    const DevGrid &g = I.h.a.g;
+    if (kz < 1) kz = 1;
+    if (kz > g.nz) kz = g.nz;
+    BatchHead &H = I.h;
+    H.kz = kz;
+    H.gx = (g.nx + kPX - 1) / kPX;
+    H.gy = (g.ny + kBY - 1) / kBY;
+    H.gz = (g.nz + kz - 1) / kz;
+    H.tiles = H.gx * H.gy * H.gz;
+}
+
+size_t batch_smem_bytes(const BatchInst &I)
+{
+    long long fl = 0;
+    const int top = I.h.nlev - 1;
+    for (int l = 0; l < top; ++l) {
+        const MGLevel &L = I.pa.lev[l];
+        const long long v = line_tile_floats(I.h.lpb[l], L.nx, L.kmax - L.kmin + 1);
+        if (v > fl) fl = v;
+    }
+    const MGLevel &C = I.pa.lev[top];
+    const long long v = coarse_line_floats(C.nx, C.P);
+    if (v > fl) fl = v;
+    return sizeof(float) * (size_t)fl;
+}
+
+// Kernel variant for a target of bps resident blocks per SM.
+static const void *batch_kernel(int bps)
+{
+    return bps >= 3 ? (const void *)batch_step_kernel<3> : (const void *)batch_step_kernel<2>;
+}
+
+cudaError_t batch_max_blocks_per_sm(size_t smem, int bps, int *out)
+{
+    const void *k = batch_kernel(bps);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, kBT, smem);
+}
+
+cudaError_t launch_batch_step(const BatchParams &p, int grid, int bps, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(p.bar, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBX, kBY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (bps >= 3) return cudaLaunchKernelEx(&cfg, batch_step_kernel<3>, p);
+    return cudaLaunchKernelEx(&cfg, batch_step_kernel<2>, p);
+}
+
+}  // namespace tdgl

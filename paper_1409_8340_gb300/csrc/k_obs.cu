@@ -82,21 +82,8 @@ __global__ void javg_K_kernel(KArgs a)
     for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += ((volatile double *)a.blockred)[q];
     t = block_sum(t, shd);
     if (threadIdx.x == 0) {
-        DevCtl *c = a.ctl;
-        c->ticket = 0u;
-        double jav = t / (2.0 * (double)g.N * a.hx);
-        c->javg = jav;
-        if (a.update_K) {
-            double K0 = c->K;
-            double K1 = K0 + a.dtK * (a.Jext - jav);
-            c->Ex = (K1 - K0) / a.dtK;
-            const double twopi = 6.283185307179586476925286766559;
-            K1 = K1 - (twopi / a.hx) * floor(K1 * a.hx / twopi);
-            c->K = K1;
-            double sn, cs;
-            sincos(a.hx * K1, &sn, &cs);
-            c->Ux = make_float2((float)cs, (float)sn);
-        }
+        a.ctl->ticket = 0u;
+        k_ode_update(a.ctl, t / (2.0 * (double)g.N * a.hx), a.hx, a.dtK, a.Jext, a.update_K);
     }
 }
 

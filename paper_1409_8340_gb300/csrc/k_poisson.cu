@@ -28,12 +28,11 @@
 #include <algorithm>
 #include <vector>
 
-#include "tdgl_internal.cuh"
+#include "mg_tile.cuh"
 
 namespace tdgl {
 
 constexpr int kThreads = 256;
-constexpr int kR = 16;          // consecutive outputs per thread in a line convolution
 
 static int grid_blocks(long long n, int per_thread = 4)
 {
@@ -91,82 +90,11 @@ int mg_line_kernel(int nx, int bcx, double cx, double s, std::vector<float> &Gs)
     return 0;
 }
 
-// ---------------------------------------------------------------------------
-// device helpers
-// ---------------------------------------------------------------------------
-// neighbour index along an axis with periodic wrap or Neumann mirror
-__device__ __forceinline__ int nb_idx(int j, int d, int n, int bc)
-{
-    int q = j + d;
-    if (bc == kPeriodic) {
-        if (q < 0) q += n;
-        if (q >= n) q -= n;
-    } else {
-        if (q < 0) q = -q;
-        if (q > n - 1) q = 2 * (n - 1) - q;
-    }
-    return q;
-}
-
-// index of the extended (periodic or mirrored) x line
-__device__ __forceinline__ int ext_idx(int j, int nx, int P, int open)
-{
-    while (j < 0) j += P;
-    while (j >= P) j -= P;
-    if (open && j > nx - 1) j = P - j;
-    return j;
-}
-
-__device__ __forceinline__ int pad(int j) { return j + (j >> 5); }
-
-// q-th line of colour c ((j + k) % 2 == c) on an ny x nz line grid
-__device__ __forceinline__ void line_jk(long long q, int c, int ny, int nz, int &j, int &k)
-{
-    if ((ny & 1) == 0) {
-        int half = ny >> 1;
-        k = (int)(q / half);
-        int jj = (int)(q % half);
-        j = 2 * jj + ((c + k) & 1);
-    } else {
-        long long kp = q / ny;
-        int rem = (int)(q % ny);
-        int cnt0 = (ny + 1 - c) / 2;
-        if (rem < cnt0) {
-            k = (int)(2 * kp);
-            j = 2 * rem + (c & 1);
-        } else {
-            k = (int)(2 * kp + 1);
-            j = 2 * (rem - cnt0) + ((c + 1) & 1);
-        }
-    }
-}
-
-static long long lines_of_colour(int ny, int nz, int c)
+long long mg_lines_of_colour(int ny, int nz, int c)
 {
     long long n = 0;
     for (int k = 0; k < nz; ++k) n += (ny + 1 - ((c + k) & 1)) / 2;
     return n;
-}
-
-// Convolve one padded smem line with the kernel Gs: outputs i0 .. i0+kR-1.
-// out[r] = sum_{k=kmin}^{kmax} Gs[k - kmin] * line(ext(i0 + r + k))
-__device__ __forceinline__ void line_convolve(const float *__restrict__ line, const float *__restrict__ Gs, int kmin,
-                                              int kmax, int i0, int nx, int P, int open, float out[kR])
-{
-    float w[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-        w[r] = line[pad(ext_idx(i0 + r + kmin, nx, P, open))];
-        out[r] = 0.f;
-    }
-    for (int k = kmin; k <= kmax; ++k) {
-        const float g = Gs[k - kmin];
-#pragma unroll
-        for (int r = 0; r < kR; ++r) out[r] = fmaf(g, w[r], out[r]);
-#pragma unroll
-        for (int r = 0; r < kR - 1; ++r) w[r] = w[r + 1];
-        w[kR - 1] = line[pad(ext_idx(i0 + kR + k, nx, P, open))];
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -186,54 +114,9 @@ struct LineArgs {
 __global__ void __launch_bounds__(kThreads) line_smooth_kernel(LineArgs A)
 {
     extern __shared__ float sm[];
-    const MGLevel &L = A.L;
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int lstride = pad(nx) + 1;
-    float *Gs = sm + A.lpb * lstride;
-    const int nG = L.kmax - L.kmin + 1;
-    for (int t = threadIdx.x; t < nG; t += blockDim.x) Gs[t] = L.G[t];
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
-    const long long plane = (long long)nx * ny;
-    // thread (q, r): line q of the block, positions r, r + tpl, ... (load), r*kR .. r*kR + kR-1 (solve)
-    const int q = threadIdx.x / A.tpl;
-    const int r = threadIdx.x - q * A.tpl;
-    const long long line = (long long)blockIdx.x * A.lpb + q;
-    const bool active = (q < A.lpb) && (line < A.nlines);
-    long long base = 0;
-    if (active) {
-        int j, k;
-        line_jk(line, A.color, ny, nz, j, k);
-        base = (long long)nx * j + plane * k;
-        const float *__restrict__ rr = L.r + base;
-        const float *__restrict__ up = nullptr, *__restrict__ um = nullptr, *__restrict__ zp = nullptr,
-                                     *__restrict__ zm = nullptr;
-        if (ny >= 2) {
-            up = L.u + (long long)nx * nb_idx(j, 1, ny, A.bcy) + plane * k;
-            um = L.u + (long long)nx * nb_idx(j, -1, ny, A.bcy) + plane * k;
-        }
-        if (nz >= 2) {
-            zp = L.u + (long long)nx * j + plane * nb_idx(k, 1, nz, A.bcz);
-            zm = L.u + (long long)nx * j + plane * nb_idx(k, -1, nz, A.bcz);
-        }
-        float *row = sm + q * lstride;
-#pragma unroll 8
-        for (int i = r; i < nx; i += A.tpl) {
-            float v = -(rr[i] - fsub);
-            if (up) v += L.cy * (up[i] + um[i]);
-            if (zp) v += L.cz * (zp[i] + zm[i]);
-            row[pad(i)] = v;
-        }
-    }
-    __syncthreads();
-    const int i0 = r * kR;
-    if (active && i0 < nx) {
-        float out[kR];
-        line_convolve(sm + q * lstride, Gs, L.kmin, L.kmax, i0, nx, L.P, A.bcx == kOpen, out);
-        float *dst = L.u + base;
-#pragma unroll
-        for (int rr2 = 0; rr2 < kR; ++rr2)
-            if (i0 + rr2 < nx) dst[i0 + rr2] = out[rr2];
-    }
+    line_smooth_lines<false>(A.L, A.bcx, A.bcy, A.bcz, A.color, A.nlines, A.lpb, A.tpl, fsub, blockIdx.x, threadIdx.x,
+                             blockDim.x, sm);
 }
 
 // 2D launch over (x, y) with a loop over z: thread (i, j) walks its z column.
@@ -243,25 +126,6 @@ static dim3 grid_xy(int nx, int ny) { return dim3((nx + kGX - 1) / kGX, ny); }
 constexpr int kGZ = 4;
 static dim3 grid_xyz(int nx, int ny, int nz) { return dim3((nx + kGX - 1) / kGX, ny, (nz + kGZ - 1) / kGZ); }
 
-__device__ __forceinline__ float lap_at(const MGLevel &L, const float *__restrict__ u, int i, int j, int k, long long m,
-                                        int bcx, int bcy, int bcz)
-{
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const float u0 = u[m];
-    const int ip = nb_idx(i, 1, nx, bcx), im = nb_idx(i, -1, nx, bcx);
-    float lap = L.cx * (u[m - i + ip] + u[m - i + im] - 2.f * u0);
-    if (ny >= 2) {
-        const int jp = nb_idx(j, 1, ny, bcy), jm = nb_idx(j, -1, ny, bcy);
-        lap += L.cy * (u[m + (long long)nx * (jp - j)] + u[m + (long long)nx * (jm - j)] - 2.f * u0);
-    }
-    if (nz >= 2) {
-        const int kp = nb_idx(k, 1, nz, bcz), km = nb_idx(k, -1, nz, bcz);
-        const long long pl = (long long)nx * ny;
-        lap += L.cz * (u[m + pl * (kp - k)] + u[m + pl * (km - k)] - 2.f * u0);
-    }
-    return lap;
-}
-
 // t = F - L u on one level (level 0: F = f - fmean)
 __global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0)
 {
@@ -269,8 +133,6 @@ __global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int b
     if (i >= L.nx) return;
     const float fsub = level0 ? (float)ctl->fmean : 0.f;
     const long long pl = (long long)L.nx * L.ny;
-    const float *__restrict__ u = L.u;
-    const float *__restrict__ rr = L.r;
     float *__restrict__ tt = L.t;
     const int ka = blockIdx.z * kGZ, kb = min(ka + kGZ, L.nz);
 #pragma unroll
@@ -278,7 +140,7 @@ __global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int b
         const int k = ka + dk;
         if (k >= kb) break;
         const long long m = i + (long long)L.nx * j + pl * k;
-        tt[m] = (rr[m] - fsub) - lap_at(L, u, i, j, k, m, bcx, bcy, bcz);
+        tt[m] = residual_at<false>(L, bcx, bcy, bcz, fsub, i, j, k, m);
     }
 }
 
@@ -294,7 +156,7 @@ __global__ void __launch_bounds__(kGX) residual_norm_kernel(MGLevel L, int bcx, 
         for (int k = 0; k < L.nz; ++k) {
             const long long m = i + (long long)L.nx * j + pl * k;
             const float F = L.r[m] - fsub;
-            rmax = fmaxf(rmax, fabsf(F - lap_at(L, L.u, i, j, k, m, bcx, bcy, bcz)));
+            rmax = fmaxf(rmax, fabsf(F - lap_at<false>(L, L.u, i, j, k, m, bcx, bcy, bcz)));
             fmax = fmaxf(fmax, fabsf(F));
         }
     }
@@ -333,18 +195,7 @@ __global__ void __launch_bounds__(kGX) restrict_kernel(MGLevel F, MGLevel C, int
     for (int dK = 0; dK < kGZ; ++dK) {
         const int K = Ka + dK;
         if (K >= Kb) break;
-        float acc = 0.f;
-        for (int dk = -1; dk <= 1; ++dk) {
-            const float wk = (F.fz == 2) ? (dk == 0 ? 0.5f : 0.25f) : (dk == 0 ? 1.f : 0.f);
-            if (wk == 0.f) continue;
-            const int kf = (F.nz >= 2) ? nb_idx(F.fz * K, dk, F.nz, bcz) : 0;
-            for (int dj = -1; dj <= 1; ++dj) {
-                const float wj = (F.fy == 2) ? (dj == 0 ? 0.5f : 0.25f) : (dj == 0 ? 1.f : 0.f);
-                if (wj == 0.f) continue;
-                const int jf = nb_idx(F.fy * J, dj, F.ny, bcy);
-                acc += wk * wj * F.t[(long long)nx * (jf + (long long)F.ny * kf) + i];
-            }
-        }
+        const float acc = restrict_at<false>(F, bcy, bcz, i, J, K);
         const long long m = i + (long long)nx * (J + (long long)C.ny * K);
         C.r[m] = acc;
         C.u[m] = 0.f;
@@ -357,37 +208,12 @@ __global__ void __launch_bounds__(kGX) prolong_kernel(MGLevel F, MGLevel C, int 
     const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
     if (i >= F.nx) return;
     const int nx = F.nx;
-    int j0, j1;
-    float wj1;
-    if (F.fy == 2) {
-        j0 = j >> 1;
-        j1 = (j & 1) ? ((j0 + 1 < C.ny) ? j0 + 1 : (bcy == kPeriodic ? 0 : j0)) : j0;
-        wj1 = (j & 1) ? 0.5f : 0.f;
-    } else {
-        j0 = j1 = j;
-        wj1 = 0.f;
-    }
-    const long long cpl = (long long)nx * C.ny;
     const int ka = blockIdx.z * kGZ, kb = min(ka + kGZ, F.nz);
 #pragma unroll
     for (int dk = 0; dk < kGZ; ++dk) {
         const int k = ka + dk;
         if (k >= kb) break;
-        int k0, k1;
-        float wk1;
-        if (F.fz == 2) {
-            k0 = k >> 1;
-            k1 = (k & 1) ? ((k0 + 1 < C.nz) ? k0 + 1 : (bcz == kPeriodic ? 0 : k0)) : k0;
-            wk1 = (k & 1) ? 0.5f : 0.f;
-        } else {
-            k0 = k1 = k;
-            wk1 = 0.f;
-        }
-        const float v00 = C.u[(long long)nx * j0 + cpl * k0 + i];
-        const float v10 = C.u[(long long)nx * j1 + cpl * k0 + i];
-        const float v01 = C.u[(long long)nx * j0 + cpl * k1 + i];
-        const float v11 = C.u[(long long)nx * j1 + cpl * k1 + i];
-        const float v = (1.f - wk1) * ((1.f - wj1) * v00 + wj1 * v10) + wk1 * ((1.f - wj1) * v01 + wj1 * v11);
+        const float v = prolong_at<false>(F, C, bcy, bcz, i, j, k);
         F.u[i + (long long)nx * (j + (long long)F.ny * k)] += v;
     }
 }
@@ -406,7 +232,7 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.bcy = a.g.bcy;
     A.bcz = a.g.bcz;
     A.color = color;
-    A.nlines = lines_of_colour(L.ny, L.nz, color);
+    A.nlines = mg_lines_of_colour(L.ny, L.nz, color);
     A.ctl = a.ctl;
     A.level0 = (l == 0);
     A.tpl = (L.nx + kR - 1) / kR;
@@ -538,14 +364,9 @@ struct CoarseArgs {
 __global__ void coarse_fwd_kernel(CoarseArgs A)
 {
     const MGLevel &L = A.L;
-    const int nx = L.nx, M = L.M;
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)M * nx; e += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(e / nx), i = (int)(e - (long long)q * nx);
-        float acc = 0.f;
-        for (int s = 0; s < M; ++s) acc += L.cw[(size_t)q * M + s] * (-(L.r[(size_t)s * nx + i] - fsub));
-        L.t[e] = acc;
-    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)L.M * L.nx; e += (long long)gridDim.x * blockDim.x)
+        L.t[e] = coarse_fwd_at<false>(L, fsub, e);
 }
 
 // X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period, in place in t.  One block
@@ -553,37 +374,15 @@ __global__ void coarse_fwd_kernel(CoarseArgs A)
 __global__ void __launch_bounds__(kThreads) coarse_conv_kernel(CoarseArgs A)
 {
     extern __shared__ float sm[];
-    const MGLevel &L = A.L;
-    const int nx = L.nx, M = L.M, P = L.P;
-    const int q = blockIdx.y;
-    float *line = sm;                       // padded copy of H[q]
-    float *Gs = sm + pad(nx) + 2;           // Gq[q], length P
-    const float *Gq = L.cw + 2 * (size_t)M * M + (size_t)q * P;
-    for (int t = threadIdx.x; t < nx; t += blockDim.x) line[pad(t)] = L.t[(size_t)q * nx + t];
-    for (int t = threadIdx.x; t < P; t += blockDim.x) Gs[t] = Gq[t];
-    __syncthreads();
-    const int i0 = threadIdx.x * kR;
-    if (i0 < nx) {
-        float out[kR];
-        line_convolve(line, Gs, 0, P - 1, i0, nx, P, A.bcx == kOpen, out);
-#pragma unroll
-        for (int r = 0; r < kR; ++r)
-            if (i0 + r < nx) L.t[(size_t)q * nx + i0 + r] = out[r];
-    }
+    coarse_conv_line<false>(A.L, A.bcx, blockIdx.y, threadIdx.x, blockDim.x, sm);
 }
 
 // u[s][i] = sum_q V[s][q] X[q][i]  (X in t)
 __global__ void coarse_inv_kernel(CoarseArgs A)
 {
     const MGLevel &L = A.L;
-    const int nx = L.nx, M = L.M;
-    const float *V = L.cw + (size_t)M * M;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)M * nx; e += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(e / nx), i = (int)(e - (long long)s * nx);
-        float acc = 0.f;
-        for (int q = 0; q < M; ++q) acc += V[(size_t)s * M + q] * L.t[(size_t)q * nx + i];
-        L.u[e] = acc;
-    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)L.M * L.nx; e += (long long)gridDim.x * blockDim.x)
+        L.u[e] = coarse_inv_at<false>(L, e);
 }
 
 static cudaError_t coarse_solve(const PoissonArgs &a, int l, cudaStream_t s, long long *nl)

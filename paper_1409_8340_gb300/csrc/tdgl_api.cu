@@ -279,6 +279,8 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     h->mu = at<float>(ws, L.mu);
     h->f = at<float>(ws, L.f);
     h->links = g.L ? at<float2>(ws, L.links) : nullptr;
+    h->nblockred = L.nblockred;
+    h->batch_owned = 0;
     h->last_sweeps = 8;
     h->last_cycles = c.poisson_cycles;
     h->step = 0;
@@ -499,7 +501,7 @@ int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out)
 
 int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
 {
-    if (!h) return TDGL_ERR_INVALID_ARG;
+    if (!h || h->batch_owned) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     SweepArgs a = sweep_args(h);
@@ -574,7 +576,7 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
 
 int tdgl_solve_mu(tdgl_handle *h)
 {
-    if (!h) return TDGL_ERR_INVALID_ARG;
+    if (!h || h->batch_owned) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     if (launch_poisson_rhs(h->pa, h->psi[h->cur], s) != cudaSuccess) return TDGL_ERR_CUDA;
@@ -604,7 +606,7 @@ int tdgl_solve_mu(tdgl_handle *h)
 
 int tdgl_step(tdgl_handle *h, int n_steps)
 {
-    if (!h || n_steps < 0) return TDGL_ERR_INVALID_ARG;
+    if (!h || h->batch_owned || n_steps < 0) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     for (int n = 0; n < n_steps; ++n) {
@@ -664,7 +666,7 @@ int tdgl_observables(tdgl_handle *h, tdgl_obs *out)
     out->Ex = ctl.Ex;
     out->last_r2 = ctl.r2;
     out->poisson_res = ctl.res;
-    out->last_sweeps = h->last_sweeps;
+    out->last_sweeps = h->batch_owned ? ctl.iter : h->last_sweeps;
     out->poisson_cycles = h->last_cycles;
     out->step = h->step;
     return TDGL_OK;

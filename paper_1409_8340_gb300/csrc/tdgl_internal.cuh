@@ -142,6 +142,16 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return r;
 }
 
+// Load through L2 only (CG) or through the read-only path.  A persistent kernel
+// reads data that other blocks wrote earlier in the same launch, so it must not
+// use the non-coherent path.
+template <bool CG, class T>
+__device__ __forceinline__ T ldx(const T *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // Last-block ticket: returns true in every thread of the block that finishes
 // last.  The caller has already written its per-block partial.
 __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nblocks, int *sh_flag)
@@ -198,6 +208,23 @@ struct KArgs {
 cudaError_t launch_javg_K(const KArgs &a, cudaStream_t s);
 cudaError_t launch_set_Ux(DevCtl *ctl, double hx, cudaStream_t s);
 
+// Explicit-Euler step of the K ODE (Sec. 2.2, Eq. K_ODE) from J_av, E_x = dK/dt,
+// and the rewind of K into [0, 2 pi / hx); run by one thread.
+__device__ __forceinline__ void k_ode_update(DevCtl *c, double jav, double hx, double dtK, double Jext, int update_K)
+{
+    c->javg = jav;
+    if (!update_K) return;
+    double K0 = c->K;
+    double K1 = K0 + dtK * (Jext - jav);
+    c->Ex = (K1 - K0) / dtK;
+    const double twopi = 6.283185307179586476925286766559;
+    K1 = K1 - (twopi / hx) * floor(K1 * hx / twopi);
+    c->K = K1;
+    double sn, cs;
+    sincos(hx * K1, &sn, &cs);
+    c->Ux = make_float2((float)cs, (float)sn);
+}
+
 // Multigrid Poisson solver
 struct MGLevel {
     int nx, ny, nz;
@@ -214,6 +241,8 @@ struct MGLevel {
     int M;                     // number of y-z modes of the coarsest level (ny * nz)
 };
 int mg_period(int nx, int bcx);
+// x lines of colour c ((j + k) % 2 == c) on an ny x nz line grid
+long long mg_lines_of_colour(int ny, int nz, int c);
 // Line-inverse kernel of a level with shift s = 2 cy + 2 cz; returns kmin.
 int mg_line_kernel(int nx, int bcx, double cx, double s, std::vector<float> &Gs);
 // Eigen-decomposition of the coarsest level's y-z operator and per-mode kernels
@@ -260,6 +289,47 @@ cudaError_t launch_adj_voltage_source(const DevGrid &g, float *mubar, float s_va
 cudaError_t launch_adj_rhs(const DevGrid &g, const float *mubar, float *r, DevCtl *ctl, double *blockred, double wsum,
                            cudaStream_t s);
 
+// Batched persistent step (k_batch.cu).  One entry per instance, in device memory.
+constexpr int kBatchMax = TDGL_BATCH_MAX;
+struct BatchHead {
+    SweepArgs a;               // sweep arguments (src/dst set per phase)
+    float2 *psi[3];            // the handle's three iterate buffers
+    int iS, iA, iB;            // state buffer and the two Jacobi buffers
+    int kz, gx, gy, gz;        // sweep tiling: tiles = gx gy gz
+    int tiles;
+    int red_chunk, red_items;  // sites per reduction item, items (<= half the partial slots)
+    int periodic_x, open_x, freeze, cycles;
+    double hx, dtK, Jext;
+    int nlev;                  // multigrid levels
+    int lpb[kMaxLevels];       // lines per smoothing tile
+    int tpl[kMaxLevels];       // threads per line
+    long long nlines[kMaxLevels][2];
+};
+struct BatchInst {
+    BatchHead h;               // staged in shared memory by every work item
+    PoissonArgs pa;
+};
+struct BatchParams {
+    const BatchInst *inst;     // [n]
+    int n;
+    int lmax;                  // max over instances of (levels - 1)
+    int cycles_max;
+    int any_px;                // some instance has a periodic x axis
+    int max_phases;            // bound on Jacobi phases per launch
+    int *act;                  // [2][n]: instance still iterating after a phase of that parity
+    int *bst;                  // [n]: 0, or the error that stopped the instance
+    long long *sweeps;         // [n]: cumulative Jacobi sweeps
+    unsigned int *bar;         // [0] barrier arrivals (zeroed before each launch), [1] error flag
+    unsigned int extra;        // arrivals a barrier waits for beyond the grid (0; >0 only to test the timeout)
+    unsigned long long timeout_ns;
+};
+size_t batch_smem_bytes(const BatchInst &I);
+// Occupancy of the kernel variant built for bps (2 or 3) resident blocks per SM.
+cudaError_t batch_max_blocks_per_sm(size_t smem, int bps, int *out);
+cudaError_t launch_batch_step(const BatchParams &p, int grid, int bps, size_t smem, cudaStream_t s);
+int batch_default_kz(const DevGrid &g);
+void batch_tiling(BatchInst &I, int kz);
+
 }  // namespace tdgl
 
 // Host-side solver handle (shared by the C ABI translation units).
@@ -275,6 +345,8 @@ struct tdgl_handle {
     float *mu, *f;
     float2 *links;
     tdgl::PoissonArgs pa;
+    size_t nblockred;          // capacity of blockred (doubles)
+    int batch_owned;           // 1: stepped only through a batch
     int last_sweeps;
     int last_cycles;
     int64_t step;

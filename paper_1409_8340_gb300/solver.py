@@ -116,11 +116,28 @@ class Solver:
                             ctypes.c_void_p(_stream_ptr(self.stream)), ctypes.byref(h)), "tdgl_create")
         self._h = h
         self._L = L
+        self._owned = True
+
+    @classmethod
+    def _attach(cls, p: Params, alpha: torch.Tensor, handle: ctypes.c_void_p, workspace: torch.Tensor, stream, L):
+        """A view of a handle owned by someone else (a batch instance)."""
+        obj = cls.__new__(cls)
+        obj.p = p
+        obj.device = alpha.device
+        obj.alpha = alpha
+        obj.link_phase = None
+        obj.stream = stream
+        obj.workspace = workspace
+        obj._h = handle
+        obj._L = L
+        obj._owned = False
+        return obj
 
     # ------------------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None):
-            self._L.tdgl_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self._L.tdgl_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -213,6 +230,104 @@ class Solver:
         o = _lib.Obs()
         check(self._L.tdgl_observables(self._h, ctypes.byref(o)), "tdgl_observables")
         return o.as_dict()
+
+
+class Batch:
+    """Independent TDGL problems (own sizes, fields, currents, time steps and alpha
+    maps) advanced together: one persistent launch per time step for all of them,
+    replayed from a CUDA graph.  instances[i] is a Solver view of instance i for
+    state access and observables; stepping goes through the batch."""
+
+    def __init__(self, params: list[Params], alphas: list[torch.Tensor], stream=None):
+        L = _lib.load()
+        if len(params) != len(alphas) or not params:
+            raise ValueError("one alpha map per instance is needed")
+        n = len(params)
+        self.params = list(params)
+        self.alphas = []
+        for p, a in zip(params, alphas):
+            if a.dtype != torch.float32 or not a.is_cuda or a.numel() != p.N:
+                raise ValueError("alpha must be a CUDA float32 tensor with nx*ny*nz elements")
+            self.alphas.append(a.contiguous())
+        self.device = self.alphas[0].device
+        self._cfgs = (_lib.Config * n)(*[p.to_c(a.data_ptr()) for p, a in zip(params, self.alphas)])
+        nbytes = L.tdgl_batch_workspace_bytes(self._cfgs, n)
+        if nbytes == 0:
+            raise TdglError(-1, "tdgl_batch_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        b = ctypes.c_void_p()
+        check(L.tdgl_batch_create(self._cfgs, n, ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                  ctypes.c_void_p(_stream_ptr(self.stream)), ctypes.byref(b)), "tdgl_batch_create")
+        self._b = b
+        self._L = L
+        self.n = n
+        self.instances = []
+        for i in range(n):
+            h = ctypes.c_void_p()
+            check(L.tdgl_batch_instance(b, i, ctypes.byref(h)), "tdgl_batch_instance")
+            self.instances.append(Solver._attach(params[i], self.alphas[i], h, self.workspace, self.stream, L))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for s in self.instances:
+                s._h = None
+            self._L.tdgl_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        """Enqueue n batch steps (asynchronous; errors surface in status())."""
+        check(self._L.tdgl_batch_step(self._b, int(n)), "tdgl_batch_step")
+
+    def status(self) -> tuple[int, list[int]]:
+        st = (ctypes.c_int32 * self.n)()
+        rc = self._L.tdgl_batch_status(self._b, st)
+        return rc, list(st)
+
+    def check(self):
+        rc, _ = self.status()
+        check(rc, "tdgl_batch_status")
+
+    def observables(self) -> list[dict]:
+        out = (_lib.Obs * self.n)()
+        check(self._L.tdgl_batch_observables(self._b, out), "tdgl_batch_observables")
+        return [o.as_dict() for o in out]
+
+    def stats(self) -> dict:
+        st = _lib.BatchStats()
+        sw = (ctypes.c_int64 * self.n)()
+        check(self._L.tdgl_batch_stats_read(self._b, ctypes.byref(st), sw), "tdgl_batch_stats_read")
+        d = st.as_dict()
+        d["instance_sweeps"] = list(sw)
+        return d
+
+    def tuning(self) -> dict:
+        t = _lib.BatchTuning()
+        check(self._L.tdgl_batch_get_tuning(self._b, ctypes.byref(t)), "tdgl_batch_get_tuning")
+        return {"blocks_per_sm": t.blocks_per_sm, "graph_steps": t.graph_steps, "timeout_ms": t.timeout_ms,
+                "test_extra_arrivals": t.test_extra_arrivals, "kz": list(t.kz)[:self.n]}
+
+    def set_tuning(self, **kw):
+        t = _lib.BatchTuning()
+        check(self._L.tdgl_batch_get_tuning(self._b, ctypes.byref(t)), "tdgl_batch_get_tuning")
+        for k, v in kw.items():
+            if k == "kz":
+                for i, z in enumerate(v):
+                    t.kz[i] = int(z)
+            else:
+                setattr(t, k, int(v))
+        check(self._L.tdgl_batch_set_tuning(self._b, ctypes.byref(t)), "tdgl_batch_set_tuning")
+
+    def autotune(self, trial_steps: int = 3) -> dict:
+        r = _lib.BatchTuneReport()
+        check(self._L.tdgl_batch_autotune(self._b, int(trial_steps), ctypes.byref(r)), "tdgl_batch_autotune")
+        return r.as_dict()
 
 
 def pattern(p: Params, candidates: np.ndarray, target_sites: int = 0, alpha_in: float = -1.0,

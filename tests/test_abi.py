@@ -63,3 +63,25 @@ def test_workspace_errors_before_device_work(lib):
     assert lib.tdgl_create(ctypes.byref(c), ctypes.c_void_p(0x100001), n, None, ctypes.byref(h)) == -6
     assert lib.tdgl_create(ctypes.byref(c), ctypes.c_void_p(0x100000), n - 1, None, ctypes.byref(h)) == -6
     assert lib.tdgl_error_string(-2).decode().startswith("Jacobi")
+
+
+def test_batch_validation_before_device_work(lib):
+    from paper_1409_8340_gb300._lib import Config
+    good = [_cfg(bc=(1, 0, 0), Bz=0.1), _cfg(nx=16, ny=16, nz=4, bc=(1, 0, 0), Bz=0.2, Jext=0.01)]
+    arr = (Config * 2)(*good)
+    n = lib.tdgl_batch_workspace_bytes(arr, 2)
+    assert n > lib.tdgl_workspace_bytes(ctypes.byref(good[0])) + lib.tdgl_workspace_bytes(ctypes.byref(good[1]))
+    assert lib.tdgl_batch_workspace_bytes(arr, 0) == 0
+    assert lib.tdgl_batch_workspace_bytes(arr, 257) == 0
+    for bad in (_cfg(nx=33, bc=(1, 0, 0)),                 # the batched sweep pairs x sites
+                _cfg(bc=(1, 0, 0), poisson_tol=1e-6),     # fixed V-cycles only
+                _cfg(bc=(1, 0, 0), general_links=True)):
+        if bad.links_mode == 1:
+            bad.d_link_phase = 0x2000
+        one = (Config * 1)(bad)
+        assert lib.tdgl_batch_workspace_bytes(one, 1) == 0
+        b = ctypes.c_void_p()
+        assert lib.tdgl_batch_create(one, 1, ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(b)) == -1
+    b = ctypes.c_void_p()
+    assert lib.tdgl_batch_create(arr, 2, ctypes.c_void_p(0x100001), n, None, ctypes.byref(b)) == -6
+    assert lib.tdgl_batch_create(arr, 2, ctypes.c_void_p(0x100000), n - 1, None, ctypes.byref(b)) == -6
