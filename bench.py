@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the batched and adjoint measurements")
     ap.add_argument("--batch-steps", type=int, default=30)
+    ap.add_argument("--batch-relax", type=int, default=20)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "batched", "adjoint"],
+                    help="run one mode alone and print its dictionary (profiling captures)")
     # profiling captures only (a number printed with these changed is not a bench value)
     ap.add_argument("--nz", type=int, default=256, help="z planes of the grid (profiling captures: a smaller case)")
     ap.add_argument("--fixed-sweeps", type=int, default=0, help="exactly this many sweeps per step (profiling)")
@@ -68,8 +72,10 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    src = os.path.join(ROOT, "paper_1409_8340_gb300", "csrc", "k_jacobi.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("k_jacobi.cu", "sweep_tile.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1409_8340_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def traffic_from_profile():
@@ -186,7 +192,7 @@ def cpu_oracle_run(J: float, budget_s: float, max_steps: int | None = None):
 # ---------------------------------------------------------------------------
 # batched and adjoint modes, reported against the plain single-instance step
 # ---------------------------------------------------------------------------
-def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5):
+def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5, autotune: bool = True):
     """The 64-member ensemble of uneven sizes in one persistent launch per step,
     replayed from a CUDA graph, after the autotuner; then the same members
     stepped one after another through plain handles from the same states."""
@@ -205,7 +211,7 @@ def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5):
                                     .astype(np.complex64)))
     b.step(relax)
     b.check()
-    rep = b.autotune(trial_steps=3)
+    rep = b.autotune(trial_steps=3) if autotune else None
     b.step(3)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
@@ -409,7 +415,7 @@ def run_native(args, rank, world, local_rank):
 
     modes = {}
     if rank == 0 and world == 1 and not args.no_modes:
-        modes["batched"] = batched_mode(dev, args.batch_steps)
+        modes["batched"] = batched_mode(dev, args.batch_steps, args.batch_relax, autotune=not args.no_autotune)
         modes["batched"]["vs_plain_step"] = modes["batched"]["value"] / value
         modes["adjoint"] = adjoint_mode(dev)
 
@@ -462,6 +468,19 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only != "all":
+        import torch
+
+        from paper_1409_8340_gb300 import build as B
+        B.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        if args.only == "batched":
+            out = batched_mode(dev, args.batch_steps, args.batch_relax, autotune=not args.no_autotune)
+        else:
+            out = adjoint_mode(dev)
+        print(json.dumps({"mode": args.only, **out}), flush=True)
+        return 0
     return run_native(args, rank, world, local_rank)
 
 
