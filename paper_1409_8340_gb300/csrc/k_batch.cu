@@ -296,8 +296,7 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const int lev = l >> 1, c = l & 1;
         const float fsub = (lev == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
         const DevGrid &g = H.a.g;
-        line_smooth_lines<true>(S.L0, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], H.lpb[lev], H.tpl[lev], fsub, li, tid,
-                                kBT, dsm);
+        line_smooth_lines<true>(S.L0, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], fsub, li, tid, kBT, dsm);
         break;
     }
     case OP_RESID: {
@@ -531,7 +530,7 @@ size_t batch_smem_bytes(const BatchInst &I)
     const int top = I.h.nlev - 1;
     for (int l = 0; l < top; ++l) {
         const MGLevel &L = I.pa.lev[l];
-        const long long v = line_tile_floats(I.h.lpb[l], L.nx, L.kmax - L.kmin + 1);
+        const long long v = line_tile_floats(L.nx, L.kmax - L.kmin + 1, kBT);
         if (v > fl) fl = v;
     }
     const MGLevel &C = I.pa.lev[top];

@@ -105,8 +105,6 @@ struct LineArgs {
     int bcx, bcy, bcz;
     int color;
     long long nlines;
-    int lpb;                   // lines per block
-    int tpl;                   // threads per line (ceil(nx / kR))
     const DevCtl *ctl;
     int level0;
 };
@@ -115,8 +113,8 @@ __global__ void __launch_bounds__(kThreads) line_smooth_kernel(LineArgs A)
 {
     extern __shared__ float sm[];
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
-    line_smooth_lines<false>(A.L, A.bcx, A.bcy, A.bcz, A.color, A.nlines, A.lpb, A.tpl, fsub, blockIdx.x, threadIdx.x,
-                             blockDim.x, sm);
+    line_smooth_lines<false>(A.L, A.bcx, A.bcy, A.bcz, A.color, A.nlines, fsub, blockIdx.x, threadIdx.x, blockDim.x,
+                             sm);
 }
 
 // 2D launch over (x, y) with a loop over z: thread (i, j) walks its z column.
@@ -218,11 +216,6 @@ __global__ void __launch_bounds__(kGX) prolong_kernel(MGLevel F, MGLevel C, int 
     }
 }
 
-static size_t line_smem(int lpb, int nx, int nG)
-{
-    return sizeof(float) * ((size_t)lpb * (nx + nx / 32 + 2) + nG);
-}
-
 static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s, long long *nl)
 {
     const MGLevel &L = a.lev[l];
@@ -235,14 +228,11 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.nlines = mg_lines_of_colour(L.ny, L.nz, color);
     A.ctl = a.ctl;
     A.level0 = (l == 0);
-    A.tpl = (L.nx + kR - 1) / kR;
-    int lpb = kThreads / A.tpl;
-    if (lpb < 1) lpb = 1;
-    A.lpb = lpb;
     if (A.nlines == 0) return cudaSuccess;
     const int nG = L.kmax - L.kmin + 1;
-    size_t smem = line_smem(lpb, L.nx, nG);
-    int nb = (int)((A.nlines + lpb - 1) / lpb);
+    const LineShape sh = line_shape(L.nx, nG, kThreads);
+    const size_t smem = sizeof(float) * (size_t)line_tile_floats(L.nx, nG, kThreads);
+    int nb = (int)((A.nlines + sh.lpb - 1) / sh.lpb);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(line_smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -370,7 +360,7 @@ __global__ void coarse_fwd_kernel(CoarseArgs A)
 }
 
 // X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period, in place in t.  One block
-// owns a whole mode line (nx <= kThreads * kR), so it reads the line before writing it.
+// owns a whole mode line, so it reads the line before writing it.
 __global__ void __launch_bounds__(kThreads) coarse_conv_kernel(CoarseArgs A)
 {
     extern __shared__ float sm[];
@@ -397,7 +387,7 @@ static cudaError_t coarse_solve(const PoissonArgs &a, int l, cudaStream_t s, lon
     if (nb > 4096) nb = 4096;
     coarse_fwd_kernel<<<nb, kThreads, 0, s>>>(C);
     dim3 grid(1, C.L.M);
-    size_t smem = sizeof(float) * ((size_t)(C.L.nx + C.L.nx / 32 + 2) + C.L.P);
+    size_t smem = sizeof(float) * (size_t)coarse_line_floats(C.L.nx, C.L.P);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(coarse_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

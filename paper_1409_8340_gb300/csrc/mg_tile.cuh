@@ -7,8 +7,6 @@
 
 namespace tdgl {
 
-constexpr int kR = 16;   // consecutive outputs per thread in a line convolution
-
 // neighbour index along an axis with periodic wrap or Neumann mirror
 __device__ __forceinline__ int nb_idx(int j, int d, int n, int bc)
 {
@@ -56,86 +54,130 @@ __device__ __forceinline__ void line_jk(long long q, int c, int ny, int nz, int 
     }
 }
 
-// Convolve one padded smem line with the kernel Gs: outputs i0 .. i0+kR-1.
-// out[r] = sum_{k=kmin}^{kmax} Gs[k - kmin] * line(ext(i0 + r + k))
-__device__ __forceinline__ void line_convolve(const float *__restrict__ line, const float *__restrict__ Gs, int kmin,
-                                              int kmax, int i0, int nx, int P, int open, float out[kR])
+// Shape of a zebra line-smoothing tile: each line is split over tpl threads, each
+// computing kLR consecutive outputs; lpb lines per block of nthr threads.  Each line
+// is staged in shared memory already extended (periodic wrap or Neumann mirror) by
+// the kernel support, lext floats at padded positions pad(t), lstride apart.
+constexpr int kLR = 8;
+struct LineShape {
+    int tpl, lpb, lext, lstride, ngp;
+};
+__host__ __device__ inline LineShape line_shape(int nx, int nG, int nthr)
 {
-    float w[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-        w[r] = line[pad(ext_idx(i0 + r + kmin, nx, P, open))];
-        out[r] = 0.f;
-    }
-    for (int k = kmin; k <= kmax; ++k) {
-        const float g = Gs[k - kmin];
-#pragma unroll
-        for (int r = 0; r < kR; ++r) out[r] = fmaf(g, w[r], out[r]);
-#pragma unroll
-        for (int r = 0; r < kR - 1; ++r) w[r] = w[r + 1];
-        w[kR - 1] = line[pad(ext_idx(i0 + kR + k, nx, P, open))];
-    }
+    LineShape s;
+    s.tpl = (nx + kLR - 1) / kLR;
+    s.lpb = nthr / s.tpl > 0 ? nthr / s.tpl : 1;
+    s.ngp = (nG + kLR - 1) / kLR * kLR;
+    s.lext = s.tpl * kLR + s.ngp + kLR;
+    const int phys = s.lext + (s.lext >> 5) + 1;
+    // several lines per warp: shift each line's banks past the previous one's
+    const int per_warp = (s.tpl < 32 && 32 % s.tpl == 0) ? 32 / s.tpl : 1;
+    const int shift = (per_warp > 1 && per_warp <= 8) ? 8 / per_warp : 1;
+    s.lstride = (phys + 31) / 32 * 32 + shift;
+    return s;
+}
+__host__ __device__ inline long long line_tile_floats(int nx, int nG, int nthr)
+{
+    const LineShape s = line_shape(nx, nG, nthr);
+    return (long long)s.lpb * s.lstride + s.ngp;
 }
 
-// Shared memory (floats) of one zebra line-smoothing tile of lpb lines.
-__host__ __device__ inline long long line_tile_floats(int lpb, int nx, int nG)
+// out[r] = sum_{j < ngp} Gs[j] E[i0 + r + j], r < R, with a register window that
+// slides R taps at a time (E and Gs zero-padded past their data).
+template <int R>
+__device__ __forceinline__ void window_convolve(const float *__restrict__ E, const float *__restrict__ Gs, int ngp, int i0,
+                                                float out[R])
 {
-    return (long long)lpb * (nx + nx / 32 + 2) + nG;
+    float win[2 * R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+        win[c] = E[pad(i0 + c)];
+        out[c] = 0.f;
+    }
+    for (int j0 = 0; j0 < ngp; j0 += R) {
+#pragma unroll
+        for (int c = 0; c < R; ++c) win[R + c] = E[pad(i0 + j0 + R + c)];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const float g = Gs[j0 + t];
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[r] = fmaf(g, win[r + t], out[r]);
+        }
+#pragma unroll
+        for (int c = 0; c < R; ++c) win[c] = win[R + c];
+    }
 }
 
 // Zebra x-line Gauss-Seidel, lines blk*lpb .. blk*lpb+lpb-1 of colour `color`:
 // each line solves T u_line = -(F - fsub) + cy (u_{j+1} + u_{j-1}) + cz (u_{k+1} + u_{k-1})
-// exactly by convolution with the line Green's function.  Thread tid of nthr
-// loads positions r, r + tpl, ... of line q = tid / tpl and computes kR outputs.
+// exactly by convolution with the line Green's function G_k, k = kmin..kmax:
+// u_i = sum_k G_k v_ext(i + k), v_ext the periodic or mirrored extension of the line.
 template <bool CG>
 __device__ __forceinline__ void line_smooth_lines(const MGLevel &L, int bcx, int bcy, int bcz, int color,
-                                                  long long nlines, int lpb, int tpl, float fsub, long long blk,
-                                                  int tid, int nthr, float *sm)
+                                                  long long nlines, float fsub, long long blk, int tid, int nthr,
+                                                  float *sm)
 {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int lstride = pad(nx) + 1;
-    float *Gs = sm + lpb * lstride;
     const int nG = L.kmax - L.kmin + 1;
+    const LineShape sh = line_shape(nx, nG, nthr);
+    float *Gs = sm + sh.lpb * sh.lstride;
     __syncthreads();   // shared memory may still be read by a previous tile
-    for (int t = tid; t < nG; t += nthr) Gs[t] = L.G[t];
+    for (int t = tid; t < sh.ngp; t += nthr) Gs[t] = (t < nG) ? L.G[t] : 0.f;
     const long long plane = (long long)nx * ny;
-    const int q = tid / tpl;
-    const int r = tid - q * tpl;
-    const long long line = blk * lpb + q;
-    const bool active = (q < lpb) && (line < nlines);
+    const int q = tid / sh.tpl;
+    const int r = tid - q * sh.tpl;
+    const long long line = blk * sh.lpb + q;
+    const bool active = (q < sh.lpb) && (line < nlines);
+    float *E = sm + q * sh.lstride;
+    const int off = -L.kmin;   // E position of x = 0
     long long base = 0;
     if (active) {
         int j, k;
         line_jk(line, color, ny, nz, j, k);
         base = (long long)nx * j + plane * k;
         const float *rr = L.r + base;
-        const float *up = nullptr, *um = nullptr, *zp = nullptr, *zm = nullptr;
-        if (ny >= 2) {
+        const float *up = L.u + base, *um = L.u + base, *zp = L.u + base, *zm = L.u + base;
+        const bool ya = ny >= 2, za = nz >= 2;
+        if (ya) {
             up = L.u + (long long)nx * nb_idx(j, 1, ny, bcy) + plane * k;
             um = L.u + (long long)nx * nb_idx(j, -1, ny, bcy) + plane * k;
         }
-        if (nz >= 2) {
+        if (za) {
             zp = L.u + (long long)nx * j + plane * nb_idx(k, 1, nz, bcz);
             zm = L.u + (long long)nx * j + plane * nb_idx(k, -1, nz, bcz);
         }
-        float *row = sm + q * lstride;
-#pragma unroll 8
-        for (int i = r; i < nx; i += tpl) {
-            float v = -(ldx<CG>(rr + i) - fsub);
-            if (up) v += L.cy * (ldx<CG>(up + i) + ldx<CG>(um + i));
-            if (zp) v += L.cz * (ldx<CG>(zp + i) + ldx<CG>(zm + i));
-            row[pad(i)] = v;
+        float v[kLR];
+#pragma unroll
+        for (int c = 0; c < kLR; ++c) {
+            const int i = r + sh.tpl * c;
+            if (i < nx) {
+                float a = -(ldx<CG>(rr + i) - fsub);
+                if (ya) a += L.cy * (ldx<CG>(up + i) + ldx<CG>(um + i));
+                if (za) a += L.cz * (ldx<CG>(zp + i) + ldx<CG>(zm + i));
+                v[c] = a;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kLR; ++c) {
+            const int i = r + sh.tpl * c;
+            if (i < nx) E[pad(i + off)] = v[c];
         }
     }
     __syncthreads();
-    const int i0 = r * kR;
+    if (active) {
+        // extension outside the line: periodic wrap (P = nx) or Neumann mirror (P = 2(nx-1))
+        for (int t = r; t < sh.lext; t += sh.tpl)
+            if (t < off || t >= off + nx) E[pad(t)] = E[pad(ext_idx(t - off, nx, L.P, bcx == kOpen) + off)];
+    }
+    __syncthreads();
+    const int i0 = r * kLR;
     if (active && i0 < nx) {
-        float out[kR];
-        line_convolve(sm + q * lstride, Gs, L.kmin, L.kmax, i0, nx, L.P, bcx == kOpen, out);
+        float out[kLR];
+        window_convolve<kLR>(E, Gs, sh.ngp, i0, out);
         float *dst = L.u + base;
 #pragma unroll
-        for (int rr2 = 0; rr2 < kR; ++rr2)
-            if (i0 + rr2 < nx) dst[i0 + rr2] = out[rr2];
+        for (int c = 0; c < kLR; ++c)
+            if (i0 + c < nx) dst[i0 + c] = out[c];
     }
 }
 
@@ -243,28 +285,37 @@ __device__ __forceinline__ float coarse_inv_at(const MGLevel &L, long long e)
     return acc;
 }
 
-// Shared memory (floats) of one coarse mode-line convolution.
-__host__ __device__ inline long long coarse_line_floats(int nx, int P) { return (long long)(nx + nx / 32 + 2) + P; }
+// Coarse mode-line convolution: outputs per thread and shared memory (floats).
+constexpr int kCR = 2;
+__host__ __device__ inline long long coarse_line_floats(int nx, int P)
+{
+    const int ngp = (P + kCR - 1) / kCR * kCR;
+    const int lext = (nx + kCR - 1) / kCR * kCR + ngp + kCR;
+    return (long long)(lext + (lext >> 5) + 1) + ngp;
+}
 
-// Mode line q: X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period, in place in t.
-// The block reads the whole line before writing it (nx <= nthr * kR).
+// Mode line q: X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period, in place in t
+// (the block stages the whole line in shared memory before writing it).
 template <bool CG>
 __device__ __forceinline__ void coarse_conv_line(const MGLevel &L, int bcx, int q, int tid, int nthr, float *sm)
 {
     const int nx = L.nx, M = L.M, P = L.P;
-    float *line = sm;
-    float *Gs = sm + pad(nx) + 2;
+    const int ngp = (P + kCR - 1) / kCR * kCR;
+    const int lext = (nx + kCR - 1) / kCR * kCR + ngp + kCR;
+    float *E = sm;
+    float *Gs = sm + lext + (lext >> 5) + 1;
     const float *Gq = L.cw + 2 * (size_t)M * M + (size_t)q * P;
     __syncthreads();   // shared memory may still be read by a previous tile
-    for (int t = tid; t < nx; t += nthr) line[pad(t)] = ldx<CG>(L.t + (size_t)q * nx + t);
-    for (int t = tid; t < P; t += nthr) Gs[t] = Gq[t];
+    for (int t = tid; t < nx; t += nthr) E[pad(t)] = ldx<CG>(L.t + (size_t)q * nx + t);
+    for (int t = tid; t < ngp; t += nthr) Gs[t] = (t < P) ? Gq[t] : 0.f;
     __syncthreads();
-    const int i0 = tid * kR;
-    if (i0 < nx) {
-        float out[kR];
-        line_convolve(line, Gs, 0, P - 1, i0, nx, P, bcx == kOpen, out);
+    for (int t = nx + tid; t < lext; t += nthr) E[pad(t)] = E[pad(ext_idx(t, nx, P, bcx == kOpen))];
+    __syncthreads();
+    for (int i0 = tid * kCR; i0 < nx; i0 += nthr * kCR) {
+        float out[kCR];
+        window_convolve<kCR>(E, Gs, ngp, i0, out);
 #pragma unroll
-        for (int r = 0; r < kR; ++r)
+        for (int r = 0; r < kCR; ++r)
             if (i0 + r < nx) L.t[(size_t)q * nx + i0 + r] = out[r];
     }
 }

@@ -10,7 +10,7 @@
 #include <tuple>
 #include <vector>
 
-#include "tdgl_internal.cuh"
+#include "mg_tile.cuh"
 
 using namespace tdgl;
 
@@ -137,8 +137,7 @@ void fill_instance(tdgl_batch *b, int i, int kz)
     H.nlev = h->pa.nlevels;
     for (int l = 0; l < H.nlev; ++l) {
         const MGLevel &M = h->pa.lev[l];
-        H.tpl[l] = (M.nx + 15) / 16;
-        H.lpb[l] = std::max(1, 256 / H.tpl[l]);
+        H.lpb[l] = line_shape(M.nx, M.kmax - M.kmin + 1, 256).lpb;
         for (int col = 0; col < 2; ++col) H.nlines[l][col] = mg_lines_of_colour(M.ny, M.nz, col);
     }
     I.pa = h->pa;

@@ -302,7 +302,6 @@ struct BatchHead {
     double hx, dtK, Jext;
     int nlev;                  // multigrid levels
     int lpb[kMaxLevels];       // lines per smoothing tile
-    int tpl[kMaxLevels];       // threads per line
     long long nlines[kMaxLevels][2];
 };
 struct BatchInst {
