@@ -296,7 +296,8 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const int lev = l >> 1, c = l & 1;
         const float fsub = (lev == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
         const DevGrid &g = H.a.g;
-        line_smooth_lines<true>(S.L0, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], fsub, li, tid, kBT, dsm);
+        const LineShape sh = line_shape(S.L0.nx, S.L0.kmin, S.L0.kmax, kBT);
+        line_smooth_lines<true>(S.L0, sh, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], fsub, li, tid, kBT, dsm);
         break;
     }
     case OP_RESID: {
@@ -440,7 +441,7 @@ __device__ __forceinline__ bool phase(const BatchParams &P, BatchSmem &S, float 
 template <int MINB>
 __global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
 {
-    extern __shared__ float dsm[];
+    extern __shared__ __align__(16) float dsm[];
     __shared__ BatchSmem S;
     if (*(volatile unsigned int *)(P.bar + 1) != 0u) return;   // sticky error from an earlier launch
     const int tid = btid();
@@ -530,7 +531,7 @@ size_t batch_smem_bytes(const BatchInst &I)
     const int top = I.h.nlev - 1;
     for (int l = 0; l < top; ++l) {
         const MGLevel &L = I.pa.lev[l];
-        const long long v = line_tile_floats(L.nx, L.kmax - L.kmin + 1, kBT);
+        const long long v = line_tile_floats(line_shape(L.nx, L.kmin, L.kmax, kBT));
         if (v > fl) fl = v;
     }
     const MGLevel &C = I.pa.lev[top];

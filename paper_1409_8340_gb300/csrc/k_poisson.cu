@@ -105,16 +105,17 @@ struct LineArgs {
     int bcx, bcy, bcz;
     int color;
     long long nlines;
+    LineShape sh;
     const DevCtl *ctl;
     int level0;
 };
 
 __global__ void __launch_bounds__(kThreads) line_smooth_kernel(LineArgs A)
 {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
-    line_smooth_lines<false>(A.L, A.bcx, A.bcy, A.bcz, A.color, A.nlines, fsub, blockIdx.x, threadIdx.x, blockDim.x,
-                             sm);
+    line_smooth_lines<false>(A.L, A.sh, A.bcx, A.bcy, A.bcz, A.color, A.nlines, fsub, blockIdx.x, threadIdx.x,
+                             blockDim.x, sm);
 }
 
 // 2D launch over (x, y) with a loop over z: thread (i, j) walks its z column.
@@ -188,15 +189,18 @@ __global__ void __launch_bounds__(kGX) restrict_kernel(MGLevel F, MGLevel C, int
     const int i = blockIdx.x * kGX + threadIdx.x, J = blockIdx.y;
     if (i >= C.nx) return;
     const int nx = C.nx;
-    const int Ka = blockIdx.z * kGZ, Kb = min(Ka + kGZ, C.nz);
+    const int Ka = blockIdx.z * kGZ, cnt = min(kGZ, C.nz - Ka);
+    float acc[kGZ];
+#pragma unroll
+    for (int dK = 0; dK < kGZ; ++dK)
+        if (dK < cnt) acc[dK] = restrict_at<false>(F, bcy, bcz, i, J, Ka + dK);
 #pragma unroll
     for (int dK = 0; dK < kGZ; ++dK) {
-        const int K = Ka + dK;
-        if (K >= Kb) break;
-        const float acc = restrict_at<false>(F, bcy, bcz, i, J, K);
-        const long long m = i + (long long)nx * (J + (long long)C.ny * K);
-        C.r[m] = acc;
-        C.u[m] = 0.f;
+        if (dK < cnt) {
+            const long long m = i + (long long)nx * (J + (long long)C.ny * (Ka + dK));
+            C.r[m] = acc[dK];
+            C.u[m] = 0.f;
+        }
     }
 }
 
@@ -229,9 +233,9 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.ctl = a.ctl;
     A.level0 = (l == 0);
     if (A.nlines == 0) return cudaSuccess;
-    const int nG = L.kmax - L.kmin + 1;
-    const LineShape sh = line_shape(L.nx, nG, kThreads);
-    const size_t smem = sizeof(float) * (size_t)line_tile_floats(L.nx, nG, kThreads);
+    const LineShape sh = line_shape(L.nx, L.kmin, L.kmax, kThreads);
+    A.sh = sh;
+    const size_t smem = sizeof(float) * (size_t)line_tile_floats(sh);
     int nb = (int)((A.nlines + sh.lpb - 1) / sh.lpb);
     static bool attr_set = false;
     if (!attr_set) {
@@ -363,7 +367,7 @@ __global__ void coarse_fwd_kernel(CoarseArgs A)
 // owns a whole mode line, so it reads the line before writing it.
 __global__ void __launch_bounds__(kThreads) coarse_conv_kernel(CoarseArgs A)
 {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     coarse_conv_line<false>(A.L, A.bcx, blockIdx.y, threadIdx.x, blockDim.x, sm);
 }
 
@@ -469,11 +473,20 @@ __global__ void __launch_bounds__(kGX) mu_mean_kernel(DevGrid g, const float *mu
     }
 }
 
+// mu -= mean, four sites per thread per pass, loads of a pass before its stores
 __global__ void mu_shift_kernel(long long N, float *mu, const DevCtl *ctl)
 {
     const float c = (float)ctl->mu_mean;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x)
-        mu[m] -= c;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long m0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; m0 < N; m0 += 4 * stride) {
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (m0 + q * stride < N) v[q] = mu[m0 + q * stride];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (m0 + q * stride < N) mu[m0 + q * stride] = v[q] - c;
+    }
 }
 
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s)

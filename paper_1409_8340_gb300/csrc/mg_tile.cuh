@@ -33,16 +33,17 @@ __device__ __forceinline__ int ext_idx(int j, int nx, int P, int open)
 __device__ __forceinline__ int pad(int j) { return j + (j >> 5); }
 
 // q-th line of colour c ((j + k) % 2 == c) on an ny x nz line grid
-__device__ __forceinline__ void line_jk(long long q, int c, int ny, int nz, int &j, int &k)
+__device__ __forceinline__ void line_jk(long long q64, int c, int ny, int nz, int &j, int &k)
 {
+    const unsigned int q = (unsigned int)q64;   // fewer than 2^31 lines per level
     if ((ny & 1) == 0) {
-        int half = ny >> 1;
+        const unsigned int half = (unsigned int)(ny >> 1);
         k = (int)(q / half);
-        int jj = (int)(q % half);
+        const int jj = (int)(q - (unsigned int)k * half);
         j = 2 * jj + ((c + k) & 1);
     } else {
-        long long kp = q / ny;
-        int rem = (int)(q % ny);
+        const unsigned int kp = q / (unsigned int)ny;
+        const int rem = (int)(q - kp * (unsigned int)ny);
         int cnt0 = (ny + 1 - c) / 2;
         if (rem < cnt0) {
             k = (int)(2 * kp);
@@ -54,130 +55,146 @@ __device__ __forceinline__ void line_jk(long long q, int c, int ny, int nz, int 
     }
 }
 
-// Shape of a zebra line-smoothing tile: each line is split over tpl threads, each
-// computing kLR consecutive outputs; lpb lines per block of nthr threads.  Each line
-// is staged in shared memory already extended (periodic wrap or Neumann mirror) by
-// the kernel support, lext floats at padded positions pad(t), lstride apart.
+// Shape of a zebra line-smoothing tile.  Each line is split over tpl threads, each
+// computing kLR = 8 consecutive outputs; lpb lines per block of nthr threads.  A
+// line is staged in shared memory already extended (periodic wrap or Neumann
+// mirror) by the kernel support: E[t] = v_ext(t + koff), t < lext, where koff is
+// kmin rounded down to a multiple of 4 (the taps get kmin - koff leading zeros),
+// so that the staged line and every 8-tap window sit on 16-byte boundaries.
+// Shared layout: the ngp taps, then lpb lines lstride floats apart, each at the
+// padded positions pad4(t) = t + 4 (t / 32), which spreads the 16-byte window
+// loads of a quarter warp over all banks.
 constexpr int kLR = 8;
 struct LineShape {
-    int tpl, lpb, lext, lstride, ngp;
+    int tpl, lpb, koff, ngp, lext, lstride;
 };
-__host__ __device__ inline LineShape line_shape(int nx, int nG, int nthr)
+__host__ __device__ inline int pad4(int t) { return t + 4 * (t >> 5); }
+__host__ __device__ inline LineShape line_shape(int nx, int kmin, int kmax, int nthr)
 {
     LineShape s;
     s.tpl = (nx + kLR - 1) / kLR;
     s.lpb = nthr / s.tpl > 0 ? nthr / s.tpl : 1;
-    s.ngp = (nG + kLR - 1) / kLR * kLR;
+    s.koff = (kmin >= 0) ? kmin / 4 * 4 : -((-kmin + 3) / 4 * 4);
+    s.ngp = (kmax - s.koff + 1 + kLR - 1) / kLR * kLR;
     s.lext = s.tpl * kLR + s.ngp + kLR;
-    const int phys = s.lext + (s.lext >> 5) + 1;
-    // several lines per warp: shift each line's banks past the previous one's
-    const int per_warp = (s.tpl < 32 && 32 % s.tpl == 0) ? 32 / s.tpl : 1;
-    const int shift = (per_warp > 1 && per_warp <= 8) ? 8 / per_warp : 1;
-    s.lstride = (phys + 31) / 32 * 32 + shift;
+    s.lstride = (pad4(s.lext - 1) + 1 + 3) / 4 * 4;
     return s;
 }
-__host__ __device__ inline long long line_tile_floats(int nx, int nG, int nthr)
-{
-    const LineShape s = line_shape(nx, nG, nthr);
-    return (long long)s.lpb * s.lstride + s.ngp;
-}
-
-// out[r] = sum_{j < ngp} Gs[j] E[i0 + r + j], r < R, with a register window that
-// slides R taps at a time (E and Gs zero-padded past their data).
-template <int R>
-__device__ __forceinline__ void window_convolve(const float *__restrict__ E, const float *__restrict__ Gs, int ngp, int i0,
-                                                float out[R])
-{
-    float win[2 * R];
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-        win[c] = E[pad(i0 + c)];
-        out[c] = 0.f;
-    }
-    for (int j0 = 0; j0 < ngp; j0 += R) {
-#pragma unroll
-        for (int c = 0; c < R; ++c) win[R + c] = E[pad(i0 + j0 + R + c)];
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-            const float g = Gs[j0 + t];
-#pragma unroll
-            for (int r = 0; r < R; ++r) out[r] = fmaf(g, win[r + t], out[r]);
-        }
-#pragma unroll
-        for (int c = 0; c < R; ++c) win[c] = win[R + c];
-    }
-}
+__host__ __device__ inline long long line_tile_floats(const LineShape &s) { return s.ngp + (long long)s.lpb * s.lstride; }
 
 // Zebra x-line Gauss-Seidel, lines blk*lpb .. blk*lpb+lpb-1 of colour `color`:
 // each line solves T u_line = -(F - fsub) + cy (u_{j+1} + u_{j-1}) + cz (u_{k+1} + u_{k-1})
 // exactly by convolution with the line Green's function G_k, k = kmin..kmax:
 // u_i = sum_k G_k v_ext(i + k), v_ext the periodic or mirrored extension of the line.
 template <bool CG>
-__device__ __forceinline__ void line_smooth_lines(const MGLevel &L, int bcx, int bcy, int bcz, int color,
-                                                  long long nlines, float fsub, long long blk, int tid, int nthr,
-                                                  float *sm)
+__device__ __forceinline__ void line_smooth_lines(const MGLevel &L, const LineShape &sh, int bcx, int bcy, int bcz,
+                                                  int color, long long nlines, float fsub, long long blk, int tid,
+                                                  int nthr, float *sm)
 {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int nG = L.kmax - L.kmin + 1;
-    const LineShape sh = line_shape(nx, nG, nthr);
-    float *Gs = sm + sh.lpb * sh.lstride;
+    const int nG = L.kmax - L.kmin + 1, lead = L.kmin - sh.koff;
+    float *Gs = sm;
     __syncthreads();   // shared memory may still be read by a previous tile
-    for (int t = tid; t < sh.ngp; t += nthr) Gs[t] = (t < nG) ? L.G[t] : 0.f;
-    const long long plane = (long long)nx * ny;
+    for (int t = tid; t < sh.ngp; t += nthr) Gs[t] = (t >= lead && t - lead < nG) ? L.G[t - lead] : 0.f;
     const int q = tid / sh.tpl;
     const int r = tid - q * sh.tpl;
     const long long line = blk * sh.lpb + q;
     const bool active = (q < sh.lpb) && (line < nlines);
-    float *E = sm + q * sh.lstride;
-    const int off = -L.kmin;   // E position of x = 0
+    float *E = sm + sh.ngp + q * sh.lstride;
+    const int off = -sh.koff;   // E position of x = 0, a multiple of 4
+    const int i0 = r * kLR;
+    const bool vec = (nx & 3) == 0 && i0 + kLR <= nx;   // rows start on 16-byte boundaries
     long long base = 0;
-    if (active) {
+    if (active && i0 < nx) {
         int j, k;
         line_jk(line, color, ny, nz, j, k);
+        const long long plane = (long long)nx * ny;
         base = (long long)nx * j + plane * k;
-        const float *rr = L.r + base;
-        const float *up = L.u + base, *um = L.u + base, *zp = L.u + base, *zm = L.u + base;
         const bool ya = ny >= 2, za = nz >= 2;
-        if (ya) {
-            up = L.u + (long long)nx * nb_idx(j, 1, ny, bcy) + plane * k;
-            um = L.u + (long long)nx * nb_idx(j, -1, ny, bcy) + plane * k;
-        }
-        if (za) {
-            zp = L.u + (long long)nx * j + plane * nb_idx(k, 1, nz, bcz);
-            zm = L.u + (long long)nx * j + plane * nb_idx(k, -1, nz, bcz);
-        }
+        const float *rr = L.r + base;
+        const float *up = ya ? L.u + (long long)nx * nb_idx(j, 1, ny, bcy) + plane * k : rr;
+        const float *um = ya ? L.u + (long long)nx * nb_idx(j, -1, ny, bcy) + plane * k : rr;
+        const float *zp = za ? L.u + (long long)nx * j + plane * nb_idx(k, 1, nz, bcz) : rr;
+        const float *zm = za ? L.u + (long long)nx * j + plane * nb_idx(k, -1, nz, bcz) : rr;
         float v[kLR];
+        if (vec) {
 #pragma unroll
-        for (int c = 0; c < kLR; ++c) {
-            const int i = r + sh.tpl * c;
-            if (i < nx) {
-                float a = -(ldx<CG>(rr + i) - fsub);
-                if (ya) a += L.cy * (ldx<CG>(up + i) + ldx<CG>(um + i));
-                if (za) a += L.cz * (ldx<CG>(zp + i) + ldx<CG>(zm + i));
-                v[c] = a;
+            for (int h = 0; h < kLR; h += 4) {
+                const float4 a = ldx<CG>(reinterpret_cast<const float4 *>(rr + i0 + h));
+                const float4 yp = ldx<CG>(reinterpret_cast<const float4 *>(up + i0 + h));
+                const float4 ym = ldx<CG>(reinterpret_cast<const float4 *>(um + i0 + h));
+                const float4 kp = ldx<CG>(reinterpret_cast<const float4 *>(zp + i0 + h));
+                const float4 km = ldx<CG>(reinterpret_cast<const float4 *>(zm + i0 + h));
+                const float av[4] = {a.x, a.y, a.z, a.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w},
+                            ymv[4] = {ym.x, ym.y, ym.z, ym.w}, kpv[4] = {kp.x, kp.y, kp.z, kp.w},
+                            kmv[4] = {km.x, km.y, km.z, km.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float x = -(av[c] - fsub);
+                    if (ya) x += L.cy * (ypv[c] + ymv[c]);
+                    if (za) x += L.cz * (kpv[c] + kmv[c]);
+                    v[h + c] = x;
+                }
             }
-        }
 #pragma unroll
-        for (int c = 0; c < kLR; ++c) {
-            const int i = r + sh.tpl * c;
-            if (i < nx) E[pad(i + off)] = v[c];
+            for (int h = 0; h < kLR; h += 4)
+                *reinterpret_cast<float4 *>(E + pad4(off + i0 + h)) = make_float4(v[h], v[h + 1], v[h + 2], v[h + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < kLR; ++c) {
+                const int i = i0 + c;
+                if (i < nx) {
+                    float x = -(ldx<CG>(rr + i) - fsub);
+                    if (ya) x += L.cy * (ldx<CG>(up + i) + ldx<CG>(um + i));
+                    if (za) x += L.cz * (ldx<CG>(zp + i) + ldx<CG>(zm + i));
+                    E[pad4(off + i)] = x;
+                }
+            }
         }
     }
     __syncthreads();
     if (active) {
         // extension outside the line: periodic wrap (P = nx) or Neumann mirror (P = 2(nx-1))
         for (int t = r; t < sh.lext; t += sh.tpl)
-            if (t < off || t >= off + nx) E[pad(t)] = E[pad(ext_idx(t - off, nx, L.P, bcx == kOpen) + off)];
+            if (t < off || t >= off + nx) E[pad4(t)] = E[pad4(ext_idx(t - off, nx, L.P, bcx == kOpen) + off)];
     }
     __syncthreads();
-    const int i0 = r * kLR;
     if (active && i0 < nx) {
-        float out[kLR];
-        window_convolve<kLR>(E, Gs, sh.ngp, i0, out);
-        float *dst = L.u + base;
+        // out[c] = sum_j Gs[j] E[i0 + j + c]: window of 16 staged values, 8 taps at a time
+        float out[kLR], win[2 * kLR];
+        {
+            const float4 w0 = *reinterpret_cast<const float4 *>(E + pad4(i0));
+            const float4 w1 = *reinterpret_cast<const float4 *>(E + pad4(i0 + 4));
+            win[0] = w0.x, win[1] = w0.y, win[2] = w0.z, win[3] = w0.w;
+            win[4] = w1.x, win[5] = w1.y, win[6] = w1.z, win[7] = w1.w;
+        }
 #pragma unroll
-        for (int c = 0; c < kLR; ++c)
-            if (i0 + c < nx) dst[i0 + c] = out[c];
+        for (int c = 0; c < kLR; ++c) out[c] = 0.f;
+        for (int j0 = 0; j0 < sh.ngp; j0 += kLR) {
+            const float4 w2 = *reinterpret_cast<const float4 *>(E + pad4(i0 + j0 + 8));
+            const float4 w3 = *reinterpret_cast<const float4 *>(E + pad4(i0 + j0 + 12));
+            win[8] = w2.x, win[9] = w2.y, win[10] = w2.z, win[11] = w2.w;
+            win[12] = w3.x, win[13] = w3.y, win[14] = w3.z, win[15] = w3.w;
+            const float4 g0 = *reinterpret_cast<const float4 *>(Gs + j0);
+            const float4 g1 = *reinterpret_cast<const float4 *>(Gs + j0 + 4);
+            const float g[kLR] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+            for (int t = 0; t < kLR; ++t) {
+#pragma unroll
+                for (int c = 0; c < kLR; ++c) out[c] = fmaf(g[t], win[c + t], out[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < kLR; ++c) win[c] = win[kLR + c];
+        }
+        float *dst = L.u + base + i0;
+        if (vec) {
+            reinterpret_cast<float4 *>(dst)[0] = make_float4(out[0], out[1], out[2], out[3]);
+            reinterpret_cast<float4 *>(dst)[1] = make_float4(out[4], out[5], out[6], out[7]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < kLR; ++c)
+                if (i0 + c < nx) dst[c] = out[c];
+        }
     }
 }
 
@@ -312,11 +329,26 @@ __device__ __forceinline__ void coarse_conv_line(const MGLevel &L, int bcx, int 
     for (int t = nx + tid; t < lext; t += nthr) E[pad(t)] = E[pad(ext_idx(t, nx, P, bcx == kOpen))];
     __syncthreads();
     for (int i0 = tid * kCR; i0 < nx; i0 += nthr * kCR) {
-        float out[kCR];
-        window_convolve<kCR>(E, Gs, ngp, i0, out);
+        float out[kCR], win[2 * kCR];
 #pragma unroll
-        for (int r = 0; r < kCR; ++r)
-            if (i0 + r < nx) L.t[(size_t)q * nx + i0 + r] = out[r];
+        for (int c = 0; c < kCR; ++c) {
+            win[c] = E[pad(i0 + c)];
+            out[c] = 0.f;
+        }
+        for (int j0 = 0; j0 < ngp; j0 += kCR) {
+#pragma unroll
+            for (int c = 0; c < kCR; ++c) win[kCR + c] = E[pad(i0 + j0 + kCR + c)];
+#pragma unroll
+            for (int t = 0; t < kCR; ++t) {
+#pragma unroll
+                for (int c = 0; c < kCR; ++c) out[c] = fmaf(Gs[j0 + t], win[c + t], out[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < kCR; ++c) win[c] = win[kCR + c];
+        }
+#pragma unroll
+        for (int c = 0; c < kCR; ++c)
+            if (i0 + c < nx) L.t[(size_t)q * nx + i0 + c] = out[c];
     }
 }
 

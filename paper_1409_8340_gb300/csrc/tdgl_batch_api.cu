@@ -137,7 +137,7 @@ void fill_instance(tdgl_batch *b, int i, int kz)
     H.nlev = h->pa.nlevels;
     for (int l = 0; l < H.nlev; ++l) {
         const MGLevel &M = h->pa.lev[l];
-        H.lpb[l] = line_shape(M.nx, M.kmax - M.kmin + 1, 256).lpb;
+        H.lpb[l] = line_shape(M.nx, M.kmin, M.kmax, 256).lpb;
         for (int col = 0; col < 2; ++col) H.nlines[l][col] = mg_lines_of_colour(M.ny, M.nz, col);
     }
     I.pa = h->pa;
