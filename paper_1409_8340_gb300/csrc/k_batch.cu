@@ -304,6 +304,15 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const MGLevel &L = S.L0;
         const DevGrid &g = H.a.g;
         const float fsub = (l == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
+        if ((L.nx & 3) == 0) {
+            const long long m0 = (long long)li * kFlat + 4 * tid;
+            if (m0 < L.N) {
+                int i, j, k;
+                flat_ijk((unsigned int)m0, L.nx, L.ny, i, j, k);
+                *reinterpret_cast<float4 *>(L.t + m0) = residual4_at<true>(L, g.bcx, g.bcy, g.bcz, fsub, i, j, k);
+            }
+            break;
+        }
 #pragma unroll
         for (int r = 0; r < kFlat / kBT; ++r) {
             const long long mm = (long long)li * kFlat + r * kBT + tid;
@@ -317,6 +326,16 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
     case OP_RESTRICT: {
         const MGLevel &F = S.L0, &C = S.L1;
         const DevGrid &g = H.a.g;
+        if ((C.nx & 3) == 0) {
+            const long long m0 = (long long)li * kFlat + 4 * tid;
+            if (m0 < C.N) {
+                int i, J, K;
+                flat_ijk((unsigned int)m0, C.nx, C.ny, i, J, K);
+                *reinterpret_cast<float4 *>(C.r + m0) = restrict4_at<true>(F, g.bcy, g.bcz, i, J, K);
+                *reinterpret_cast<float4 *>(C.u + m0) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            break;
+        }
 #pragma unroll
         for (int r = 0; r < kFlat / kBT; ++r) {
             const long long mm = (long long)li * kFlat + r * kBT + tid;
@@ -331,6 +350,17 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
     case OP_PROLONG: {
         const MGLevel &F = S.L0, &C = S.L1;
         const DevGrid &g = H.a.g;
+        if ((F.nx & 3) == 0) {
+            const long long m0 = (long long)li * kFlat + 4 * tid;
+            if (m0 < F.N) {
+                int i, j, k;
+                flat_ijk((unsigned int)m0, F.nx, F.ny, i, j, k);
+                const float4 v = prolong4_at<true>(F, C, g.bcy, g.bcz, i, j, k);
+                const float4 o = ld4<true>(F.u + m0);
+                *reinterpret_cast<float4 *>(F.u + m0) = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+            }
+            break;
+        }
 #pragma unroll
         for (int r = 0; r < kFlat / kBT; ++r) {
             const long long mm = (long long)li * kFlat + r * kBT + tid;

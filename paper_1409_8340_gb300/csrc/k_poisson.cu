@@ -143,6 +143,58 @@ __global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int b
     }
 }
 
+// Four-site versions (nx % 4 == 0): thread (i0 / 4, j) of a kGX-thread block over
+// 4 kGX x sites, kGZ planes per block.
+static dim3 grid_xyz4(int nx, int ny, int nz) { return dim3((nx / 4 + kGX - 1) / kGX, ny, (nz + kGZ - 1) / kGZ); }
+
+__global__ void __launch_bounds__(kGX) residual4_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0)
+{
+    const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, j = blockIdx.y;
+    if (i0 >= L.nx) return;
+    const float fsub = level0 ? (float)ctl->fmean : 0.f;
+    const long long pl = (long long)L.nx * L.ny;
+    const int ka = blockIdx.z * kGZ, kb = min(ka + kGZ, L.nz);
+#pragma unroll
+    for (int dk = 0; dk < kGZ; ++dk) {
+        const int k = ka + dk;
+        if (k >= kb) break;
+        *reinterpret_cast<float4 *>(L.t + i0 + (long long)L.nx * j + pl * k) = residual4_at<false>(L, bcx, bcy, bcz, fsub, i0, j, k);
+    }
+}
+
+__global__ void __launch_bounds__(kGX) restrict4_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+{
+    const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, J = blockIdx.y;
+    if (i0 >= C.nx) return;
+    const int nx = C.nx;
+    const int Ka = blockIdx.z * kGZ, Kb = min(Ka + kGZ, C.nz);
+#pragma unroll
+    for (int dK = 0; dK < kGZ; ++dK) {
+        const int K = Ka + dK;
+        if (K >= Kb) break;
+        const long long m = i0 + (long long)nx * (J + (long long)C.ny * K);
+        *reinterpret_cast<float4 *>(C.r + m) = restrict4_at<false>(F, bcy, bcz, i0, J, K);
+        *reinterpret_cast<float4 *>(C.u + m) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(kGX) prolong4_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+{
+    const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, j = blockIdx.y;
+    if (i0 >= F.nx) return;
+    const int nx = F.nx;
+    const int ka = blockIdx.z * kGZ, kb = min(ka + kGZ, F.nz);
+#pragma unroll
+    for (int dk = 0; dk < kGZ; ++dk) {
+        const int k = ka + dk;
+        if (k >= kb) break;
+        float4 *p = reinterpret_cast<float4 *>(F.u + i0 + (long long)nx * (j + (long long)F.ny * k));
+        const float4 v = prolong4_at<false>(F, C, bcy, bcz, i0, j, k);
+        const float4 o = *p;
+        *p = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+    }
+}
+
 // max |F - L u| and max |F| on level 0 (ctl->res = ratio)
 __global__ void __launch_bounds__(kGX) residual_norm_kernel(MGLevel L, int bcx, int bcy, int bcz, DevCtl *ctl,
                                                             double *blockred)
@@ -418,13 +470,19 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     }
     smooth(a, l, 0, s, nl);
     smooth(a, l, 1, s, nl);
-    residual_kernel<<<grid_xyz(a.lev[l].nx, a.lev[l].ny, a.lev[l].nz), kGX, 0, s>>>(a.lev[l], bcx, bcy, bcz, a.ctl,
-                                                                                   l == 0);
-    restrict_kernel<<<grid_xyz(a.lev[l + 1].nx, a.lev[l + 1].ny, a.lev[l + 1].nz), kGX, 0, s>>>(a.lev[l], a.lev[l + 1],
-                                                                                               bcy, bcz);
+    const MGLevel &F = a.lev[l], &C = a.lev[l + 1];
+    const bool v4 = (F.nx % 4) == 0;   // rows on 16-byte boundaries (x is never coarsened)
+    if (v4) {
+        residual4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0);
+        restrict4_kernel<<<grid_xyz4(C.nx, C.ny, C.nz), kGX, 0, s>>>(F, C, bcy, bcz);
+    } else {
+        residual_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0);
+        restrict_kernel<<<grid_xyz(C.nx, C.ny, C.nz), kGX, 0, s>>>(F, C, bcy, bcz);
+    }
     *nl += 3;
     vcycle(a, l + 1, s, nl);
-    prolong_kernel<<<grid_xyz(a.lev[l].nx, a.lev[l].ny, a.lev[l].nz), kGX, 0, s>>>(a.lev[l], a.lev[l + 1], bcy, bcz);
+    if (v4) prolong4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz);
+    else prolong_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz);
     smooth(a, l, 1, s, nl);
     smooth(a, l, 0, s, nl);
     return cudaGetLastError();

@@ -278,6 +278,111 @@ __device__ __forceinline__ float prolong_at(const MGLevel &F, const MGLevel &C, 
     return (1.f - wk1) * ((1.f - wj1) * v00 + wj1 * v10) + wk1 * ((1.f - wj1) * v01 + wj1 * v11);
 }
 
+// Four consecutive x sites i0..i0+3 (nx % 4 == 0, so rows start on 16-byte
+// boundaries): the same per-site arithmetic as residual_at / restrict_at /
+// prolong_at, with 16-byte loads.
+template <bool CG>
+__device__ __forceinline__ float4 ld4(const float *p)
+{
+    return ldx<CG>(reinterpret_cast<const float4 *>(p));
+}
+
+template <bool CG>
+__device__ __forceinline__ float4 residual4_at(const MGLevel &L, int bcx, int bcy, int bcz, float fsub, int i0, int j,
+                                               int k)
+{
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const long long pl = (long long)nx * ny;
+    const long long row = (long long)nx * j + pl * k;
+    const float *u = L.u;
+    const float4 c = ld4<CG>(u + row + i0);
+    const float4 rr = ld4<CG>(L.r + row + i0);
+    const float xl = ldx<CG>(u + row + nb_idx(i0, -1, nx, bcx));
+    const float xr = ldx<CG>(u + row + nb_idx(i0 + 3, 1, nx, bcx));
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+    const float fwd[4] = {c.y, c.z, c.w, xr};
+    const float bwd[4] = {xl, c.x, c.y, c.z};
+    float lap[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lap[q] = L.cx * (fwd[q] + bwd[q] - 2.f * cv[q]);
+    if (ny >= 2) {
+        const int jp = nb_idx(j, 1, ny, bcy), jm = nb_idx(j, -1, ny, bcy);
+        const float4 a = ld4<CG>(u + row + (long long)nx * (jp - j) + i0);
+        const float4 b = ld4<CG>(u + row + (long long)nx * (jm - j) + i0);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lap[q] += L.cy * (av[q] + bv[q] - 2.f * cv[q]);
+    }
+    if (nz >= 2) {
+        const int kp = nb_idx(k, 1, nz, bcz), km = nb_idx(k, -1, nz, bcz);
+        const float4 a = ld4<CG>(u + row + pl * (kp - k) + i0);
+        const float4 b = ld4<CG>(u + row + pl * (km - k) + i0);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lap[q] += L.cz * (av[q] + bv[q] - 2.f * cv[q]);
+    }
+    return make_float4((rr.x - fsub) - lap[0], (rr.y - fsub) - lap[1], (rr.z - fsub) - lap[2], (rr.w - fsub) - lap[3]);
+}
+
+template <bool CG>
+__device__ __forceinline__ float4 restrict4_at(const MGLevel &F, int bcy, int bcz, int i0, int J, int K)
+{
+    const int nx = F.nx;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nk = (F.fz == 2) ? 3 : 1, nj = (F.fy == 2) ? 3 : 1;
+    for (int a = 0; a < nk; ++a) {
+        const int dk = (nk == 3) ? a - 1 : 0;
+        const float wk = (nk == 3) ? (dk == 0 ? 0.5f : 0.25f) : 1.f;
+        const int kf = (F.nz >= 2) ? nb_idx(F.fz * K, dk, F.nz, bcz) : 0;
+        for (int b = 0; b < nj; ++b) {
+            const int dj = (nj == 3) ? b - 1 : 0;
+            const float wj = (nj == 3) ? (dj == 0 ? 0.5f : 0.25f) : 1.f;
+            const int jf = nb_idx(F.fy * J, dj, F.ny, bcy);
+            const float4 t = ld4<CG>(F.t + (long long)nx * (jf + (long long)F.ny * kf) + i0);
+            acc.x += wk * wj * t.x;
+            acc.y += wk * wj * t.y;
+            acc.z += wk * wj * t.z;
+            acc.w += wk * wj * t.w;
+        }
+    }
+    return acc;
+}
+
+template <bool CG>
+__device__ __forceinline__ float4 prolong4_at(const MGLevel &F, const MGLevel &C, int bcy, int bcz, int i0, int j, int k)
+{
+    const int nx = F.nx;
+    int j0, j1, k0, k1;
+    float wj1, wk1;
+    if (F.fy == 2) {
+        j0 = j >> 1;
+        j1 = (j & 1) ? ((j0 + 1 < C.ny) ? j0 + 1 : (bcy == kPeriodic ? 0 : j0)) : j0;
+        wj1 = (j & 1) ? 0.5f : 0.f;
+    } else {
+        j0 = j1 = j;
+        wj1 = 0.f;
+    }
+    if (F.fz == 2) {
+        k0 = k >> 1;
+        k1 = (k & 1) ? ((k0 + 1 < C.nz) ? k0 + 1 : (bcz == kPeriodic ? 0 : k0)) : k0;
+        wk1 = (k & 1) ? 0.5f : 0.f;
+    } else {
+        k0 = k1 = k;
+        wk1 = 0.f;
+    }
+    const long long cpl = (long long)nx * C.ny;
+    const float4 a = ld4<CG>(C.u + (long long)nx * j0 + cpl * k0 + i0);
+    const float4 b = ld4<CG>(C.u + (long long)nx * j1 + cpl * k0 + i0);
+    const float4 c = ld4<CG>(C.u + (long long)nx * j0 + cpl * k1 + i0);
+    const float4 d = ld4<CG>(C.u + (long long)nx * j1 + cpl * k1 + i0);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w}, cv[4] = {c.x, c.y, c.z, c.w},
+                dv[4] = {d.x, d.y, d.z, d.w};
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = (1.f - wk1) * ((1.f - wj1) * av[q] + wj1 * bv[q]) + wk1 * ((1.f - wj1) * cv[q] + wj1 * dv[q]);
+    return make_float4(o[0], o[1], o[2], o[3]);
+}
+
 // Coarsest level, exact solve.  cw = [W (M x M) | V (M x M) | Gq (M x P)].
 // Forward y-z transform: H[q][i] = sum_s W[q][s] * (-(r[s][i] - fsub)), element e = q nx + i.
 template <bool CG>
