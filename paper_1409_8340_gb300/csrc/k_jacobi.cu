@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kBX *kBY) poisson_rhs_kernel(DevGrid g, DevCtl
 
 
 template <int MODE>
-__global__ void __launch_bounds__(kBX *kBY) sweep2_kernel(SweepArgs a, int kz)
+__global__ void __launch_bounds__(kBX *kBY, 4) sweep2_kernel(SweepArgs a, int kz)
 {
     if ((MODE == 0 || MODE == 3) && *(volatile int *)&a.ctl->done) return;
     float rmax = 0.f, facc = 0.f;
