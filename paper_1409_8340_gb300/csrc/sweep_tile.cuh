@@ -330,8 +330,9 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
             }
             const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
             const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
-            const float2 n0 = cscale(1.0f / cabs2(D0), cmulc(D0, s0));
-            const float2 n1 = cscale(1.0f / cabs2(D1), cmulc(D1, s1));
+            // 1 / |D|^2, correctly rounded (the same value as 1.0f / |D|^2)
+            const float2 n0 = cscale(__frcp_rn(cabs2(D0)), cmulc(D0, s0));
+            const float2 n1 = cscale(__frcp_rn(cabs2(D1)), cmulc(D1, s1));
             dst[q] = make_float4(n0.x, n0.y, n1.x, n1.y);
             float r2a = cabs2(r0), r2b = cabs2(r1);
             r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
