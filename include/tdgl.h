@@ -77,6 +77,12 @@ extern "C" {
  *   poisson_tol     > 0: keep cycling (up to poisson_max_cycles) until
  *                   max|F - Lap mu| <= poisson_tol * max|F|.
  *   links_mode      TDGL_LINKS_LANDAU or TDGL_LINKS_GENERAL.
+ *   sweeps_per_pass 0 or 1: one Jacobi sweep per pass over memory.  2: where the
+ *                   grid allows (Landau links, nx even), two sweeps per pass
+ *                   (temporal blocking) with the per-sweep test kept exactly, so
+ *                   the results are those of one sweep at a time (to FP32
+ *                   rounding).  On GB300 the two-sweep pass is slower than two
+ *                   single sweeps at every size measured, so 1 is the default.
  *   d_alpha         device f32[N], eps(r) of Eq. epsilon (caller-owned, read-only
  *                   for the handle's lifetime).
  *   d_link_phase    device f32[3N] link phases theta_{a,m} of the link from m to
@@ -99,7 +105,7 @@ typedef struct tdgl_config {
     int32_t poisson_max_cycles;
     double poisson_tol;
     int32_t links_mode;
-    int32_t reserved0;
+    int32_t sweeps_per_pass;
     const float *d_alpha;
     const float *d_link_phase;
 } tdgl_config;

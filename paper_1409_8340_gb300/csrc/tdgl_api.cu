@@ -43,6 +43,7 @@ int validate(const tdgl_config *c)
     if (!(c->hx > 0) || !(c->hy > 0) || !(c->hz > 0) || !(c->g > 0) || !(c->ht > 0)) return TDGL_ERR_INVALID_ARG;
     if (!(c->u > 0) || !(c->beta >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->max_iter < 1 || c->check_every < 1 || c->fixed_sweeps < 0) return TDGL_ERR_INVALID_ARG;
+    if (c->sweeps_per_pass < 0 || c->sweeps_per_pass > 2) return TDGL_ERR_INVALID_ARG;
     if (c->fixed_sweeps == 0 && !(c->eps > 0)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_cycles < 1 || c->poisson_max_cycles < c->poisson_cycles) return TDGL_ERR_INVALID_ARG;
     if (!c->d_alpha) return TDGL_ERR_INVALID_ARG;
@@ -99,6 +100,7 @@ Layout layout(const tdgl_config *c)
     if (nb < 4 * 4096) nb = 4 * 4096;
     const size_t nb2d = 2 * (size_t)((c->nx + 127) / 128) * (size_t)c->ny;   // 2-D reduction grids, 2 values each
     if (nb < nb2d) nb = nb2d;
+    if (nb < 2 * pair_blocks(g)) nb = 2 * pair_blocks(g);
     L.nblockred = nb;
     L.blockred = take(sizeof(double) * nb);
     for (int q = 0; q < 3; ++q) L.psi[q] = take(8 * (size_t)N);
@@ -210,7 +212,8 @@ void ev_collect(tdgl_handle *h)
     if (!h->prof_on) return;
     if (h->pend_K) h->prof.ms_K += ev_ms(h, 4, 5);
     if (h->pend_P) h->prof.ms_poisson += ev_ms(h, 6, 7);
-    h->pend_K = h->pend_P = false;
+    if (h->pend_R) h->prof.ms_sweeps += ev_ms(h, 8, 9);
+    h->pend_K = h->pend_P = h->pend_R = false;
 }
 
 }  // namespace
@@ -410,7 +413,7 @@ void tdgl_destroy(tdgl_handle *h)
 {
     if (!h) return;
     if (h->ev_made)
-        for (int i = 0; i < 8; ++i) cudaEventDestroy(h->ev[i]);
+        for (int i = 0; i < tdgl_handle::kEvents; ++i) cudaEventDestroy(h->ev[i]);
     delete h;
 }
 
@@ -419,12 +422,12 @@ int tdgl_profile_enable(tdgl_handle *h, int on)
     if (!h) return TDGL_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
     if (on && !h->ev_made) {
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < tdgl_handle::kEvents; ++i)
             if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return TDGL_ERR_CUDA;
         h->ev_made = true;
     }
     h->prof_on = on ? 1 : 0;
-    h->pend_K = h->pend_P = false;
+    h->pend_K = h->pend_P = h->pend_R = false;
     memset(&h->prof, 0, sizeof(h->prof));
     return TDGL_OK;
 }
@@ -506,6 +509,8 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     cudaStream_t s = h->stream;
     SweepArgs a = sweep_args(h);
     const int ia = (h->cur + 1) % 3, ib = (h->cur + 2) % 3;
+    // two sweeps per pass over memory on request, where the grid allows (same results)
+    const bool pairs = c.sweeps_per_pass == 2 && pair_supported(h->g);
     a.src = h->psi[h->cur];
     a.dst = h->psi[ia];
     a.dst_index = ia;
@@ -513,7 +518,7 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     if (launch_init_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
     ev_rec(h, 1);
     h->prof.kernel_launches += 1;
-    int launched = 1;
+    int launched = 1;   // sweeps enqueued (the init fuses the first)
     bool first_sync = true;
     auto collect = [&]() {
         if (!h->prof_on) return;
@@ -521,20 +526,35 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
         first_sync = false;
         h->prof.ms_sweeps += ev_ms(h, 2, 3);
     };
+    // enqueue at least n more sweeps
     auto enqueue = [&](int n) -> int {
         ev_rec(h, 2);
-        h->prof.sweep_launches += n;
-        h->prof.kernel_launches += n;
-        for (int q = 0; q < n; ++q) {
-            // sweep number `launched` (1-based count of sweeps before it) reads the
-            // output of the previous one: odd -> A to B, even -> B to A
-            const bool odd = (launched % 2) == 1;
-            a.src = odd ? h->psi[ia] : h->psi[ib];
-            a.dst = odd ? h->psi[ib] : h->psi[ia];
-            a.dst_index = odd ? ib : ia;
-            if (launch_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
-            ++launched;
+        int launches = 0;
+        for (int q = 0; q < n;) {
+            if (pairs) {
+                // pass p covers sweeps 2p and 2p+1: p odd reads A and writes B, p even the reverse
+                const int p = (launched + 1) / 2;
+                a.src = (p & 1) ? h->psi[ia] : h->psi[ib];
+                a.dst = (p & 1) ? h->psi[ib] : h->psi[ia];
+                a.dst_index = (p & 1) ? ib : ia;
+                if (launch_sweep_pair(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+                launched += 2;
+                q += 2;
+            } else {
+                // sweep number `launched` (1-based count of sweeps before it) reads the
+                // output of the previous one: odd -> A to B, even -> B to A
+                const bool odd = (launched % 2) == 1;
+                a.src = odd ? h->psi[ia] : h->psi[ib];
+                a.dst = odd ? h->psi[ib] : h->psi[ia];
+                a.dst_index = odd ? ib : ia;
+                if (launch_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+                ++launched;
+                ++q;
+            }
+            ++launches;
         }
+        h->prof.sweep_launches += launches;
+        h->prof.kernel_launches += launches;
         ev_rec(h, 3);
         return TDGL_OK;
     };
@@ -567,6 +587,20 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     }
     if (ctl.status != TDGL_OK) return ctl.status;
     if (!ctl.done) return TDGL_ERR_NOT_CONVERGED;
+    if (ctl.redo) {
+        // the first sweep of the deciding pass is the result: recompute it from
+        // the pass's input into the pass's output buffer
+        const int p = ctl.iter / 2;
+        a.src = (p & 1) ? h->psi[ia] : h->psi[ib];
+        a.dst = (p & 1) ? h->psi[ib] : h->psi[ia];
+        a.dst_index = (p & 1) ? ib : ia;
+        if (h->prof_on) cudaEventRecord(h->ev[8], s);
+        if (launch_sweep_redo(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+        if (h->prof_on) cudaEventRecord(h->ev[9], s);
+        h->pend_R = h->prof_on;
+        h->prof.sweep_launches += 1;
+        h->prof.kernel_launches += 1;
+    }
     h->cur = ctl.result;
     h->last_sweeps = ctl.iter;
     h->prof.sweeps += ctl.iter;

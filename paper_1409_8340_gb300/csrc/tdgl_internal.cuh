@@ -49,7 +49,8 @@ struct DevCtl {
     int status;                // TDGL_OK or error
     int result;                // buffer index holding the solve's result
     unsigned int ticket;       // last-block ticket (reset by the last block)
-    int pad[3];
+    int redo;                  // 1: the result is the first sweep of the last two-sweep pass (recompute it)
+    int pad[2];
 };
 
 // ----------------------------------------------------------------------------
@@ -195,7 +196,13 @@ struct SweepArgs {
 
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
+// one sweep src -> dst that neither tests nor touches the control block
+cudaError_t launch_sweep_redo(const SweepArgs &a, cudaStream_t s);
 int sweep_blocks(const DevGrid &g);
+// two sweeps per pass (k_pair.cu); the decision is the per-sweep one
+bool pair_supported(const DevGrid &g);
+size_t pair_blocks(const DevGrid &g);
+cudaError_t launch_sweep_pair(const SweepArgs &a, cudaStream_t s);
 
 struct KArgs {
     DevGrid g;
@@ -354,8 +361,9 @@ struct tdgl_handle {
     double last_javg;
     // profiling
     int prof_on;
-    cudaEvent_t ev[8];
+    static constexpr int kEvents = 10;
+    cudaEvent_t ev[kEvents];
     bool ev_made;
-    bool pend_K, pend_P;   // K / Poisson event pairs recorded but not yet read
+    bool pend_K, pend_P, pend_R;   // K / Poisson / recomputed-sweep event pairs recorded but not yet read
     tdgl_profile prof;
 };

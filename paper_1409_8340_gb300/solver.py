@@ -43,6 +43,7 @@ class Params:
     poisson_max_cycles: int = 50
     poisson_tol: float = 0.0
     general_links: bool = False
+    sweeps_per_pass: int = 1       # 2: temporal blocking, two Jacobi sweeps per pass over memory
 
     @property
     def shape(self):
@@ -78,6 +79,7 @@ class Params:
         c.poisson_max_cycles = max(self.poisson_max_cycles, self.poisson_cycles)
         c.poisson_tol = self.poisson_tol
         c.links_mode = _lib.LINKS_GENERAL if self.general_links else _lib.LINKS_LANDAU
+        c.sweeps_per_pass = int(self.sweeps_per_pass)
         c.d_alpha = d_alpha
         c.d_link_phase = d_link_phase or None
         return c

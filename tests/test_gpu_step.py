@@ -126,3 +126,39 @@ def test_check_every_k_runs_whole_passes(O):
                                   check_every=3)
     assert no == n
     assert np.max(np.abs(gpu_state(s)[0] - psi_o)) <= TOL_PSI
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=[c[0] for c in CASES])
+def test_two_sweep_passes_match_single_sweeps(name, p):
+    """Temporal blocking (two sweeps per pass over memory) keeps the per-sweep test:
+    from the same state, the sweep counts are those of one sweep per pass and the
+    states agree to FP32 rounding (the compiler may contract the same complex
+    products into FMAs differently in the two kernels)."""
+    base = fresh(p)
+    base.poisson_tol = 0.0
+    alpha = inclusion_alpha(base, 41)
+    psi0 = I.random_psi(base.nx, base.ny, base.nz, 42)
+    one = dataclasses.replace(base, sweeps_per_pass=1)
+    two = dataclasses.replace(base, sweeps_per_pass=2)
+    s1 = make_solver(one, alpha, psi0)
+    s2 = make_solver(two, alpha, psi0)
+    odd = even = 0
+    for n in range(8):
+        s1.step(1)
+        s2.step(1)
+        n1, n2 = s1.observables()["last_sweeps"], s2.observables()["last_sweeps"]
+        assert n1 == n2, (n, n1, n2)
+        odd += n1 % 2
+        even += 1 - n1 % 2
+        a, b = gpu_state(s1), gpu_state(s2)
+        assert np.max(np.abs(a[0] - b[0])) <= 1e-6, (n, np.max(np.abs(a[0] - b[0])))
+        assert np.max(np.abs(a[1] - b[1])) <= 1e-6 * max(1.0, np.max(np.abs(a[1]))), n
+    # fixed sweep counts of both parities end on either stage of a pass
+    for fs in (2, 3, 6, 7):
+        t1 = make_solver(dataclasses.replace(one, fixed_sweeps=fs), alpha, psi0)
+        t2 = make_solver(dataclasses.replace(two, fixed_sweeps=fs), alpha, psi0)
+        t1.step(2)
+        t2.step(2)
+        a, b = gpu_state(t1), gpu_state(t2)
+        assert np.max(np.abs(a[0] - b[0])) <= 1e-6, fs
+    assert odd > 0 and even > 0   # both stages of a pass ended a solve
