@@ -360,6 +360,18 @@ int tdgl_batch_observables(tdgl_batch *b, tdgl_obs *out);
 int tdgl_batch_stats_read(tdgl_batch *b, tdgl_batch_stats *out, int64_t *sweeps);
 int tdgl_batch_get_tuning(tdgl_batch *b, tdgl_batch_tuning *out);
 int tdgl_batch_set_tuning(tdgl_batch *b, const tdgl_batch_tuning *in);
+/* Phase log: with logging on, every launch records when each of its phases ended
+ * (device globaltimer, read by one thread after the phase's grid barrier).
+ * tdgl_batch_phase_read sums the last launch's phase durations by kind into
+ * ms_by_op[TDGL_BATCH_OPS] and counts the phases into phases_by_op; the kinds are
+ * 0 init + first sweep, 1 Jacobi sweep, 2 J_av and K, 3 Poisson right-hand side,
+ * 4 line smoothing, 5 residual, 6 restriction, 7-9 coarsest-level transform,
+ * line solve and inverse transform, 10 prolongation, 11 zero mode and voltage,
+ * 12 projection.  Synchronises. */
+#define TDGL_BATCH_OPS 13
+int tdgl_batch_phase_log(tdgl_batch *b, int32_t on);
+int tdgl_batch_phase_read(tdgl_batch *b, double *ms_by_op, int32_t *phases_by_op, int32_t nops);
+
 /* Time trial_steps steps (after one warm-up step) for each candidate launch
  * shape and per-size-class sweep tile depth, restoring the states before every
  * trial and at the end; keeps the fastest.  The states are left unchanged. */

@@ -101,6 +101,8 @@ class AdjointStats(ctypes.Structure):
 
 
 BATCH_MAX = 256
+BATCH_OPS = ("init", "sweep", "javg", "rhs", "smooth", "residual", "restrict", "coarse_fwd", "coarse_conv",
+             "coarse_inv", "prolong", "mean", "shift")
 
 
 class BatchTuning(ctypes.Structure):
@@ -159,6 +161,9 @@ _SIGS = {
     "tdgl_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
     "tdgl_batch_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(BatchTuning)]),
     "tdgl_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(BatchTuneReport)]),
+    "tdgl_batch_phase_log": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "tdgl_batch_phase_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.c_int32]),
     "tdgl_pattern_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64]),
     "tdgl_pattern": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
                                     ctypes.c_float, _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_int64),

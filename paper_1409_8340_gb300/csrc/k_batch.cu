@@ -114,7 +114,7 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
     case OP_JAVG: return (S.ok[t] && I.h.periodic_x) ? I.h.red_items : 0;
     case OP_RHS: return S.ok[t] ? I.h.tiles : 0;
     case OP_MEAN: return (S.ok[t] && (!I.h.freeze || I.h.open_x)) ? I.h.red_items : 0;
-    case OP_SHIFT: return (S.ok[t] && !I.h.freeze) ? (int)((I.h.a.g.N + kFlat - 1) / kFlat) : 0;
+    case OP_SHIFT: return (S.ok[t] && !I.h.freeze) ? I.h.red_items : 0;
     default: break;
     }
     // multigrid phases: l is the level, or the cycle for the coarsest-level ops
@@ -236,9 +236,8 @@ __device__ __forceinline__ void flat_ijk(unsigned int m, int nx, int ny, int &i,
 // site m (Sec. 3.1.1, J_av), Landau links with the periodic-x wrap phase.
 __device__ __forceinline__ double javg_site(const DevGrid &g, float2 Ux, const float2 *psi, long long m)
 {
-    const int i = (int)(m % g.nx);
-    const long long t = m / g.nx;
-    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    int i, j, k;
+    flat_ijk((unsigned int)m, g.nx, g.ny, i, j, k);
     const float2 p = ldx<true>(psi + m);
     const long long mp = (i == g.nx - 1) ? m - (g.nx - 1) : m + 1;
     const long long mm = (i == 0) ? m + (g.nx - 1) : m - 1;
@@ -391,23 +390,51 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         // sum w mu (zero mode) and the x-face difference of mu (open-x voltage)
         const DevGrid &g = H.a.g;
         const float *mu = H.a.mu;
-        const long long m0 = (long long)li * H.red_chunk;
-        const long long m1 = min(m0 + H.red_chunk, g.N);
+        const unsigned int m0 = (unsigned int)li * (unsigned int)H.red_chunk;
+        const unsigned int m1 = (unsigned int)min((long long)m0 + H.red_chunk, g.N);
+        const bool ox = g.bcx == kOpen, oy = g.bcy == kOpen, oz = g.bcz == kOpen && g.nz >= 2;
         float accf = 0.f;
         double accv = 0.0;
-        for (long long q = m0 + tid; q < m1; q += kBT) {
-            const int i = (int)(q % g.nx);
-            const long long t = q / g.nx;
-            const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+        auto site = [&](unsigned int q, int i, int j, int k, float v) {
             float w = 1.f;
-            if (g.bcx == kOpen && (i == 0 || i == g.nx - 1)) w *= 0.5f;
-            if (g.bcy == kOpen && (j == 0 || j == g.ny - 1)) w *= 0.5f;
-            if (g.bcz == kOpen && g.nz >= 2 && (k == 0 || k == g.nz - 1)) w *= 0.5f;
-            const float v = ldx<true>(mu + q);
+            if (ox && (i == 0 || i == g.nx - 1)) w *= 0.5f;
+            if (oy && (j == 0 || j == g.ny - 1)) w *= 0.5f;
+            if (oz && (k == 0 || k == g.nz - 1)) w *= 0.5f;
             accf += w * v;
             if (H.open_x) {
                 if (i == 0) accv += (double)v;
                 if (i == g.nx - 1) accv -= (double)v;
+            }
+        };
+        if ((g.nx & 3) == 0) {
+            // four sites of one row per thread and pass; the loads of all passes first
+            constexpr int kMP = 8;
+            float4 v[kMP];
+#pragma unroll
+            for (int r = 0; r < kMP; ++r) {
+                const unsigned int q = m0 + 4u * (tid + r * kBT);
+                if (q < m1) v[r] = ld4<true>(mu + q);
+            }
+            for (unsigned int base = m0; base < m1; base += 4u * kBT * kMP) {
+#pragma unroll
+                for (int r = 0; r < kMP; ++r) {
+                    const unsigned int q = base + 4u * (tid + r * kBT);
+                    if (q < m1) {
+                        const float4 x = (base == m0) ? v[r] : ld4<true>(mu + q);
+                        int i, j, k;
+                        flat_ijk(q, g.nx, g.ny, i, j, k);
+                        site(q, i, j, k, x.x);
+                        site(q + 1, i + 1, j, k, x.y);
+                        site(q + 2, i + 2, j, k, x.z);
+                        site(q + 3, i + 3, j, k, x.w);
+                    }
+                }
+            }
+        } else {
+            for (unsigned int q = m0 + tid; q < m1; q += kBT) {
+                int i, j, k;
+                flat_ijk(q, g.nx, g.ny, i, j, k);
+                site(q, i, j, k, ldx<true>(mu + q));
             }
         }
         __shared__ double shd[32];
@@ -436,11 +463,15 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
     case OP_SHIFT: {
         const float c = (float)ldx<true>(&H.a.ctl->mu_mean);
         float *mu = const_cast<float *>(H.a.mu);
-#pragma unroll
-        for (int r = 0; r < kFlat / kBT; ++r) {
-            const long long q = (long long)li * kFlat + r * kBT + tid;
-            if (q >= H.a.g.N) break;
-            mu[q] = ldx<true>(mu + q) - c;
+        const long long m0 = (long long)li * H.red_chunk;
+        const long long m1 = min(m0 + H.red_chunk, H.a.g.N);
+        if ((H.a.g.N & 3) == 0) {
+            for (long long q = m0 + 4 * tid; q < m1; q += 4 * kBT) {
+                const float4 v = ld4<true>(mu + q);
+                *reinterpret_cast<float4 *>(mu + q) = make_float4(v.x - c, v.y - c, v.z - c, v.w - c);
+            }
+        } else {
+            for (long long q = m0 + tid; q < m1; q += kBT) mu[q] = ldx<true>(mu + q) - c;
         }
         break;
     }
@@ -458,12 +489,23 @@ __device__ void run_items(const BatchParams &P, BatchSmem &S, float *dsm, int op
     }
 }
 
+// Phase log entry (block 0): the time every block has finished phase nb, and its op.
+__device__ __forceinline__ void log_phase(const BatchParams &P, unsigned int nb, int op, int l)
+{
+    if (P.plog && blockIdx.x == 0 && btid() == 0 && (int)nb < P.plog_cap) {
+        P.plog[2 * nb] = gtimer();
+        P.plog[2 * nb + 1] = (unsigned long long)(op * 256 + l);
+    }
+}
+
 // One phase: item table, this block's items, then the grid barrier.
 __device__ __forceinline__ bool phase(const BatchParams &P, BatchSmem &S, float *dsm, unsigned int &nbar, int op,
                                       int l, int parity)
 {
     run_items(P, S, dsm, op, l, parity, build_phase(P, S, op, l));
-    return grid_barrier(P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag);
+    if (!grid_barrier(P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag)) return false;
+    log_phase(P, nbar, op, l);
+    return true;
 }
 
 // MINB: resident blocks per SM the register budget is sized for (2: no spills;
@@ -476,6 +518,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
     if (*(volatile unsigned int *)(P.bar + 1) != 0u) return;   // sticky error from an earlier launch
     const int tid = btid();
     unsigned int nbar = 0;
+    log_phase(P, 0, 255, 0);   // launch start
     for (int t = tid; t < P.n; t += kBT) {
         S.alive[t] = (ldx<true>(P.bst + t) == 0) ? 1 : 0;
         S.active[t] = S.alive[t];
@@ -496,6 +539,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
         if (total == 0) break;
         run_items(P, S, dsm, OP_SWEEP, 0, p & 1, total);
         if (!grid_barrier(P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag)) return;
+        log_phase(P, nbar, OP_SWEEP, 0);
     }
     __syncthreads();
     for (int t = tid; t < P.n; t += kBT) {
@@ -527,6 +571,8 @@ __global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
     }
     if (!phase(P, S, dsm, nbar, OP_MEAN, 0, 0)) return;
     run_items(P, S, dsm, OP_SHIFT, 0, 0, build_phase(P, S, OP_SHIFT, 0));
+    log_phase(P, nbar + 1, OP_SHIFT, 0);   // block 0's own end (no barrier follows)
+    if (P.plog && blockIdx.x == 0 && tid == 0 && (int)(nbar + 2) < P.plog_cap) P.plog[2 * (nbar + 2) + 1] = 0xffffull;
 }
 
 // ---------------------------------------------------------------------------

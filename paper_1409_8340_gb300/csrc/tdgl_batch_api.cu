@@ -17,6 +17,7 @@ using namespace tdgl;
 namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr int kPhaseLogCap = 8192;   // phase-log entries (one launch)
 
 int batch_check(const tdgl_config *c)
 {
@@ -30,7 +31,7 @@ int batch_check(const tdgl_config *c)
 
 struct BLayout {
     std::vector<size_t> inst;   // offset of each instance's workspace
-    size_t table, act, bst, sweeps, bar, save, total;
+    size_t table, act, bst, sweeps, bar, plog, save, total;
     std::vector<size_t> save_psi, save_mu, save_ctl;
 };
 
@@ -49,6 +50,7 @@ BLayout blayout(const tdgl_config *cfgs, int n)
     L.bst = take(sizeof(int) * (size_t)n);
     L.sweeps = take(sizeof(long long) * (size_t)n);
     L.bar = take(2 * sizeof(unsigned int));
+    L.plog = take(2 * sizeof(unsigned long long) * kPhaseLogCap);
     L.save = off;
     for (int i = 0; i < n; ++i) {
         const size_t N = (size_t)cfgs[i].nx * cfgs[i].ny * cfgs[i].nz;
@@ -85,6 +87,7 @@ struct tdgl_batch {
     cudaGraphExec_t gexec;
     int graph_built;            // gexec matches the current table and launch shape
     int graph_ok;               // capture worked (0: plain launches)
+    int log_on;                 // phase log of every launch
     int64_t steps;
 };
 
@@ -123,7 +126,7 @@ void fill_instance(tdgl_batch *b, int i, int kz)
     while ((size_t)H.tiles > h->nblockred && H.kz < c.nz) batch_tiling(I, H.kz * 2);
     const long long N = h->g.N;
     const long long half = (long long)(h->nblockred / 2);
-    long long chunk = std::max<long long>(1024, (N + half - 1) / half);
+    long long chunk = std::max<long long>(32768, (N + half - 1) / half);
     chunk = (chunk + 255) / 256 * 256;
     H.red_chunk = (int)chunk;
     H.red_items = (int)((N + chunk - 1) / chunk);
@@ -155,6 +158,8 @@ void fill_params(tdgl_batch *b)
     P.bar = at<unsigned int>(b->ws, b->L.bar);
     P.extra = (unsigned int)std::max(0, b->tune.test_extra_arrivals);
     P.timeout_ns = (unsigned long long)std::max(1, b->tune.timeout_ms) * 1000000ull;
+    P.plog = b->log_on ? at<unsigned long long>(b->ws, b->L.plog) : nullptr;
+    P.plog_cap = b->log_on ? kPhaseLogCap : 0;
     int phases = 1;
     for (int i = 0; i < b->n; ++i) {
         const BatchHead &H = b->inst[i].h;
@@ -440,6 +445,40 @@ int tdgl_batch_set_tuning(tdgl_batch *b, const tdgl_batch_tuning *in)
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TDGL_ERR_CUDA;
     b->tune = *in;
     return apply_tuning(b);
+}
+
+int tdgl_batch_phase_log(tdgl_batch *b, int32_t on)
+{
+    if (!b) return TDGL_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TDGL_ERR_CUDA;
+    b->log_on = on ? 1 : 0;
+    return apply_tuning(b);
+}
+
+int tdgl_batch_phase_read(tdgl_batch *b, double *ms_by_op, int32_t *phases_by_op, int32_t nops)
+{
+    if (!b || !ms_by_op || !phases_by_op || nops < TDGL_BATCH_OPS) return TDGL_ERR_INVALID_ARG;
+    if (!b->log_on) return TDGL_ERR_INVALID_ARG;
+    std::vector<unsigned long long> log(2 * (size_t)kPhaseLogCap);
+    if (cudaMemcpyAsync(log.data(), at<char>(b->ws, b->L.plog), sizeof(unsigned long long) * log.size(),
+                        cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    for (int q = 0; q < nops; ++q) {
+        ms_by_op[q] = 0.0;
+        phases_by_op[q] = 0;
+    }
+    unsigned long long t_prev = log[0];
+    for (int i = 1; i < kPhaseLogCap; ++i) {
+        const unsigned long long tag = log[2 * i + 1];
+        if (tag == 0xffffull) break;
+        const int op = (int)(tag >> 8);
+        if (op < 0 || op >= TDGL_BATCH_OPS) break;
+        ms_by_op[op] += (double)(log[2 * i] - t_prev) * 1e-6;
+        phases_by_op[op] += 1;
+        t_prev = log[2 * i];
+    }
+    return TDGL_OK;
 }
 
 int tdgl_batch_autotune(tdgl_batch *b, int32_t trial_steps, tdgl_batch_tune_report *report)

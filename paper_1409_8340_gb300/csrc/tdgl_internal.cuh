@@ -143,9 +143,11 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return r;
 }
 
-// Load through L2 only (CG) or through the read-only path.  A persistent kernel
-// reads data that other blocks wrote earlier in the same launch, so it must not
-// use the non-coherent path.
+// Load through L2 only (CG) or a plain dereference that the compiler may turn
+// into a read-only-path load.  A persistent kernel reads data that other blocks
+// wrote earlier in the same launch, so it uses the L2 form (L2 is the point of
+// coherence; the non-coherent read-only path has no such guarantee).  Measured
+// on the batched step, L1-cached loads were not faster.
 template <bool CG, class T>
 __device__ __forceinline__ T ldx(const T *p)
 {
@@ -328,6 +330,8 @@ struct BatchParams {
     unsigned int *bar;         // [0] barrier arrivals (zeroed before each launch), [1] error flag
     unsigned int extra;        // arrivals a barrier waits for beyond the grid (0; >0 only to test the timeout)
     unsigned long long timeout_ns;
+    unsigned long long *plog;  // optional phase log: [2 i] globaltimer at the end of phase i, [2 i + 1] its op
+    int plog_cap;              // entries in plog (0: no log)
 };
 size_t batch_smem_bytes(const BatchInst &I);
 // Occupancy of the kernel variant built for bps (2 or 3) resident blocks per SM.

@@ -326,6 +326,18 @@ class Batch:
                 setattr(t, k, int(v))
         check(self._L.tdgl_batch_set_tuning(self._b, ctypes.byref(t)), "tdgl_batch_set_tuning")
 
+    def phase_log(self, on: bool = True):
+        """Record the phase timings of every launch (tdgl_batch_phase_log)."""
+        check(self._L.tdgl_batch_phase_log(self._b, int(bool(on))), "tdgl_batch_phase_log")
+
+    def phase_profile(self) -> dict:
+        """Per phase kind of the last launch: (ms, number of phases)."""
+        n = len(_lib.BATCH_OPS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int32 * n)()
+        check(self._L.tdgl_batch_phase_read(self._b, ms, cnt, n), "tdgl_batch_phase_read")
+        return {name: (ms[q], cnt[q]) for q, name in enumerate(_lib.BATCH_OPS)}
+
     def autotune(self, trial_steps: int = 3) -> dict:
         r = _lib.BatchTuneReport()
         check(self._L.tdgl_batch_autotune(self._b, int(trial_steps), ctypes.byref(r)), "tdgl_batch_autotune")

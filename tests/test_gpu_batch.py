@@ -221,3 +221,25 @@ def test_ensemble_64_full_size_sampled():
         x, y = gpu_state(b.instances[i]), gpu_state(s)
         assert np.max(np.abs(x[0] - y[0])) <= 1e-6, i
         assert np.max(np.abs(x[1] - y[1])) <= 1e-6 * max(1.0, np.max(np.abs(y[1]))), i
+
+
+def test_phase_log_accounts_for_the_launch():
+    import torch
+    ps = batch_cases()[:4]
+    alphas, psi0s, mu0s = inputs(ps, 800)
+    b = make_batch(ps, alphas, psi0s, mu0s)
+    b.set_tuning(graph_steps=0)
+    b.phase_log(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = b.phase_profile()
+    total = sum(v[0] for v in prof.values())
+    assert 0.3 * e0.elapsed_time(e1) <= total <= 1.05 * e0.elapsed_time(e1) + 0.05
+    obs = b.observables()
+    assert prof["init"][1] == 1
+    assert prof["sweep"][1] == max(o["last_sweeps"] for o in obs) - 1
+    assert prof["smooth"][1] > 0 and prof["shift"][1] == 1
