@@ -76,6 +76,9 @@ def lib():
         gp = P(_Grid)
         L.or_landau_link_phases.argtypes = [gp, dp]
         L.or_init.argtypes = [gp, dp, d, dp, dp, dp, dp, dp]
+        u32p = P(ctypes.c_uint32)
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_noise.argtypes = [gp, d, ctypes.c_uint64, ctypes.c_int64, dp]
         L.or_sweep.argtypes = [gp, dp, d, dp, dp, dp, dp]
         L.or_sweep.restype = d
         L.or_residual.argtypes = [gp, dp, d, dp, dp, dp, dp]
@@ -113,6 +116,8 @@ class Grid:
     By: float = 0.0
     Bz: float = 0.0
     Jext: float = 0.0
+    noise_T: float = 0.0          # grid-independent noise parameter T_zeta (Sec. 3.1.2); 0: no noise
+    noise_seed: int = 0
 
     @property
     def shape(self):
@@ -313,12 +318,39 @@ class NotConverged(RuntimeError):
     pass
 
 
+def philox4x32_10(counter, key):
+    """Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): four 32-bit outputs."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in counter])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    out = (ctypes.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, out)
+    return [int(v) for v in out]
+
+
+def noise_amplitude(G: Grid) -> float:
+    """h_t zeta_max with zeta_max = (T_zeta / (h_t hx hy hz))^(1/2) (Sec. 3.1.2); a film
+    (Nz = 1) drops hz."""
+    if G.noise_T <= 0:
+        return 0.0
+    vol = G.hx * G.hy * (G.hz if G.nz >= 2 else 1.0)
+    return G.ht * math.sqrt(G.noise_T / (G.ht * vol))
+
+
+def add_noise(G: Grid, b, step: int):
+    """b += h_t zeta(step) in place (the 2 zeta_m term of Eq. b times h_t/2)."""
+    amp = noise_amplitude(G)
+    if amp > 0:
+        lib().or_noise(ctypes.byref(G.c()), amp, int(G.noise_seed) & 0xFFFFFFFFFFFFFFFF, int(step), _dp(b))
+    return b
+
+
 def solve_psi(G: Grid, psi_prev, mu, alpha, K=0.0, theta=None, eps=1e-6, max_iter=200,
-              check_every=1, fixed_sweeps=0):
+              check_every=1, fixed_sweeps=0, step=0):
     """Linear solve M psi = b by Jacobi (Eq. final) from psi^(0) = psi^-.
 
     Returns (psi, sweeps, r2 of the last tested residual, list of per-sweep r2)."""
     b, D = init(G, psi_prev, mu, alpha, K, theta)
+    add_noise(G, b, step)
     cur = _cplx(psi_prev)
     hist = []
     for l in range(max_iter):
@@ -358,7 +390,8 @@ def rewind(K: float, hx: float) -> float:
 def step(G: Grid, st: State, alpha, theta=None, eps=1e-6, max_iter=200, check_every=1,
          fixed_sweeps=0, freeze_mu_K=False) -> StepStats:
     """One time step in the paper's order: psi, then K (E_x), then mu (Sec. 3)."""
-    psi, nsw, r2, _ = solve_psi(G, st.psi, st.mu, alpha, st.K, theta, eps, max_iter, check_every, fixed_sweeps)
+    psi, nsw, r2, _ = solve_psi(G, st.psi, st.mu, alpha, st.K, theta, eps, max_iter, check_every, fixed_sweeps,
+                                st.step)
     Kold = st.K
     Knew = Kold
     Jav = 0.0

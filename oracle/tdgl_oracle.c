@@ -197,6 +197,58 @@ void or_init(const or_grid *G, const double *theta, double K, const double *psi_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Thermal noise (Sec. 3.1.2): b_m gains (h_t/2) 2 zeta_m = h_t zeta_m with   */
+/* zeta = zeta_max (v1 + i v2), v1 and v2 independent and uniform on [-1, 1), */
+/* fresh for every site m and time step n.  The random numbers come from the  */
+/* counter-based generator Philox4x32 with 10 rounds (Salmon, Moraes, Dror &  */
+/* Shaw, SC'11), counter (m, n) and key = the seed: each 32-bit output x      */
+/* gives v = (x >> 8) 2^-23 - 1, exact in single precision.                   */
+/* ------------------------------------------------------------------------ */
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0], n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    for (int q = 0; q < 4; ++q) out[q] = c[q];
+}
+
+void or_noise(const or_grid *G, double amp, uint64_t seed, int64_t step, double *b)
+{
+    const int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < N; ++m) {
+        const uint32_t ctr[4] = {(uint32_t)m, (uint32_t)((uint64_t)m >> 32), (uint32_t)step,
+                                 (uint32_t)((uint64_t)step >> 32)};
+        uint32_t x[4];
+        or_philox4x32_10(ctr, key, x);
+        const double v1 = ldexp((double)(x[0] >> 8), -23) - 1.0;
+        const double v2 = ldexp((double)(x[1] >> 8), -23) - 1.0;
+        b[2 * m] += amp * v1;
+        b[2 * m + 1] += amp * v2;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One Jacobi sweep (Eq. final) and the residual of its input iterate        */
 /* (Eq. convergence): r^(l) = b - M psi^(l).                                 */
 /* Off-diagonal entries of M are -(ht/2) times the neighbour coefficients.   */
