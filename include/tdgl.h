@@ -83,6 +83,14 @@ extern "C" {
  *                   the results are those of one sweep at a time (to FP32
  *                   rounding).  On GB300 the two-sweep pass is slower than two
  *                   single sweeps at every size measured, so 1 is the default.
+ *   noise_T         thermal noise of Eq. b (Sec. 3.1.2): the grid-independent
+ *                   parameter T_zeta = h_t hx hy hz zeta_max^2 (hz dropped on a
+ *                   film); 0 = no noise.  Each step adds h_t zeta_m to b_m with
+ *                   zeta = zeta_max (v1 + i v2), v1, v2 uniform on [-1, 1) drawn by
+ *                   Philox4x32-10 with counter (site m, step n) and key noise_seed;
+ *                   n counts the handle's steps since creation or the last
+ *                   tdgl_set_state / tdgl_upload_state.
+ *   noise_seed      key of the noise generator.
  *   d_alpha         device f32[N], eps(r) of Eq. epsilon (caller-owned, read-only
  *                   for the handle's lifetime).
  *   d_link_phase    device f32[3N] link phases theta_{a,m} of the link from m to
@@ -106,6 +114,8 @@ typedef struct tdgl_config {
     double poisson_tol;
     int32_t links_mode;
     int32_t sweeps_per_pass;
+    double noise_T;
+    uint64_t noise_seed;
     const float *d_alpha;
     const float *d_link_phase;
 } tdgl_config;

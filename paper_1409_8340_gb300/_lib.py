@@ -52,7 +52,7 @@ class Config(ctypes.Structure):
         ("poisson_max_cycles", ctypes.c_int32),
         ("poisson_tol", ctypes.c_double),
         ("links_mode", ctypes.c_int32),
-        ("sweeps_per_pass", ctypes.c_int32),
+        ("sweeps_per_pass", ctypes.c_int32), ("noise_T", ctypes.c_double), ("noise_seed", ctypes.c_uint64),
         ("d_alpha", ctypes.c_void_p),
         ("d_link_phase", ctypes.c_void_p),
     ]

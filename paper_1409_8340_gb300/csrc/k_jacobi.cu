@@ -13,6 +13,7 @@
 #include <float.h>
 #include <string.h>
 
+#include "philox.cuh"
 #include "sweep_tile.cuh"
 
 namespace tdgl {
@@ -121,6 +122,7 @@ __device__ __forceinline__ float2 ns_z(const DevGrid &g, int i, int k, long long
 template <bool GEN>
 __global__ void __launch_bounds__(kBX *kBY) init_sweep_kernel(SweepArgs a, int kz)
 {
+    const unsigned long long nstep = a.ctl->nstep;
     const DevGrid &g = a.g;
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
@@ -153,7 +155,12 @@ __global__ void __launch_bounds__(kBX *kBY) init_sweep_kernel(SweepArgs a, int k
             const float cr = al - g.beta * a2 - 2.f * g.S;
             const float ci = -g.u * mu;
             const float2 lin = cmk(cr * pc.x - ci * pc.y, cr * pc.y + ci * pc.x);
-            const float2 b = cadd(pc, cscale(g.ht2, cadd(lin, ns)));
+            float2 b = cadd(pc, cscale(g.ht2, cadd(lin, ns)));
+            if (a.noise_amp != 0.f) {
+                // thermal noise h_t zeta_m (Sec. 3.1.2)
+                const float2 v = noise_uv(a.noise_seed, m, nstep);
+                b = cmk(b.x + a.noise_amp * v.x, b.y + a.noise_amp * v.y);
+            }
             // first sweep: s = b - sum_{m'!=m} M psi = b + (ht/2) NS
             const float2 s = cadd(b, cscale(g.ht2, ns));
             const float2 r = csub(s, cmul(D, pc));

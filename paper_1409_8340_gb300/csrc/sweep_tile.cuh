@@ -4,6 +4,7 @@
 #pragma once
 #include <float.h>
 
+#include "philox.cuh"
 #include "tdgl_internal.cuh"
 
 namespace tdgl {
@@ -17,7 +18,10 @@ __device__ __forceinline__ void sweep_decide(const SweepArgs &a, float gf, bool 
 {
     DevCtl *c = a.ctl;
     int it = init ? 1 : c->iter + 1;
-    if (init) c->status = TDGL_OK;
+    if (init) {
+        c->status = TDGL_OK;
+        c->nstep += 1;   // the init blocks have all read the noise counter
+    }
     c->iter = it;
     c->r2 = (double)gf;
     c->result = a.dst_index;
@@ -117,6 +121,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
     const int k1 = min(k0 + kz, g.nz);
     const bool in = (x < g.nx) && (j < g.ny);
     const float2 Ux = ldx<CG>(&a.ctl->Ux);
+    const unsigned long long nstep = INIT ? ldx<CG>(&a.ctl->nstep) : 0ull;
     const float4 *__restrict__ src = reinterpret_cast<const float4 *>(a.src);
     const float2 *__restrict__ src2 = a.src;
     const float4 *__restrict__ bq = reinterpret_cast<const float4 *>(a.b);
@@ -315,6 +320,11 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                     const float ci = -g.u * mus[s2];
                     const float2 lin = cmk(cr * cs[s2].x - ci * cs[s2].y, cr * cs[s2].y + ci * cs[s2].x);
                     bo[s2] = cadd(cadd(cs[s2], cscale(g.ht2, lin)), nss[s2]);   // nss = (ht/2) NS
+                    if (a.noise_amp != 0.f) {
+                        // thermal noise h_t zeta_m (Sec. 3.1.2), counter (site, step)
+                        const float2 v = noise_uv(a.noise_seed, m + s2, nstep);
+                        bo[s2] = cmk(bo[s2].x + a.noise_amp * v.x, bo[s2].y + a.noise_amp * v.y);
+                    }
                 }
                 b0 = bo[0];
                 b1 = bo[1];

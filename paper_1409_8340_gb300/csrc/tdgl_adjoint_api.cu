@@ -80,7 +80,8 @@ extern "C" int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, voi
 {
     int rc = adj_validate(h, acfg);
     if (rc != TDGL_OK) return rc;
-    if (!d_grad_alpha || h->batch_owned) return TDGL_ERR_INVALID_ARG;
+    // the reverse pass assumes a deterministic forward without noise
+    if (!d_grad_alpha || h->batch_owned || h->noise_amp != 0.f) return TDGL_ERR_INVALID_ARG;
     const tdgl_adjoint_config &A = *acfg;
     const AdjLayout L = adj_layout(h, acfg);
     if (!d_ws || ((uintptr_t)d_ws & 255u) || ws_bytes < L.total) return TDGL_ERR_WORKSPACE;

@@ -44,6 +44,7 @@ int validate(const tdgl_config *c)
     if (!(c->u > 0) || !(c->beta >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->max_iter < 1 || c->check_every < 1 || c->fixed_sweeps < 0) return TDGL_ERR_INVALID_ARG;
     if (c->sweeps_per_pass < 0 || c->sweeps_per_pass > 2) return TDGL_ERR_INVALID_ARG;
+    if (!(c->noise_T >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->fixed_sweeps == 0 && !(c->eps > 0)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_cycles < 1 || c->poisson_max_cycles < c->poisson_cycles) return TDGL_ERR_INVALID_ARG;
     if (!c->d_alpha) return TDGL_ERR_INVALID_ARG;
@@ -190,6 +191,8 @@ SweepArgs sweep_args(tdgl_handle *h)
     a.fixed_sweeps = h->cfg.fixed_sweeps;
     a.max_iter = h->cfg.max_iter;
     a.eps = h->cfg.eps;
+    a.noise_amp = h->noise_amp;
+    a.noise_seed = h->cfg.noise_seed;
     return a;
 }
 
@@ -284,6 +287,11 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     h->links = g.L ? at<float2>(ws, L.links) : nullptr;
     h->nblockred = L.nblockred;
     h->batch_owned = 0;
+    {
+        // h_t zeta_max, zeta_max = (T_zeta / (h_t hx hy hz))^(1/2) (Sec. 3.1.2); a film drops hz
+        const double vol = c.hx * c.hy * (c.nz >= 2 ? c.hz : 1.0);
+        h->noise_amp = c.noise_T > 0 ? (float)(c.ht * sqrt(c.noise_T / (c.ht * vol))) : 0.f;
+    }
     h->last_sweeps = 8;
     h->last_cycles = c.poisson_cycles;
     h->step = 0;

@@ -113,6 +113,8 @@ void fill_instance(tdgl_batch *b, int i, int kz)
     a.max_iter = c.max_iter;
     a.eps = c.eps;
     a.rel_eps = 0;
+    a.noise_amp = h->noise_amp;
+    a.noise_seed = c.noise_seed;
     a.f = h->f;
     a.inj = h->pa.inject ? (float)(2.0 * c.Jext / c.hx) : 0.f;
     a.wsum = h->wsum;

@@ -51,6 +51,8 @@ struct DevCtl {
     unsigned int ticket;       // last-block ticket (reset by the last block)
     int redo;                  // 1: the result is the first sweep of the last two-sweep pass (recompute it)
     int pad[2];
+    unsigned long long nstep;  // time steps initialised since creation or the last state load (noise counter)
+    unsigned long long pad2;
 };
 
 // ----------------------------------------------------------------------------
@@ -194,6 +196,8 @@ struct SweepArgs {
     float *f;                  // Poisson right-hand side (right-hand-side mode)
     float inj;                 // 2 J / hx at open x faces (right-hand-side mode)
     double wsum;               // sum of trapezoid weights (right-hand-side mode)
+    float noise_amp;           // h_t zeta_max (init mode; 0: no noise)
+    unsigned long long noise_seed;
 };
 
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
@@ -357,6 +361,7 @@ struct tdgl_handle {
     tdgl::PoissonArgs pa;
     size_t nblockred;          // capacity of blockred (doubles)
     int batch_owned;           // 1: stepped only through a batch
+    float noise_amp;           // h_t zeta_max, 0 without noise
     int last_sweeps;
     int last_cycles;
     int64_t step;

@@ -44,6 +44,8 @@ class Params:
     poisson_tol: float = 0.0
     general_links: bool = False
     sweeps_per_pass: int = 1       # 2: temporal blocking, two Jacobi sweeps per pass over memory
+    noise_T: float = 0.0           # thermal noise parameter T_zeta (Sec. 3.1.2); 0: none
+    noise_seed: int = 0
 
     @property
     def shape(self):
@@ -80,6 +82,8 @@ class Params:
         c.poisson_tol = self.poisson_tol
         c.links_mode = _lib.LINKS_GENERAL if self.general_links else _lib.LINKS_LANDAU
         c.sweeps_per_pass = int(self.sweeps_per_pass)
+        c.noise_T = float(self.noise_T)
+        c.noise_seed = int(self.noise_seed) & 0xFFFFFFFFFFFFFFFF
         c.d_alpha = d_alpha
         c.d_link_phase = d_link_phase or None
         return c
