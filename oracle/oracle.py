@@ -76,6 +76,7 @@ def lib():
         gp = P(_Grid)
         L.or_landau_link_phases.argtypes = [gp, dp]
         L.or_init.argtypes = [gp, dp, d, dp, dp, dp, dp, dp]
+        L.or_xz_link_phases.argtypes = [gp, d, dp]
         u32p = P(ctypes.c_uint32)
         L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.or_noise.argtypes = [gp, d, ctypes.c_uint64, ctypes.c_int64, dp]
@@ -168,6 +169,13 @@ def threads() -> int:
 def landau_link_phases(G: Grid) -> np.ndarray:
     th = np.zeros((3,) + G.shape, dtype=np.float64)
     lib().or_landau_link_phases(ctypes.byref(G.c()), _dp(th))
+    return th
+
+
+def xz_link_phases(G: Grid, Bx: float) -> np.ndarray:
+    """Link phases of the Landau gauge of Eq. A_xz (field (Bx, 0, Bz)), quasi-periodic in y."""
+    th = np.zeros((3,) + G.shape, dtype=np.float64)
+    lib().or_xz_link_phases(ctypes.byref(G.c()), float(Bx), _dp(th))
     return th
 
 

@@ -170,6 +170,33 @@ void or_landau_link_phases(const or_grid *G, double *theta_out)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Link phases of the other Landau gauge, field in the xz plane (Eq. B_xz,  */
+/* Eq. A_xz: A = ybar [-Bz, 0, Bx], ybar = j hy - Ly/2), for the explicit-    */
+/* link mode (K is added to the x links by link()):                          */
+/*   U_x(j) = exp(i hx Bz ybar_j),  U_y = 1,  U_z(j) = exp(-i hz Bx ybar_j);  */
+/* on a periodic y axis the wrap link from j = Ny-1 to j = 0 carries          */
+/* conj(P_{i,k}), P_{i,k} = exp(i(i hx Ly Bz - k hz Ly Bx)) (Sec. 3.3.1,      */
+/* xz-field paragraph: psi_{i,-1,k} = P_{i,k} psi_{i,Ny-1,k}).                */
+/* ------------------------------------------------------------------------ */
+void or_xz_link_phases(const or_grid *G, double Bx, double *theta_out)
+{
+    int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+    double Ly = box_length(G, 1);
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                double ybar = j * G->h[1] - 0.5 * Ly;
+                double ty = 0.0;
+                if (G->bc[1] == OR_PERIODIC && j == G->n[1] - 1)
+                    ty = -(i * G->h[0] * Ly * G->Bz - k * G->h[2] * Ly * Bx);
+                theta_out[m] = G->h[0] * G->Bz * ybar;
+                theta_out[N + m] = ty;
+                theta_out[2 * N + m] = -G->h[2] * Bx * ybar;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Init: diagonal M_mm and right-hand side b_m (Sec. 3.1, matrix M, Eq. b),  */
 /* with psi_est = psi^- and no noise.                                       */
 /*   M_mm = 1 + (ht/2)[beta|psi^-|^2 + 2S + i u mu - alpha]                  */
