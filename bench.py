@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=30)
     ap.add_argument("--batch-relax", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "batched", "adjoint"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "xz"],
                     help="run one mode alone and print its dictionary (profiling captures)")
     # profiling captures only (a number printed with these changed is not a bench value)
     ap.add_argument("--nz", type=int, default=256, help="z planes of the grid (profiling captures: a smaller case)")
@@ -303,6 +303,58 @@ def adjoint_mode(dev, n_steps: int = 400, every: int = 20, relax: int = 50):
             "reverse_step_vs_forward_step": (st["ms_reverse"] / n_steps) / (1e3 * fwd_s / n_steps)}
 
 
+def xz_mode(dev, steps: int = 20, relax: int = 20, quanta_x: int = 600):
+    """The mesoscopic workload with the field tilted in the xz plane, B = (Bx, 0, 0.2) with
+    Bx Ly Lz = 2 pi * 600 (about 30 degrees from z), in the Landau gauge of Eq. A_xz:
+    the link phases vary along y only, so the sweep takes them from j-indexed tables and
+    moves the same 32 B/site as in the yz gauge."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_1409_8340_gb300 import inputs
+    from paper_1409_8340_gb300.solver import Solver, pattern
+    w = workload(0.025)
+    p = w.params
+    p.xz_gauge = True
+    p.Bx = 2 * math.pi * quanta_x / (p.length(1) * p.length(2))
+    alpha, _, _ = pattern(p, w.candidates, w.target_sites, w.alpha_in, w.alpha_out, device=dev)
+    s = Solver(p, alpha)
+    s.set_state(torch.as_tensor(inputs.random_psi(p.nx, p.ny, p.nz, w.seed).astype(np.complex64)))
+    s.step(relax)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    s.profile_enable(True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    s.profile_enable(False)
+    obs = s.observables()
+    n_plain = prof["sweeps"] - prof["steps"]
+    sweep_ms = prof["ms_sweeps"] / max(1, n_plain)
+    bpl = BYTES_PER_SITE_ITER * p.N
+    peak, peak_kind = measured_peaks()
+    del s
+    torch.cuda.empty_cache()
+    return {"workload": f"mesoscopic_512x512x256 in the xz gauge: B = ({p.Bx:.5f}, 0, {p.Bz}), J 0.025",
+            "value": prof["sweeps"] * p.N / (ms * 1e-3) / 1e9, "unit": METRIC, "steps": steps,
+            "ms_per_step": ms / steps, "sweeps_per_step": prof["sweeps"] / max(1, prof["steps"]),
+            "phase_ms_per_step": {"init_sweep": prof["ms_init"] / steps, "sweeps": prof["ms_sweeps"] / steps,
+                                  "K": prof["ms_K"] / steps, "poisson": prof["ms_poisson"] / steps},
+            "sweep_roofline": {"kernel": "sweep2_kernel<0, XZ>", "bound": "hbm", "bytes_per_launch": bpl,
+                               "avg_launch_ms": sweep_ms, "achieved": bpl / (sweep_ms * 1e-3) / 1e9,
+                               "peak": peak, "unit": "GB/s", "frac": bpl / (sweep_ms * 1e-3) / 1e9 / peak,
+                               "peak_source": peak_kind},
+            "observables": {"Ex": obs["Ex"], "psi2_mean": obs["psi2_mean"],
+                            "vortex_unsigned_per_layer": obs["vortex_unsigned"]}}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -423,6 +475,7 @@ def run_native(args, rank, world, local_rank):
         modes["batched"] = batched_mode(dev, args.batch_steps, args.batch_relax, autotune=not args.no_autotune)
         modes["batched"]["vs_plain_step"] = modes["batched"]["value"] / value
         modes["adjoint"] = adjoint_mode(dev)
+        modes["xz_gauge"] = xz_mode(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,6 +535,8 @@ def main():
         torch.cuda.set_device(dev)
         if args.only == "batched":
             out = batched_mode(dev, args.batch_steps, args.batch_relax, autotune=not args.no_autotune)
+        elif args.only == "xz":
+            out = xz_mode(dev)
         else:
             out = adjoint_mode(dev)
         print(json.dumps({"mode": args.only, **out}), flush=True)

@@ -50,6 +50,7 @@ extern "C" {
 
 #define TDGL_LINKS_LANDAU 0   /* yz-plane field, Landau gauge A = xbar [0, Bz, -By] (Eq. A_yz) */
 #define TDGL_LINKS_GENERAL 1  /* explicit per-link phases (gauge tests)                         */
+#define TDGL_LINKS_XZ 2       /* xz-plane field, Landau gauge A = ybar [-Bz, 0, Bx] (Eq. A_xz)   */
 
 /*
  * Problem description.
@@ -57,13 +58,16 @@ extern "C" {
  *   bc[3]           TDGL_PERIODIC or TDGL_OPEN per axis (Sec. 3.3).  Periodic x
  *                   with a field uses the quasi-periodic wrap phase of Sec. 3.3.1;
  *                   periodic x and y then require Bz Lx Ly = 2 pi n_z, periodic x
- *                   and z require By Lx Lz = 2 pi n_y (flux quantisation).
+ *                   and z require By Lx Lz = 2 pi n_y (flux quantisation).  In the
+ *                   xz gauge the wrap is along y instead: periodic y and x require
+ *                   Bz Lx Ly = 2 pi n_z, periodic y and z require Bx Ly Lz = 2 pi n_x.
  *   hx, hy, hz      grid spacings in units of xi_0 (L = N h periodic, (N-1) h open).
  *   g               anisotropy: z derivatives carry 1/g^2 (Sec. 2.1).
  *   u, beta         u of Eq. GL_dimensionless (absorbed into ht as in the
  *                   footnote of Eq. GL_numCN) and the |psi|^2 psi coefficient.
  *   ht              time step h_t.
- *   By, Bz          field in the yz plane, units of H_c2(0) (Eq. B_yz).
+ *   By, Bz          field in the yz plane, units of H_c2(0) (Eq. B_yz); in the xz
+ *                   gauge By must be 0.
  *   Jext            applied current along x.  Periodic x: enters through the K
  *                   ODE (Eq. K_ODE).  Open x: injected as normal current through
  *                   the x faces via the Neumann condition d(mu)/dx = -Jext.
@@ -76,7 +80,10 @@ extern "C" {
  *   poisson_cycles  multigrid V-cycles per step (>= 1).
  *   poisson_tol     > 0: keep cycling (up to poisson_max_cycles) until
  *                   max|F - Lap mu| <= poisson_tol * max|F|.
- *   links_mode      TDGL_LINKS_LANDAU or TDGL_LINKS_GENERAL.
+ *   links_mode      TDGL_LINKS_LANDAU (field (0, By, Bz)), TDGL_LINKS_XZ (field
+ *                   (Bx, 0, Bz), links built on the device from FP64 phases and kept
+ *                   as a 3N table; tdgl_batch_*, the adjoint and tdgl_sweep_noalloc
+ *                   take Landau links only) or TDGL_LINKS_GENERAL.
  *   sweeps_per_pass 0 or 1: one Jacobi sweep per pass over memory.  2: where the
  *                   grid allows (Landau links, nx even), two sweeps per pass
  *                   (temporal blocking) with the per-sweep test kept exactly, so
@@ -91,6 +98,7 @@ extern "C" {
  *                   n counts the handle's steps since creation or the last
  *                   tdgl_set_state / tdgl_upload_state.
  *   noise_seed      key of the noise generator.
+ *   Bx              field along x (Eq. B_xz), TDGL_LINKS_XZ only (0 otherwise).
  *   d_alpha         device f32[N], eps(r) of Eq. epsilon (caller-owned, read-only
  *                   for the handle's lifetime).
  *   d_link_phase    device f32[3N] link phases theta_{a,m} of the link from m to
@@ -116,6 +124,7 @@ typedef struct tdgl_config {
     int32_t sweeps_per_pass;
     double noise_T;
     uint64_t noise_seed;
+    double Bx;
     const float *d_alpha;
     const float *d_link_phase;
 } tdgl_config;
@@ -168,6 +177,13 @@ typedef struct tdgl_profile {
 } tdgl_profile;
 
 const char *tdgl_error_string(int code);
+
+/* sizeof of the ABI structs, so that a binding can check its own layout:
+ * which = 0 tdgl_config, 1 tdgl_obs, 2 tdgl_state_ptrs, 3 tdgl_profile,
+ * 4 tdgl_adjoint_config, 5 tdgl_adjoint_stats, 6 tdgl_batch_tuning,
+ * 7 tdgl_batch_stats, 8 tdgl_batch_tune_report; 0 for any other value.
+ * Host only, needs no device. */
+size_t tdgl_abi_struct_size(int32_t which);
 
 /* Bytes of device workspace tdgl_create() needs for cfg (0 if cfg is invalid). */
 size_t tdgl_workspace_bytes(const tdgl_config *cfg);

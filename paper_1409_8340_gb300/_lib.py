@@ -16,6 +16,7 @@ PERIODIC = 0
 OPEN = 1
 LINKS_LANDAU = 0
 LINKS_GENERAL = 1
+LINKS_XZ = 2
 
 TDGL_OK = 0
 TDGL_ERR_INVALID_ARG = -1
@@ -53,6 +54,7 @@ class Config(ctypes.Structure):
         ("poisson_tol", ctypes.c_double),
         ("links_mode", ctypes.c_int32),
         ("sweeps_per_pass", ctypes.c_int32), ("noise_T", ctypes.c_double), ("noise_seed", ctypes.c_uint64),
+        ("Bx", ctypes.c_double),
         ("d_alpha", ctypes.c_void_p),
         ("d_link_phase", ctypes.c_void_p),
     ]
@@ -127,10 +129,15 @@ class BatchTuneReport(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+# order of tdgl_abi_struct_size's argument
+ABI_STRUCTS = (Config, Obs, StatePtrs, Profile, AdjointConfig, AdjointStats, BatchTuning, BatchStats,
+               BatchTuneReport)
+
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
 _SIGS = {
     "tdgl_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tdgl_abi_struct_size": (ctypes.c_size_t, [ctypes.c_int32]),
     "tdgl_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config)]),
     "tdgl_create": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "tdgl_destroy": (None, [_P]),
@@ -184,6 +191,10 @@ def load(path: str = LIB_PATH):
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        for which, cls in enumerate(ABI_STRUCTS):
+            if L.tdgl_abi_struct_size(which) != ctypes.sizeof(cls):
+                raise OSError(f"{cls.__name__}: binding layout ({ctypes.sizeof(cls)} bytes) differs from "
+                              f"the library's ({L.tdgl_abi_struct_size(which)} bytes)")
         _lib = L
     return _lib
 

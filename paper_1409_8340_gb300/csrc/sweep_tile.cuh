@@ -1,4 +1,4 @@
-// One tile of the Landau-gauge Jacobi sweep and the per-block finishing
+// One tile of the Landau-gauge Jacobi sweep (yz- or xz-plane field) and the per-block finishing
 // reductions, shared by the per-instance kernels and the batched persistent
 // kernel (arXiv:1409.8340, Sec. 3.1: matrix M, Eq. b, Eq. final, Eq. convergence).
 #pragma once
@@ -105,7 +105,9 @@ __device__ __forceinline__ bool finish_rhs_sum_at(DevCtl *ctl, double *blockred,
 // One tile (block coordinates bx, by, bz of the sweep2 grid) of a sweep; returns the
 // thread's max |r|^2 in rmax (sweep modes) or its sum of w f in facc (right-hand side).
 // CG: loads of data written earlier in the same launch go through L2 only.
-template <int MODE, bool CG = false>
+// XZ: links of the xz-plane gauge (Eq. A_xz) from the j-indexed tables Xj, Zj and, on a
+// periodic y axis, the wrap link Wx[i] Wz[k] from row ny-1 to row 0 (x wrap plain U_x).
+template <int MODE, bool CG = false, bool XZ = false>
 __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, int by, int bz, float &rmax,
                                             float &facc)
 {
@@ -154,18 +156,26 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                             : (ADJ ? (ylo ? 0.f : (j - 1 == 0 ? 2.f : 1.f)) : (yhi ? 2.f : (ylo ? 0.f : 1.f)));
     const bool yedge = (wy_f != 1.f) || (wy_b != 1.f);
     float2 yf0 = cmk(0.f, 0.f), yf1 = yf0, zf0 = yf0, zf1 = yf0;
+    const bool ywrap = XZ && yper && (ylo || yhi);   // a row next to the xz gauge's y wrap
+    float4 wxq = make_float4(1.f, 0.f, 1.f, 0.f);
     if (in) {
-        const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
-        const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
         const float sy = g.ht2 * g.cy, szc = g.ht2 * g.cz;
-        yf0 = cscale(sy, lo2(uy));
-        yf1 = cscale(sy, hi2(uy));
-        zf0 = cscale(szc, lo2(uz));
-        zf1 = cscale(szc, hi2(uz));
+        if (XZ) {
+            yf0 = yf1 = cmk(sy, 0.f);
+            zf0 = zf1 = cscale(szc, g.Zj[jc]);
+            if (ywrap) wxq = reinterpret_cast<const float4 *>(g.Wx)[x >> 1];
+        } else {
+            const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
+            const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
+            yf0 = cscale(sy, lo2(uy));
+            yf1 = cscale(sy, hi2(uy));
+            zf0 = cscale(szc, lo2(uz));
+            zf1 = cscale(szc, hi2(uz));
+        }
     }
     // x: site x has forward neighbour c1 and backward xl; site x+1 has forward xr and backward c0.
     // Backward coefficients are the conjugates of the forward ones.
-    const float2 xf = cscale(g.ht2 * g.cx, Ux);
+    const float2 xf = cscale(g.ht2 * g.cx, XZ ? cmul(Ux, g.Xj[jc]) : Ux);
     const float inv_ht2 = 1.0f / g.ht2;
 
     auto knext = [&](int k) { return (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1; };
@@ -226,13 +236,16 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
         if (in) {
             const float2 c0 = lo2(pc), c1 = hi2(pc);
             // x neighbours with the boundary rules: open faces double the inner
-            // neighbour; the periodic wrap link (i = nx-1 -> 0) carries conj(P_jk).
+            // neighbour; the periodic wrap link (i = nx-1 -> 0) carries conj(P_jk)
+            // in the yz gauge and is the plain x link in the xz gauge.
             float2 xl0 = xl, xr1 = xr, c1x = c1, c0x = c0;
             if (xlo || xhi) {
                 if (xper) {
-                    const float2 P = cmul(g.Py[jc], g.Pz[k]);
-                    if (xlo) xl0 = cmul(P, xl);      // conj(Ux conj(P)) xl = conj(Ux) (P xl)
-                    if (xhi) xr1 = cmulc(P, xr);     // Ux conj(P) xr = Ux (conj(P) xr)
+                    if (!XZ) {
+                        const float2 P = cmul(g.Py[jc], g.Pz[k]);
+                        if (xlo) xl0 = cmul(P, xl);      // conj(Ux conj(P)) xl = conj(Ux) (P xl)
+                        if (xhi) xr1 = cmulc(P, xr);     // Ux conj(P) xr = Ux (conj(P) xr)
+                    }
                 } else if (!ADJ) {
                     if (xlo) {
                         c1x = cscale(2.f, c1);
@@ -255,6 +268,19 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 }
             }
             float2 yf_0 = lo2(yf), yf_1 = hi2(yf), yb_0 = lo2(yb), yb_1 = hi2(yb);
+            if (ywrap) {
+                // wrap link W = Wx[i] Wz[k] from row ny-1 to row 0: forward W psi, backward conj(W) psi
+                const float2 wz = g.Wz[k];
+                const float2 W0 = cmul(lo2(wxq), wz), W1 = cmul(hi2(wxq), wz);
+                if (yhi) {
+                    yf_0 = cmul(W0, yf_0);
+                    yf_1 = cmul(W1, yf_1);
+                }
+                if (ylo) {
+                    yb_0 = cmulc(W0, yb_0);
+                    yb_1 = cmulc(W1, yb_1);
+                }
+            }
             if (yedge) {
                 yf_0 = cscale(wy_f, yf_0);
                 yf_1 = cscale(wy_f, yf_1);

@@ -48,22 +48,33 @@ int validate(const tdgl_config *c)
     if (c->fixed_sweeps == 0 && !(c->eps > 0)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_cycles < 1 || c->poisson_max_cycles < c->poisson_cycles) return TDGL_ERR_INVALID_ARG;
     if (!c->d_alpha) return TDGL_ERR_INVALID_ARG;
-    if (c->links_mode != TDGL_LINKS_LANDAU && c->links_mode != TDGL_LINKS_GENERAL) return TDGL_ERR_INVALID_ARG;
+    if (c->links_mode != TDGL_LINKS_LANDAU && c->links_mode != TDGL_LINKS_GENERAL && c->links_mode != TDGL_LINKS_XZ)
+        return TDGL_ERR_INVALID_ARG;
     if (c->links_mode == TDGL_LINKS_GENERAL && !c->d_link_phase) return TDGL_ERR_INVALID_ARG;
     if (c->nx > 1500) return TDGL_ERR_INVALID_ARG;   // x lines of the Poisson smoother live in shared memory
+    if (!(c->Bx == c->Bx) || !(c->By == c->By) || !(c->Bz == c->Bz)) return TDGL_ERR_INVALID_ARG;
+    // each gauge carries the field components of its plane only
+    if (c->links_mode == TDGL_LINKS_LANDAU && c->Bx != 0.0) return TDGL_ERR_INVALID_ARG;
+    if (c->links_mode == TDGL_LINKS_XZ && c->By != 0.0) return TDGL_ERR_INVALID_ARG;
+    const double Lx = box_len(c->nx, c->hx, c->bc[0]), Ly = box_len(c->ny, c->hy, c->bc[1]);
+    const double Lz = box_len(c->nz, c->hz, c->bc[2]);
+    const bool pz = c->bc[2] == TDGL_PERIODIC && c->nz >= 2;
+    long long n;
     if (c->links_mode == TDGL_LINKS_LANDAU && c->bc[0] == TDGL_PERIODIC) {
-        double Lx = box_len(c->nx, c->hx, c->bc[0]);
-        long long n;
-        if (c->bc[1] == TDGL_PERIODIC && !quantised(c->Bz, Lx, box_len(c->ny, c->hy, c->bc[1]), &n))
-            return TDGL_ERR_INVALID_ARG;
-        if (c->bc[2] == TDGL_PERIODIC && c->nz >= 2 && !quantised(c->By, Lx, box_len(c->nz, c->hz, c->bc[2]), &n))
-            return TDGL_ERR_INVALID_ARG;
+        // quasi-periodic x wrap (Sec. 3.3.1)
+        if (c->bc[1] == TDGL_PERIODIC && !quantised(c->Bz, Lx, Ly, &n)) return TDGL_ERR_INVALID_ARG;
+        if (pz && !quantised(c->By, Lx, Lz, &n)) return TDGL_ERR_INVALID_ARG;
+    }
+    if (c->links_mode == TDGL_LINKS_XZ && c->bc[1] == TDGL_PERIODIC) {
+        // quasi-periodic y wrap of the xz-plane gauge
+        if (c->bc[0] == TDGL_PERIODIC && !quantised(c->Bz, Lx, Ly, &n)) return TDGL_ERR_INVALID_ARG;
+        if (pz && !quantised(c->Bx, Ly, Lz, &n)) return TDGL_ERR_INVALID_ARG;
     }
     return TDGL_OK;
 }
 
 struct Layout {
-    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, Uy, Uz, Py, Pz, total;
+    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, xzt, Uy, Uz, Py, Pz, total;
     int nlevels;
     int ny[kMaxLevels], nz[kMaxLevels], fy[kMaxLevels], fz[kMaxLevels];
     size_t u[kMaxLevels], r[kMaxLevels], tri[kMaxLevels];
@@ -110,7 +121,8 @@ Layout layout(const tdgl_config *c)
     L.mu = take(4 * (size_t)N);
     L.f = take(4 * (size_t)N);
     L.t = take(4 * (size_t)N);
-    L.links = (c->links_mode == TDGL_LINKS_GENERAL) ? take(8 * 3 * (size_t)N) : 0;
+    L.links = (c->links_mode != TDGL_LINKS_LANDAU) ? take(8 * 3 * (size_t)N) : 0;
+    L.xzt = (c->links_mode == TDGL_LINKS_XZ) ? take(8 * (2 * (size_t)c->ny + c->nx + c->nz)) : 0;
     L.Uy = take(8 * (size_t)c->nx);
     L.Uz = take(8 * (size_t)c->nx);
     L.Py = take(8 * (size_t)c->ny);
@@ -162,6 +174,25 @@ __global__ void phases_to_links(const float *theta, float2 *L, long long n3)
         float s, c;
         sincosf(theta[q], &s, &c);
         L[q] = make_float2(c, s);
+    }
+}
+
+// Links of the xz-plane Landau gauge (A = ybar [-Bz, 0, Bx], ybar = j hy - Ly/2): the
+// x and z links depend on j only (tables X[j], Z[j]); on a periodic y axis the wrap link
+// from j = Ny-1 to j = 0 is Wx[i] Wz[k] = exp(-i(i hx Ly Bz - k hz Ly Bx)), the conjugate
+// of the quasi-periodic factor psi_{i,-1,k} = P_{i,k} psi_{i,Ny-1,k} (Sec. 3.3.1).
+// t = [X ny][Z ny][Wx nx][Wz nz], each entry rounded from FP64 once.
+__global__ void xz_links(const float2 *t, float2 *L, int nx, int ny, int nz, int wrap_y)
+{
+    const long long N = (long long)nx * ny * nz;
+    const float2 *X = t, *Z = t + ny, *Wx = t + 2 * ny, *Wz = Wx + nx;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(m % nx);
+        const long long jk = m / nx;
+        const int j = (int)(jk % ny), k = (int)(jk / ny);
+        L[m] = X[j];
+        L[N + m] = (wrap_y && j == ny - 1) ? cmul(Wx[i], Wz[k]) : make_float2(1.f, 0.f);
+        L[2 * N + m] = Z[j];
     }
 }
 
@@ -237,6 +268,22 @@ const char *tdgl_error_string(int code)
     }
 }
 
+size_t tdgl_abi_struct_size(int32_t which)
+{
+    switch (which) {
+    case 0: return sizeof(tdgl_config);
+    case 1: return sizeof(tdgl_obs);
+    case 2: return sizeof(tdgl_state_ptrs);
+    case 3: return sizeof(tdgl_profile);
+    case 4: return sizeof(tdgl_adjoint_config);
+    case 5: return sizeof(tdgl_adjoint_stats);
+    case 6: return sizeof(tdgl_batch_tuning);
+    case 7: return sizeof(tdgl_batch_stats);
+    case 8: return sizeof(tdgl_batch_tune_report);
+    default: return 0;
+    }
+}
+
 size_t tdgl_workspace_bytes(const tdgl_config *cfg)
 {
     if (validate(cfg) != TDGL_OK) return 0;
@@ -275,7 +322,16 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     g.Uz = at<float2>(ws, L.Uz);
     g.Py = at<float2>(ws, L.Py);
     g.Pz = at<float2>(ws, L.Pz);
-    g.L = (c.links_mode == TDGL_LINKS_GENERAL) ? at<float2>(ws, L.links) : nullptr;
+    g.L = (c.links_mode != TDGL_LINKS_LANDAU) ? at<float2>(ws, L.links) : nullptr;
+    if (c.links_mode == TDGL_LINKS_XZ) {
+        float2 *t = at<float2>(ws, L.xzt);   // [X ny][Z ny][Wx nx][Wz nz]
+        g.Xj = t;
+        g.Zj = t + c.ny;
+        g.Wx = t + 2 * (size_t)c.ny;
+        g.Wz = t + 2 * (size_t)c.ny + c.nx;
+    } else {
+        g.Xj = g.Zj = g.Wx = g.Wz = nullptr;
+    }
     h->ctl = at<DevCtl>(ws, L.ctl);
     h->blockred = at<double>(ws, L.blockred);
     for (int q = 0; q < 3; ++q) h->psi[q] = at<float2>(ws, L.psi[q]);
@@ -344,10 +400,41 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     chk(cudaMemcpyAsync((void *)g.Uz, Uz.data(), 8 * c.nx, cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync((void *)g.Py, Py.data(), 8 * c.ny, cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync((void *)g.Pz, Pz.data(), 8 * c.nz, cudaMemcpyHostToDevice, s));
-    if (g.L) {
+    std::vector<float2> xzt;
+    if (c.links_mode == TDGL_LINKS_GENERAL) {
         long long n3 = 3 * N;
         int nb = (int)((n3 + 255) / 256 < 8192 ? (n3 + 255) / 256 : 8192);
         phases_to_links<<<nb, 256, 0, s>>>(c.d_link_phase, h->links, n3);
+        chk(cudaGetLastError());
+    } else if (c.links_mode == TDGL_LINKS_XZ) {
+        // Eq. A_xz: U_x(j) = exp(i hx Bz ybar_j) (K is applied by the kernels), U_y = 1 inside
+        // the box, U_z(j) = exp(-i hz Bx ybar_j); FP64 phases, whole flux quanta reduced exactly
+        const double Ly = box_len(c.ny, c.hy, c.bc[1]), Lz = box_len(c.nz, c.hz, c.bc[2]);
+        xzt.resize(2 * (size_t)c.ny + c.nx + c.nz);
+        float2 *X = xzt.data(), *Z = X + c.ny, *Wx = Z + c.ny, *Wz = Wx + c.nx;
+        auto e = [](double ph) { return make_float2((float)cos(ph), (float)sin(ph)); };
+        for (int j = 0; j < c.ny; ++j) {
+            double ybar = j * c.hy - 0.5 * Ly;
+            X[j] = e(fmod(c.hx * c.Bz * ybar, kTwoPi));
+            Z[j] = e(fmod(-c.hz * c.Bx * ybar, kTwoPi));
+        }
+        long long nzq = 0, nxq = 0;
+        bool qx = c.bc[0] == TDGL_PERIODIC && quantised(c.Bz, Lx, Ly, &nzq);
+        bool qz = c.bc[2] == TDGL_PERIODIC && quantised(c.Bx, Ly, Lz, &nxq);
+        for (int i = 0; i < c.nx; ++i) {   // -i hx Ly Bz; periodic x: = -2 pi nz i / Nx
+            double ph = qx ? -kTwoPi * (double)(((nzq * i) % c.nx + c.nx) % c.nx) / (double)c.nx
+                           : -fmod(i * c.hx * Ly * c.Bz, kTwoPi);
+            Wx[i] = e(ph);
+        }
+        for (int k = 0; k < c.nz; ++k) {   // +k hz Ly Bx; periodic z: = 2 pi nx k / Nz
+            double ph = qz ? kTwoPi * (double)(((nxq * k) % c.nz + c.nz) % c.nz) / (double)c.nz
+                           : fmod(k * c.hz * Ly * c.Bx, kTwoPi);
+            Wz[k] = e(ph);
+        }
+        float2 *dt = at<float2>(ws, L.xzt);
+        chk(cudaMemcpyAsync((void *)dt, xzt.data(), 8 * xzt.size(), cudaMemcpyHostToDevice, s));
+        int nb = (int)((N + 255) / 256 < 8192 ? (N + 255) / 256 : 8192);
+        xz_links<<<nb, 256, 0, s>>>(dt, h->links, c.nx, c.ny, c.nz, c.bc[1] == TDGL_PERIODIC);
         chk(cudaGetLastError());
     }
     DevCtl ctl0;

@@ -27,6 +27,11 @@ struct DevGrid {
     const float2 *Py;          // [ny] periodic-x wrap phase, y part
     const float2 *Pz;          // [nz] periodic-x wrap phase, z part
     const float2 *L;           // [3N] general links, or nullptr (Landau)
+    // xz-plane gauge (Eq. A_xz), nullptr otherwise; L then holds the same links as a 3N table
+    const float2 *Xj;          // [ny] x links exp(i hx Bz ybar_j) (times exp(i hx K))
+    const float2 *Zj;          // [ny] z links exp(-i hz Bx ybar_j)
+    const float2 *Wx;          // [nx] periodic-y wrap link, x part exp(-i i hx Ly Bz)
+    const float2 *Wz;          // [nz] periodic-y wrap link, z part exp(+i k hz Ly Bx)
 };
 
 // Device-resident control block.  Written only by single threads at the end of

@@ -43,6 +43,8 @@ class Params:
     poisson_max_cycles: int = 50
     poisson_tol: float = 0.0
     general_links: bool = False
+    xz_gauge: bool = False         # field (Bx, 0, Bz) in the Landau gauge of Eq. A_xz (By must be 0)
+    Bx: float = 0.0
     sweeps_per_pass: int = 1       # 2: temporal blocking, two Jacobi sweeps per pass over memory
     noise_T: float = 0.0           # thermal noise parameter T_zeta (Sec. 3.1.2); 0: none
     noise_seed: int = 0
@@ -80,7 +82,9 @@ class Params:
         c.poisson_cycles = self.poisson_cycles
         c.poisson_max_cycles = max(self.poisson_max_cycles, self.poisson_cycles)
         c.poisson_tol = self.poisson_tol
-        c.links_mode = _lib.LINKS_GENERAL if self.general_links else _lib.LINKS_LANDAU
+        c.links_mode = (_lib.LINKS_GENERAL if self.general_links else
+                        _lib.LINKS_XZ if self.xz_gauge else _lib.LINKS_LANDAU)
+        c.Bx = float(self.Bx)
         c.sweeps_per_pass = int(self.sweeps_per_pass)
         c.noise_T = float(self.noise_T)
         c.noise_seed = int(self.noise_seed) & 0xFFFFFFFFFFFFFFFF

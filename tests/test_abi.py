@@ -30,6 +30,14 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_struct_layouts_match_the_library(lib):
+    from paper_1409_8340_gb300 import _lib
+    for which, cls in enumerate(_lib.ABI_STRUCTS):
+        assert lib.tdgl_abi_struct_size(which) == ctypes.sizeof(cls), cls.__name__
+    assert lib.tdgl_abi_struct_size(len(_lib.ABI_STRUCTS)) == 0
+    assert lib.tdgl_abi_struct_size(-1) == 0
+
+
 def _cfg(**kw):
     from paper_1409_8340_gb300.solver import Params
     p = Params(32, 16, 8)
@@ -54,6 +62,30 @@ def test_workspace_size_and_validation(lib):
     nul = _cfg(bc=(1, 0, 0))
     nul.d_alpha = None
     assert lib.tdgl_workspace_bytes(ctypes.byref(nul)) == 0
+
+
+def test_xz_gauge_validation(lib):
+    import math
+    ok = [
+        _cfg(xz_gauge=True, bc=(1, 1, 1), Bx=0.3, Bz=0.2),                 # open y: no wrap, no quantisation
+        _cfg(xz_gauge=True, bc=(0, 1, 0), Bx=0.3, Bz=0.2),                 # periodic x without y wrap: any field
+        _cfg(xz_gauge=True, bc=(0, 0, 1), Bz=2 * math.pi * 3 / (16 * 8), Bx=0.4),
+        _cfg(xz_gauge=True, bc=(1, 0, 0), Bz=0.2, Bx=2 * math.pi * 1 / (8 * 4)),
+    ]
+    for c in ok:
+        assert lib.tdgl_workspace_bytes(ctypes.byref(c)) > 3 * 8 * 32 * 16 * 8
+    bad = [
+        _cfg(xz_gauge=True, bc=(0, 0, 1), Bz=0.2),                         # Bz Lx Ly not 2 pi n
+        _cfg(xz_gauge=True, bc=(1, 0, 0), Bx=0.3),                         # Bx Ly Lz not 2 pi n
+        _cfg(xz_gauge=True, bc=(1, 1, 1), By=0.1),                         # the xz gauge has no By
+        _cfg(bc=(1, 1, 1), Bx=0.1),                                        # the yz gauge has no Bx
+        _cfg(bc=(1, 1, 1), Bx=float("nan")),
+    ]
+    for c in bad:
+        assert lib.tdgl_workspace_bytes(ctypes.byref(c)) == 0
+    # the batch takes yz Landau links only
+    c = (type(ok[0]) * 1)(ok[0])
+    assert lib.tdgl_batch_workspace_bytes(c, 1) == 0
 
 
 def test_workspace_errors_before_device_work(lib):
