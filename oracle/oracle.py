@@ -96,6 +96,16 @@ def lib():
         L.or_inside_q.argtypes = [gp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_inside_q.restype = d
         L.or_threads.restype = ctypes.c_int
+        i64 = ctypes.c_int64
+        L.or_shape_contains.argtypes = [gp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or_shape_contains.restype = ctypes.c_int
+        L.or_lattice_shapes.argtypes = [dp, dp]
+        L.or_lattice_shapes.restype = i64
+        L.or_voronoi_owner.argtypes = [gp, dp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or_voronoi_owner.restype = i64
+        L.or_pattern_ex.argtypes = [gp, dp, i64, i64, ctypes.c_int, ctypes.c_int, d, dp, dp, d, ctypes.c_uint64,
+                                    dp, i64, dp, P(ctypes.c_uint8), P(i64)]
+        L.or_pattern_ex.restype = i64
         _lib = L
     return _lib
 
@@ -313,6 +323,67 @@ def pattern(G: Grid, inclusions, target=0, alpha_in=-1.0, alpha_out=1.0):
 def inside_q(G: Grid, inclusion, i, j, k) -> float:
     inc = np.ascontiguousarray(inclusion, dtype=np.float64)
     return lib().or_inside_q(ctypes.byref(G.c()), _dp(inc), i, j, k)
+
+
+# Full pattern generator (Sec. 3.4).  A shape is 13 numbers: kind, flags, centre[3],
+# semi-axes[3], unit quaternion (w, x, y, z)[4], value.
+ELLIPSOID, CUBOID, CYLINDER, CROSS, OCTANT = 0, 1, 2, 3, 4
+INVERT, INSULATING = 1, 2
+BG_CONSTANT, BG_CHECKER, BG_VORONOI = 0, 1, 2
+EUCLIDEAN, ABSOLUTE, MAXIMUM = 0, 1, 2
+SQUARE, TRIANGULAR, HONEYCOMB, KAGOME, RECTANGULAR, HEXAGONAL = 0, 1, 2, 3, 4, 5
+
+
+def shape_contains(G: Grid, shape, i, j, k) -> bool:
+    """Whether the shape's set (before its invert flag) holds site (i, j, k)."""
+    sh = np.ascontiguousarray(shape, dtype=np.float64)
+    return bool(lib().or_shape_contains(ctypes.byref(G.c()), _dp(sh), i, j, k))
+
+
+def _lattice_record(lat: dict) -> np.ndarray:
+    rec = np.zeros(24, dtype=np.float64)
+    rec[0] = lat["kind"]
+    rec[1:4] = lat["count"]
+    rec[4:7] = lat.get("origin", (0.0, 0.0, 0.0))
+    rec[7:10] = lat["spacing"]
+    rec[10:23] = lat["motif"]
+    return rec
+
+
+def lattice_shapes(lat: dict) -> np.ndarray:
+    """The shapes of one lattice: {kind, count[3], origin[3], spacing[3] (a, b, c), motif[13]}."""
+    rec = _lattice_record(lat)
+    n = lib().or_lattice_shapes(_dp(rec), None)
+    out = np.zeros((n, 13), dtype=np.float64)
+    lib().or_lattice_shapes(_dp(rec), _dp(out))
+    return out
+
+
+def voronoi_owner(G: Grid, seeds, metric, i, j, k) -> int:
+    sd = np.ascontiguousarray(seeds, dtype=np.float64).reshape(-1, 4)
+    return int(lib().or_voronoi_owner(ctypes.byref(G.c()), _dp(sd), sd.shape[0], int(metric), i, j, k))
+
+
+def pattern_ex(G: Grid, shapes=None, lattices=(), background=None, target=0):
+    """Pinning landscape: explicit shapes, then each lattice's shapes, first claim wins;
+    the rest takes the background {kind, metric, value, cell[3], values[2], p_odd, seed,
+    seeds (n, 4)}.  Returns (alpha, insulating (uint8), shapes used, sites claimed)."""
+    parts = [np.asarray(shapes, dtype=np.float64).reshape(-1, 13)] if shapes is not None else []
+    parts += [lattice_shapes(lat) for lat in lattices]
+    allsh = np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros((0, 13)), dtype=np.float64)
+    bg = dict(background or {})
+    cell = np.ascontiguousarray(bg.get("cell", (0.0, 0.0, 0.0)), dtype=np.float64)
+    vals = np.ascontiguousarray(bg.get("values", (0.0, 0.0)), dtype=np.float64)
+    seeds = np.ascontiguousarray(bg.get("seeds", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4)
+    alpha = np.empty(G.shape, dtype=np.float64)
+    ins = np.empty(G.shape, dtype=np.uint8)
+    marked = ctypes.c_int64(0)
+    used = lib().or_pattern_ex(ctypes.byref(G.c()), _dp(allsh), allsh.shape[0], int(target),
+                               int(bg.get("kind", BG_CONSTANT)), int(bg.get("metric", EUCLIDEAN)),
+                               float(bg.get("value", 1.0)), _dp(cell), _dp(vals), float(bg.get("p_odd", -1.0)),
+                               int(bg.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF, _dp(seeds), seeds.shape[0],
+                               _dp(alpha), ins.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(marked))
+    return alpha, ins, int(used), int(marked.value)
 
 
 def voltage_open_x(G: Grid, mu) -> float:

@@ -575,6 +575,213 @@ double or_inside_q(const or_grid *G, const double *inc, int i, int j, int k)
     return inside_q(G, inc, i, j, k);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Pattern generator, full form (Sec. 3.4): pinning landscapes built from     */
+/* shapes (rectangles/cuboids, circles/spheres/ellipsoids, crosses, octants,  */
+/* cylinders), lattices of a shape (square, triangular, honeycomb, kagome,    */
+/* rectangular, hexagonal), a shape that claims its outside (a shaped         */
+/* integration domain), and tessellations (checkerboard, Voronoi with the     */
+/* Euclidean, absolute or maximum distance) as the background.               */
+/*                                                                            */
+/* A shape is 13 doubles: kind, flags, centre c[3], semi-axes a[3],           */
+/* quaternion q[4] (body -> lab), value.  Site (i,j,k) sits at (i hx, j hy,   */
+/* k hz); d = r - c with the minimum image on periodic axes; body coordinates */
+/* e_a = sum_r R[r][a] d_r.  A site takes the value of the first shape (in    */
+/* list order) that claims it; shapes are taken in order while fewer than     */
+/* `target` sites are claimed (target <= 0: all).  Unclaimed sites take the   */
+/* background.  flags bit 0: the shape claims its outside; bit 1: claimed     */
+/* sites are insulating.                                                      */
+/* ------------------------------------------------------------------------ */
+enum { OR_ELLIPSOID = 0, OR_CUBOID = 1, OR_CYLINDER = 2, OR_CROSS = 3, OR_OCTANT = 4 };
+enum { OR_INVERT = 1, OR_INSULATING = 2 };
+enum { OR_BG_CONSTANT = 0, OR_BG_CHECKER = 1, OR_BG_VORONOI = 2 };
+enum { OR_EUCLIDEAN = 0, OR_ABSOLUTE = 1, OR_MAXIMUM = 2 };
+enum { OR_SQUARE = 0, OR_TRIANGULAR = 1, OR_HONEYCOMB = 2, OR_KAGOME = 3, OR_RECTANGULAR = 4, OR_HEXAGONAL = 5 };
+
+static void min_image(const or_grid *G, const double *c, int i, int j, int k, double d[3])
+{
+    double r[3] = {i * G->h[0], j * G->h[1], k * G->h[2]};
+    for (int ax = 0; ax < 3; ++ax) {
+        d[ax] = r[ax] - c[ax];
+        if (G->bc[ax] == OR_PERIODIC) {
+            double L = G->n[ax] * G->h[ax];
+            d[ax] -= L * floor(d[ax] / L + 0.5);
+        }
+    }
+}
+
+/* 1 if the shape contains site (i,j,k) (before the invert flag) */
+int or_shape_contains(const or_grid *G, const double *sh, int i, int j, int k)
+{
+    const int kind = (int)sh[0];
+    const double *c = sh + 2, *a = sh + 5, *q = sh + 8;
+    double d[3], R[3][3], e[3];
+    min_image(G, c, i, j, k, d);
+    quat_to_rot(q, R);
+    for (int b = 0; b < 3; ++b) e[b] = R[0][b] * d[0] + R[1][b] * d[1] + R[2][b] * d[2];
+    double s0 = e[0] / a[0], s1 = e[1] / a[1], s2 = e[2] / a[2];
+    switch (kind) {
+    case OR_ELLIPSOID: return s0 * s0 + s1 * s1 + s2 * s2 <= 1.0;
+    case OR_CUBOID: return fabs(e[0]) <= a[0] && fabs(e[1]) <= a[1] && fabs(e[2]) <= a[2];
+    case OR_CYLINDER: return s0 * s0 + s1 * s1 <= 1.0 && fabs(e[2]) <= a[2];
+    case OR_CROSS:
+        return (fabs(e[0]) <= a[0] && fabs(e[1]) <= a[1] && fabs(e[2]) <= a[2]) ||
+               (fabs(e[0]) <= a[1] && fabs(e[1]) <= a[0] && fabs(e[2]) <= a[2]);
+    case OR_OCTANT: return e[0] >= 0.0 && e[1] >= 0.0 && e[2] >= 0.0 && s0 * s0 + s1 * s1 + s2 * s2 <= 1.0;
+    default: return 0;
+    }
+}
+
+/* Lattice (24 doubles: kind, n1, n2, n3, origin[3], spacing a b c, motif[13],  */
+/* one pad) to shapes: point = origin + n1 a1 + n2 a2 + n3 a3 + basis_b, with   */
+/* the motif centred at point + motif.c.  Order: n3, n2, n1, basis (fastest).   */
+/* Triangular family: a1 = (a, 0, 0), a2 = (a/2, a sqrt(3)/2, 0); honeycomb     */
+/* basis {0, (a1 + a2)/3}; kagome basis {0, a1/2, a2/2}.  2-D kinds stack n3    */
+/* layers a3 = (0, 0, c); hexagonal = triangular layers, period c along z.      */
+/* Returns the number of shapes (out may be NULL to count).                    */
+int64_t or_lattice_shapes(const double *lat, double *out)
+{
+    const int kind = (int)lat[0];
+    const int64_t n1 = (int64_t)lat[1], n2 = (int64_t)lat[2], n3 = (int64_t)lat[3];
+    const double *o = lat + 4, *sp = lat + 7, *motif = lat + 10;
+    const double a = sp[0], b = sp[1], cz = sp[2];
+    const double s3h = sqrt(3.0) * 0.5;
+    double a1[3] = {a, 0.0, 0.0}, a2[3] = {0.0, a, 0.0}, a3[3] = {0.0, 0.0, cz};
+    double basis[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    int nb = 1;
+    if (kind == OR_TRIANGULAR || kind == OR_HONEYCOMB || kind == OR_KAGOME || kind == OR_HEXAGONAL) {
+        a2[0] = 0.5 * a;
+        a2[1] = s3h * a;
+    }
+    if (kind == OR_RECTANGULAR) a2[1] = b;
+    if (kind == OR_HONEYCOMB) {
+        nb = 2;
+        basis[1][0] = 0.5 * a;
+        basis[1][1] = (s3h * a) / 3.0;
+    }
+    if (kind == OR_KAGOME) {
+        nb = 3;
+        basis[1][0] = 0.5 * a;
+        basis[2][0] = 0.25 * a;
+        basis[2][1] = 0.5 * (s3h * a);
+    }
+    int64_t n = 0;
+    for (int64_t k3 = 0; k3 < n3; ++k3)
+        for (int64_t k2 = 0; k2 < n2; ++k2)
+            for (int64_t k1 = 0; k1 < n1; ++k1)
+                for (int bb = 0; bb < nb; ++bb, ++n) {
+                    if (!out) continue;
+                    double *sh = out + 13 * n;
+                    for (int t = 0; t < 13; ++t) sh[t] = motif[t];
+                    for (int ax = 0; ax < 3; ++ax) {
+                        double p = o[ax] + (double)k1 * a1[ax];
+                        p = p + (double)k2 * a2[ax];
+                        p = p + (double)k3 * a3[ax];
+                        p = p + basis[bb][ax];
+                        sh[2 + ax] = p + motif[2 + ax];
+                    }
+                }
+    return n;
+}
+
+/* Background value at site (i,j,k). */
+static double checker_value(const or_grid *G, const double *cell, const double *vals, double p_odd, uint64_t seed,
+                            int i, int j, int k)
+{
+    const int ijk[3] = {i, j, k};
+    int64_t ci[3], nc[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        if (cell[ax] > 0.0) {
+            ci[ax] = (int64_t)floor((ijk[ax] * G->h[ax]) / cell[ax]);
+            nc[ax] = (int64_t)floor(((G->n[ax] - 1) * G->h[ax]) / cell[ax]) + 1;
+        } else {
+            ci[ax] = 0;
+            nc[ax] = 1;
+        }
+    }
+    if (p_odd < 0.0) return ((ci[0] + ci[1] + ci[2]) & 1) ? vals[1] : vals[0];
+    /* random checkerboard: cell takes vals[1] with probability p_odd, drawn by       */
+    /* Philox4x32-10 with counter (cell index, 0, 0x4B434548) and key = seed          */
+    const uint64_t cidx = (uint64_t)(ci[0] + nc[0] * (ci[1] + nc[1] * ci[2]));
+    const uint32_t ctr[4] = {(uint32_t)cidx, (uint32_t)(cidx >> 32), 0u, 0x4B434548u};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    or_philox4x32_10(ctr, key, x);
+    const double u = ldexp((double)(x[0] >> 8), -24);
+    return (u < p_odd) ? vals[1] : vals[0];
+}
+
+/* Voronoi: the value of the nearest seed (x, y, z, value), minimum image on   */
+/* periodic axes, distance Euclidean (compared squared), absolute or maximum;  */
+/* equal distances go to the lower seed index.  Brute force over all seeds.    */
+int64_t or_voronoi_owner(const or_grid *G, const double *seeds, int64_t n_seeds, int metric, int i, int j, int k)
+{
+    int64_t best = -1;
+    double bd = 0.0;
+    for (int64_t s = 0; s < n_seeds; ++s) {
+        double d[3];
+        min_image(G, seeds + 4 * s, i, j, k, d);
+        double v;
+        if (metric == OR_EUCLIDEAN) v = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        else if (metric == OR_ABSOLUTE) v = fabs(d[0]) + fabs(d[1]) + fabs(d[2]);
+        else v = fmax(fmax(fabs(d[0]), fabs(d[1])), fabs(d[2]));
+        if (best < 0 || v < bd) {
+            best = s;
+            bd = v;
+        }
+    }
+    return best;
+}
+
+int64_t or_pattern_ex(const or_grid *G, const double *shapes, int64_t n_shapes, int64_t target, int bg_kind,
+                      int bg_metric, double bg_value, const double *cell, const double *vals, double p_odd,
+                      uint64_t seed, const double *seeds, int64_t n_seeds, double *alpha, uint8_t *insulating,
+                      int64_t *marked_out)
+{
+    const int64_t N = (int64_t)G->n[0] * G->n[1] * G->n[2];
+    int64_t *owner = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    for (int64_t m = 0; m < N; ++m) owner[m] = -1;
+    int64_t marked = 0, used = 0;
+    for (int64_t n = 0; n < n_shapes; ++n) {
+        if (target > 0 && marked >= target) break;
+        const double *sh = shapes + 13 * n;
+        const int inv = ((int)sh[1] & OR_INVERT) != 0;
+        int64_t add = 0;
+#pragma omp parallel for collapse(2) schedule(static) reduction(+ : add)
+        for (int k = 0; k < G->n[2]; ++k)
+            for (int j = 0; j < G->n[1]; ++j)
+                for (int i = 0; i < G->n[0]; ++i) {
+                    int64_t m = idx3(G, i, j, k);
+                    if (owner[m] >= 0) continue;
+                    if (or_shape_contains(G, sh, i, j, k) != inv) {
+                        owner[m] = n;
+                        ++add;
+                    }
+                }
+        marked += add;
+        used = n + 1;
+    }
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < G->n[2]; ++k)
+        for (int j = 0; j < G->n[1]; ++j)
+            for (int i = 0; i < G->n[0]; ++i) {
+                int64_t m = idx3(G, i, j, k);
+                if (owner[m] >= 0) {
+                    alpha[m] = shapes[13 * owner[m] + 12];
+                    if (insulating) insulating[m] = (((int)shapes[13 * owner[m] + 1]) & OR_INSULATING) ? 1 : 0;
+                    continue;
+                }
+                if (insulating) insulating[m] = 0;
+                if (bg_kind == OR_BG_CHECKER) alpha[m] = checker_value(G, cell, vals, p_odd, seed, i, j, k);
+                else if (bg_kind == OR_BG_VORONOI && n_seeds > 0)
+                    alpha[m] = seeds[4 * or_voronoi_owner(G, seeds, n_seeds, bg_metric, i, j, k) + 3];
+                else alpha[m] = bg_value;
+            }
+    free(owner);
+    if (marked_out) *marked_out = marked;
+    return used;
+}
+
 /* Number of OpenMP threads the oracle's parallel loops use (for reporting). */
 #ifdef _OPENMP
 #include <omp.h>
