@@ -181,7 +181,8 @@ const char *tdgl_error_string(int code);
 /* sizeof of the ABI structs, so that a binding can check its own layout:
  * which = 0 tdgl_config, 1 tdgl_obs, 2 tdgl_state_ptrs, 3 tdgl_profile,
  * 4 tdgl_adjoint_config, 5 tdgl_adjoint_stats, 6 tdgl_batch_tuning,
- * 7 tdgl_batch_stats, 8 tdgl_batch_tune_report; 0 for any other value.
+ * 7 tdgl_batch_stats, 8 tdgl_batch_tune_report, 9 tdgl_shape, 10 tdgl_lattice,
+ * 11 tdgl_background; 0 for any other value.
  * Host only, needs no device. */
 size_t tdgl_abi_struct_size(int32_t which);
 
@@ -239,6 +240,112 @@ size_t tdgl_pattern_scratch_bytes(const tdgl_config *grid, int64_t n_candidates)
 int tdgl_pattern(const tdgl_config *grid, const double *host_candidates, int64_t n_candidates,
                  int64_t target_sites, float alpha_in, float alpha_out, float *d_alpha,
                  void *d_scratch, size_t scratch_bytes, void *stream, int64_t *n_used, int64_t *n_marked);
+
+/*
+ * Pattern generator, full form (Sec. 3.4): pinning landscapes from shapes,
+ * lattices of a shape, shapes that claim their outside (a shaped integration
+ * domain) and tessellated backgrounds.
+ *
+ * Shapes.  A site r = (i hx, j hy, k hz) is tested in the body frame of the
+ * shape: d = r - c with the minimum image on periodic axes, e_a = sum_r R_ra d_r,
+ * R the rotation of the unit quaternion q (body -> lab).  All in FP64 with each
+ * product and sum rounded separately, so the decision at every site is
+ * reproducible.  A shape with TDGL_SHAPE_INVERT claims the sites it does not
+ * contain.  A site takes the value of the first shape (list order) that claims
+ * it.  Shapes are taken in order while fewer than target_sites sites are
+ * claimed (target_sites <= 0: all).  TDGL_SHAPE_INSULATING marks the claimed
+ * sites in d_insulating (the insulating inclusions of Sec. 3.4 (ii)).
+ */
+#define TDGL_SHAPE_ELLIPSOID 0   /* sum_a (e_a / a_a)^2 <= 1: spheres, ellipsoids, circles on a film   */
+#define TDGL_SHAPE_CUBOID 1      /* |e_a| <= a_a: cuboids, rectangles on a film                     */
+#define TDGL_SHAPE_CYLINDER 2    /* (e_x/a_x)^2 + (e_y/a_y)^2 <= 1 and |e_z| <= a_z (axis body z)     */
+#define TDGL_SHAPE_CROSS 3       /* bar (a_x, a_y, a_z) united with bar (a_y, a_x, a_z)              */
+#define TDGL_SHAPE_OCTANT 4      /* ellipsoid restricted to e_x, e_y, e_z >= 0                        */
+#define TDGL_SHAPE_INVERT 1      /* flags: claims the outside                                         */
+#define TDGL_SHAPE_INSULATING 2  /* flags: claimed sites are insulating                               */
+
+typedef struct tdgl_shape {
+    int32_t kind;
+    int32_t flags;
+    double c[3];     /* centre, units of xi_0                                   */
+    double a[3];     /* semi-axes / half-extents (> 0)                          */
+    double q[4];     /* unit quaternion (w, x, y, z)                            */
+    double value;    /* eps(r) of the claimed sites                             */
+} tdgl_shape;
+
+/*
+ * Lattices of a motif shape, expanded on the device: point = origin + n1 a1 +
+ * n2 a2 + n3 a3 + basis_b (0 <= n_i < count[i]), motif centred at point +
+ * motif.c; shapes ordered n3, n2, n1, basis (fastest).  With spacing (a, b, c):
+ *   SQUARE      a1 = (a,0,0), a2 = (0,a,0)
+ *   TRIANGULAR  a1 = (a,0,0), a2 = (a/2, a sqrt(3)/2, 0)
+ *   HONEYCOMB   triangular, basis {0, (a/2, a sqrt(3)/6, 0)}
+ *   KAGOME      triangular, basis {0, a1/2, a2/2}
+ *   RECTANGULAR a1 = (a,0,0), a2 = (0,b,0), a3 = (0,0,c)      (3-D)
+ *   HEXAGONAL   triangular layers stacked with a3 = (0,0,c)     (3-D)
+ * The 2-D kinds stack count[2] layers with a3 = (0,0,c) (count[2] = 1: one layer).
+ */
+#define TDGL_LATTICE_SQUARE 0
+#define TDGL_LATTICE_TRIANGULAR 1
+#define TDGL_LATTICE_HONEYCOMB 2
+#define TDGL_LATTICE_KAGOME 3
+#define TDGL_LATTICE_RECTANGULAR 4
+#define TDGL_LATTICE_HEXAGONAL 5
+
+typedef struct tdgl_lattice {
+    int32_t kind;
+    int32_t count[3];
+    double origin[3];
+    double spacing[3];
+    tdgl_shape motif;
+} tdgl_lattice;
+
+/*
+ * Background of the sites no shape claims.
+ *   CONSTANT  value.
+ *   CHECKER   cells of size cell[a] (<= 0: axis not divided), cell index
+ *             c_a = floor(i_a h_a / cell[a]).  p_odd < 0: values[(c_x+c_y+c_z) & 1].
+ *             p_odd in [0, 1]: random checkerboard, a cell takes values[1] when
+ *             u < p_odd, u = (x0 >> 8) 2^-24 from Philox4x32-10 with counter
+ *             (cell, 0, 0x4B434548) and key = seed, cell = c_x + n_x (c_y + n_y c_z),
+ *             n_a = floor((N_a - 1) h_a / cell[a]) + 1; else values[0].
+ *   VORONOI   the value of the nearest seed (host_seeds: n_seeds x (x, y, z, value))
+ *             under the metric (Euclidean, absolute = sum |d_a|, maximum = max |d_a|),
+ *             minimum image on periodic axes, equal distances to the lower seed index.
+ */
+#define TDGL_BG_CONSTANT 0
+#define TDGL_BG_CHECKER 1
+#define TDGL_BG_VORONOI 2
+#define TDGL_METRIC_EUCLIDEAN 0
+#define TDGL_METRIC_ABSOLUTE 1
+#define TDGL_METRIC_MAXIMUM 2
+
+typedef struct tdgl_background {
+    int32_t kind;
+    int32_t metric;
+    double value;
+    double cell[3];
+    double values[2];
+    double p_odd;
+    uint64_t seed;
+    const double *host_seeds;
+    int64_t n_seeds;
+} tdgl_background;
+
+/* Scratch for tdgl_pattern_ex (0: invalid arguments).  bg may be NULL (constant 1). */
+size_t tdgl_pattern_ex_scratch_bytes(const tdgl_config *grid, int64_t n_shapes, const tdgl_lattice *lattices,
+                                     int32_t n_lattices, const tdgl_background *bg);
+/* Shapes (host, n_shapes), then the shapes of each lattice (host, n_lattices) in order;
+ * d_alpha f32[N] receives the pattern, d_insulating (u8[N], may be NULL) 1 where the
+ * claiming shape is insulating.  Only nx..nz, bc and h of grid are read.  Synchronises;
+ * *n_used (shapes taken) and *n_marked (claimed sites) may be NULL.
+ * Errors: TDGL_ERR_INVALID_ARG (bad kind, non-positive size, quaternion not of unit
+ * norm within 1e-6, more than 2^31 - 16 shapes, Voronoi without seeds),
+ * TDGL_ERR_WORKSPACE (scratch too small or not 256-byte aligned). */
+int tdgl_pattern_ex(const tdgl_config *grid, const tdgl_shape *shapes, int64_t n_shapes,
+                    const tdgl_lattice *lattices, int32_t n_lattices, const tdgl_background *bg,
+                    int64_t target_sites, float *d_alpha, uint8_t *d_insulating, void *d_scratch,
+                    size_t scratch_bytes, void *stream, int64_t *n_used, int64_t *n_marked);
 
 /*
  * Adjoint of the time loop: gradient of the time-averaged electric field with

@@ -129,9 +129,34 @@ class BatchTuneReport(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+# Pattern generator, full form (include/tdgl.h, tdgl_pattern_ex)
+SHAPE_ELLIPSOID, SHAPE_CUBOID, SHAPE_CYLINDER, SHAPE_CROSS, SHAPE_OCTANT = 0, 1, 2, 3, 4
+SHAPE_INVERT, SHAPE_INSULATING = 1, 2
+LATTICE_SQUARE, LATTICE_TRIANGULAR, LATTICE_HONEYCOMB, LATTICE_KAGOME = 0, 1, 2, 3
+LATTICE_RECTANGULAR, LATTICE_HEXAGONAL = 4, 5
+BG_CONSTANT, BG_CHECKER, BG_VORONOI = 0, 1, 2
+METRIC_EUCLIDEAN, METRIC_ABSOLUTE, METRIC_MAXIMUM = 0, 1, 2
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("flags", ctypes.c_int32), ("c", ctypes.c_double * 3),
+                ("a", ctypes.c_double * 3), ("q", ctypes.c_double * 4), ("value", ctypes.c_double)]
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("count", ctypes.c_int32 * 3), ("origin", ctypes.c_double * 3),
+                ("spacing", ctypes.c_double * 3), ("motif", Shape)]
+
+
+class Background(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("metric", ctypes.c_int32), ("value", ctypes.c_double),
+                ("cell", ctypes.c_double * 3), ("values", ctypes.c_double * 2), ("p_odd", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("host_seeds", ctypes.c_void_p), ("n_seeds", ctypes.c_int64)]
+
+
 # order of tdgl_abi_struct_size's argument
 ABI_STRUCTS = (Config, Obs, StatePtrs, Profile, AdjointConfig, AdjointStats, BatchTuning, BatchStats,
-               BatchTuneReport)
+               BatchTuneReport, Shape, Lattice, Background)
 
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -172,6 +197,11 @@ _SIGS = {
     "tdgl_batch_phase_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                              ctypes.c_int32]),
     "tdgl_pattern_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64]),
+    "tdgl_pattern_ex_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64, _P, ctypes.c_int32,
+                                                        ctypes.POINTER(Background)]),
+    "tdgl_pattern_ex": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_int64, _P, ctypes.c_int32,
+                                       ctypes.POINTER(Background), ctypes.c_int64, _P, _P, _P, ctypes.c_size_t, _P,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "tdgl_pattern": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
                                     ctypes.c_float, _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)]),

@@ -280,6 +280,9 @@ size_t tdgl_abi_struct_size(int32_t which)
     case 6: return sizeof(tdgl_batch_tuning);
     case 7: return sizeof(tdgl_batch_stats);
     case 8: return sizeof(tdgl_batch_tune_report);
+    case 9: return sizeof(tdgl_shape);
+    case 10: return sizeof(tdgl_lattice);
+    case 11: return sizeof(tdgl_background);
     default: return 0;
     }
 }
@@ -801,12 +804,31 @@ int tdgl_observables(tdgl_handle *h, tdgl_obs *out)
     return TDGL_OK;
 }
 
+// The candidates of tdgl_pattern (centre, semi-axes, quaternion) as ellipsoid shapes.
+static std::vector<tdgl_shape> candidates_as_shapes(const double *c, int64_t n, float alpha_in)
+{
+    std::vector<tdgl_shape> v((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *q = c + 10 * i;
+        tdgl_shape &S = v[(size_t)i];
+        S.kind = TDGL_SHAPE_ELLIPSOID;
+        S.flags = 0;
+        for (int a = 0; a < 3; ++a) {
+            S.c[a] = q[a];
+            S.a[a] = q[3 + a];
+        }
+        for (int a = 0; a < 4; ++a) S.q[a] = q[6 + a];
+        S.value = (double)alpha_in;
+    }
+    return v;
+}
+
 size_t tdgl_pattern_scratch_bytes(const tdgl_config *grid, int64_t n_candidates)
 {
-    if (!grid || grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || n_candidates < 0) return 0;
-    const long long N = (long long)grid->nx * grid->ny * grid->nz;
-    return align256(4 * (size_t)N) + align256(8 * (size_t)n_candidates + 8) + align256(16) +
-           align256(80 * (size_t)n_candidates + 8);
+    if (n_candidates < 0 || n_candidates > 0x7ffffff0LL) return 0;
+    tdgl_background bg;
+    memset(&bg, 0, sizeof(bg));
+    return pattern_ex_scratch(grid, n_candidates, nullptr, 0, &bg);
 }
 
 int tdgl_pattern(const tdgl_config *grid, const double *host_candidates, int64_t n_candidates, int64_t target_sites,
@@ -814,48 +836,33 @@ int tdgl_pattern(const tdgl_config *grid, const double *host_candidates, int64_t
                  int64_t *n_used, int64_t *n_marked)
 {
     if (!grid || !d_alpha || n_candidates < 0 || (n_candidates > 0 && !host_candidates)) return TDGL_ERR_INVALID_ARG;
-    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return TDGL_ERR_INVALID_ARG;
-    if (!(grid->hx > 0) || !(grid->hy > 0) || !(grid->hz > 0)) return TDGL_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (grid->bc[a] != TDGL_PERIODIC && grid->bc[a] != TDGL_OPEN) return TDGL_ERR_INVALID_ARG;
     if (n_candidates > 0x7ffffff0LL) return TDGL_ERR_INVALID_ARG;
-    size_t need = tdgl_pattern_scratch_bytes(grid, n_candidates);
-    if (!d_scratch || ((uintptr_t)d_scratch & 255u) || scratch_bytes < need) return TDGL_ERR_WORKSPACE;
     for (int64_t n = 0; n < n_candidates; ++n) {
         const double *q = host_candidates + 10 * n;
         if (!(q[3] > 0) || !(q[4] > 0) || !(q[5] > 0)) return TDGL_ERR_INVALID_ARG;
     }
-    const long long N = (long long)grid->nx * grid->ny * grid->nz;
-    size_t off = 0;
-    int *first = at<int>(d_scratch, off);
-    off += align256(4 * (size_t)N);
-    unsigned long long *counts = at<unsigned long long>(d_scratch, off);
-    off += align256(8 * (size_t)n_candidates + 8);
-    long long *result = at<long long>(d_scratch, off);
-    off += align256(16);
-    double *incl = at<double>(d_scratch, off);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (n_candidates > 0 &&
-        cudaMemcpyAsync(incl, host_candidates, 80 * (size_t)n_candidates, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return TDGL_ERR_CUDA;
-    DevGrid g;
-    memset(&g, 0, sizeof(g));
-    g.nx = grid->nx;
-    g.ny = grid->ny;
-    g.nz = grid->nz;
-    g.N = N;
-    g.bcx = grid->bc[0];
-    g.bcy = grid->bc[1];
-    g.bcz = grid->bc[2];
-    if (launch_pattern(g, grid->hx, grid->hy, grid->hz, incl, n_candidates, target_sites, alpha_in, alpha_out, d_alpha,
-                       first, counts, result, s) != cudaSuccess)
-        return TDGL_ERR_CUDA;
-    long long res[2];
-    if (cudaMemcpyAsync(res, result, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
-    if (n_used) *n_used = res[0];
-    if (n_marked) *n_marked = res[1];
-    return TDGL_OK;
+    std::vector<tdgl_shape> sh = candidates_as_shapes(host_candidates, n_candidates, alpha_in);
+    tdgl_background bg;
+    memset(&bg, 0, sizeof(bg));
+    bg.kind = TDGL_BG_CONSTANT;
+    bg.value = (double)alpha_out;
+    return pattern_ex_run(grid, sh.data(), n_candidates, nullptr, 0, &bg, target_sites, d_alpha, nullptr, d_scratch,
+                          scratch_bytes, (cudaStream_t)stream, n_used, n_marked);
+}
+
+size_t tdgl_pattern_ex_scratch_bytes(const tdgl_config *grid, int64_t n_shapes, const tdgl_lattice *lattices,
+                                     int32_t n_lattices, const tdgl_background *bg)
+{
+    return pattern_ex_scratch(grid, n_shapes, lattices, n_lattices, bg);
+}
+
+int tdgl_pattern_ex(const tdgl_config *grid, const tdgl_shape *shapes, int64_t n_shapes, const tdgl_lattice *lattices,
+                    int32_t n_lattices, const tdgl_background *bg, int64_t target_sites, float *d_alpha,
+                    uint8_t *d_insulating, void *d_scratch, size_t scratch_bytes, void *stream, int64_t *n_used,
+                    int64_t *n_marked)
+{
+    return pattern_ex_run(grid, shapes, n_shapes, lattices, n_lattices, bg, target_sites, d_alpha, d_insulating,
+                          d_scratch, scratch_bytes, (cudaStream_t)stream, n_used, n_marked);
 }
 
 }  // extern "C"

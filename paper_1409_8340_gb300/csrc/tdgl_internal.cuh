@@ -289,10 +289,13 @@ cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_observables(const DevGrid &g, DevCtl *ctl, double *blockred, const float2 *psi,
                                const float *alpha, int32_t *scratch_i, double flux, cudaStream_t s);
 
-// Pattern
-cudaError_t launch_pattern(const DevGrid &g, double hx, double hy, double hz, const double *d_incl,
-                           long long n_incl, long long target, float alpha_in, float alpha_out, float *alpha,
-                           int *first_idx, unsigned long long *counts, long long *result, cudaStream_t s);
+// Pattern generator (k_pattern.cu): the work of tdgl_pattern_ex after argument checks
+size_t pattern_ex_scratch(const tdgl_config *grid, int64_t n_shapes, const tdgl_lattice *lats, int32_t n_lattices,
+                          const tdgl_background *bg);
+int pattern_ex_run(const tdgl_config *grid, const tdgl_shape *shapes, int64_t n_shapes, const tdgl_lattice *lats,
+                   int32_t n_lattices, const tdgl_background *bg, int64_t target, float *d_alpha,
+                   uint8_t *d_insulating, void *d_scratch, size_t scratch_bytes, cudaStream_t s, int64_t *n_used,
+                   int64_t *n_marked);
 
 // Adjoint kernels (k_adjoint.cu) and the adjoint sweep (k_jacobi.cu)
 cudaError_t launch_adj_sweep(const SweepArgs &a, cudaStream_t s);

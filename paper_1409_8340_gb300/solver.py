@@ -371,6 +371,67 @@ def pattern(p: Params, candidates: np.ndarray, target_sites: int = 0, alpha_in: 
     return alpha, used.value, marked.value
 
 
+def _shape_struct(row, out: _lib.Shape):
+    row = np.asarray(row, dtype=np.float64).ravel()
+    out.kind, out.flags = int(row[0]), int(row[1])
+    out.c[:] = list(row[2:5])
+    out.a[:] = list(row[5:8])
+    out.q[:] = list(row[8:12])
+    out.value = float(row[12])
+
+
+def pattern_ex(p: Params, shapes=None, lattices=(), background=None, target_sites: int = 0, insulating: bool = False,
+               device="cuda", stream=None):
+    """Pinning landscape on the device (tdgl_pattern_ex, Sec. 3.4).
+
+    shapes: (n, 13) rows (kind, flags, centre[3], semi-axes[3], quaternion (w, x, y, z)[4],
+    value); lattices: dicts {kind, count[3], origin[3], spacing[3], motif (13 numbers)};
+    background: dict {kind, metric, value, cell[3], values[2], p_odd, seed, seeds (n, 4)}
+    (None: constant 1).  Returns (alpha, insulating mask or None, n_used, n_marked)."""
+    L = _lib.load()
+    sh = np.asarray(shapes if shapes is not None else np.zeros((0, 13)), dtype=np.float64).reshape(-1, 13)
+    ns = sh.shape[0]
+    sarr = (_lib.Shape * max(1, ns))()
+    for n in range(ns):
+        _shape_struct(sh[n], sarr[n])
+    lats = list(lattices)
+    larr = (_lib.Lattice * max(1, len(lats)))()
+    for n, lat in enumerate(lats):
+        larr[n].kind = int(lat["kind"])
+        larr[n].count[:] = [int(v) for v in lat["count"]]
+        larr[n].origin[:] = [float(v) for v in lat.get("origin", (0.0, 0.0, 0.0))]
+        larr[n].spacing[:] = [float(v) for v in lat["spacing"]]
+        _shape_struct(lat["motif"], larr[n].motif)
+    bg = dict(background or {})
+    B = _lib.Background()
+    B.kind = int(bg.get("kind", _lib.BG_CONSTANT))
+    B.metric = int(bg.get("metric", _lib.METRIC_EUCLIDEAN))
+    B.value = float(bg.get("value", 1.0))
+    B.cell[:] = [float(v) for v in bg.get("cell", (0.0, 0.0, 0.0))]
+    B.values[:] = [float(v) for v in bg.get("values", (0.0, 0.0))]
+    B.p_odd = float(bg.get("p_odd", -1.0))
+    B.seed = int(bg.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    seeds = np.ascontiguousarray(bg.get("seeds", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4)
+    B.host_seeds = seeds.ctypes.data if seeds.shape[0] else None
+    B.n_seeds = seeds.shape[0]
+    alpha = torch.empty(p.shape, dtype=torch.float32, device=device)
+    ins = torch.empty(p.shape, dtype=torch.uint8, device=device) if insulating else None
+    cfg = p.to_c(alpha.data_ptr())
+    nb = L.tdgl_pattern_ex_scratch_bytes(ctypes.byref(cfg), ns, ctypes.addressof(larr), len(lats), ctypes.byref(B))
+    if nb == 0:
+        raise TdglError(-1, "tdgl_pattern_ex_scratch_bytes")
+    scratch = torch.empty(nb, dtype=torch.uint8, device=device)
+    used = ctypes.c_int64()
+    marked = ctypes.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream(alpha.device)
+    check(L.tdgl_pattern_ex(ctypes.byref(cfg), ctypes.addressof(sarr), ns, ctypes.addressof(larr), len(lats),
+                            ctypes.byref(B), int(target_sites), ctypes.c_void_p(alpha.data_ptr()),
+                            ctypes.c_void_p(ins.data_ptr()) if ins is not None else None,
+                            ctypes.c_void_p(scratch.data_ptr()), nb, ctypes.c_void_p(st.cuda_stream),
+                            ctypes.byref(used), ctypes.byref(marked)), "tdgl_pattern_ex")
+    return alpha, ins, used.value, marked.value
+
+
 class TimeAveragedVoltage(torch.autograd.Function):
     """J(alpha) = time-averaged E_x of a run of n_steps from (psi0, mu0), differentiable
     in the pinning map alpha through the hand-written adjoint (tdgl_adjoint).
