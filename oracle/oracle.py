@@ -59,7 +59,7 @@ class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("bc", ctypes.c_int32 * 3), ("h", ctypes.c_double * 3),
                 ("g", ctypes.c_double), ("u", ctypes.c_double), ("beta", ctypes.c_double),
                 ("ht", ctypes.c_double), ("By", ctypes.c_double), ("Bz", ctypes.c_double),
-                ("Jext", ctypes.c_double)]
+                ("Jext", ctypes.c_double), ("ins", ctypes.c_void_p)]
 
 
 _lib = None
@@ -129,6 +129,7 @@ class Grid:
     Jext: float = 0.0
     noise_T: float = 0.0          # grid-independent noise parameter T_zeta (Sec. 3.1.2); 0: no noise
     noise_seed: int = 0
+    insulating: object = None     # u8 array of the grid's shape: insulating sites (Sec. 3.4 (ii)); None: none
 
     @property
     def shape(self):
@@ -145,7 +146,14 @@ class Grid:
         g.h[:] = [self.hx, self.hy, self.hz]
         g.g, g.u, g.beta, g.ht = self.g, self.u, self.beta, self.ht
         g.By, g.Bz, g.Jext = self.By, self.Bz, self.Jext
+        if self.insulating is not None:
+            self._ins = np.ascontiguousarray(self.insulating, dtype=np.uint8).reshape(self.shape)
+            g.ins = self._ins.ctypes.data
         return g
+
+    def conducting(self):
+        return np.ones(self.shape, dtype=bool) if self.insulating is None else \
+            (np.asarray(self.insulating).reshape(self.shape) == 0)
 
     def length(self, ax):
         n = (self.nx, self.ny, self.nz)[ax]
@@ -223,8 +231,9 @@ def poisson_rhs(G: Grid, psi, K=0.0, theta=None):
     f = np.empty(G.shape, dtype=np.float64)
     lib().or_poisson_rhs(ctypes.byref(G.c()), _theta_ptr(theta), K, _dp(_cplx(psi)), _dp(f))
     if G.bc[0] == OPEN and G.Jext != 0.0:
-        f[:, :, 0] -= 2.0 * G.Jext / G.hx
-        f[:, :, -1] += 2.0 * G.Jext / G.hx
+        cond = G.conducting()      # no current enters an insulating face site
+        f[:, :, 0] -= 2.0 * G.Jext / G.hx * cond[:, :, 0]
+        f[:, :, -1] += 2.0 * G.Jext / G.hx * cond[:, :, -1]
     return f
 
 
@@ -247,6 +256,8 @@ def poisson_solve(G: Grid, F):
     """Exact solution of Lap mu = F (Sec. 3.2 operator, periodic or Neumann per
     axis) with the zero mode removed (sum_m w_m mu_m = 0).  The component of F
     along the null space is discarded, which is the compatibility projection."""
+    if G.insulating is not None:
+        return poisson_solve_insulating(G, F)
     F = np.asarray(F, dtype=np.float64)
     ns = (G.nx, G.ny, G.nz)
     hs = (G.hx, G.hy, G.hz)
@@ -275,6 +286,87 @@ def poisson_solve(G: Grid, F):
         if ns[ax] >= 2 and G.bc[ax] == OPEN:
             X = sfft.idct(X.real, type=1, axis=arr_axis[ax]) + 1j * sfft.idct(X.imag, type=1, axis=arr_axis[ax])
     return X.real.copy()
+
+
+def masked_laplacian_matrix(G: Grid):
+    """The Poisson operator of Sec. 3.2 with the links next to insulating sites removed
+    (Sec. 3.4 (ii)), as a sparse matrix over all sites: for every link joining two
+    conducting sites, c_a (2 c_a for the inner link of an open face, the Neumann ghost)
+    on the neighbour and minus the same on the diagonal; rows of insulating sites empty."""
+    import scipy.sparse as sp
+    cond = G.conducting()
+    ns = (G.nx, G.ny, G.nz)
+    hs = (G.hx, G.hy, G.hz)
+    k, j, i = np.meshgrid(np.arange(G.nz), np.arange(G.ny), np.arange(G.nx), indexing="ij")
+    idx = (i, j, k)
+    m = (i + G.nx * (j + G.ny * k)).ravel()
+    rows, cols, vals = [], [], []
+    for ax in range(3):
+        n = ns[ax]
+        if n < 2:
+            continue
+        c = 1.0 / (hs[ax] * hs[ax]) / (G.g * G.g if ax == 2 else 1.0)
+        for sgn in (1, -1):
+            t = [a.copy() for a in idx]
+            t[ax] = t[ax] + sgn
+            exists = np.ones(G.shape, dtype=bool)
+            if G.bc[ax] == OPEN:
+                exists = (t[ax] >= 0) & (t[ax] < n)
+            t[ax] = t[ax] % n
+            nb = (t[0] + G.nx * (t[1] + G.ny * t[2]))
+            ok = exists & cond & cond.ravel()[nb.ravel()].reshape(G.shape)
+            wt = np.ones(G.shape)
+            if G.bc[ax] == OPEN:
+                face = (idx[ax] == 0) if sgn > 0 else (idx[ax] == n - 1)
+                wt = np.where(face, 2.0, 1.0)
+            v = (c * wt * ok).ravel()
+            sel = v != 0
+            rows += [m[sel], m[sel]]
+            cols += [nb.ravel()[sel], m[sel]]
+            vals += [v[sel], -v[sel]]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(G.N, G.N))
+
+
+def conducting_components(G: Grid):
+    """Labels of the connected components of the conducting sites (joined by the links
+    that remain), -1 on insulating sites; and the number of components."""
+    from scipy.sparse.csgraph import connected_components
+    cond = G.conducting().ravel()
+    idx = np.nonzero(cond)[0]
+    A = masked_laplacian_matrix(G)[idx][:, idx]
+    n, lab = connected_components(A, directed=False)
+    out = np.full(G.N, -1)
+    out[idx] = lab
+    return out.reshape(G.shape), int(n)
+
+
+def poisson_solve_insulating(G: Grid, F):
+    """Lap mu = F on the conducting sites with no flux through links next to insulating
+    sites (Sec. 3.4 (ii)), mu = 0 on insulating sites.  Each connected component of the
+    conducting sites carries its own constant: F is made compatible on each (sum w F = 0
+    over the component) and mu has zero weighted mean on each.  W Lap is symmetric (w the
+    trapezoid weights), so CG on -W Lap in FP64 to 1e-14 gives the solution."""
+    import scipy.sparse.linalg as sla
+    cond = G.conducting().ravel()
+    w = site_weights(G).ravel()
+    lab, ncomp = conducting_components(G)
+    lab = lab.ravel()
+    idx = np.nonzero(cond)[0]
+    A = masked_laplacian_matrix(G)
+    Ac = A[idx][:, idx]
+    wc = w[idx]
+    lc = lab[idx]
+    wsum = np.bincount(lc, weights=wc, minlength=ncomp)
+    f = np.asarray(F, dtype=np.float64).ravel()[idx]
+    f = f - (np.bincount(lc, weights=wc * f, minlength=ncomp) / wsum)[lc]
+    Wm = -(Ac.multiply(wc[:, None])).tocsr()
+    sol, info = sla.cg(Wm, -wc * f, rtol=1e-14, atol=0.0, maxiter=20000)
+    if info != 0:
+        raise RuntimeError(f"masked Poisson CG did not converge ({info})")
+    sol = sol - (np.bincount(lc, weights=wc * sol, minlength=ncomp) / wsum)[lc]
+    mu = np.zeros(G.N)
+    mu[idx] = sol
+    return mu.reshape(G.shape)
 
 
 def site_weights(G: Grid):
@@ -387,7 +479,11 @@ def pattern_ex(G: Grid, shapes=None, lattices=(), background=None, target=0):
 
 
 def voltage_open_x(G: Grid, mu) -> float:
-    return float((mu[:, :, 0].mean() - mu[:, :, -1].mean()) / ((G.nx - 1) * G.hx))
+    """E_x from the mean potential of the conducting sites of each x face."""
+    c = G.conducting()
+    m0 = mu[:, :, 0][c[:, :, 0]].mean()
+    m1 = mu[:, :, -1][c[:, :, -1]].mean()
+    return float((m0 - m1) / ((G.nx - 1) * G.hx))
 
 
 # --------------------------------------------------------------------------

@@ -39,6 +39,7 @@ typedef struct {
     double ht;         /* time step h_t (Eq. GL_numCN)                     */
     double By, Bz;     /* field components, yz plane (Eq. B_yz)            */
     double Jext;       /* applied current along x                          */
+    const uint8_t *ins; /* insulating sites (Sec. 3.4 (ii)), u8[N]; NULL: none */
 } or_grid;
 
 static inline int64_t idx3(const or_grid *G, int i, int j, int k)
@@ -105,6 +106,31 @@ static void step_index(const or_grid *G, int ax, int sgn, int c[3])
 }
 
 /*
+ * Insulating inclusions (Sec. 3.4 (ii)): no current crosses an internal edge
+ * next to an insulating site.  Reading: a link that touches an insulating
+ * site is removed from every link sum (the stencil of psi, its diagonal, the
+ * Poisson operator and right-hand side, J_av, the energy); insulating sites
+ * themselves hold psi = 0 and mu = 0.  Without insulating sites every factor
+ * below is 1 and the operators are the plain ones.
+ */
+static inline int insulating(const or_grid *G, int i, int j, int k)
+{
+    return G->ins && G->ins[idx3(G, i, j, k)];
+}
+
+/* 1 if the link from (i,j,k) one step sgn along ax exists (inside the grid or
+ * across a periodic wrap) and joins two conducting sites */
+static double link_ok(const or_grid *G, int ax, int sgn, int i, int j, int k)
+{
+    int c[3] = {i, j, k};
+    if (G->bc[ax] == OR_OPEN && ((sgn > 0 && c[ax] == G->n[ax] - 1) || (sgn < 0 && c[ax] == 0))) return 0.0;
+    if (!G->ins) return 1.0;
+    if (insulating(G, i, j, k)) return 0.0;
+    step_index(G, ax, sgn, c);
+    return insulating(G, c[0], c[1], c[2]) ? 0.0 : 1.0;
+}
+
+/*
  * Neighbour sum NS_m(psi) = sum over axes of c_a (U_a psi_{m+a} + U*_{a,m-a} psi_{m-a}),
  * where at an open face the missing neighbour is replaced by the Neumann ghost
  * (Sec. 3.3.2), which gives 2 c_a U psi_1 at index 0 and 2 c_a U* psi_{N-2}
@@ -124,8 +150,9 @@ static cplx neighbour_sum(const or_grid *G, const double *theta, double K, const
         int cp[3] = {i, j, k}, cm[3] = {i, j, k};
         step_index(G, ax, +1, cp);
         step_index(G, ax, -1, cm);
-        cplx fwd = link(G, theta, K, ax, i, j, k) * load(psi, idx3(G, cp[0], cp[1], cp[2]));
-        cplx bwd = conj(link(G, theta, K, ax, cm[0], cm[1], cm[2])) * load(psi, idx3(G, cm[0], cm[1], cm[2]));
+        cplx fwd = link_ok(G, ax, +1, i, j, k) * link(G, theta, K, ax, i, j, k) * load(psi, idx3(G, cp[0], cp[1], cp[2]));
+        cplx bwd = link_ok(G, ax, -1, i, j, k) * conj(link(G, theta, K, ax, cm[0], cm[1], cm[2])) *
+                   load(psi, idx3(G, cm[0], cm[1], cm[2]));
         if (G->bc[ax] == OR_PERIODIC) {
             acc += c * (fwd + bwd);
         } else if (idx == 0) {
@@ -135,6 +162,23 @@ static cplx neighbour_sum(const or_grid *G, const double *theta, double K, const
         } else {
             acc += c * (fwd + bwd);
         }
+    }
+    return acc;
+}
+
+/* Diagonal weight of the gauge Laplacian at a site: sum over its links of c_a
+ * (the ghost doubles the one link of an open face); 2S without insulators. */
+static double diag_sum(const or_grid *G, int i, int j, int k)
+{
+    double acc = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (!axis_active(G, ax)) continue;
+        int c0[3] = {i, j, k};
+        double c = axis_coef(G, ax), f = link_ok(G, ax, +1, i, j, k), b = link_ok(G, ax, -1, i, j, k);
+        if (G->bc[ax] == OR_PERIODIC) acc += c * (f + b);
+        else if (c0[ax] == 0) acc += 2.0 * c * f;
+        else if (c0[ax] == G->n[ax] - 1) acc += 2.0 * c * b;
+        else acc += c * (f + b);
     }
     return acc;
 }
@@ -213,10 +257,16 @@ void or_init(const or_grid *G, const double *theta, double K, const double *psi_
         for (int j = 0; j < G->n[1]; ++j)
             for (int i = 0; i < G->n[0]; ++i) {
                 int64_t m = idx3(G, i, j, k);
+                if (insulating(G, i, j, k)) {   /* psi = 0: b = 0, M_mm = 1, no links */
+                    store(D, m, 1.0);
+                    store(b, m, 0.0);
+                    continue;
+                }
                 cplx p = load(psi_prev, m);
                 double a2 = creal(p) * creal(p) + cimag(p) * cimag(p);
-                cplx lap = neighbour_sum(G, theta, K, psi_prev, i, j, k) - 2.0 * S * p;
-                cplx Dm = 1.0 + ht2 * (G->beta * a2 + 2.0 * S + I * G->u * mu[m] - alpha[m]);
+                const double S2 = G->ins ? diag_sum(G, i, j, k) : 2.0 * S;
+                cplx lap = neighbour_sum(G, theta, K, psi_prev, i, j, k) - S2 * p;
+                cplx Dm = 1.0 + ht2 * (G->beta * a2 + S2 + I * G->u * mu[m] - alpha[m]);
                 cplx bm = p + ht2 * ((alpha[m] - I * G->u * mu[m]) * p - G->beta * a2 * p + lap);
                 store(D, m, Dm);
                 store(b, m, bm);
@@ -264,6 +314,7 @@ void or_noise(const or_grid *G, double amp, uint64_t seed, int64_t step, double 
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
 #pragma omp parallel for schedule(static)
     for (int64_t m = 0; m < N; ++m) {
+        if (G->ins && G->ins[m]) continue;   /* insulating sites hold psi = 0 */
         const uint32_t ctr[4] = {(uint32_t)m, (uint32_t)((uint64_t)m >> 32), (uint32_t)step,
                                  (uint32_t)((uint64_t)step >> 32)};
         uint32_t x[4];
@@ -338,8 +389,10 @@ double or_javg(const or_grid *G, const double *theta, double K, const double *ps
                 step_index(G, 0, +1, cp);
                 step_index(G, 0, -1, cm);
                 cplx p = load(psi, idx3(G, c[0], c[1], c[2]));
-                cplx fwd = link(G, theta, K, 0, i, j, k) * load(psi, idx3(G, cp[0], cp[1], cp[2]));
-                cplx bwd = conj(link(G, theta, K, 0, cm[0], cm[1], cm[2])) * load(psi, idx3(G, cm[0], cm[1], cm[2]));
+                cplx fwd = link_ok(G, 0, +1, i, j, k) * link(G, theta, K, 0, i, j, k) *
+                           load(psi, idx3(G, cp[0], cp[1], cp[2]));
+                cplx bwd = link_ok(G, 0, -1, i, j, k) * conj(link(G, theta, K, 0, cm[0], cm[1], cm[2])) *
+                           load(psi, idx3(G, cm[0], cm[1], cm[2]));
                 s += cimag(conj(p) * (fwd - bwd));
             }
     return s / (2.0 * (double)N * G->h[0]);
@@ -379,13 +432,14 @@ void or_laplacian_mu(const or_grid *G, const double *mu, double *out)
                     int cp[3] = {i, j, k}, cm[3] = {i, j, k};
                     step_index(G, ax, +1, cp);
                     step_index(G, ax, -1, cm);
-                    double vp = mu[idx3(G, cp[0], cp[1], cp[2])];
-                    double vm = mu[idx3(G, cm[0], cm[1], cm[2])];
+                    const double okp = link_ok(G, ax, +1, i, j, k), okm = link_ok(G, ax, -1, i, j, k);
+                    double vp = okp * (mu[idx3(G, cp[0], cp[1], cp[2])] - mu[m]);
+                    double vm = okm * (mu[idx3(G, cm[0], cm[1], cm[2])] - mu[m]);
                     if (G->bc[ax] == OR_OPEN) {
                         if (c0[ax] == 0) vm = vp;
                         if (c0[ax] == G->n[ax] - 1) vp = vm;
                     }
-                    acc += axis_coef(G, ax) * (vp + vm - 2.0 * mu[m]);
+                    acc += axis_coef(G, ax) * (vp + vm);
                 }
                 out[m] = acc;
             }
@@ -429,7 +483,7 @@ double or_energy(const or_grid *G, const double *theta, double K, const double *
                     for (int o = 0; o < 3; ++o)
                         if (o != ax) wl *= face_weight(G, o, c[o]);
                     cplx d = link(G, theta, K, ax, i, j, k) * load(psi, idx3(G, cp[0], cp[1], cp[2])) - p;
-                    F += wl * axis_coef(G, ax) * (creal(d) * creal(d) + cimag(d) * cimag(d));
+                    F += link_ok(G, ax, +1, i, j, k) * wl * axis_coef(G, ax) * (creal(d) * creal(d) + cimag(d) * cimag(d));
                 }
             }
     return F * dV;
@@ -460,6 +514,10 @@ int64_t or_winding(const or_grid *G, const double *theta, double K, const double
                 step_index(G, 1, +1, d);
                 int c[3] = {bb[0], bb[1], bb[2]};
                 step_index(G, 1, +1, c);
+                /* plaquettes with an insulating corner hold no winding */
+                if (insulating(G, a[0], a[1], a[2]) || insulating(G, bb[0], bb[1], bb[2]) ||
+                    insulating(G, c[0], c[1], c[2]) || insulating(G, d[0], d[1], d[2]))
+                    continue;
                 cplx pa = load(psi, idx3(G, a[0], a[1], a[2]));
                 cplx pb = load(psi, idx3(G, bb[0], bb[1], bb[2]));
                 cplx pc = load(psi, idx3(G, c[0], c[1], c[2]));
