@@ -99,6 +99,20 @@ extern "C" {
  *                   tdgl_set_state / tdgl_upload_state.
  *   noise_seed      key of the noise generator.
  *   Bx              field along x (Eq. B_xz), TDGL_LINKS_XZ only (0 otherwise).
+ *   d_insulating    device u8[N] or NULL: nonzero marks an insulating site
+ *                   (Sec. 3.4 (ii), e.g. the mask of tdgl_pattern_ex).  Every link
+ *                   that touches an insulating site carries no current: it leaves
+ *                   the psi stencil and its diagonal, J_av, the energy, and the
+ *                   Poisson operator and right-hand side; insulating sites hold
+ *                   psi = mu = 0 and take no injected current.  Read once by
+ *                   tdgl_create.  Needs Landau links (either plane) and even nx;
+ *                   unless freeze_mu_K, the conducting sites must form one
+ *                   connected domain (and, with current injected through open x
+ *                   faces, touch both faces), else TDGL_ERR_INVALID_ARG.  The
+ *                   Poisson solve is then conjugate gradients preconditioned by
+ *                   V-cycles: poisson_cycles iterations, or with poisson_tol > 0
+ *                   until the relative residual is below it.  Not for batches, the
+ *                   adjoint or two sweeps per pass.
  *   d_alpha         device f32[N], eps(r) of Eq. epsilon (caller-owned, read-only
  *                   for the handle's lifetime).
  *   d_link_phase    device f32[3N] link phases theta_{a,m} of the link from m to
@@ -127,6 +141,7 @@ typedef struct tdgl_config {
     double Bx;
     const float *d_alpha;
     const float *d_link_phase;
+    const uint8_t *d_insulating;
 } tdgl_config;
 
 typedef struct tdgl_handle tdgl_handle;

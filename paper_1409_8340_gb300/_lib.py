@@ -57,6 +57,7 @@ class Config(ctypes.Structure):
         ("Bx", ctypes.c_double),
         ("d_alpha", ctypes.c_void_p),
         ("d_link_phase", ctypes.c_void_p),
+        ("d_insulating", ctypes.c_void_p),
     ]
 
 

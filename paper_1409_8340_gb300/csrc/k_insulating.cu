@@ -1,0 +1,563 @@
+// Insulating inclusions (arXiv:1409.8340, Sec. 3.4 (ii): no-current conditions
+// across internal grid edges).  A link that touches an insulating site carries
+// no current: it is removed from the psi stencil and its diagonal (tiled sweep,
+// sweep_tile.cuh), from J_av and the observables (k_obs.cu), and from the
+// Poisson operator and right-hand side; insulating sites hold psi = mu = 0.
+//
+// This file builds the per-site link bits, checks that the conducting sites form
+// one connected component (the Poisson problem then has the constants as its only
+// null space), and solves the Poisson equation with the removed links.  That
+// operator has variable coefficients, so the constant-coefficient multigrid
+// becomes a preconditioner: conjugate gradients in the trapezoid-weighted inner
+// product (in which the operator is symmetric), each iteration preconditioned by
+// one symmetric V-cycle of the plain operator; sums in FP64, bulk in FP32.
+#include <float.h>
+
+#include "tdgl_internal.cuh"
+
+namespace tdgl {
+
+namespace {
+
+constexpr int kT = 256;
+
+int red_grid(long long N)
+{
+    long long b = (N + kT * 8 - 1) / (kT * 8);
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+__device__ __forceinline__ void ijk_of(const DevGrid &g, long long m, int &i, int &j, int &k)
+{
+    i = (int)(m % g.nx);
+    const long long t = m / g.nx;
+    j = (int)(t % g.ny);
+    k = (int)(t / g.ny);
+}
+
+__device__ __forceinline__ float face_w(int bc, int n, int idx)
+{
+    return (bc == kOpen && n >= 2 && (idx == 0 || idx == n - 1)) ? 0.5f : 1.0f;
+}
+
+// neighbour index one step sgn along axis ax (periodic wrap; callers only use it
+// where the link exists)
+__device__ __forceinline__ long long nbr(const DevGrid &g, long long m, int i, int j, int k, int ax, int sgn)
+{
+    const long long sz = (long long)g.nx * g.ny;
+    if (ax == 0) return (sgn > 0) ? (i == g.nx - 1 ? m - (g.nx - 1) : m + 1) : (i == 0 ? m + (g.nx - 1) : m - 1);
+    if (ax == 1)
+        return (sgn > 0) ? (j == g.ny - 1 ? m - (long long)(g.ny - 1) * g.nx : m + g.nx)
+                         : (j == 0 ? m + (long long)(g.ny - 1) * g.nx : m - g.nx);
+    return (sgn > 0) ? (k == g.nz - 1 ? m - (long long)(g.nz - 1) * sz : m + sz)
+                     : (k == 0 ? m + (long long)(g.nz - 1) * sz : m - sz);
+}
+
+// Block sum of v into blockred[bid]; the last block writes the total to *out.
+__device__ __forceinline__ void finish_sum(DevCtl *ctl, double *blockred, double v, double *out)
+{
+    __shared__ double shd[32];
+    __shared__ int flag;
+    double s = block_sum(v, shd);
+    if (threadIdx.x == 0) blockred[blockIdx.x] = s;
+    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += ((volatile double *)blockred)[q];
+    t = block_sum(t, shd);
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0u;
+        *out = t;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Link bits
+// ---------------------------------------------------------------------------
+__global__ void link_bits_kernel(DevGrid g, const uint8_t *__restrict__ ins, uint8_t *__restrict__ lk)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        ijk_of(g, m, i, j, k);
+        if (ins[m]) {
+            lk[m] = (uint8_t)kLkIns;
+            continue;
+        }
+        const int idx[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz}, bc[3] = {g.bcx, g.bcy, g.bcz};
+        unsigned bits = 0;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (n[ax] < 2) continue;
+            for (int sgn = 1; sgn >= -1; sgn -= 2) {
+                const bool inside = bc[ax] == kPeriodic || (sgn > 0 ? idx[ax] < n[ax] - 1 : idx[ax] > 0);
+                if (inside && !ins[nbr(g, m, i, j, k, ax, sgn)]) bits |= (sgn > 0 ? 1u : 2u) << (2 * ax);
+            }
+        }
+        lk[m] = (uint8_t)bits;
+    }
+}
+
+cudaError_t launch_link_bits(const DevGrid &g, const uint8_t *ins, uint8_t *lk, cudaStream_t s)
+{
+    link_bits_kernel<<<red_grid(g.N) * 8 > 8192 ? 8192 : red_grid(g.N) * 8, kT, 0, s>>>(g, ins, lk);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Connected components of the conducting sites: labels start as the site index
+// and drop to the smallest label reachable; each pass takes the minimum over the
+// present links, hooks the old representative to it, then follows labels to
+// their representatives (pointer jumping).
+// ---------------------------------------------------------------------------
+__global__ void cc_init_kernel(DevGrid g, long long *lab)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x)
+        lab[m] = (g.lk[m] & kLkIns) ? -1 : m;
+}
+
+__global__ void cc_hook_kernel(DevGrid g, long long *lab, int *changed)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x) {
+        const unsigned l = g.lk[m];
+        if (l & kLkIns) continue;
+        int i, j, k;
+        ijk_of(g, m, i, j, k);
+        const long long cur = lab[m];
+        long long best = cur;
+        for (int ax = 0; ax < 3; ++ax)
+            for (int sgn = 1; sgn >= -1; sgn -= 2) {
+                const unsigned bit = (sgn > 0 ? 1u : 2u) << (2 * ax);
+                if (l & bit) {
+                    const long long v = lab[nbr(g, m, i, j, k, ax, sgn)];
+                    best = v < best ? v : best;
+                }
+            }
+        if (best < cur) {
+            atomicMin(lab + cur, best);
+            atomicMin(lab + m, best);
+            *changed = 1;
+        }
+    }
+}
+
+__global__ void cc_jump_kernel(DevGrid g, long long *lab)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x) {
+        long long v = lab[m];
+        if (v < 0) continue;
+        for (int t = 0; t < 8; ++t) {
+            const long long w = lab[v];
+            if (w == v) break;
+            v = w;
+        }
+        lab[m] = v;
+    }
+}
+
+__global__ void cc_count_kernel(DevGrid g, const long long *lab, DevCtl *ctl, double *blockred)
+{
+    double roots = 0.0, cond = 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x) {
+        if (lab[m] < 0) continue;
+        cond += 1.0;
+        if (lab[m] == m) roots += 1.0;
+    }
+    __shared__ double shd[32];
+    __shared__ int flag;
+    const double a = block_sum(roots, shd), b = block_sum(cond, shd);
+    if (threadIdx.x == 0) {
+        blockred[2 * blockIdx.x] = a;
+        blockred[2 * blockIdx.x + 1] = b;
+    }
+    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
+    double ta = 0.0, tb = 0.0;
+    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+        ta += ((volatile double *)blockred)[2 * q];
+        tb += ((volatile double *)blockred)[2 * q + 1];
+    }
+    ta = block_sum(ta, shd);
+    tb = block_sum(tb, shd);
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0u;
+        ctl->sums[4] = ta;
+        ctl->sums[5] = tb;
+    }
+}
+
+int conducting_components(const DevGrid &g, long long *lab, DevCtl *ctl, double *blockred, cudaStream_t s,
+                          long long *ncomp, long long *ncond)
+{
+    const int nb = red_grid(g.N) * 8 > 8192 ? 8192 : red_grid(g.N) * 8;
+    int *changed = reinterpret_cast<int *>(&ctl->sums[6]);
+    cc_init_kernel<<<nb, kT, 0, s>>>(g, lab);
+    if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
+    // at most a few thousand passes: the labels fall along every path each pass and
+    // pointer jumping shortens the chains; an unfinished search is an error
+    for (int pass = 0; pass < 4096; ++pass) {
+        if (cudaMemsetAsync(changed, 0, sizeof(int), s) != cudaSuccess) return TDGL_ERR_CUDA;
+        cc_hook_kernel<<<nb, kT, 0, s>>>(g, lab, changed);
+        cc_jump_kernel<<<nb, kT, 0, s>>>(g, lab);
+        int h = 0;
+        if (cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+        if (!h) {
+            cc_count_kernel<<<red_grid(g.N), kT, 0, s>>>(g, lab, ctl, blockred);
+            double v[2];
+            if (cudaMemcpyAsync(v, &ctl->sums[4], sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return TDGL_ERR_CUDA;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+            *ncomp = (long long)v[0];
+            *ncond = (long long)v[1];
+            return TDGL_OK;
+        }
+    }
+    return TDGL_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// Weights of the conducting sites
+// ---------------------------------------------------------------------------
+__global__ void cond_weights_kernel(DevGrid g, DevCtl *ctl, double *blockred)
+{
+    double ws = 0.0, f0 = 0.0, f1 = 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x) {
+        if (g.lk[m] & kLkIns) continue;
+        int i, j, k;
+        ijk_of(g, m, i, j, k);
+        ws += (double)(face_w(g.bcx, g.nx, i) * face_w(g.bcy, g.ny, j) * face_w(g.bcz, g.nz, k));
+        if (i == 0) f0 += 1.0;
+        if (i == g.nx - 1) f1 += 1.0;
+    }
+    __shared__ double shd[32];
+    __shared__ int flag;
+    const double v[3] = {ws, f0, f1};
+    for (int q = 0; q < 3; ++q) {
+        const double t = block_sum(v[q], shd);
+        if (threadIdx.x == 0) blockred[3 * blockIdx.x + q] = t;
+    }
+    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
+    for (int q = 0; q < 3; ++q) {
+        double t = 0.0;
+        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += ((volatile double *)blockred)[3 * b + q];
+        t = block_sum(t, shd);
+        if (threadIdx.x == 0) ctl->sums[4 + q] = t;
+    }
+    if (threadIdx.x == 0) ctl->ticket = 0u;
+}
+
+int conducting_weights(const DevGrid &g, DevCtl *ctl, double *blockred, cudaStream_t s, double *wsum_c,
+                       double *n_face0, double *n_face1)
+{
+    cond_weights_kernel<<<red_grid(g.N), kT, 0, s>>>(g, ctl, blockred);
+    if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
+    double v[3];
+    if (cudaMemcpyAsync(v, &ctl->sums[4], sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    *wsum_c = v[0];
+    *n_face0 = v[1];
+    *n_face1 = v[2];
+    return TDGL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Poisson operator with removed links: (A u)_m = sum_a c_a [b+ (u+ - u) + b- (u- - u)],
+// the ghost doubling the inner link on an open face; rows of insulating sites 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float masked_lap(const DevGrid &g, const float *__restrict__ u, long long m, int i, int j,
+                                            int k, unsigned l)
+{
+    const float um = u[m];
+    const int idx[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz}, bc[3] = {g.bcx, g.bcy, g.bcz};
+    const float c[3] = {g.cx, g.cy, g.cz};
+    float acc = 0.f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (n[ax] < 2) continue;
+        float vp = (l & (1u << (2 * ax))) ? u[nbr(g, m, i, j, k, ax, 1)] - um : 0.f;
+        float vm = (l & (2u << (2 * ax))) ? u[nbr(g, m, i, j, k, ax, -1)] - um : 0.f;
+        if (bc[ax] == kOpen) {
+            if (idx[ax] == 0) vm = vp;
+            if (idx[ax] == n[ax] - 1) vp = vm;
+        }
+        acc += c[ax] * (vp + vm);
+    }
+    return acc;
+}
+
+struct InsArgs {
+    DevGrid g;
+    DevCtl *ctl;
+    double *blockred;
+    float *mu, *f, *r, *z, *p, *q;
+    double wsum, wsum_c;
+};
+
+// f -= (sum_c w f) / sum_c w on conducting sites, 0 elsewhere; fmax; clear fmean
+// (the level-0 multigrid kernels subtract ctl->fmean, which the preconditioner must not do)
+__global__ void ins_fproj_kernel(InsArgs a)
+{
+    const float c = (float)(a.ctl->fmean * a.wsum / a.wsum_c);
+    float mx = 0.f;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        const bool ins = (a.g.lk[m] & kLkIns) != 0;
+        const float v = ins ? 0.f : a.f[m] - c;
+        a.f[m] = v;
+        mx = fmaxf(mx, fabsf(v));
+    }
+    __shared__ float shf[32];
+    __shared__ int flag;
+    const float bm = block_max(mx, shf);
+    if (threadIdx.x == 0) a.blockred[blockIdx.x] = (double)bm;
+    if (!last_block(&a.ctl->ticket, gridDim.x, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+        const double v = ((volatile double *)a.blockred)[q];
+        t = v > t ? v : t;
+    }
+    const float tm = block_max((float)t, shf);
+    if (threadIdx.x == 0) {
+        a.ctl->ticket = 0u;
+        a.ctl->fmax = (double)tm;
+        a.ctl->fmean = 0.0;
+    }
+}
+
+// r = f - A mu
+__global__ void ins_resid_kernel(InsArgs a)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        const unsigned l = a.g.lk[m];
+        if (l & kLkIns) {
+            a.r[m] = 0.f;
+            continue;
+        }
+        int i, j, k;
+        ijk_of(a.g, m, i, j, k);
+        a.r[m] = a.f[m] - masked_lap(a.g, a.mu, m, i, j, k, l);
+    }
+}
+
+// sums[slot] = sum_c w v
+__global__ void ins_wsum_kernel(InsArgs a, const float *v, int slot)
+{
+    double acc = 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        if (a.g.lk[m] & kLkIns) continue;
+        int i, j, k;
+        ijk_of(a.g, m, i, j, k);
+        acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) * v[m]);
+    }
+    finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
+}
+
+// v -= sums[mslot] / wsum_c on conducting sites, 0 on insulating ones; when dslot >= 0
+// also sums[dslot] = sum_c w r v (r after the shift of v)
+__global__ void ins_shift_dot_kernel(InsArgs a, float *v, int mslot, int dslot)
+{
+    const float c = (float)(a.ctl->sums[mslot] / a.wsum_c);
+    double acc = 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        if (a.g.lk[m] & kLkIns) {
+            v[m] = 0.f;
+            continue;
+        }
+        const float x = v[m] - c;
+        v[m] = x;
+        if (dslot >= 0) {
+            int i, j, k;
+            ijk_of(a.g, m, i, j, k);
+            acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) *
+                            a.r[m] * x);
+        }
+    }
+    if (dslot >= 0) finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[dslot]);
+}
+
+// p = z + beta p, beta = sums[num] / sums[den] (first: beta = 0)
+__global__ void ins_dir_kernel(InsArgs a, int num, int den, int first)
+{
+    const double d = a.ctl->sums[den];
+    const float beta = (first || d == 0.0) ? 0.f : (float)(a.ctl->sums[num] / d);   // r = 0 exactly: restart
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x)
+        a.p[m] = a.z[m] + beta * a.p[m];
+}
+
+// q = A p, sums[slot] = sum_c w p q
+__global__ void ins_apply_kernel(InsArgs a, int slot)
+{
+    double acc = 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        const unsigned l = a.g.lk[m];
+        if (l & kLkIns) {
+            a.q[m] = 0.f;
+            continue;
+        }
+        int i, j, k;
+        ijk_of(a.g, m, i, j, k);
+        const float v = masked_lap(a.g, a.p, m, i, j, k, l);
+        a.q[m] = v;
+        acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) *
+                        a.p[m] * v);
+    }
+    finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
+}
+
+// alpha = sums[rz] / sums[pq] (the operator is negative semi-definite: both sums are
+// negative or zero); mu += alpha p, r -= alpha q; ctl->res = max|r| / fmax
+__global__ void ins_update_kernel(InsArgs a, int rz, int pq)
+{
+    const double den = a.ctl->sums[pq];
+    const float al = den != 0.0 ? (float)(a.ctl->sums[rz] / den) : 0.f;
+    float mx = 0.f;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        float r = a.r[m];
+        if (al != 0.f) {
+            a.mu[m] += al * a.p[m];
+            r -= al * a.q[m];
+            a.r[m] = r;
+        }
+        mx = fmaxf(mx, fabsf(r));
+    }
+    __shared__ float shf[32];
+    __shared__ int flag;
+    const float bm = block_max(mx, shf);
+    if (threadIdx.x == 0) a.blockred[blockIdx.x] = (double)bm;
+    if (!last_block(&a.ctl->ticket, gridDim.x, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+        const double v = ((volatile double *)a.blockred)[q];
+        t = v > t ? v : t;
+    }
+    const float tm = block_max((float)t, shf);
+    if (threadIdx.x == 0) {
+        a.ctl->ticket = 0u;
+        a.ctl->res = a.ctl->fmax > 0.0 ? (double)tm / a.ctl->fmax : (double)tm;
+    }
+}
+
+int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol, int iters, int max_iters,
+                         cudaStream_t s, int *done, long long *launches)
+{
+    InsArgs a;
+    a.g = pa.g;
+    a.ctl = pa.ctl;
+    a.blockred = pa.blockred;
+    a.mu = pa.mu;
+    a.f = pa.f;
+    a.r = ip.r;
+    a.z = ip.z;
+    a.p = ip.p;
+    a.q = ip.q;
+    a.wsum = pa.wsum;
+    a.wsum_c = ip.wsum_c;
+    const int nb = red_grid(a.g.N);
+    const size_t bytes = 4 * (size_t)a.g.N;
+    // the preconditioner: one V-cycle of the plain operator on r, from z = 0
+    PoissonArgs pz = pa;
+    pz.lev[0].u = ip.z;
+    pz.lev[0].r = ip.r;
+    pz.mu = ip.z;
+    pz.f = ip.r;
+    long long nl = 0;
+    auto precondition = [&](int rzslot) -> bool {
+        if (cudaMemsetAsync(ip.z, 0, bytes, s) != cudaSuccess) return false;
+        if (launch_vcycle(pz, s, &nl) != cudaSuccess) return false;
+        ins_wsum_kernel<<<nb, kT, 0, s>>>(a, ip.z, 4);
+        ins_shift_dot_kernel<<<nb, kT, 0, s>>>(a, ip.z, 4, rzslot);
+        nl += 2;
+        return cudaGetLastError() == cudaSuccess;
+    };
+    ins_fproj_kernel<<<nb, kT, 0, s>>>(a);
+    ins_resid_kernel<<<nb, kT, 0, s>>>(a);
+    nl += 2;
+    if (!precondition(5)) return TDGL_ERR_CUDA;
+    ins_dir_kernel<<<nb, kT, 0, s>>>(a, 5, 5, 1);
+    ++nl;
+    const int cap = iters > 0 ? iters : max_iters;
+    int it = 0, rc = TDGL_OK;
+    for (; it < cap; ++it) {
+        const int rz = (it & 1) ? 6 : 5, rzn = (it & 1) ? 5 : 6;
+        ins_apply_kernel<<<nb, kT, 0, s>>>(a, 7);
+        ins_update_kernel<<<nb, kT, 0, s>>>(a, rz, 7);
+        nl += 2;
+        if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
+        if (iters <= 0) {
+            double res = 0.0;
+            if (cudaMemcpyAsync(&res, &a.ctl->res, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return TDGL_ERR_CUDA;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+            if (!(res == res)) {
+                rc = TDGL_ERR_NONFINITE;
+                ++it;
+                break;
+            }
+            if (res <= tol) {
+                ++it;
+                break;
+            }
+        }
+        if (it + 1 == cap) {   // the iteration cap ends the solve, as the cycle cap of the plain solver does
+            ++it;
+            break;
+        }
+        if (!precondition(rzn)) return TDGL_ERR_CUDA;
+        ins_dir_kernel<<<nb, kT, 0, s>>>(a, rzn, rz, 0);
+        ++nl;
+    }
+    // zero weighted mean over the conducting sites, mu = 0 on insulating ones
+    ins_wsum_kernel<<<nb, kT, 0, s>>>(a, a.mu, 4);
+    ins_shift_dot_kernel<<<nb, kT, 0, s>>>(a, a.mu, 4, -1);
+    nl += 2;
+    if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
+    *done = it;
+    *launches += nl;
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// E_x from the mean mu of the conducting sites of each open x face
+// ---------------------------------------------------------------------------
+__global__ void voltage_masked_kernel(DevGrid g, const float *mu, DevCtl *ctl, double *blockred, double hx, double n0,
+                                      double n1)
+{
+    const long long nf = (long long)g.ny * g.nz;
+    double acc = 0.0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nf; q += (long long)gridDim.x * blockDim.x) {
+        const long long m0 = q * g.nx, m1 = q * g.nx + g.nx - 1;
+        if (!(g.lk[m0] & kLkIns)) acc += (double)mu[m0] / n0;
+        if (!(g.lk[m1] & kLkIns)) acc -= (double)mu[m1] / n1;
+    }
+    __shared__ double shd[32];
+    __shared__ int flag;
+    double s = block_sum(acc, shd);
+    if (threadIdx.x == 0) blockred[blockIdx.x] = s;
+    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += ((volatile double *)blockred)[q];
+    t = block_sum(t, shd);
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0u;
+        ctl->Ex = t / ((g.nx - 1) * hx);
+    }
+}
+
+cudaError_t launch_voltage_masked(const PoissonArgs &a, const InsPoisson &ip, cudaStream_t s)
+{
+    const long long nf = (long long)a.g.ny * a.g.nz;
+    int nb = (int)((nf + kT - 1) / kT);
+    if (nb > 256) nb = 256;
+    voltage_masked_kernel<<<nb, kT, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.hx, ip.n_face0 > 0 ? ip.n_face0 : 1.0,
+                                            ip.n_face1 > 0 ? ip.n_face1 : 1.0);
+    return cudaGetLastError();
+}
+
+}  // namespace tdgl

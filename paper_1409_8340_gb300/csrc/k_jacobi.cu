@@ -291,13 +291,13 @@ __global__ void __launch_bounds__(kBX *kBY) poisson_rhs_kernel(DevGrid g, DevCtl
 }
 
 
-template <int MODE, bool XZ = false>
+template <int MODE, bool XZ = false, bool MASK = false>
 __global__ void __launch_bounds__(kBX *kBY, 4) sweep2_kernel(SweepArgs a, int kz)
 {
     // MODE 5: a plain sweep that recomputes a known result (no test, no early exit)
     if ((MODE == 0 || MODE == 3) && *(volatile int *)&a.ctl->done) return;
     float rmax = 0.f, facc = 0.f;
-    sweep2_body<MODE, false, XZ>(a, kz, blockIdx.x, blockIdx.y, blockIdx.z, rmax, facc);
+    sweep2_body<MODE, false, XZ, MASK>(a, kz, blockIdx.x, blockIdx.y, blockIdx.z, rmax, facc);
     if (MODE == 2) {
         finish_rhs_sum_at(a.ctl, a.blockred, (double)facc, a.wsum, grid_bid(), grid_nb());
         return;
@@ -319,12 +319,23 @@ static dim3 sweep2_grid(const DevGrid &g, int kz)
 // the two-site tiled kernels: Landau links of either plane (tables), even nx
 static bool use_sweep2(const DevGrid &g) { return (g.L == nullptr || g.Xj != nullptr) && (g.nx % 2) == 0; }
 
+// the tiled kernel of MODE for the grid's gauge plane and link bits
+template <int MODE>
+static void launch_sweep2(const SweepArgs &a, int kz, cudaStream_t s)
+{
+    const dim3 grid = sweep2_grid(a.g, kz), block(kBX, kBY);
+    const bool xz = a.g.Xj != nullptr, mk = a.g.lk != nullptr;
+    if (xz && mk) sweep2_kernel<MODE, true, true><<<grid, block, 0, s>>>(a, kz);
+    else if (xz) sweep2_kernel<MODE, true, false><<<grid, block, 0, s>>>(a, kz);
+    else if (mk) sweep2_kernel<MODE, false, true><<<grid, block, 0, s>>>(a, kz);
+    else sweep2_kernel<MODE, false, false><<<grid, block, 0, s>>>(a, kz);
+}
+
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s)
 {
     int kz = zchunk(a.g);
     dim3 block(kBX, kBY);
-    if (use_sweep2(a.g) && a.g.Xj) sweep2_kernel<1, true><<<sweep2_grid(a.g, kz), block, 0, s>>>(a, kz);
-    else if (use_sweep2(a.g)) sweep2_kernel<1><<<sweep2_grid(a.g, kz), block, 0, s>>>(a, kz);
+    if (use_sweep2(a.g)) launch_sweep2<1>(a, kz, s);
     else if (a.g.L) init_sweep_kernel<true><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
     else init_sweep_kernel<false><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
     return cudaGetLastError();
@@ -334,8 +345,7 @@ cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s)
 {
     int kz = zchunk(a.g);
     dim3 block(kBX, kBY);
-    if (use_sweep2(a.g) && a.g.Xj) sweep2_kernel<0, true><<<sweep2_grid(a.g, kz), block, 0, s>>>(a, kz);
-    else if (use_sweep2(a.g)) sweep2_kernel<0><<<sweep2_grid(a.g, kz), block, 0, s>>>(a, kz);
+    if (use_sweep2(a.g)) launch_sweep2<0>(a, kz, s);
     else if (a.g.L) sweep_kernel<true><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
     else sweep_kernel<false><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
     return cudaGetLastError();
@@ -343,7 +353,7 @@ cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s)
 
 cudaError_t launch_sweep_redo(const SweepArgs &a, cudaStream_t s)
 {
-    if (!use_sweep2(a.g) || a.g.Xj) return cudaErrorInvalidValue;
+    if (!use_sweep2(a.g) || a.g.Xj || a.g.lk) return cudaErrorInvalidValue;
     int kz = zchunk(a.g);
     sweep2_kernel<5><<<sweep2_grid(a.g, kz), dim3(kBX, kBY), 0, s>>>(a, kz);
     return cudaGetLastError();
@@ -364,8 +374,7 @@ cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStre
         sa.f = a.f;
         sa.inj = inj;
         sa.wsum = a.wsum;
-        if (a.g.Xj) sweep2_kernel<2, true><<<sweep2_grid(a.g, kz), block, 0, s>>>(sa, kz);
-        else sweep2_kernel<2><<<sweep2_grid(a.g, kz), block, 0, s>>>(sa, kz);
+        launch_sweep2<2>(sa, kz, s);
     } else if (a.g.L) poisson_rhs_kernel<true><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
     else poisson_rhs_kernel<false><<<grid, block, 0, s>>>(a.g, a.ctl, a.blockred, psi, a.f, inj, a.wsum, kz);
     return cudaGetLastError();
@@ -385,6 +394,6 @@ cudaError_t launch_adj_sweep(const SweepArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-bool adj_supported(const DevGrid &g) { return g.L == nullptr && (g.nx % 2) == 0; }
+bool adj_supported(const DevGrid &g) { return g.L == nullptr && g.lk == nullptr && (g.nx % 2) == 0; }
 
 }  // namespace tdgl

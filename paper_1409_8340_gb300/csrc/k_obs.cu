@@ -70,6 +70,11 @@ __global__ void javg_K_kernel(KArgs a)
         float2 fwd = cmul(link_x<GEN>(g, Ux, i, j, k, m), a.psi[mp]);
         int im = (i - 1 + g.nx) % g.nx;
         float2 bwd = cmulc(link_x<GEN>(g, Ux, im, j, k, mm), a.psi[mm]);
+        if (g.lk) {   // links next to insulating sites carry no current
+            const unsigned l = g.lk[m];
+            if (!(l & kLkXp)) fwd = cmk(0.f, 0.f);
+            if (!(l & kLkXm)) bwd = cmk(0.f, 0.f);
+        }
         float2 d = csub(fwd, bwd);
         acc += (double)(p.x * d.y - p.y * d.x);   // Im[conj(p) d]
     }
@@ -134,22 +139,29 @@ __global__ void observables_kernel(DevGrid g, DevCtl *ctl, double *blockred, con
         s_psi2 += (double)a2;
         float wx = face_w(g.bcx, g.nx, i), wy = face_w(g.bcy, g.ny, j), wz = face_w(g.bcz, g.nz, k);
         float e = wx * wy * wz * (-alpha[m] * a2 + 0.5f * g.beta * a2 * a2);
-        // links along x, y, z leaving this site
-        if (g.bcx == kPeriodic || i < g.nx - 1) {
+        // links along x, y, z leaving this site (without the removed ones next to insulating sites)
+        const unsigned l = g.lk ? g.lk[m] : 0x3Fu;
+        if ((g.bcx == kPeriodic || i < g.nx - 1) && (l & kLkXp)) {
             float2 d = csub(cmul(link_x<GEN>(g, Ux, i, j, k, m), psi[wrapped(g, i + 1, j, k)]), p);
             e += wy * wz * g.cx * cabs2(d);
         }
-        if (g.bcy == kPeriodic || j < g.ny - 1) {
+        if ((g.bcy == kPeriodic || j < g.ny - 1) && (l & kLkYp)) {
             float2 d = csub(cmul(link_y<GEN>(g, i, m), psi[wrapped(g, i, j + 1, k)]), p);
             e += wx * wz * g.cy * cabs2(d);
         }
-        if (g.nz >= 2 && (g.bcz == kPeriodic || k < g.nz - 1)) {
+        if (g.nz >= 2 && (g.bcz == kPeriodic || k < g.nz - 1) && (l & kLkZp)) {
             float2 d = csub(cmul(link_z<GEN>(g, i, m), psi[wrapped(g, i, j, k + 1)]), p);
             e += wx * wy * g.cz * cabs2(d);
         }
         s_F += (double)e;
         // xy plaquette with lower-left corner (i, j)
         bool has = (g.bcx == kPeriodic || i < g.nx - 1) && (g.bcy == kPeriodic || j < g.ny - 1);
+        if (has) {
+            int i1 = (i + 1) % g.nx, j1 = (j + 1) % g.ny;
+            long long mb = wrapped(g, i1, j, k), mc = wrapped(g, i1, j1, k), md = wrapped(g, i, j1, k);
+            // plaquettes with an insulating corner hold no winding
+            if (g.lk && ((g.lk[m] | g.lk[mb] | g.lk[mc] | g.lk[md]) & kLkIns)) has = false;
+        }
         if (has) {
             int i1 = (i + 1) % g.nx, j1 = (j + 1) % g.ny;
             long long mb = wrapped(g, i1, j, k), mc = wrapped(g, i1, j1, k), md = wrapped(g, i, j1, k);

@@ -342,7 +342,7 @@ size_t pair_blocks(const DevGrid &g)
     return (size_t)gr.x * gr.y * gr.z;
 }
 
-bool pair_supported(const DevGrid &g) { return g.L == nullptr && (g.nx % 2) == 0; }
+bool pair_supported(const DevGrid &g) { return g.L == nullptr && g.lk == nullptr && (g.nx % 2) == 0; }
 
 cudaError_t launch_sweep_pair(const SweepArgs &a, cudaStream_t s)
 {

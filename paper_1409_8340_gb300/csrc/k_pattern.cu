@@ -55,7 +55,9 @@ struct PGrid {
     long long N;
 };
 
-// d = r - c with the minimum image on periodic axes
+// d = r - c with the minimum image on periodic axes.  When |d| < 0.49 L the image
+// shift floor(d / L + 0.5) is 0 whatever the rounding, so the division is skipped
+// (the result is the same bits).
 __device__ __forceinline__ void min_image(const PGrid &G, const double *c, const int *ijk, double *d)
 {
 #pragma unroll
@@ -63,7 +65,7 @@ __device__ __forceinline__ void min_image(const PGrid &G, const double *c, const
         d[ax] = ds(dm((double)ijk[ax], G.h[ax]), c[ax]);
         if (G.bc[ax] == kPeriodic) {
             const double L = dm((double)G.n[ax], G.h[ax]);
-            d[ax] = ds(d[ax], dm(L, floor(da(dd(d[ax], L), 0.5))));
+            if (!(fabs(d[ax]) < 0.49 * L)) d[ax] = ds(d[ax], dm(L, floor(da(dd(d[ax], L), 0.5))));
         }
     }
 }

@@ -107,7 +107,10 @@ __device__ __forceinline__ bool finish_rhs_sum_at(DevCtl *ctl, double *blockred,
 // CG: loads of data written earlier in the same launch go through L2 only.
 // XZ: links of the xz-plane gauge (Eq. A_xz) from the j-indexed tables Xj, Zj and, on a
 // periodic y axis, the wrap link Wx[i] Wz[k] from row ny-1 to row 0 (x wrap plain U_x).
-template <int MODE, bool CG = false, bool XZ = false>
+// MASK: insulating inclusions (Sec. 3.4 (ii)): the link bits g.lk remove the links next
+// to insulating sites from the neighbour sum and from the diagonal; an insulating site
+// gets b = 0, diag M = 1 (psi = 0) and no injected current.
+template <int MODE, bool CG = false, bool XZ = false, bool MASK = false>
 __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, int by, int bz, float &rmax,
                                             float &facc)
 {
@@ -181,6 +184,9 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
     auto knext = [&](int k) { return (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1; };
     float4 pzm = make_float4(0.f, 0.f, 0.f, 0.f), pc = pzm, pzp_n = pzm, b_n = pzm, D_n = pzm;
     float2 mu_n = cmk(0.f, 0.f), al_n = mu_n;
+    const uchar2 *__restrict__ lk2 = reinterpret_cast<const uchar2 *>(g.lk);
+    uchar2 lk_n = make_uchar2(0, 0);
+    if (MASK && in) lk_n = ldx<CG>(lk2 + q0 + plq * k0);
     if (in) {
         if (zact) pzm = ldx<CG>(src + q0 + plq * ((k0 == 0) ? (zper ? g.nz - 1 : 1) : k0 - 1));
         pc = ldx<CG>(src + q0 + plq * k0);
@@ -203,11 +209,13 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
         const float4 pzp = pzp_n;
         const float4 bc = b_n, Dc = D_n;
         const float2 muc = mu_n, alc = al_n;
+        const uchar2 lkc = lk_n;
         const long long q = q0 + plq * k;
         float4 yf = make_float4(0.f, 0.f, 0.f, 0.f), yb = yf;
         float2 xl = cmk(0.f, 0.f), xr = xl;
         if (in) {
             if (k + 1 < k1) {
+                if (MASK) lk_n = ldx<CG>(lk2 + q + plq);
                 if (zact) pzp_n = ldx<CG>(src + q0 + plq * knext(k + 1));
                 if (INIT) {
                     mu_n = ldx<CG>(mu2 + q + plq);
@@ -287,6 +295,18 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 yb_0 = cscale(wy_b, yb_0);
                 yb_1 = cscale(wy_b, yb_1);
             }
+            if (MASK) {
+                // removed links (0) and present ones (1) of each site of the pair
+                const unsigned l0 = lkc.x, l1 = lkc.y;
+                c1x = cscale((l0 & kLkXp) ? 1.f : 0.f, c1x);
+                xl0 = cscale((l0 & kLkXm) ? 1.f : 0.f, xl0);
+                xr1 = cscale((l1 & kLkXp) ? 1.f : 0.f, xr1);
+                c0x = cscale((l1 & kLkXm) ? 1.f : 0.f, c0x);
+                yf_0 = cscale((l0 & kLkYp) ? 1.f : 0.f, yf_0);
+                yb_0 = cscale((l0 & kLkYm) ? 1.f : 0.f, yb_0);
+                yf_1 = cscale((l1 & kLkYp) ? 1.f : 0.f, yf_1);
+                yb_1 = cscale((l1 & kLkYm) ? 1.f : 0.f, yb_1);
+            }
             // S = (ht/2) NS for both sites
             float2 ns0 = cmul(xf, c1x), ns1 = cmulc(xf, c0x);
             cfmac(ns0, xf, xl0);
@@ -309,8 +329,14 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                         wz_b = 2.f;
                     }
                 }
-                const float4 zpp = (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
-                const float4 zmm = (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
+                float4 zpp = (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
+                float4 zmm = (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
+                if (MASK) {
+                    const float f0 = (lkc.x & kLkZp) ? 1.f : 0.f, b0 = (lkc.x & kLkZm) ? 1.f : 0.f;
+                    const float f1 = (lkc.y & kLkZp) ? 1.f : 0.f, b1 = (lkc.y & kLkZm) ? 1.f : 0.f;
+                    zpp = make_float4(f0 * zpp.x, f0 * zpp.y, f1 * zpp.z, f1 * zpp.w);
+                    zmm = make_float4(b0 * zmm.x, b0 * zmm.y, b1 * zmm.z, b1 * zmm.w);
+                }
                 cfma(ns0, zf0, lo2(zpp));
                 cfmac(ns0, zf0, lo2(zmm));
                 cfma(ns1, zf1, hi2(zpp));
@@ -321,8 +347,8 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 float f0 = (c0.x * ns0.y - c0.y * ns0.x) * inv_ht2;
                 float f1 = (c1.x * ns1.y - c1.y * ns1.x) * inv_ht2;
                 if (!xper) {
-                    if (xlo) f0 -= a.inj;
-                    if (xhi) f1 += a.inj;
+                    if (xlo && !(MASK && (lkc.x & kLkIns))) f0 -= a.inj;
+                    if (xhi && !(MASK && (lkc.y & kLkIns))) f1 += a.inj;
                 }
                 reinterpret_cast<float2 *>(a.f)[q] = make_float2(f0, f1);
                 if (COPY) dst[q] = pc;
@@ -337,12 +363,28 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 const float2 cs[2] = {c0, c1};
                 const float2 nss[2] = {ns0, ns1};
                 const float mus[2] = {muc.x, muc.y}, als[2] = {alc.x, alc.y};
+                float S2[2] = {2.f * g.S, 2.f * g.S};
+                if (MASK) {
+                    // diagonal: c_a per present link, the ghost doubling an open face's inner link
+                    const unsigned ls[2] = {lkc.x, lkc.y};
+                    const float fy = (!yper && (ylo || yhi)) ? 2.f : 1.f;
+                    const float fz = (zact && !zper && (k == 0 || k == g.nz - 1)) ? 2.f : 1.f;
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const unsigned l = ls[s2];
+                        const float fx = (!xper && (s2 == 0 ? xlo : xhi)) ? 2.f : 1.f;
+                        const float nxl = (float)(((l & kLkXp) ? 1 : 0) + ((l & kLkXm) ? 1 : 0));
+                        const float nyl = (float)(((l & kLkYp) ? 1 : 0) + ((l & kLkYm) ? 1 : 0));
+                        const float nzl = (float)(((l & kLkZp) ? 1 : 0) + ((l & kLkZm) ? 1 : 0));
+                        S2[s2] = g.cx * fx * nxl + g.cy * fy * nyl + (zact ? g.cz * fz * nzl : 0.f);
+                    }
+                }
                 float2 bo[2], Do[2];
 #pragma unroll
                 for (int s2 = 0; s2 < 2; ++s2) {
                     const float a2 = cabs2(cs[s2]);
-                    Do[s2] = cmk(1.f + g.ht2 * (g.beta * a2 + 2.f * g.S - als[s2]), g.ht2 * g.u * mus[s2]);
-                    const float cr = als[s2] - g.beta * a2 - 2.f * g.S;
+                    Do[s2] = cmk(1.f + g.ht2 * (g.beta * a2 + S2[s2] - als[s2]), g.ht2 * g.u * mus[s2]);
+                    const float cr = als[s2] - g.beta * a2 - S2[s2];
                     const float ci = -g.u * mus[s2];
                     const float2 lin = cmk(cr * cs[s2].x - ci * cs[s2].y, cr * cs[s2].y + ci * cs[s2].x);
                     bo[s2] = cadd(cadd(cs[s2], cscale(g.ht2, lin)), nss[s2]);   // nss = (ht/2) NS
@@ -350,6 +392,10 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                         // thermal noise h_t zeta_m (Sec. 3.1.2), counter (site, step)
                         const float2 v = noise_uv(a.noise_seed, m + s2, nstep);
                         bo[s2] = cmk(bo[s2].x + a.noise_amp * v.x, bo[s2].y + a.noise_amp * v.y);
+                    }
+                    if (MASK && ((s2 == 0 ? lkc.x : lkc.y) & kLkIns)) {   // insulating: psi = 0
+                        bo[s2] = cmk(0.f, 0.f);
+                        Do[s2] = cmk(1.f, 0.f);
                     }
                 }
                 b0 = bo[0];

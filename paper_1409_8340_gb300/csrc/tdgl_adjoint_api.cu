@@ -22,7 +22,7 @@ int adj_validate(const tdgl_handle *h, const tdgl_adjoint_config *a)
     if (a->n_steps < 1 || a->checkpoint_every < 1 || a->window_start < 0 || a->window_start >= a->n_steps)
         return TDGL_ERR_INVALID_ARG;
     if (a->adj_max_iter < 1 || !(a->adj_eps > 0) || a->poisson_cycles < 1) return TDGL_ERR_INVALID_ARG;
-    if (h->cfg.bc[0] != TDGL_OPEN || h->g.L != nullptr || !adj_supported(h->g) || h->cfg.freeze_mu_K)
+    if (h->cfg.bc[0] != TDGL_OPEN || h->g.L != nullptr || h->lk || !adj_supported(h->g) || h->cfg.freeze_mu_K)
         return TDGL_ERR_INVALID_ARG;
     return TDGL_OK;
 }

@@ -53,6 +53,8 @@ int validate(const tdgl_config *c)
     if (c->links_mode == TDGL_LINKS_GENERAL && !c->d_link_phase) return TDGL_ERR_INVALID_ARG;
     if (c->nx > 1500) return TDGL_ERR_INVALID_ARG;   // x lines of the Poisson smoother live in shared memory
     if (!(c->Bx == c->Bx) || !(c->By == c->By) || !(c->Bz == c->Bz)) return TDGL_ERR_INVALID_ARG;
+    // insulating inclusions run on the tiled kernels: Landau links of either plane, even nx
+    if (c->d_insulating && (c->links_mode == TDGL_LINKS_GENERAL || (c->nx % 2) != 0)) return TDGL_ERR_INVALID_ARG;
     // each gauge carries the field components of its plane only
     if (c->links_mode == TDGL_LINKS_LANDAU && c->Bx != 0.0) return TDGL_ERR_INVALID_ARG;
     if (c->links_mode == TDGL_LINKS_XZ && c->By != 0.0) return TDGL_ERR_INVALID_ARG;
@@ -74,7 +76,7 @@ int validate(const tdgl_config *c)
 }
 
 struct Layout {
-    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, xzt, Uy, Uz, Py, Pz, total;
+    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, xzt, lk, insv, Uy, Uz, Py, Pz, total;
     int nlevels;
     int ny[kMaxLevels], nz[kMaxLevels], fy[kMaxLevels], fz[kMaxLevels];
     size_t u[kMaxLevels], r[kMaxLevels], tri[kMaxLevels];
@@ -123,6 +125,10 @@ Layout layout(const tdgl_config *c)
     L.t = take(4 * (size_t)N);
     L.links = (c->links_mode != TDGL_LINKS_LANDAU) ? take(8 * 3 * (size_t)N) : 0;
     L.xzt = (c->links_mode == TDGL_LINKS_XZ) ? take(8 * (2 * (size_t)c->ny + c->nx + c->nz)) : 0;
+    // insulating inclusions: link bits, and r, z, p, q of the Poisson CG (also the labels
+    // of the connectivity check, 8 bytes per site, at creation)
+    L.lk = c->d_insulating ? take((size_t)N) : 0;
+    L.insv = c->d_insulating ? take(16 * (size_t)N) : 0;
     L.Uy = take(8 * (size_t)c->nx);
     L.Uz = take(8 * (size_t)c->nx);
     L.Py = take(8 * (size_t)c->ny);
@@ -335,6 +341,16 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     } else {
         g.Xj = g.Zj = g.Wx = g.Wz = nullptr;
     }
+    g.lk = c.d_insulating ? at<uint8_t>(ws, L.lk) : nullptr;
+    h->lk = const_cast<uint8_t *>(g.lk);
+    memset(&h->ip, 0, sizeof(h->ip));
+    if (c.d_insulating) {
+        float *v = at<float>(ws, L.insv);
+        h->ip.r = v;
+        h->ip.z = v + N;
+        h->ip.p = v + 2 * N;
+        h->ip.q = v + 3 * N;
+    }
     h->ctl = at<DevCtl>(ws, L.ctl);
     h->blockred = at<double>(ws, L.blockred);
     for (int q = 0; q < 3; ++q) h->psi[q] = at<float2>(ws, L.psi[q]);
@@ -447,6 +463,26 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     chk(cudaMemsetAsync(h->psi[0], 0, 8 * (size_t)N, s));
     chk(cudaMemsetAsync(h->mu, 0, 4 * (size_t)N, s));
     chk(cudaMemsetAsync(h->f, 0, 4 * (size_t)N, s));
+    if (c.d_insulating && rc == TDGL_OK) {
+        // link bits; the Poisson problem needs one connected conducting domain (its null
+        // space is then the constants), and current injected through the x faces needs
+        // conducting sites on both faces
+        chk(launch_link_bits(g, c.d_insulating, h->lk, s));
+        if (rc == TDGL_OK && !c.freeze_mu_K) {
+            long long ncomp = 0, ncond = 0;
+            int r2 = conducting_components(g, reinterpret_cast<long long *>(h->ip.r), h->ctl, h->blockred, s, &ncomp,
+                                           &ncond);
+            if (r2 != TDGL_OK) rc = r2;
+            else if (ncomp != 1 || ncond < 1) rc = TDGL_ERR_INVALID_ARG;
+        }
+        if (rc == TDGL_OK) {
+            int r2 = conducting_weights(g, h->ctl, h->blockred, s, &h->ip.wsum_c, &h->ip.n_face0, &h->ip.n_face1);
+            if (r2 != TDGL_OK) rc = r2;
+            else if (!(h->ip.wsum_c > 0) ||
+                     (c.bc[0] == TDGL_OPEN && c.Jext != 0.0 && (h->ip.n_face0 < 1 || h->ip.n_face1 < 1)))
+                rc = TDGL_ERR_INVALID_ARG;
+        }
+    }
 
     // multigrid
     PoissonArgs &pa = h->pa;
@@ -712,6 +748,18 @@ int tdgl_solve_mu(tdgl_handle *h)
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     if (launch_poisson_rhs(h->pa, h->psi[h->cur], s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (h->lk) {
+        // removed links: CG iterations preconditioned by V-cycles; poisson_cycles of them, or
+        // (poisson_tol > 0) until max|F - Lap mu| <= poisson_tol max|F|, at most poisson_max_cycles
+        long long nl = 1;
+        int it = 0;
+        int rc = masked_poisson_solve(h->pa, h->ip, c.poisson_tol, c.poisson_tol > 0 ? 0 : c.poisson_cycles,
+                                      c.poisson_max_cycles, s, &it, &nl);
+        h->last_cycles = it;
+        h->prof.vcycles += it + 1;
+        h->prof.kernel_launches += nl;
+        return rc;
+    }
     long long nl = 1;
     int cycles = 0;
     for (int q = 0; q < c.poisson_cycles; ++q, ++cycles)
@@ -766,7 +814,8 @@ int tdgl_step(tdgl_handle *h, int n_steps)
             if (rc != TDGL_OK) return rc;
         }
         if (c.bc[0] == TDGL_OPEN) {
-            if (launch_voltage(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
+            if ((h->lk ? launch_voltage_masked(h->pa, h->ip, s) : launch_voltage(h->pa, s)) != cudaSuccess)
+                return TDGL_ERR_CUDA;
             h->prof.kernel_launches += 1;
         }
         ev_rec(h, 7);

@@ -23,7 +23,7 @@ int batch_check(const tdgl_config *c)
 {
     if (!c) return TDGL_ERR_INVALID_ARG;
     if (tdgl_workspace_bytes(c) == 0) return TDGL_ERR_INVALID_ARG;
-    if (c->links_mode != TDGL_LINKS_LANDAU || (c->nx % 2) != 0) return TDGL_ERR_INVALID_ARG;
+    if (c->links_mode != TDGL_LINKS_LANDAU || (c->nx % 2) != 0 || c->d_insulating) return TDGL_ERR_INVALID_ARG;
     if ((long long)c->nx * c->ny * c->nz >= (1LL << 31)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_tol > 0) return TDGL_ERR_INVALID_ARG;
     return TDGL_OK;

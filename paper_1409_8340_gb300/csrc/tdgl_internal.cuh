@@ -32,7 +32,13 @@ struct DevGrid {
     const float2 *Zj;          // [ny] z links exp(-i hz Bx ybar_j)
     const float2 *Wx;          // [nx] periodic-y wrap link, x part exp(-i i hx Ly Bz)
     const float2 *Wz;          // [nz] periodic-y wrap link, z part exp(+i k hz Ly Bx)
+    const uint8_t *lk;         // [N] link bits (insulating inclusions), or nullptr: every link present
 };
+
+// Link bits of a site (insulating inclusions, Sec. 3.4 (ii)): the link to the +x,
+// -x, +y, -y, +z, -z neighbour exists and joins two conducting sites; kLkIns: the
+// site itself is insulating (psi = mu = 0, no links).
+constexpr unsigned kLkXp = 1u, kLkXm = 2u, kLkYp = 4u, kLkYm = 8u, kLkZp = 16u, kLkZm = 32u, kLkIns = 64u;
 
 // Device-resident control block.  Written only by single threads at the end of
 // kernels (last-block reductions), read by later launches on the same stream.
@@ -285,6 +291,28 @@ cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
 
+// Insulating inclusions (k_insulating.cu)
+cudaError_t launch_link_bits(const DevGrid &g, const uint8_t *ins, uint8_t *lk, cudaStream_t s);
+// Connected components of the conducting sites (lab: long long[N] scratch); returns
+// TDGL_OK and the number of components and of conducting sites, or an error code.
+int conducting_components(const DevGrid &g, long long *lab, DevCtl *ctl, double *blockred, cudaStream_t s,
+                          long long *ncomp, long long *ncond);
+// sum of trapezoid weights over conducting sites, conducting sites on the x = 0 and x = L faces
+int conducting_weights(const DevGrid &g, DevCtl *ctl, double *blockred, cudaStream_t s, double *wsum_c,
+                       double *n_face0, double *n_face1);
+struct InsPoisson {
+    float *r, *z, *p, *q;      // residual, preconditioned residual, direction, A p
+    double wsum_c;             // sum of w over conducting sites
+    double n_face0, n_face1;   // conducting sites on the open-x faces
+};
+// Poisson solve with the links next to insulating sites removed: CG in the trapezoid-
+// weighted inner product, preconditioned by one V-cycle of the plain operator.
+// iters > 0: exactly that many iterations; else up to max_iters until res <= tol
+// (a host read per iteration).  Returns a TDGL_* code and the iterations done.
+int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol, int iters, int max_iters,
+                         cudaStream_t s, int *done, long long *launches);
+cudaError_t launch_voltage_masked(const PoissonArgs &a, const InsPoisson &ip, cudaStream_t s);
+
 // Observables
 cudaError_t launch_observables(const DevGrid &g, DevCtl *ctl, double *blockred, const float2 *psi,
                                const float *alpha, int32_t *scratch_i, double flux, cudaStream_t s);
@@ -376,6 +404,8 @@ struct tdgl_handle {
     double wsum;
     double dtK;
     double last_javg;
+    uint8_t *lk;               // link bits when insulating sites are given, else nullptr
+    tdgl::InsPoisson ip;
     // profiling
     int prof_on;
     static constexpr int kEvents = 10;

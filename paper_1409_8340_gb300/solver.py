@@ -103,7 +103,9 @@ class Solver:
     """One TDGL problem on one GPU.  alpha: CUDA float32 tensor of shape (nz, ny, nx)."""
 
     def __init__(self, p: Params, alpha: torch.Tensor, link_phase: torch.Tensor | None = None, stream=None,
-                 device=None):
+                 device=None, insulating: torch.Tensor | None = None):
+        """insulating: optional CUDA uint8 tensor of shape (nz, ny, nx), nonzero on insulating
+        sites (Sec. 3.4 (ii)); read once at creation."""
         L = _lib.load()
         self.p = p
         self.device = alpha.device if device is None else torch.device(device)
@@ -116,6 +118,12 @@ class Solver:
                 raise ValueError("general links need a float32 phase tensor of 3*N elements")
             self.link_phase = link_phase.contiguous().to(torch.float32)
         self._cfg = p.to_c(self.alpha.data_ptr(), self.link_phase.data_ptr() if self.link_phase is not None else 0)
+        self.insulating = None
+        if insulating is not None:
+            if insulating.dtype != torch.uint8 or not insulating.is_cuda or insulating.numel() != p.N:
+                raise ValueError("insulating must be a CUDA uint8 tensor with nx*ny*nz elements")
+            self.insulating = insulating.contiguous()
+            self._cfg.d_insulating = self.insulating.data_ptr()
         nbytes = L.tdgl_workspace_bytes(ctypes.byref(self._cfg))
         if nbytes == 0:
             raise TdglError(-1, "tdgl_workspace_bytes")
@@ -136,6 +144,7 @@ class Solver:
         obj.device = alpha.device
         obj.alpha = alpha
         obj.link_phase = None
+        obj.insulating = None
         obj.stream = stream
         obj.workspace = workspace
         obj._h = handle

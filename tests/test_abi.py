@@ -88,6 +88,21 @@ def test_xz_gauge_validation(lib):
     assert lib.tdgl_batch_workspace_bytes(c, 1) == 0
 
 
+def test_insulating_validation(lib):
+    good = _cfg(bc=(1, 0, 0), Bz=0.1)
+    good.d_insulating = 0x2000
+    assert lib.tdgl_workspace_bytes(ctypes.byref(good)) > lib.tdgl_workspace_bytes(ctypes.byref(_cfg(bc=(1, 0, 0))))
+    odd = _cfg(nx=33, bc=(1, 0, 0))
+    odd.d_insulating = 0x2000
+    gen = _cfg(bc=(1, 0, 0), general_links=True)
+    gen.d_link_phase = 0x3000
+    gen.d_insulating = 0x2000
+    for c in (odd, gen):
+        assert lib.tdgl_workspace_bytes(ctypes.byref(c)) == 0
+    arr = (type(good) * 1)(good)
+    assert lib.tdgl_batch_workspace_bytes(arr, 1) == 0
+
+
 def test_workspace_errors_before_device_work(lib):
     c = _cfg(bc=(1, 0, 0), Bz=0.1)
     h = ctypes.c_void_p()

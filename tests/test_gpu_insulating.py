@@ -1,0 +1,173 @@
+"""Insulating inclusions (Sec. 3.4 (ii)) on the GPU against the FP64 oracle.
+
+The mask comes from the oracle's pattern generator (insulating spheres and
+cylinders), with any enclosed conducting pocket filled so the conducting sites
+form one domain.  Parity: b and diag M at every site and the first sweep; full
+steps (psi, K, mu, E_x) with fixed sweeps and a tight Poisson tolerance; the
+observables.  Invariants of the GPU path itself: an all-conducting mask gives the
+plain solver's trajectory; insulating tubes along the current leave the Ohmic
+normal state E_x = J_ext.  Refusals: a disconnected conducting domain (unless mu
+is frozen), batches and the adjoint.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from _helpers import OP, P, gpu_state, inclusion_alpha, oracle_grid
+from paper_1409_8340_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_PSI = 2e-5
+
+
+def shape(kind, c, a, q=(1.0, 0.0, 0.0, 0.0), value=-1.0, flags=2):
+    return np.array([kind, flags, *c, *a, *q, value], dtype=np.float64)
+
+
+def insulating_mask(O, p, seed, n=10, rmin=1.0, rmax=2.2):
+    """insulating spheres and a tilted cylinder; enclosed conducting pockets filled"""
+    G = oracle_grid(O, p)
+    rng = np.random.default_rng(seed)
+    box = np.array([p.length(0), p.length(1), max(p.length(2), 0.5)])
+    sh = [shape(0, rng.uniform(0, 1, 3) * box, np.full(3, rng.uniform(rmin, rmax))) for _ in range(n)]
+    sh.append(shape(2, box / 2, (0.9, 0.9, box.max()), (math.cos(0.4), 0.0, math.sin(0.4), 0.0)))
+    _, ins, _, _ = O.pattern_ex(G, sh)
+    G.insulating = ins
+    lab, ncomp = O.conducting_components(G)
+    if ncomp > 1:
+        big = np.bincount(lab[lab >= 0]).argmax()
+        ins = np.where((lab >= 0) & (lab != big), 1, ins).astype(np.uint8)
+    return ins
+
+
+def solver(p, alpha, ins, psi0=None, mu0=None, K=0.0):
+    import torch
+    from paper_1409_8340_gb300.solver import Solver
+    s = Solver(p, torch.as_tensor(np.ascontiguousarray(alpha, dtype=np.float32)).cuda(),
+               insulating=torch.as_tensor(np.ascontiguousarray(ins, dtype=np.uint8)).cuda())
+    if psi0 is not None:
+        s.set_state(torch.as_tensor(np.ascontiguousarray(psi0).astype(np.complex64)),
+                    None if mu0 is None else torch.as_tensor(np.asarray(mu0, dtype=np.float32)), K)
+    return s
+
+
+def cases():
+    from paper_1409_8340_gb300.solver import Params
+    q = lambda p, n: dataclasses.replace(p, Bz=2 * math.pi * n / (p.length(0) * p.length(1)))
+    return [
+        ("openx_48x30x14_J", Params(48, 30, 14, bc=(OP, P, P), Bz=0.25, Jext=0.015, g=1.2)),
+        ("periodic_40x24x12", q(Params(40, 24, 12, bc=(P, P, P), Jext=0.01), 3)),
+        ("allopen_34x21x9", Params(34, 21, 9, bc=(OP, OP, OP), Bz=0.35)),
+        ("film_40x26x1", Params(40, 26, 1, bc=(OP, P, P), Bz=0.3, Jext=0.02)),
+        ("xz_openx_36x22x12", Params(36, 22, 12, bc=(OP, P, OP), Bz=0.2, Bx=0.15, xz_gauge=True, Jext=0.01)),
+    ]
+
+
+CASES = cases()
+IDS = [c[0] for c in CASES]
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_init_and_first_sweep(O, name, p):
+    p = dataclasses.replace(p, fixed_sweeps=1)
+    ins = insulating_mask(O, p, 1)
+    G = oracle_grid(O, p)
+    G.insulating = ins
+    th = O.xz_link_phases(G, p.Bx) if p.xz_gauge else None
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 7).astype(np.complex64).astype(np.complex128)
+    mu0 = ((I.uniform(8, "t.mu", p.N).reshape(p.shape) - 0.5) * 0.2).astype(np.float32)
+    alpha = inclusion_alpha(p, 9)
+    K = 0.3 if p.bc[0] == P else 0.0
+    s = solver(p, alpha, ins, psi0, mu0, K)
+    assert s.solve_psi() == 1
+    b_g, D_g, _ = s.internals()
+    b_o, D_o = O.init(G, psi0, mu0, alpha, K, theta=th)
+    np.testing.assert_allclose(b_g.cpu().numpy(), b_o, rtol=0, atol=3e-6)
+    np.testing.assert_allclose(D_g.cpu().numpy(), D_o, rtol=0, atol=3e-6)
+    psi1_o, _ = O.sweep(G, psi0, b_o, D_o, K, theta=th)
+    psi1 = gpu_state(s)[0]
+    np.testing.assert_allclose(psi1, psi1_o, rtol=0, atol=3e-6)
+    assert np.all(psi1[ins.astype(bool)] == 0)
+
+
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_fixed_sweeps_trajectory(O, name, p):
+    p = dataclasses.replace(p, fixed_sweeps=40, poisson_tol=1e-6, poisson_max_cycles=200)
+    ins = insulating_mask(O, p, 2)
+    G = oracle_grid(O, p)
+    G.insulating = ins
+    th = O.xz_link_phases(G, p.Bx) if p.xz_gauge else None
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 17).astype(np.complex64).astype(np.complex128)
+    alpha = inclusion_alpha(p, 19)
+    s = solver(p, alpha, ins, psi0)
+    st = O.State(psi0.copy(), np.zeros(p.shape))
+    for n in range(8):
+        s.step(1)
+        so = O.step(G, st, alpha.astype(np.float64), theta=th, fixed_sweeps=40)
+        psi_g, mu_g = gpu_state(s)
+        assert np.max(np.abs(psi_g - st.psi)) <= TOL_PSI, (n, np.max(np.abs(psi_g - st.psi)))
+        scale = max(1.0, np.max(np.abs(st.mu)))
+        assert np.max(np.abs(mu_g - st.mu)) <= 3e-5 * scale, (n, np.max(np.abs(mu_g - st.mu)))
+        assert np.all(mu_g[ins.astype(bool)] == 0)
+    obs = s.observables()
+    assert abs(obs["K"] - st.K) < 1e-5
+    assert abs(obs["Ex"] - so.Ex) < 2e-5 + 1e-3 * abs(so.Ex)
+    # observables of the final state
+    psi_g, _ = gpu_state(s)
+    F = O.energy(G, psi_g, alpha.astype(np.float64), obs["K"], th)
+    assert abs(obs["energy"] - F) < 1e-4 * abs(F)
+    _, sgn = O.vortex_count(G, psi_g, obs["K"], th)
+    assert abs(obs["vortex_signed"] - sgn) <= 2.0 / p.nz + 1e-9     # one plaquette's rounding at most
+
+
+def test_all_conducting_mask_matches_the_plain_solver():
+    from _helpers import make_solver
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(48, 32, 16, bc=(OP, P, P), Bz=0.2, Jext=0.02, fixed_sweeps=30, poisson_tol=1e-6,
+               poisson_max_cycles=200)
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 3)
+    alpha = inclusion_alpha(p, 4)
+    a = solver(p, alpha, np.zeros(p.shape, np.uint8), psi0)
+    b = make_solver(p, alpha, psi0)
+    for n in range(6):
+        a.step(1)
+        b.step(1)
+        (xa, ma), (xb, mb) = gpu_state(a), gpu_state(b)
+        assert np.abs(xa - xb).max() < 1e-5, n
+        assert np.abs(ma - mb).max() < 2e-5 * max(1.0, np.abs(mb).max()), n
+    assert abs(a.observables()["Ex"] - b.observables()["Ex"]) < 1e-5
+
+
+def test_insulating_tubes_along_the_current_keep_the_ohmic_state():
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(40, 20, 12, bc=(OP, P, P), Jext=0.03, poisson_tol=1e-7, poisson_max_cycles=400)
+    ins = np.zeros(p.shape, np.uint8)
+    ins[2:5, 1:6, :] = 1
+    ins[8, 12, :] = 1
+    s = solver(p, -np.ones(p.shape, np.float32), ins, np.zeros(p.shape, np.complex64))
+    s.step(2)
+    assert abs(s.observables()["Ex"] - p.Jext) < 1e-5
+
+
+def test_refusals():
+    from paper_1409_8340_gb300._lib import TdglError
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(32, 24, 8, bc=(OP, P, P), Bz=0.2, Jext=0.01)
+    planes = np.zeros(p.shape, np.uint8)
+    planes[:, 5, :] = 1
+    planes[:, 15, :] = 1                         # two slabs: mu would have two null vectors
+    alpha = np.ones(p.shape, np.float32)
+    with pytest.raises(TdglError):
+        solver(p, alpha, planes)
+    solver(dataclasses.replace(p, freeze_mu_K=True), alpha, planes).step(2)
+    odd = Params(33, 24, 8, bc=(OP, P, P))
+    with pytest.raises(TdglError):
+        solver(odd, np.ones(odd.shape, np.float32), np.zeros(odd.shape, np.uint8))
+    ins = np.zeros(p.shape, np.uint8)
+    ins[3, 3, 3] = 1
+    s = solver(p, alpha, ins, I.random_psi(p.nx, p.ny, p.nz, 1))
+    with pytest.raises(TdglError):
+        s.adjoint(4, checkpoint_every=2)
