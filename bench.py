@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=30)
     ap.add_argument("--batch-relax", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "xz"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "xz", "pattern", "insulating"],
                     help="run one mode alone and print its dictionary (profiling captures)")
     # profiling captures only (a number printed with these changed is not a bench value)
     ap.add_argument("--nz", type=int, default=256, help="z planes of the grid (profiling captures: a smaller case)")
@@ -355,6 +355,116 @@ def xz_mode(dev, steps: int = 20, relax: int = 20, quanta_x: int = 600):
                             "vortex_unsigned_per_layer": obs["vortex_unsigned"]}}
 
 
+def insulating_mode(dev, steps: int = 20, relax: int = 20):
+    """The mesoscopic workload with insulating inclusions (Sec. 3.4 (ii)): the same
+    ellipsoids as the metallic ones, every fourth marked insulating (links next to them
+    removed), the rest eps = -1; the Poisson solve is 2 CG iterations preconditioned by
+    V-cycles per step (warm start).  The tiled sweep reads one link byte per site more
+    (33 B/site)."""
+    import numpy as np
+    import torch
+
+    from paper_1409_8340_gb300 import inputs
+    from paper_1409_8340_gb300.solver import Solver, pattern_ex
+    w = workload(0.025)
+    p = w.params
+    cand = np.asarray(w.candidates)
+    sh = np.zeros((cand.shape[0], 13))
+    sh[:, 2:5] = cand[:, 0:3]
+    sh[:, 5:8] = cand[:, 3:6]
+    sh[:, 8:12] = cand[:, 6:10]
+    sh[:, 12] = w.alpha_in
+    sh[::4, 1] = 2                                   # insulating
+    alpha, ins, used, marked = pattern_ex(p, sh, (), {"kind": 0, "value": w.alpha_out}, w.target_sites,
+                                          insulating=True, device=dev)
+    s = Solver(p, alpha, insulating=ins)
+    s.set_state(torch.as_tensor(inputs.random_psi(p.nx, p.ny, p.nz, w.seed).astype(np.complex64)))
+    s.step(relax)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    s.profile_enable(True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    s.profile_enable(False)
+    obs = s.observables()
+    n_plain = prof["sweeps"] - prof["steps"]
+    sweep_ms = prof["ms_sweeps"] / max(1, n_plain)
+    bpl = (BYTES_PER_SITE_ITER + 1) * p.N
+    peak, peak_kind = measured_peaks()
+    frac_ins = float(ins.float().mean())
+    del s, alpha, ins
+    torch.cuda.empty_cache()
+    return {"workload": "mesoscopic_512x512x256 with insulating inclusions (every 4th ellipsoid), J 0.025",
+            "insulating_fraction": frac_ins, "inclusion_fraction": marked / p.N,
+            "value": prof["sweeps"] * p.N / (ms * 1e-3) / 1e9, "unit": METRIC, "steps": steps,
+            "ms_per_step": ms / steps, "sweeps_per_step": prof["sweeps"] / max(1, prof["steps"]),
+            "phase_ms_per_step": {"init_sweep": prof["ms_init"] / steps, "sweeps": prof["ms_sweeps"] / steps,
+                                  "K": prof["ms_K"] / steps, "poisson": prof["ms_poisson"] / steps},
+            "sweep_roofline": {"kernel": "sweep2_kernel<0, MASK>", "bound": "hbm", "bytes_per_launch": bpl,
+                               "avg_launch_ms": sweep_ms, "achieved": bpl / (sweep_ms * 1e-3) / 1e9,
+                               "peak": peak, "unit": "GB/s", "frac": bpl / (sweep_ms * 1e-3) / 1e9 / peak,
+                               "peak_source": peak_kind},
+            "observables": {"Ex": obs["Ex"], "psi2_mean": obs["psi2_mean"]}}
+
+
+def pattern_mode(dev, reps: int = 5):
+    """The pattern generator (Sec. 3.4) at 512x512x256 (open x, periodic y z): the
+    mesoscopic ellipsoids to 10 % (20 000 candidates), a polycrystalline Voronoi
+    background of 20 000 grains, a random checkerboard, and a cylindrical domain mask
+    with a kagome lattice of +-45 degree columnar insulating cylinders over the Voronoi
+    grains.  Each timed with CUDA events over `reps` runs (the call synchronises)."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_1409_8340_gb300.solver import pattern, pattern_ex
+    w = workload(0.0)
+    p = w.params
+    rng = np.random.default_rng(33)
+    seeds = np.zeros((20000, 4))
+    seeds[:, :3] = rng.uniform(0, 1, (20000, 3)) * (p.length(0), p.length(1), p.length(2))
+    seeds[:, 3] = rng.uniform(0.5, 1.0, 20000)
+    vor = {"kind": 2, "metric": 0, "seeds": seeds}
+    dom = [1, 1, 128.0, 128.0, 64.0, 120.0, 120.0, 1e3, 1.0, 0.0, 0.0, 0.0, -1.0]          # inverted cylinder
+    q45 = [math.cos(math.pi / 8), 0.0, math.sin(math.pi / 8), 0.0]
+    motif = [2, 2, 0.0, 0.0, 0.0, 1.5, 1.5, 60.0] + q45 + [-1.0]
+    lat = {"kind": 3, "count": (25, 29, 3), "origin": (2.0, 2.0, 40.0), "spacing": (10.0, 0.0, 40.0), "motif": motif}
+    cases = {
+        "ellipsoids_10pct": lambda: pattern(p, w.candidates, w.target_sites, w.alpha_in, w.alpha_out, device=dev),
+        "voronoi_20000": lambda: pattern_ex(p, None, (), vor, device=dev),
+        "random_checkerboard": lambda: pattern_ex(p, None, (), {"kind": 1, "cell": (2.0, 2.0, 2.0),
+                                                                "values": (0.5, 1.0), "p_odd": 0.5, "seed": 7},
+                                                  device=dev),
+        "domain_kagome_columns_voronoi": lambda: pattern_ex(p, [dom], [lat], vor, insulating=True, device=dev),
+    }
+    out = {}
+    for name, fn in cases.items():
+        r = fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        a = r[0]
+        out[name] = {"ms": float(np.median(ms)), "gsites_per_s": p.N / (np.median(ms) * 1e-3) / 1e9,
+                     "fraction_below_1": float((a < 1.0).float().mean())}
+        del r, a
+    torch.cuda.empty_cache()
+    return {"workload": "pattern generator at 512x512x256, open x, periodic y z", "sites": p.N, "cases": out}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -476,6 +586,8 @@ def run_native(args, rank, world, local_rank):
         modes["batched"]["vs_plain_step"] = modes["batched"]["value"] / value
         modes["adjoint"] = adjoint_mode(dev)
         modes["xz_gauge"] = xz_mode(dev)
+        modes["pattern"] = pattern_mode(dev)
+        modes["insulating"] = insulating_mode(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -537,6 +649,10 @@ def main():
             out = batched_mode(dev, args.batch_steps, args.batch_relax, autotune=not args.no_autotune)
         elif args.only == "xz":
             out = xz_mode(dev)
+        elif args.only == "pattern":
+            out = pattern_mode(dev)
+        elif args.only == "insulating":
+            out = insulating_mode(dev)
         else:
             out = adjoint_mode(dev)
         print(json.dumps({"mode": args.only, **out}), flush=True)

@@ -479,8 +479,14 @@ def pattern_ex(G: Grid, shapes=None, lattices=(), background=None, target=0):
 
 
 def voltage_open_x(G: Grid, mu) -> float:
-    """E_x from the mean potential of the conducting sites of each x face."""
-    c = G.conducting()
+    """E_x from the mean potential of each x face.  With insulating sites: over the face
+    sites of the largest conducting component (an island enclosed by insulators carries
+    its own constant in mu and no current from face to face)."""
+    if G.insulating is None:
+        return float((mu[:, :, 0].mean() - mu[:, :, -1].mean()) / ((G.nx - 1) * G.hx))
+    lab, _ = conducting_components(G)
+    main = np.bincount(lab[lab >= 0]).argmax()
+    c = lab == main
     m0 = mu[:, :, 0][c[:, :, 0]].mean()
     m1 = mu[:, :, -1][c[:, :, -1]].mean()
     return float((m0 - m1) / ((G.nx - 1) * G.hx))

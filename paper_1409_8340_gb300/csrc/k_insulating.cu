@@ -4,13 +4,15 @@
 // sweep_tile.cuh), from J_av and the observables (k_obs.cu), and from the
 // Poisson operator and right-hand side; insulating sites hold psi = mu = 0.
 //
-// This file builds the per-site link bits, checks that the conducting sites form
-// one connected component (the Poisson problem then has the constants as its only
-// null space), and solves the Poisson equation with the removed links.  That
-// operator has variable coefficients, so the constant-coefficient multigrid
-// becomes a preconditioner: conjugate gradients in the trapezoid-weighted inner
-// product (in which the operator is symmetric), each iteration preconditioned by
-// one symmetric V-cycle of the plain operator; sums in FP64, bulk in FP32.
+// This file builds the per-site link bits and the connected components of the
+// conducting sites (islands enclosed by insulators are components of their own; the
+// constants of each component span the Poisson operator's null space), and solves
+// the Poisson equation with the removed links.  That operator has variable
+// coefficients, so the constant-coefficient multigrid becomes a preconditioner:
+// conjugate gradients in the trapezoid-weighted inner product (in which the operator
+// is symmetric), each iteration preconditioned by one symmetric V-cycle of the plain
+// operator, the right-hand side and the iterates projected on every component; sums
+// in FP64, bulk in FP32.
 #include <float.h>
 
 #include "tdgl_internal.cuh"
@@ -186,47 +188,63 @@ __global__ void cc_count_kernel(DevGrid g, const long long *lab, DevCtl *ctl, do
     }
 }
 
-int conducting_components(const DevGrid &g, long long *lab, DevCtl *ctl, double *blockred, cudaStream_t s,
-                          long long *ncomp, long long *ncond)
+// roots' sizes (one atomic per run of equal roots in a warp)
+__global__ void cc_size_kernel(DevGrid g, const long long *lab, int *cnt)
 {
-    const int nb = red_grid(g.N) * 8 > 8192 ? 8192 : red_grid(g.N) * 8;
-    int *changed = reinterpret_cast<int *>(&ctl->sums[6]);
-    cc_init_kernel<<<nb, kT, 0, s>>>(g, lab);
-    if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
-    // at most a few thousand passes: the labels fall along every path each pass and
-    // pointer jumping shortens the chains; an unfinished search is an error
-    for (int pass = 0; pass < 4096; ++pass) {
-        if (cudaMemsetAsync(changed, 0, sizeof(int), s) != cudaSuccess) return TDGL_ERR_CUDA;
-        cc_hook_kernel<<<nb, kT, 0, s>>>(g, lab, changed);
-        cc_jump_kernel<<<nb, kT, 0, s>>>(g, lab);
-        int h = 0;
-        if (cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
-        if (!h) {
-            cc_count_kernel<<<red_grid(g.N), kT, 0, s>>>(g, lab, ctl, blockred);
-            double v[2];
-            if (cudaMemcpyAsync(v, &ctl->sums[4], sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-                return TDGL_ERR_CUDA;
-            if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
-            *ncomp = (long long)v[0];
-            *ncond = (long long)v[1];
-            return TDGL_OK;
-        }
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = warp * 32; base < g.N; base += nwarps * 32) {
+        const long long m = base + lane;
+        const long long r = (m < g.N) ? lab[m] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, r);
+        if (r >= 0 && lane == __ffs(peers) - 1) atomicAdd(cnt + r, __popc(peers));
     }
-    return TDGL_ERR_NOT_CONVERGED;
 }
 
-// ---------------------------------------------------------------------------
-// Weights of the conducting sites
-// ---------------------------------------------------------------------------
-__global__ void cond_weights_kernel(DevGrid g, DevCtl *ctl, double *blockred)
+// the largest size over roots, then the smallest root of that size (the main component)
+__global__ void cc_max_kernel(DevGrid g, const long long *lab, const int *cnt, unsigned long long *mx)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x)
+        if (lab[m] == m) atomicMax(mx, (unsigned long long)cnt[m]);
+}
+
+__global__ void cc_main_kernel(DevGrid g, const long long *lab, const int *cnt, const unsigned long long *mx,
+                               unsigned long long *main_root)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x)
+        if (lab[m] == m && (unsigned long long)cnt[m] == *mx) atomicMin(main_root, (unsigned long long)m);
+}
+
+// compact ids: 0 for the main root, 1, 2, ... for the other roots (in no particular order)
+__global__ void cc_id_kernel(DevGrid g, const long long *lab, int *cnt, const unsigned long long *main_root,
+                             unsigned int *counter)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x)
+        if (lab[m] == m) cnt[m] = ((unsigned long long)m == *main_root) ? 0 : 1 + (int)atomicAdd(counter, 1u);
+}
+
+__global__ void cc_comp_kernel(DevGrid g, const long long *lab, const int *cnt, int *comp)
+{
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x)
+        comp[m] = lab[m] < 0 ? -1 : cnt[lab[m]];
+}
+
+// sum of w over the main component (and its x-face sites) into sums[4..6]; per island into isl_w
+__global__ void comp_weights_kernel(DevGrid g, const int *comp, DevCtl *ctl, double *blockred, double *isl_w)
 {
     double ws = 0.0, f0 = 0.0, f1 = 0.0;
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < g.N; m += (long long)gridDim.x * blockDim.x) {
-        if (g.lk[m] & kLkIns) continue;
+        const int c = comp[m];
+        if (c < 0) continue;
         int i, j, k;
         ijk_of(g, m, i, j, k);
-        ws += (double)(face_w(g.bcx, g.nx, i) * face_w(g.bcy, g.ny, j) * face_w(g.bcz, g.nz, k));
+        const double w = (double)(face_w(g.bcx, g.nx, i) * face_w(g.bcy, g.ny, j) * face_w(g.bcz, g.nz, k));
+        if (c > 0) {
+            atomicAdd(isl_w + (c - 1), w);
+            continue;
+        }
+        ws += w;
         if (i == 0) f0 += 1.0;
         if (i == g.nx - 1) f1 += 1.0;
     }
@@ -247,17 +265,56 @@ __global__ void cond_weights_kernel(DevGrid g, DevCtl *ctl, double *blockred)
     if (threadIdx.x == 0) ctl->ticket = 0u;
 }
 
-int conducting_weights(const DevGrid &g, DevCtl *ctl, double *blockred, cudaStream_t s, double *wsum_c,
-                       double *n_face0, double *n_face1)
+int build_components(const DevGrid &g, InsPoisson &ip, DevCtl *ctl, double *blockred, cudaStream_t s)
 {
-    cond_weights_kernel<<<red_grid(g.N), kT, 0, s>>>(g, ctl, blockred);
+    const int nb = red_grid(g.N) * 8 > 8192 ? 8192 : red_grid(g.N) * 8;
+    long long *lab = reinterpret_cast<long long *>(ip.r);   // r and z: 8 bytes per site
+    int *cnt = reinterpret_cast<int *>(ip.p);
+    int *changed = reinterpret_cast<int *>(&ctl->sums[6]);
+    unsigned long long *mx = reinterpret_cast<unsigned long long *>(&ctl->sums[5]);
+    unsigned long long *main_root = reinterpret_cast<unsigned long long *>(&ctl->sums[6]);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(&ctl->sums[7]);
+    cc_init_kernel<<<nb, kT, 0, s>>>(g, lab);
     if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
-    double v[3];
+    // at most a few thousand passes: the labels fall along every path each pass and
+    // pointer jumping shortens the chains; an unfinished search is an error
+    bool done = false;
+    for (int pass = 0; pass < 4096 && !done; ++pass) {
+        if (cudaMemsetAsync(changed, 0, sizeof(int), s) != cudaSuccess) return TDGL_ERR_CUDA;
+        cc_hook_kernel<<<nb, kT, 0, s>>>(g, lab, changed);
+        cc_jump_kernel<<<nb, kT, 0, s>>>(g, lab);
+        int h = 0;
+        if (cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+        done = (h == 0);
+    }
+    if (!done) return TDGL_ERR_NOT_CONVERGED;
+    cc_count_kernel<<<red_grid(g.N), kT, 0, s>>>(g, lab, ctl, blockred);
+    double v[2];
     if (cudaMemcpyAsync(v, &ctl->sums[4], sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
-    *wsum_c = v[0];
-    *n_face0 = v[1];
-    *n_face1 = v[2];
+    const long long ncomp = (long long)v[0], ncond = (long long)v[1];
+    if (ncond < 1) return TDGL_ERR_INVALID_ARG;
+    if (ncomp - 1 > kMaxIslands) return TDGL_ERR_INVALID_ARG;
+    ip.n_isl = (int)(ncomp - 1);
+    if (cudaMemsetAsync(cnt, 0, 4 * (size_t)g.N, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaMemsetAsync(mx, 0, 8, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaMemsetAsync(main_root, 0xFF, 8, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaMemsetAsync(counter, 0, 4, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    cc_size_kernel<<<nb, kT, 0, s>>>(g, lab, cnt);
+    cc_max_kernel<<<nb, kT, 0, s>>>(g, lab, cnt, mx);
+    cc_main_kernel<<<nb, kT, 0, s>>>(g, lab, cnt, mx, main_root);
+    cc_id_kernel<<<nb, kT, 0, s>>>(g, lab, cnt, main_root, counter);
+    cc_comp_kernel<<<nb, kT, 0, s>>>(g, lab, cnt, ip.comp);
+    if (cudaMemsetAsync(ip.isl_w, 0, 8 * (size_t)kMaxIslands, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    comp_weights_kernel<<<red_grid(g.N), kT, 0, s>>>(g, ip.comp, ctl, blockred, ip.isl_w);
+    if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
+    double w[3];
+    if (cudaMemcpyAsync(w, &ctl->sums[4], sizeof(w), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    ip.wsum_c = w[0];
+    ip.n_face0 = w[1];
+    ip.n_face1 = w[2];
     return TDGL_OK;
 }
 
@@ -291,22 +348,57 @@ struct InsArgs {
     DevCtl *ctl;
     double *blockred;
     float *mu, *f, *r, *z, *p, *q;
-    double wsum, wsum_c;
+    const int *comp;
+    const double *isl_w;
+    double *isl_acc;
+    double wsum_c;
 };
 
-// f -= (sum_c w f) / sum_c w on conducting sites, 0 elsewhere; fmax; clear fmean
-// (the level-0 multigrid kernels subtract ctl->fmean, which the preconditioner must not do)
-__global__ void ins_fproj_kernel(InsArgs a)
+// Component sums of w v: the main component's by blocks into sums[slot], each
+// island's by atomics into isl_acc (cleared before the launch).
+__global__ void ins_csum_kernel(InsArgs a, const float *v, int slot)
 {
-    const float c = (float)(a.ctl->fmean * a.wsum / a.wsum_c);
+    double acc = 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        const int c = a.comp[m];
+        if (c < 0) continue;
+        int i, j, k;
+        ijk_of(a.g, m, i, j, k);
+        const double w = (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k));
+        if (c == 0) acc += w * (double)v[m];
+        else atomicAdd(a.isl_acc + (c - 1), w * (double)v[m]);
+    }
+    finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
+}
+
+// v -= its component's weighted mean, 0 on insulating sites.  dslot >= 0: also
+// sums[dslot] = sum w r v.  fmax: also ctl->fmax = max|v| and ctl->fmean = 0 (the
+// level-0 multigrid kernels subtract ctl->fmean, which the preconditioner must not).
+__global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int dslot, int fmax)
+{
+    const float cm = (float)(a.ctl->sums[mslot] / a.wsum_c);
+    double acc = 0.0;
     float mx = 0.f;
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
          m += (long long)gridDim.x * blockDim.x) {
-        const bool ins = (a.g.lk[m] & kLkIns) != 0;
-        const float v = ins ? 0.f : a.f[m] - c;
-        a.f[m] = v;
-        mx = fmaxf(mx, fabsf(v));
+        const int c = a.comp[m];
+        if (c < 0) {
+            v[m] = 0.f;
+            continue;
+        }
+        const float x = v[m] - (c == 0 ? cm : (float)(a.isl_acc[c - 1] / a.isl_w[c - 1]));
+        v[m] = x;
+        mx = fmaxf(mx, fabsf(x));
+        if (dslot >= 0) {
+            int i, j, k;
+            ijk_of(a.g, m, i, j, k);
+            acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) *
+                            a.r[m] * x);
+        }
     }
+    if (dslot >= 0) finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[dslot]);
+    if (!fmax) return;
     __shared__ float shf[32];
     __shared__ int flag;
     const float bm = block_max(mx, shf);
@@ -314,8 +406,8 @@ __global__ void ins_fproj_kernel(InsArgs a)
     if (!last_block(&a.ctl->ticket, gridDim.x, &flag)) return;
     double t = 0.0;
     for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
-        const double v = ((volatile double *)a.blockred)[q];
-        t = v > t ? v : t;
+        const double w = ((volatile double *)a.blockred)[q];
+        t = w > t ? w : t;
     }
     const float tm = block_max((float)t, shf);
     if (threadIdx.x == 0) {
@@ -339,44 +431,6 @@ __global__ void ins_resid_kernel(InsArgs a)
         ijk_of(a.g, m, i, j, k);
         a.r[m] = a.f[m] - masked_lap(a.g, a.mu, m, i, j, k, l);
     }
-}
-
-// sums[slot] = sum_c w v
-__global__ void ins_wsum_kernel(InsArgs a, const float *v, int slot)
-{
-    double acc = 0.0;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
-         m += (long long)gridDim.x * blockDim.x) {
-        if (a.g.lk[m] & kLkIns) continue;
-        int i, j, k;
-        ijk_of(a.g, m, i, j, k);
-        acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) * v[m]);
-    }
-    finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
-}
-
-// v -= sums[mslot] / wsum_c on conducting sites, 0 on insulating ones; when dslot >= 0
-// also sums[dslot] = sum_c w r v (r after the shift of v)
-__global__ void ins_shift_dot_kernel(InsArgs a, float *v, int mslot, int dslot)
-{
-    const float c = (float)(a.ctl->sums[mslot] / a.wsum_c);
-    double acc = 0.0;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
-         m += (long long)gridDim.x * blockDim.x) {
-        if (a.g.lk[m] & kLkIns) {
-            v[m] = 0.f;
-            continue;
-        }
-        const float x = v[m] - c;
-        v[m] = x;
-        if (dslot >= 0) {
-            int i, j, k;
-            ijk_of(a.g, m, i, j, k);
-            acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) *
-                            a.r[m] * x);
-        }
-    }
-    if (dslot >= 0) finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[dslot]);
 }
 
 // p = z + beta p, beta = sums[num] / sums[den] (first: beta = 0)
@@ -457,7 +511,9 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
     a.z = ip.z;
     a.p = ip.p;
     a.q = ip.q;
-    a.wsum = pa.wsum;
+    a.comp = ip.comp;
+    a.isl_w = ip.isl_w;
+    a.isl_acc = ip.isl_acc;
     a.wsum_c = ip.wsum_c;
     const int nb = red_grid(a.g.N);
     const size_t bytes = 4 * (size_t)a.g.N;
@@ -468,17 +524,23 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
     pz.mu = ip.z;
     pz.f = ip.r;
     long long nl = 0;
-    auto precondition = [&](int rzslot) -> bool {
-        if (cudaMemsetAsync(ip.z, 0, bytes, s) != cudaSuccess) return false;
-        if (launch_vcycle(pz, s, &nl) != cudaSuccess) return false;
-        ins_wsum_kernel<<<nb, kT, 0, s>>>(a, ip.z, 4);
-        ins_shift_dot_kernel<<<nb, kT, 0, s>>>(a, ip.z, 4, rzslot);
+    // v -= the weighted mean of v's component (the constants of each component are the
+    // operator's null space)
+    auto project = [&](float *v, int dslot, int fmax) -> bool {
+        if (ip.n_isl > 0 && cudaMemsetAsync(ip.isl_acc, 0, 8 * (size_t)ip.n_isl, s) != cudaSuccess) return false;
+        ins_csum_kernel<<<nb, kT, 0, s>>>(a, v, 4);
+        ins_cshift_kernel<<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
         nl += 2;
         return cudaGetLastError() == cudaSuccess;
     };
-    ins_fproj_kernel<<<nb, kT, 0, s>>>(a);
+    auto precondition = [&](int rzslot) -> bool {
+        if (cudaMemsetAsync(ip.z, 0, bytes, s) != cudaSuccess) return false;
+        if (launch_vcycle(pz, s, &nl) != cudaSuccess) return false;
+        return project(ip.z, rzslot, 0);
+    };
+    if (!project(a.f, -1, 1)) return TDGL_ERR_CUDA;   // compatible right-hand side on every component
     ins_resid_kernel<<<nb, kT, 0, s>>>(a);
-    nl += 2;
+    ++nl;
     if (!precondition(5)) return TDGL_ERR_CUDA;
     ins_dir_kernel<<<nb, kT, 0, s>>>(a, 5, 5, 1);
     ++nl;
@@ -513,28 +575,26 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
         ins_dir_kernel<<<nb, kT, 0, s>>>(a, rzn, rz, 0);
         ++nl;
     }
-    // zero weighted mean over the conducting sites, mu = 0 on insulating ones
-    ins_wsum_kernel<<<nb, kT, 0, s>>>(a, a.mu, 4);
-    ins_shift_dot_kernel<<<nb, kT, 0, s>>>(a, a.mu, 4, -1);
-    nl += 2;
-    if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
+    // zero weighted mean on every component, mu = 0 on insulating sites
+    if (!project(a.mu, -1, 0)) return TDGL_ERR_CUDA;
     *done = it;
     *launches += nl;
     return rc;
 }
 
 // ---------------------------------------------------------------------------
-// E_x from the mean mu of the conducting sites of each open x face
+// E_x from the mean mu of each open x face over the sites of the largest conducting
+// component (islands carry their own constant and no current from face to face)
 // ---------------------------------------------------------------------------
-__global__ void voltage_masked_kernel(DevGrid g, const float *mu, DevCtl *ctl, double *blockred, double hx, double n0,
-                                      double n1)
+__global__ void voltage_masked_kernel(DevGrid g, const float *mu, const int *comp, DevCtl *ctl, double *blockred,
+                                      double hx, double n0, double n1)
 {
     const long long nf = (long long)g.ny * g.nz;
     double acc = 0.0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nf; q += (long long)gridDim.x * blockDim.x) {
         const long long m0 = q * g.nx, m1 = q * g.nx + g.nx - 1;
-        if (!(g.lk[m0] & kLkIns)) acc += (double)mu[m0] / n0;
-        if (!(g.lk[m1] & kLkIns)) acc -= (double)mu[m1] / n1;
+        if (comp[m0] == 0) acc += (double)mu[m0] / n0;
+        if (comp[m1] == 0) acc -= (double)mu[m1] / n1;
     }
     __shared__ double shd[32];
     __shared__ int flag;
@@ -555,7 +615,7 @@ cudaError_t launch_voltage_masked(const PoissonArgs &a, const InsPoisson &ip, cu
     const long long nf = (long long)a.g.ny * a.g.nz;
     int nb = (int)((nf + kT - 1) / kT);
     if (nb > 256) nb = 256;
-    voltage_masked_kernel<<<nb, kT, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.hx, ip.n_face0 > 0 ? ip.n_face0 : 1.0,
+    voltage_masked_kernel<<<nb, kT, 0, s>>>(a.g, a.mu, ip.comp, a.ctl, a.blockred, a.hx, ip.n_face0 > 0 ? ip.n_face0 : 1.0,
                                             ip.n_face1 > 0 ? ip.n_face1 : 1.0);
     return cudaGetLastError();
 }

@@ -76,7 +76,7 @@ int validate(const tdgl_config *c)
 }
 
 struct Layout {
-    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, xzt, lk, insv, Uy, Uz, Py, Pz, total;
+    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, xzt, lk, insv, comp, isl, Uy, Uz, Py, Pz, total;
     int nlevels;
     int ny[kMaxLevels], nz[kMaxLevels], fy[kMaxLevels], fz[kMaxLevels];
     size_t u[kMaxLevels], r[kMaxLevels], tri[kMaxLevels];
@@ -129,6 +129,8 @@ Layout layout(const tdgl_config *c)
     // of the connectivity check, 8 bytes per site, at creation)
     L.lk = c->d_insulating ? take((size_t)N) : 0;
     L.insv = c->d_insulating ? take(16 * (size_t)N) : 0;
+    L.comp = c->d_insulating ? take(4 * (size_t)N) : 0;
+    L.isl = c->d_insulating ? take(16 * (size_t)kMaxIslands) : 0;
     L.Uy = take(8 * (size_t)c->nx);
     L.Uz = take(8 * (size_t)c->nx);
     L.Py = take(8 * (size_t)c->ny);
@@ -350,6 +352,9 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
         h->ip.z = v + N;
         h->ip.p = v + 2 * N;
         h->ip.q = v + 3 * N;
+        h->ip.comp = at<int>(ws, L.comp);
+        h->ip.isl_w = at<double>(ws, L.isl);
+        h->ip.isl_acc = h->ip.isl_w + kMaxIslands;
     }
     h->ctl = at<DevCtl>(ws, L.ctl);
     h->blockred = at<double>(ws, L.blockred);
@@ -464,22 +469,13 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     chk(cudaMemsetAsync(h->mu, 0, 4 * (size_t)N, s));
     chk(cudaMemsetAsync(h->f, 0, 4 * (size_t)N, s));
     if (c.d_insulating && rc == TDGL_OK) {
-        // link bits; the Poisson problem needs one connected conducting domain (its null
-        // space is then the constants), and current injected through the x faces needs
-        // conducting sites on both faces
+        // link bits and conducting components; current injected through the x faces needs
+        // the largest component on both faces
         chk(launch_link_bits(g, c.d_insulating, h->lk, s));
-        if (rc == TDGL_OK && !c.freeze_mu_K) {
-            long long ncomp = 0, ncond = 0;
-            int r2 = conducting_components(g, reinterpret_cast<long long *>(h->ip.r), h->ctl, h->blockred, s, &ncomp,
-                                           &ncond);
-            if (r2 != TDGL_OK) rc = r2;
-            else if (ncomp != 1 || ncond < 1) rc = TDGL_ERR_INVALID_ARG;
-        }
         if (rc == TDGL_OK) {
-            int r2 = conducting_weights(g, h->ctl, h->blockred, s, &h->ip.wsum_c, &h->ip.n_face0, &h->ip.n_face1);
+            int r2 = build_components(g, h->ip, h->ctl, h->blockred, s);
             if (r2 != TDGL_OK) rc = r2;
-            else if (!(h->ip.wsum_c > 0) ||
-                     (c.bc[0] == TDGL_OPEN && c.Jext != 0.0 && (h->ip.n_face0 < 1 || h->ip.n_face1 < 1)))
+            else if (!(h->ip.wsum_c > 0) || (c.bc[0] == TDGL_OPEN && (h->ip.n_face0 < 1 || h->ip.n_face1 < 1)))
                 rc = TDGL_ERR_INVALID_ARG;
         }
     }

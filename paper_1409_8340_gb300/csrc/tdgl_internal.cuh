@@ -293,18 +293,18 @@ cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
 
 // Insulating inclusions (k_insulating.cu)
 cudaError_t launch_link_bits(const DevGrid &g, const uint8_t *ins, uint8_t *lk, cudaStream_t s);
-// Connected components of the conducting sites (lab: long long[N] scratch); returns
-// TDGL_OK and the number of components and of conducting sites, or an error code.
-int conducting_components(const DevGrid &g, long long *lab, DevCtl *ctl, double *blockred, cudaStream_t s,
-                          long long *ncomp, long long *ncond);
-// sum of trapezoid weights over conducting sites, conducting sites on the x = 0 and x = L faces
-int conducting_weights(const DevGrid &g, DevCtl *ctl, double *blockred, cudaStream_t s, double *wsum_c,
-                       double *n_face0, double *n_face1);
+constexpr int kMaxIslands = 1 << 16;   // conducting components besides the largest one
 struct InsPoisson {
     float *r, *z, *p, *q;      // residual, preconditioned residual, direction, A p
-    double wsum_c;             // sum of w over conducting sites
-    double n_face0, n_face1;   // conducting sites on the open-x faces
+    int *comp;                 // [N] 0: largest conducting component, 1..: islands, -1: insulating
+    double *isl_w, *isl_acc;   // [kMaxIslands] sum of w per island, per-island scratch sums
+    int n_isl;                 // islands (conducting components enclosed by insulators)
+    double wsum_c;             // sum of w over the largest component
+    double n_face0, n_face1;   // its sites on the x = 0 and x = L faces
 };
+// Conducting components (labels by propagation in r..z as scratch), their compact ids,
+// and the weights of each; TDGL_ERR_INVALID_ARG beyond kMaxIslands islands.
+int build_components(const DevGrid &g, InsPoisson &ip, DevCtl *ctl, double *blockred, cudaStream_t s);
 // Poisson solve with the links next to insulating sites removed: CG in the trapezoid-
 // weighted inner product, preconditioned by one V-cycle of the plain operator.
 // iters > 0: exactly that many iterations; else up to max_iters until res <= tol

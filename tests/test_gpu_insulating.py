@@ -1,13 +1,14 @@
 """Insulating inclusions (Sec. 3.4 (ii)) on the GPU against the FP64 oracle.
 
 The mask comes from the oracle's pattern generator (insulating spheres and
-cylinders), with any enclosed conducting pocket filled so the conducting sites
-form one domain.  Parity: b and diag M at every site and the first sweep; full
-steps (psi, K, mu, E_x) with fixed sweeps and a tight Poisson tolerance; the
-observables.  Invariants of the GPU path itself: an all-conducting mask gives the
+cylinders).  Parity: b and diag M at every site and the first sweep; full steps
+(psi, K, mu, E_x) with fixed sweeps and a tight Poisson tolerance; the
+observables; conducting islands enclosed by insulators (a spherical shell, two
+slabs cut by insulating planes), where mu has zero weighted mean on every
+component.  Invariants of the GPU path itself: an all-conducting mask gives the
 plain solver's trajectory; insulating tubes along the current leave the Ohmic
-normal state E_x = J_ext.  Refusals: a disconnected conducting domain (unless mu
-is frozen), batches and the adjoint.
+normal state E_x = J_ext.  Refusals: odd nx, an open-x sample whose largest
+conducting component misses a face, the adjoint.
 """
 import dataclasses
 import math
@@ -28,18 +29,13 @@ def shape(kind, c, a, q=(1.0, 0.0, 0.0, 0.0), value=-1.0, flags=2):
 
 
 def insulating_mask(O, p, seed, n=10, rmin=1.0, rmax=2.2):
-    """insulating spheres and a tilted cylinder; enclosed conducting pockets filled"""
+    """insulating spheres and a tilted cylinder"""
     G = oracle_grid(O, p)
     rng = np.random.default_rng(seed)
     box = np.array([p.length(0), p.length(1), max(p.length(2), 0.5)])
     sh = [shape(0, rng.uniform(0, 1, 3) * box, np.full(3, rng.uniform(rmin, rmax))) for _ in range(n)]
     sh.append(shape(2, box / 2, (0.9, 0.9, box.max()), (math.cos(0.4), 0.0, math.sin(0.4), 0.0)))
     _, ins, _, _ = O.pattern_ex(G, sh)
-    G.insulating = ins
-    lab, ncomp = O.conducting_components(G)
-    if ncomp > 1:
-        big = np.bincount(lab[lab >= 0]).argmax()
-        ins = np.where((lab >= 0) & (lab != big), 1, ins).astype(np.uint8)
     return ins
 
 
@@ -152,17 +148,49 @@ def test_insulating_tubes_along_the_current_keep_the_ohmic_state():
     assert abs(s.observables()["Ex"] - p.Jext) < 1e-5
 
 
+def islands(p, kind):
+    ins = np.zeros(p.shape, np.uint8)
+    if kind == "slabs":                          # two slabs, both touching the x faces
+        ins[:, 5, :] = 1
+        ins[:, 15, :] = 1
+        return ins
+    k, j, i = np.meshgrid(np.arange(p.nz), np.arange(p.ny), np.arange(p.nx), indexing="ij")
+    r = np.sqrt((i * p.hx - 9.0) ** 2 + (j * p.hy - 6.0) ** 2 + (k * p.hz - 3.1) ** 2)
+    ins[(r > 2.0) & (r <= 3.0)] = 1              # a spherical shell around a conducting island
+    return ins
+
+
+@pytest.mark.parametrize("kind", ["slabs", "shell"])
+def test_islands_match_the_oracle(O, kind):
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(40, 24, 14, bc=(OP, P, P), Bz=0.25, Jext=0.015, fixed_sweeps=40, poisson_tol=1e-6,
+               poisson_max_cycles=300)
+    ins = islands(p, kind)
+    G = oracle_grid(O, p)
+    G.insulating = ins
+    assert O.conducting_components(G)[1] == 2
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 23).astype(np.complex64).astype(np.complex128)
+    alpha = inclusion_alpha(p, 24)
+    s = solver(p, alpha, ins, psi0)
+    st = O.State(psi0.copy(), np.zeros(p.shape))
+    for n in range(6):
+        s.step(1)
+        so = O.step(G, st, alpha.astype(np.float64), fixed_sweeps=40)
+        psi_g, mu_g = gpu_state(s)
+        assert np.max(np.abs(psi_g - st.psi)) <= TOL_PSI, n
+        assert np.max(np.abs(mu_g - st.mu)) <= 3e-5 * max(1.0, np.max(np.abs(st.mu))), n
+    assert abs(s.observables()["Ex"] - so.Ex) < 2e-5 + 1e-3 * abs(so.Ex)
+
+
 def test_refusals():
     from paper_1409_8340_gb300._lib import TdglError
     from paper_1409_8340_gb300.solver import Params
     p = Params(32, 24, 8, bc=(OP, P, P), Bz=0.2, Jext=0.01)
-    planes = np.zeros(p.shape, np.uint8)
-    planes[:, 5, :] = 1
-    planes[:, 15, :] = 1                         # two slabs: mu would have two null vectors
+    cut = np.zeros(p.shape, np.uint8)
+    cut[:, :, 10] = 1                            # the largest part touches one x face only
     alpha = np.ones(p.shape, np.float32)
     with pytest.raises(TdglError):
-        solver(p, alpha, planes)
-    solver(dataclasses.replace(p, freeze_mu_K=True), alpha, planes).step(2)
+        solver(p, alpha, cut)
     odd = Params(33, 24, 8, bc=(OP, P, P))
     with pytest.raises(TdglError):
         solver(odd, np.ones(odd.shape, np.float32), np.zeros(odd.shape, np.uint8))
