@@ -60,6 +60,8 @@ def parse():
     # profiling captures only (a number printed with these changed is not a bench value)
     ap.add_argument("--nz", type=int, default=256, help="z planes of the grid (profiling captures: a smaller case)")
     ap.add_argument("--fixed-sweeps", type=int, default=0, help="exactly this many sweeps per step (profiling)")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="Jacobi sweep kernel: 1 register-tiled, 2 staged in shared memory, 0 library default")
     return ap.parse_args()
 
 
@@ -73,7 +75,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_jacobi.cu", "sweep_tile.cuh"):
+    for f in ("k_sweep_tma.cu",):
         h.update(open(os.path.join(ROOT, "paper_1409_8340_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -503,6 +505,7 @@ def run_native(args, rank, world, local_rank):
     w = workload(args.J, None if args.nz == 256 else args.nz)
     p = w.params
     p.fixed_sweeps = args.fixed_sweeps
+    p.sweep_kernel = args.sweep_kernel
     alpha, used, marked = pattern(p, w.candidates, w.target_sites, w.alpha_in, w.alpha_out, device=dev)
     psi0 = inputs.random_psi(p.nx, p.ny, p.nz, w.seed + rank).astype(np.complex64)
     s = Solver(p, alpha)
@@ -612,7 +615,7 @@ def run_native(args, rank, world, local_rank):
                                   "sweeps": prof["ms_sweeps"] / args.steps, "K": prof["ms_K"] / args.steps,
                                   "poisson": prof["ms_poisson"] / args.steps},
             "implicit_step_gsite_iter_s": site_iters / (implicit_ms * 1e-3) / 1e9 if implicit_ms > 0 else None,
-            "roofline": {"kernel": "sweep_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": "sweep_tma_kernel" if p.sweep_kernel != 1 else "sweep2_kernel<0>", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_sweep_ms,
                          "traffic": traffic_from_profile()},

@@ -99,6 +99,14 @@ extern "C" {
  *                   tdgl_set_state / tdgl_upload_state.
  *   noise_seed      key of the noise generator.
  *   Bx              field along x (Eq. B_xz), TDGL_LINKS_XZ only (0 otherwise).
+ *   sweep_kernel    Jacobi sweep kernel: 1 register-tiled (two sites per thread,
+ *                   the next plane prefetched in registers); 2 staged in shared
+ *                   memory by the tensor memory accelerator (a producer thread
+ *                   keeps three planes of boxes in flight; Landau yz links, no
+ *                   insulating sites, even nx, else the register-tiled kernel
+ *                   runs); 0 the default, which is 2.  Both give the same iterates
+ *                   (same arithmetic, same order).
+ *   reserved1       0.
  *   d_insulating    device u8[N] or NULL: nonzero marks an insulating site
  *                   (Sec. 3.4 (ii), e.g. the mask of tdgl_pattern_ex).  Every link
  *                   that touches an insulating site carries no current: it leaves
@@ -142,6 +150,8 @@ typedef struct tdgl_config {
     const float *d_alpha;
     const float *d_link_phase;
     const uint8_t *d_insulating;
+    int32_t sweep_kernel;
+    int32_t reserved1;
 } tdgl_config;
 
 typedef struct tdgl_handle tdgl_handle;

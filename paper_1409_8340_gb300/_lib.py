@@ -58,6 +58,7 @@ class Config(ctypes.Structure):
         ("d_alpha", ctypes.c_void_p),
         ("d_link_phase", ctypes.c_void_p),
         ("d_insulating", ctypes.c_void_p),
+        ("sweep_kernel", ctypes.c_int32), ("reserved1", ctypes.c_int32),
     ]
 
 

@@ -1,0 +1,386 @@
+// Jacobi sweep (arXiv:1409.8340, Sec. 3.1, Eq. final and Eq. convergence) with
+// its tile staged in shared memory by the tensor memory accelerator.
+//
+// A block owns 64 x-sites by 8 rows and marches along z.  One producer thread
+// streams, per z plane, three boxes into a ring of five plane stages with
+// cp.async.bulk.tensor: psi over 68 x-sites (the tile and one site beyond each
+// end, on 16-byte boundaries) by 10 rows (the tile and its y halo), and the
+// tile's b and diag M; each stage completes an mbarrier by transaction bytes.
+// Eight consumer warps (one row each, two sites per lane) read the plane below,
+// the plane and the plane above from the ring, write the new iterate to global
+// memory and release the plane below through a second mbarrier per stage.  The
+// ring keeps three planes in flight ahead of the consumers without holding them
+// in registers.  Box parts outside the grid arrive as zeros; the few neighbours
+// across a periodic wrap (the x ends of the first and last tiles, the y halo of
+// the first and last row tiles) are read from global memory by the lanes that
+// need them.  Arithmetic per site is the register-tiled kernel's, in the same
+// order.  Every wait is bounded by the global timer; a wait that runs out sets
+// TDGL_ERR_TIMEOUT and ends the sweep, and the producer drains its copies in
+// flight (again bounded) before the block exits.
+//
+// Landau links of the yz plane, no insulating sites, even nx.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <float.h>
+
+#include "sweep_tile.cuh"
+#include "tdgl_internal.cuh"
+
+namespace tdgl {
+
+namespace {
+
+constexpr int kTR = 8;            // rows per block (consumer warps)
+constexpr int kTX = 64;           // x-sites per block
+constexpr int kTS = 5;            // ring stages (planes)
+constexpr int kRowP = kTX + 4;    // psi row in a stage: [2 halo | 64 | 2 halo]
+constexpr int kThreads = (kTR + 1) * 32;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s: far beyond any plane's copy time
+
+struct Stage {
+    float2 psi[kTR + 2][kRowP];   // 5440 bytes, padded to a 128-byte boundary
+    float2 pad[8];
+    float2 b[kTR][kTX];
+    float2 D[kTR][kTX];
+};
+static_assert(sizeof(Stage) % 128 == 0, "stages on 128-byte boundaries");
+static_assert(offsetof(Stage, b) % 128 == 0 && offsetof(Stage, D) % 128 == 0, "boxes on 128-byte boundaries");
+constexpr unsigned kPlaneBytes = (kTR + 2) * kRowP * 8 + 2 * kTR * kTX * 8;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for the phase of the given parity to complete; false when the deadline passes
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long deadline)
+{
+    for (unsigned it = 0;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 255u) == 255u && gtime() > deadline) return false;
+    }
+}
+
+// one box of a 3-D tensor map at (x, y, z) into shared memory
+__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                         unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+}  // namespace
+
+// Tile geometry shared by the producer and the consumers.
+struct TmaTile {
+    int x0, w;       // first x-site, valid x-sites (even)
+    int j0, nr;      // first row, valid rows
+};
+
+__device__ __forceinline__ int plane_of(const DevGrid &g, int z)
+{
+    if (z < 0) return (g.bcz == kPeriodic) ? z + g.nz : (g.nz >= 2 ? 1 : 0);
+    if (z >= g.nz) return (g.bcz == kPeriodic) ? z - g.nz : (g.nz >= 2 ? g.nz - 2 : 0);
+    return z;
+}
+
+__device__ __forceinline__ int row_of(const DevGrid &g, int y)
+{
+    if (y < 0) return (g.bcy == kPeriodic) ? y + g.ny : 0;
+    if (y >= g.ny) return (g.bcy == kPeriodic) ? y - g.ny : g.ny - 1;
+    return y;
+}
+
+// Producer: the three boxes of plane z into stage S.  x starts two sites before the
+// tile (even, as the tensor memory accelerator requires of 8-byte elements).
+__device__ __forceinline__ void issue_plane(const TmaTile &T, int zp, Stage &S, unsigned long long *full,
+                                           const CUtensorMap *mp, const CUtensorMap *mb, const CUtensorMap *md)
+{
+    mbar_expect(full, kPlaneBytes);
+    tma_load3(&S.psi[0][0], mp, T.x0 - 2, T.j0 - 1, zp, full);
+    tma_load3(&S.b[0][0], mb, T.x0, T.j0, zp, full);
+    tma_load3(&S.D[0][0], md, T.x0, T.j0, zp, full);
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
+    sweep_tma_kernel(SweepArgs a, int kz, const __grid_constant__ CUtensorMap map_psi,
+                     const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_D)
+{
+    if (*(volatile int *)&a.ctl->done) return;
+    extern __shared__ __align__(128) unsigned char tma_smem[];
+    Stage *ring = reinterpret_cast<Stage *>(tma_smem);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(tma_smem + kTS * sizeof(Stage));
+    unsigned long long *empty = full + kTS;
+    __shared__ int failed;
+
+    const DevGrid &g = a.g;
+    TmaTile T;
+    T.x0 = blockIdx.x * kTX;
+    T.w = min(kTX, g.nx - T.x0);
+    T.j0 = blockIdx.y * kTR;
+    T.nr = min(kTR, g.ny - T.j0);
+    const int k0 = blockIdx.z * kz, k1 = min(k0 + kz, g.nz);
+    const int nplanes = (k1 - k0) + 2;   // k0 - 1 .. k1
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kTR);
+        }
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const unsigned long long deadline = gtime() + kWaitNs;
+    float rmax = 0.f;
+
+    if (warp == kTR) {
+        // ---------------- producer (one thread) ----------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int t = 0; t < nplanes; ++t) {
+                const int s = t % kTS;
+                if (t >= kTS && (!mbar_wait(&empty[s], (unsigned)((t / kTS - 1) & 1), deadline) ||
+                                 *(volatile int *)&failed)) {
+                    failed = 1;
+                    break;
+                }
+                issue_plane(T, plane_of(g, k0 - 1 + t), ring[s], &full[s], &map_psi, &map_b, &map_D);
+                issued = t + 1;
+            }
+            // drain: every issued plane's copies complete before the block can exit
+            for (int t = max(0, issued - kTS); t < issued; ++t)
+                mbar_wait(&full[t % kTS], (unsigned)((t / kTS) & 1), deadline + kWaitNs);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- consumers: row `warp`, sites x, x+1 ----------------
+        const int r = warp;
+        const int x = T.x0 + 2 * lane, j = T.j0 + r;
+        const bool in = (r < T.nr) && (2 * lane < T.w);
+        const bool xper = (g.bcx == kPeriodic), yper = (g.bcy == kPeriodic), zper = (g.bcz == kPeriodic);
+        const bool xlo = (x == 0), xhi = (x + 2 >= g.nx);
+        const bool ylo = (j == 0), yhi = (j == g.ny - 1);
+        const bool zact = g.nz >= 2;
+        const int jc = min(j, g.ny - 1);
+        const float wy_f = yper ? 1.f : (ylo ? 2.f : (yhi ? 0.f : 1.f));
+        const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
+        const bool yedge = (wy_f != 1.f) || (wy_b != 1.f);
+        float2 yf0 = cmk(0.f, 0.f), yf1 = yf0, zf0 = yf0, zf1 = yf0;
+        if (in) {
+            const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
+            const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
+            const float sy = g.ht2 * g.cy, szc = g.ht2 * g.cz;
+            yf0 = cscale(sy, lo2(uy));
+            yf1 = cscale(sy, hi2(uy));
+            zf0 = cscale(szc, lo2(uz));
+            zf1 = cscale(szc, hi2(uz));
+        }
+        const float2 xf = cscale(g.ht2 * g.cx, ldx<false>(&a.ctl->Ux));
+        float4 *__restrict__ dst = reinterpret_cast<float4 *>(a.dst);
+        const long long rowq = g.nx >> 1, plq = rowq * g.ny;
+        const long long q0 = (x >> 1) + rowq * jc;
+        bool ok = true;
+        for (int t = 1; t + 1 < nplanes; ++t) {
+            const int k = k0 - 1 + t;
+            if (t == 1) {
+                ok = mbar_wait(&full[0], 0u, deadline) && mbar_wait(&full[1], 0u, deadline);
+            }
+            ok = ok && mbar_wait(&full[(t + 1) % kTS], (unsigned)(((t + 1) / kTS) & 1), deadline);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) failed = 1;
+                break;
+            }
+            const Stage &Pm = ring[(t - 1) % kTS], &Pc = ring[t % kTS], &Pp = ring[(t + 1) % kTS];
+            if (in) {
+                const int cx = 2 + 2 * lane;
+                const float4 pc = *reinterpret_cast<const float4 *>(&Pc.psi[r + 1][cx]);
+                const float2 c0 = lo2(pc), c1 = hi2(pc);
+                float2 xl = Pc.psi[r + 1][cx - 1], xr = Pc.psi[r + 1][cx + 2];
+                float4 yf = *reinterpret_cast<const float4 *>(&Pc.psi[r + 2][cx]);
+                float4 yb = *reinterpret_cast<const float4 *>(&Pc.psi[r][cx]);
+                // neighbours across a periodic wrap lie outside the boxes: read them directly
+                const long long rowk = (long long)k * g.ny;
+                if (xper && xlo) xl = a.src[(rowk + j) * g.nx + g.nx - 1];
+                if (xper && xhi) xr = a.src[(rowk + j) * g.nx];
+                if (yper && ylo) yb = reinterpret_cast<const float4 *>(a.src)[((rowk + g.ny - 1) * g.nx + x) >> 1];
+                if (yper && yhi) yf = reinterpret_cast<const float4 *>(a.src)[(rowk * g.nx + x) >> 1];
+                const float4 bc = *reinterpret_cast<const float4 *>(&Pc.b[r][2 * lane]);
+                const float4 Dc = *reinterpret_cast<const float4 *>(&Pc.D[r][2 * lane]);
+                // the same boundary rules and arithmetic order as the tiled kernel (MODE 0)
+                float2 xl0 = xl, xr1 = xr, c1x = c1, c0x = c0;
+                if (xlo || xhi) {
+                    if (xper) {
+                        const float2 P = cmul(g.Py[jc], g.Pz[k]);
+                        if (xlo) xl0 = cmul(P, xl);
+                        if (xhi) xr1 = cmulc(P, xr);
+                    } else {
+                        if (xlo) {
+                            c1x = cscale(2.f, c1);
+                            xl0 = cmk(0.f, 0.f);
+                        }
+                        if (xhi) {
+                            c0x = cscale(2.f, c0);
+                            xr1 = cmk(0.f, 0.f);
+                        }
+                    }
+                }
+                float2 yf_0 = lo2(yf), yf_1 = hi2(yf), yb_0 = lo2(yb), yb_1 = hi2(yb);
+                if (yedge) {
+                    yf_0 = cscale(wy_f, yf_0);
+                    yf_1 = cscale(wy_f, yf_1);
+                    yb_0 = cscale(wy_b, yb_0);
+                    yb_1 = cscale(wy_b, yb_1);
+                }
+                float2 ns0 = cmul(xf, c1x), ns1 = cmulc(xf, c0x);
+                cfmac(ns0, xf, xl0);
+                cfma(ns1, xf, xr1);
+                cfma(ns0, yf0, yf_0);
+                cfmac(ns0, yf0, yb_0);
+                cfma(ns1, yf1, yf_1);
+                cfmac(ns1, yf1, yb_1);
+                if (zact) {
+                    const float4 pzp = *reinterpret_cast<const float4 *>(&Pp.psi[r + 1][cx]);
+                    const float4 pzm = *reinterpret_cast<const float4 *>(&Pm.psi[r + 1][cx]);
+                    float wz_f = 1.f, wz_b = 1.f;
+                    if (!zper) {
+                        if (k == 0) {
+                            wz_f = 2.f;
+                            wz_b = 0.f;
+                        } else if (k == g.nz - 1) {
+                            wz_f = 0.f;
+                            wz_b = 2.f;
+                        }
+                    }
+                    const float4 zpp =
+                        (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
+                    const float4 zmm =
+                        (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
+                    cfma(ns0, zf0, lo2(zpp));
+                    cfmac(ns0, zf0, lo2(zmm));
+                    cfma(ns1, zf1, hi2(zpp));
+                    cfmac(ns1, zf1, hi2(zmm));
+                }
+                const float2 b0 = lo2(bc), b1 = hi2(bc), D0 = lo2(Dc), D1 = hi2(Dc);
+                const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
+                const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
+                const float2 n0 = cscale(__frcp_rn(cabs2(D0)), cmulc(D0, s0));
+                const float2 n1 = cscale(__frcp_rn(cabs2(D1)), cmulc(D1, s1));
+                dst[q0 + plq * k] = make_float4(n0.x, n0.y, n1.x, n1.y);
+                float r2a = cabs2(r0), r2b = cabs2(r1);
+                r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
+                r2b = (r2b <= FLT_MAX) ? r2b : INFINITY;
+                rmax = fmaxf(rmax, fmaxf(r2a, r2b));
+            }
+            // the plane below is no longer needed by this warp
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[(t - 1) % kTS]);
+        }
+    }
+    __syncthreads();
+    if (failed) {
+        if (threadIdx.x == 0) {
+            a.ctl->status = TDGL_ERR_TIMEOUT;
+            a.ctl->done = 1;
+        }
+        return;   // every thread of the block returns here: the finishing reduction is skipped
+    }
+    finish_sweep_at(a, rmax, false, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                    gridDim.x * gridDim.y * gridDim.z);
+}
+
+bool tma_sweep_supported(const DevGrid &g)
+{
+    return g.L == nullptr && g.lk == nullptr && g.Xj == nullptr && (g.nx % 2) == 0;
+}
+
+size_t tma_sweep_smem() { return kTS * sizeof(Stage) + 2 * kTS * sizeof(unsigned long long); }
+
+// Tensor map of one complex64 field (nx, ny, nz) with the given box; false on failure.
+bool tma_encode_field(const DevGrid &g, const float2 *base, int box_x, int box_y, CUtensorMap *out)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 8, (cuuint64_t)g.nx * g.ny * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<float2 *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tma_encode_maps(const DevGrid &g, float2 *const psi[3], const float2 *b, const float2 *D, TmaMaps *m)
+{
+    for (int q = 0; q < 3; ++q)
+        if (!tma_encode_field(g, psi[q], kRowP, kTR + 2, &m->psi[q])) return false;
+    return tma_encode_field(g, b, kTX, kTR, &m->b) && tma_encode_field(g, D, kTX, kTR, &m->D);
+}
+
+static int tma_kz(const DevGrid &g)
+{
+    const long long bxy = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTR - 1) / kTR);
+    long long kz = (bxy * g.nz) / 1824;   // about 1824 blocks (four waves of three per SM) or more
+    if (kz < 2) kz = 2;
+    if (kz > 32) kz = 32;
+    return (int)kz;
+}
+
+cudaError_t launch_sweep_tma(const SweepArgs &a, const CUtensorMap &map_psi, const TmaMaps &m, cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t smem = tma_sweep_smem();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int kz = tma_kz(a.g);
+    const dim3 grid((a.g.nx + kTX - 1) / kTX, (a.g.ny + kTR - 1) / kTR, (a.g.nz + kz - 1) / kz);
+    sweep_tma_kernel<<<grid, kThreads, smem, s>>>(a, kz, map_psi, m.b, m.D);
+    return cudaGetLastError();
+}
+
+}  // namespace tdgl

@@ -44,6 +44,7 @@ int validate(const tdgl_config *c)
     if (!(c->u > 0) || !(c->beta >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->max_iter < 1 || c->check_every < 1 || c->fixed_sweeps < 0) return TDGL_ERR_INVALID_ARG;
     if (c->sweeps_per_pass < 0 || c->sweeps_per_pass > 2) return TDGL_ERR_INVALID_ARG;
+    if (c->sweep_kernel < 0 || c->sweep_kernel > 2) return TDGL_ERR_INVALID_ARG;
     if (!(c->noise_T >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->fixed_sweeps == 0 && !(c->eps > 0)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_cycles < 1 || c->poisson_max_cycles < c->poisson_cycles) return TDGL_ERR_INVALID_ARG;
@@ -366,6 +367,11 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     h->f = at<float>(ws, L.f);
     h->links = g.L ? at<float2>(ws, L.links) : nullptr;
     h->nblockred = L.nblockred;
+    // Jacobi sweep kernel: 1 register-tiled; 2 or 0 (default) staged in shared memory by the
+    // tensor memory accelerator where it applies (Landau yz links, no insulating sites, even
+    // nx), measured faster at every size tried; the register-tiled kernel elsewhere
+    h->use_tma = (c.sweep_kernel != 1 && tma_sweep_supported(g)) ? 1 : 0;
+    if (h->use_tma && !tma_encode_maps(g, h->psi, h->b, h->D, &h->tmaps)) h->use_tma = 0;
     h->batch_owned = 0;
     {
         // h_t zeta_max, zeta_max = (T_zeta / (h_t hx hy hz))^(1/2) (Sec. 3.1.2); a film drops hz
@@ -677,7 +683,15 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
                 a.src = odd ? h->psi[ia] : h->psi[ib];
                 a.dst = odd ? h->psi[ib] : h->psi[ia];
                 a.dst_index = odd ? ib : ia;
-                if (launch_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+                cudaError_t e;
+                if (h->use_tma) {
+                    int src = 0;
+                    while (src < 2 && h->psi[src] != a.src) ++src;
+                    e = launch_sweep_tma(a, h->tmaps.psi[src], h->tmaps, s);
+                } else {
+                    e = launch_sweep(a, s);
+                }
+                if (e != cudaSuccess) return TDGL_ERR_CUDA;
                 ++launched;
                 ++q;
             }

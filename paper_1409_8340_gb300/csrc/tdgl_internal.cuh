@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of the solver.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -215,6 +216,14 @@ cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
 // one sweep src -> dst that neither tests nor touches the control block
 cudaError_t launch_sweep_redo(const SweepArgs &a, cudaStream_t s);
+// the Jacobi sweep with its tile staged in shared memory by the tensor memory
+// accelerator (k_sweep_tma.cu); tensor maps of the psi buffers, b and diag M
+struct TmaMaps {
+    CUtensorMap psi[3], b, D;
+};
+bool tma_sweep_supported(const DevGrid &g);
+bool tma_encode_maps(const DevGrid &g, float2 *const psi[3], const float2 *b, const float2 *D, TmaMaps *m);
+cudaError_t launch_sweep_tma(const SweepArgs &a, const CUtensorMap &map_psi, const TmaMaps &m, cudaStream_t s);
 int sweep_blocks(const DevGrid &g);
 // two sweeps per pass (k_pair.cu); the decision is the per-sweep one
 bool pair_supported(const DevGrid &g);
@@ -405,6 +414,8 @@ struct tdgl_handle {
     double dtK;
     double last_javg;
     uint8_t *lk;               // link bits when insulating sites are given, else nullptr
+    int use_tma;               // 1: Jacobi sweeps by the shared-memory staged kernel
+    tdgl::TmaMaps tmaps;       // its tensor maps
     tdgl::InsPoisson ip;
     // profiling
     int prof_on;

@@ -46,6 +46,7 @@ class Params:
     xz_gauge: bool = False         # field (Bx, 0, Bz) in the Landau gauge of Eq. A_xz (By must be 0)
     Bx: float = 0.0
     sweeps_per_pass: int = 1       # 2: temporal blocking, two Jacobi sweeps per pass over memory
+    sweep_kernel: int = 0          # 1 register-tiled, 2 staged in shared memory by bulk copies, 0 default
     noise_T: float = 0.0           # thermal noise parameter T_zeta (Sec. 3.1.2); 0: none
     noise_seed: int = 0
 
@@ -86,6 +87,7 @@ class Params:
                         _lib.LINKS_XZ if self.xz_gauge else _lib.LINKS_LANDAU)
         c.Bx = float(self.Bx)
         c.sweeps_per_pass = int(self.sweeps_per_pass)
+        c.sweep_kernel = int(self.sweep_kernel)
         c.noise_T = float(self.noise_T)
         c.noise_seed = int(self.noise_seed) & 0xFFFFFFFFFFFFFFFF
         c.d_alpha = d_alpha
