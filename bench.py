@@ -349,7 +349,7 @@ def xz_mode(dev, steps: int = 20, relax: int = 20, quanta_x: int = 600):
             "ms_per_step": ms / steps, "sweeps_per_step": prof["sweeps"] / max(1, prof["steps"]),
             "phase_ms_per_step": {"init_sweep": prof["ms_init"] / steps, "sweeps": prof["ms_sweeps"] / steps,
                                   "K": prof["ms_K"] / steps, "poisson": prof["ms_poisson"] / steps},
-            "sweep_roofline": {"kernel": "sweep2_kernel<0, XZ>", "bound": "hbm", "bytes_per_launch": bpl,
+            "sweep_roofline": {"kernel": "sweep_tma_kernel<XZ>", "bound": "hbm", "bytes_per_launch": bpl,
                                "avg_launch_ms": sweep_ms, "achieved": bpl / (sweep_ms * 1e-3) / 1e9,
                                "peak": peak, "unit": "GB/s", "frac": bpl / (sweep_ms * 1e-3) / 1e9 / peak,
                                "peak_source": peak_kind},
@@ -408,7 +408,7 @@ def insulating_mode(dev, steps: int = 20, relax: int = 20):
             "ms_per_step": ms / steps, "sweeps_per_step": prof["sweeps"] / max(1, prof["steps"]),
             "phase_ms_per_step": {"init_sweep": prof["ms_init"] / steps, "sweeps": prof["ms_sweeps"] / steps,
                                   "K": prof["ms_K"] / steps, "poisson": prof["ms_poisson"] / steps},
-            "sweep_roofline": {"kernel": "sweep2_kernel<0, MASK>", "bound": "hbm", "bytes_per_launch": bpl,
+            "sweep_roofline": {"kernel": "sweep_tma_kernel<MASK>", "bound": "hbm", "bytes_per_launch": bpl,
                                "avg_launch_ms": sweep_ms, "achieved": bpl / (sweep_ms * 1e-3) / 1e9,
                                "peak": peak, "unit": "GB/s", "frac": bpl / (sweep_ms * 1e-3) / 1e9 / peak,
                                "peak_source": peak_kind},

@@ -102,10 +102,10 @@ extern "C" {
  *   sweep_kernel    Jacobi sweep kernel: 1 register-tiled (two sites per thread,
  *                   the next plane prefetched in registers); 2 staged in shared
  *                   memory by the tensor memory accelerator (a producer thread
- *                   keeps three planes of boxes in flight; Landau yz links, no
- *                   insulating sites, even nx, else the register-tiled kernel
- *                   runs); 0 the default, which is 2.  Both give the same iterates
- *                   (same arithmetic, same order).
+ *                   keeps three planes of boxes in flight; Landau links of either
+ *                   plane, with or without insulating sites, even nx, else the
+ *                   register-tiled kernel runs); 0 the default, which is 2.  Both
+ *                   give the same iterates (same arithmetic, same order).
  *   reserved1       0.
  *   d_insulating    device u8[N] or NULL: nonzero marks an insulating site
  *                   (Sec. 3.4 (ii), e.g. the mask of tdgl_pattern_ex).  Every link

@@ -18,7 +18,8 @@
 // TDGL_ERR_TIMEOUT and ends the sweep, and the producer drains its copies in
 // flight (again bounded) before the block exits.
 //
-// Landau links of the yz plane, no insulating sites, even nx.
+// Landau links of either plane (XZ: the j-indexed tables and the y wrap of the
+// xz gauge), insulating sites (MASK: link bits, read per site pair), even nx.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <float.h>
@@ -135,6 +136,7 @@ __device__ __forceinline__ void issue_plane(const TmaTile &T, int zp, Stage &S, 
     tma_load3(&S.D[0][0], md, T.x0, T.j0, zp, full);
 }
 
+template <bool XZ, bool MASK>
 __global__ void __launch_bounds__(kThreads, 3)
     sweep_tma_kernel(SweepArgs a, int kz, const __grid_constant__ CUtensorMap map_psi,
                      const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_D)
@@ -201,16 +203,26 @@ __global__ void __launch_bounds__(kThreads, 3)
         const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
         const bool yedge = (wy_f != 1.f) || (wy_b != 1.f);
         float2 yf0 = cmk(0.f, 0.f), yf1 = yf0, zf0 = yf0, zf1 = yf0;
+        const bool ywrap = XZ && yper && (ylo || yhi);   // a row next to the xz gauge's y wrap
+        float4 wxq = make_float4(1.f, 0.f, 1.f, 0.f);
         if (in) {
-            const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
-            const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
             const float sy = g.ht2 * g.cy, szc = g.ht2 * g.cz;
-            yf0 = cscale(sy, lo2(uy));
-            yf1 = cscale(sy, hi2(uy));
-            zf0 = cscale(szc, lo2(uz));
-            zf1 = cscale(szc, hi2(uz));
+            if (XZ) {
+                yf0 = yf1 = cmk(sy, 0.f);
+                zf0 = zf1 = cscale(szc, g.Zj[jc]);
+                if (ywrap) wxq = reinterpret_cast<const float4 *>(g.Wx)[x >> 1];
+            } else {
+                const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
+                const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
+                yf0 = cscale(sy, lo2(uy));
+                yf1 = cscale(sy, hi2(uy));
+                zf0 = cscale(szc, lo2(uz));
+                zf1 = cscale(szc, hi2(uz));
+            }
         }
-        const float2 xf = cscale(g.ht2 * g.cx, ldx<false>(&a.ctl->Ux));
+        const float2 Ux = ldx<false>(&a.ctl->Ux);
+        const float2 xf = cscale(g.ht2 * g.cx, XZ ? cmul(Ux, g.Xj[jc]) : Ux);
+        const uchar2 *__restrict__ lk2 = reinterpret_cast<const uchar2 *>(g.lk);
         float4 *__restrict__ dst = reinterpret_cast<float4 *>(a.dst);
         const long long rowq = g.nx >> 1, plq = rowq * g.ny;
         const long long q0 = (x >> 1) + rowq * jc;
@@ -227,6 +239,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             }
             const Stage &Pm = ring[(t - 1) % kTS], &Pc = ring[t % kTS], &Pp = ring[(t + 1) % kTS];
             if (in) {
+                const uchar2 lkc = MASK ? lk2[q0 + plq * k] : make_uchar2(0x3f, 0x3f);
                 const int cx = 2 + 2 * lane;
                 const float4 pc = *reinterpret_cast<const float4 *>(&Pc.psi[r + 1][cx]);
                 const float2 c0 = lo2(pc), c1 = hi2(pc);
@@ -245,9 +258,11 @@ __global__ void __launch_bounds__(kThreads, 3)
                 float2 xl0 = xl, xr1 = xr, c1x = c1, c0x = c0;
                 if (xlo || xhi) {
                     if (xper) {
-                        const float2 P = cmul(g.Py[jc], g.Pz[k]);
-                        if (xlo) xl0 = cmul(P, xl);
-                        if (xhi) xr1 = cmulc(P, xr);
+                        if (!XZ) {   // the yz gauge's wrap link carries conj(P_jk); the xz gauge's is plain
+                            const float2 P = cmul(g.Py[jc], g.Pz[k]);
+                            if (xlo) xl0 = cmul(P, xl);
+                            if (xhi) xr1 = cmulc(P, xr);
+                        }
                     } else {
                         if (xlo) {
                             c1x = cscale(2.f, c1);
@@ -260,11 +275,34 @@ __global__ void __launch_bounds__(kThreads, 3)
                     }
                 }
                 float2 yf_0 = lo2(yf), yf_1 = hi2(yf), yb_0 = lo2(yb), yb_1 = hi2(yb);
+                if (ywrap) {   // xz gauge: wrap link W = Wx[i] Wz[k] from row ny-1 to row 0
+                    const float2 wz = g.Wz[k];
+                    const float2 W0 = cmul(lo2(wxq), wz), W1 = cmul(hi2(wxq), wz);
+                    if (yhi) {
+                        yf_0 = cmul(W0, yf_0);
+                        yf_1 = cmul(W1, yf_1);
+                    }
+                    if (ylo) {
+                        yb_0 = cmulc(W0, yb_0);
+                        yb_1 = cmulc(W1, yb_1);
+                    }
+                }
                 if (yedge) {
                     yf_0 = cscale(wy_f, yf_0);
                     yf_1 = cscale(wy_f, yf_1);
                     yb_0 = cscale(wy_b, yb_0);
                     yb_1 = cscale(wy_b, yb_1);
+                }
+                if (MASK) {   // links next to insulating sites removed
+                    const unsigned l0 = lkc.x, l1 = lkc.y;
+                    c1x = cscale((l0 & kLkXp) ? 1.f : 0.f, c1x);
+                    xl0 = cscale((l0 & kLkXm) ? 1.f : 0.f, xl0);
+                    xr1 = cscale((l1 & kLkXp) ? 1.f : 0.f, xr1);
+                    c0x = cscale((l1 & kLkXm) ? 1.f : 0.f, c0x);
+                    yf_0 = cscale((l0 & kLkYp) ? 1.f : 0.f, yf_0);
+                    yb_0 = cscale((l0 & kLkYm) ? 1.f : 0.f, yb_0);
+                    yf_1 = cscale((l1 & kLkYp) ? 1.f : 0.f, yf_1);
+                    yb_1 = cscale((l1 & kLkYm) ? 1.f : 0.f, yb_1);
                 }
                 float2 ns0 = cmul(xf, c1x), ns1 = cmulc(xf, c0x);
                 cfmac(ns0, xf, xl0);
@@ -286,10 +324,16 @@ __global__ void __launch_bounds__(kThreads, 3)
                             wz_b = 2.f;
                         }
                     }
-                    const float4 zpp =
+                    float4 zpp =
                         (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
-                    const float4 zmm =
+                    float4 zmm =
                         (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
+                    if (MASK) {
+                        const float f0 = (lkc.x & kLkZp) ? 1.f : 0.f, b0 = (lkc.x & kLkZm) ? 1.f : 0.f;
+                        const float f1 = (lkc.y & kLkZp) ? 1.f : 0.f, b1 = (lkc.y & kLkZm) ? 1.f : 0.f;
+                        zpp = make_float4(f0 * zpp.x, f0 * zpp.y, f1 * zpp.z, f1 * zpp.w);
+                        zmm = make_float4(b0 * zmm.x, b0 * zmm.y, b1 * zmm.z, b1 * zmm.w);
+                    }
                     cfma(ns0, zf0, lo2(zpp));
                     cfmac(ns0, zf0, lo2(zmm));
                     cfma(ns1, zf1, hi2(zpp));
@@ -323,10 +367,7 @@ __global__ void __launch_bounds__(kThreads, 3)
                     gridDim.x * gridDim.y * gridDim.z);
 }
 
-bool tma_sweep_supported(const DevGrid &g)
-{
-    return g.L == nullptr && g.lk == nullptr && g.Xj == nullptr && (g.nx % 2) == 0;
-}
+bool tma_sweep_supported(const DevGrid &g) { return (g.L == nullptr || g.Xj != nullptr) && (g.nx % 2) == 0; }
 
 size_t tma_sweep_smem() { return kTS * sizeof(Stage) + 2 * kTS * sizeof(unsigned long long); }
 
@@ -368,19 +409,30 @@ static int tma_kz(const DevGrid &g)
     return (int)kz;
 }
 
-cudaError_t launch_sweep_tma(const SweepArgs &a, const CUtensorMap &map_psi, const TmaMaps &m, cudaStream_t s)
+template <bool XZ, bool MASK>
+static cudaError_t launch_variant(const SweepArgs &a, const CUtensorMap &map_psi, const TmaMaps &m, cudaStream_t s)
 {
     static bool attr = false;
     const size_t smem = tma_sweep_smem();
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(sweep_tma_kernel<XZ, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int kz = tma_kz(a.g);
     const dim3 grid((a.g.nx + kTX - 1) / kTX, (a.g.ny + kTR - 1) / kTR, (a.g.nz + kz - 1) / kz);
-    sweep_tma_kernel<<<grid, kThreads, smem, s>>>(a, kz, map_psi, m.b, m.D);
+    sweep_tma_kernel<XZ, MASK><<<grid, kThreads, smem, s>>>(a, kz, map_psi, m.b, m.D);
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_tma(const SweepArgs &a, const CUtensorMap &map_psi, const TmaMaps &m, cudaStream_t s)
+{
+    const bool xz = a.g.Xj != nullptr, mk = a.g.lk != nullptr;
+    if (xz && mk) return launch_variant<true, true>(a, map_psi, m, s);
+    if (xz) return launch_variant<true, false>(a, map_psi, m, s);
+    if (mk) return launch_variant<false, true>(a, map_psi, m, s);
+    return launch_variant<false, false>(a, map_psi, m, s);
 }
 
 }  // namespace tdgl

@@ -368,8 +368,8 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     h->links = g.L ? at<float2>(ws, L.links) : nullptr;
     h->nblockred = L.nblockred;
     // Jacobi sweep kernel: 1 register-tiled; 2 or 0 (default) staged in shared memory by the
-    // tensor memory accelerator where it applies (Landau yz links, no insulating sites, even
-    // nx), measured faster at every size tried; the register-tiled kernel elsewhere
+    // tensor memory accelerator where it applies (Landau links of either plane, even nx),
+    // measured faster at every size tried; the register-tiled kernel elsewhere
     h->use_tma = (c.sweep_kernel != 1 && tma_sweep_supported(g)) ? 1 : 0;
     if (h->use_tma && !tma_encode_maps(g, h->psi, h->b, h->D, &h->tmaps)) h->use_tma = 0;
     h->batch_owned = 0;

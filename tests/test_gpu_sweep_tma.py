@@ -1,5 +1,6 @@
-"""The Jacobi sweep staged in shared memory by bulk asynchronous copies
-(sweep_kernel = 2) against the register-tiled kernel and the FP64 oracle.
+"""The Jacobi sweep staged in shared memory by the tensor memory accelerator
+(sweep_kernel = 2, the default) against the register-tiled kernel and the FP64
+oracle.
 
 Both kernels do the same arithmetic in the same order, so their iterates agree
 to the last bits; the staged kernel is also checked against the oracle step by
@@ -86,6 +87,42 @@ def test_staged_tolerance_mode(O, name, p):
             continue
         assert np.max(np.abs(gpu_state(s)[0] - st.psi)) <= TOL_PSI
     assert mism <= 2
+
+
+@pytest.mark.parametrize("mode", ["xz_periodic", "xz_openx", "insulating_openx", "insulating_periodic"])
+def test_staged_variants_equal_register_tiled(O, mode):
+    """the xz gauge (j-indexed links, y wrap) and insulating sites (link bits) in the
+    staged kernel against the register-tiled kernel"""
+    import math
+
+    import torch
+    from paper_1409_8340_gb300.solver import Params, Solver
+    if mode == "xz_periodic":
+        p = Params(40, 20, 12, bc=(P, P, P), xz_gauge=True, Jext=0.01)
+        p.Bz = 2 * math.pi * 3 / (p.length(0) * p.length(1))
+        p.Bx = 2 * math.pi * 1 / (p.length(1) * p.length(2))
+    elif mode == "xz_openx":
+        p = Params(66, 18, 9, bc=(OP, P, OP), xz_gauge=True, Bz=0.2, Bx=0.15, Jext=0.01)
+    elif mode == "insulating_openx":
+        p = Params(70, 26, 10, bc=(OP, P, P), Bz=0.25, Jext=0.015)
+    else:
+        p = quantised(Params(40, 24, 12, bc=(P, P, P), Jext=0.01), 2)
+    ins = None
+    if mode.startswith("insulating"):
+        rng = np.random.default_rng(9)
+        ins = (rng.uniform(size=p.shape) < 0.05).astype(np.uint8)
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 5)
+    alpha = inclusion_alpha(p, 6)
+    out = []
+    for sk in (1, 2):
+        q = dataclasses.replace(p, sweep_kernel=sk, fixed_sweeps=25, poisson_tol=1e-6, poisson_max_cycles=200)
+        s = Solver(q, torch.as_tensor(alpha).cuda(),
+                   insulating=None if ins is None else torch.as_tensor(ins).cuda())
+        s.set_state(torch.as_tensor(psi0.astype(np.complex64)))
+        s.step(3)
+        out.append(gpu_state(s))
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-6
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-5 * max(1.0, np.abs(out[0][1]).max())
 
 
 def test_staged_full_size_matches_register_tiled():
