@@ -272,6 +272,105 @@ __global__ void __launch_bounds__(kGX) prolong_kernel(MGLevel F, MGLevel C, int 
     }
 }
 
+// Zebra x-line Gauss-Seidel by the recursive exact line solve (levels with short
+// decay): one warp per line, C = nx / 32 consecutive sites per lane.  The line
+// operator T = (2 cx + s) - cx (S- + S+) equals (cx / rho)(1 - rho S-)(1 - rho S+), so
+// u = (rho / cx) (1 - rho S+)^-1 (1 - rho S-)^-1 E: a forward recursion w_x = E_x +
+// rho w_(x-1), then a backward one z_x = w_x + rho z_(x+1), u = (rho / cx) z.  Each lane
+// starts its forward recursion from the C values before its chunk (the previous lane's,
+// by shuffle) and its backward recursion from the C w-values after it (the next
+// lane's): the dropped terms carry rho^C <= 1e-9.  The ends of the line use the
+// periodic wrap or the Neumann mirror of the extended line, as the convolution does.
+template <int C>
+__global__ void __launch_bounds__(kThreads) line_iir_kernel(LineArgs A)
+{
+    const MGLevel &L = A.L;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long line = (long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (line >= A.nlines) return;   // whole warps
+    const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
+    int j, k;
+    line_jk(line, A.color, L.ny, L.nz, j, k);
+    const int nx = L.nx;
+    const long long plane = (long long)nx * L.ny;
+    const long long base = (long long)nx * j + plane * k;
+    const bool ya = L.ny >= 2, za = L.nz >= 2;
+    const float *rr = L.r + base;
+    const float *up = ya ? L.u + (long long)nx * nb_idx(j, 1, L.ny, A.bcy) + plane * k : rr;
+    const float *um = ya ? L.u + (long long)nx * nb_idx(j, -1, L.ny, A.bcy) + plane * k : rr;
+    const float *zp = za ? L.u + (long long)nx * j + plane * nb_idx(k, 1, L.nz, A.bcz) : rr;
+    const float *zm = za ? L.u + (long long)nx * j + plane * nb_idx(k, -1, L.nz, A.bcz) : rr;
+    const int i0 = lane * C;
+    float e[C];
+#pragma unroll
+    for (int h = 0; h < C; h += 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(rr + i0 + h);
+        const float4 yp = *reinterpret_cast<const float4 *>(up + i0 + h);
+        const float4 ym = *reinterpret_cast<const float4 *>(um + i0 + h);
+        const float4 kp = *reinterpret_cast<const float4 *>(zp + i0 + h);
+        const float4 km = *reinterpret_cast<const float4 *>(zm + i0 + h);
+        const float av[4] = {a.x, a.y, a.z, a.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w}, ymv[4] = {ym.x, ym.y, ym.z, ym.w},
+                    kpv[4] = {kp.x, kp.y, kp.z, kp.w}, kmv[4] = {km.x, km.y, km.z, km.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float x = -(av[c] - fsub);
+            if (ya) x += L.cy * (ypv[c] + ymv[c]);
+            if (za) x += L.cz * (kpv[c] + kmv[c]);
+            e[h + c] = x;
+        }
+    }
+    const bool open = (A.bcx == kOpen);
+    const float rho = L.rho;
+    // values beyond the chunk that the two mirrored ends need: e(C) from lane 1 (left
+    // mirror, lane 0) and e(nx - 1 - C) from lane 30 (right mirror, lane 31)
+    const float e_next0 = __shfl_sync(FULL, e[0], 1);
+    const float e_prevlast = __shfl_sync(FULL, e[C - 1], 30);
+    // forward warm-up over x = i0 - C .. i0 - 1
+    float w = 0.f;
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        float v = __shfl_sync(FULL, e[m], (lane + 31) & 31);
+        if (open && lane == 0) v = (m == 0) ? e_next0 : e[C - m];   // e_ext(-d) = e(d), d = C - m
+        w = fmaf(rho, w, v);
+    }
+    float wv[C];
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        w = fmaf(rho, w, e[m]);
+        wv[m] = w;
+    }
+    // right mirror: the forward recursion continued over e_ext(nx + m) = e(nx - 2 - m)
+    float wext[C];
+    {
+        float wc = wv[C - 1];
+#pragma unroll
+        for (int m = 0; m < C; ++m) {
+            const float v = (m <= C - 2) ? e[C - 2 - m] : e_prevlast;
+            wc = fmaf(rho, wc, v);
+            wext[m] = wc;
+        }
+    }
+    // backward warm-up over x = i0 + 2C - 1 down to i0 + C
+    float z = 0.f;
+#pragma unroll
+    for (int m = C - 1; m >= 0; --m) {
+        float v = __shfl_sync(FULL, wv[m], (lane + 1) & 31);
+        if (open && lane == 31) v = wext[m];
+        z = fmaf(rho, z, v);
+    }
+    float out[C];
+#pragma unroll
+    for (int m = C - 1; m >= 0; --m) {
+        z = fmaf(rho, z, wv[m]);
+        out[m] = z * L.rscale;
+    }
+    float *dst = L.u + base + i0;
+#pragma unroll
+    for (int h = 0; h < C; h += 4)
+        *reinterpret_cast<float4 *>(dst + h) = make_float4(out[h], out[h + 1], out[h + 2], out[h + 3]);
+}
+
 static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s, long long *nl)
 {
     const MGLevel &L = a.lev[l];
@@ -285,6 +384,13 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.ctl = a.ctl;
     A.level0 = (l == 0);
     if (A.nlines == 0) return cudaSuccess;
+    if (L.iir == 16 || L.iir == 32) {
+        const int nb = (int)((A.nlines + kThreads / 32 - 1) / (kThreads / 32));
+        if (L.iir == 16) line_iir_kernel<16><<<nb, kThreads, 0, s>>>(A);
+        else line_iir_kernel<32><<<nb, kThreads, 0, s>>>(A);
+        ++*nl;
+        return cudaGetLastError();
+    }
     const LineShape sh = line_shape(L.nx, L.kmin, L.kmax, kThreads);
     A.sh = sh;
     const size_t smem = sizeof(float) * (size_t)line_tile_floats(sh);
@@ -455,7 +561,10 @@ static cudaError_t coarse_solve(const PoissonArgs &a, int l, cudaStream_t s, lon
     return cudaGetLastError();
 }
 
-static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long *nl)
+// skip_first: the finest level's first colour-0 pass is left out.  Right after a
+// V-cycle (which ends with a colour-0 pass on the same right-hand side) it would repeat
+// exact line solves on identical input: the same bits.
+static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long *nl, bool skip_first = false)
 {
     const int bcx = a.g.bcx, bcy = a.g.bcy, bcz = a.g.bcz;
     if (l == a.nlevels - 1) {
@@ -468,7 +577,7 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
         }
         return cudaGetLastError();
     }
-    smooth(a, l, 0, s, nl);
+    if (!skip_first) smooth(a, l, 0, s, nl);
     smooth(a, l, 1, s, nl);
     const MGLevel &F = a.lev[l], &C = a.lev[l + 1];
     const bool v4 = (F.nx % 4) == 0;   // rows on 16-byte boundaries (x is never coarsened)
@@ -488,7 +597,15 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     return cudaGetLastError();
 }
 
-cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches) { return vcycle(a, 0, s, launches); }
+cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches, bool after_cycle)
+{
+    // the zebra colouring (j + k) % 2 is a proper two-colouring of the lines unless a
+    // periodic axis has odd length; only then is a repeated colour-0 pass not a no-op
+    const MGLevel &F = a.lev[0];
+    const bool proper = (a.g.bcy == kOpen || F.ny == 1 || (F.ny % 2) == 0) &&
+                        (a.g.bcz == kOpen || F.nz == 1 || (F.nz % 2) == 0);
+    return vcycle(a, 0, s, launches, after_cycle && proper && a.nlevels > 1);
+}
 
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s)
 {

@@ -518,6 +518,17 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
         M.G = at<float>(ws, L.tri[l]);
         M.P = mg_period(c.nx, c.bc[0]);
         M.kmin = mg_line_kernel(c.nx, c.bc[0], M.cx, 2.0 * M.cy + 2.0 * M.cz, tri);
+        {
+            // the line operator (2 cx + s) - cx (shift + shift^-1) = (cx / rho)(1 - rho S-)(1 - rho S+):
+            // a causal and an anticausal first-order recursion.  One lane's C values carry the
+            // warm-up of its neighbour when rho^C <= 1e-9 (far below FP32 rounding)
+            const double sx = 2.0 * M.cy + 2.0 * M.cz, tt = 1.0 + sx / (2.0 * M.cx);
+            const double rho = tt - sqrt(tt * tt - 1.0);
+            M.rho = (float)rho;
+            M.rscale = (float)(rho / M.cx);
+            const int C = c.nx / 32;
+            M.iir = ((C == 16 || C == 32) && c.nx == 32 * C && sx > 0 && pow(rho, (double)C) <= 1e-9) ? C : 0;
+        }
         M.kmax = M.kmin + (int)tri.size() - 1;
         chk(cudaMemcpyAsync(M.G, tri.data(), 4 * tri.size(), cudaMemcpyHostToDevice, s));
         M.cw = nullptr;
@@ -773,7 +784,7 @@ int tdgl_solve_mu(tdgl_handle *h)
     long long nl = 1;
     int cycles = 0;
     for (int q = 0; q < c.poisson_cycles; ++q, ++cycles)
-        if (launch_vcycle(h->pa, s, &nl) != cudaSuccess) return TDGL_ERR_CUDA;
+        if (launch_vcycle(h->pa, s, &nl, q > 0) != cudaSuccess) return TDGL_ERR_CUDA;
     if (c.poisson_tol > 0) {
         for (;;) {
             if (launch_poisson_residual(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
@@ -782,7 +793,7 @@ int tdgl_solve_mu(tdgl_handle *h)
             int rc = read_ctl(h, &ctl);
             if (rc != TDGL_OK) return rc;
             if (ctl.res <= c.poisson_tol || cycles >= c.poisson_max_cycles) break;
-            if (launch_vcycle(h->pa, s, &nl) != cudaSuccess) return TDGL_ERR_CUDA;
+            if (launch_vcycle(h->pa, s, &nl, true) != cudaSuccess) return TDGL_ERR_CUDA;
             ++cycles;
         }
     }

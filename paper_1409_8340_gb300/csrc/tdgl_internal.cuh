@@ -272,6 +272,10 @@ struct MGLevel {
     int kmin, kmax;            // kernel support (kmax - kmin + 1 <= P)
     float *cw;                 // coarsest level only: [W (M x M) | V (M x M) | G_q (M x P)], or nullptr
     int M;                     // number of y-z modes of the coarsest level (ny * nz)
+    // recursive exact line solve (short decay): chunk C = nx / 32 sites per lane, or 0;
+    // rho = t - sqrt(t^2 - 1), t = 1 + s / (2 cx), and the output scale rho / cx
+    int iir;
+    float rho, rscale;
 };
 int mg_period(int nx, int bcx);
 // x lines of colour c ((j + k) % 2 == c) on an ny x nz line grid
@@ -295,7 +299,8 @@ struct PoissonArgs {
     double wsum;
 };
 cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStream_t s);
-cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches);
+// after_cycle: the call directly follows a V-cycle on the same right-hand side
+cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches, bool after_cycle = false);
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
