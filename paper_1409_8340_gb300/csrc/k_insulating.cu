@@ -352,23 +352,39 @@ struct InsArgs {
     const double *isl_w;
     double *isl_acc;
     double wsum_c;
+    int islands;               // 0: every conducting site is in the main component
 };
+
+// Rows (j, k) of the grid spread over the blocks, sites of a row over the threads:
+// (i, j, k) and the face weights without per-site division.
+template <class F>
+__device__ __forceinline__ void for_sites(const DevGrid &g, F &&fn)
+{
+    const int rows = g.ny * g.nz;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % g.ny, k = row / g.ny;
+        const float wyz = face_w(g.bcy, g.ny, j) * face_w(g.bcz, g.nz, k);
+        const long long base = (long long)row * g.nx;
+        for (int i = threadIdx.x; i < g.nx; i += blockDim.x) fn(base + i, i, j, k, wyz * face_w(g.bcx, g.nx, i));
+    }
+}
+
+__device__ __forceinline__ int comp_of(const InsArgs &a, long long m)
+{
+    if (a.islands) return a.comp[m];
+    return (a.g.lk[m] & kLkIns) ? -1 : 0;
+}
 
 // Component sums of w v: the main component's by blocks into sums[slot], each
 // island's by atomics into isl_acc (cleared before the launch).
 __global__ void ins_csum_kernel(InsArgs a, const float *v, int slot)
 {
     double acc = 0.0;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
-         m += (long long)gridDim.x * blockDim.x) {
-        const int c = a.comp[m];
-        if (c < 0) continue;
-        int i, j, k;
-        ijk_of(a.g, m, i, j, k);
-        const double w = (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k));
-        if (c == 0) acc += w * (double)v[m];
-        else atomicAdd(a.isl_acc + (c - 1), w * (double)v[m]);
-    }
+    for_sites(a.g, [&](long long m, int, int, int, float w) {
+        const int c = comp_of(a, m);
+        if (c == 0) acc += (double)(w * v[m]);
+        else if (c > 0) atomicAdd(a.isl_acc + (c - 1), (double)(w * v[m]));
+    });
     finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
 }
 
@@ -380,23 +396,17 @@ __global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int dslot, int
     const float cm = (float)(a.ctl->sums[mslot] / a.wsum_c);
     double acc = 0.0;
     float mx = 0.f;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
-         m += (long long)gridDim.x * blockDim.x) {
-        const int c = a.comp[m];
+    for_sites(a.g, [&](long long m, int, int, int, float w) {
+        const int c = comp_of(a, m);
         if (c < 0) {
             v[m] = 0.f;
-            continue;
+            return;
         }
         const float x = v[m] - (c == 0 ? cm : (float)(a.isl_acc[c - 1] / a.isl_w[c - 1]));
         v[m] = x;
         mx = fmaxf(mx, fabsf(x));
-        if (dslot >= 0) {
-            int i, j, k;
-            ijk_of(a.g, m, i, j, k);
-            acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) *
-                            a.r[m] * x);
-        }
-    }
+        if (dslot >= 0) acc += (double)(w * a.r[m] * x);
+    });
     if (dslot >= 0) finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[dslot]);
     if (!fmax) return;
     __shared__ float shf[32];
@@ -420,17 +430,10 @@ __global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int dslot, int
 // r = f - A mu
 __global__ void ins_resid_kernel(InsArgs a)
 {
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
-         m += (long long)gridDim.x * blockDim.x) {
+    for_sites(a.g, [&](long long m, int i, int j, int k, float) {
         const unsigned l = a.g.lk[m];
-        if (l & kLkIns) {
-            a.r[m] = 0.f;
-            continue;
-        }
-        int i, j, k;
-        ijk_of(a.g, m, i, j, k);
-        a.r[m] = a.f[m] - masked_lap(a.g, a.mu, m, i, j, k, l);
-    }
+        a.r[m] = (l & kLkIns) ? 0.f : a.f[m] - masked_lap(a.g, a.mu, m, i, j, k, l);
+    });
 }
 
 // p = z + beta p, beta = sums[num] / sums[den] (first: beta = 0)
@@ -447,20 +450,16 @@ __global__ void ins_dir_kernel(InsArgs a, int num, int den, int first)
 __global__ void ins_apply_kernel(InsArgs a, int slot)
 {
     double acc = 0.0;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.g.N;
-         m += (long long)gridDim.x * blockDim.x) {
+    for_sites(a.g, [&](long long m, int i, int j, int k, float w) {
         const unsigned l = a.g.lk[m];
         if (l & kLkIns) {
             a.q[m] = 0.f;
-            continue;
+            return;
         }
-        int i, j, k;
-        ijk_of(a.g, m, i, j, k);
         const float v = masked_lap(a.g, a.p, m, i, j, k, l);
         a.q[m] = v;
-        acc += (double)(face_w(a.g.bcx, a.g.nx, i) * face_w(a.g.bcy, a.g.ny, j) * face_w(a.g.bcz, a.g.nz, k) *
-                        a.p[m] * v);
-    }
+        acc += (double)(w * a.p[m] * v);
+    });
     finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
 }
 
@@ -515,7 +514,9 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
     a.isl_w = ip.isl_w;
     a.isl_acc = ip.isl_acc;
     a.wsum_c = ip.wsum_c;
-    const int nb = red_grid(a.g.N);
+    a.islands = ip.n_isl > 0 ? 1 : 0;
+    // one block per row (up to 4096 blocks, grid-stride beyond): within the partial-sum slots
+    const int nb = a.g.ny * a.g.nz < 4096 ? a.g.ny * a.g.nz : 4096;
     const size_t bytes = 4 * (size_t)a.g.N;
     // the preconditioner: one V-cycle of the plain operator on r, from z = 0
     PoissonArgs pz = pa;

@@ -19,6 +19,10 @@ def poisson_cases():
         ("allopen_33x17x9", Params(33, 17, 9, bc=(OP, OP, OP), Bz=0.2)),
         ("film_64x48x1", Params(64, 48, 1, bc=(OP, P, P), Bz=0.2, Jext=0.01)),
         ("uneven_96x96x48", Params(96, 96, 48, bc=(OP, P, P), Bz=0.3, Jext=0.02)),
+        # nx = 512: the finest level's lines are solved by the recursive (two-pass) exact solve
+        ("recursive_openx_512x24x12_J", Params(512, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        ("recursive_periodic_512x16x16", quantised(Params(512, 16, 16, bc=(P, P, P)), 2)),
+        ("recursive_allopen_512x17x9", Params(512, 17, 9, bc=(OP, OP, OP), Bz=0.25)),
     ]
 
 
