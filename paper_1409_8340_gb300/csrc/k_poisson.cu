@@ -126,7 +126,10 @@ constexpr int kGZ = 4;
 static dim3 grid_xyz(int nx, int ny, int nz) { return dim3((nx + kGX - 1) / kGX, ny, (nz + kGZ - 1) / kGZ); }
 
 // t = F - L u on one level (level 0: F = f - fmean)
-__global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0)
+// skip_color >= 0: rows (j, k) of that zebra colour are left out (their residual is zero
+// right after that colour's exact line solves; the restriction does not read them)
+__global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0,
+                                                      int skip_color)
 {
     const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
     if (i >= L.nx) return;
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int b
     for (int dk = 0; dk < kGZ; ++dk) {
         const int k = ka + dk;
         if (k >= kb) break;
+        if (skip_color >= 0 && ((j + k) & 1) == skip_color) continue;
         const long long m = i + (long long)L.nx * j + pl * k;
         tt[m] = residual_at<false>(L, bcx, bcy, bcz, fsub, i, j, k, m);
     }
@@ -147,7 +151,8 @@ __global__ void __launch_bounds__(kGX) residual_kernel(MGLevel L, int bcx, int b
 // 4 kGX x sites, kGZ planes per block.
 static dim3 grid_xyz4(int nx, int ny, int nz) { return dim3((nx / 4 + kGX - 1) / kGX, ny, (nz + kGZ - 1) / kGZ); }
 
-__global__ void __launch_bounds__(kGX) residual4_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl, int level0)
+__global__ void __launch_bounds__(kGX) residual4_kernel(MGLevel L, int bcx, int bcy, int bcz, const DevCtl *ctl,
+                                                       int level0, int skip_color)
 {
     const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, j = blockIdx.y;
     if (i0 >= L.nx) return;
@@ -158,11 +163,12 @@ __global__ void __launch_bounds__(kGX) residual4_kernel(MGLevel L, int bcx, int 
     for (int dk = 0; dk < kGZ; ++dk) {
         const int k = ka + dk;
         if (k >= kb) break;
+        if (skip_color >= 0 && ((j + k) & 1) == skip_color) continue;
         *reinterpret_cast<float4 *>(L.t + i0 + (long long)L.nx * j + pl * k) = residual4_at<false>(L, bcx, bcy, bcz, fsub, i0, j, k);
     }
 }
 
-__global__ void __launch_bounds__(kGX) restrict4_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+__global__ void __launch_bounds__(kGX) restrict4_kernel(MGLevel F, MGLevel C, int bcy, int bcz, int zero_color)
 {
     const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, J = blockIdx.y;
     if (i0 >= C.nx) return;
@@ -173,12 +179,14 @@ __global__ void __launch_bounds__(kGX) restrict4_kernel(MGLevel F, MGLevel C, in
         const int K = Ka + dK;
         if (K >= Kb) break;
         const long long m = i0 + (long long)nx * (J + (long long)C.ny * K);
-        *reinterpret_cast<float4 *>(C.r + m) = restrict4_at<false>(F, bcy, bcz, i0, J, K);
+        *reinterpret_cast<float4 *>(C.r + m) = restrict4_at<false>(F, bcy, bcz, i0, J, K, zero_color);
         *reinterpret_cast<float4 *>(C.u + m) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-__global__ void __launch_bounds__(kGX) prolong4_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+// only_color >= 0: only rows of that zebra colour take the correction (the other
+// colour's lines are solved exactly next, from r and these rows alone)
+__global__ void __launch_bounds__(kGX) prolong4_kernel(MGLevel F, MGLevel C, int bcy, int bcz, int only_color)
 {
     const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, j = blockIdx.y;
     if (i0 >= F.nx) return;
@@ -188,6 +196,7 @@ __global__ void __launch_bounds__(kGX) prolong4_kernel(MGLevel F, MGLevel C, int
     for (int dk = 0; dk < kGZ; ++dk) {
         const int k = ka + dk;
         if (k >= kb) break;
+        if (only_color >= 0 && ((j + k) & 1) != only_color) continue;
         float4 *p = reinterpret_cast<float4 *>(F.u + i0 + (long long)nx * (j + (long long)F.ny * k));
         const float4 v = prolong4_at<false>(F, C, bcy, bcz, i0, j, k);
         const float4 o = *p;
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(kGX) residual_norm_kernel(MGLevel L, int bcx, 
 }
 
 // r_c = full weighting of t_f (y, z); u_c = 0.  Grid over the coarse (x, y).
-__global__ void __launch_bounds__(kGX) restrict_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+__global__ void __launch_bounds__(kGX) restrict_kernel(MGLevel F, MGLevel C, int bcy, int bcz, int zero_color)
 {
     const int i = blockIdx.x * kGX + threadIdx.x, J = blockIdx.y;
     if (i >= C.nx) return;
@@ -245,7 +254,7 @@ __global__ void __launch_bounds__(kGX) restrict_kernel(MGLevel F, MGLevel C, int
     float acc[kGZ];
 #pragma unroll
     for (int dK = 0; dK < kGZ; ++dK)
-        if (dK < cnt) acc[dK] = restrict_at<false>(F, bcy, bcz, i, J, Ka + dK);
+        if (dK < cnt) acc[dK] = restrict_at<false>(F, bcy, bcz, i, J, Ka + dK, zero_color);
 #pragma unroll
     for (int dK = 0; dK < kGZ; ++dK) {
         if (dK < cnt) {
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(kGX) restrict_kernel(MGLevel F, MGLevel C, int
 }
 
 // u_f += bilinear interpolation of u_c.  Grid over the fine (x, y).
-__global__ void __launch_bounds__(kGX) prolong_kernel(MGLevel F, MGLevel C, int bcy, int bcz)
+__global__ void __launch_bounds__(kGX) prolong_kernel(MGLevel F, MGLevel C, int bcy, int bcz, int only_color)
 {
     const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
     if (i >= F.nx) return;
@@ -267,6 +276,7 @@ __global__ void __launch_bounds__(kGX) prolong_kernel(MGLevel F, MGLevel C, int 
     for (int dk = 0; dk < kGZ; ++dk) {
         const int k = ka + dk;
         if (k >= kb) break;
+        if (only_color >= 0 && ((j + k) & 1) != only_color) continue;
         const float v = prolong_at<false>(F, C, bcy, bcz, i, j, k);
         F.u[i + (long long)nx * (j + (long long)F.ny * k)] += v;
     }
@@ -581,17 +591,25 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     smooth(a, l, 1, s, nl);
     const MGLevel &F = a.lev[l], &C = a.lev[l + 1];
     const bool v4 = (F.nx % 4) == 0;   // rows on 16-byte boundaries (x is never coarsened)
+    // With a proper zebra colouring the post-smoothing starts with colour 1, whose lines are
+    // solved from r and the colour-0 rows alone (their old values are never read): only
+    // colour 0 takes the prolonged correction, with the same result bit for bit.  (After the
+    // pre-smoothing the colour-1 rows' residual is zero in exact arithmetic, but in FP32 it
+    // is rounding noise of the size of the colour-0 residual near convergence, so it is
+    // still computed and restricted: zc = -1.)
+    const bool proper = (bcy == kOpen || F.ny == 1 || (F.ny % 2) == 0) && (bcz == kOpen || F.nz == 1 || (F.nz % 2) == 0);
+    const int zc = -1, oc = proper ? 0 : -1;
     if (v4) {
-        residual4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0);
-        restrict4_kernel<<<grid_xyz4(C.nx, C.ny, C.nz), kGX, 0, s>>>(F, C, bcy, bcz);
+        residual4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0, zc);
+        restrict4_kernel<<<grid_xyz4(C.nx, C.ny, C.nz), kGX, 0, s>>>(F, C, bcy, bcz, zc);
     } else {
-        residual_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0);
-        restrict_kernel<<<grid_xyz(C.nx, C.ny, C.nz), kGX, 0, s>>>(F, C, bcy, bcz);
+        residual_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0, zc);
+        restrict_kernel<<<grid_xyz(C.nx, C.ny, C.nz), kGX, 0, s>>>(F, C, bcy, bcz, zc);
     }
     *nl += 3;
     vcycle(a, l + 1, s, nl);
-    if (v4) prolong4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz);
-    else prolong_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz);
+    if (v4) prolong4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz, oc);
+    else prolong_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz, oc);
     smooth(a, l, 1, s, nl);
     smooth(a, l, 0, s, nl);
     return cudaGetLastError();

@@ -229,7 +229,10 @@ __device__ __forceinline__ float residual_at(const MGLevel &L, int bcx, int bcy,
 
 // Full weighting in (y, z) of the fine residual t at coarse site (i, J, K).
 template <bool CG>
-__device__ __forceinline__ float restrict_at(const MGLevel &F, int bcy, int bcz, int i, int J, int K)
+// zero_color >= 0: the fine rows of that zebra colour hold a zero residual (the colour
+// just solved exactly) and are not read
+__device__ __forceinline__ float restrict_at(const MGLevel &F, int bcy, int bcz, int i, int J, int K,
+                                             int zero_color = -1)
 {
     const int nx = F.nx;
     float acc = 0.f;
@@ -241,6 +244,7 @@ __device__ __forceinline__ float restrict_at(const MGLevel &F, int bcy, int bcz,
             const float wj = (F.fy == 2) ? (dj == 0 ? 0.5f : 0.25f) : (dj == 0 ? 1.f : 0.f);
             if (wj == 0.f) continue;
             const int jf = nb_idx(F.fy * J, dj, F.ny, bcy);
+            if (zero_color >= 0 && ((jf + kf) & 1) == zero_color) continue;
             acc += wk * wj * ldx<CG>(F.t + (long long)nx * (jf + (long long)F.ny * kf) + i);
         }
     }
@@ -325,7 +329,8 @@ __device__ __forceinline__ float4 residual4_at(const MGLevel &L, int bcx, int bc
 }
 
 template <bool CG>
-__device__ __forceinline__ float4 restrict4_at(const MGLevel &F, int bcy, int bcz, int i0, int J, int K)
+__device__ __forceinline__ float4 restrict4_at(const MGLevel &F, int bcy, int bcz, int i0, int J, int K,
+                                               int zero_color = -1)
 {
     const int nx = F.nx;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -338,6 +343,7 @@ __device__ __forceinline__ float4 restrict4_at(const MGLevel &F, int bcy, int bc
             const int dj = (nj == 3) ? b - 1 : 0;
             const float wj = (nj == 3) ? (dj == 0 ? 0.5f : 0.25f) : 1.f;
             const int jf = nb_idx(F.fy * J, dj, F.ny, bcy);
+            if (zero_color >= 0 && ((jf + kf) & 1) == zero_color) continue;
             const float4 t = ld4<CG>(F.t + (long long)nx * (jf + (long long)F.ny * kf) + i0);
             acc.x += wk * wj * t.x;
             acc.y += wk * wj * t.y;
