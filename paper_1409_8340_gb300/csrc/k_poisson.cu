@@ -381,6 +381,142 @@ __global__ void __launch_bounds__(kThreads) line_iir_kernel(LineArgs A)
         *reinterpret_cast<float4 *>(dst + h) = make_float4(out[h], out[h + 1], out[h + 2], out[h + 3]);
 }
 
+// The same recursive line solve with the line's five rows (r and the four neighbour
+// rows) brought into shared memory by 16-byte asynchronous copies: each warp loops over
+// lines and copies the next line's rows while it solves the current one, so the loads
+// of a whole line are in flight without holding them in registers.  Rows are stored
+// with 4 floats of padding per 32 (the lanes' 16-site chunks then fall on distinct banks).
+constexpr int kIirWarps = 4;
+__device__ __forceinline__ int pad32(int t) { return t + 4 * (t >> 5); }
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+template <int C>
+__global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs A)
+{
+    constexpr int NX = 32 * C, ROW = NX + NX / 8;   // padded row length in floats
+    extern __shared__ __align__(16) float sm_iir[];
+    const MGLevel &L = A.L;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *buf = sm_iir + (size_t)wib * 2 * 5 * ROW;   // [2 buffers][5 rows][ROW]
+    const long long nwarps = (long long)gridDim.x * kIirWarps;
+    const long long first = (long long)blockIdx.x * kIirWarps + wib;
+    const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
+    const long long plane = (long long)NX * L.ny;
+    const bool ya = L.ny >= 2, za = L.nz >= 2;
+    // the five rows of a line: r, u(j+1), u(j-1), u(k+1), u(k-1)
+    auto rows_of = [&](long long line, const float **src, long long &base) {
+        int j, k;
+        line_jk(line, A.color, L.ny, L.nz, j, k);
+        base = (long long)NX * j + plane * k;
+        src[0] = L.r + base;
+        src[1] = ya ? L.u + (long long)NX * nb_idx(j, 1, L.ny, A.bcy) + plane * k : src[0];
+        src[2] = ya ? L.u + (long long)NX * nb_idx(j, -1, L.ny, A.bcy) + plane * k : src[0];
+        src[3] = za ? L.u + (long long)NX * j + plane * nb_idx(k, 1, L.nz, A.bcz) : src[0];
+        src[4] = za ? L.u + (long long)NX * j + plane * nb_idx(k, -1, L.nz, A.bcz) : src[0];
+    };
+    auto issue = [&](long long line, float *dst) {
+        const float *src[5];
+        long long base;
+        rows_of(line, src, base);
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int h = 0; h < C / 4; ++h) {
+                const int t = 4 * (h * 32 + lane);   // coalesced: lane-consecutive 16-byte chunks
+                cp_async16(dst + a * ROW + pad32(t), src[a] + t);
+            }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (first >= A.nlines) return;   // whole warps
+    issue(first, buf);
+    int b = 0;
+    for (long long line = first; line < A.nlines; line += nwarps, b ^= 1) {
+        const long long next = line + nwarps;
+        if (next < A.nlines) {
+            issue(next, buf + (b ^ 1) * 5 * ROW);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncwarp();
+        const float *cur = buf + b * 5 * ROW;
+        const int i0 = lane * C;
+        float e[C];
+#pragma unroll
+        for (int h = 0; h < C; h += 4) {
+            const int t = pad32(i0 + h);
+            const float4 a = *reinterpret_cast<const float4 *>(cur + t);
+            const float4 yp = *reinterpret_cast<const float4 *>(cur + ROW + t);
+            const float4 ym = *reinterpret_cast<const float4 *>(cur + 2 * ROW + t);
+            const float4 kp = *reinterpret_cast<const float4 *>(cur + 3 * ROW + t);
+            const float4 km = *reinterpret_cast<const float4 *>(cur + 4 * ROW + t);
+            const float av[4] = {a.x, a.y, a.z, a.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w},
+                        ymv[4] = {ym.x, ym.y, ym.z, ym.w}, kpv[4] = {kp.x, kp.y, kp.z, kp.w},
+                        kmv[4] = {km.x, km.y, km.z, km.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float x = -(av[c] - fsub);
+                if (ya) x += L.cy * (ypv[c] + ymv[c]);
+                if (za) x += L.cz * (kpv[c] + kmv[c]);
+                e[h + c] = x;
+            }
+        }
+        const bool open = (A.bcx == kOpen);
+        const float rho = L.rho;
+        const float e_next0 = __shfl_sync(FULL, e[0], 1);
+        const float e_prevlast = __shfl_sync(FULL, e[C - 1], 30);
+        float w = 0.f;
+#pragma unroll
+        for (int m = 0; m < C; ++m) {
+            float v = __shfl_sync(FULL, e[m], (lane + 31) & 31);
+            if (open && lane == 0) v = (m == 0) ? e_next0 : e[C - m];
+            w = fmaf(rho, w, v);
+        }
+        float wv[C];
+#pragma unroll
+        for (int m = 0; m < C; ++m) {
+            w = fmaf(rho, w, e[m]);
+            wv[m] = w;
+        }
+        float wext[C];
+        {
+            float wc = wv[C - 1];
+#pragma unroll
+            for (int m = 0; m < C; ++m) {
+                const float v = (m <= C - 2) ? e[C - 2 - m] : e_prevlast;
+                wc = fmaf(rho, wc, v);
+                wext[m] = wc;
+            }
+        }
+        float z = 0.f;
+#pragma unroll
+        for (int m = C - 1; m >= 0; --m) {
+            float v = __shfl_sync(FULL, wv[m], (lane + 1) & 31);
+            if (open && lane == 31) v = wext[m];
+            z = fmaf(rho, z, v);
+        }
+        float out[C];
+#pragma unroll
+        for (int m = C - 1; m >= 0; --m) {
+            z = fmaf(rho, z, wv[m]);
+            out[m] = z * L.rscale;
+        }
+        int j, k;
+        line_jk(line, A.color, L.ny, L.nz, j, k);
+        float *dst = L.u + (long long)NX * j + plane * k + i0;
+#pragma unroll
+        for (int h = 0; h < C; h += 4)
+            *reinterpret_cast<float4 *>(dst + h) = make_float4(out[h], out[h + 1], out[h + 2], out[h + 3]);
+        __syncwarp();   // the buffer is refilled two lines later
+    }
+}
+
 static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s, long long *nl)
 {
     const MGLevel &L = a.lev[l];
@@ -394,10 +530,27 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.ctl = a.ctl;
     A.level0 = (l == 0);
     if (A.nlines == 0) return cudaSuccess;
-    if (L.iir == 16 || L.iir == 32) {
+    if (L.iir == 16) {
+        // asynchronous-copy variant: about four lines per warp, two blocks of four warps per SM
+        const size_t smem = (size_t)kIirWarps * 2 * 5 * (512 + 64) * sizeof(float);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(line_iir_async_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        // one resident wave: shared memory allows two blocks per SM
+        static int sms = 0;
+        if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 152;
+        long long warps = (A.nlines + 3) / 4;
+        long long nb = (warps + kIirWarps - 1) / kIirWarps;
+        if (nb > 2LL * sms) nb = 2LL * sms;
+        line_iir_async_kernel<16><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
+        ++*nl;
+        return cudaGetLastError();
+    }
+    if (L.iir == 32) {
         const int nb = (int)((A.nlines + kThreads / 32 - 1) / (kThreads / 32));
-        if (L.iir == 16) line_iir_kernel<16><<<nb, kThreads, 0, s>>>(A);
-        else line_iir_kernel<32><<<nb, kThreads, 0, s>>>(A);
+        line_iir_kernel<32><<<nb, kThreads, 0, s>>>(A);
         ++*nl;
         return cudaGetLastError();
     }
