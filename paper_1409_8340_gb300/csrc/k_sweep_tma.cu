@@ -118,13 +118,6 @@ __device__ __forceinline__ int plane_of(const DevGrid &g, int z)
     return z;
 }
 
-__device__ __forceinline__ int row_of(const DevGrid &g, int y)
-{
-    if (y < 0) return (g.bcy == kPeriodic) ? y + g.ny : 0;
-    if (y >= g.ny) return (g.bcy == kPeriodic) ? y - g.ny : g.ny - 1;
-    return y;
-}
-
 // Producer: the three boxes of plane z into stage S.  x starts two sites before the
 // tile (even, as the tensor memory accelerator requires of 8-byte elements).
 __device__ __forceinline__ void issue_plane(const TmaTile &T, int zp, Stage &S, unsigned long long *full,
