@@ -420,6 +420,13 @@ struct tdgl_handle {
     double last_javg;
     uint8_t *lk;               // link bits when insulating sites are given, else nullptr
     int use_tma;               // 1: Jacobi sweeps by the shared-memory staged kernel
+    // the Poisson solve of a step (right-hand side, V-cycles, projection) as CUDA graphs,
+    // one per psi buffer, captured on a private stream and replayed on the handle's stream
+    cudaStream_t cap_stream;
+    cudaGraphExec_t pgraph[3];
+    int pgraph_fail;
+    int poisson_calls;
+    long long pgraph_launches;
     tdgl::TmaMaps tmaps;       // its tensor maps
     tdgl::InsPoisson ip;
     // profiling
