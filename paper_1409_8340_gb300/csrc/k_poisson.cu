@@ -540,7 +540,11 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
         }
         // one resident wave: shared memory allows two blocks per SM
         static int sms = 0;
-        if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 152;
+        if (!sms) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                sms = 152;
+        }
         long long warps = (A.nlines + 3) / 4;
         long long nb = (warps + kIirWarps - 1) / kIirWarps;
         if (nb > 2LL * sms) nb = 2LL * sms;
