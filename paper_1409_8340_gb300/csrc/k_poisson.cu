@@ -395,9 +395,14 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
                  : "memory");
 }
 
-template <int C>
+// NW = 2 (levels whose decay needs rho^(2C) <= 1e-9): each lane warms its recursions up
+// over the 2C values of the two lanes before (after) its chunk; at the mirrored ends the
+// first two (last two) lanes read the extended line's values by shuffle from the lanes
+// that hold them.
+template <int C, int NW>
 __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs A)
 {
+    static_assert(NW == 1 || NW == 2, "warm-up over one or two neighbour lanes");
     constexpr int NX = 32 * C, ROW = NX + NX / 8;   // padded row length in floats
     extern __shared__ __align__(16) float sm_iir[];
     const MGLevel &L = A.L;
@@ -469,37 +474,79 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
         }
         const bool open = (A.bcx == kOpen);
         const float rho = L.rho;
-        const float e_next0 = __shfl_sync(FULL, e[0], 1);
-        const float e_prevlast = __shfl_sync(FULL, e[C - 1], 30);
-        float w = 0.f;
-#pragma unroll
-        for (int m = 0; m < C; ++m) {
-            float v = __shfl_sync(FULL, e[m], (lane + 31) & 31);
-            if (open && lane == 0) v = (m == 0) ? e_next0 : e[C - m];
-            w = fmaf(rho, w, v);
-        }
         float wv[C];
-#pragma unroll
-        for (int m = 0; m < C; ++m) {
-            w = fmaf(rho, w, e[m]);
-            wv[m] = w;
-        }
-        float wext[C];
-        {
-            float wc = wv[C - 1];
+        float z = 0.f;
+        if constexpr (NW == 1) {
+            const float e_next0 = __shfl_sync(FULL, e[0], 1);
+            const float e_prevlast = __shfl_sync(FULL, e[C - 1], 30);
+            float w = 0.f;
 #pragma unroll
             for (int m = 0; m < C; ++m) {
-                const float v = (m <= C - 2) ? e[C - 2 - m] : e_prevlast;
-                wc = fmaf(rho, wc, v);
-                wext[m] = wc;
+                float v = __shfl_sync(FULL, e[m], (lane + 31) & 31);
+                if (open && lane == 0) v = (m == 0) ? e_next0 : e[C - m];
+                w = fmaf(rho, w, v);
             }
-        }
-        float z = 0.f;
 #pragma unroll
-        for (int m = C - 1; m >= 0; --m) {
-            float v = __shfl_sync(FULL, wv[m], (lane + 1) & 31);
-            if (open && lane == 31) v = wext[m];
-            z = fmaf(rho, z, v);
+            for (int m = 0; m < C; ++m) {
+                w = fmaf(rho, w, e[m]);
+                wv[m] = w;
+            }
+            float wext[C];
+            {
+                float wc = wv[C - 1];
+#pragma unroll
+                for (int m = 0; m < C; ++m) {
+                    const float v = (m <= C - 2) ? e[C - 2 - m] : e_prevlast;
+                    wc = fmaf(rho, wc, v);
+                    wext[m] = wc;
+                }
+            }
+#pragma unroll
+            for (int m = C - 1; m >= 0; --m) {
+                float v = __shfl_sync(FULL, wv[m], (lane + 1) & 31);
+                if (open && lane == 31) v = wext[m];
+                z = fmaf(rho, z, v);
+            }
+        } else {
+            constexpr int W = NW * C;
+            // forward warm-up over x = i0 - W .. i0 - 1; on an open line, x < 0 reads the
+            // mirror e_ext(x) = e(-x), held by lane (-x) / C at element (-x) mod C
+            float w = 0.f;
+#pragma unroll
+            for (int m = 0; m < W; ++m) {
+                float v = __shfl_sync(FULL, e[m % C], (lane - NW + m / C) & 31);
+                const int d = W - m - lane * C;   // -x
+                const float vm = __shfl_sync(FULL, e[(C - m % C) % C], (d > 0 ? d : 0) / C);
+                if (open && d > 0) v = vm;
+                w = fmaf(rho, w, v);
+            }
+#pragma unroll
+            for (int m = 0; m < C; ++m) {
+                w = fmaf(rho, w, e[m]);
+                wv[m] = w;
+            }
+            // right mirror: lane 31 continues the forward recursion over
+            // e_ext(nx - 1 + d) = e(nx - 1 - d), d = 1 .. W
+            float wext[W];
+            if (open) {   // uniform over the warp
+                float wc = __shfl_sync(FULL, wv[C - 1], 31);
+#pragma unroll
+                for (int d = 1; d <= W; ++d) {
+                    const int pos = 32 * C - 1 - d;
+                    const float v = __shfl_sync(FULL, e[pos % C], pos / C);
+                    wc = fmaf(rho, wc, v);
+                    wext[d - 1] = wc;
+                }
+            }
+            // backward warm-up over x = i0 + C + W - 1 down to i0 + C; past the end lane 31
+            // reads wext[m] and lane 30 wext[m - C] (both computed in every lane)
+#pragma unroll
+            for (int m = W - 1; m >= 0; --m) {
+                float v = __shfl_sync(FULL, wv[m % C], (lane + 1 + m / C) & 31);
+                if (open && lane == 31) v = wext[m];
+                if (open && lane == 30 && m >= C) v = wext[m - C];
+                z = fmaf(rho, z, v);
+            }
         }
         float out[C];
 #pragma unroll
@@ -535,7 +582,8 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
         const size_t smem = (size_t)kIirWarps * 2 * 5 * (512 + 64) * sizeof(float);
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(line_iir_async_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(line_iir_async_kernel<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(line_iir_async_kernel<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
         // one resident wave: shared memory allows two blocks per SM
@@ -548,7 +596,8 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
         long long warps = (A.nlines + 3) / 4;
         long long nb = (warps + kIirWarps - 1) / kIirWarps;
         if (nb > 2LL * sms) nb = 2LL * sms;
-        line_iir_async_kernel<16><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
+        if (L.iir_nw == 2) line_iir_async_kernel<16, 2><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
+        else line_iir_async_kernel<16, 1><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
         ++*nl;
         return cudaGetLastError();
     }

@@ -23,6 +23,11 @@ def poisson_cases():
         ("recursive_openx_512x24x12_J", Params(512, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
         ("recursive_periodic_512x16x16", quantised(Params(512, 16, 16, bc=(P, P, P)), 2)),
         ("recursive_allopen_512x17x9", Params(512, 17, 9, bc=(OP, OP, OP), Bz=0.25)),
+        # nx = 512 with a smoothed second level (rho = 0.38 there): its recursions warm up
+        # over two neighbour lanes
+        ("recursive_two_lane_openx_512x48x24_J", Params(512, 48, 24, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        ("recursive_two_lane_periodic_512x32x32", quantised(Params(512, 32, 32, bc=(P, P, P)), 2)),
+        ("recursive_two_lane_allopen_512x33x17", Params(512, 33, 17, bc=(OP, OP, OP), Bz=0.25)),
     ]
 
 
@@ -73,6 +78,24 @@ def test_mg_converges_fast_from_cold(O):
         res.append(s.observables()["poisson_res"])
         s.close()
     # at least a factor 4 per cycle until the FP32 floor
+    for a, b in zip(res[:-1], res[1:]):
+        assert b < max(a / 4.0, 3e-6), res
+
+
+@pytest.mark.parametrize("bc", [(OP, P, P), (OP, OP, OP)])
+def test_mg_two_lane_level_converges_fast(O, bc):
+    """512 x-sites with a smoothed second level whose recursive line solves warm up over
+    two lanes: the same reduction per V-cycle from a cold start."""
+    from paper_1409_8340_gb300.solver import Params
+    ny, nz = (48, 24) if bc[1] == P else (33, 17)
+    psi = I.random_psi(512, ny, nz, 53)
+    res = []
+    for c in range(1, 5):
+        p = Params(512, ny, nz, bc=bc, Bz=0.2, Jext=0.01, poisson_cycles=c, poisson_max_cycles=c, poisson_tol=1e-12)
+        s = make_solver(p, np.ones(p.shape, np.float32), psi)
+        s.solve_mu()
+        res.append(s.observables()["poisson_res"])
+        s.close()
     for a, b in zip(res[:-1], res[1:]):
         assert b < max(a / 4.0, 3e-6), res
 
