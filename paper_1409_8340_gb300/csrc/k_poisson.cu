@@ -184,6 +184,136 @@ __global__ void __launch_bounds__(kGX) restrict4_kernel(MGLevel F, MGLevel C, in
     }
 }
 
+constexpr int kRZ = 4;   // coarse planes per block
+struct Rows3 {
+    float4 m, c, p;   // rows 2J-1, 2J, 2J+1 of one fine plane
+};
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+// FAST: every fine row and plane the block touches is interior (no wrap or mirror), so
+// the plane and row bookkeeping is fixed at compile time and each coarse plane's loads
+// are independent of one another.
+template <bool FAST>
+__device__ __forceinline__ void residual_restrict_march(const MGLevel &F, const MGLevel &C, int bcx, int bcy, int bcz,
+                                                        float fsub, int i0, int J, int Ka, int Kb)
+{
+    const int nx = F.nx, ny = F.ny, nz = F.nz;
+    const long long pl = (long long)nx * ny;
+    const int j0 = 2 * J, jm = nb_idx(j0, -1, ny, bcy), jp = nb_idx(j0, 1, ny, bcy);
+    // y neighbours of the outer rows (those of the centre row are jm and jp)
+    const int jmm = nb_idx(jm, -1, ny, bcy), jmp = nb_idx(jm, 1, ny, bcy);
+    const int jpm = nb_idx(jp, -1, ny, bcy), jpp = nb_idx(jp, 1, ny, bcy);
+    const int xl = nb_idx(i0, -1, nx, bcx), xr = nb_idx(i0 + 3, 1, nx, bcx);
+    const float *u = F.u;
+    auto load3 = [&](int k) {
+        const float *b = u + pl * k + i0;
+        Rows3 t;
+        t.m = ldg4(b + (long long)nx * jm);
+        t.c = ldg4(b + (long long)nx * j0);
+        t.p = ldg4(b + (long long)nx * jp);
+        return t;
+    };
+    // residual of the three rows of plane k from its rows U and the rows of the planes
+    // below (Zm) and above (Zp)
+    auto resid3 = [&](int k, const Rows3 &U, const Rows3 &Zm, const Rows3 &Zp, float4 &tm, float4 &tc, float4 &tp) {
+        const float *ub = u + pl * k;
+        const float *rb = F.r + pl * k + i0;
+        {
+            const float *row = ub + (long long)nx * jm;
+            const float4 ym = ldg4(ub + (long long)nx * jmm + i0);
+            const float4 yp = (FAST || jmp == j0) ? U.c : ldg4(ub + (long long)nx * jmp + i0);
+            tm = residual4_core(F, fsub, U.m, ldg4(rb + (long long)nx * jm), __ldg(row + xl), __ldg(row + xr), true, yp,
+                                ym, true, Zp.m, Zm.m);
+        }
+        {
+            const float *row = ub + (long long)nx * j0;
+            tc = residual4_core(F, fsub, U.c, ldg4(rb + (long long)nx * j0), __ldg(row + xl), __ldg(row + xr), true, U.p,
+                                U.m, true, Zp.c, Zm.c);
+        }
+        {
+            const float *row = ub + (long long)nx * jp;
+            const float4 ym = (FAST || jpm == j0) ? U.c : ldg4(ub + (long long)nx * jpm + i0);
+            const float4 yp = ldg4(ub + (long long)nx * jpp + i0);
+            tp = residual4_core(F, fsub, U.p, ldg4(rb + (long long)nx * jp), __ldg(row + xl), __ldg(row + xr), true, yp,
+                                ym, true, Zp.p, Zm.p);
+        }
+    };
+    // acc += w t in restrict4_at's order (rows 2J-1, 2J, 2J+1 of one fine plane)
+    auto add3 = [](float4 &acc, float wk, const float4 &tm, const float4 &tc, const float4 &tp) {
+        const float4 ts[3] = {tm, tc, tp};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float wj = (b == 1) ? 0.5f : 0.25f;
+            acc.x += wk * wj * ts[b].x;
+            acc.y += wk * wj * ts[b].y;
+            acc.z += wk * wj * ts[b].z;
+            acc.w += wk * wj * ts[b].w;
+        }
+    };
+    // plane 2Ka - 1 (A) and 2Ka (B)
+    int pA = FAST ? 2 * Ka - 1 : nb_idx(2 * Ka, -1, nz, bcz);
+    Rows3 uA = load3(pA), uB = load3(2 * Ka);
+    float4 tAm, tAc, tAp;
+    {
+        const int zm = FAST ? pA - 1 : nb_idx(pA, -1, nz, bcz), zp = FAST ? pA + 1 : nb_idx(pA, 1, nz, bcz);
+        const Rows3 Zm = (!FAST && zm == 2 * Ka) ? uB : load3(zm);
+        const Rows3 Zp = (FAST || zp == 2 * Ka) ? uB : load3(zp);
+        resid3(pA, uA, Zm, Zp, tAm, tAc, tAp);
+    }
+    for (int K = Ka; K < Kb; ++K) {
+        // planes A = nb(2K, -1) (pA), B = 2K, C = nb(2K, +1); N = nb(C, +1)
+        const int pB = 2 * K;
+        const int pC = FAST ? pB + 1 : nb_idx(pB, 1, nz, bcz);
+        const int pN = FAST ? pB + 2 : nb_idx(pC, 1, nz, bcz);
+        const Rows3 uC = (!FAST && pC == pA) ? uA : load3(pC);
+        const Rows3 uN = (!FAST && pN == pB) ? uB : load3(pN);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        add3(acc, 0.25f, tAm, tAc, tAp);
+        {
+            float4 tBm, tBc, tBp;
+            resid3(pB, uB, uA, uC, tBm, tBc, tBp);
+            add3(acc, 0.5f, tBm, tBc, tBp);
+        }
+        {
+            const int cm = FAST ? pB : nb_idx(pC, -1, nz, bcz);
+            const Rows3 Zm = (FAST || cm == pB) ? uB : load3(cm);
+            resid3(pC, uC, Zm, uN, tAm, tAc, tAp);   // plane C's residual, carried as the next A
+            add3(acc, 0.25f, tAm, tAc, tAp);
+        }
+        const long long m = i0 + (long long)C.nx * (J + (long long)C.ny * K);
+        *reinterpret_cast<float4 *>(C.r + m) = acc;
+        *reinterpret_cast<float4 *>(C.u + m) = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (K + 1 < Kb) {
+            uA = uC;
+            pA = pC;
+            uB = (FAST || pN == pB + 2) ? uN : load3(pB + 2);
+        }
+    }
+}
+
+// Residual and full-weighting restriction in one pass, for a level coarsened by 2 in
+// both y and z (the fine residual t is never stored).  Thread (i0 / 4, J) marches over
+// the coarse planes K of its block: coarse site (J, K) sums t over the fine rows
+// 2J-1, 2J, 2J+1 (mirrored or wrapped at the ends) of the fine planes 2K-1, 2K, 2K+1
+// with the weights of restrict4_at, in its order.  The residual of plane 2K+1 is the
+// 2K'-1 plane of the next coarse plane and is carried over; the u rows of a fine plane
+// are loaded once and kept while the planes next to it need them.  The residual of each
+// fine site is residual4_at's arithmetic, so the coarse right-hand side equals that of
+// residual4_kernel followed by restrict4_kernel.
+__global__ void __launch_bounds__(kGX) residual_restrict4_kernel(MGLevel F, MGLevel C, int bcx, int bcy, int bcz,
+                                                                 const DevCtl *ctl, int level0)
+{
+    const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, J = blockIdx.y;
+    if (i0 >= F.nx) return;
+    const float fsub = level0 ? (float)ctl->fmean : 0.f;
+    const int Ka = blockIdx.z * kRZ, Kb = min(Ka + kRZ, C.nz);
+    // interior block: rows 2J-2 .. 2J+2 and planes 2Ka-2 .. 2Kb exist without wrap or mirror
+    const bool fast = (2 * J - 2 >= 0) && (2 * J + 2 <= F.ny - 1) && (2 * Ka - 2 >= 0) && (2 * Kb <= F.nz - 1);
+    if (fast) residual_restrict_march<true>(F, C, bcx, bcy, bcz, fsub, i0, J, Ka, Kb);
+    else residual_restrict_march<false>(F, C, bcx, bcy, bcz, fsub, i0, J, Ka, Kb);
+}
+
 // only_color >= 0: only rows of that zebra colour take the correction (the other
 // colour's lines are solved exactly next, from r and these rows alone)
 __global__ void __launch_bounds__(kGX) prolong4_kernel(MGLevel F, MGLevel C, int bcy, int bcz, int only_color)
@@ -381,11 +511,14 @@ __global__ void __launch_bounds__(kThreads) line_iir_kernel(LineArgs A)
         *reinterpret_cast<float4 *>(dst + h) = make_float4(out[h], out[h + 1], out[h + 2], out[h + 3]);
 }
 
-// The same recursive line solve with the line's five rows (r and the four neighbour
-// rows) brought into shared memory by 16-byte asynchronous copies: each warp loops over
-// lines and copies the next line's rows while it solves the current one, so the loads
-// of a whole line are in flight without holding them in registers.  Rows are stored
-// with 4 floats of padding per 32 (the lanes' 16-site chunks then fall on distinct banks).
+// The same recursive line solve with the line's four neighbour rows brought into shared
+// memory by 16-byte asynchronous copies, one buffer per warp: as soon as a line's
+// right-hand side e is in registers the buffer takes the next line's copies, which fly
+// while the warp runs the recursions (the long part of a line), so the loads of a whole
+// line are in flight without holding them in registers.  The line's own row of r (16
+// values per lane) goes to registers one line ahead.  At 9 KB of shared memory per warp,
+// up to 24 warps (independent recursion chains) fit on an SM.  Rows are stored with 4
+// floats of padding per 32 (the lanes' 16-site chunks then fall on distinct banks).
 constexpr int kIirWarps = 4;
 __device__ __forceinline__ int pad32(int t) { return t + 4 * (t >> 5); }
 
@@ -408,59 +541,51 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
     const MGLevel &L = A.L;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *buf = sm_iir + (size_t)wib * 2 * 5 * ROW;   // [2 buffers][5 rows][ROW]
+    float *buf = sm_iir + (size_t)wib * 4 * ROW;   // [4 rows][ROW]
     const long long nwarps = (long long)gridDim.x * kIirWarps;
     const long long first = (long long)blockIdx.x * kIirWarps + wib;
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
     const long long plane = (long long)NX * L.ny;
     const bool ya = L.ny >= 2, za = L.nz >= 2;
-    // the five rows of a line: r, u(j+1), u(j-1), u(k+1), u(k-1)
-    auto rows_of = [&](long long line, const float **src, long long &base) {
+    const int i0 = lane * C;
+    // the staged rows of a line: u(j+1), u(j-1), u(k+1), u(k-1) (an inactive axis points
+    // at the line's own row, whose values are not used); its r row goes to registers
+    auto issue = [&](long long line, float *dst, float4 *rv) {
         int j, k;
         line_jk(line, A.color, L.ny, L.nz, j, k);
-        base = (long long)NX * j + plane * k;
-        src[0] = L.r + base;
-        src[1] = ya ? L.u + (long long)NX * nb_idx(j, 1, L.ny, A.bcy) + plane * k : src[0];
-        src[2] = ya ? L.u + (long long)NX * nb_idx(j, -1, L.ny, A.bcy) + plane * k : src[0];
-        src[3] = za ? L.u + (long long)NX * j + plane * nb_idx(k, 1, L.nz, A.bcz) : src[0];
-        src[4] = za ? L.u + (long long)NX * j + plane * nb_idx(k, -1, L.nz, A.bcz) : src[0];
-    };
-    auto issue = [&](long long line, float *dst) {
-        const float *src[5];
-        long long base;
-        rows_of(line, src, base);
+        const long long base = (long long)NX * j + plane * k;
+        const float *src[4];
+        src[0] = ya ? L.u + (long long)NX * nb_idx(j, 1, L.ny, A.bcy) + plane * k : L.u + base;
+        src[1] = ya ? L.u + (long long)NX * nb_idx(j, -1, L.ny, A.bcy) + plane * k : L.u + base;
+        src[2] = za ? L.u + (long long)NX * j + plane * nb_idx(k, 1, L.nz, A.bcz) : L.u + base;
+        src[3] = za ? L.u + (long long)NX * j + plane * nb_idx(k, -1, L.nz, A.bcz) : L.u + base;
 #pragma unroll
-        for (int a = 0; a < 5; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int h = 0; h < C / 4; ++h) {
                 const int t = 4 * (h * 32 + lane);   // coalesced: lane-consecutive 16-byte chunks
                 cp_async16(dst + a * ROW + pad32(t), src[a] + t);
             }
         asm volatile("cp.async.commit_group;" ::: "memory");
+#pragma unroll
+        for (int h = 0; h < C / 4; ++h) rv[h] = __ldg(reinterpret_cast<const float4 *>(L.r + base + i0 + 4 * h));
     };
     if (first >= A.nlines) return;   // whole warps
-    issue(first, buf);
-    int b = 0;
-    for (long long line = first; line < A.nlines; line += nwarps, b ^= 1) {
-        const long long next = line + nwarps;
-        if (next < A.nlines) {
-            issue(next, buf + (b ^ 1) * 5 * ROW);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
+    float4 rc[C / 4], rn[C / 4];
+    issue(first, buf, rc);
+    for (long long line = first; line < A.nlines; line += nwarps) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
-        const float *cur = buf + b * 5 * ROW;
-        const int i0 = lane * C;
+        const float *cur = buf;
         float e[C];
 #pragma unroll
         for (int h = 0; h < C; h += 4) {
             const int t = pad32(i0 + h);
-            const float4 a = *reinterpret_cast<const float4 *>(cur + t);
-            const float4 yp = *reinterpret_cast<const float4 *>(cur + ROW + t);
-            const float4 ym = *reinterpret_cast<const float4 *>(cur + 2 * ROW + t);
-            const float4 kp = *reinterpret_cast<const float4 *>(cur + 3 * ROW + t);
-            const float4 km = *reinterpret_cast<const float4 *>(cur + 4 * ROW + t);
+            const float4 a = rc[h / 4];
+            const float4 yp = *reinterpret_cast<const float4 *>(cur + t);
+            const float4 ym = *reinterpret_cast<const float4 *>(cur + ROW + t);
+            const float4 kp = *reinterpret_cast<const float4 *>(cur + 2 * ROW + t);
+            const float4 km = *reinterpret_cast<const float4 *>(cur + 3 * ROW + t);
             const float av[4] = {a.x, a.y, a.z, a.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w},
                         ymv[4] = {ym.x, ym.y, ym.z, ym.w}, kpv[4] = {kp.x, kp.y, kp.z, kp.w},
                         kmv[4] = {km.x, km.y, km.z, km.w};
@@ -472,6 +597,8 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
                 e[h + c] = x;
             }
         }
+        __syncwarp();   // every lane has read the buffer: it takes the next line
+        if (line + nwarps < A.nlines) issue(line + nwarps, buf, rn);
         const bool open = (A.bcx == kOpen);
         const float rho = L.rho;
         float wv[C];
@@ -560,7 +687,8 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
 #pragma unroll
         for (int h = 0; h < C; h += 4)
             *reinterpret_cast<float4 *>(dst + h) = make_float4(out[h], out[h + 1], out[h + 2], out[h + 3]);
-        __syncwarp();   // the buffer is refilled two lines later
+#pragma unroll
+        for (int h = 0; h < C / 4; ++h) rc[h] = rn[h];
     }
 }
 
@@ -578,24 +706,34 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.level0 = (l == 0);
     if (A.nlines == 0) return cudaSuccess;
     if (L.iir == 16) {
-        // asynchronous-copy variant: about four lines per warp, two blocks of four warps per SM
-        const size_t smem = (size_t)kIirWarps * 2 * 5 * (512 + 64) * sizeof(float);
-        static bool attr = false;
-        if (!attr) {
+        // asynchronous-copy variant, one resident wave of blocks (shared memory and
+        // registers decide how many fit on an SM)
+        const size_t smem = (size_t)kIirWarps * 4 * (512 + 64) * sizeof(float);
+        static int sms = 0, occ1 = 0, occ2 = 0;
+        if (!sms) {
             cudaFuncSetAttribute(line_iir_async_kernel<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             cudaFuncSetAttribute(line_iir_async_kernel<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
-        // one resident wave: shared memory allows two blocks per SM
-        static int sms = 0;
-        if (!sms) {
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 sms = 152;
+            // a failed query leaves one block per SM (and clears its error)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, line_iir_async_kernel<16, 1>, kIirWarps * 32, smem) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                occ1 = 1;
+            }
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, line_iir_async_kernel<16, 2>, kIirWarps * 32, smem) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                occ2 = 1;
+            }
+            occ1 = occ1 < 1 ? 1 : occ1;
+            occ2 = occ2 < 1 ? 1 : occ2;
         }
         long long warps = (A.nlines + 3) / 4;
         long long nb = (warps + kIirWarps - 1) / kIirWarps;
-        if (nb > 2LL * sms) nb = 2LL * sms;
+        const long long cap = (long long)(L.iir_nw == 2 ? occ2 : occ1) * sms;
+        if (nb > cap) nb = cap;
         if (L.iir_nw == 2) line_iir_async_kernel<16, 2><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
         else line_iir_async_kernel<16, 1><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
         ++*nl;
@@ -728,30 +866,67 @@ struct CoarseArgs {
     int level0;
 };
 
-// H[q][i] = sum_s W[q][s] * (-(r[s][i] - fsub)), stored in t
-__global__ void coarse_fwd_kernel(CoarseArgs A)
+// The two basis changes of the coarsest level as tiled products: Out[a][i] = sum_b
+// Mat[a][b] In[b][i] over the M y-z modes.  Block (x-tile, a-tile) stages In[b][64 x-sites]
+// and Mat[8 rows][b] in shared memory, kCB terms of the sum at a time; each thread sums
+// two outputs in the order of coarse_fwd_at / coarse_inv_at (b ascending).
+// FWD: Mat = W, In = -(r - fsub), Out = H in t.  Otherwise Mat = V, In = X, Out = u.
+constexpr int kCT = 64, kCA = 8, kCB = 128;
+template <bool FWD>
+__global__ void __launch_bounds__(256) coarse_mat_kernel(CoarseArgs A, const float *X)
 {
+    __shared__ float In[kCB][kCT];
+    __shared__ float Mt[kCA][kCB + 1];
     const MGLevel &L = A.L;
-    const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)L.M * L.nx; e += (long long)gridDim.x * blockDim.x)
-        L.t[e] = coarse_fwd_at<false>(L, fsub, e);
+    const int nx = L.nx, M = L.M;
+    const float fsub = (FWD && A.level0) ? (float)A.ctl->fmean : 0.f;
+    const float *Mat = FWD ? L.cw : L.cw + (size_t)M * M;
+    const float *src = FWD ? L.r : (X ? X : L.t);
+    float *out = FWD ? L.t : L.u;
+    const int i0 = blockIdx.x * kCT, a0 = blockIdx.y * kCA;
+    const int ii = threadIdx.x % kCT, aa = threadIdx.x / kCT;   // rows aa and aa + 4
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int b0 = 0; b0 < M; b0 += kCB) {
+        const int nb = min(kCB, M - b0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * kCT; e += 256) {
+            const int b = e / kCT, x = e % kCT;
+            float v = 0.f;
+            if (i0 + x < nx) {
+                v = src[(size_t)(b0 + b) * nx + i0 + x];
+                if (FWD) v = -(v - fsub);
+            }
+            In[b][x] = v;
+        }
+        for (int e = threadIdx.x; e < kCA * nb; e += 256) {
+            const int a = e / nb, b = e % nb;
+            Mt[a][b] = (a0 + a < M) ? Mat[(size_t)(a0 + a) * M + b0 + b] : 0.f;
+        }
+        __syncthreads();
+        for (int b = 0; b < nb; ++b) {
+            const float v = In[b][ii];
+            acc0 += Mt[aa][b] * v;
+            acc1 += Mt[aa + 4][b] * v;
+        }
+    }
+    if (i0 + ii < nx) {
+        if (a0 + aa < M) out[(size_t)(a0 + aa) * nx + i0 + ii] = acc0;
+        if (a0 + aa + 4 < M) out[(size_t)(a0 + aa + 4) * nx + i0 + ii] = acc1;
+    }
 }
 
-// X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period, in place in t.  One block
-// owns a whole mode line, so it reads the line before writing it.
-__global__ void __launch_bounds__(kThreads) coarse_conv_kernel(CoarseArgs A)
+// X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period.  With X null, in place in t:
+// one block owns a whole mode line, so it reads the line before writing it.  Otherwise
+// block (c, q) writes the c-th of gridDim.x chunks of line q into X.
+__global__ void __launch_bounds__(kThreads) coarse_conv_kernel(CoarseArgs A, float *X)
 {
     extern __shared__ __align__(16) float sm[];
-    coarse_conv_line<false>(A.L, A.bcx, blockIdx.y, threadIdx.x, blockDim.x, sm);
+    const int nx = A.L.nx;
+    const int chunk = ((nx + gridDim.x - 1) / gridDim.x + kCR - 1) / kCR * kCR;
+    const int ib = blockIdx.x * chunk, ie = min(nx, ib + chunk);
+    coarse_conv_line<false>(A.L, A.bcx, blockIdx.y, threadIdx.x, blockDim.x, sm, X, ib, X ? ie : -1);
 }
 
-// u[s][i] = sum_q V[s][q] X[q][i]  (X in t)
-__global__ void coarse_inv_kernel(CoarseArgs A)
-{
-    const MGLevel &L = A.L;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)L.M * L.nx; e += (long long)gridDim.x * blockDim.x)
-        L.u[e] = coarse_inv_at<false>(L, e);
-}
 
 static cudaError_t coarse_solve(const PoissonArgs &a, int l, cudaStream_t s, long long *nl)
 {
@@ -761,18 +936,20 @@ static cudaError_t coarse_solve(const PoissonArgs &a, int l, cudaStream_t s, lon
     C.ctl = a.ctl;
     C.level0 = (l == 0);
     const long long n = (long long)C.L.M * C.L.nx;
-    int nb = (int)((n + kThreads - 1) / kThreads);
-    if (nb > 4096) nb = 4096;
-    coarse_fwd_kernel<<<nb, kThreads, 0, s>>>(C);
-    dim3 grid(1, C.L.M);
+    const dim3 mgrid((C.L.nx + kCT - 1) / kCT, (C.L.M + kCA - 1) / kCA);
+    coarse_mat_kernel<true><<<mgrid, 256, 0, s>>>(C, nullptr);
+    // below the finest level the shared scratch t (finest-level size) has room for X after
+    // H, and each mode line is split over four blocks
+    float *X = (l > 0 && 2 * n <= a.lev[0].N) ? C.L.t + n : nullptr;
+    dim3 grid(X ? 4 : 1, C.L.M);
     size_t smem = sizeof(float) * (size_t)coarse_line_floats(C.L.nx, C.L.P);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(coarse_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    coarse_conv_kernel<<<grid, kThreads, smem, s>>>(C);
-    coarse_inv_kernel<<<nb, kThreads, 0, s>>>(C);
+    coarse_conv_kernel<<<grid, kThreads, smem, s>>>(C, X);
+    coarse_mat_kernel<false><<<mgrid, 256, 0, s>>>(C, X);
     *nl += 3;
     return cudaGetLastError();
 }
@@ -805,7 +982,15 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     // still computed and restricted: zc = -1.)
     const bool proper = (bcy == kOpen || F.ny == 1 || (F.ny % 2) == 0) && (bcz == kOpen || F.nz == 1 || (F.nz % 2) == 0);
     const int zc = -1, oc = proper ? 0 : -1;
-    if (v4) {
+    // the fused pass marches kRZ coarse planes per thread: it pays where that still leaves
+    // several blocks per SM (the two finest transfers of a 512x512x256 grid), not on
+    // small levels, where the two short kernels are faster
+    const dim3 rr_grid((F.nx / 4 + kGX - 1) / kGX, C.ny, (C.nz + kRZ - 1) / kRZ);
+    if (v4 && F.fy == 2 && F.fz == 2 && zc < 0 && (long long)rr_grid.x * rr_grid.y * rr_grid.z >= 2048) {
+        const dim3 grid = rr_grid;
+        residual_restrict4_kernel<<<grid, kGX, 0, s>>>(F, C, bcx, bcy, bcz, a.ctl, l == 0);
+        *nl -= 1;
+    } else if (v4) {
         residual4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0, zc);
         restrict4_kernel<<<grid_xyz4(C.nx, C.ny, C.nz), kGX, 0, s>>>(F, C, bcy, bcz, zc);
     } else {

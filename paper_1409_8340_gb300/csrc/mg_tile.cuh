@@ -291,6 +291,31 @@ __device__ __forceinline__ float4 ld4(const float *p)
     return ldx<CG>(reinterpret_cast<const float4 *>(p));
 }
 
+// t = F - L u at four x sites from values already loaded: the centre c, F (rr), the x
+// neighbours xl (of i0) and xr (of i0 + 3), the rows above/below in y (yp, ym; ya: y
+// active) and in z (zp, zm; za).  Shared by residual4_at and the fused residual-restriction.
+__device__ __forceinline__ float4 residual4_core(const MGLevel &L, float fsub, float4 c, float4 rr, float xl, float xr,
+                                                 bool ya, float4 yp, float4 ym, bool za, float4 zp, float4 zm)
+{
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+    const float fwd[4] = {c.y, c.z, c.w, xr};
+    const float bwd[4] = {xl, c.x, c.y, c.z};
+    float lap[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) lap[q] = L.cx * (fwd[q] + bwd[q] - 2.f * cv[q]);
+    if (ya) {
+        const float av[4] = {yp.x, yp.y, yp.z, yp.w}, bv[4] = {ym.x, ym.y, ym.z, ym.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lap[q] += L.cy * (av[q] + bv[q] - 2.f * cv[q]);
+    }
+    if (za) {
+        const float av[4] = {zp.x, zp.y, zp.z, zp.w}, bv[4] = {zm.x, zm.y, zm.z, zm.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lap[q] += L.cz * (av[q] + bv[q] - 2.f * cv[q]);
+    }
+    return make_float4((rr.x - fsub) - lap[0], (rr.y - fsub) - lap[1], (rr.z - fsub) - lap[2], (rr.w - fsub) - lap[3]);
+}
+
 template <bool CG>
 __device__ __forceinline__ float4 residual4_at(const MGLevel &L, int bcx, int bcy, int bcz, float fsub, int i0, int j,
                                                int k)
@@ -303,29 +328,19 @@ __device__ __forceinline__ float4 residual4_at(const MGLevel &L, int bcx, int bc
     const float4 rr = ld4<CG>(L.r + row + i0);
     const float xl = ldx<CG>(u + row + nb_idx(i0, -1, nx, bcx));
     const float xr = ldx<CG>(u + row + nb_idx(i0 + 3, 1, nx, bcx));
-    const float cv[4] = {c.x, c.y, c.z, c.w};
-    const float fwd[4] = {c.y, c.z, c.w, xr};
-    const float bwd[4] = {xl, c.x, c.y, c.z};
-    float lap[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) lap[q] = L.cx * (fwd[q] + bwd[q] - 2.f * cv[q]);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 yp = zero, ym = zero, zp = zero, zm = zero;
     if (ny >= 2) {
         const int jp = nb_idx(j, 1, ny, bcy), jm = nb_idx(j, -1, ny, bcy);
-        const float4 a = ld4<CG>(u + row + (long long)nx * (jp - j) + i0);
-        const float4 b = ld4<CG>(u + row + (long long)nx * (jm - j) + i0);
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) lap[q] += L.cy * (av[q] + bv[q] - 2.f * cv[q]);
+        yp = ld4<CG>(u + row + (long long)nx * (jp - j) + i0);
+        ym = ld4<CG>(u + row + (long long)nx * (jm - j) + i0);
     }
     if (nz >= 2) {
         const int kp = nb_idx(k, 1, nz, bcz), km = nb_idx(k, -1, nz, bcz);
-        const float4 a = ld4<CG>(u + row + pl * (kp - k) + i0);
-        const float4 b = ld4<CG>(u + row + pl * (km - k) + i0);
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) lap[q] += L.cz * (av[q] + bv[q] - 2.f * cv[q]);
+        zp = ld4<CG>(u + row + pl * (kp - k) + i0);
+        zm = ld4<CG>(u + row + pl * (km - k) + i0);
     }
-    return make_float4((rr.x - fsub) - lap[0], (rr.y - fsub) - lap[1], (rr.z - fsub) - lap[2], (rr.w - fsub) - lap[3]);
+    return residual4_core(L, fsub, c, rr, xl, xr, ny >= 2, yp, ym, nz >= 2, zp, zm);
 }
 
 template <bool CG>
@@ -422,10 +437,12 @@ __host__ __device__ inline long long coarse_line_floats(int nx, int P)
     return (long long)(lext + (lext >> 5) + 1) + ngp;
 }
 
-// Mode line q: X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period, in place in t
-// (the block stages the whole line in shared memory before writing it).
+// Mode line q: X[q][i] = sum_k Gq[q][k] H~[q][i + k] over one period for i in
+// [ibeg, iend) (ibeg a multiple of kCR), into X (in place in t when X is null: the block
+// stages the whole line in shared memory before writing it).
 template <bool CG>
-__device__ __forceinline__ void coarse_conv_line(const MGLevel &L, int bcx, int q, int tid, int nthr, float *sm)
+__device__ __forceinline__ void coarse_conv_line(const MGLevel &L, int bcx, int q, int tid, int nthr, float *sm,
+                                                 float *X = nullptr, int ibeg = 0, int iend = -1)
 {
     const int nx = L.nx, M = L.M, P = L.P;
     const int ngp = (P + kCR - 1) / kCR * kCR;
@@ -439,7 +456,9 @@ __device__ __forceinline__ void coarse_conv_line(const MGLevel &L, int bcx, int 
     __syncthreads();
     for (int t = nx + tid; t < lext; t += nthr) E[pad(t)] = E[pad(ext_idx(t, nx, P, bcx == kOpen))];
     __syncthreads();
-    for (int i0 = tid * kCR; i0 < nx; i0 += nthr * kCR) {
+    float *Xo = X ? X : L.t;
+    if (iend < 0) iend = nx;
+    for (int i0 = ibeg + tid * kCR; i0 < iend; i0 += nthr * kCR) {
         float out[kCR], win[2 * kCR];
 #pragma unroll
         for (int c = 0; c < kCR; ++c) {
@@ -459,7 +478,7 @@ __device__ __forceinline__ void coarse_conv_line(const MGLevel &L, int bcx, int 
         }
 #pragma unroll
         for (int c = 0; c < kCR; ++c)
-            if (i0 + c < nx) L.t[(size_t)q * nx + i0 + c] = out[c];
+            if (i0 + c < iend) Xo[(size_t)q * nx + i0 + c] = out[c];
     }
 }
 
