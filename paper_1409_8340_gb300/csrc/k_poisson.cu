@@ -108,7 +108,16 @@ struct LineArgs {
     LineShape sh;
     const DevCtl *ctl;
     int level0;
+    // weighted sum of the final mu over the last two finest-level passes (recursive
+    // smoother only): stage 1 (colour 1) leaves block partials in blockred[0, nb1);
+    // stage 2 (colour 0) adds its own at blockred[kMeanOff + b] and its last block writes
+    // ctl->mu_mean.  0: off.
+    int mean_stage, mean_nb1;
+    DevCtl *ctlw;
+    double *blockred;
+    double wsum;
 };
+constexpr int kMeanOff = 4096;
 
 __global__ void __launch_bounds__(kThreads) line_smooth_kernel(LineArgs A)
 {
@@ -570,7 +579,8 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
 #pragma unroll
         for (int h = 0; h < C / 4; ++h) rv[h] = __ldg(reinterpret_cast<const float4 *>(L.r + base + i0 + 4 * h));
     };
-    if (first >= A.nlines) return;   // whole warps
+    float macc = 0.f;   // mean stage: this lane's weighted sum of the new values
+    if (first < A.nlines) {
     float4 rc[C / 4], rn[C / 4];
     issue(first, buf, rc);
     for (long long line = first; line < A.nlines; line += nwarps) {
@@ -687,12 +697,48 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
 #pragma unroll
         for (int h = 0; h < C; h += 4)
             *reinterpret_cast<float4 *>(dst + h) = make_float4(out[h], out[h + 1], out[h + 2], out[h + 3]);
+        if (A.mean_stage) {
+            // trapezoid weights: 1/2 on each open face
+            float ls = 0.f;
+#pragma unroll
+            for (int m = 0; m < C; ++m) {
+                const bool face = open && ((lane == 0 && m == 0) || (lane == 31 && m == C - 1));
+                ls += (face ? 0.5f : 1.f) * out[m];
+            }
+            float wyz = (A.bcy == kOpen && L.ny >= 2 && (j == 0 || j == L.ny - 1)) ? 0.5f : 1.f;
+            if (A.bcz == kOpen && L.nz >= 2 && (k == 0 || k == L.nz - 1)) wyz *= 0.5f;
+            macc += wyz * ls;
+        }
 #pragma unroll
         for (int h = 0; h < C / 4; ++h) rc[h] = rn[h];
     }
+    }
+    if (!A.mean_stage) return;
+    __shared__ double shd[32];
+    __shared__ int flag;
+    const double bs = block_sum((double)macc, shd);
+    if (threadIdx.x == 0) A.blockred[(A.mean_stage == 2 ? kMeanOff : 0) + blockIdx.x] = bs;
+    if (A.mean_stage != 2 || !last_block(&A.ctlw->ticket, gridDim.x, &flag)) return;
+    double t = 0.0;
+    for (int q = threadIdx.x; q < A.mean_nb1; q += blockDim.x) t += ((volatile double *)A.blockred)[q];
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) t += ((volatile double *)A.blockred)[kMeanOff + q];
+    t = block_sum(t, shd);
+    if (threadIdx.x == 0) {
+        A.ctlw->ticket = 0u;
+        A.ctlw->mu_mean = t / A.wsum;
+    }
 }
 
-static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s, long long *nl)
+// blocks of one recursive-smoother pass over nlines lines (one resident wave)
+static long long async_grid(long long nlines, int occ, int sms)
+{
+    const long long warps = (nlines + 3) / 4;
+    long long nb = (warps + kIirWarps - 1) / kIirWarps;
+    const long long cap = (long long)occ * sms;
+    return nb > cap ? cap : nb;
+}
+
+static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s, long long *nl, int mean_stage = 0)
 {
     const MGLevel &L = a.lev[l];
     LineArgs A;
@@ -704,7 +750,12 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.nlines = mg_lines_of_colour(L.ny, L.nz, color);
     A.ctl = a.ctl;
     A.level0 = (l == 0);
-    if (A.nlines == 0) return cudaSuccess;
+    A.mean_stage = 0;
+    A.mean_nb1 = 0;
+    A.ctlw = a.ctl;
+    A.blockred = a.blockred;
+    A.wsum = a.wsum;
+    if (A.nlines == 0 && mean_stage == 0) return cudaSuccess;
     if (L.iir == 16) {
         // asynchronous-copy variant, one resident wave of blocks (shared memory and
         // registers decide how many fit on an SM)
@@ -730,10 +781,13 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
             occ1 = occ1 < 1 ? 1 : occ1;
             occ2 = occ2 < 1 ? 1 : occ2;
         }
-        long long warps = (A.nlines + 3) / 4;
-        long long nb = (warps + kIirWarps - 1) / kIirWarps;
-        const long long cap = (long long)(L.iir_nw == 2 ? occ2 : occ1) * sms;
-        if (nb > cap) nb = cap;
+        const int occ = (L.iir_nw == 2) ? occ2 : occ1;
+        long long nb = async_grid(A.nlines, occ, sms);
+        if (mean_stage) {
+            A.mean_stage = mean_stage;
+            A.mean_nb1 = (int)async_grid(mg_lines_of_colour(L.ny, L.nz, 1), occ, sms);
+            if (nb < 1) nb = 1;   // the reduction runs even without lines of this colour
+        }
         if (L.iir_nw == 2) line_iir_async_kernel<16, 2><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
         else line_iir_async_kernel<16, 1><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
         ++*nl;
@@ -957,7 +1011,10 @@ static cudaError_t coarse_solve(const PoissonArgs &a, int l, cudaStream_t s, lon
 // skip_first: the finest level's first colour-0 pass is left out.  Right after a
 // V-cycle (which ends with a colour-0 pass on the same right-hand side) it would repeat
 // exact line solves on identical input: the same bits.
-static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long *nl, bool skip_first = false)
+// mean_out (finest level only): the closing two passes also sum the weighted final mu
+// into ctl->mu_mean (vcycle_mean_fusable says when the smoother there can)
+static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long *nl, bool skip_first = false,
+                          bool mean_out = false)
 {
     const int bcx = a.g.bcx, bcy = a.g.bcy, bcz = a.g.bcz;
     if (l == a.nlevels - 1) {
@@ -1001,19 +1058,21 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     vcycle(a, l + 1, s, nl);
     if (v4) prolong4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz, oc);
     else prolong_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz, oc);
-    smooth(a, l, 1, s, nl);
-    smooth(a, l, 0, s, nl);
+    smooth(a, l, 1, s, nl, mean_out ? 1 : 0);
+    smooth(a, l, 0, s, nl, mean_out ? 2 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches, bool after_cycle)
+bool vcycle_mean_fusable(const PoissonArgs &a) { return a.nlevels > 1 && a.lev[0].iir == 16; }
+
+cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches, bool after_cycle, bool mean_out)
 {
     // the zebra colouring (j + k) % 2 is a proper two-colouring of the lines unless a
     // periodic axis has odd length; only then is a repeated colour-0 pass not a no-op
     const MGLevel &F = a.lev[0];
     const bool proper = (a.g.bcy == kOpen || F.ny == 1 || (F.ny % 2) == 0) &&
                         (a.g.bcz == kOpen || F.nz == 1 || (F.nz % 2) == 0);
-    return vcycle(a, 0, s, launches, after_cycle && proper && a.nlevels > 1);
+    return vcycle(a, 0, s, launches, after_cycle && proper && a.nlevels > 1, mean_out && vcycle_mean_fusable(a));
 }
 
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s)
@@ -1073,9 +1132,9 @@ __global__ void mu_shift_kernel(long long N, float *mu, const DevCtl *ctl)
     }
 }
 
-cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s)
+cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s, bool mean_done)
 {
-    mu_mean_kernel<<<grid_xy(a.g.nx, a.g.ny), kGX, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum);
+    if (!mean_done) mu_mean_kernel<<<grid_xy(a.g.nx, a.g.ny), kGX, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum);
     mu_shift_kernel<<<grid_blocks(a.g.N, 8), kThreads, 0, s>>>(a.g.N, a.mu, a.ctl);
     return cudaGetLastError();
 }

@@ -774,11 +774,13 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
 static long long poisson_sequence(tdgl_handle *h, cudaStream_t s, cudaError_t *err)
 {
     long long nl = 1;
+    const int nc = h->cfg.poisson_cycles;
+    const bool fm = nc > 0 && vcycle_mean_fusable(h->pa);   // the last cycle leaves the mean of mu
     cudaError_t e = launch_poisson_rhs(h->pa, h->psi[h->cur], s);
-    for (int q = 0; q < h->cfg.poisson_cycles && e == cudaSuccess; ++q) e = launch_vcycle(h->pa, s, &nl, q > 0);
-    if (e == cudaSuccess) e = launch_project_mu(h->pa, s);
+    for (int q = 0; q < nc && e == cudaSuccess; ++q) e = launch_vcycle(h->pa, s, &nl, q > 0, fm && q == nc - 1);
+    if (e == cudaSuccess) e = launch_project_mu(h->pa, s, fm);
     *err = e;
-    return nl + 2;
+    return nl + (fm ? 1 : 2);
 }
 
 // Capture the sequence for the current psi buffer (false: graphs are not used).
@@ -842,8 +844,10 @@ int tdgl_solve_mu(tdgl_handle *h)
     }
     long long nl = 1;
     int cycles = 0;
+    // a fixed number of cycles: the last one leaves the mean of mu
+    const bool fm = c.poisson_tol <= 0 && c.poisson_cycles > 0 && vcycle_mean_fusable(h->pa);
     for (int q = 0; q < c.poisson_cycles; ++q, ++cycles)
-        if (launch_vcycle(h->pa, s, &nl, q > 0) != cudaSuccess) return TDGL_ERR_CUDA;
+        if (launch_vcycle(h->pa, s, &nl, q > 0, fm && q == c.poisson_cycles - 1) != cudaSuccess) return TDGL_ERR_CUDA;
     if (c.poisson_tol > 0) {
         for (;;) {
             if (launch_poisson_residual(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
@@ -856,8 +860,8 @@ int tdgl_solve_mu(tdgl_handle *h)
             ++cycles;
         }
     }
-    if (launch_project_mu(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
-    nl += 2;
+    if (launch_project_mu(h->pa, s, fm) != cudaSuccess) return TDGL_ERR_CUDA;
+    nl += fm ? 1 : 2;
     h->last_cycles = cycles;
     h->prof.vcycles += cycles;
     h->prof.kernel_launches += nl;

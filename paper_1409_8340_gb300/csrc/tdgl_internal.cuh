@@ -300,9 +300,13 @@ struct PoissonArgs {
 };
 cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStream_t s);
 // after_cycle: the call directly follows a V-cycle on the same right-hand side
-cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches, bool after_cycle = false);
+// mean_out: the cycle's closing finest-level passes also leave the weighted mean of mu in
+// ctl->mu_mean, where vcycle_mean_fusable allows (launch_project_mu then skips its own sum)
+cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launches, bool after_cycle = false,
+                          bool mean_out = false);
+bool vcycle_mean_fusable(const PoissonArgs &a);
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s);
-cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s);
+cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s, bool mean_done = false);
 cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
 
 // Insulating inclusions (k_insulating.cu)

@@ -139,3 +139,34 @@ def test_observables_match_oracle(O):
     assert obs["vortex_signed"] * p.nz == pytest.approx(5 * p.nz)
     assert tot_o == 5 * p.nz
     assert abs(obs["vortex_unsigned"] - np.abs(n_o).sum() / p.nz) <= 0.01 * max(1.0, np.abs(n_o).sum() / p.nz)
+
+
+@pytest.mark.parametrize("bc", [(OP, P, P), (OP, OP, OP), (P, P, P)])
+def test_fused_mean_projection(O, bc):
+    """With a fixed number of V-cycles on a 512-site line, the closing finest-level passes
+    also sum the trapezoid-weighted mu; the projection then removes that mean.  A start
+    shifted by a constant (which the V-cycles keep) must come out with zero weighted
+    mean, on the direct path (first solve) and the graph-replayed one (later solves),
+    and equal the exact solution."""
+    import torch
+    from paper_1409_8340_gb300.solver import Params
+    ny, nz = (48, 24) if bc[1] == P else (33, 17)
+    p = Params(512, ny, nz, bc=bc, Bz=0.2, Jext=0.02 if bc[0] == OP else 0.0, poisson_cycles=8)
+    if bc == (P, P, P):
+        p = quantised(p, 2)
+    G = oracle_grid(O, p)
+    w = O.site_weights(G)
+    psi = I.random_psi(p.nx, p.ny, p.nz, 61).astype(np.complex64).astype(np.complex128)
+    s = make_solver(p, np.ones(p.shape, np.float32), psi)
+    mu0 = (I.uniform(62, "t.mu", p.N).reshape(p.shape) + 0.5).astype(np.float32)
+    # the shift is applied in FP32: each site may keep half an ulp of the raw values
+    bound = w.sum() * 0.5 * np.spacing(np.float32(2.0))
+    for n in range(3):
+        s.set_state(torch.as_tensor(psi.astype(np.complex64)), torch.as_tensor(mu0), 0.0)
+        s.solve_mu()
+        _, mu_g = gpu_state(s)
+        assert abs((w * mu_g).sum()) <= bound + 1e-6 * (w * np.abs(mu_g)).sum(), n
+        f = s.internals()[2].cpu().numpy().astype(np.float64)
+        mu_o = O.poisson_solve(G, f)
+        err = np.max(np.abs(mu_g - mu_o)) / max(1e-30, np.max(np.abs(mu_o)))
+        assert err < 2e-4, (n, err)
