@@ -24,6 +24,8 @@
 #include <cudaTypedefs.h>
 #include <float.h>
 
+#include <type_traits>
+
 #include "sweep_tile.cuh"
 #include "tdgl_internal.cuh"
 
@@ -184,169 +186,177 @@ __global__ void __launch_bounds__(kThreads, 3)
         __syncwarp();
     } else {
         // ---------------- consumers: row `warp`, sites x, x+1 ----------------
-        const int r = warp;
-        const int x = T.x0 + 2 * lane, j = T.j0 + r;
-        const bool in = (r < T.nr) && (2 * lane < T.w);
-        const bool xper = (g.bcx == kPeriodic), yper = (g.bcy == kPeriodic), zper = (g.bcz == kPeriodic);
-        const bool xlo = (x == 0), xhi = (x + 2 >= g.nx);
-        const bool ylo = (j == 0), yhi = (j == g.ny - 1);
-        const bool zact = g.nz >= 2;
-        const int jc = min(j, g.ny - 1);
-        const float wy_f = yper ? 1.f : (ylo ? 2.f : (yhi ? 0.f : 1.f));
-        const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
-        const bool yedge = (wy_f != 1.f) || (wy_b != 1.f);
-        float2 yf0 = cmk(0.f, 0.f), yf1 = yf0, zf0 = yf0, zf1 = yf0;
-        const bool ywrap = XZ && yper && (ylo || yhi);   // a row next to the xz gauge's y wrap
-        float4 wxq = make_float4(1.f, 0.f, 1.f, 0.f);
-        if (in) {
-            const float sy = g.ht2 * g.cy, szc = g.ht2 * g.cz;
-            if (XZ) {
-                yf0 = yf1 = cmk(sy, 0.f);
-                zf0 = zf1 = cscale(szc, g.Zj[jc]);
-                if (ywrap) wxq = reinterpret_cast<const float4 *>(g.Wx)[x >> 1];
-            } else {
-                const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
-                const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
-                yf0 = cscale(sy, lo2(uy));
-                yf1 = cscale(sy, hi2(uy));
-                zf0 = cscale(szc, lo2(uz));
-                zf1 = cscale(szc, hi2(uz));
-            }
-        }
-        const float2 Ux = ldx<false>(&a.ctl->Ux);
-        const float2 xf = cscale(g.ht2 * g.cx, XZ ? cmul(Ux, g.Xj[jc]) : Ux);
-        const uchar2 *__restrict__ lk2 = reinterpret_cast<const uchar2 *>(g.lk);
-        float4 *__restrict__ dst = reinterpret_cast<float4 *>(a.dst);
-        const long long rowq = g.nx >> 1, plq = rowq * g.ny;
-        const long long q0 = (x >> 1) + rowq * jc;
-        bool ok = true;
-        for (int t = 1; t + 1 < nplanes; ++t) {
-            const int k = k0 - 1 + t;
-            if (t == 1) {
-                ok = mbar_wait(&full[0], 0u, deadline) && mbar_wait(&full[1], 0u, deadline);
-            }
-            ok = ok && mbar_wait(&full[(t + 1) % kTS], (unsigned)(((t + 1) / kTS) & 1), deadline);
-            if (!__all_sync(0xffffffffu, ok)) {
-                if (lane == 0) failed = 1;
-                break;
-            }
-            const Stage &Pm = ring[(t - 1) % kTS], &Pc = ring[t % kTS], &Pp = ring[(t + 1) % kTS];
+        // blocks whose tile touches no x or y face (nor a periodic wrap there) run the
+        // same code with the face tests folded away
+        const bool edge = T.x0 == 0 || T.x0 + kTX >= g.nx || T.j0 == 0 || T.j0 + kTR >= g.ny;
+        auto consume = [&](auto edge_t) {
+            constexpr bool EDGE = decltype(edge_t)::value;
+            const int r = warp;
+            const int x = T.x0 + 2 * lane, j = T.j0 + r;
+            const bool in = !EDGE || ((r < T.nr) && (2 * lane < T.w));
+            const bool xper = (g.bcx == kPeriodic), yper = (g.bcy == kPeriodic), zper = (g.bcz == kPeriodic);
+            const bool xlo = EDGE && (x == 0), xhi = EDGE && (x + 2 >= g.nx);
+            const bool ylo = EDGE && (j == 0), yhi = EDGE && (j == g.ny - 1);
+            const bool zact = g.nz >= 2;
+            const int jc = min(j, g.ny - 1);
+            const float wy_f = yper ? 1.f : (ylo ? 2.f : (yhi ? 0.f : 1.f));
+            const float wy_b = yper ? 1.f : (yhi ? 2.f : (ylo ? 0.f : 1.f));
+            const bool yedge = (wy_f != 1.f) || (wy_b != 1.f);
+            float2 yf0 = cmk(0.f, 0.f), yf1 = yf0, zf0 = yf0, zf1 = yf0;
+            const bool ywrap = XZ && yper && (ylo || yhi);   // a row next to the xz gauge's y wrap
+            float4 wxq = make_float4(1.f, 0.f, 1.f, 0.f);
             if (in) {
-                const uchar2 lkc = MASK ? lk2[q0 + plq * k] : make_uchar2(0x3f, 0x3f);
-                const int cx = 2 + 2 * lane;
-                const float4 pc = *reinterpret_cast<const float4 *>(&Pc.psi[r + 1][cx]);
-                const float2 c0 = lo2(pc), c1 = hi2(pc);
-                float2 xl = Pc.psi[r + 1][cx - 1], xr = Pc.psi[r + 1][cx + 2];
-                float4 yf = *reinterpret_cast<const float4 *>(&Pc.psi[r + 2][cx]);
-                float4 yb = *reinterpret_cast<const float4 *>(&Pc.psi[r][cx]);
-                // neighbours across a periodic wrap lie outside the boxes: read them directly
-                const long long rowk = (long long)k * g.ny;
-                if (xper && xlo) xl = a.src[(rowk + j) * g.nx + g.nx - 1];
-                if (xper && xhi) xr = a.src[(rowk + j) * g.nx];
-                if (yper && ylo) yb = reinterpret_cast<const float4 *>(a.src)[((rowk + g.ny - 1) * g.nx + x) >> 1];
-                if (yper && yhi) yf = reinterpret_cast<const float4 *>(a.src)[(rowk * g.nx + x) >> 1];
-                const float4 bc = *reinterpret_cast<const float4 *>(&Pc.b[r][2 * lane]);
-                const float4 Dc = *reinterpret_cast<const float4 *>(&Pc.D[r][2 * lane]);
-                // the same boundary rules and arithmetic order as the tiled kernel (MODE 0)
-                float2 xl0 = xl, xr1 = xr, c1x = c1, c0x = c0;
-                if (xlo || xhi) {
-                    if (xper) {
-                        if (!XZ) {   // the yz gauge's wrap link carries conj(P_jk); the xz gauge's is plain
-                            const float2 P = cmul(g.Py[jc], g.Pz[k]);
-                            if (xlo) xl0 = cmul(P, xl);
-                            if (xhi) xr1 = cmulc(P, xr);
-                        }
-                    } else {
-                        if (xlo) {
-                            c1x = cscale(2.f, c1);
-                            xl0 = cmk(0.f, 0.f);
-                        }
-                        if (xhi) {
-                            c0x = cscale(2.f, c0);
-                            xr1 = cmk(0.f, 0.f);
-                        }
-                    }
+                const float sy = g.ht2 * g.cy, szc = g.ht2 * g.cz;
+                if (XZ) {
+                    yf0 = yf1 = cmk(sy, 0.f);
+                    zf0 = zf1 = cscale(szc, g.Zj[jc]);
+                    if (ywrap) wxq = reinterpret_cast<const float4 *>(g.Wx)[x >> 1];
+                } else {
+                    const float4 uy = reinterpret_cast<const float4 *>(g.Uy)[x >> 1];
+                    const float4 uz = reinterpret_cast<const float4 *>(g.Uz)[x >> 1];
+                    yf0 = cscale(sy, lo2(uy));
+                    yf1 = cscale(sy, hi2(uy));
+                    zf0 = cscale(szc, lo2(uz));
+                    zf1 = cscale(szc, hi2(uz));
                 }
-                float2 yf_0 = lo2(yf), yf_1 = hi2(yf), yb_0 = lo2(yb), yb_1 = hi2(yb);
-                if (ywrap) {   // xz gauge: wrap link W = Wx[i] Wz[k] from row ny-1 to row 0
-                    const float2 wz = g.Wz[k];
-                    const float2 W0 = cmul(lo2(wxq), wz), W1 = cmul(hi2(wxq), wz);
-                    if (yhi) {
-                        yf_0 = cmul(W0, yf_0);
-                        yf_1 = cmul(W1, yf_1);
-                    }
-                    if (ylo) {
-                        yb_0 = cmulc(W0, yb_0);
-                        yb_1 = cmulc(W1, yb_1);
-                    }
-                }
-                if (yedge) {
-                    yf_0 = cscale(wy_f, yf_0);
-                    yf_1 = cscale(wy_f, yf_1);
-                    yb_0 = cscale(wy_b, yb_0);
-                    yb_1 = cscale(wy_b, yb_1);
-                }
-                if (MASK) {   // links next to insulating sites removed
-                    const unsigned l0 = lkc.x, l1 = lkc.y;
-                    c1x = cscale((l0 & kLkXp) ? 1.f : 0.f, c1x);
-                    xl0 = cscale((l0 & kLkXm) ? 1.f : 0.f, xl0);
-                    xr1 = cscale((l1 & kLkXp) ? 1.f : 0.f, xr1);
-                    c0x = cscale((l1 & kLkXm) ? 1.f : 0.f, c0x);
-                    yf_0 = cscale((l0 & kLkYp) ? 1.f : 0.f, yf_0);
-                    yb_0 = cscale((l0 & kLkYm) ? 1.f : 0.f, yb_0);
-                    yf_1 = cscale((l1 & kLkYp) ? 1.f : 0.f, yf_1);
-                    yb_1 = cscale((l1 & kLkYm) ? 1.f : 0.f, yb_1);
-                }
-                float2 ns0 = cmul(xf, c1x), ns1 = cmulc(xf, c0x);
-                cfmac(ns0, xf, xl0);
-                cfma(ns1, xf, xr1);
-                cfma(ns0, yf0, yf_0);
-                cfmac(ns0, yf0, yb_0);
-                cfma(ns1, yf1, yf_1);
-                cfmac(ns1, yf1, yb_1);
-                if (zact) {
-                    const float4 pzp = *reinterpret_cast<const float4 *>(&Pp.psi[r + 1][cx]);
-                    const float4 pzm = *reinterpret_cast<const float4 *>(&Pm.psi[r + 1][cx]);
-                    float wz_f = 1.f, wz_b = 1.f;
-                    if (!zper) {
-                        if (k == 0) {
-                            wz_f = 2.f;
-                            wz_b = 0.f;
-                        } else if (k == g.nz - 1) {
-                            wz_f = 0.f;
-                            wz_b = 2.f;
-                        }
-                    }
-                    float4 zpp =
-                        (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
-                    float4 zmm =
-                        (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
-                    if (MASK) {
-                        const float f0 = (lkc.x & kLkZp) ? 1.f : 0.f, b0 = (lkc.x & kLkZm) ? 1.f : 0.f;
-                        const float f1 = (lkc.y & kLkZp) ? 1.f : 0.f, b1 = (lkc.y & kLkZm) ? 1.f : 0.f;
-                        zpp = make_float4(f0 * zpp.x, f0 * zpp.y, f1 * zpp.z, f1 * zpp.w);
-                        zmm = make_float4(b0 * zmm.x, b0 * zmm.y, b1 * zmm.z, b1 * zmm.w);
-                    }
-                    cfma(ns0, zf0, lo2(zpp));
-                    cfmac(ns0, zf0, lo2(zmm));
-                    cfma(ns1, zf1, hi2(zpp));
-                    cfmac(ns1, zf1, hi2(zmm));
-                }
-                const float2 b0 = lo2(bc), b1 = hi2(bc), D0 = lo2(Dc), D1 = hi2(Dc);
-                const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
-                const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
-                const float2 n0 = cscale(__frcp_rn(cabs2(D0)), cmulc(D0, s0));
-                const float2 n1 = cscale(__frcp_rn(cabs2(D1)), cmulc(D1, s1));
-                dst[q0 + plq * k] = make_float4(n0.x, n0.y, n1.x, n1.y);
-                float r2a = cabs2(r0), r2b = cabs2(r1);
-                r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
-                r2b = (r2b <= FLT_MAX) ? r2b : INFINITY;
-                rmax = fmaxf(rmax, fmaxf(r2a, r2b));
             }
-            // the plane below is no longer needed by this warp
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[(t - 1) % kTS]);
-        }
+            const float2 Ux = ldx<false>(&a.ctl->Ux);
+            const float2 xf = cscale(g.ht2 * g.cx, XZ ? cmul(Ux, g.Xj[jc]) : Ux);
+            const uchar2 *__restrict__ lk2 = reinterpret_cast<const uchar2 *>(g.lk);
+            float4 *__restrict__ dst = reinterpret_cast<float4 *>(a.dst);
+            const long long rowq = g.nx >> 1, plq = rowq * g.ny;
+            const long long q0 = (x >> 1) + rowq * jc;
+            bool ok = true;
+            for (int t = 1; t + 1 < nplanes; ++t) {
+                const int k = k0 - 1 + t;
+                if (t == 1) {
+                    ok = mbar_wait(&full[0], 0u, deadline) && mbar_wait(&full[1], 0u, deadline);
+                }
+                ok = ok && mbar_wait(&full[(t + 1) % kTS], (unsigned)(((t + 1) / kTS) & 1), deadline);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) failed = 1;
+                    break;
+                }
+                const Stage &Pm = ring[(t - 1) % kTS], &Pc = ring[t % kTS], &Pp = ring[(t + 1) % kTS];
+                if (in) {
+                    const uchar2 lkc = MASK ? lk2[q0 + plq * k] : make_uchar2(0x3f, 0x3f);
+                    const int cx = 2 + 2 * lane;
+                    const float4 pc = *reinterpret_cast<const float4 *>(&Pc.psi[r + 1][cx]);
+                    const float2 c0 = lo2(pc), c1 = hi2(pc);
+                    float2 xl = Pc.psi[r + 1][cx - 1], xr = Pc.psi[r + 1][cx + 2];
+                    float4 yf = *reinterpret_cast<const float4 *>(&Pc.psi[r + 2][cx]);
+                    float4 yb = *reinterpret_cast<const float4 *>(&Pc.psi[r][cx]);
+                    // neighbours across a periodic wrap lie outside the boxes: read them directly
+                    const long long rowk = (long long)k * g.ny;
+                    if (xper && xlo) xl = a.src[(rowk + j) * g.nx + g.nx - 1];
+                    if (xper && xhi) xr = a.src[(rowk + j) * g.nx];
+                    if (yper && ylo) yb = reinterpret_cast<const float4 *>(a.src)[((rowk + g.ny - 1) * g.nx + x) >> 1];
+                    if (yper && yhi) yf = reinterpret_cast<const float4 *>(a.src)[(rowk * g.nx + x) >> 1];
+                    const float4 bc = *reinterpret_cast<const float4 *>(&Pc.b[r][2 * lane]);
+                    const float4 Dc = *reinterpret_cast<const float4 *>(&Pc.D[r][2 * lane]);
+                    // the same boundary rules and arithmetic order as the tiled kernel (MODE 0)
+                    float2 xl0 = xl, xr1 = xr, c1x = c1, c0x = c0;
+                    if (xlo || xhi) {
+                        if (xper) {
+                            if (!XZ) {   // the yz gauge's wrap link carries conj(P_jk); the xz gauge's is plain
+                                const float2 P = cmul(g.Py[jc], g.Pz[k]);
+                                if (xlo) xl0 = cmul(P, xl);
+                                if (xhi) xr1 = cmulc(P, xr);
+                            }
+                        } else {
+                            if (xlo) {
+                                c1x = cscale(2.f, c1);
+                                xl0 = cmk(0.f, 0.f);
+                            }
+                            if (xhi) {
+                                c0x = cscale(2.f, c0);
+                                xr1 = cmk(0.f, 0.f);
+                            }
+                        }
+                    }
+                    float2 yf_0 = lo2(yf), yf_1 = hi2(yf), yb_0 = lo2(yb), yb_1 = hi2(yb);
+                    if (ywrap) {   // xz gauge: wrap link W = Wx[i] Wz[k] from row ny-1 to row 0
+                        const float2 wz = g.Wz[k];
+                        const float2 W0 = cmul(lo2(wxq), wz), W1 = cmul(hi2(wxq), wz);
+                        if (yhi) {
+                            yf_0 = cmul(W0, yf_0);
+                            yf_1 = cmul(W1, yf_1);
+                        }
+                        if (ylo) {
+                            yb_0 = cmulc(W0, yb_0);
+                            yb_1 = cmulc(W1, yb_1);
+                        }
+                    }
+                    if (yedge) {
+                        yf_0 = cscale(wy_f, yf_0);
+                        yf_1 = cscale(wy_f, yf_1);
+                        yb_0 = cscale(wy_b, yb_0);
+                        yb_1 = cscale(wy_b, yb_1);
+                    }
+                    if (MASK) {   // links next to insulating sites removed
+                        const unsigned l0 = lkc.x, l1 = lkc.y;
+                        c1x = cscale((l0 & kLkXp) ? 1.f : 0.f, c1x);
+                        xl0 = cscale((l0 & kLkXm) ? 1.f : 0.f, xl0);
+                        xr1 = cscale((l1 & kLkXp) ? 1.f : 0.f, xr1);
+                        c0x = cscale((l1 & kLkXm) ? 1.f : 0.f, c0x);
+                        yf_0 = cscale((l0 & kLkYp) ? 1.f : 0.f, yf_0);
+                        yb_0 = cscale((l0 & kLkYm) ? 1.f : 0.f, yb_0);
+                        yf_1 = cscale((l1 & kLkYp) ? 1.f : 0.f, yf_1);
+                        yb_1 = cscale((l1 & kLkYm) ? 1.f : 0.f, yb_1);
+                    }
+                    float2 ns0 = cmul(xf, c1x), ns1 = cmulc(xf, c0x);
+                    cfmac(ns0, xf, xl0);
+                    cfma(ns1, xf, xr1);
+                    cfma(ns0, yf0, yf_0);
+                    cfmac(ns0, yf0, yb_0);
+                    cfma(ns1, yf1, yf_1);
+                    cfmac(ns1, yf1, yb_1);
+                    if (zact) {
+                        const float4 pzp = *reinterpret_cast<const float4 *>(&Pp.psi[r + 1][cx]);
+                        const float4 pzm = *reinterpret_cast<const float4 *>(&Pm.psi[r + 1][cx]);
+                        float wz_f = 1.f, wz_b = 1.f;
+                        if (!zper) {
+                            if (k == 0) {
+                                wz_f = 2.f;
+                                wz_b = 0.f;
+                            } else if (k == g.nz - 1) {
+                                wz_f = 0.f;
+                                wz_b = 2.f;
+                            }
+                        }
+                        float4 zpp =
+                            (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
+                        float4 zmm =
+                            (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
+                        if (MASK) {
+                            const float f0 = (lkc.x & kLkZp) ? 1.f : 0.f, b0 = (lkc.x & kLkZm) ? 1.f : 0.f;
+                            const float f1 = (lkc.y & kLkZp) ? 1.f : 0.f, b1 = (lkc.y & kLkZm) ? 1.f : 0.f;
+                            zpp = make_float4(f0 * zpp.x, f0 * zpp.y, f1 * zpp.z, f1 * zpp.w);
+                            zmm = make_float4(b0 * zmm.x, b0 * zmm.y, b1 * zmm.z, b1 * zmm.w);
+                        }
+                        cfma(ns0, zf0, lo2(zpp));
+                        cfmac(ns0, zf0, lo2(zmm));
+                        cfma(ns1, zf1, hi2(zpp));
+                        cfmac(ns1, zf1, hi2(zmm));
+                    }
+                    const float2 b0 = lo2(bc), b1 = hi2(bc), D0 = lo2(Dc), D1 = hi2(Dc);
+                    const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
+                    const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
+                    const float2 n0 = cscale(__frcp_rn(cabs2(D0)), cmulc(D0, s0));
+                    const float2 n1 = cscale(__frcp_rn(cabs2(D1)), cmulc(D1, s1));
+                    dst[q0 + plq * k] = make_float4(n0.x, n0.y, n1.x, n1.y);
+                    float r2a = cabs2(r0), r2b = cabs2(r1);
+                    r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
+                    r2b = (r2b <= FLT_MAX) ? r2b : INFINITY;
+                    rmax = fmaxf(rmax, fmaxf(r2a, r2b));
+                }
+                // the plane below is no longer needed by this warp
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(t - 1) % kTS]);
+            }
+        };
+        if (edge) consume(std::true_type{});
+        else consume(std::false_type{});
     }
     __syncthreads();
     if (failed) {
