@@ -227,17 +227,22 @@ __global__ void __launch_bounds__(kThreads, 3)
             const long long rowq = g.nx >> 1, plq = rowq * g.ny;
             const long long q0 = (x >> 1) + rowq * jc;
             bool ok = true;
+            // stages of planes t - 1, t, t + 1 and the phase parity of plane t + 1's stage,
+            // advanced by one plane per iteration
+            int sm = 0, sc = 1, sp = 2;
+            unsigned php = 0u;
+            float4 *dp = dst + q0 + plq * k0;   // plane k0 - 1 + t of this lane's site pair
             for (int t = 1; t + 1 < nplanes; ++t) {
                 const int k = k0 - 1 + t;
                 if (t == 1) {
                     ok = mbar_wait(&full[0], 0u, deadline) && mbar_wait(&full[1], 0u, deadline);
                 }
-                ok = ok && mbar_wait(&full[(t + 1) % kTS], (unsigned)(((t + 1) / kTS) & 1), deadline);
+                ok = ok && mbar_wait(&full[sp], php, deadline);
                 if (!__all_sync(0xffffffffu, ok)) {
                     if (lane == 0) failed = 1;
                     break;
                 }
-                const Stage &Pm = ring[(t - 1) % kTS], &Pc = ring[t % kTS], &Pp = ring[(t + 1) % kTS];
+                const Stage &Pm = ring[sm], &Pc = ring[sc], &Pp = ring[sp];
                 if (in) {
                     const uchar2 lkc = MASK ? lk2[q0 + plq * k] : make_uchar2(0x3f, 0x3f);
                     const int cx = 2 + 2 * lane;
@@ -314,20 +319,12 @@ __global__ void __launch_bounds__(kThreads, 3)
                     if (zact) {
                         const float4 pzp = *reinterpret_cast<const float4 *>(&Pp.psi[r + 1][cx]);
                         const float4 pzm = *reinterpret_cast<const float4 *>(&Pm.psi[r + 1][cx]);
-                        float wz_f = 1.f, wz_b = 1.f;
-                        if (!zper) {
-                            if (k == 0) {
-                                wz_f = 2.f;
-                                wz_b = 0.f;
-                            } else if (k == g.nz - 1) {
-                                wz_f = 0.f;
-                                wz_b = 2.f;
-                            }
+                        float4 zpp = pzp, zmm = pzm;
+                        if (!zper && (k == 0 || k == g.nz - 1)) {   // an open z face (the whole plane)
+                            const float wz_f = (k == 0) ? 2.f : 0.f, wz_b = (k == 0) ? 0.f : 2.f;
+                            zpp = make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
+                            zmm = make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
                         }
-                        float4 zpp =
-                            (wz_f == 1.f) ? pzp : make_float4(wz_f * pzp.x, wz_f * pzp.y, wz_f * pzp.z, wz_f * pzp.w);
-                        float4 zmm =
-                            (wz_b == 1.f) ? pzm : make_float4(wz_b * pzm.x, wz_b * pzm.y, wz_b * pzm.z, wz_b * pzm.w);
                         if (MASK) {
                             const float f0 = (lkc.x & kLkZp) ? 1.f : 0.f, b0 = (lkc.x & kLkZm) ? 1.f : 0.f;
                             const float f1 = (lkc.y & kLkZp) ? 1.f : 0.f, b1 = (lkc.y & kLkZm) ? 1.f : 0.f;
@@ -344,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 3)
                     const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
                     const float2 n0 = cscale(__frcp_rn(cabs2(D0)), cmulc(D0, s0));
                     const float2 n1 = cscale(__frcp_rn(cabs2(D1)), cmulc(D1, s1));
-                    dst[q0 + plq * k] = make_float4(n0.x, n0.y, n1.x, n1.y);
+                    *dp = make_float4(n0.x, n0.y, n1.x, n1.y);
                     float r2a = cabs2(r0), r2b = cabs2(r1);
                     r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
                     r2b = (r2b <= FLT_MAX) ? r2b : INFINITY;
@@ -352,7 +349,14 @@ __global__ void __launch_bounds__(kThreads, 3)
                 }
                 // the plane below is no longer needed by this warp
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[(t - 1) % kTS]);
+                if (lane == 0) mbar_arrive(&empty[sm]);
+                sm = sc;
+                sc = sp;
+                if (++sp == kTS) {
+                    sp = 0;
+                    php ^= 1u;
+                }
+                dp += plq;
             }
         };
         if (edge) consume(std::true_type{});
