@@ -22,6 +22,7 @@
 // (constants) is removed in FP64: the right-hand side is projected onto
 // sum_m w_m F_m = 0 and the solution onto sum_m w_m mu_m = 0, w the trapezoid
 // weights (1/2 per open face).
+#include <cudaTypedefs.h>
 #include <float.h>
 #include <math.h>
 
@@ -29,6 +30,7 @@
 #include <vector>
 
 #include "mg_tile.cuh"
+#include "tma_util.cuh"
 
 namespace tdgl {
 
@@ -541,16 +543,39 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
 // over the 2C values of the two lanes before (after) its chunk; at the mirrored ends the
 // first two (last two) lanes read the extended line's values by shuffle from the lanes
 // that hold them.
-template <int C, int NW>
-__global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs A)
+// TMA: the four rows come as four boxes of the level's tensor map (one lane issues them,
+// completing the warp's mbarrier) into an unpadded 8 KB buffer in the 128-byte swizzled
+// layout, which keeps the lanes' 16-byte reads on distinct banks: no per-lane copies.
+// Each wait is bounded; one that runs out records TDGL_ERR_TIMEOUT and ends the warp's
+// lines after its copies in flight have landed (again bounded).
+constexpr int kIirTmaBytes = 4 * 512 * 4;   // a warp's buffer: four 512-site rows
+constexpr unsigned long long kIirWaitNs = 2000000000ull;
+template <int C, int NW, bool TMA>
+__global__ void __launch_bounds__(kIirWarps * 32)
+    line_iir_async_kernel(LineArgs A, const __grid_constant__ CUtensorMap map_u)
 {
     static_assert(NW == 1 || NW == 2, "warm-up over one or two neighbour lanes");
-    constexpr int NX = 32 * C, ROW = NX + NX / 8;   // padded row length in floats
+    static_assert(!TMA || C == 16, "tensor-map boxes hold 512-site lines");
+    constexpr int NX = 32 * C, ROW = TMA ? NX : NX + NX / 8;   // row length in floats (padded for copies)
     extern __shared__ __align__(16) float sm_iir[];
     const MGLevel &L = A.L;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *buf = sm_iir + (size_t)wib * 4 * ROW;   // [4 rows][ROW]
+    float *sm_base = sm_iir;
+    if (TMA)   // the swizzled layout repeats every 1024 bytes: buffers on 1024-byte boundaries
+        sm_base = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sm_iir) + 1023) & ~(uintptr_t)1023);
+    float *buf = sm_base + (size_t)wib * 4 * ROW;   // [4 rows][ROW]
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(sm_base + (size_t)kIirWarps * 4 * ROW) + wib;
+    unsigned parity = 0u;
+    bool issued = false;   // TMA: a line's boxes are in flight
+    if (TMA) {
+        if (lane == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+    }
+    const unsigned long long deadline = TMA ? gtime() + kIirWaitNs : 0ull;
     const long long nwarps = (long long)gridDim.x * kIirWarps;
     const long long first = (long long)blockIdx.x * kIirWarps + wib;
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
@@ -563,34 +588,66 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
         int j, k;
         line_jk(line, A.color, L.ny, L.nz, j, k);
         const long long base = (long long)NX * j + plane * k;
-        const float *src[4];
-        src[0] = ya ? L.u + (long long)NX * nb_idx(j, 1, L.ny, A.bcy) + plane * k : L.u + base;
-        src[1] = ya ? L.u + (long long)NX * nb_idx(j, -1, L.ny, A.bcy) + plane * k : L.u + base;
-        src[2] = za ? L.u + (long long)NX * j + plane * nb_idx(k, 1, L.nz, A.bcz) : L.u + base;
-        src[3] = za ? L.u + (long long)NX * j + plane * nb_idx(k, -1, L.nz, A.bcz) : L.u + base;
+        long long src[4];   // float offsets of the rows in u
+        src[0] = ya ? (long long)NX * nb_idx(j, 1, L.ny, A.bcy) + plane * k : base;
+        src[1] = ya ? (long long)NX * nb_idx(j, -1, L.ny, A.bcy) + plane * k : base;
+        src[2] = za ? (long long)NX * j + plane * nb_idx(k, 1, L.nz, A.bcz) : base;
+        src[3] = za ? (long long)NX * j + plane * nb_idx(k, -1, L.nz, A.bcz) : base;
+        if constexpr (TMA) {
+            if (lane == 0) {
+                // the warp's reads of the buffer (generic proxy) precede these writes
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect(bar, (unsigned)kIirTmaBytes);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int h = 0; h < C / 4; ++h) {
-                const int t = 4 * (h * 32 + lane);   // coalesced: lane-consecutive 16-byte chunks
-                cp_async16(dst + a * ROW + pad32(t), src[a] + t);
+                for (int a = 0; a < 4; ++a) tma_load2(dst + a * ROW, &map_u, 0, (int)(src[a] >> 5), bar);
             }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+            issued = true;
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int h = 0; h < C / 4; ++h) {
+                    const int t = 4 * (h * 32 + lane);   // coalesced: lane-consecutive 16-byte chunks
+                    cp_async16(dst + a * ROW + pad32(t), L.u + src[a] + t);
+                }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
 #pragma unroll
         for (int h = 0; h < C / 4; ++h) rv[h] = __ldg(reinterpret_cast<const float4 *>(L.r + base + i0 + 4 * h));
+    };
+    // shared-memory offset of the float4 holding sites i0 + h .. i0 + h + 3 of a row
+    auto slot = [&](int h) {
+        if constexpr (TMA) {
+            // 16-byte chunk c = (i0 + h) / 4 lies in 128-byte row c / 8 at chunk c % 8, which
+            // the 128-byte swizzle stores at chunk (c % 8) ^ (row % 8)
+            const int c = (i0 + h) >> 2, r = c >> 3;
+            return r * 32 + (((c & 7) ^ (r & 7)) << 2);
+        } else {
+            return pad32(i0 + h);
+        }
     };
     float macc = 0.f;   // mean stage: this lane's weighted sum of the new values
     if (first < A.nlines) {
     float4 rc[C / 4], rn[C / 4];
     issue(first, buf, rc);
     for (long long line = first; line < A.nlines; line += nwarps) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if constexpr (TMA) {
+            const bool ok = mbar_wait(bar, parity, deadline);
+            if (!__all_sync(FULL, ok)) {
+                if (lane == 0) A.ctlw->status = TDGL_ERR_TIMEOUT;
+                break;
+            }
+            parity ^= 1u;
+            issued = false;
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
         __syncwarp();
         const float *cur = buf;
         float e[C];
 #pragma unroll
         for (int h = 0; h < C; h += 4) {
-            const int t = pad32(i0 + h);
+            const int t = slot(h);
             const float4 a = rc[h / 4];
             const float4 yp = *reinterpret_cast<const float4 *>(cur + t);
             const float4 ym = *reinterpret_cast<const float4 *>(cur + ROW + t);
@@ -713,6 +770,8 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
         for (int h = 0; h < C / 4; ++h) rc[h] = rn[h];
     }
     }
+    // a wait that ran out: the boxes in flight land before the buffer is given up
+    if (TMA && issued) mbar_wait(bar, parity, deadline + kIirWaitNs);
     if (!A.mean_stage) return;
     __shared__ double shd[32];
     __shared__ int flag;
@@ -727,6 +786,30 @@ __global__ void __launch_bounds__(kIirWarps * 32) line_iir_async_kernel(LineArgs
         A.ctlw->ticket = 0u;
         A.ctlw->mu_mean = t / A.wsum;
     }
+}
+
+bool mg_encode_line_maps(PoissonArgs &pa)
+{
+    bool any = false;
+    for (int l = 0; l < kMaxLevels; ++l) pa.umap_u[l] = nullptr;
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tma_encode_entry());
+    if (!encode) return false;
+    for (int l = 0; l < pa.nlevels; ++l) {
+        const MGLevel &L = pa.lev[l];
+        if (L.iir != 16 || L.nx != 512 || (reinterpret_cast<uintptr_t>(L.u) & 15) != 0) continue;
+        // u as rows of 32 floats (128 bytes); a box of 16 rows is one line
+        const cuuint64_t dims[2] = {32, (cuuint64_t)(L.N / 32)};
+        const cuuint64_t strides[1] = {128};
+        const cuuint32_t box[2] = {32, 16};
+        const cuuint32_t estr[2] = {1, 1};
+        if (encode(&pa.umap[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, L.u, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+            pa.umap_u[l] = L.u;
+            any = true;
+        }
+    }
+    return any;
 }
 
 // blocks of one recursive-smoother pass over nlines lines (one resident wave)
@@ -757,39 +840,42 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.wsum = a.wsum;
     if (A.nlines == 0 && mean_stage == 0) return cudaSuccess;
     if (L.iir == 16) {
-        // asynchronous-copy variant, one resident wave of blocks (shared memory and
-        // registers decide how many fit on an SM)
-        const size_t smem = (size_t)kIirWarps * 4 * (512 + 64) * sizeof(float);
-        static int sms = 0, occ1 = 0, occ2 = 0;
+        // staged by the tensor memory accelerator where this level's map describes its u,
+        // else by per-lane asynchronous copies; one resident wave of blocks (shared memory
+        // and registers decide how many fit on an SM)
+        const bool tma = a.umap_u[l] != nullptr && a.umap_u[l] == L.u;
+        const size_t smem_cp = (size_t)kIirWarps * 4 * (512 + 64) * sizeof(float);
+        const size_t smem_tma = (size_t)kIirWarps * kIirTmaBytes + 1024 + kIirWarps * sizeof(unsigned long long);
+        const size_t smem = tma ? smem_tma : smem_cp;
+        using KFn = void (*)(LineArgs, const CUtensorMap);
+        static const KFn kfn[2][2] = {{line_iir_async_kernel<16, 1, false>, line_iir_async_kernel<16, 2, false>},
+                                      {line_iir_async_kernel<16, 1, true>, line_iir_async_kernel<16, 2, true>}};
+        static int sms = 0, occ[2][2];
         if (!sms) {
-            cudaFuncSetAttribute(line_iir_async_kernel<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(line_iir_async_kernel<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 sms = 152;
-            // a failed query leaves one block per SM (and clears its error)
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, line_iir_async_kernel<16, 1>, kIirWarps * 32, smem) !=
-                cudaSuccess) {
-                cudaGetLastError();
-                occ1 = 1;
-            }
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, line_iir_async_kernel<16, 2>, kIirWarps * 32, smem) !=
-                cudaSuccess) {
-                cudaGetLastError();
-                occ2 = 1;
-            }
-            occ1 = occ1 < 1 ? 1 : occ1;
-            occ2 = occ2 < 1 ? 1 : occ2;
+            for (int t = 0; t < 2; ++t)
+                for (int w = 0; w < 2; ++w) {
+                    const size_t sz = t ? smem_tma : smem_cp;
+                    cudaFuncSetAttribute(kfn[t][w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
+                    // a failed query leaves one block per SM (and clears its error)
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[t][w], kfn[t][w], kIirWarps * 32, sz) !=
+                        cudaSuccess) {
+                        cudaGetLastError();
+                        occ[t][w] = 1;
+                    }
+                    if (occ[t][w] < 1) occ[t][w] = 1;
+                }
         }
-        const int occ = (L.iir_nw == 2) ? occ2 : occ1;
-        long long nb = async_grid(A.nlines, occ, sms);
+        const int occ_l = occ[tma ? 1 : 0][L.iir_nw == 2 ? 1 : 0];
+        long long nb = async_grid(A.nlines, occ_l, sms);
         if (mean_stage) {
             A.mean_stage = mean_stage;
-            A.mean_nb1 = (int)async_grid(mg_lines_of_colour(L.ny, L.nz, 1), occ, sms);
+            A.mean_nb1 = (int)async_grid(mg_lines_of_colour(L.ny, L.nz, 1), occ_l, sms);
             if (nb < 1) nb = 1;   // the reduction runs even without lines of this colour
         }
-        if (L.iir_nw == 2) line_iir_async_kernel<16, 2><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
-        else line_iir_async_kernel<16, 1><<<(int)nb, kIirWarps * 32, smem, s>>>(A);
+        kfn[tma ? 1 : 0][L.iir_nw == 2 ? 1 : 0]<<<(int)nb, kIirWarps * 32, smem, s>>>(A, a.umap[tma ? l : 0]);
         ++*nl;
         return cudaGetLastError();
     }

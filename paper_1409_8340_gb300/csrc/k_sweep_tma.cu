@@ -31,6 +31,7 @@
 
 #include "sweep_tile.cuh"
 #include "tdgl_internal.cuh"
+#include "tma_util.cuh"
 
 namespace tdgl {
 
@@ -52,50 +53,6 @@ struct Stage {
 static_assert(sizeof(Stage) % 128 == 0, "stages on 128-byte boundaries");
 static_assert(offsetof(Stage, b) % 128 == 0 && offsetof(Stage, D) % 128 == 0, "boxes on 128-byte boundaries");
 constexpr unsigned kPlaneBytes = (kTR + 2) * kRowP * 8 + 2 * kTR * kTX * 8;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtime()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// wait for the phase of the given parity to complete; false when the deadline passes
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long deadline)
-{
-    for (unsigned it = 0;; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if ((it & 255u) == 255u && gtime() > deadline) return false;
-    }
-}
 
 // 1 / x by the hardware reciprocal approximation (relative error within about 2^-23 in
 // the normal range; |diag M|^2 is of order 1 to 10, far from it)
@@ -391,18 +348,25 @@ bool tma_sweep_supported(const DevGrid &g) { return (g.L == nullptr || g.Xj != n
 size_t tma_sweep_smem() { return kTS * sizeof(Stage) + 2 * kTS * sizeof(unsigned long long); }
 
 // Tensor map of one complex64 field (nx, ny, nz) with the given box; false on failure.
+void *tma_encode_entry()
+{
+    static void *fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f)
+            return nullptr;
+        fn = f;
+    }
+    return fn;
+}
+
 bool tma_encode_field(const DevGrid &g, const float2 *base, int box_x, int box_y, CUtensorMap *out)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return false;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+    const auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tma_encode_entry());
+    if (!encode) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 8, (cuuint64_t)g.nx * g.ny * 8};
     const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};

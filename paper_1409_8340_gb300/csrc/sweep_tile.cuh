@@ -19,7 +19,8 @@ __device__ __forceinline__ void sweep_decide(const SweepArgs &a, float gf, bool 
     DevCtl *c = a.ctl;
     int it = init ? 1 : c->iter + 1;
     if (init) {
-        c->status = TDGL_OK;
+        // a timed-out wait of a staged kernel (sweep or smoother) stays reported
+        if (c->status != TDGL_ERR_TIMEOUT) c->status = TDGL_OK;
         c->nstep += 1;   // the init blocks have all read the noise counter
     }
     c->iter = it;

@@ -550,6 +550,8 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
         // a synchronous wait keeps `tri` valid for the copy above
         chk(cudaStreamSynchronize(s));
     }
+    // tensor maps for the recursive smoother's row staging (none: per-lane copies)
+    mg_encode_line_maps(pa);
     chk(cudaStreamSynchronize(s));
     if (rc != TDGL_OK) {
         delete h;

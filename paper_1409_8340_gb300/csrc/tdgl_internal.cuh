@@ -221,6 +221,8 @@ cudaError_t launch_sweep_redo(const SweepArgs &a, cudaStream_t s);
 struct TmaMaps {
     CUtensorMap psi[3], b, D;
 };
+// cuTensorMapEncodeTiled from the driver (nullptr if unavailable)
+void *tma_encode_entry();
 bool tma_sweep_supported(const DevGrid &g);
 bool tma_encode_maps(const DevGrid &g, float2 *const psi[3], const float2 *b, const float2 *D, TmaMaps *m);
 cudaError_t launch_sweep_tma(const SweepArgs &a, const CUtensorMap &map_psi, const TmaMaps &m, cudaStream_t s);
@@ -297,7 +299,15 @@ struct PoissonArgs {
     double hx, Jext;
     int inject;                // open x with applied current
     double wsum;
+    // levels smoothed by the recursive line solve: 2-D tensor maps of u viewed as rows of
+    // 32 floats, a box being one 512-site line (16 rows, 128-byte swizzle), and the u each
+    // map was made for (nullptr: none; a copy of these arguments pointing its u elsewhere
+    // falls back to the asynchronous-copy smoother)
+    CUtensorMap umap[kMaxLevels];
+    const float *umap_u[kMaxLevels];
 };
+// tensor maps for the levels of pa that the recursive smoother handles (false: none made)
+bool mg_encode_line_maps(PoissonArgs &pa);
 cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStream_t s);
 // after_cycle: the call directly follows a V-cycle on the same right-hand side
 // mean_out: the cycle's closing finest-level passes also leave the weighted mean of mu in
