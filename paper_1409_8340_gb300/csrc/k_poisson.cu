@@ -539,10 +539,11 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
                  : "memory");
 }
 
-// NW = 2 (levels whose decay needs rho^(2C) <= 1e-9): each lane warms its recursions up
-// over the 2C values of the two lanes before (after) its chunk; at the mirrored ends the
-// first two (last two) lanes read the extended line's values by shuffle from the lanes
-// that hold them.
+// W: the warm-up length, the smallest of 12, 16, 24, 32 with rho^W <= 1e-8 (below FP32
+// rounding).  W <= C: each lane warms up over the last W values of the previous lane.
+// C < W <= 2C: over values of the two lanes before (after) its chunk; at the mirrored
+// ends the first two (last two) lanes read the extended line's values by shuffle from
+// the lanes that hold them.
 // TMA: the four rows come as four boxes of the level's tensor map (one lane issues them,
 // completing the warp's mbarrier) into an unpadded 8 KB buffer in the 128-byte swizzled
 // layout, which keeps the lanes' 16-byte reads on distinct banks: no per-lane copies.
@@ -550,11 +551,11 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
 // lines after its copies in flight have landed (again bounded).
 constexpr int kIirTmaBytes = 4 * 512 * 4;   // a warp's buffer: four 512-site rows
 constexpr unsigned long long kIirWaitNs = 2000000000ull;
-template <int C, int NW, bool TMA>
+template <int C, int W, bool TMA>
 __global__ void __launch_bounds__(kIirWarps * 32)
     line_iir_async_kernel(LineArgs A, const __grid_constant__ CUtensorMap map_u)
 {
-    static_assert(NW == 1 || NW == 2, "warm-up over one or two neighbour lanes");
+    static_assert(W >= 1 && W <= 2 * C, "warm-up over at most two neighbour lanes");
     static_assert(!TMA || C == 16, "tensor-map boxes hold 512-site lines");
     constexpr int NX = 32 * C, ROW = TMA ? NX : NX + NX / 8;   // row length in floats (padded for copies)
     extern __shared__ __align__(16) float sm_iir[];
@@ -670,14 +671,16 @@ __global__ void __launch_bounds__(kIirWarps * 32)
         const float rho = L.rho;
         float wv[C];
         float z = 0.f;
-        if constexpr (NW == 1) {
+        if constexpr (W <= C) {
             const float e_next0 = __shfl_sync(FULL, e[0], 1);
             const float e_prevlast = __shfl_sync(FULL, e[C - 1], 30);
+            // forward warm-up over x = i0 - W .. i0 - 1 (the previous lane's last W values);
+            // on an open line lane 0 reads the mirror e_ext(-d) = e(d), d = W - m
             float w = 0.f;
 #pragma unroll
-            for (int m = 0; m < C; ++m) {
-                float v = __shfl_sync(FULL, e[m], (lane + 31) & 31);
-                if (open && lane == 0) v = (m == 0) ? e_next0 : e[C - m];
+            for (int m = 0; m < W; ++m) {
+                float v = __shfl_sync(FULL, e[C - W + m], (lane + 31) & 31);
+                if (open && lane == 0) v = (W - m == C) ? e_next0 : e[(W - m) % C];
                 w = fmaf(rho, w, v);
             }
 #pragma unroll
@@ -685,32 +688,35 @@ __global__ void __launch_bounds__(kIirWarps * 32)
                 w = fmaf(rho, w, e[m]);
                 wv[m] = w;
             }
-            float wext[C];
+            // right mirror: lane 31 continues the forward recursion over e(nx - 2 - m)
+            float wext[W];
             {
                 float wc = wv[C - 1];
 #pragma unroll
-                for (int m = 0; m < C; ++m) {
-                    const float v = (m <= C - 2) ? e[C - 2 - m] : e_prevlast;
+                for (int m = 0; m < W; ++m) {
+                    const float v = (m <= C - 2) ? e[(C - 2 - m + C) % C] : e_prevlast;
                     wc = fmaf(rho, wc, v);
                     wext[m] = wc;
                 }
             }
+            // backward warm-up over x = i0 + C + W - 1 down to i0 + C
 #pragma unroll
-            for (int m = C - 1; m >= 0; --m) {
+            for (int m = W - 1; m >= 0; --m) {
                 float v = __shfl_sync(FULL, wv[m], (lane + 1) & 31);
                 if (open && lane == 31) v = wext[m];
                 z = fmaf(rho, z, v);
             }
         } else {
-            constexpr int W = NW * C;
             // forward warm-up over x = i0 - W .. i0 - 1; on an open line, x < 0 reads the
             // mirror e_ext(x) = e(-x), held by lane (-x) / C at element (-x) mod C
             float w = 0.f;
 #pragma unroll
             for (int m = 0; m < W; ++m) {
-                float v = __shfl_sync(FULL, e[m % C], (lane - NW + m / C) & 31);
+                // x - i0 = m - W: lane - 2 for m < W - C, else lane - 1
+                const int dl = (m < W - C) ? 2 : 1;
+                float v = __shfl_sync(FULL, e[m - W + dl * C], (lane - dl) & 31);
                 const int d = W - m - lane * C;   // -x
-                const float vm = __shfl_sync(FULL, e[(C - m % C) % C], (d > 0 ? d : 0) / C);
+                const float vm = __shfl_sync(FULL, e[(W - m) % C], (d > 0 ? d : 0) / C);
                 if (open && d > 0) v = vm;
                 w = fmaf(rho, w, v);
             }
@@ -848,15 +854,17 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
         const size_t smem_tma = (size_t)kIirWarps * kIirTmaBytes + 1024 + kIirWarps * sizeof(unsigned long long);
         const size_t smem = tma ? smem_tma : smem_cp;
         using KFn = void (*)(LineArgs, const CUtensorMap);
-        static const KFn kfn[2][2] = {{line_iir_async_kernel<16, 1, false>, line_iir_async_kernel<16, 2, false>},
-                                      {line_iir_async_kernel<16, 1, true>, line_iir_async_kernel<16, 2, true>}};
-        static int sms = 0, occ[2][2];
+        static const KFn kfn[2][4] = {{line_iir_async_kernel<16, 12, false>, line_iir_async_kernel<16, 16, false>,
+                                       line_iir_async_kernel<16, 24, false>, line_iir_async_kernel<16, 32, false>},
+                                      {line_iir_async_kernel<16, 12, true>, line_iir_async_kernel<16, 16, true>,
+                                       line_iir_async_kernel<16, 24, true>, line_iir_async_kernel<16, 32, true>}};
+        static int sms = 0, occ[2][4];
         if (!sms) {
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 sms = 152;
             for (int t = 0; t < 2; ++t)
-                for (int w = 0; w < 2; ++w) {
+                for (int w = 0; w < 4; ++w) {
                     const size_t sz = t ? smem_tma : smem_cp;
                     cudaFuncSetAttribute(kfn[t][w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
                     // a failed query leaves one block per SM (and clears its error)
@@ -868,14 +876,15 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
                     if (occ[t][w] < 1) occ[t][w] = 1;
                 }
         }
-        const int occ_l = occ[tma ? 1 : 0][L.iir_nw == 2 ? 1 : 0];
+        const int wi = L.iir_w <= 12 ? 0 : (L.iir_w <= 16 ? 1 : (L.iir_w <= 24 ? 2 : 3));
+        const int occ_l = occ[tma ? 1 : 0][wi];
         long long nb = async_grid(A.nlines, occ_l, sms);
         if (mean_stage) {
             A.mean_stage = mean_stage;
             A.mean_nb1 = (int)async_grid(mg_lines_of_colour(L.ny, L.nz, 1), occ_l, sms);
             if (nb < 1) nb = 1;   // the reduction runs even without lines of this colour
         }
-        kfn[tma ? 1 : 0][L.iir_nw == 2 ? 1 : 0]<<<(int)nb, kIirWarps * 32, smem, s>>>(A, a.umap[tma ? l : 0]);
+        kfn[tma ? 1 : 0][wi]<<<(int)nb, kIirWarps * 32, smem, s>>>(A, a.umap[tma ? l : 0]);
         ++*nl;
         return cudaGetLastError();
     }

@@ -520,17 +520,27 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
         M.kmin = mg_line_kernel(c.nx, c.bc[0], M.cx, 2.0 * M.cy + 2.0 * M.cz, tri);
         {
             // the line operator (2 cx + s) - cx (shift + shift^-1) = (cx / rho)(1 - rho S-)(1 - rho S+):
-            // a causal and an anticausal first-order recursion.  One lane's C values carry the
-            // warm-up of its neighbour when rho^C <= 1e-9 (far below FP32 rounding); with 16
-            // sites per lane, two lanes' values when rho^(2C) <= 1e-9
+            // a causal and an anticausal first-order recursion.  Each lane starts them W values
+            // before (after) its chunk: the dropped terms carry rho^W.  With 16 sites per lane,
+            // W is the smallest of 12, 16, 24, 32 with rho^W <= 1e-8 (below FP32 rounding);
+            // with 32 sites per lane W = 32 and rho^32 <= 1e-9
             const double sx = 2.0 * M.cy + 2.0 * M.cz, tt = 1.0 + sx / (2.0 * M.cx);
             const double rho = tt - sqrt(tt * tt - 1.0);
             M.rho = (float)rho;
             M.rscale = (float)(rho / M.cx);
             const int C = c.nx / 32;
             const bool shape = (C == 16 || C == 32) && c.nx == 32 * C && sx > 0;
-            M.iir_nw = !shape ? 0 : (pow(rho, (double)C) <= 1e-9 ? 1 : ((C == 16 && pow(rho, 2.0 * C) <= 1e-9) ? 2 : 0));
-            M.iir = M.iir_nw ? C : 0;
+            M.iir_w = 0;
+            if (shape && C == 16) {
+                for (int w : {12, 16, 24, 32})
+                    if (pow(rho, (double)w) <= 1e-8) {
+                        M.iir_w = w;
+                        break;
+                    }
+            } else if (shape && pow(rho, 32.0) <= 1e-9) {
+                M.iir_w = 32;
+            }
+            M.iir = M.iir_w ? C : 0;
         }
         M.kmax = M.kmin + (int)tri.size() - 1;
         chk(cudaMemcpyAsync(M.G, tri.data(), 4 * tri.size(), cudaMemcpyHostToDevice, s));

@@ -276,7 +276,7 @@ struct MGLevel {
     int M;                     // number of y-z modes of the coarsest level (ny * nz)
     // recursive exact line solve (short decay): chunk C = nx / 32 sites per lane, or 0;
     // rho = t - sqrt(t^2 - 1), t = 1 + s / (2 cx), and the output scale rho / cx
-    int iir, iir_nw;   // recursive line solve: C sites per lane, warm-up over iir_nw lanes
+    int iir, iir_w;    // recursive line solve: C sites per lane, warm-up length iir_w
     float rho, rscale;
 };
 int mg_period(int nx, int bcx);
