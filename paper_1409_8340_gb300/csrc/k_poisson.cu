@@ -539,11 +539,11 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
                  : "memory");
 }
 
-// W: the warm-up length, the smallest of 12, 16, 24, 32 with rho^W <= 1e-8 (below FP32
-// rounding).  W <= C: each lane warms up over the last W values of the previous lane.
-// C < W <= 2C: over values of the two lanes before (after) its chunk; at the mirrored
-// ends the first two (last two) lanes read the extended line's values by shuffle from
-// the lanes that hold them.
+// W: the warm-up length, the smallest of 12, 16, 24, 32, 40, 48 with rho^W <= 1e-8
+// (below FP32 rounding).  W <= C: each lane warms up over the last W values of the
+// previous lane.  C < W <= 3C: over values of the two or three lanes before (after) its
+// chunk; at the mirrored ends the first (last) lanes read the extended line's values by
+// shuffle from the lanes that hold them.
 // TMA: the four rows come as four boxes of the level's tensor map (one lane issues them,
 // completing the warp's mbarrier) into an unpadded 8 KB buffer in the 128-byte swizzled
 // layout, which keeps the lanes' 16-byte reads on distinct banks: no per-lane copies.
@@ -555,7 +555,7 @@ template <int C, int W, bool TMA>
 __global__ void __launch_bounds__(kIirWarps * 32)
     line_iir_async_kernel(LineArgs A, const __grid_constant__ CUtensorMap map_u)
 {
-    static_assert(W >= 1 && W <= 2 * C, "warm-up over at most two neighbour lanes");
+    static_assert(W >= 1 && W <= 3 * C, "warm-up over at most three neighbour lanes");
     static_assert(!TMA || C == 16, "tensor-map boxes hold 512-site lines");
     constexpr int NX = 32 * C, ROW = TMA ? NX : NX + NX / 8;   // row length in floats (padded for copies)
     extern __shared__ __align__(16) float sm_iir[];
@@ -712,8 +712,8 @@ __global__ void __launch_bounds__(kIirWarps * 32)
             float w = 0.f;
 #pragma unroll
             for (int m = 0; m < W; ++m) {
-                // x - i0 = m - W: lane - 2 for m < W - C, else lane - 1
-                const int dl = (m < W - C) ? 2 : 1;
+                // x - i0 = m - W: lane - 3, lane - 2 or lane - 1
+                const int dl = (m < W - 2 * C) ? 3 : ((m < W - C) ? 2 : 1);
                 float v = __shfl_sync(FULL, e[m - W + dl * C], (lane - dl) & 31);
                 const int d = W - m - lane * C;   // -x
                 const float vm = __shfl_sync(FULL, e[(W - m) % C], (d > 0 ? d : 0) / C);
@@ -739,12 +739,13 @@ __global__ void __launch_bounds__(kIirWarps * 32)
                 }
             }
             // backward warm-up over x = i0 + C + W - 1 down to i0 + C; past the end lane 31
-            // reads wext[m] and lane 30 wext[m - C] (both computed in every lane)
+            // reads wext[m], lane 30 wext[m - C], lane 29 wext[m - 2C] (computed in every lane)
 #pragma unroll
             for (int m = W - 1; m >= 0; --m) {
                 float v = __shfl_sync(FULL, wv[m % C], (lane + 1 + m / C) & 31);
                 if (open && lane == 31) v = wext[m];
-                if (open && lane == 30 && m >= C) v = wext[m - C];
+                if (open && lane == 30 && m >= C) v = wext[m >= C ? m - C : 0];
+                if (open && lane == 29 && m >= 2 * C) v = wext[m >= 2 * C ? m - 2 * C : 0];
                 z = fmaf(rho, z, v);
             }
         }
@@ -854,17 +855,19 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
         const size_t smem_tma = (size_t)kIirWarps * kIirTmaBytes + 1024 + kIirWarps * sizeof(unsigned long long);
         const size_t smem = tma ? smem_tma : smem_cp;
         using KFn = void (*)(LineArgs, const CUtensorMap);
-        static const KFn kfn[2][4] = {{line_iir_async_kernel<16, 12, false>, line_iir_async_kernel<16, 16, false>,
-                                       line_iir_async_kernel<16, 24, false>, line_iir_async_kernel<16, 32, false>},
-                                      {line_iir_async_kernel<16, 12, true>, line_iir_async_kernel<16, 16, true>,
-                                       line_iir_async_kernel<16, 24, true>, line_iir_async_kernel<16, 32, true>}};
-        static int sms = 0, occ[2][4];
+        static const KFn kfn[2][6] = {
+            {line_iir_async_kernel<16, 12, false>, line_iir_async_kernel<16, 16, false>,
+             line_iir_async_kernel<16, 24, false>, line_iir_async_kernel<16, 32, false>,
+             line_iir_async_kernel<16, 40, false>, line_iir_async_kernel<16, 48, false>},
+            {line_iir_async_kernel<16, 12, true>, line_iir_async_kernel<16, 16, true>, line_iir_async_kernel<16, 24, true>,
+             line_iir_async_kernel<16, 32, true>, line_iir_async_kernel<16, 40, true>, line_iir_async_kernel<16, 48, true>}};
+        static int sms = 0, occ[2][6];
         if (!sms) {
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 sms = 152;
             for (int t = 0; t < 2; ++t)
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < 6; ++w) {
                     const size_t sz = t ? smem_tma : smem_cp;
                     cudaFuncSetAttribute(kfn[t][w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
                     // a failed query leaves one block per SM (and clears its error)
@@ -876,7 +879,7 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
                     if (occ[t][w] < 1) occ[t][w] = 1;
                 }
         }
-        const int wi = L.iir_w <= 12 ? 0 : (L.iir_w <= 16 ? 1 : (L.iir_w <= 24 ? 2 : 3));
+        const int wi = L.iir_w <= 12 ? 0 : (L.iir_w <= 16 ? 1 : (L.iir_w <= 24 ? 2 : (L.iir_w <= 32 ? 3 : (L.iir_w <= 40 ? 4 : 5))));
         const int occ_l = occ[tma ? 1 : 0][wi];
         long long nb = async_grid(A.nlines, occ_l, sms);
         if (mean_stage) {

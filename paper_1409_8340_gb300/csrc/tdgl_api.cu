@@ -522,7 +522,7 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
             // the line operator (2 cx + s) - cx (shift + shift^-1) = (cx / rho)(1 - rho S-)(1 - rho S+):
             // a causal and an anticausal first-order recursion.  Each lane starts them W values
             // before (after) its chunk: the dropped terms carry rho^W.  With 16 sites per lane,
-            // W is the smallest of 12, 16, 24, 32 with rho^W <= 1e-8 (below FP32 rounding);
+            // W is the smallest of 12, 16, 24, 32, 40, 48 with rho^W <= 1e-8 (below FP32 rounding);
             // with 32 sites per lane W = 32 and rho^32 <= 1e-9
             const double sx = 2.0 * M.cy + 2.0 * M.cz, tt = 1.0 + sx / (2.0 * M.cx);
             const double rho = tt - sqrt(tt * tt - 1.0);
@@ -532,7 +532,7 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
             const bool shape = (C == 16 || C == 32) && c.nx == 32 * C && sx > 0;
             M.iir_w = 0;
             if (shape && C == 16) {
-                for (int w : {12, 16, 24, 32})
+                for (int w : {12, 16, 24, 32, 40, 48})
                     if (pow(rho, (double)w) <= 1e-8) {
                         M.iir_w = w;
                         break;
