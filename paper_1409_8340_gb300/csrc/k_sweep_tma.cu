@@ -23,6 +23,13 @@
 //
 // Landau links of either plane (XZ: the j-indexed tables and the y wrap of the
 // xz gauge), insulating sites (MASK: link bits, read per site pair), even nx.
+//
+// RHS: the same tile pipeline for the Poisson right-hand side (Sec. 3.3): only the psi
+// box is streamed, through a deeper ring of twelve smaller stages (psi is the only
+// stream, so more planes must be in flight), and each site pair writes
+// f = Im[conj(psi) NS(psi)] / (ht/2) plus the injected current on the open x faces,
+// the register-tiled kernel's arithmetic; the trapezoid-weighted FP64 sum of f is
+// reduced over the blocks and the last block stores its mean.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <float.h>
@@ -52,7 +59,19 @@ struct Stage {
 };
 static_assert(sizeof(Stage) % 128 == 0, "stages on 128-byte boundaries");
 static_assert(offsetof(Stage, b) % 128 == 0 && offsetof(Stage, D) % 128 == 0, "boxes on 128-byte boundaries");
-constexpr unsigned kPlaneBytes = (kTR + 2) * kRowP * 8 + 2 * kTR * kTX * 8;
+constexpr unsigned kPsiBytes = (kTR + 2) * kRowP * 8;
+constexpr unsigned kPlaneBytes = kPsiBytes + 2 * kTR * kTX * 8;
+// right-hand side: psi boxes only, twelve stages
+struct StageR {
+    float2 psi[kTR + 2][kRowP];
+    float2 pad[8];
+};
+static_assert(sizeof(StageR) % 128 == 0, "stages on 128-byte boundaries");
+constexpr int kTSR = 12;
+template <bool RHS>
+using StageT = typename std::conditional<RHS, StageR, Stage>::type;
+template <bool RHS>
+constexpr int kStages = RHS ? kTSR : kTS;
 
 // 1 / x by the hardware reciprocal approximation (relative error within about 2^-23 in
 // the normal range; |diag M|^2 is of order 1 to 10, far from it)
@@ -89,27 +108,33 @@ __device__ __forceinline__ int plane_of(const DevGrid &g, int z)
     return z;
 }
 
-// Producer: the three boxes of plane z into stage S.  x starts two sites before the
-// tile (even, as the tensor memory accelerator requires of 8-byte elements).
-__device__ __forceinline__ void issue_plane(const TmaTile &T, int zp, Stage &S, unsigned long long *full,
+// Producer: the three boxes of plane z into stage S (the psi box alone for the
+// right-hand side).  x starts two sites before the tile (even, as the tensor memory
+// accelerator requires of 8-byte elements).
+template <bool RHS>
+__device__ __forceinline__ void issue_plane(const TmaTile &T, int zp, StageT<RHS> &S, unsigned long long *full,
                                            const CUtensorMap *mp, const CUtensorMap *mb, const CUtensorMap *md)
 {
-    mbar_expect(full, kPlaneBytes);
+    mbar_expect(full, RHS ? kPsiBytes : kPlaneBytes);
     tma_load3(&S.psi[0][0], mp, T.x0 - 2, T.j0 - 1, zp, full);
-    tma_load3(&S.b[0][0], mb, T.x0, T.j0, zp, full);
-    tma_load3(&S.D[0][0], md, T.x0, T.j0, zp, full);
+    if constexpr (!RHS) {
+        tma_load3(&S.b[0][0], mb, T.x0, T.j0, zp, full);
+        tma_load3(&S.D[0][0], md, T.x0, T.j0, zp, full);
+    }
 }
 
-template <bool XZ, bool MASK>
+template <bool XZ, bool MASK, bool RHS>
 __global__ void __launch_bounds__(kThreads, 3)
     sweep_tma_kernel(SweepArgs a, int kz, const __grid_constant__ CUtensorMap map_psi,
                      const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_D)
 {
-    if (*(volatile int *)&a.ctl->done) return;
+    constexpr int NS = kStages<RHS>;
+    using St = StageT<RHS>;
+    if (!RHS && *(volatile int *)&a.ctl->done) return;
     extern __shared__ __align__(128) unsigned char tma_smem[];
-    Stage *ring = reinterpret_cast<Stage *>(tma_smem);
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(tma_smem + kTS * sizeof(Stage));
-    unsigned long long *empty = full + kTS;
+    St *ring = reinterpret_cast<St *>(tma_smem);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(tma_smem + NS * sizeof(St));
+    unsigned long long *empty = full + NS;
     __shared__ int failed;
 
     const DevGrid &g = a.g;
@@ -123,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTS; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kTR);
         }
@@ -133,24 +158,25 @@ __global__ void __launch_bounds__(kThreads, 3)
     __syncthreads();
     const unsigned long long deadline = gtime() + kWaitNs;
     float rmax = 0.f;
+    float facc = 0.f;   // RHS: sum of w f over the thread's sites
 
     if (warp == kTR) {
         // ---------------- producer (one thread) ----------------
         if (lane == 0) {
             int issued = 0;
             for (int t = 0; t < nplanes; ++t) {
-                const int s = t % kTS;
-                if (t >= kTS && (!mbar_wait(&empty[s], (unsigned)((t / kTS - 1) & 1), deadline) ||
-                                 *(volatile int *)&failed)) {
+                const int s = t % NS;
+                if (t >= NS && (!mbar_wait(&empty[s], (unsigned)((t / NS - 1) & 1), deadline) ||
+                                *(volatile int *)&failed)) {
                     failed = 1;
                     break;
                 }
-                issue_plane(T, plane_of(g, k0 - 1 + t), ring[s], &full[s], &map_psi, &map_b, &map_D);
+                issue_plane<RHS>(T, plane_of(g, k0 - 1 + t), ring[s], &full[s], &map_psi, &map_b, &map_D);
                 issued = t + 1;
             }
             // drain: every issued plane's copies complete before the block can exit
-            for (int t = max(0, issued - kTS); t < issued; ++t)
-                mbar_wait(&full[t % kTS], (unsigned)((t / kTS) & 1), deadline + kWaitNs);
+            for (int t = max(0, issued - NS); t < issued; ++t)
+                mbar_wait(&full[t % NS], (unsigned)((t / NS) & 1), deadline + kWaitNs);
         }
         __syncwarp();
     } else {
@@ -195,6 +221,12 @@ __global__ void __launch_bounds__(kThreads, 3)
             float4 *__restrict__ dst = reinterpret_cast<float4 *>(a.dst);
             const long long rowq = g.nx >> 1, plq = rowq * g.ny;
             const long long q0 = (x >> 1) + rowq * jc;
+            // RHS: trapezoid weights of the pair on open faces, 1 / (ht/2)
+            const float wy = (g.bcy == kOpen && (j == 0 || j == g.ny - 1)) ? 0.5f : 1.f;
+            const float wxy0 = wy * ((g.bcx == kOpen && x == 0) ? 0.5f : 1.f);
+            const float wxy1 = wy * ((g.bcx == kOpen && x + 1 == g.nx - 1) ? 0.5f : 1.f);
+            const float inv_ht2 = 1.0f / g.ht2;
+            float2 *fdp = reinterpret_cast<float2 *>(a.f) + q0 + plq * k0;
             bool ok = true;
             // stages of planes t - 1, t, t + 1 and the phase parity of plane t + 1's stage,
             // advanced by one plane per iteration
@@ -211,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 3)
                     if (lane == 0) failed = 1;
                     break;
                 }
-                const Stage &Pm = ring[sm], &Pc = ring[sc], &Pp = ring[sp];
+                const St &Pm = ring[sm], &Pc = ring[sc], &Pp = ring[sp];
                 if (in) {
                     const uchar2 lkc = MASK ? lk2[q0 + plq * k] : make_uchar2(0x3f, 0x3f);
                     const int cx = 2 + 2 * lane;
@@ -226,8 +258,11 @@ __global__ void __launch_bounds__(kThreads, 3)
                     if (xper && xhi) xr = a.src[(rowk + j) * g.nx];
                     if (yper && ylo) yb = reinterpret_cast<const float4 *>(a.src)[((rowk + g.ny - 1) * g.nx + x) >> 1];
                     if (yper && yhi) yf = reinterpret_cast<const float4 *>(a.src)[(rowk * g.nx + x) >> 1];
-                    const float4 bc = *reinterpret_cast<const float4 *>(&Pc.b[r][2 * lane]);
-                    const float4 Dc = *reinterpret_cast<const float4 *>(&Pc.D[r][2 * lane]);
+                    float4 bc = make_float4(0.f, 0.f, 0.f, 0.f), Dc = bc;
+                    if constexpr (!RHS) {
+                        bc = *reinterpret_cast<const float4 *>(&Pc.b[r][2 * lane]);
+                        Dc = *reinterpret_cast<const float4 *>(&Pc.D[r][2 * lane]);
+                    }
                     // the same boundary rules and arithmetic order as the tiled kernel (MODE 0)
                     float2 xl0 = xl, xr1 = xr, c1x = c1, c0x = c0;
                     if (xlo || xhi) {
@@ -305,27 +340,41 @@ __global__ void __launch_bounds__(kThreads, 3)
                         cfma(ns1, zf1, hi2(zpp));
                         cfmac(ns1, zf1, hi2(zmm));
                     }
-                    const float2 b0 = lo2(bc), b1 = hi2(bc), D0 = lo2(Dc), D1 = hi2(Dc);
-                    const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
-                    const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
-                    const float2 n0 = cscale(rcp_approx(cabs2(D0)), cmulc(D0, s0));
-                    const float2 n1 = cscale(rcp_approx(cabs2(D1)), cmulc(D1, s1));
-                    *dp = make_float4(n0.x, n0.y, n1.x, n1.y);
-                    float r2a = cabs2(r0), r2b = cabs2(r1);
-                    r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
-                    r2b = (r2b <= FLT_MAX) ? r2b : INFINITY;
-                    rmax = fmaxf(rmax, fmaxf(r2a, r2b));
+                    if constexpr (RHS) {
+                        // f = Im[conj(psi) NS(psi)] plus the open-x injection terms
+                        float f0 = (c0.x * ns0.y - c0.y * ns0.x) * inv_ht2;
+                        float f1 = (c1.x * ns1.y - c1.y * ns1.x) * inv_ht2;
+                        if (!xper) {
+                            if (xlo && !(MASK && (lkc.x & kLkIns))) f0 -= a.inj;
+                            if (xhi && !(MASK && (lkc.y & kLkIns))) f1 += a.inj;
+                        }
+                        *fdp = make_float2(f0, f1);
+                        const float wz = (g.bcz == kOpen && g.nz >= 2 && (k == 0 || k == g.nz - 1)) ? 0.5f : 1.f;
+                        facc += wz * (wxy0 * f0 + wxy1 * f1);
+                    } else {
+                        const float2 b0 = lo2(bc), b1 = hi2(bc), D0 = lo2(Dc), D1 = hi2(Dc);
+                        const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
+                        const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
+                        const float2 n0 = cscale(rcp_approx(cabs2(D0)), cmulc(D0, s0));
+                        const float2 n1 = cscale(rcp_approx(cabs2(D1)), cmulc(D1, s1));
+                        *dp = make_float4(n0.x, n0.y, n1.x, n1.y);
+                        float r2a = cabs2(r0), r2b = cabs2(r1);
+                        r2a = (r2a <= FLT_MAX) ? r2a : INFINITY;
+                        r2b = (r2b <= FLT_MAX) ? r2b : INFINITY;
+                        rmax = fmaxf(rmax, fmaxf(r2a, r2b));
+                    }
                 }
                 // the plane below is no longer needed by this warp
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[sm]);
                 sm = sc;
                 sc = sp;
-                if (++sp == kTS) {
+                if (++sp == NS) {
                     sp = 0;
                     php ^= 1u;
                 }
                 dp += plq;
+                if constexpr (RHS) fdp += plq;
             }
         };
         if (edge) consume(std::true_type{});
@@ -335,17 +384,21 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (failed) {
         if (threadIdx.x == 0) {
             a.ctl->status = TDGL_ERR_TIMEOUT;
-            a.ctl->done = 1;
+            if (!RHS) a.ctl->done = 1;
         }
         return;   // every thread of the block returns here: the finishing reduction is skipped
     }
-    finish_sweep_at(a, rmax, false, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
-                    gridDim.x * gridDim.y * gridDim.z);
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    if constexpr (RHS) finish_rhs_sum_at(a.ctl, a.blockred, (double)facc, a.wsum, bid, nb);
+    else finish_sweep_at(a, rmax, false, bid, nb);
 }
 
 bool tma_sweep_supported(const DevGrid &g) { return (g.L == nullptr || g.Xj != nullptr) && (g.nx % 2) == 0; }
 
-size_t tma_sweep_smem() { return kTS * sizeof(Stage) + 2 * kTS * sizeof(unsigned long long); }
+template <bool RHS>
+static size_t tma_smem() { return kStages<RHS> * sizeof(StageT<RHS>) + 2 * kStages<RHS> * sizeof(unsigned long long); }
+size_t tma_sweep_smem() { return tma_smem<false>(); }
 
 // Tensor map of one complex64 field (nx, ny, nz) with the given box; false on failure.
 void *tma_encode_entry()
@@ -392,20 +445,20 @@ static int tma_kz(const DevGrid &g)
     return (int)kz;
 }
 
-template <bool XZ, bool MASK>
+template <bool XZ, bool MASK, bool RHS = false>
 static cudaError_t launch_variant(const SweepArgs &a, const CUtensorMap &map_psi, const TmaMaps &m, cudaStream_t s)
 {
     static bool attr = false;
-    const size_t smem = tma_sweep_smem();
+    const size_t smem = tma_smem<RHS>();
     if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(sweep_tma_kernel<XZ, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<XZ, MASK, RHS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int kz = tma_kz(a.g);
     const dim3 grid((a.g.nx + kTX - 1) / kTX, (a.g.ny + kTR - 1) / kTR, (a.g.nz + kz - 1) / kz);
-    sweep_tma_kernel<XZ, MASK><<<grid, kThreads, smem, s>>>(a, kz, map_psi, m.b, m.D);
+    sweep_tma_kernel<XZ, MASK, RHS><<<grid, kThreads, smem, s>>>(a, kz, map_psi, m.b, m.D);
     return cudaGetLastError();
 }
 
@@ -416,6 +469,25 @@ cudaError_t launch_sweep_tma(const SweepArgs &a, const CUtensorMap &map_psi, con
     if (xz) return launch_variant<true, false>(a, map_psi, m, s);
     if (mk) return launch_variant<false, true>(a, map_psi, m, s);
     return launch_variant<false, false>(a, map_psi, m, s);
+}
+
+cudaError_t launch_poisson_rhs_tma(const PoissonArgs &pa, const float2 *psi, const CUtensorMap &map_psi,
+                                   const TmaMaps &m, cudaStream_t s)
+{
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = pa.g;
+    a.ctl = pa.ctl;
+    a.blockred = pa.blockred;
+    a.src = psi;
+    a.f = pa.f;
+    a.inj = pa.inject ? (float)(2.0 * pa.Jext / pa.hx) : 0.f;
+    a.wsum = pa.wsum;
+    const bool xz = a.g.Xj != nullptr, mk = a.g.lk != nullptr;
+    if (xz && mk) return launch_variant<true, true, true>(a, map_psi, m, s);
+    if (xz) return launch_variant<true, false, true>(a, map_psi, m, s);
+    if (mk) return launch_variant<false, true, true>(a, map_psi, m, s);
+    return launch_variant<false, false, true>(a, map_psi, m, s);
 }
 
 }  // namespace tdgl

@@ -783,12 +783,18 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
 
 // The fixed launch sequence of a plain Poisson solve (poisson_tol == 0): right-hand side,
 // poisson_cycles V-cycles, projection.  Returns the launches enqueued.
+static cudaError_t poisson_rhs(tdgl_handle *h, cudaStream_t s)
+{
+    if (h->use_tma) return launch_poisson_rhs_tma(h->pa, h->psi[h->cur], h->tmaps.psi[h->cur], h->tmaps, s);
+    return launch_poisson_rhs(h->pa, h->psi[h->cur], s);
+}
+
 static long long poisson_sequence(tdgl_handle *h, cudaStream_t s, cudaError_t *err)
 {
     long long nl = 1;
     const int nc = h->cfg.poisson_cycles;
     const bool fm = nc > 0 && vcycle_mean_fusable(h->pa);   // the last cycle leaves the mean of mu
-    cudaError_t e = launch_poisson_rhs(h->pa, h->psi[h->cur], s);
+    cudaError_t e = poisson_rhs(h, s);
     for (int q = 0; q < nc && e == cudaSuccess; ++q) e = launch_vcycle(h->pa, s, &nl, q > 0, fm && q == nc - 1);
     if (e == cudaSuccess) e = launch_project_mu(h->pa, s, fm);
     *err = e;
@@ -841,7 +847,7 @@ int tdgl_solve_mu(tdgl_handle *h)
             return TDGL_OK;
         }
     }
-    if (launch_poisson_rhs(h->pa, h->psi[h->cur], s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (poisson_rhs(h, s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (h->lk) {
         // removed links: CG iterations preconditioned by V-cycles; poisson_cycles of them, or
         // (poisson_tol > 0) until max|F - Lap mu| <= poisson_tol max|F|, at most poisson_max_cycles

@@ -309,6 +309,9 @@ struct PoissonArgs {
 // tensor maps for the levels of pa that the recursive smoother handles (false: none made)
 bool mg_encode_line_maps(PoissonArgs &pa);
 cudaError_t launch_poisson_rhs(const PoissonArgs &a, const float2 *psi, cudaStream_t s);
+// the right-hand side through the staged sweep tile (psi boxes only); map_psi describes psi
+cudaError_t launch_poisson_rhs_tma(const PoissonArgs &pa, const float2 *psi, const CUtensorMap &map_psi,
+                                   const TmaMaps &m, cudaStream_t s);
 // after_cycle: the call directly follows a V-cycle on the same right-hand side
 // mean_out: the cycle's closing finest-level passes also leave the weighted mean of mu in
 // ctl->mu_mean, where vcycle_mean_fusable allows (launch_project_mu then skips its own sum)
