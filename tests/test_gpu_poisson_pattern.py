@@ -30,6 +30,9 @@ def poisson_cases():
         ("recursive_two_lane_allopen_512x33x17", Params(512, 33, 17, bc=(OP, OP, OP), Bz=0.25)),
         # and a smoothed third level (rho = 0.61): warm-up over three lanes
         ("recursive_three_lane_openx_512x96x48_J", Params(512, 96, 48, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        # 1024-site lines: 32 sites per lane, the register-only recursive kernel
+        ("recursive_openx_1024x24x12_J", Params(1024, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        ("recursive_periodic_1024x32x16", quantised(Params(1024, 32, 16, bc=(P, P, P)), 2)),
     ]
 
 
