@@ -541,11 +541,15 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
                  : "memory");
 }
 
-// W: the warm-up length, the smallest of 12, 16, 24, 32, 40, 48 with rho^W <= 1e-8
-// (below FP32 rounding).  W <= C: each lane warms up over the last W values of the
-// previous lane.  C < W <= 3C: over values of the two or three lanes before (after) its
-// chunk; at the mirrored ends the first (last) lanes read the extended line's values by
-// shuffle from the lanes that hold them.
+// W = 12 (levels with rho^12 <= 1e-8, below FP32 rounding): each lane warms its
+// recursions up over the last 12 values of the previous lane (the first 12 of the next).
+// W = 0 (every other level): the exact solve by scans over the lanes, for any rho < 1.
+// Each lane runs both recursions from zero over its chunk; the value entering a chunk is
+// a linear recurrence over the lanes (c_L = rho^C c_(L-1) + end_(L-1)), evaluated by a
+// five-step shuffle scan; it is seeded at the line's ends in closed form: w(-1) is a
+// weighted sum over the periodic or mirrored extension (a warp reduction), and the
+// backward seed z(N) follows from the mirror symmetry of the solution (z(N) = z(N - 2))
+// or, on a periodic line, from a second weighted sum.
 // TMA: the four rows come as four boxes of the level's tensor map (one lane issues them,
 // completing the warp's mbarrier) into an unpadded 8 KB buffer in the 128-byte swizzled
 // layout, which keeps the lanes' 16-byte reads on distinct banks: no per-lane copies.
@@ -554,10 +558,10 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
 constexpr int kIirTmaBytes = 4 * 512 * 4;   // a warp's buffer: four 512-site rows
 constexpr unsigned long long kIirWaitNs = 2000000000ull;
 template <int C, int W, bool TMA>
-__global__ void __launch_bounds__(kIirWarps * 32)
+__global__ void __launch_bounds__(kIirWarps * 32, 6)
     line_iir_async_kernel(LineArgs A, const __grid_constant__ CUtensorMap map_u)
 {
-    static_assert(W >= 1 && W <= 3 * C, "warm-up over at most three neighbour lanes");
+    static_assert(W >= 0 && W <= C, "warm-up within the previous lane (0: exact scan)");
     static_assert(!TMA || C == 16, "tensor-map boxes hold 512-site lines");
     constexpr int NX = 32 * C, ROW = TMA ? NX : NX + NX / 8;   // row length in floats (padded for copies)
     extern __shared__ __align__(16) float sm_iir[];
@@ -579,6 +583,19 @@ __global__ void __launch_bounds__(kIirWarps * 32)
         __syncwarp();
     }
     const unsigned long long deadline = TMA ? gtime() + kIirWaitNs : 0ull;
+    // exact solve (W = 0): the lane's powers of rho, once per kernel: the weights of its
+    // first (pw_f1) and last (pw_f2) site in w(-1), of its first site in z(N) (pw_b), and
+    // the carries' seeds rho^(C(L+1)) (pw_c1) and rho^(C(32-L)) (pw_c2)
+    float pw_f1 = 0.f, pw_f2 = 0.f, pw_b = 0.f, pw_c1 = 0.f, pw_c2 = 0.f;
+    if (W == 0) {
+        const int N = 32 * C, x0 = lane * C, x1 = x0 + C - 1;
+        const bool op = (A.bcx == kOpen);
+        pw_f1 = exp2f(L.l2rho * (float)(x0 - 1));
+        pw_f2 = exp2f(L.l2rho * (float)(op ? 2 * N - 3 - x1 : N - 1 - x1));
+        pw_b = exp2f(L.l2rho * (float)x0);
+        pw_c1 = exp2f(L.l2rho * (float)(C * (lane + 1)));
+        pw_c2 = exp2f(L.l2rho * (float)(C * (32 - lane)));
+    }
     const long long nwarps = (long long)gridDim.x * kIirWarps;
     const long long first = (long long)blockIdx.x * kIirWarps + wib;
     const float fsub = A.level0 ? (float)A.ctl->fmean : 0.f;
@@ -673,7 +690,98 @@ __global__ void __launch_bounds__(kIirWarps * 32)
         const float rho = L.rho;
         float wv[C];
         float z = 0.f;
-        if constexpr (W <= C) {
+        float out[C];
+        if constexpr (W == 0) {
+            // exact: each lane runs its recursions from zero over its chunk; the values
+            // entering a chunk follow from a scan over the lanes (carry c_L = rho^C c_(L-1)
+            // + end_(L-1)), seeded at the line's ends in closed form
+            // w(-1) over the extended line: open, sum_x (rho^(x-1) [x >= 1] + rho^(2N-3-x)
+            // [x <= N-2]) e(x) / (1 - rho^(2N-2)); periodic, sum_x rho^(N-1-x) e(x) / (1 - rho^N)
+            float ps = 0.f;
+            {
+                float p1 = pw_f1, p2 = pw_f2;   // at m = 0 and m = C - 1
+#pragma unroll
+                for (int m = 0; m < C; ++m) {
+                    const float t1 = (open && !(lane == 0 && m == 0)) ? p1 : 0.f;
+                    ps = fmaf(t1, e[m], ps);
+                    p1 *= rho;
+                }
+#pragma unroll
+                for (int m = C - 1; m >= 0; --m) {
+                    const float t2 = (open && lane == 31 && m == C - 1) ? 0.f : p2;
+                    ps = fmaf(t2, e[m], ps);
+                    p2 *= rho;
+                }
+            }
+            float w = 0.f;
+#pragma unroll
+            for (int m = 0; m < C; ++m) {
+                w = fmaf(rho, w, e[m]);
+                wv[m] = w;
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) ps += __shfl_xor_sync(FULL, ps, o);
+            const float wm1 = ps * L.gf;
+            // forward carries: S_L = sum_(l <= L) rho^(C(L-l)) end_l + rho^(C(L+1)) w(-1)
+            float S = w;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const float t = __shfl_up_sync(FULL, S, 1 << q);
+                if (lane >= (1 << q)) S = fmaf(L.rhoC[q], t, S);
+            }
+            S = fmaf(pw_c1, wm1, S);
+            float cin = __shfl_up_sync(FULL, S, 1);
+            if (lane == 0) cin = wm1;
+            {
+                float p = rho;
+#pragma unroll
+                for (int m = 0; m < C; ++m) {
+                    wv[m] = fmaf(p, cin, wv[m]);
+                    p *= rho;
+                }
+            }
+            // backward, from zero over the chunk
+#pragma unroll
+            for (int m = C - 1; m >= 0; --m) {
+                z = fmaf(rho, z, wv[m]);
+                out[m] = z;
+            }
+            // z(N): open, by the mirror symmetry of the solution z(N) = z(N-2), hence
+            // z(N) = (rho w(N-1) + w(N-2)) / (1 - rho^2); periodic, z(N) = z(0) =
+            // sum_x rho^x w(x) / (1 - rho^N)
+            float zN;
+            if (open) {
+                zN = __shfl_sync(FULL, fmaf(rho, wv[C - 1], wv[C - 2]) * L.gb, 31);
+            } else {
+                float pz = 0.f, p = pw_b;
+#pragma unroll
+                for (int m = 0; m < C; ++m) {
+                    pz = fmaf(p, wv[m], pz);
+                    p *= rho;
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) pz += __shfl_xor_sync(FULL, pz, o);
+                zN = pz * L.gf;
+            }
+            // backward carries: T_L = sum_(l >= L) rho^(C(l-L)) start_l + rho^(C(32-L)) z(N)
+            float T = z;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const float t = __shfl_down_sync(FULL, T, 1 << q);
+                if (lane + (1 << q) < 32) T = fmaf(L.rhoC[q], t, T);
+            }
+            T = fmaf(pw_c2, zN, T);
+            float din = __shfl_down_sync(FULL, T, 1);
+            if (lane == 31) din = zN;
+            {
+                float p = rho;
+#pragma unroll
+                for (int m = C - 1; m >= 0; --m) {
+                    out[m] = fmaf(p, din, out[m]) * L.rscale;
+                    p *= rho;
+                }
+            }
+        } else if constexpr (W <= C) {
             const float e_next0 = __shfl_sync(FULL, e[0], 1);
             const float e_prevlast = __shfl_sync(FULL, e[C - 1], 30);
             // forward warm-up over x = i0 - W .. i0 - 1 (the previous lane's last W values);
@@ -708,54 +816,13 @@ __global__ void __launch_bounds__(kIirWarps * 32)
                 if (open && lane == 31) v = wext[m];
                 z = fmaf(rho, z, v);
             }
-        } else {
-            // forward warm-up over x = i0 - W .. i0 - 1; on an open line, x < 0 reads the
-            // mirror e_ext(x) = e(-x), held by lane (-x) / C at element (-x) mod C
-            float w = 0.f;
-#pragma unroll
-            for (int m = 0; m < W; ++m) {
-                // x - i0 = m - W: lane - 3, lane - 2 or lane - 1
-                const int dl = (m < W - 2 * C) ? 3 : ((m < W - C) ? 2 : 1);
-                float v = __shfl_sync(FULL, e[m - W + dl * C], (lane - dl) & 31);
-                const int d = W - m - lane * C;   // -x
-                const float vm = __shfl_sync(FULL, e[(W - m) % C], (d > 0 ? d : 0) / C);
-                if (open && d > 0) v = vm;
-                w = fmaf(rho, w, v);
-            }
-#pragma unroll
-            for (int m = 0; m < C; ++m) {
-                w = fmaf(rho, w, e[m]);
-                wv[m] = w;
-            }
-            // right mirror: lane 31 continues the forward recursion over
-            // e_ext(nx - 1 + d) = e(nx - 1 - d), d = 1 .. W
-            float wext[W];
-            if (open) {   // uniform over the warp
-                float wc = __shfl_sync(FULL, wv[C - 1], 31);
-#pragma unroll
-                for (int d = 1; d <= W; ++d) {
-                    const int pos = 32 * C - 1 - d;
-                    const float v = __shfl_sync(FULL, e[pos % C], pos / C);
-                    wc = fmaf(rho, wc, v);
-                    wext[d - 1] = wc;
-                }
-            }
-            // backward warm-up over x = i0 + C + W - 1 down to i0 + C; past the end lane 31
-            // reads wext[m], lane 30 wext[m - C], lane 29 wext[m - 2C] (computed in every lane)
-#pragma unroll
-            for (int m = W - 1; m >= 0; --m) {
-                float v = __shfl_sync(FULL, wv[m % C], (lane + 1 + m / C) & 31);
-                if (open && lane == 31) v = wext[m];
-                if (open && lane == 30 && m >= C) v = wext[m >= C ? m - C : 0];
-                if (open && lane == 29 && m >= 2 * C) v = wext[m >= 2 * C ? m - 2 * C : 0];
-                z = fmaf(rho, z, v);
-            }
         }
-        float out[C];
+        if constexpr (W != 0) {
 #pragma unroll
-        for (int m = C - 1; m >= 0; --m) {
-            z = fmaf(rho, z, wv[m]);
-            out[m] = z * L.rscale;
+            for (int m = C - 1; m >= 0; --m) {
+                z = fmaf(rho, z, wv[m]);
+                out[m] = z * L.rscale;
+            }
         }
         int j, k;
         line_jk(line, A.color, L.ny, L.nz, j, k);
@@ -821,11 +888,11 @@ bool mg_encode_line_maps(PoissonArgs &pa)
     return any;
 }
 
-// blocks of one recursive-smoother pass over nlines lines (one resident wave)
+// blocks of one recursive-smoother pass over nlines lines: a warp per line up to one
+// resident wave (small levels are latency-bound, so every line gets its own warp)
 static long long async_grid(long long nlines, int occ, int sms)
 {
-    const long long warps = (nlines + 3) / 4;
-    long long nb = (warps + kIirWarps - 1) / kIirWarps;
+    long long nb = (nlines + kIirWarps - 1) / kIirWarps;
     const long long cap = (long long)occ * sms;
     return nb > cap ? cap : nb;
 }
@@ -857,19 +924,15 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
         const size_t smem_tma = (size_t)kIirWarps * kIirTmaBytes + 1024 + kIirWarps * sizeof(unsigned long long);
         const size_t smem = tma ? smem_tma : smem_cp;
         using KFn = void (*)(LineArgs, const CUtensorMap);
-        static const KFn kfn[2][6] = {
-            {line_iir_async_kernel<16, 12, false>, line_iir_async_kernel<16, 16, false>,
-             line_iir_async_kernel<16, 24, false>, line_iir_async_kernel<16, 32, false>,
-             line_iir_async_kernel<16, 40, false>, line_iir_async_kernel<16, 48, false>},
-            {line_iir_async_kernel<16, 12, true>, line_iir_async_kernel<16, 16, true>, line_iir_async_kernel<16, 24, true>,
-             line_iir_async_kernel<16, 32, true>, line_iir_async_kernel<16, 40, true>, line_iir_async_kernel<16, 48, true>}};
-        static int sms = 0, occ[2][6];
+        static const KFn kfn[2][2] = {{line_iir_async_kernel<16, 12, false>, line_iir_async_kernel<16, 0, false>},
+                                      {line_iir_async_kernel<16, 12, true>, line_iir_async_kernel<16, 0, true>}};
+        static int sms = 0, occ[2][2];
         if (!sms) {
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 sms = 152;
             for (int t = 0; t < 2; ++t)
-                for (int w = 0; w < 6; ++w) {
+                for (int w = 0; w < 2; ++w) {
                     const size_t sz = t ? smem_tma : smem_cp;
                     cudaFuncSetAttribute(kfn[t][w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz);
                     // a failed query leaves one block per SM (and clears its error)
@@ -881,7 +944,7 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
                     if (occ[t][w] < 1) occ[t][w] = 1;
                 }
         }
-        const int wi = L.iir_w <= 12 ? 0 : (L.iir_w <= 16 ? 1 : (L.iir_w <= 24 ? 2 : (L.iir_w <= 32 ? 3 : (L.iir_w <= 40 ? 4 : 5))));
+        const int wi = (L.iir_w == 12) ? 0 : 1;
         const int occ_l = occ[tma ? 1 : 0][wi];
         long long nb = async_grid(A.nlines, occ_l, sms);
         if (mean_stage) {

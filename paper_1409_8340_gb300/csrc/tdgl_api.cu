@@ -520,27 +520,30 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
         M.kmin = mg_line_kernel(c.nx, c.bc[0], M.cx, 2.0 * M.cy + 2.0 * M.cz, tri);
         {
             // the line operator (2 cx + s) - cx (shift + shift^-1) = (cx / rho)(1 - rho S-)(1 - rho S+):
-            // a causal and an anticausal first-order recursion.  Each lane starts them W values
-            // before (after) its chunk: the dropped terms carry rho^W.  With 16 sites per lane,
-            // W is the smallest of 12, 16, 24, 32, 40, 48 with rho^W <= 1e-8 (below FP32 rounding);
-            // with 32 sites per lane W = 32 and rho^32 <= 1e-9
+            // a causal and an anticausal first-order recursion.  With 16 sites per lane: each
+            // lane starts them 12 values before (after) its chunk where rho^12 <= 1e-8 (the
+            // dropped terms fall below FP32 rounding), else the exact scan over the lanes
+            // (iir_w = 0).  With 32 sites per lane: a 32-value warm-up where rho^32 <= 1e-9.
             const double sx = 2.0 * M.cy + 2.0 * M.cz, tt = 1.0 + sx / (2.0 * M.cx);
             const double rho = tt - sqrt(tt * tt - 1.0);
             M.rho = (float)rho;
             M.rscale = (float)(rho / M.cx);
             const int C = c.nx / 32;
             const bool shape = (C == 16 || C == 32) && c.nx == 32 * C && sx > 0;
+            M.iir = 0;
             M.iir_w = 0;
             if (shape && C == 16) {
-                for (int w : {12, 16, 24, 32, 40, 48})
-                    if (pow(rho, (double)w) <= 1e-8) {
-                        M.iir_w = w;
-                        break;
-                    }
+                M.iir = 16;
+                M.iir_w = (pow(rho, 12.0) <= 1e-8) ? 12 : 0;
             } else if (shape && pow(rho, 32.0) <= 1e-9) {
+                M.iir = 32;
                 M.iir_w = 32;
             }
-            M.iir = M.iir_w ? C : 0;
+            const int P = (c.bc[0] == TDGL_OPEN) ? 2 * c.nx - 2 : c.nx;
+            for (int q = 0; q < 5; ++q) M.rhoC[q] = (float)pow(rho, (double)C * (1 << q));
+            M.l2rho = (float)log2(rho);
+            M.gf = (float)(1.0 / (1.0 - pow(rho, (double)P)));
+            M.gb = (float)(1.0 / (1.0 - rho * rho));
         }
         M.kmax = M.kmin + (int)tri.size() - 1;
         chk(cudaMemcpyAsync(M.G, tri.data(), 4 * tri.size(), cudaMemcpyHostToDevice, s));

@@ -276,8 +276,11 @@ struct MGLevel {
     int M;                     // number of y-z modes of the coarsest level (ny * nz)
     // recursive exact line solve (short decay): chunk C = nx / 32 sites per lane, or 0;
     // rho = t - sqrt(t^2 - 1), t = 1 + s / (2 cx), and the output scale rho / cx
-    int iir, iir_w;    // recursive line solve: C sites per lane, warm-up length iir_w
+    int iir, iir_w;    // recursive line solve: C sites per lane, warm-up length iir_w (0: exact scan)
     float rho, rscale;
+    // exact scan: rho^(C 2^q) (q = 0..4), log2 rho, 1 / (1 - rho^P) (P the period of the
+    // extended line), 1 / (1 - rho^2)
+    float rhoC[5], l2rho, gf, gb;
 };
 int mg_period(int nx, int bcx);
 // x lines of colour c ((j + k) % 2 == c) on an ny x nz line grid

@@ -23,13 +23,12 @@ def poisson_cases():
         ("recursive_openx_512x24x12_J", Params(512, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
         ("recursive_periodic_512x16x16", quantised(Params(512, 16, 16, bc=(P, P, P)), 2)),
         ("recursive_allopen_512x17x9", Params(512, 17, 9, bc=(OP, OP, OP), Bz=0.25)),
-        # nx = 512 with a smoothed second level (rho = 0.38 there): its recursions warm up
-        # over two neighbour lanes
-        ("recursive_two_lane_openx_512x48x24_J", Params(512, 48, 24, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
-        ("recursive_two_lane_periodic_512x32x32", quantised(Params(512, 32, 32, bc=(P, P, P)), 2)),
-        ("recursive_two_lane_allopen_512x33x17", Params(512, 33, 17, bc=(OP, OP, OP), Bz=0.25)),
-        # and a smoothed third level (rho = 0.61): warm-up over three lanes
-        ("recursive_three_lane_openx_512x96x48_J", Params(512, 96, 48, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        # nx = 512 with smoothed coarser levels (rho = 0.38, 0.61, ...): their lines are
+        # solved by the exact scan over the lanes
+        ("recursive_scan_openx_512x48x24_J", Params(512, 48, 24, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        ("recursive_scan_periodic_512x32x32", quantised(Params(512, 32, 32, bc=(P, P, P)), 2)),
+        ("recursive_scan_allopen_512x33x17", Params(512, 33, 17, bc=(OP, OP, OP), Bz=0.25)),
+        ("recursive_scan_openx_512x96x48_J", Params(512, 96, 48, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
         # 1024-site lines: 32 sites per lane, the register-only recursive kernel
         ("recursive_openx_1024x24x12_J", Params(1024, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
         ("recursive_periodic_1024x32x16", quantised(Params(1024, 32, 16, bc=(P, P, P)), 2)),
@@ -88,10 +87,9 @@ def test_mg_converges_fast_from_cold(O):
 
 
 @pytest.mark.parametrize("bc,ny,nz", [((OP, P, P), 48, 24), ((OP, OP, OP), 33, 17), ((OP, P, P), 96, 48)])
-def test_mg_two_lane_level_converges_fast(O, bc, ny, nz):
-    """512 x-sites with smoothed coarser levels whose recursive line solves warm up over
-    two lanes (and three on the third level of 96 x 48): the same reduction per V-cycle
-    from a cold start."""
+def test_mg_scan_levels_converge_fast(O, bc, ny, nz):
+    """512 x-sites with smoothed coarser levels, whose lines the exact scan over the
+    lanes solves: the same reduction per V-cycle from a cold start."""
     from paper_1409_8340_gb300.solver import Params
     psi = I.random_psi(512, ny, nz, 53)
     res = []

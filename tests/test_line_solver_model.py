@@ -1,13 +1,13 @@
 """Models of the index rules of two multigrid kernels, checked on the CPU.
 
-The recursive x-line solve (zebra line Gauss-Seidel on levels with short decay) splits
-a 512-site line over 32 lanes of 16 sites.  The line operator (2 cx + s) - cx (S- + S+)
-factors as (cx / rho)(1 - rho S-)(1 - rho S+), so the solve is a forward and a backward
-first-order recursion; each lane starts them W values before (after) its chunk, taking
-those values from the lanes that hold them, with the periodic wrap or the Neumann mirror
-at the line's ends.  `lane_model` follows the kernel's choice of source lane and element
-for every warm-up value (one, two or three lanes, both ends) in FP32, and is compared
-with a dense FP64 solve of the line system.
+The recursive x-line solve (zebra line Gauss-Seidel) splits a 512-site line over 32
+lanes of 16 sites.  The line operator (2 cx + s) - cx (S- + S+) factors as
+(cx / rho)(1 - rho S-)(1 - rho S+), so the solve is a forward and a backward first-order
+recursion.  On short-decay levels each lane starts them W values before (after) its
+chunk (`lane_model`, with the kernel's choice of source lane and element and the
+periodic wrap or Neumann mirror at the ends); elsewhere the exact scan over the lanes
+(`scan_model`: local recursions from zero, carries by a lane scan, closed-form seeds at
+the ends).  Both run in FP32 and are compared with a dense FP64 solve of the line system.
 
 The fused residual and restriction marches a thread over coarse planes, carrying the
 residual of fine plane 2K+1 and a window of u rows; `fused_model` replays its plane and
@@ -21,6 +21,9 @@ P, OP = 0, 1
 
 
 def lane_model(E, cx, s, open_, W, C=16):
+    """W <= C: each lane warms up over the previous lane's last W values (the next
+    lane's first W for the backward recursion); lane 0 and lane 31 of an open line read
+    the mirror from their own registers."""
     t = 1 + s / (2 * cx)
     rho = np.float32(t - np.sqrt(t * t - 1))
     rsc = np.float32(rho / cx)
@@ -30,16 +33,9 @@ def lane_model(E, cx, s, open_, W, C=16):
     for lane in range(32):
         w = np.float32(0)
         for m in range(W):
-            if W <= C:
-                v = e[(lane - 1) % 32, C - W + m]
-                if open_ and lane == 0:
-                    v = e_next0 if W - m == C else e[0, (W - m) % C]
-            else:
-                dl = 3 if m < W - 2 * C else (2 if m < W - C else 1)
-                v = e[(lane - dl) % 32, m - W + dl * C]
-                d = W - m - lane * C      # -x for the mirror
-                if open_ and d > 0:
-                    v = e[d // C, (W - m) % C]
+            v = e[(lane - 1) % 32, C - W + m]
+            if open_ and lane == 0:
+                v = e_next0 if W - m == C else e[0, (W - m) % C]
             w = np.float32(rho * w + v)
         for m in range(C):
             w = np.float32(rho * w + e[lane, m])
@@ -47,24 +43,96 @@ def lane_model(E, cx, s, open_, W, C=16):
     wext = np.zeros(W, np.float32)         # forward recursion continued past the right end
     wc = wv[31, C - 1]
     for d in range(1, W + 1):
-        pos = 32 * C - 1 - d
-        v = e[pos // C, pos % C] if W > C else (e[31, C - 1 - d] if d <= C - 1 else e_prevlast)
+        v = e[31, C - 1 - d] if d <= C - 1 else e_prevlast
         wc = np.float32(rho * wc + v)
         wext[d - 1] = wc
     out = np.zeros((32, C), np.float32)
     for lane in range(32):
         z = np.float32(0)
         for m in range(W - 1, -1, -1):
-            v = wv[(lane + 1 + m // C) % 32, m % C]
-            if open_:
-                for back in range(3):         # lanes 31, 30, 29 read past the end
-                    if lane == 31 - back and m >= back * C:
-                        v = wext[m - back * C]
+            v = wext[m] if (open_ and lane == 31) else wv[(lane + 1) % 32, m]
             z = np.float32(rho * z + v)
         for m in range(C - 1, -1, -1):
             z = np.float32(rho * z + wv[lane, m])
             out[lane, m] = z * rsc
     return out.ravel(), float(rho)
+
+
+def scan_model(E, cx, s, open_, C=16):
+    """The exact solve: both recursions from zero per lane, the entering values by a scan
+    over the lanes (c_L = rho^C c_(L-1) + end_(L-1)), seeded by w(-1) (a weighted sum
+    over the extended line) and z(N) (mirror symmetry, or a weighted sum of w)."""
+    f32 = np.float32
+    N = E.size
+    t = 1 + s / (2 * cx)
+    rho_d = t - np.sqrt(t * t - 1)
+    rho, rsc = f32(rho_d), f32(rho_d / cx)
+    P = 2 * N - 2 if open_ else N
+    rhoC = [f32(rho_d ** (C * (1 << q))) for q in range(5)]
+    gf, gb, l2 = f32(1 / (1 - rho_d ** P)), f32(1 / (1 - rho_d ** 2)), np.log2(rho_d)
+    e = E.astype(f32).reshape(32, C)
+    ps = np.zeros(32, f32)
+    for L in range(32):
+        x0, x1 = C * L, C * L + C - 1
+        p1 = f32(2.0 ** (l2 * (x0 - 1)))
+        p2 = f32(2.0 ** (l2 * ((2 * N - 3 - x1) if open_ else (N - 1 - x1))))
+        for m in range(C):
+            if open_ and not (L == 0 and m == 0):
+                ps[L] = f32(ps[L] + p1 * e[L, m])
+            p1 = f32(p1 * rho)
+        for m in range(C - 1, -1, -1):
+            if not (open_ and L == 31 and m == C - 1):
+                ps[L] = f32(ps[L] + p2 * e[L, m])
+            p2 = f32(p2 * rho)
+    wm1 = f32(f32(ps.sum(dtype=np.float64)) * gf)
+    w = np.zeros((32, C), f32)
+    for L in range(32):
+        acc = f32(0)
+        for m in range(C):
+            acc = f32(rho * acc + e[L, m])
+            w[L, m] = acc
+    S = w[:, C - 1].copy()
+    for q in range(5):
+        prev = S.copy()
+        for L in range(1 << q, 32):
+            S[L] = f32(prev[L] + rhoC[q] * prev[L - (1 << q)])
+    S = np.array([f32(S[L] + f32(2.0 ** (l2 * C * (L + 1))) * wm1) for L in range(32)], f32)
+    cin = np.concatenate([[wm1], S[:-1]]).astype(f32)
+    for L in range(32):
+        p = rho
+        for m in range(C):
+            w[L, m] = f32(w[L, m] + p * cin[L])
+            p = f32(p * rho)
+    z = np.zeros((32, C), f32)
+    for L in range(32):
+        acc = f32(0)
+        for m in range(C - 1, -1, -1):
+            acc = f32(rho * acc + w[L, m])
+            z[L, m] = acc
+    if open_:
+        zN = f32((rho * w[31, C - 1] + w[31, C - 2]) * gb)
+    else:
+        pz = np.zeros(32, f32)
+        for L in range(32):
+            p = f32(2.0 ** (l2 * C * L))
+            for m in range(C):
+                pz[L] = f32(pz[L] + p * w[L, m])
+                p = f32(p * rho)
+        zN = f32(f32(pz.sum(dtype=np.float64)) * gf)
+    T = z[:, 0].copy()
+    for q in range(5):
+        prev = T.copy()
+        for L in range(32 - (1 << q)):
+            T[L] = f32(prev[L] + rhoC[q] * prev[L + (1 << q)])
+    T = np.array([f32(T[L] + f32(2.0 ** (l2 * C * (32 - L))) * zN) for L in range(32)], f32)
+    din = np.concatenate([T[1:], [zN]]).astype(f32)
+    out = np.zeros((32, C), f32)
+    for L in range(32):
+        p = rho
+        for m in range(C - 1, -1, -1):
+            out[L, m] = f32(f32(z[L, m] + p * din[L]) * rsc)
+            p = f32(p * rho)
+    return out.ravel(), float(rho_d)
 
 
 def dense_line(E, cx, s, open_):
@@ -86,15 +154,25 @@ def dense_line(E, cx, s, open_):
     return np.linalg.solve(A, E)
 
 
-# (W, shift s at cx = 4): the levels of a 512-site line at h = 0.5 and their warm-ups
-@pytest.mark.parametrize("W,s", [(12, 16.0), (16, 16.0), (24, 4.0), (32, 4.0), (40, 1.0), (48, 1.0)])
+# the finest level of a 512-site line at h = 0.5 (shift s = 16 at cx = 4)
+@pytest.mark.parametrize("W", [12, 16])
 @pytest.mark.parametrize("open_", [False, True])
-def test_recursive_line_solve_model(W, s, open_):
-    E = np.random.default_rng(W + int(4 * s)).normal(size=512)
-    got, rho = lane_model(E, 4.0, s, open_, W)
+def test_warm_up_line_solve_model(W, open_):
+    E = np.random.default_rng(W).normal(size=512)
+    got, rho = lane_model(E, 4.0, 16.0, open_, W)
     assert rho ** W <= 1e-8
-    ref = dense_line(E, 4.0, s, open_)
+    ref = dense_line(E, 4.0, 16.0, open_)
     assert np.abs(got - ref).max() <= 5e-7 * np.abs(ref).max()
+
+
+# the coarser levels (rho from 0.17 to 0.98, the last far beyond any warm-up)
+@pytest.mark.parametrize("s", [16.0, 4.0, 1.0, 0.25, 0.0625, 0.01, 0.001])
+@pytest.mark.parametrize("open_", [False, True])
+def test_scan_line_solve_model(s, open_):
+    E = np.random.default_rng(int(1000 * s)).normal(size=512)
+    got, rho = scan_model(E, 4.0, s, open_)
+    ref = dense_line(E, 4.0, s, open_)
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max(), rho
 
 
 def nb(j, d, n, bc):
