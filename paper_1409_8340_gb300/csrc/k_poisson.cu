@@ -1206,7 +1206,7 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     // several blocks per SM (the two finest transfers of a 512x512x256 grid), not on
     // small levels, where the two short kernels are faster
     const dim3 rr_grid((F.nx / 4 + kGX - 1) / kGX, C.ny, (C.nz + kRZ - 1) / kRZ);
-    if (v4 && F.fy == 2 && F.fz == 2 && zc < 0 && (long long)rr_grid.x * rr_grid.y * rr_grid.z >= 512) {
+    if (v4 && F.fy == 2 && F.fz == 2 && zc < 0 && (long long)rr_grid.x * rr_grid.y * rr_grid.z >= 100) {
         const dim3 grid = rr_grid;
         residual_restrict4_kernel<<<grid, kGX, 0, s>>>(F, C, bcx, bcy, bcz, a.ctl, l == 0);
         *nl -= 1;
