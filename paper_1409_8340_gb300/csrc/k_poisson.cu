@@ -1202,11 +1202,10 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     // still computed and restricted: zc = -1.)
     const bool proper = (bcy == kOpen || F.ny == 1 || (F.ny % 2) == 0) && (bcz == kOpen || F.nz == 1 || (F.nz % 2) == 0);
     const int zc = -1, oc = proper ? 0 : -1;
-    // the fused pass marches kRZ coarse planes per thread: it pays where that still leaves
-    // several blocks per SM (the two finest transfers of a 512x512x256 grid), not on
-    // small levels, where the two short kernels are faster
+    // residual and restriction in one pass wherever the level is coarsened in y and z
+    // (measured faster than the two kernels on every level of a 512x512x256 grid)
     const dim3 rr_grid((F.nx / 4 + kGX - 1) / kGX, C.ny, (C.nz + kRZ - 1) / kRZ);
-    if (v4 && F.fy == 2 && F.fz == 2 && zc < 0 && (long long)rr_grid.x * rr_grid.y * rr_grid.z >= 100) {
+    if (v4 && F.fy == 2 && F.fz == 2 && zc < 0) {
         const dim3 grid = rr_grid;
         residual_restrict4_kernel<<<grid, kGX, 0, s>>>(F, C, bcx, bcy, bcz, a.ctl, l == 0);
         *nl -= 1;
