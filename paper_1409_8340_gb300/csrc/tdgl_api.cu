@@ -532,7 +532,9 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
             const bool shape = (C == 16 || C == 32) && c.nx == 32 * C && sx > 0;
             M.iir = 0;
             M.iir_w = 0;
-            if (shape && C == 16) {
+            if (shape && C == 16 && rho <= 0.999) {
+                // (rho closer to 1, a line barely coupled in y and z, keeps the convolution:
+                // the scan's seeds would divide by 1 - rho^P near cancellation)
                 M.iir = 16;
                 M.iir_w = (pow(rho, 12.0) <= 1e-8) ? 12 : 0;
             } else if (shape && pow(rho, 32.0) <= 1e-9) {
