@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kGX) restrict4_kernel(MGLevel F, MGLevel C, in
     }
 }
 
-constexpr int kRZ = 4;   // coarse planes per block
+constexpr int kRZ = 4;   // coarse planes per block (at most; fewer on small levels)
 struct Rows3 {
     float4 m, c, p;   // rows 2J-1, 2J, 2J+1 of one fine plane
 };
@@ -314,13 +314,14 @@ __device__ __forceinline__ void residual_restrict_march(const MGLevel &F, const 
 // residual4_kernel followed by restrict4_kernel.
 // Six blocks per SM (80 registers, a few spilled bytes) hide more of the load latency
 // than four without spills: 138 against 154 us at 512x512x256.
+template <int RZ>
 __global__ void __launch_bounds__(kGX, 6) residual_restrict4_kernel(MGLevel F, MGLevel C, int bcx, int bcy, int bcz,
-                                                                 const DevCtl *ctl, int level0)
+                                                                    const DevCtl *ctl, int level0)
 {
     const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, J = blockIdx.y;
     if (i0 >= F.nx) return;
     const float fsub = level0 ? (float)ctl->fmean : 0.f;
-    const int Ka = blockIdx.z * kRZ, Kb = min(Ka + kRZ, C.nz);
+    const int Ka = blockIdx.z * RZ, Kb = min(Ka + RZ, C.nz);
     // interior block: rows 2J-2 .. 2J+2 and planes 2Ka-2 .. 2Kb exist without wrap or mirror
     const bool fast = (2 * J - 2 >= 0) && (2 * J + 2 <= F.ny - 1) && (2 * Ka - 2 >= 0) && (2 * Kb <= F.nz - 1);
     if (fast) residual_restrict_march<true>(F, C, bcx, bcy, bcz, fsub, i0, J, Ka, Kb);
@@ -1203,11 +1204,18 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     const bool proper = (bcy == kOpen || F.ny == 1 || (F.ny % 2) == 0) && (bcz == kOpen || F.nz == 1 || (F.nz % 2) == 0);
     const int zc = -1, oc = proper ? 0 : -1;
     // residual and restriction in one pass wherever the level is coarsened in y and z
-    // (measured faster than the two kernels on every level of a 512x512x256 grid)
-    const dim3 rr_grid((F.nx / 4 + kGX - 1) / kGX, C.ny, (C.nz + kRZ - 1) / kRZ);
+    // (measured faster than the two kernels on every level of a 512x512x256 grid); a
+    // thread marches over kRZ coarse planes, or over one where the level has too few
+    // blocks to fill the GPU (short chains hide the latency of small levels better)
     if (v4 && F.fy == 2 && F.fz == 2 && zc < 0) {
-        const dim3 grid = rr_grid;
-        residual_restrict4_kernel<<<grid, kGX, 0, s>>>(F, C, bcx, bcy, bcz, a.ctl, l == 0);
+        const long long cols = (long long)((F.nx / 4 + kGX - 1) / kGX) * C.ny;
+        if (cols * C.nz >= 2048LL * kRZ) {
+            const dim3 grid((F.nx / 4 + kGX - 1) / kGX, C.ny, (C.nz + kRZ - 1) / kRZ);
+            residual_restrict4_kernel<kRZ><<<grid, kGX, 0, s>>>(F, C, bcx, bcy, bcz, a.ctl, l == 0);
+        } else {
+            const dim3 grid((F.nx / 4 + kGX - 1) / kGX, C.ny, C.nz);
+            residual_restrict4_kernel<1><<<grid, kGX, 0, s>>>(F, C, bcx, bcy, bcz, a.ctl, l == 0);
+        }
         *nl -= 1;
     } else if (v4) {
         residual4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, bcx, bcy, bcz, a.ctl, l == 0, zc);
