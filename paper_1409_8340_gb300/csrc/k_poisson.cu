@@ -329,15 +329,17 @@ __global__ void __launch_bounds__(kGX, 6) residual_restrict4_kernel(MGLevel F, M
 }
 
 // only_color >= 0: only rows of that zebra colour take the correction (the other
-// colour's lines are solved exactly next, from r and these rows alone)
+// colour's lines are solved exactly next, from r and these rows alone).  GZ planes per
+// block (one on small levels, for more blocks).
+template <int GZ>
 __global__ void __launch_bounds__(kGX) prolong4_kernel(MGLevel F, MGLevel C, int bcy, int bcz, int only_color)
 {
     const int i0 = (blockIdx.x * kGX + threadIdx.x) * 4, j = blockIdx.y;
     if (i0 >= F.nx) return;
     const int nx = F.nx;
-    const int ka = blockIdx.z * kGZ, kb = min(ka + kGZ, F.nz);
+    const int ka = blockIdx.z * GZ, kb = min(ka + GZ, F.nz);
 #pragma unroll
-    for (int dk = 0; dk < kGZ; ++dk) {
+    for (int dk = 0; dk < GZ; ++dk) {
         const int k = ka + dk;
         if (k >= kb) break;
         if (only_color >= 0 && ((j + k) & 1) != only_color) continue;
@@ -1086,10 +1088,10 @@ struct CoarseArgs {
 
 // The two basis changes of the coarsest level as tiled products: Out[a][i] = sum_b
 // Mat[a][b] In[b][i] over the M y-z modes.  Block (x-tile, a-tile) stages In[b][64 x-sites]
-// and Mat[8 rows][b] in shared memory, kCB terms of the sum at a time; each thread sums
-// two outputs in the order of coarse_fwd_at / coarse_inv_at (b ascending).
+// and Mat[4 rows][b] in shared memory, kCB terms of the sum at a time; each thread sums
+// one output in the order of coarse_fwd_at / coarse_inv_at (b ascending).
 // FWD: Mat = W, In = -(r - fsub), Out = H in t.  Otherwise Mat = V, In = X, Out = u.
-constexpr int kCT = 64, kCA = 8, kCB = 128;
+constexpr int kCT = 64, kCA = 4, kCB = 128;
 template <bool FWD>
 __global__ void __launch_bounds__(256) coarse_mat_kernel(CoarseArgs A, const float *X)
 {
@@ -1102,8 +1104,8 @@ __global__ void __launch_bounds__(256) coarse_mat_kernel(CoarseArgs A, const flo
     const float *src = FWD ? L.r : (X ? X : L.t);
     float *out = FWD ? L.t : L.u;
     const int i0 = blockIdx.x * kCT, a0 = blockIdx.y * kCA;
-    const int ii = threadIdx.x % kCT, aa = threadIdx.x / kCT;   // rows aa and aa + 4
-    float acc0 = 0.f, acc1 = 0.f;
+    const int ii = threadIdx.x % kCT, aa = threadIdx.x / kCT;   // row aa
+    float acc0 = 0.f;
     for (int b0 = 0; b0 < M; b0 += kCB) {
         const int nb = min(kCB, M - b0);
         __syncthreads();
@@ -1124,12 +1126,10 @@ __global__ void __launch_bounds__(256) coarse_mat_kernel(CoarseArgs A, const flo
         for (int b = 0; b < nb; ++b) {
             const float v = In[b][ii];
             acc0 += Mt[aa][b] * v;
-            acc1 += Mt[aa + 4][b] * v;
         }
     }
     if (i0 + ii < nx) {
         if (a0 + aa < M) out[(size_t)(a0 + aa) * nx + i0 + ii] = acc0;
-        if (a0 + aa + 4 < M) out[(size_t)(a0 + aa + 4) * nx + i0 + ii] = acc1;
     }
 }
 
@@ -1226,7 +1226,13 @@ static cudaError_t vcycle(const PoissonArgs &a, int l, cudaStream_t s, long long
     }
     *nl += 3;
     vcycle(a, l + 1, s, nl);
-    if (v4) prolong4_kernel<<<grid_xyz4(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz, oc);
+    if (v4) {
+        const dim3 g4 = grid_xyz4(F.nx, F.ny, F.nz);
+        if ((long long)g4.x * g4.y * g4.z >= 2048)
+            prolong4_kernel<kGZ><<<g4, kGX, 0, s>>>(F, C, bcy, bcz, oc);
+        else
+            prolong4_kernel<1><<<dim3(g4.x, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz, oc);
+    }
     else prolong_kernel<<<grid_xyz(F.nx, F.ny, F.nz), kGX, 0, s>>>(F, C, bcy, bcz, oc);
     smooth(a, l, 1, s, nl, mean_out ? 1 : 0);
     smooth(a, l, 0, s, nl, mean_out ? 2 : 0);
