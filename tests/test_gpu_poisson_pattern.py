@@ -29,6 +29,9 @@ def poisson_cases():
         ("recursive_scan_periodic_512x32x32", quantised(Params(512, 32, 32, bc=(P, P, P)), 2)),
         ("recursive_scan_allopen_512x33x17", Params(512, 33, 17, bc=(OP, OP, OP), Bz=0.25)),
         ("recursive_scan_openx_512x96x48_J", Params(512, 96, 48, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        # a film (no z neighbours): the finest level itself (rho = 0.27) takes the exact scan
+        ("recursive_scan_film_512x256x1_J", Params(512, 256, 1, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
+        ("recursive_scan_film_periodic_512x256x1", quantised(Params(512, 256, 1, bc=(P, P, P)), 3)),
         # 1024-site lines: 32 sites per lane, the register-only recursive kernel
         ("recursive_openx_1024x24x12_J", Params(1024, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02)),
         ("recursive_periodic_1024x32x16", quantised(Params(1024, 32, 16, bc=(P, P, P)), 2)),
