@@ -96,7 +96,7 @@ extern "C" {
  *                   zeta = zeta_max (v1 + i v2), v1, v2 uniform on [-1, 1) drawn by
  *                   Philox4x32-10 with counter (site m, step n) and key noise_seed;
  *                   n counts the handle's steps since creation or the last
- *                   tdgl_set_state / tdgl_upload_state.
+ *                   tdgl_set_state / tdgl_upload_state, or is set by tdgl_set_step.
  *   noise_seed      key of the noise generator.
  *   Bx              field along x (Eq. B_xz), TDGL_LINKS_XZ only (0 otherwise).
  *   sweep_kernel    Jacobi sweep kernel: 1 register-tiled (two sites per thread,
@@ -170,6 +170,8 @@ typedef struct tdgl_obs {
     double vortex_signed;    /* sum_p n_p per z layer, averaged over layers            */
     double last_r2;          /* max |r|^2 at the last convergence test                 */
     double poisson_res;      /* max|F - Lap mu| / max|F| after the last Poisson solve  */
+                             /* (0 before the first solve; with a fixed number of     */
+                             /* V-cycles measured when the observables are computed)  */
     int32_t last_sweeps;     /* Jacobi sweeps of the last step                         */
     int32_t poisson_cycles;  /* V-cycles of the last step                              */
     int64_t step;            /* completed time steps                                   */
@@ -230,6 +232,14 @@ int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double 
 
 int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out);
 
+/* Set the step index: the count of completed steps that tdgl_obs.step reports, and
+ * the counter n of the thermal noise (Philox4x32-10 counter (site, n), Sec. 3.1.2)
+ * that the next step draws with.  A state load (tdgl_set_state, tdgl_upload_state)
+ * restarts the noise counter at 0; a checkpoint that stores psi, mu, K and the step
+ * index and is restored by a state load followed by tdgl_set_step continues the run
+ * exactly as if it had not been interrupted, noise included.  Synchronises. */
+int tdgl_set_step(tdgl_handle *h, int64_t step);
+
 /* Advance n_steps full time steps (psi, K, mu).  Synchronises once per step to
  * read the convergence status; returns the first error met. */
 int tdgl_step(tdgl_handle *h, int n_steps);
@@ -245,6 +255,25 @@ int tdgl_solve_mu(tdgl_handle *h);
 /* Start (on != 0) or stop collecting tdgl_profile data; enabling resets it. */
 int tdgl_profile_enable(tdgl_handle *h, int on);
 int tdgl_profile_read(tdgl_handle *h, tdgl_profile *out);
+
+/* Test hook for the bounded waits of the staged kernels (the Jacobi sweep and the
+ * Poisson right-hand side staged by the tensor memory accelerator, and the staged
+ * line smoother).  Each of their mbarrier waits ends after wait_ns nanoseconds
+ * (0: the default of 2 s; at most 2 s); extra_tx_bytes (0 .. 65536) is added to the
+ * bytes that the stages of the first block of each staged sweep or right-hand-side
+ * launch, and the boxes of the first warp of each staged smoother launch, expect.
+ * With a value > 0 those stages never complete and their waits run out while the
+ * rest of the launch completes -- no copy faults, the copies land and are waited
+ * for as in a real timeout.  The waits that run out record TDGL_ERR_TIMEOUT, which
+ * the step reports.  (0, 0), the state at creation, is normal use.  Synchronises the stream
+ * and drops the handle's captured Poisson graphs (captured again on the next solve).
+ *
+ * After TDGL_ERR_TIMEOUT, from this hook or from a copy that never landed, the
+ * handle's psi, mu and K stay at the last completed step and every later step
+ * reports TDGL_ERR_TIMEOUT again; tdgl_observables still works.  Loading a state
+ * (tdgl_set_state or tdgl_upload_state) clears the error and the handle steps
+ * normally again. */
+int tdgl_test_staged_waits(tdgl_handle *h, int64_t wait_ns, int32_t extra_tx_bytes);
 
 /* Compute observables of the current state (synchronises). */
 int tdgl_observables(tdgl_handle *h, tdgl_obs *out);

@@ -172,6 +172,7 @@ _SIGS = {
     "tdgl_upload_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
     "tdgl_download_state": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "tdgl_get_state": (ctypes.c_int, [_P, ctypes.POINTER(StatePtrs)]),
+    "tdgl_set_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "tdgl_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "tdgl_solve_psi": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "tdgl_solve_mu": (ctypes.c_int, [_P]),
@@ -181,6 +182,7 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(AdjointStats)]),
     "tdgl_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "tdgl_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "tdgl_test_staged_waits": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
     "tdgl_sweep_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), _P, _P, _P, ctypes.c_double, _P,
                                           ctypes.POINTER(ctypes.c_double), _P]),
     "tdgl_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int32]),

@@ -118,6 +118,8 @@ struct LineArgs {
     DevCtl *ctlw;
     double *blockred;
     double wsum;
+    unsigned long long wait_ns;   // staged smoother: wait bound (0: default)
+    unsigned int extra_tx;        // staged smoother: extra expected bytes (0 in normal use)
 };
 constexpr int kMeanOff = 4096;
 
@@ -585,7 +587,10 @@ __global__ void __launch_bounds__(kIirWarps * 32, 6)
         }
         __syncwarp();
     }
-    const unsigned long long deadline = TMA ? gtime() + kIirWaitNs : 0ull;
+    const unsigned long long wait_ns = A.wait_ns ? A.wait_ns : kIirWaitNs;
+    // timeout test only: the first warp's boxes expect bytes that never come
+    const unsigned xtx = (blockIdx.x == 0 && wib == 0) ? A.extra_tx : 0u;
+    const unsigned long long deadline = TMA ? gtime() + wait_ns : 0ull;
     // exact solve (W = 0): the lane's powers of rho, once per kernel: the weights of its
     // first (pw_f1) and last (pw_f2) site in w(-1), of its first site in z(N) (pw_b), and
     // the carries' seeds rho^(C(L+1)) (pw_c1) and rho^(C(32-L)) (pw_c2)
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(kIirWarps * 32, 6)
             if (lane == 0) {
                 // the warp's reads of the buffer (generic proxy) precede these writes
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect(bar, (unsigned)kIirTmaBytes);
+                mbar_expect(bar, (unsigned)kIirTmaBytes + xtx);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) tma_load2(dst + a * ROW, &map_u, 0, (int)(src[a] >> 5), bar);
             }
@@ -850,7 +855,7 @@ __global__ void __launch_bounds__(kIirWarps * 32, 6)
     }
     }
     // a wait that ran out: the boxes in flight land before the buffer is given up
-    if (TMA && issued) mbar_wait(bar, parity, deadline + kIirWaitNs);
+    if (TMA && issued) mbar_wait(bar, parity, deadline + wait_ns);
     if (!A.mean_stage) return;
     __shared__ double shd[32];
     __shared__ int flag;
@@ -917,6 +922,8 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.ctlw = a.ctl;
     A.blockred = a.blockred;
     A.wsum = a.wsum;
+    A.wait_ns = a.wait_ns;
+    A.extra_tx = a.extra_tx;
     if (A.nlines == 0 && mean_stage == 0) return cudaSuccess;
     if (L.iir == 16) {
         // staged by the tensor memory accelerator where this level's map describes its u,

@@ -18,8 +18,9 @@
 // approximation instead of the correctly rounded one (the new iterate then differs
 // by about one FP32 ulp).  Blocks whose tile touches no x or y face run the same
 // code with the face tests folded away.  Every wait is bounded by the global timer; a wait that runs out sets
-// TDGL_ERR_TIMEOUT and ends the sweep, and the producer drains its copies in
-// flight (again bounded) before the block exits.
+// TDGL_ERR_TIMEOUT and ends the block's planes, the producer drains its copies in
+// flight (again bounded), and the block still takes its part in the last-block
+// reduction, whose deciding block then ends the solve with that status.
 //
 // Landau links of either plane (XZ: the j-indexed tables and the y wrap of the
 // xz gauge), insulating sites (MASK: link bits, read per site pair), even nx.
@@ -113,9 +114,10 @@ __device__ __forceinline__ int plane_of(const DevGrid &g, int z)
 // accelerator requires of 8-byte elements).
 template <bool RHS>
 __device__ __forceinline__ void issue_plane(const TmaTile &T, int zp, StageT<RHS> &S, unsigned long long *full,
-                                           const CUtensorMap *mp, const CUtensorMap *mb, const CUtensorMap *md)
+                                           const CUtensorMap *mp, const CUtensorMap *mb, const CUtensorMap *md,
+                                           unsigned extra_tx)
 {
-    mbar_expect(full, RHS ? kPsiBytes : kPlaneBytes);
+    mbar_expect(full, (RHS ? kPsiBytes : kPlaneBytes) + extra_tx);
     tma_load3(&S.psi[0][0], mp, T.x0 - 2, T.j0 - 1, zp, full);
     if constexpr (!RHS) {
         tma_load3(&S.b[0][0], mb, T.x0, T.j0, zp, full);
@@ -156,7 +158,10 @@ __global__ void __launch_bounds__(kThreads, 3)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const unsigned long long deadline = gtime() + kWaitNs;
+    const unsigned long long wait_ns = a.wait_ns ? a.wait_ns : kWaitNs;
+    // timeout test only: the first block's stages expect bytes that never come
+    const unsigned xtx = (blockIdx.x | blockIdx.y | blockIdx.z) == 0 ? a.extra_tx : 0u;
+    const unsigned long long deadline = gtime() + wait_ns;
     float rmax = 0.f;
     float facc = 0.f;   // RHS: sum of w f over the thread's sites
 
@@ -171,12 +176,13 @@ __global__ void __launch_bounds__(kThreads, 3)
                     failed = 1;
                     break;
                 }
-                issue_plane<RHS>(T, plane_of(g, k0 - 1 + t), ring[s], &full[s], &map_psi, &map_b, &map_D);
+                issue_plane<RHS>(T, plane_of(g, k0 - 1 + t), ring[s], &full[s], &map_psi, &map_b, &map_D,
+                                 xtx);
                 issued = t + 1;
             }
             // drain: every issued plane's copies complete before the block can exit
             for (int t = max(0, issued - NS); t < issued; ++t)
-                mbar_wait(&full[t % NS], (unsigned)((t / NS) & 1), deadline + kWaitNs);
+                mbar_wait(&full[t % NS], (unsigned)((t / NS) & 1), deadline + wait_ns);
         }
         __syncwarp();
     } else {
@@ -381,12 +387,14 @@ __global__ void __launch_bounds__(kThreads, 3)
         else consume(std::false_type{});
     }
     __syncthreads();
+    // A block whose wait ran out records the timeout before it takes its ticket, so the
+    // deciding block sees it (the ticket's fence orders the write); it still takes the
+    // ticket, so the count returns to zero, and the deciding block ends the solve
+    // (sweep_decide keeps TDGL_ERR_TIMEOUT and sets done).  Its partial carries no value.
     if (failed) {
-        if (threadIdx.x == 0) {
-            a.ctl->status = TDGL_ERR_TIMEOUT;
-            if (!RHS) a.ctl->done = 1;
-        }
-        return;   // every thread of the block returns here: the finishing reduction is skipped
+        rmax = 0.f;
+        facc = 0.f;
+        if (threadIdx.x == 0) *(volatile int *)&a.ctl->status = TDGL_ERR_TIMEOUT;
     }
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
@@ -483,6 +491,8 @@ cudaError_t launch_poisson_rhs_tma(const PoissonArgs &pa, const float2 *psi, con
     a.f = pa.f;
     a.inj = pa.inject ? (float)(2.0 * pa.Jext / pa.hx) : 0.f;
     a.wsum = pa.wsum;
+    a.wait_ns = pa.wait_ns;
+    a.extra_tx = pa.extra_tx;
     const bool xz = a.g.Xj != nullptr, mk = a.g.lk != nullptr;
     if (xz && mk) return launch_variant<true, true, true>(a, map_psi, m, s);
     if (xz) return launch_variant<true, false, true>(a, map_psi, m, s);

@@ -24,6 +24,11 @@ __device__ __forceinline__ void sweep_decide(const SweepArgs &a, float gf, bool 
         c->nstep += 1;   // the init blocks have all read the noise counter
     }
     c->iter = it;
+    if (*(volatile int *)&c->status == TDGL_ERR_TIMEOUT) {
+        // a block of this sweep (or an earlier staged kernel) gave up waiting: end the solve
+        c->done = 1;
+        return;
+    }
     c->r2 = (double)gf;
     c->result = a.dst_index;
     if (!(gf <= FLT_MAX)) {

@@ -233,6 +233,8 @@ SweepArgs sweep_args(tdgl_handle *h)
     a.eps = h->cfg.eps;
     a.noise_amp = h->noise_amp;
     a.noise_seed = h->cfg.noise_seed;
+    a.wait_ns = h->dbg_wait_ns;
+    a.extra_tx = h->dbg_extra_tx;
     return a;
 }
 
@@ -602,6 +604,24 @@ int tdgl_profile_enable(tdgl_handle *h, int on)
     return TDGL_OK;
 }
 
+int tdgl_test_staged_waits(tdgl_handle *h, int64_t wait_ns, int32_t extra_tx_bytes)
+{
+    if (!h || wait_ns < 0 || wait_ns > 2000000000LL || extra_tx_bytes < 0 || extra_tx_bytes > 65536)
+        return TDGL_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->dbg_wait_ns = (unsigned long long)wait_ns;
+    h->dbg_extra_tx = (unsigned int)extra_tx_bytes;
+    h->pa.wait_ns = h->dbg_wait_ns;
+    h->pa.extra_tx = h->dbg_extra_tx;
+    // the captured Poisson graphs hold the old kernel arguments: capture again on the next solve
+    for (int q = 0; q < 3; ++q)
+        if (h->pgraph[q]) {
+            cudaGraphExecDestroy(h->pgraph[q]);
+            h->pgraph[q] = nullptr;
+        }
+    return TDGL_OK;
+}
+
 int tdgl_profile_read(tdgl_handle *h, tdgl_profile *out)
 {
     if (!h || !out) return TDGL_ERR_INVALID_ARG;
@@ -626,6 +646,7 @@ int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double
     c.Ux = make_float2((float)cos(h->cfg.hx * K), (float)sin(h->cfg.hx * K));
     if (cudaMemcpyAsync(h->ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (launch_set_Ux(h->ctl, h->cfg.hx, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->mu_solved = 0;   // f no longer belongs to mu
     return cuda_err(cudaStreamSynchronize(s));
 }
 
@@ -643,7 +664,19 @@ int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_m
     c.K = K;
     if (cudaMemcpyAsync(h->ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (launch_set_Ux(h->ctl, h->cfg.hx, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->mu_solved = 0;   // f no longer belongs to mu
     return cuda_err(cudaStreamSynchronize(s));
+}
+
+int tdgl_set_step(tdgl_handle *h, int64_t step)
+{
+    if (!h || step < 0) return TDGL_ERR_INVALID_ARG;
+    cudaStream_t s = h->stream;
+    const unsigned long long n = (unsigned long long)step;
+    if (cudaMemcpyAsync(&h->ctl->nstep, &n, sizeof(n), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->step = step;
+    return TDGL_OK;
 }
 
 int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double *K)
@@ -840,6 +873,7 @@ int tdgl_solve_mu(tdgl_handle *h)
     if (!h || h->batch_owned) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
+    h->mu_solved = 1;
     // plain solve from the second call on: replay a captured graph (the first call runs the
     // launches directly, which also sets the kernels' one-time attributes outside a capture)
     if (!h->lk && c.poisson_tol <= 0 && !h->pgraph_fail && h->poisson_calls++ >= 1) {
@@ -938,6 +972,11 @@ int tdgl_observables(tdgl_handle *h, tdgl_obs *out)
     if (!h || !out) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     double flux = c.hx * c.hy * c.Bz;
+    // a solve with a fixed number of V-cycles never measured its residual: measure it now
+    // (max|F - Lap mu| / max|F| of the last solve's right-hand side and result)
+    if (h->mu_solved && !h->batch_owned && !h->lk && c.poisson_tol <= 0 &&
+        launch_poisson_residual(h->pa, h->stream) != cudaSuccess)
+        return TDGL_ERR_CUDA;
     if (launch_observables(h->g, h->ctl, h->blockred, h->psi[h->cur], c.d_alpha, nullptr, flux, h->stream) != cudaSuccess)
         return TDGL_ERR_CUDA;
     DevCtl ctl;

@@ -210,6 +210,11 @@ struct SweepArgs {
     double wsum;               // sum of trapezoid weights (right-hand-side mode)
     float noise_amp;           // h_t zeta_max (init mode; 0: no noise)
     unsigned long long noise_seed;
+    // staged (tensor-map) kernels: bound of each mbarrier wait in ns (0: the kernel's
+    // default) and bytes added to each stage's expected transaction count (0 in normal
+    // use; > 0 makes every wait run out, for the timeout test)
+    unsigned long long wait_ns;
+    unsigned int extra_tx;
 };
 
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
@@ -308,6 +313,9 @@ struct PoissonArgs {
     // falls back to the asynchronous-copy smoother)
     CUtensorMap umap[kMaxLevels];
     const float *umap_u[kMaxLevels];
+    // staged kernels' wait bound and extra expected bytes (as in SweepArgs; 0: normal use)
+    unsigned long long wait_ns;
+    unsigned int extra_tx;
 };
 // tensor maps for the levels of pa that the recursive smoother handles (false: none made)
 bool mg_encode_line_maps(PoissonArgs &pa);
@@ -440,6 +448,9 @@ struct tdgl_handle {
     double last_javg;
     uint8_t *lk;               // link bits when insulating sites are given, else nullptr
     int use_tma;               // 1: Jacobi sweeps by the shared-memory staged kernel
+    int mu_solved;             // 1: a Poisson solve has run (f and mu hold its right-hand side and result)
+    unsigned long long dbg_wait_ns;   // tdgl_test_staged_waits: wait bound (0: default)
+    unsigned int dbg_extra_tx;        // tdgl_test_staged_waits: extra expected bytes (0: none)
     // the Poisson solve of a step (right-hand side, V-cycles, projection) as CUDA graphs,
     // one per psi buffer, captured on a private stream and replayed on the handle's stream
     cudaStream_t cap_stream;

@@ -209,6 +209,21 @@ class Solver:
                                           ctypes.c_void_p(mu_out.data_ptr()), ctypes.byref(K)), "tdgl_download_state")
         return psi_out, mu_out, K.value
 
+    def set_step(self, n: int):
+        """Set the step index and the noise counter of the next step (tdgl_set_step)."""
+        check(self._L.tdgl_set_step(self._h, int(n)), "tdgl_set_step")
+
+    def checkpoint(self) -> dict:
+        """The resumable state in host memory: psi, mu, K and the step index (which is
+        also the counter of the thermal noise)."""
+        psi, mu, K = self.download_state()
+        return {"psi": psi, "mu": mu, "K": K, "step": int(self.observables()["step"])}
+
+    def restore(self, ck: dict):
+        """Load a checkpoint(): the run continues exactly as it would have, noise included."""
+        self.upload_state(ck["psi"], ck["mu"], ck["K"])
+        self.set_step(ck["step"])
+
     def step(self, n: int = 1):
         check(self._L.tdgl_step(self._h, int(n)), "tdgl_step")
 
@@ -241,6 +256,12 @@ class Solver:
 
     def profile_enable(self, on: bool = True):
         check(self._L.tdgl_profile_enable(self._h, int(bool(on))), "tdgl_profile_enable")
+
+    def test_staged_waits(self, wait_ns: int = 0, extra_tx_bytes: int = 0):
+        """Test hook (tdgl_test_staged_waits): bound the staged kernels' waits by wait_ns and
+        add extra_tx_bytes to every stage's expected bytes, so that the waits run out;
+        (0, 0) is normal use."""
+        check(self._L.tdgl_test_staged_waits(self._h, int(wait_ns), int(extra_tx_bytes)), "tdgl_test_staged_waits")
 
     def profile(self) -> dict:
         pr = _lib.Profile()

@@ -137,3 +137,90 @@ def test_host_buffers_round_trip(O):
     psi2, mu2, K = s.download_state()
     np.testing.assert_array_equal(psi2.numpy(), psi)
     np.testing.assert_array_equal(mu2.numpy(), mu)
+
+
+def _timeout_case():
+    """512-site x lines, so that the Jacobi sweep, the Poisson right-hand side and the
+    finest multigrid level all run on the staged kernels."""
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(512, 32, 16, bc=(OP, P, P), Bz=0.2, Jext=0.01, eps=1e-6)
+    alpha = inclusion_alpha(p, 111)
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 112).astype(np.complex64)
+    return p, alpha, psi0
+
+
+def test_staged_sweep_timeout_is_reported_and_handle_recovers(O):
+    """The first block of every staged sweep waits for bytes that never come: its waits
+    run out after 20 ms (no copy faults), the step reports TDGL_ERR_TIMEOUT, the state
+    stays at the last completed step, and the last-block reductions of the handle stay
+    intact (the timed-out block still took its ticket): the observables of the same
+    state equal those of an untouched handle.  The error persists until a state is
+    loaded; then the handle steps exactly as the untouched one."""
+    import torch
+    from paper_1409_8340_gb300._lib import TDGL_ERR_TIMEOUT, TdglError
+    p, alpha, psi0 = _timeout_case()
+    s = make_solver(p, alpha, psi0)
+    ref = make_solver(p, alpha, psi0)
+    o_ref = ref.observables()
+    s.test_staged_waits(20_000_000, 64)
+    with pytest.raises(TdglError) as e:
+        s.step(1)
+    assert e.value.code == TDGL_ERR_TIMEOUT
+    s.test_staged_waits(0, 0)
+    psi_s, _ = gpu_state(s)
+    np.testing.assert_array_equal(psi_s, psi0.astype(np.complex128))
+    o = s.observables()
+    for k in ("psi2_mean", "energy", "vortex_unsigned", "vortex_signed"):
+        assert o[k] == pytest.approx(o_ref[k], rel=1e-12, abs=1e-12), k
+    with pytest.raises(TdglError) as e:
+        s.step(1)
+    assert e.value.code == TDGL_ERR_TIMEOUT
+    s.set_state(torch.as_tensor(psi0))
+    s.step(3)
+    ref.step(3)
+    a, b = gpu_state(s), gpu_state(ref)
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(a[1], b[1], rtol=0, atol=1e-5)
+
+
+def test_staged_poisson_timeout_is_reported_and_handle_recovers(O):
+    """The same for the Poisson solve: the first block of the staged right-hand side and
+    the first warp of every staged smoother launch time out; the solve itself returns
+    (it is asynchronous) and the next step reports TDGL_ERR_TIMEOUT; after a state load
+    the handle steps as an untouched one."""
+    import torch
+    from paper_1409_8340_gb300._lib import TDGL_ERR_TIMEOUT, TdglError
+    p, alpha, psi0 = _timeout_case()
+    s = make_solver(p, alpha, psi0)
+    ref = make_solver(p, alpha, psi0)
+    s.step(1)
+    ref.step(1)
+    psi1, mu1 = gpu_state(s)
+    s.test_staged_waits(20_000_000, 64)
+    s.solve_mu()
+    s.test_staged_waits(0, 0)
+    with pytest.raises(TdglError) as e:
+        s.step(1)
+    assert e.value.code == TDGL_ERR_TIMEOUT
+    s.set_state(torch.as_tensor(psi1.astype(np.complex64)), torch.as_tensor(mu1.astype(np.float32)),
+                ref.observables()["K"])
+    s.step(2)
+    ref.step(2)
+    a, b = gpu_state(s), gpu_state(ref)
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(a[1], b[1], rtol=0, atol=1e-5)
+
+
+def test_vortex_count_of_known_defects_on_the_gpu():
+    """Vortices and antivortices at known plaquette centres (zero field, open x and y):
+    the GPU's unsigned count per layer is the number of defects, the signed count their
+    net charge (the oracle's winding is pinned on the same state)."""
+    import torch
+    from test_oracle_pins import DEFECTS, vortex_state
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(24, 22, 3, bc=(OP, OP, P))
+    s = make_solver(p, np.ones(p.shape, dtype=np.float32))
+    s.set_state(torch.as_tensor(vortex_state(p.nx, p.ny, p.nz, DEFECTS).astype(np.complex64)))
+    o = s.observables()
+    assert o["vortex_unsigned"] == len(DEFECTS)
+    assert o["vortex_signed"] == sum(sg for _, _, sg in DEFECTS)

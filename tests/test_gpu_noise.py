@@ -107,3 +107,30 @@ def test_adjoint_refuses_noise():
     s = make_solver(p, inclusion_alpha(p, 50), I.random_psi(p.nx, p.ny, p.nz, 51))
     with pytest.raises(TdglError):
         s.adjoint(4, checkpoint_every=2)
+
+
+@pytest.mark.parametrize("noise_T", [0.0, 0.004], ids=["no_noise", "noise"])
+def test_checkpoint_resume_is_bitwise_continuous(noise_T):
+    """100 straight steps equal 50 steps, a checkpoint to host memory (psi, mu, K and the
+    step index, which is the noise counter), a fresh handle restored from it, and 50 more
+    steps: bit for bit, with and without thermal noise."""
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(64, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02, noise_T=noise_T, noise_seed=91)
+    alpha = inclusion_alpha(p, 92)
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 93)
+    a = make_solver(p, alpha, psi0)
+    a.step(100)
+    b = make_solver(p, alpha, psi0)
+    b.step(50)
+    ck = b.checkpoint()
+    assert ck["step"] == 50
+    b.close()
+    c = make_solver(p, alpha)
+    c.restore(ck)
+    c.step(50)
+    assert c.observables()["step"] == 100
+    pa, ma = gpu_state(a)
+    pc, mc = gpu_state(c)
+    np.testing.assert_array_equal(pa, pc)
+    np.testing.assert_array_equal(ma, mc)
+    assert a.observables()["K"] == c.observables()["K"]
