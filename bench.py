@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--relax", type=int, default=150, help="untimed steps from the random start")
     ap.add_argument("--J", type=float, default=0.025)
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the batched and adjoint measurements")
     ap.add_argument("--batch-steps", type=int, default=30)
@@ -162,18 +162,51 @@ def workload(J: float, nz_override: int | None = None):
     return w
 
 
-def cpu_oracle_run(J: float, budget_s: float, max_steps: int | None = None):
-    """Time the FP64 oracle on the slab sample.  Returns (value, info)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_oracle_run(J: float, budget_s: float, max_steps: int | None = None, case: str = "slab",
+                   threads: int | None = None, warm: bool = True):
+    """Time the FP64 oracle on a bounded sample: `slab` = a 512x512x8 slab of the
+    512x512x256 workload, `transport` = the 128x128x64 transport workload in full
+    size (a bounded number of its steps).  threads: OpenMP threads (None: all).  warm: one
+    untimed step first.  Returns (value, info, seconds, steps, sweeps)."""
     import numpy as np
 
     from oracle import oracle as O
     from paper_1409_8340_gb300 import inputs
-    w = workload(J, SLAB_NZ)
+    if case == "transport":
+        from paper_1409_8340_gb300.presets import transport_128x128x64
+        w = transport_128x128x64()
+        label = "the 128x128x64 transport workload (full size; open x, periodic y z, Bz 0.1, J 0.01)"
+    else:
+        w = workload(J, SLAB_NZ)
+        label = (f"a 512x512x{SLAB_NZ} slab of the 512x512x256 workload (same h, BCs, field, current, "
+                 f"inclusion recipe)")
     p = w.params
     G = O.Grid(p.nx, p.ny, p.nz, hx=p.hx, hy=p.hy, hz=p.hz, bc=tuple(p.bc), Bz=p.Bz, Jext=p.Jext, ht=p.ht)
     alpha, _, _ = O.pattern(G, w.candidates, w.target_sites, w.alpha_in, w.alpha_out)
+    n_all = os.cpu_count() or 1
+    O.set_threads(threads if threads else n_all)
     st = O.State(inputs.random_psi(p.nx, p.ny, p.nz, w.seed), np.zeros(p.shape))
-    O.step(G, st, alpha, eps=p.eps)            # one untimed step (first-touch, build)
+    if warm:
+        O.step(G, st, alpha, eps=p.eps)        # one untimed step (first-touch, build)
     t0 = time.perf_counter()
     sweeps = steps = 0
     while True:
@@ -183,12 +216,28 @@ def cpu_oracle_run(J: float, budget_s: float, max_steps: int | None = None):
         el = time.perf_counter() - t0
         if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= budget_s):
             break
+    used = O.threads()
+    O.set_threads(n_all)
     value = sweeps * p.N / el / 1e9
-    info = {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
-            "sample": f"{steps} FP64 oracle time steps ({sweeps} Jacobi sweeps) on a {p.nx}x{p.ny}x{p.nz} slab of "
-                      f"the 512x512x256 workload (same h, BCs, field, current, inclusion recipe); "
-                      f"{el:.1f} s wall, OpenMP threads = {O.threads()}"}
+    info = {"value": value, "unit": METRIC, "cores": used, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle time steps ({sweeps} Jacobi sweeps) on {label}; "
+                      f"{el:.1f} s wall, OpenMP threads = {used}"}
     return value, info, el, steps, sweeps
+
+
+def cpu_baseline_report(J: float, budget_s: float):
+    """The oracle on the host cores: the 512x512x256 slab sample on all cores (the
+    headline cpu_baseline), the same on one core, and the 128x128x64 transport workload
+    on all cores and on one core; with the CPU model and core count."""
+    value, info, _, _, _ = cpu_oracle_run(J, budget_s)
+    info["cpu_model"] = cpu_model()
+    info["host_cores"] = os.cpu_count()
+    _, one, _, _, _ = cpu_oracle_run(J, budget_s / 3, threads=1, warm=False)
+    info["one_thread"] = one
+    _, tr_all, _, _, _ = cpu_oracle_run(J, budget_s / 3, case="transport")
+    _, tr_one, _, _, _ = cpu_oracle_run(J, budget_s / 3, case="transport", threads=1, warm=False)
+    info["transport_128x128x64"] = {"all_cores": tr_all, "one_thread": tr_one}
+    return value, info
 
 
 # ---------------------------------------------------------------------------
@@ -594,7 +643,7 @@ def run_native(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        _, cpu, _, _, _ = cpu_oracle_run(args.J, args.cpu_seconds)
+        _, cpu = cpu_baseline_report(args.J, args.cpu_seconds)
 
     if rank == 0:
         line = {
@@ -624,7 +673,8 @@ def run_native(args, rank, world, local_rank):
             "gpu_launches": prof["kernel_launches"],
             "clocks": clk,
             "observables": {"Ex": obs["Ex"], "psi2_mean": obs["psi2_mean"],
-                            "vortex_unsigned_per_layer": obs["vortex_unsigned"], "last_sweeps": obs["last_sweeps"]},
+                            "vortex_unsigned_per_layer": obs["vortex_unsigned"], "last_sweeps": obs["last_sweeps"],
+                            "poisson_res": obs["poisson_res"], "poisson_cycles": obs["poisson_cycles"]},
             "cpu_baseline": cpu,
         }
         line.update(modes)

@@ -1,0 +1,106 @@
+"""Parity of the configuration the benchmark times: the library defaults.
+
+Defaults: eps = 1e-6, poisson_cycles = 2 and poisson_tol = 0 (two multigrid V-cycles
+per step, warm-started from the previous mu, with no residual test), and the Poisson
+solve replayed from a CUDA graph from the second step on.  The case is an open-x
+flux-flow sample with 512-site x lines, so that the staged sweep, the staged
+right-hand side and both variants of the recursive line smoother run: 512 x 64 x 32,
+with the field, current and inclusion recipe of the 512 x 512 x 256 workload (Bz = 0.2,
+J = 0.025, ellipsoids with semi-axes U[1.5, 5] to 10 % volume).
+
+Per step, against the oracle (Sec. 3.2, Eq. Poisson: the exact discrete solution of
+Lap mu = f with zero weighted mean):
+  * mu against the exact solve of the GPU's own right-hand side f.  Bound: the step
+    lags mu by one step in the psi update (psi first, then mu, Sec. 3 and Sec. 4.1),
+    so the scheme itself works with an error of max|mu^n - mu^(n-1)| in mu within
+    every step.  The solve error must stay below a tenth of that lag, plus the FP32
+    floor of a converged multigrid solve, 1e-4 max|mu| (measured: 6e-5 max|mu| at a
+    relative residual of 7e-5).
+  * E_x (Sec. 2.2, read from the face potentials) against the E_x of the exact mu,
+    within 1e-3 relative: a tenth of the 1 % budget of the time-averaged voltage.
+Long run: time averages of <|psi|^2>, the vortex count and E_x against the oracle's
+run from the same start, within 1 % (the statistical parity of the method).
+"""
+import numpy as np
+import pytest
+
+from _helpers import OP, P, gpu_state, oracle_grid
+from paper_1409_8340_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+LAG_FRACTION = 0.1
+FP32_FLOOR = 1e-4
+EX_REL = 1e-3
+
+
+def flux_flow_case(nx, ny, nz):
+    from paper_1409_8340_gb300.solver import Params, pattern
+    p = Params(nx, ny, nz, bc=(OP, P, P), Bz=0.2, Jext=0.025)
+    box = (p.length(0), p.length(1), p.length(2))
+    cand = I.ellipsoids(max(200, int(20000 * p.N / (512 * 512 * 256))), box, 1.5, 5.0, seed=3)
+    alpha, _, _ = pattern(p, cand, I.target_sites(0.10, p.N))
+    return p, alpha
+
+
+def test_defaults_are_the_benchmark_configuration():
+    from paper_1409_8340_gb300.presets import mesoscopic_512x512x256
+    from paper_1409_8340_gb300.solver import Params
+    p, d = mesoscopic_512x512x256(0.025).params, Params(8, 8, 8)
+    assert (p.poisson_cycles, p.poisson_tol, p.eps) == (d.poisson_cycles, d.poisson_tol, d.eps) == (2, 0.0, 1e-6)
+    assert (p.sweep_kernel, p.sweeps_per_pass, p.check_every, p.fixed_sweeps) == (0, 1, 1, 0)
+
+
+def test_default_poisson_solve_per_step(O):
+    import torch
+    from paper_1409_8340_gb300.solver import Solver
+    p, alpha = flux_flow_case(512, 64, 32)
+    G = oracle_grid(O, p)
+    s = Solver(p, alpha)
+    s.set_state(torch.as_tensor(I.random_psi(p.nx, p.ny, p.nz, 3).astype(np.complex64)))
+    s.step(100)                                  # into steady flux flow (graph replay from step 2)
+    worst = 0.0
+    for n in range(30):
+        _, mu_prev = gpu_state(s)
+        s.step(1)
+        o = s.observables()
+        f = s.internals()[2].cpu().numpy().astype(np.float64)
+        _, mu = gpu_state(s)
+        mu_ex = O.poisson_solve(G, f)
+        lag = np.max(np.abs(mu_ex - mu_prev))
+        bound = LAG_FRACTION * lag + FP32_FLOOR * np.max(np.abs(mu_ex))
+        err = np.max(np.abs(mu - mu_ex))
+        assert err <= bound, (n, err, lag, bound)
+        worst = max(worst, err / bound)
+        ex_ex = O.voltage_open_x(G, mu_ex)
+        assert abs(o["Ex"] - ex_ex) <= EX_REL * abs(ex_ex), (n, o["Ex"], ex_ex)
+        assert 0.0 < o["poisson_res"] < 1e-2, o["poisson_res"]
+        assert o["poisson_cycles"] == 2
+    assert worst < 1.0
+
+
+def test_default_configuration_long_run(O):
+    """512 x 32 x 16 from a random start, 300 steps at the defaults on the GPU and with
+    exact solves in the oracle; averages over the second half."""
+    import torch
+    from paper_1409_8340_gb300.solver import Solver
+    p, alpha = flux_flow_case(512, 32, 16)
+    a = alpha.cpu().numpy().astype(np.float64)
+    G = oracle_grid(O, p)
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 33).astype(np.complex64)
+    s = Solver(p, alpha)
+    s.set_state(torch.as_tensor(psi0))
+    st = O.State(psi0.astype(np.complex128), np.zeros(p.shape))
+    steps = 300
+    rec_o, rec_g = [], []
+    for n in range(steps):
+        so = O.step(G, st, a, eps=p.eps)
+        s.step(1)
+        if n >= steps // 2:
+            rec_o.append((float(np.mean(np.abs(st.psi) ** 2)), O.vortex_count(G, st.psi, st.K)[0], so.Ex))
+            o = s.observables()
+            rec_g.append((o["psi2_mean"], o["vortex_unsigned"], o["Ex"]))
+    avg_o, avg_g = np.mean(rec_o, axis=0), np.mean(rec_g, axis=0)
+    assert abs(avg_g[0] - avg_o[0]) <= 0.01 * abs(avg_o[0]), (avg_g, avg_o)
+    assert abs(avg_g[1] - avg_o[1]) <= 0.01 * max(abs(avg_o[1]), 1.0), (avg_g, avg_o)
+    assert abs(avg_g[2] - avg_o[2]) <= max(0.01 * abs(avg_o[2]), 1e-4 * p.Jext), (avg_g, avg_o)
