@@ -74,28 +74,44 @@ def test_batch_matches_plain_handles():
 
 
 def test_batch_against_oracle(O):
-    """Two instances, 4 steps, convergence-tested sweeps; the oracle's mu is the
-    exact Poisson solution, the batch runs enough fixed V-cycles to reach it."""
+    """Two instances, 4 steps, convergence-tested sweeps, each step checked against the
+    oracle from the batch's own input state at the per-step tolerance of the plain path
+    (2e-5); the oracle's mu is the exact Poisson solution and the batch runs enough fixed
+    V-cycles to reach it (within the FP32 floor of the multigrid, 1e-4 max|mu|).  Where the
+    convergence test passed within FP32 rounding on one side only, the oracle is run to
+    the batch's sweep count."""
     from paper_1409_8340_gb300.solver import Params
     ps = [Params(34, 22, 13, bc=(OP, P, P), Bz=0.21, Jext=0.02, eps=1e-7, poisson_cycles=12),
           quantised(Params(16, 16, 8, bc=(P, P, P), eps=1e-7, poisson_cycles=12), 2)]
     alphas, psi0s, _ = inputs(ps, 200)
     psi0s = [p.astype(np.complex64).astype(np.complex128) for p in psi0s]
     b = make_batch(ps, alphas, psi0s)
-    for i, p in enumerate(ps):
-        G = oracle_grid(O, p)
-        st = O.State(psi0s[i].copy(), np.zeros(p.shape))
-        sweeps_o = []
-        for n in range(4):
-            sweeps_o.append(O.step(G, st, alphas[i].astype(np.float64), eps=p.eps).sweeps)
-        if i == 0:
-            b.step(4)
-            b.check()
-        psi_b, mu_b = gpu_state(b.instances[i])
-        assert np.max(np.abs(psi_b - st.psi)) <= 4 * TOL_PSI, (i, np.max(np.abs(psi_b - st.psi)))
-        scale = max(1.0, np.max(np.abs(st.mu)))
-        assert np.max(np.abs(mu_b - st.mu)) <= 1e-4 * scale, (i, np.max(np.abs(mu_b - st.mu)))
-        assert abs(b.observables()[i]["K"] - st.K) <= 1e-5
+    Gs = [oracle_grid(O, p) for p in ps]
+    mism = 0
+    for n in range(4):
+        ins = []
+        for i in range(len(ps)):
+            psi_in, mu_in = gpu_state(b.instances[i])
+            ins.append((psi_in, mu_in, b.observables()[i]["K"]))
+        b.step(1)
+        b.check()
+        obs = b.observables()
+        for i, p in enumerate(ps):
+            a = alphas[i].astype(np.float64)
+            st = O.State(ins[i][0], ins[i][1], K=ins[i][2])
+            so = O.step(Gs[i], st, a, eps=p.eps)
+            ng = obs[i]["last_sweeps"]
+            if ng != so.sweeps:
+                mism += 1
+                assert abs(ng - so.sweeps) <= 1
+                st = O.State(ins[i][0], ins[i][1], K=ins[i][2])
+                O.step(Gs[i], st, a, fixed_sweeps=ng)
+            psi_b, mu_b = gpu_state(b.instances[i])
+            assert np.max(np.abs(psi_b - st.psi)) <= TOL_PSI, (n, i, np.max(np.abs(psi_b - st.psi)))
+            scale = max(1.0, np.max(np.abs(st.mu)))
+            assert np.max(np.abs(mu_b - st.mu)) <= 1e-4 * scale, (n, i, np.max(np.abs(mu_b - st.mu)))
+            assert abs(obs[i]["K"] - st.K) <= 1e-5
+    assert mism <= 2
 
 
 def test_graph_replay_and_launch_shapes_agree():

@@ -106,10 +106,13 @@ def test_tolerance_mode_per_step(O, name, p):
         ng = s.observables()["last_sweeps"]
         psi_g, _ = gpu_state(s)
         if ng != so.sweeps:
+            # r2 met eps within FP32 rounding on one side only: the two results differ by one
+            # sweep of the iteration, so compare with the oracle run to the GPU's count
             mism += 1
             assert abs(ng - so.sweeps) <= 1
-            continue
-        assert np.max(np.abs(psi_g - st.psi)) <= TOL_PSI
+            st = O.State(psi_in, mu_in, K=K_in)
+            O.step(G, st, alpha.astype(np.float64), fixed_sweeps=ng)
+        assert np.max(np.abs(psi_g - st.psi)) <= TOL_PSI, (n, ng, so.sweeps)
     assert mism <= 2
 
 

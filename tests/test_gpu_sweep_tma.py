@@ -77,15 +77,19 @@ def test_staged_tolerance_mode(O, name, p):
     mism = 0
     for n in range(8):
         psi_in, mu_in = gpu_state(s)
-        st = O.State(psi_in, mu_in, K=s.observables()["K"])
+        K_in = s.observables()["K"]
+        st = O.State(psi_in, mu_in, K=K_in)
         so = O.step(G, st, alpha.astype(np.float64), eps=p.eps)
         s.step(1)
         ng = s.observables()["last_sweeps"]
         if ng != so.sweeps:
+            # the test passed within FP32 rounding on one side only: compare with the
+            # oracle run to the GPU's sweep count from the same input
             mism += 1
             assert abs(ng - so.sweeps) <= 1
-            continue
-        assert np.max(np.abs(gpu_state(s)[0] - st.psi)) <= TOL_PSI
+            st = O.State(psi_in, mu_in, K=K_in)
+            O.step(G, st, alpha.astype(np.float64), fixed_sweeps=ng)
+        assert np.max(np.abs(gpu_state(s)[0] - st.psi)) <= TOL_PSI, (n, ng, so.sweeps)
     assert mism <= 2
 
 
