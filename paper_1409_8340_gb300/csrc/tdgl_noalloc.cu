@@ -13,7 +13,8 @@
 // Set-up: the first call on a device, with that device current, looks up the
 // device address of the array (cudaGetSymbolAddress); make that first call
 // before any stream capture.  Every call overwrites the whole control block
-// and the link tables, so nothing depends on what an earlier call left there.
+// and the entries of the link tables that its grid reads, so nothing depends on
+// what an earlier call left there.
 // All calls share the one array: calls that overlap on the GPU (on different
 // streams, or from different host threads) race on it and must not be issued.
 #include <math.h>
@@ -117,31 +118,39 @@ extern "C" int tdgl_sweep_noalloc(const tdgl_config *cfg, const float *d_psi_in,
     float2 *tUz = tUy + kNaMaxAxis, *tPy = tUz + kNaMaxAxis, *tPz = tPy + kNaMaxAxis;
     DevCtl *ctl = reinterpret_cast<DevCtl *>(sb + NaLayout::ctl);
 
-    // link tables of the Landau gauge and the periodic-x wrap phase, in FP64
-    std::vector<float2> host(4 * (size_t)kNaMaxAxis, make_float2(1.f, 0.f));
+    // link tables of the Landau gauge and the periodic-x wrap phase, in FP64; only the
+    // entries the grid uses are built and copied, each table at its fixed offset
+    // (the x tables are read in pairs: an odd nx gets one padding entry, exp(0))
+    const size_t nxp = (size_t)c.nx + (c.nx & 1);
+    std::vector<float2> hUy(nxp, make_float2(1.f, 0.f)), hUz(nxp, make_float2(1.f, 0.f));
+    std::vector<float2> hPy((size_t)c.ny), hPz((size_t)c.nz);
     for (int i = 0; i < c.nx; ++i) {
         const double xbar = i * c.hx - 0.5 * Lx;
         const double ay = fmod(-c.hy * c.Bz * xbar, kTwoPi), az = fmod(c.hz * c.By * xbar, kTwoPi);
-        host[i] = make_float2((float)cos(ay), (float)sin(ay));
-        host[kNaMaxAxis + i] = make_float2((float)cos(az), (float)sin(az));
+        hUy[i] = make_float2((float)cos(ay), (float)sin(ay));
+        hUz[i] = make_float2((float)cos(az), (float)sin(az));
     }
     for (int j = 0; j < c.ny; ++j) {
         const double ph = qy ? -kTwoPi * (double)(((nzq * j) % c.ny + c.ny) % c.ny) / c.ny
                              : -fmod(j * c.hy * Lx * c.Bz, kTwoPi);
-        host[2 * (size_t)kNaMaxAxis + j] = make_float2((float)cos(ph), (float)sin(ph));
+        hPy[j] = make_float2((float)cos(ph), (float)sin(ph));
     }
     for (int k = 0; k < c.nz; ++k) {
         const double ph = qz ? kTwoPi * (double)(((nyq * k) % c.nz + c.nz) % c.nz) / c.nz
                              : fmod(k * c.hz * Lx * c.By, kTwoPi);
-        host[3 * (size_t)kNaMaxAxis + k] = make_float2((float)cos(ph), (float)sin(ph));
+        hPz[k] = make_float2((float)cos(ph), (float)sin(ph));
     }
     DevCtl h;
     memset(&h, 0, sizeof(h));
     h.K = K;
     h.Ux = make_float2((float)cos(c.hx * K), (float)sin(c.hx * K));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(tUy, host.data(), sizeof(float2) * host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return TDGL_ERR_CUDA;
+    const std::vector<float2> *tabs[4] = {&hUy, &hUz, &hPy, &hPz};
+    float2 *dtabs[4] = {tUy, tUz, tPy, tPz};
+    for (int q = 0; q < 4; ++q)
+        if (cudaMemcpyAsync(dtabs[q], tabs[q]->data(), sizeof(float2) * tabs[q]->size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return TDGL_ERR_CUDA;
     if (cudaMemcpyAsync(ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
 
     const bool zact = c.nz >= 2;
