@@ -96,6 +96,8 @@ def lib():
         L.or_inside_q.argtypes = [gp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_inside_q.restype = d
         L.or_threads.restype = ctypes.c_int
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_set_threads.restype = ctypes.c_int
         i64 = ctypes.c_int64
         L.or_shape_contains.argtypes = [gp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_shape_contains.restype = ctypes.c_int
@@ -182,6 +184,11 @@ def _theta_ptr(theta):
 def threads() -> int:
     """OpenMP threads used by the C loops."""
     return int(lib().or_threads())
+
+
+def set_threads(n: int) -> int:
+    """Run the C loops on n OpenMP threads; returns the count now in use."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def landau_link_phases(G: Grid) -> np.ndarray:

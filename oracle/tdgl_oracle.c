@@ -853,6 +853,18 @@ int or_threads(void)
 #endif
 }
 
+/* Set the number of OpenMP threads of the parallel loops (n >= 1); returns the new count. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Neighbour sum NS_m(psi) (complex) and its conjugate transpose, for the    */
 /* adjoint of the step.  NS^H has entries conj(NS_{m',m}): the open-face      */
