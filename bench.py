@@ -657,6 +657,7 @@ def run_native(args, rank, world, local_rank):
                        "inclusions": {"kind": "ellipsoids", "used": used, "sites": marked,
                                       "fraction": marked / p.N},
                        "relax_steps": args.relax, "poisson_cycles": p.poisson_cycles,
+                       "poisson_guess": "2 mu^(n-1) - mu^(n-2)" if p.poisson_guess in (0, 2) else "mu^(n-1)",
                        "l2": "inputs larger than L2 (512 MiB per complex64 array vs 129 MB L2); no flush",
                        "parallelism": f"replicas x{world}"},
             "sweeps_per_step": prof["sweeps"] / max(1, prof["steps"]),

@@ -106,7 +106,16 @@ extern "C" {
  *                   plane, with or without insulating sites, even nx, else the
  *                   register-tiled kernel runs); 0 the default, which is 2.  Both
  *                   give the same iterates (same arithmetic, same order).
- *   reserved1       0.
+ *   poisson_guess   starting guess of each Poisson solve: 1 the previous step's mu;
+ *                   2 its linear extrapolation in time, 2 mu^(n-1) - mu^(n-2) (the
+ *                   previous mu on the first step after creation or a state load);
+ *                   0 the default, which is 2 for a single handle and 1 for the
+ *                   members of a batch (which refuse 2).  With insulating sites, and
+ *                   for tdgl_solve_mu called on its own (not after the psi solve of
+ *                   a step), the guess is the current mu.  The solution the solve
+ *                   converges to does not depend on it; with a fixed number of
+ *                   V-cycles the extrapolated guess leaves a smaller error (one cycle
+ *                   from it about as small as two from the previous mu on flux flow).
  *   d_insulating    device u8[N] or NULL: nonzero marks an insulating site
  *                   (Sec. 3.4 (ii), e.g. the mask of tdgl_pattern_ex).  Every link
  *                   that touches an insulating site carries no current: it leaves
@@ -151,7 +160,7 @@ typedef struct tdgl_config {
     const float *d_link_phase;
     const uint8_t *d_insulating;
     int32_t sweep_kernel;
-    int32_t reserved1;
+    int32_t poisson_guess;
 } tdgl_config;
 
 typedef struct tdgl_handle tdgl_handle;
@@ -177,7 +186,8 @@ typedef struct tdgl_obs {
     int64_t step;            /* completed time steps                                   */
 } tdgl_obs;
 
-/* Device pointers into the handle's workspace (valid until tdgl_destroy). */
+/* Device pointers into the handle's workspace, where the current state lies: the
+ * arrays rotate among buffers, so fetch them again after each step. */
 typedef struct tdgl_state_ptrs {
     float *psi;   /* complex64[N], current psi^n                  */
     float *mu;    /* f32[N], current mu^n                         */
@@ -235,10 +245,21 @@ int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out);
 /* Set the step index: the count of completed steps that tdgl_obs.step reports, and
  * the counter n of the thermal noise (Philox4x32-10 counter (site, n), Sec. 3.1.2)
  * that the next step draws with.  A state load (tdgl_set_state, tdgl_upload_state)
- * restarts the noise counter at 0; a checkpoint that stores psi, mu, K and the step
- * index and is restored by a state load followed by tdgl_set_step continues the run
- * exactly as if it had not been interrupted, noise included.  Synchronises. */
+ * restarts the noise counter at 0.  Synchronises. */
 int tdgl_set_step(tdgl_handle *h, int64_t step);
+
+/* The previous step's mu (f32[N]), which the extrapolated Poisson guess of the next
+ * step reads (tdgl_config.poisson_guess).  tdgl_get_mu_prev copies it to out (host
+ * memory if out_on_host, else device memory) and returns 1, or returns 0 when the
+ * handle holds none (after creation or a state load, or without the extrapolated
+ * guess).  tdgl_set_mu_prev copies one in (NULL: none); it is refused without the
+ * extrapolated guess.  A state load clears it, so load the state first.
+ *
+ * Checkpoints: psi, mu and K (tdgl_download_state), the previous mu and the step
+ * index, restored by a state load, tdgl_set_mu_prev and tdgl_set_step, continue the
+ * run exactly as if it had not been interrupted, noise included.  Both synchronise. */
+int tdgl_get_mu_prev(tdgl_handle *h, float *out, int32_t out_on_host);
+int tdgl_set_mu_prev(tdgl_handle *h, const float *in, int32_t in_on_host);
 
 /* Advance n_steps full time steps (psi, K, mu).  Synchronises once per step to
  * read the convergence status; returns the first error met. */

@@ -58,7 +58,7 @@ class Config(ctypes.Structure):
         ("d_alpha", ctypes.c_void_p),
         ("d_link_phase", ctypes.c_void_p),
         ("d_insulating", ctypes.c_void_p),
-        ("sweep_kernel", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("sweep_kernel", ctypes.c_int32), ("poisson_guess", ctypes.c_int32),
     ]
 
 
@@ -173,6 +173,8 @@ _SIGS = {
     "tdgl_download_state": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "tdgl_get_state": (ctypes.c_int, [_P, ctypes.POINTER(StatePtrs)]),
     "tdgl_set_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "tdgl_get_mu_prev": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "tdgl_set_mu_prev": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "tdgl_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "tdgl_solve_psi": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "tdgl_solve_mu": (ctypes.c_int, [_P]),

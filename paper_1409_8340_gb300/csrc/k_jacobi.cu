@@ -331,13 +331,45 @@ static void launch_sweep2(const SweepArgs &a, int kz, cudaStream_t s)
     else sweep2_kernel<MODE, false, false><<<grid, block, 0, s>>>(a, kz);
 }
 
+// P = a S + b P, four sites per thread where the arrays allow 16-byte access
+__global__ void mu_guess_kernel(long long N, const float *__restrict__ S, float *__restrict__ P, float ca, float cb)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = N >> 2;
+    const float4 *S4 = reinterpret_cast<const float4 *>(S);
+    float4 *P4 = reinterpret_cast<float4 *>(P);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const float4 sv = S4[q], pv = P4[q];
+        P4[q] = make_float4(ca * sv.x + cb * pv.x, ca * sv.y + cb * pv.y, ca * sv.z + cb * pv.z, ca * sv.w + cb * pv.w);
+    }
+    for (long long m = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += stride)
+        P[m] = ca * S[m] + cb * P[m];
+}
+
+cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, float b, cudaStream_t s)
+{
+    long long nb = ((N >> 2) + 255) / 256;
+    if (nb < 1) nb = 1;
+    if (nb > 4096) nb = 4096;
+    mu_guess_kernel<<<(int)nb, 256, 0, s>>>(N, S, P, a, b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s)
 {
     int kz = zchunk(a.g);
     dim3 block(kBX, kBY);
-    if (use_sweep2(a.g)) launch_sweep2<1>(a, kz, s);
-    else if (a.g.L) init_sweep_kernel<true><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
+    if (use_sweep2(a.g)) {
+        launch_sweep2<1>(a, kz, s);   // forms the Poisson guess too
+        return cudaGetLastError();
+    }
+    if (a.g.L) init_sweep_kernel<true><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
     else init_sweep_kernel<false><<<sweep_grid(a.g, kz), block, 0, s>>>(a, kz);
+    if (a.mu_guess) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_mu_guess(a.g.N, a.mu, a.mu_guess, a.ex_a, a.ex_b, s);
+    }
     return cudaGetLastError();
 }
 

@@ -189,7 +189,9 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
 
     auto knext = [&](int k) { return (k == g.nz - 1) ? (zper ? 0 : g.nz - 2) : k + 1; };
     float4 pzm = make_float4(0.f, 0.f, 0.f, 0.f), pc = pzm, pzp_n = pzm, b_n = pzm, D_n = pzm;
-    float2 mu_n = cmk(0.f, 0.f), al_n = mu_n;
+    float2 mu_n = cmk(0.f, 0.f), al_n = mu_n, pg_n = mu_n;
+    float2 *__restrict__ guess2 = reinterpret_cast<float2 *>(a.mu_guess);
+    const bool guess = INIT && guess2 != nullptr;
     const uchar2 *__restrict__ lk2 = reinterpret_cast<const uchar2 *>(g.lk);
     uchar2 lk_n = make_uchar2(0, 0);
     if (MASK && in) lk_n = ldx<CG>(lk2 + q0 + plq * k0);
@@ -200,6 +202,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
         if (INIT) {
             mu_n = ldx<CG>(mu2 + q0 + plq * k0);
             al_n = ldx<CG>(al2 + q0 + plq * k0);
+            if (guess) pg_n = ldx<CG>(guess2 + q0 + plq * k0);
         } else if (!RHS) {
             b_n = ldx<CG>(bq + q0 + plq * k0);
             D_n = ldx<CG>(Dq + q0 + plq * k0);
@@ -214,7 +217,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
     for (int k = k0; k < k1; ++k) {
         const float4 pzp = pzp_n;
         const float4 bc = b_n, Dc = D_n;
-        const float2 muc = mu_n, alc = al_n;
+        const float2 muc = mu_n, alc = al_n, pgc = pg_n;
         const uchar2 lkc = lk_n;
         const long long q = q0 + plq * k;
         float4 yf = make_float4(0.f, 0.f, 0.f, 0.f), yb = yf;
@@ -226,6 +229,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 if (INIT) {
                     mu_n = ldx<CG>(mu2 + q + plq);
                     al_n = ldx<CG>(al2 + q + plq);
+                    if (guess) pg_n = ldx<CG>(guess2 + q + plq);
                 } else if (!RHS) {
                     b_n = ldx<CG>(bq + q + plq);
                     D_n = ldx<CG>(Dq + q + plq);
@@ -410,6 +414,9 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 D1 = Do[1];
                 bout[q] = make_float4(b0.x, b0.y, b1.x, b1.y);
                 Dout[q] = make_float4(D0.x, D0.y, D1.x, D1.y);
+                // the coming Poisson solve starts from a mu^(n-1) + b mu^(n-2), written over the latter
+                if (guess)
+                    guess2[q] = make_float2(a.ex_a * muc.x + a.ex_b * pgc.x, a.ex_a * muc.y + a.ex_b * pgc.y);
             } else {
                 b0 = lo2(bc);
                 b1 = hi2(bc);

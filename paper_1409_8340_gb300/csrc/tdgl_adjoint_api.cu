@@ -2,6 +2,8 @@
 // and reverse steps (see k_adjoint.cu for the reverse-step equations).
 #include <string.h>
 
+#include <vector>
+
 #include "tdgl_internal.cuh"
 
 using namespace tdgl;
@@ -11,7 +13,7 @@ namespace {
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct AdjLayout {
-    size_t slot_psi, slot_bytes;
+    size_t slot_psi, slot_mu, slot_bytes;
     int nck, nseg;
     size_t ck, seg, fin, psibar, gv, lam0, lam1, mubar, au, ar, total;
 };
@@ -32,7 +34,9 @@ AdjLayout adj_layout(const tdgl_handle *h, const tdgl_adjoint_config *a)
     AdjLayout L;
     const size_t N = (size_t)h->g.N;
     L.slot_psi = al256(8 * N);
-    L.slot_bytes = L.slot_psi + al256(4 * N);
+    L.slot_mu = al256(4 * N);
+    // psi, mu and, where the Poisson guess is extrapolated, the previous step's mu
+    L.slot_bytes = L.slot_psi + L.slot_mu + (handle_extrapolates(h) ? al256(4 * N) : 0);
     L.nck = (a->n_steps + a->checkpoint_every - 1) / a->checkpoint_every;
     L.nseg = a->checkpoint_every + 1;
     size_t off = 0;
@@ -94,11 +98,27 @@ extern "C" int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, voi
     auto slot_mu = [&](size_t base, int q) {
         return reinterpret_cast<float *>(ws + base + L.slot_bytes * (size_t)q + L.slot_psi);
     };
+    // with the extrapolated Poisson guess a state also holds the previous step's mu (and
+    // whether there is one), so that a recomputed step repeats the forward one exactly
+    const bool ex = handle_extrapolates(h);
+    auto slot_mup = [&](size_t base, int q) {
+        return reinterpret_cast<float *>(ws + base + L.slot_bytes * (size_t)q + L.slot_psi + L.slot_mu);
+    };
+    std::vector<char> pv_ck((size_t)L.nck), pv_seg((size_t)L.nseg), pv_fin(1);
+    auto pv_of = [&](size_t base) -> std::vector<char> & {
+        return base == L.ck ? pv_ck : (base == L.seg ? pv_seg : pv_fin);
+    };
     auto save = [&](size_t base, int q) -> int {
         if (cudaMemcpyAsync(slot_psi(base, q), h->psi[h->cur], 8 * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return TDGL_ERR_CUDA;
         if (cudaMemcpyAsync(slot_mu(base, q), h->mu, 4 * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return TDGL_ERR_CUDA;
+        if (ex) {
+            if (cudaMemcpyAsync(slot_mup(base, q), h->mu_buf[1 - h->mu_q], 4 * N, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess)
+                return TDGL_ERR_CUDA;
+            pv_of(base)[(size_t)q] = (char)h->prev_valid;
+        }
         return TDGL_OK;
     };
     auto restore = [&](size_t base, int q) -> int {
@@ -106,6 +126,13 @@ extern "C" int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, voi
             return TDGL_ERR_CUDA;
         if (cudaMemcpyAsync(h->mu, slot_mu(base, q), 4 * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return TDGL_ERR_CUDA;
+        if (ex) {
+            if (cudaMemcpyAsync(h->mu_buf[1 - h->mu_q], slot_mup(base, q), 4 * N, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess)
+                return TDGL_ERR_CUDA;
+            h->prev_valid = pv_of(base)[(size_t)q];
+            h->guess_ready = 0;
+        }
         return TDGL_OK;
     };
     float2 *psibar = reinterpret_cast<float2 *>(ws + L.psibar);

@@ -11,6 +11,28 @@
 
 using namespace tdgl;
 
+namespace tdgl {
+
+// The Poisson solve starts from the extrapolated guess (tdgl_config.poisson_guess 0 or 2),
+// where the handle has the second mu buffer and solves mu itself
+bool handle_extrapolates(const tdgl_handle *h)
+{
+    const int gm = h->cfg.poisson_guess;
+    return h->mu_buf[1] != nullptr && !h->batch_owned && !h->cfg.freeze_mu_K && (gm == 0 || gm == 2);
+}
+
+// make mu_buf[q] the state: the finest multigrid level solves in it
+void use_mu_buffer(tdgl_handle *h, int q)
+{
+    h->mu_q = q;
+    h->mu = h->mu_buf[q];
+    h->pa.mu = h->pa.lev[0].u = h->mu;
+    h->pa.umap[0] = h->umap0[q];
+    h->pa.umap_u[0] = h->umap0_u[q];
+}
+
+}  // namespace tdgl
+
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -45,6 +67,7 @@ int validate(const tdgl_config *c)
     if (c->max_iter < 1 || c->check_every < 1 || c->fixed_sweeps < 0) return TDGL_ERR_INVALID_ARG;
     if (c->sweeps_per_pass < 0 || c->sweeps_per_pass > 2) return TDGL_ERR_INVALID_ARG;
     if (c->sweep_kernel < 0 || c->sweep_kernel > 2) return TDGL_ERR_INVALID_ARG;
+    if (c->poisson_guess < 0 || c->poisson_guess > 2) return TDGL_ERR_INVALID_ARG;
     if (!(c->noise_T >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->fixed_sweeps == 0 && !(c->eps > 0)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_cycles < 1 || c->poisson_max_cycles < c->poisson_cycles) return TDGL_ERR_INVALID_ARG;
@@ -77,7 +100,7 @@ int validate(const tdgl_config *c)
 }
 
 struct Layout {
-    size_t ctl, blockred, psi[3], b, D, mu, f, t, links, xzt, lk, insv, comp, isl, Uy, Uz, Py, Pz, total;
+    size_t ctl, blockred, psi[3], b, D, mu, mu2, f, t, links, xzt, lk, insv, comp, isl, Uy, Uz, Py, Pz, total;
     int nlevels;
     int ny[kMaxLevels], nz[kMaxLevels], fy[kMaxLevels], fz[kMaxLevels];
     size_t u[kMaxLevels], r[kMaxLevels], tri[kMaxLevels];
@@ -122,6 +145,9 @@ Layout layout(const tdgl_config *c)
     L.b = take(8 * (size_t)N);
     L.D = take(8 * (size_t)N);
     L.mu = take(4 * (size_t)N);
+    // the second mu buffer: the previous step's mu, over which the init writes the guess
+    // that the next Poisson solve starts from (multigrid solves only)
+    L.mu2 = c->d_insulating ? 0 : take(4 * (size_t)N);
     L.f = take(4 * (size_t)N);
     L.t = take(4 * (size_t)N);
     L.links = (c->links_mode != TDGL_LINKS_LANDAU) ? take(8 * 3 * (size_t)N) : 0;
@@ -237,6 +263,8 @@ SweepArgs sweep_args(tdgl_handle *h)
     a.extra_tx = h->dbg_extra_tx;
     return a;
 }
+
+bool extrapolating(const tdgl_handle *h) { return handle_extrapolates(h); }
 
 void ev_rec(tdgl_handle *h, int i)
 {
@@ -365,7 +393,10 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     h->cur = 0;
     h->b = at<float2>(ws, L.b);
     h->D = at<float2>(ws, L.D);
-    h->mu = at<float>(ws, L.mu);
+    h->mu_buf[0] = at<float>(ws, L.mu);
+    h->mu_buf[1] = c.d_insulating ? nullptr : at<float>(ws, L.mu2);
+    h->mu_q = 0;
+    h->mu = h->mu_buf[0];
     h->f = at<float>(ws, L.f);
     h->links = g.L ? at<float2>(ws, L.links) : nullptr;
     h->nblockred = L.nblockred;
@@ -475,6 +506,7 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     chk(cudaMemcpyAsync(h->ctl, &ctl0, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
     chk(cudaMemsetAsync(h->psi[0], 0, 8 * (size_t)N, s));
     chk(cudaMemsetAsync(h->mu, 0, 4 * (size_t)N, s));
+    if (h->mu_buf[1]) chk(cudaMemsetAsync(h->mu_buf[1], 0, 4 * (size_t)N, s));
     chk(cudaMemsetAsync(h->f, 0, 4 * (size_t)N, s));
     if (c.d_insulating && rc == TDGL_OK) {
         // link bits and conducting components; current injected through the x faces needs
@@ -567,8 +599,15 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
         // a synchronous wait keeps `tri` valid for the copy above
         chk(cudaStreamSynchronize(s));
     }
-    // tensor maps for the recursive smoother's row staging (none: per-lane copies)
-    mg_encode_line_maps(pa);
+    // tensor maps for the recursive smoother's row staging (none: per-lane copies), for
+    // each of the two mu buffers that the finest level can solve in
+    for (int q = 1; q >= 0; --q) {
+        if (!h->mu_buf[q]) continue;
+        pa.lev[0].u = pa.mu = h->mu_buf[q];
+        mg_encode_line_maps(pa);
+        h->umap0[q] = pa.umap[0];
+        h->umap0_u[q] = pa.umap_u[0];
+    }
     chk(cudaStreamSynchronize(s));
     if (rc != TDGL_OK) {
         delete h;
@@ -581,7 +620,7 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
 void tdgl_destroy(tdgl_handle *h)
 {
     if (!h) return;
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 6; ++q)
         if (h->pgraph[q]) cudaGraphExecDestroy(h->pgraph[q]);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->ev_made)
@@ -614,7 +653,7 @@ int tdgl_test_staged_waits(tdgl_handle *h, int64_t wait_ns, int32_t extra_tx_byt
     h->pa.wait_ns = h->dbg_wait_ns;
     h->pa.extra_tx = h->dbg_extra_tx;
     // the captured Poisson graphs hold the old kernel arguments: capture again on the next solve
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 6; ++q)
         if (h->pgraph[q]) {
             cudaGraphExecDestroy(h->pgraph[q]);
             h->pgraph[q] = nullptr;
@@ -647,6 +686,8 @@ int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double
     if (cudaMemcpyAsync(h->ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (launch_set_Ux(h->ctl, h->cfg.hx, s) != cudaSuccess) return TDGL_ERR_CUDA;
     h->mu_solved = 0;   // f no longer belongs to mu
+    h->prev_valid = 0;  // no mu of an earlier step to extrapolate from
+    h->guess_ready = 0;
     return cuda_err(cudaStreamSynchronize(s));
 }
 
@@ -665,7 +706,41 @@ int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_m
     if (cudaMemcpyAsync(h->ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (launch_set_Ux(h->ctl, h->cfg.hx, s) != cudaSuccess) return TDGL_ERR_CUDA;
     h->mu_solved = 0;   // f no longer belongs to mu
+    h->prev_valid = 0;  // no mu of an earlier step to extrapolate from
+    h->guess_ready = 0;
     return cuda_err(cudaStreamSynchronize(s));
+}
+
+int tdgl_get_mu_prev(tdgl_handle *h, float *out, int32_t out_on_host)
+{
+    if (!h || !out) return TDGL_ERR_INVALID_ARG;
+    if (!extrapolating(h) || !h->prev_valid) return 0;
+    cudaStream_t s = h->stream;
+    const size_t N = (size_t)h->g.N;
+    if (cudaMemcpyAsync(out, h->mu_buf[1 - h->mu_q], 4 * N, out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    return 1;
+}
+
+int tdgl_set_mu_prev(tdgl_handle *h, const float *in, int32_t in_on_host)
+{
+    if (!h) return TDGL_ERR_INVALID_ARG;
+    h->guess_ready = 0;
+    if (!in) {
+        h->prev_valid = 0;
+        return TDGL_OK;
+    }
+    if (!extrapolating(h)) return TDGL_ERR_INVALID_ARG;
+    cudaStream_t s = h->stream;
+    const size_t N = (size_t)h->g.N;
+    if (cudaMemcpyAsync(h->mu_buf[1 - h->mu_q], in, 4 * N, in_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->prev_valid = 1;
+    return TDGL_OK;
 }
 
 int tdgl_set_step(tdgl_handle *h, int64_t step)
@@ -717,8 +792,16 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     a.src = h->psi[h->cur];
     a.dst = h->psi[ia];
     a.dst_index = ia;
+    if (extrapolating(h)) {
+        // the init also writes the coming Poisson solve's guess over mu^(n-2)
+        a.mu_guess = h->mu_buf[1 - h->mu_q];
+        a.ex_a = h->prev_valid ? 2.f : 1.f;
+        a.ex_b = h->prev_valid ? -1.f : 0.f;
+        h->guess_ready = 1;
+    }
     ev_rec(h, 0);
     if (launch_init_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    a.mu_guess = nullptr;
     ev_rec(h, 1);
     h->prof.kernel_launches += 1;
     int launched = 1;   // sweeps enqueued (the init fuses the first)
@@ -863,7 +946,7 @@ static bool build_poisson_graph(tdgl_handle *h)
         cudaGetLastError();
         return false;
     }
-    h->pgraph[h->cur] = exec;
+    h->pgraph[h->cur + 3 * h->mu_q] = exec;
     h->pgraph_launches = nl;
     return true;
 }
@@ -874,12 +957,23 @@ int tdgl_solve_mu(tdgl_handle *h)
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     h->mu_solved = 1;
+    if (extrapolating(h) && h->guess_ready) {
+        // the step's init wrote the guess over the other mu buffer: solve there; the old
+        // state becomes the previous mu of the next extrapolation.  (A solve that no init
+        // prepared -- repeated solves of one right-hand side -- starts from the current mu
+        // in place: on a fixed right-hand side the extrapolation of two iterates would
+        // converge more slowly than the plain restart.)
+        use_mu_buffer(h, 1 - h->mu_q);
+        h->prev_valid = 1;
+    }
+    h->guess_ready = 0;
     // plain solve from the second call on: replay a captured graph (the first call runs the
     // launches directly, which also sets the kernels' one-time attributes outside a capture)
+    const int gk = h->cur + 3 * h->mu_q;
     if (!h->lk && c.poisson_tol <= 0 && !h->pgraph_fail && h->poisson_calls++ >= 1) {
-        if (!h->pgraph[h->cur] && !build_poisson_graph(h)) h->pgraph_fail = 1;
-        if (h->pgraph[h->cur]) {
-            if (cudaGraphLaunch(h->pgraph[h->cur], s) != cudaSuccess) return TDGL_ERR_CUDA;
+        if (!h->pgraph[gk] && !build_poisson_graph(h)) h->pgraph_fail = 1;
+        if (h->pgraph[gk]) {
+            if (cudaGraphLaunch(h->pgraph[gk], s) != cudaSuccess) return TDGL_ERR_CUDA;
             h->last_cycles = c.poisson_cycles;
             h->prof.vcycles += c.poisson_cycles;
             h->prof.kernel_launches += h->pgraph_launches;

@@ -26,6 +26,7 @@ int batch_check(const tdgl_config *c)
     if (c->links_mode != TDGL_LINKS_LANDAU || (c->nx % 2) != 0 || c->d_insulating) return TDGL_ERR_INVALID_ARG;
     if ((long long)c->nx * c->ny * c->nz >= (1LL << 31)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_tol > 0) return TDGL_ERR_INVALID_ARG;
+    if (c->poisson_guess == 2) return TDGL_ERR_INVALID_ARG;   // members start from the previous mu
     return TDGL_OK;
 }
 

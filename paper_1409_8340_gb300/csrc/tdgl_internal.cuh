@@ -215,9 +215,15 @@ struct SweepArgs {
     // use; > 0 makes every wait run out, for the timeout test)
     unsigned long long wait_ns;
     unsigned int extra_tx;
+    // init only: starting guess of the coming Poisson solve, written in place over the
+    // previous-but-one mu: mu_guess = ex_a mu + ex_b mu_guess (nullptr: none)
+    float *mu_guess;
+    float ex_a, ex_b;
 };
 
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
+// the guess of launch_init_sweep on its own: P = a S + b P over N sites
+cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, float b, cudaStream_t s);
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
 // one sweep src -> dst that neither tests nor touches the control block
 cudaError_t launch_sweep_redo(const SweepArgs &a, cudaStream_t s);
@@ -434,7 +440,16 @@ struct tdgl_handle {
     float2 *psi[3];
     int cur;
     float2 *b, *D;
-    float *mu, *f;
+    float *mu, *f;             // mu: the current state, mu_buf[mu_q]
+    // Poisson guess by extrapolation in time: the solve of a step runs in the other buffer,
+    // which the init has overwritten with 2 mu^(n-1) - mu^(n-2) (mu^(n-1) when prev_valid is
+    // 0), and then becomes the state; the old state is the next step's mu^(n-2)
+    float *mu_buf[2];
+    int mu_q;
+    int prev_valid;            // 1: mu_buf[1 - mu_q] holds the state of the step before
+    int guess_ready;           // 1: the init of this step has written the guess
+    CUtensorMap umap0[2];      // the finest level's smoother maps for each mu buffer
+    const float *umap0_u[2];
     float2 *links;
     tdgl::PoissonArgs pa;
     size_t nblockred;          // capacity of blockred (doubles)
@@ -454,7 +469,7 @@ struct tdgl_handle {
     // the Poisson solve of a step (right-hand side, V-cycles, projection) as CUDA graphs,
     // one per psi buffer, captured on a private stream and replayed on the handle's stream
     cudaStream_t cap_stream;
-    cudaGraphExec_t pgraph[3];
+    cudaGraphExec_t pgraph[6];   // per psi buffer (3) and mu buffer (2)
     int pgraph_fail;
     int poisson_calls;
     long long pgraph_launches;
@@ -468,3 +483,8 @@ struct tdgl_handle {
     bool pend_K, pend_P, pend_R;   // K / Poisson / recomputed-sweep event pairs recorded but not yet read
     tdgl_profile prof;
 };
+
+namespace tdgl {
+bool handle_extrapolates(const tdgl_handle *h);
+void use_mu_buffer(tdgl_handle *h, int q);
+}  // namespace tdgl

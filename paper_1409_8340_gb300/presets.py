@@ -54,7 +54,8 @@ MESOSCOPIC_CURRENTS = tuple(0.005 * n for n in range(11))
 
 def ensemble_member(m: inputs.EnsembleMember) -> Workload:
     nx, ny, nz = m.shape
-    p = Params(nx, ny, nz, bc=(OPEN, PERIODIC, PERIODIC), Bz=m.Bz, Jext=m.Jext, eps=1e-6, ht=0.1)
+    # members of a batch start each Poisson solve from the previous mu: two V-cycles
+    p = Params(nx, ny, nz, bc=(OPEN, PERIODIC, PERIODIC), Bz=m.Bz, Jext=m.Jext, eps=1e-6, ht=0.1, poisson_cycles=2)
     cand = inputs.spheres(800, (p.length(0), p.length(1), p.length(2)), 2.0, 4.0, seed=m.seed)
     return Workload(f"ensemble_member_{nx}x{ny}x{nz}", p, m.seed, 1000, cand, inputs.target_sites(m.fraction, p.N),
                     alpha_in=-m.alpha_scale, alpha_out=m.alpha_scale)
@@ -65,6 +66,6 @@ def ensemble_64(seed: int = 4) -> list[Workload]:
 
 
 def adjoint_64x64x32() -> Workload:
-    p = Params(64, 64, 32, bc=(OPEN, PERIODIC, PERIODIC), Bz=0.1, Jext=0.01, eps=1e-6, ht=0.1)
+    p = Params(64, 64, 32, bc=(OPEN, PERIODIC, PERIODIC), Bz=0.1, Jext=0.01, eps=1e-6, ht=0.1, poisson_cycles=2)
     field = inputs.smoothed_field(64, 64, 32, seed=5, sigma_sites=4.0).astype(np.float32)
     return Workload("adjoint_64x64x32", p, 5, 400, None, 0, alpha_field=field)

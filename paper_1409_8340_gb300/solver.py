@@ -39,9 +39,10 @@ class Params:
     check_every: int = 1
     fixed_sweeps: int = 0
     freeze_mu_K: bool = False
-    poisson_cycles: int = 2
+    poisson_cycles: int = 1
     poisson_max_cycles: int = 50
     poisson_tol: float = 0.0
+    poisson_guess: int = 0         # 1 previous mu, 2 linear extrapolation in time, 0 default (2; batches 1)
     general_links: bool = False
     xz_gauge: bool = False         # field (Bx, 0, Bz) in the Landau gauge of Eq. A_xz (By must be 0)
     Bx: float = 0.0
@@ -88,6 +89,7 @@ class Params:
         c.Bx = float(self.Bx)
         c.sweeps_per_pass = int(self.sweeps_per_pass)
         c.sweep_kernel = int(self.sweep_kernel)
+        c.poisson_guess = int(self.poisson_guess)
         c.noise_T = float(self.noise_T)
         c.noise_seed = int(self.noise_seed) & 0xFFFFFFFFFFFFFFFF
         c.d_alpha = d_alpha
@@ -214,14 +216,24 @@ class Solver:
         check(self._L.tdgl_set_step(self._h, int(n)), "tdgl_set_step")
 
     def checkpoint(self) -> dict:
-        """The resumable state in host memory: psi, mu, K and the step index (which is
-        also the counter of the thermal noise)."""
+        """The resumable state in host memory: psi, mu, K, the previous step's mu (read by
+        the extrapolated Poisson guess; None when the handle holds none) and the step index
+        (which is also the counter of the thermal noise)."""
         psi, mu, K = self.download_state()
-        return {"psi": psi, "mu": mu, "K": K, "step": int(self.observables()["step"])}
+        prev = torch.empty(self.p.shape, dtype=torch.float32)
+        rc = self._L.tdgl_get_mu_prev(self._h, ctypes.c_void_p(prev.data_ptr()), 1)
+        if rc < 0:
+            check(rc, "tdgl_get_mu_prev")
+        return {"psi": psi, "mu": mu, "K": K, "mu_prev": prev if rc == 1 else None,
+                "step": int(self.observables()["step"])}
 
     def restore(self, ck: dict):
         """Load a checkpoint(): the run continues exactly as it would have, noise included."""
         self.upload_state(ck["psi"], ck["mu"], ck["K"])
+        prev = ck.get("mu_prev")
+        if prev is not None:
+            prev = torch.as_tensor(prev).to(torch.float32).contiguous()
+            check(self._L.tdgl_set_mu_prev(self._h, ctypes.c_void_p(prev.data_ptr()), 1), "tdgl_set_mu_prev")
         self.set_step(ck["step"])
 
     def step(self, n: int = 1):

@@ -1,8 +1,9 @@
 """Parity of the configuration the benchmark times: the library defaults.
 
-Defaults: eps = 1e-6, poisson_cycles = 2 and poisson_tol = 0 (two multigrid V-cycles
-per step, warm-started from the previous mu, with no residual test), and the Poisson
-solve replayed from a CUDA graph from the second step on.  The case is an open-x
+Defaults: eps = 1e-6, poisson_cycles = 1, poisson_tol = 0 and poisson_guess = 0 (one
+multigrid V-cycle per step with no residual test, started from the linear extrapolation
+in time 2 mu^(n-1) - mu^(n-2) that the step's init writes), and the Poisson solve
+replayed from a CUDA graph from the second step on.  The case is an open-x
 flux-flow sample with 512-site x lines, so that the staged sweep, the staged
 right-hand side and both variants of the recursive line smoother run: 512 x 64 x 32,
 with the field, current and inclusion recipe of the 512 x 512 x 256 workload (Bz = 0.2,
@@ -47,7 +48,8 @@ def test_defaults_are_the_benchmark_configuration():
     from paper_1409_8340_gb300.presets import mesoscopic_512x512x256
     from paper_1409_8340_gb300.solver import Params
     p, d = mesoscopic_512x512x256(0.025).params, Params(8, 8, 8)
-    assert (p.poisson_cycles, p.poisson_tol, p.eps) == (d.poisson_cycles, d.poisson_tol, d.eps) == (2, 0.0, 1e-6)
+    assert (p.poisson_cycles, p.poisson_tol, p.eps) == (d.poisson_cycles, d.poisson_tol, d.eps) == (1, 0.0, 1e-6)
+    assert p.poisson_guess == d.poisson_guess == 0
     assert (p.sweep_kernel, p.sweeps_per_pass, p.check_every, p.fixed_sweeps) == (0, 1, 1, 0)
 
 
@@ -75,7 +77,7 @@ def test_default_poisson_solve_per_step(O):
         ex_ex = O.voltage_open_x(G, mu_ex)
         assert abs(o["Ex"] - ex_ex) <= EX_REL * abs(ex_ex), (n, o["Ex"], ex_ex)
         assert 0.0 < o["poisson_res"] < 1e-2, o["poisson_res"]
-        assert o["poisson_cycles"] == 2
+        assert o["poisson_cycles"] == 1
     assert worst < 1.0
 
 

@@ -80,9 +80,10 @@ def test_c3_converged_step_residual_and_potential(O, c3):
     obs = s.observables()
     assert 1 <= obs["last_sweeps"] <= 60
     assert math.isfinite(obs["Ex"])
-    # the step ran two V-cycles from mu = 0; four more solves of the same right-hand
-    # side (8 more V-cycles, warm-started) take the multigrid to its FP32 floor
-    for _ in range(4):
+    # the step ran p.poisson_cycles V-cycles from mu = 0; more solves of the same right-hand
+    # side (10 V-cycles in all, each solve warm-started from the last) take the multigrid to
+    # its FP32 floor
+    for _ in range(-(-(10 - p.poisson_cycles) // p.poisson_cycles)):
         s.solve_mu()
     _, mu_g = gpu_state(s)
     f = s.internals()[2].cpu().numpy().astype(np.float64)

@@ -202,8 +202,11 @@ def test_staged_poisson_timeout_is_reported_and_handle_recovers(O):
     with pytest.raises(TdglError) as e:
         s.step(1)
     assert e.value.code == TDGL_ERR_TIMEOUT
-    s.set_state(torch.as_tensor(psi1.astype(np.complex64)), torch.as_tensor(mu1.astype(np.float32)),
-                ref.observables()["K"])
+    # both handles load the same state (which also drops the previous mu that the
+    # extrapolated Poisson guess reads), then step alike
+    K1 = ref.observables()["K"]
+    for h in (s, ref):
+        h.set_state(torch.as_tensor(psi1.astype(np.complex64)), torch.as_tensor(mu1.astype(np.float32)), K1)
     s.step(2)
     ref.step(2)
     a, b = gpu_state(s), gpu_state(ref)

@@ -92,7 +92,7 @@ def test_batch_with_noise_matches_plain_handles():
     b = Batch(ps, [torch.as_tensor(a).cuda() for a in alphas])
     for i, s in enumerate(b.instances):
         s.set_state(torch.as_tensor(psi0s[i]))
-    plain = [make_solver(p, a, x) for p, a, x in zip(ps, alphas, psi0s)]
+    plain = [make_solver(dataclasses.replace(p, poisson_guess=1), a, x) for p, a, x in zip(ps, alphas, psi0s)]
     b.step(4)
     b.check()
     for i, s in enumerate(plain):
@@ -111,9 +111,10 @@ def test_adjoint_refuses_noise():
 
 @pytest.mark.parametrize("noise_T", [0.0, 0.004], ids=["no_noise", "noise"])
 def test_checkpoint_resume_is_bitwise_continuous(noise_T):
-    """100 straight steps equal 50 steps, a checkpoint to host memory (psi, mu, K and the
-    step index, which is the noise counter), a fresh handle restored from it, and 50 more
-    steps: bit for bit, with and without thermal noise."""
+    """100 straight steps equal 50 steps, a checkpoint to host memory (psi, mu, K, the
+    previous step's mu that the extrapolated Poisson guess reads, and the step index,
+    which is the noise counter), a fresh handle restored from it, and 50 more steps:
+    bit for bit, with and without thermal noise."""
     from paper_1409_8340_gb300.solver import Params
     p = Params(64, 24, 12, bc=(OP, P, P), Bz=0.2, Jext=0.02, noise_T=noise_T, noise_seed=91)
     alpha = inclusion_alpha(p, 92)
@@ -123,7 +124,7 @@ def test_checkpoint_resume_is_bitwise_continuous(noise_T):
     b = make_solver(p, alpha, psi0)
     b.step(50)
     ck = b.checkpoint()
-    assert ck["step"] == 50
+    assert ck["step"] == 50 and ck["mu_prev"] is not None
     b.close()
     c = make_solver(p, alpha)
     c.restore(ck)
