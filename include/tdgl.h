@@ -109,8 +109,7 @@ extern "C" {
  *   poisson_guess   starting guess of each Poisson solve: 1 the previous step's mu;
  *                   2 its linear extrapolation in time, 2 mu^(n-1) - mu^(n-2) (the
  *                   previous mu on the first step after creation or a state load);
- *                   0 the default, which is 2 for a single handle and 1 for the
- *                   members of a batch (which refuse 2).  With insulating sites, and
+ *                   0 the default, which is 2.  With insulating sites, and
  *                   for tdgl_solve_mu called on its own (not after the psi solve of
  *                   a step), the guess is the current mu.  The solution the solve
  *                   converges to does not depend on it; with a fixed number of
@@ -253,7 +252,9 @@ int tdgl_set_step(tdgl_handle *h, int64_t step);
  * memory if out_on_host, else device memory) and returns 1, or returns 0 when the
  * handle holds none (after creation or a state load, or without the extrapolated
  * guess).  tdgl_set_mu_prev copies one in (NULL: none); it is refused without the
- * extrapolated guess.  A state load clears it, so load the state first.
+ * extrapolated guess.  A state load clears it, so load the state first.  (Single
+ * handles only: a batch member keeps its previous mu inside the batch, and a state
+ * load clears it.)
  *
  * Checkpoints: psi, mu and K (tdgl_download_state), the previous mu and the step
  * index, restored by a state load, tdgl_set_mu_prev and tdgl_set_step, continue the

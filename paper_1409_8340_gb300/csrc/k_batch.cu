@@ -208,6 +208,14 @@ __device__ void stage(const BatchParams &P, BatchSmem &S, int m, int op, int l, 
             a.src = S.H.psi[S.H.iS];
             a.dst = S.H.psi[S.H.iA];
             a.dst_index = S.H.iA;
+            if (S.H.mu_solve != a.mu) {
+                // the init writes the Poisson guess 2 mu^(n-1) - mu^(n-2) (mu^(n-1) on the
+                // first step after a state load) over the previous mu in the solve buffer
+                const bool prev = ldx<true>(&a.ctl->mu_prev_ok) != 0;
+                a.mu_guess = S.H.mu_solve;
+                a.ex_a = prev ? 2.f : 1.f;
+                a.ex_b = prev ? -1.f : 0.f;
+            }
         } else if (op == OP_SWEEP) {
             // sweep p reads the output of sweep p-1: odd p A -> B, even p B -> A
             const int ia = parity ? S.H.iA : S.H.iB, ib = parity ? S.H.iB : S.H.iA;
@@ -389,7 +397,7 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
     case OP_MEAN: {
         // sum w mu (zero mode) and the x-face difference of mu (open-x voltage)
         const DevGrid &g = H.a.g;
-        const float *mu = H.a.mu;
+        const float *mu = H.mu_solve;
         const unsigned int m0 = (unsigned int)li * (unsigned int)H.red_chunk;
         const unsigned int m1 = (unsigned int)min((long long)m0 + H.red_chunk, g.N);
         const bool ox = g.bcx == kOpen, oy = g.bcy == kOpen, oz = g.bcz == kOpen && g.nz >= 2;
@@ -457,6 +465,8 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
             c->ticket = 0u;
             if (!H.freeze) c->mu_mean = t0 / H.a.wsum;
             if (H.open_x) c->Ex = t1 / (double)((long long)g.ny * g.nz) / ((g.nx - 1) * H.hx);
+            // after the shift the solve buffer holds this step's starting mu
+            if (!H.freeze && H.mu_solve != H.a.mu) c->mu_prev_ok = 1;
         }
         break;
     }
@@ -465,6 +475,25 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         float *mu = const_cast<float *>(H.a.mu);
         const long long m0 = (long long)li * H.red_chunk;
         const long long m1 = min(m0 + H.red_chunk, H.a.g.N);
+        if (H.mu_solve != H.a.mu) {
+            // state <- solution - mean; the solve buffer keeps the old state (mu^(n-1)) for
+            // the next step's extrapolation
+            float *sv = H.mu_solve;
+            if ((H.a.g.N & 3) == 0) {
+                for (long long q = m0 + 4 * tid; q < m1; q += 4 * kBT) {
+                    const float4 v = ld4<true>(sv + q), o = ld4<true>(mu + q);
+                    *reinterpret_cast<float4 *>(mu + q) = make_float4(v.x - c, v.y - c, v.z - c, v.w - c);
+                    *reinterpret_cast<float4 *>(sv + q) = o;
+                }
+            } else {
+                for (long long q = m0 + tid; q < m1; q += kBT) {
+                    const float v = ldx<true>(sv + q), o = ldx<true>(mu + q);
+                    mu[q] = v - c;
+                    sv[q] = o;
+                }
+            }
+            break;
+        }
         if ((H.a.g.N & 3) == 0) {
             for (long long q = m0 + 4 * tid; q < m1; q += 4 * kBT) {
                 const float4 v = ld4<true>(mu + q);

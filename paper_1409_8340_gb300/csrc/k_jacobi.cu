@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kBX *kBY) init_sweep_kernel(SweepArgs a, int k
             }
             float2 ns = cadd(ns_xy<GEN>(g, a.src, i, j, k, m, Ux), ns_z<GEN>(g, i, k, m, pzm, pzp));
             const float a2 = cabs2(pc);
-            const float mu = a.mu[m], al = a.alpha[m];
+            const float mu = a.mu[m] - (a.mu_off ? (float)*a.mu_off : 0.f), al = a.alpha[m];
             const float2 D = cmk(1.f + g.ht2 * (g.beta * a2 + 2.f * g.S - al), g.ht2 * g.u * mu);
             // b = p + (ht/2)[(alpha - i u mu) p - beta|p|^2 p + NS - 2 S p]
             const float cr = al - g.beta * a2 - 2.f * g.S;
@@ -331,27 +331,31 @@ static void launch_sweep2(const SweepArgs &a, int kz, cudaStream_t s)
     else sweep2_kernel<MODE, false, false><<<grid, block, 0, s>>>(a, kz);
 }
 
-// P = a S + b P, four sites per thread where the arrays allow 16-byte access
-__global__ void mu_guess_kernel(long long N, const float *__restrict__ S, float *__restrict__ P, float ca, float cb)
+// P = a (S - offS) + b (P - offP), four sites per thread where the arrays allow 16-byte access
+__global__ void mu_guess_kernel(long long N, const float *__restrict__ S, float *__restrict__ P, float ca, float cb,
+                                const double *offS, const double *offP)
 {
+    const float os = offS ? (float)*offS : 0.f, op = offP ? (float)*offP : 0.f;
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n4 = N >> 2;
     const float4 *S4 = reinterpret_cast<const float4 *>(S);
     float4 *P4 = reinterpret_cast<float4 *>(P);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += stride) {
         const float4 sv = S4[q], pv = P4[q];
-        P4[q] = make_float4(ca * sv.x + cb * pv.x, ca * sv.y + cb * pv.y, ca * sv.z + cb * pv.z, ca * sv.w + cb * pv.w);
+        P4[q] = make_float4(ca * (sv.x - os) + cb * (pv.x - op), ca * (sv.y - os) + cb * (pv.y - op),
+                            ca * (sv.z - os) + cb * (pv.z - op), ca * (sv.w - os) + cb * (pv.w - op));
     }
     for (long long m = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += stride)
-        P[m] = ca * S[m] + cb * P[m];
+        P[m] = ca * (S[m] - os) + cb * (P[m] - op);
 }
 
-cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, float b, cudaStream_t s)
+cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, float b, const double *offS,
+                            const double *offP, cudaStream_t s)
 {
     long long nb = ((N >> 2) + 255) / 256;
     if (nb < 1) nb = 1;
     if (nb > 4096) nb = 4096;
-    mu_guess_kernel<<<(int)nb, 256, 0, s>>>(N, S, P, a, b);
+    mu_guess_kernel<<<(int)nb, 256, 0, s>>>(N, S, P, a, b, offS, offP);
     return cudaGetLastError();
 }
 
@@ -368,7 +372,7 @@ cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s)
     if (a.mu_guess) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return launch_mu_guess(a.g.N, a.mu, a.mu_guess, a.ex_a, a.ex_b, s);
+        return launch_mu_guess(a.g.N, a.mu, a.mu_guess, a.ex_a, a.ex_b, a.mu_off, a.mu_off_prev, s);
     }
     return cudaGetLastError();
 }

@@ -1300,9 +1300,12 @@ __global__ void __launch_bounds__(kGX) mu_mean_kernel(DevGrid g, const float *mu
 }
 
 // mu -= mean, four sites per thread per pass, loads of a pass before its stores
-__global__ void mu_shift_kernel(long long N, float *mu, const DevCtl *ctl)
+// mu -= c with c the weighted mean (from_off: the pending mean mu_off[q] instead); thread 0
+// clears mu_off[q] (zero_q >= 0), which no thread of this launch reads unless from_off
+__global__ void mu_shift_kernel(long long N, float *mu, DevCtl *ctl, int zero_q, int from_off)
 {
-    const float c = (float)ctl->mu_mean;
+    const float c = (float)(from_off ? ctl->mu_off[zero_q] : ctl->mu_mean);
+    if (!from_off && zero_q >= 0 && blockIdx.x == 0 && threadIdx.x == 0) ctl->mu_off[zero_q] = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long m0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; m0 < N; m0 += 4 * stride) {
         float v[4];
@@ -1318,8 +1321,25 @@ __global__ void mu_shift_kernel(long long N, float *mu, const DevCtl *ctl)
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s, bool mean_done)
 {
     if (!mean_done) mu_mean_kernel<<<grid_xy(a.g.nx, a.g.ny), kGX, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum);
-    mu_shift_kernel<<<grid_blocks(a.g.N, 8), kThreads, 0, s>>>(a.g.N, a.mu, a.ctl);
+    mu_shift_kernel<<<grid_blocks(a.g.N, 8), kThreads, 0, s>>>(a.g.N, a.mu, a.ctl, a.mu_q, 0);
     return cudaGetLastError();
+}
+
+__global__ void commit_mean_kernel(DevCtl *ctl, int q) { ctl->mu_off[q] = ctl->mu_mean; }
+
+cudaError_t launch_commit_mean(const PoissonArgs &a, cudaStream_t s)
+{
+    if (a.mu_q < 0) return cudaErrorInvalidValue;
+    commit_mean_kernel<<<1, 1, 0, s>>>(a.ctl, a.mu_q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_materialize(long long N, float *mu, DevCtl *ctl, int q, cudaStream_t s)
+{
+    mu_shift_kernel<<<grid_blocks(N, 8), kThreads, 0, s>>>(N, mu, ctl, q, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(&ctl->mu_off[q], 0, sizeof(double), s);
 }
 
 // ---------------------------------------------------------------------------

@@ -192,6 +192,9 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
     float2 mu_n = cmk(0.f, 0.f), al_n = mu_n, pg_n = mu_n;
     float2 *__restrict__ guess2 = reinterpret_cast<float2 *>(a.mu_guess);
     const bool guess = INIT && guess2 != nullptr;
+    // pending means of mu and of the previous-but-one mu (the zero-mode projection)
+    const float offS = (INIT && a.mu_off) ? (float)ldx<CG>(a.mu_off) : 0.f;
+    const float offP = (INIT && a.mu_off_prev) ? (float)ldx<CG>(a.mu_off_prev) : 0.f;
     const uchar2 *__restrict__ lk2 = reinterpret_cast<const uchar2 *>(g.lk);
     uchar2 lk_n = make_uchar2(0, 0);
     if (MASK && in) lk_n = ldx<CG>(lk2 + q0 + plq * k0);
@@ -217,7 +220,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
     for (int k = k0; k < k1; ++k) {
         const float4 pzp = pzp_n;
         const float4 bc = b_n, Dc = D_n;
-        const float2 muc = mu_n, alc = al_n, pgc = pg_n;
+        const float2 muc = make_float2(mu_n.x - offS, mu_n.y - offS), alc = al_n, pgc = pg_n;
         const uchar2 lkc = lk_n;
         const long long q = q0 + plq * k;
         float4 yf = make_float4(0.f, 0.f, 0.f, 0.f), yb = yf;
@@ -416,7 +419,8 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 Dout[q] = make_float4(D0.x, D0.y, D1.x, D1.y);
                 // the coming Poisson solve starts from a mu^(n-1) + b mu^(n-2), written over the latter
                 if (guess)
-                    guess2[q] = make_float2(a.ex_a * muc.x + a.ex_b * pgc.x, a.ex_a * muc.y + a.ex_b * pgc.y);
+                    guess2[q] = make_float2(a.ex_a * muc.x + a.ex_b * (pgc.x - offP),
+                                            a.ex_a * muc.y + a.ex_b * (pgc.y - offP));
             } else {
                 b0 = lo2(bc);
                 b1 = hi2(bc);

@@ -86,6 +86,19 @@ extern "C" int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, voi
     if (rc != TDGL_OK) return rc;
     // the reverse pass assumes a deterministic forward without noise
     if (!d_grad_alpha || h->batch_owned || h->noise_amp != 0.f) return TDGL_ERR_INVALID_ARG;
+    // every stored state holds its own projected mu: apply the pending projections now and
+    // project at once inside (the captured Poisson graphs are recaptured either way)
+    if ((rc = mu_materialize(h, 0)) != TDGL_OK || (rc = mu_materialize(h, 1)) != TDGL_OK) return rc;
+    drop_poisson_graphs(h);
+    h->in_adjoint = 1;
+    struct Leave {
+        tdgl_handle *h;
+        ~Leave()
+        {
+            h->in_adjoint = 0;
+            drop_poisson_graphs(h);
+        }
+    } leave{h};
     const tdgl_adjoint_config &A = *acfg;
     const AdjLayout L = adj_layout(h, acfg);
     if (!d_ws || ((uintptr_t)d_ws & 255u) || ws_bytes < L.total) return TDGL_ERR_WORKSPACE;
@@ -180,11 +193,37 @@ extern "C" int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, voi
         return fail(TDGL_ERR_CUDA);
     const float vsrc = (float)(1.0 / ((double)nwin * g.ny * g.nz * (g.nx - 1) * h->cfg.hx));
     PoissonArgs pa = h->pa;
+    pa.mu_q = -1;   // not one of the handle's mu buffers
     pa.lev[0].u = au;
     pa.lev[0].r = ar;
     pa.mu = au;
     pa.f = ar;
     const float2 Ux0 = make_float2(1.f, 0.f);   // open x: K = 0
+    // the fixed adjoint Poisson sequence (right-hand side, V-cycles, projection) on stream q
+    auto adj_poisson_fixed = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = launch_adj_rhs(g, mubar, ar, h->ctl, h->blockred, h->wsum, q);
+        long long nl = 0;
+        for (int c = 0; c < A.poisson_cycles && e == cudaSuccess; ++c) e = launch_vcycle(pa, q, &nl);
+        if (e == cudaSuccess) e = launch_project_mu(pa, q);
+        return e;
+    };
+    cudaGraphExec_t rgraph = nullptr;
+    bool graph_fail = false;
+    long long rev_solves = 0;
+    cudaStream_t cap = nullptr;
+    if (A.poisson_tol <= 0 && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cap = nullptr;
+        graph_fail = true;
+    }
+    struct GraphGuard {
+        cudaGraphExec_t *g;
+        cudaStream_t *c;
+        ~GraphGuard()
+        {
+            if (*g) cudaGraphExecDestroy(*g);
+            if (*c) cudaStreamDestroy(*c);
+        }
+    } graph_guard{&rgraph, &cap};
     for (int c = L.nck - 1; c >= 0; --c) {
         const int s0 = c * C, s1 = (s0 + C < T) ? s0 + C : T;
         cudaEventRecord(e0, s);
@@ -202,23 +241,45 @@ extern "C" int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, voi
             const float *mu_p = slot_mu(L.seg, n - 1 - s0);
             if (n > A.window_start && launch_adj_voltage_source(g, mubar, vsrc, s) != cudaSuccess)
                 return fail(TDGL_ERR_CUDA);
-            // adjoint Poisson: w = W * G(mubar / W)
-            if (launch_adj_rhs(g, mubar, ar, h->ctl, h->blockred, h->wsum, s) != cudaSuccess) return fail(TDGL_ERR_CUDA);
-            long long nl = 0;
-            int cycles = 0;
-            for (; cycles < A.poisson_cycles; ++cycles)
-                if (launch_vcycle(pa, s, &nl) != cudaSuccess) return fail(TDGL_ERR_CUDA);
-            if (A.poisson_tol > 0) {
-                for (;;) {
-                    if (launch_poisson_residual(pa, s) != cudaSuccess) return fail(TDGL_ERR_CUDA);
-                    DevCtl cc;
-                    if ((rc = sync_ctl(h, &cc)) != TDGL_OK) return fail(rc);
-                    if (cc.res <= A.poisson_tol || cycles >= h->cfg.poisson_max_cycles) break;
-                    if (launch_vcycle(pa, s, &nl) != cudaSuccess) return fail(TDGL_ERR_CUDA);
-                    ++cycles;
+            // adjoint Poisson: w = W * G(mubar / W); with a fixed number of V-cycles the whole
+            // sequence is replayed from a graph from the second reverse step on (the first runs
+            // the launches directly, which also sets the kernels' one-time attributes)
+            const bool replay = A.poisson_tol <= 0 && !graph_fail && rev_solves++ > 0;
+            if (replay) {
+                if (!rgraph) {
+                    cudaGraph_t gr = nullptr;
+                    cudaError_t e1 = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                    cudaError_t e2 = (e1 == cudaSuccess) ? adj_poisson_fixed(cap) : e1;
+                    cudaError_t e3 = (e1 == cudaSuccess) ? cudaStreamEndCapture(cap, &gr) : e1;
+                    if (e2 != cudaSuccess || e3 != cudaSuccess || !gr ||
+                        cudaGraphInstantiate(&rgraph, gr, 0) != cudaSuccess) {
+                        rgraph = nullptr;
+                        graph_fail = true;
+                        cudaGetLastError();
+                    }
+                    if (gr) cudaGraphDestroy(gr);
                 }
+                if (rgraph && cudaGraphLaunch(rgraph, s) != cudaSuccess) return fail(TDGL_ERR_CUDA);
             }
-            if (launch_project_mu(pa, s) != cudaSuccess) return fail(TDGL_ERR_CUDA);
+            if (!replay || graph_fail) {
+                if (launch_adj_rhs(g, mubar, ar, h->ctl, h->blockred, h->wsum, s) != cudaSuccess)
+                    return fail(TDGL_ERR_CUDA);
+                long long nl = 0;
+                int cycles = 0;
+                for (; cycles < A.poisson_cycles; ++cycles)
+                    if (launch_vcycle(pa, s, &nl) != cudaSuccess) return fail(TDGL_ERR_CUDA);
+                if (A.poisson_tol > 0) {
+                    for (;;) {
+                        if (launch_poisson_residual(pa, s) != cudaSuccess) return fail(TDGL_ERR_CUDA);
+                        DevCtl cc;
+                        if ((rc = sync_ctl(h, &cc)) != TDGL_OK) return fail(rc);
+                        if (cc.res <= A.poisson_tol || cycles >= h->cfg.poisson_max_cycles) break;
+                        if (launch_vcycle(pa, s, &nl) != cudaSuccess) return fail(TDGL_ERR_CUDA);
+                        ++cycles;
+                    }
+                }
+                if (launch_project_mu(pa, s) != cudaSuccess) return fail(TDGL_ERR_CUDA);
+            }
             // g = psibar + i [NS^H(w psi^n) - w NS(psi^n)]
             if (launch_adj_fterm(g, Ux0, psi_n, au, psibar, gv, s) != cudaSuccess) return fail(TDGL_ERR_CUDA);
             // M^H lam = g

@@ -27,8 +27,26 @@ void use_mu_buffer(tdgl_handle *h, int q)
     h->mu_q = q;
     h->mu = h->mu_buf[q];
     h->pa.mu = h->pa.lev[0].u = h->mu;
+    h->pa.mu_q = q;
     h->pa.umap[0] = h->umap0[q];
     h->pa.umap_u[0] = h->umap0_u[q];
+}
+
+// Apply the pending zero-mode projection of mu buffer q (a fixed-cycle solve leaves it in
+// ctl->mu_off[q]; nothing to do without one)
+int mu_materialize(tdgl_handle *h, int q)
+{
+    if (h->lk || h->batch_owned || !h->mu_buf[q]) return TDGL_OK;
+    return launch_mu_materialize(h->g.N, h->mu_buf[q], h->ctl, q, h->stream) == cudaSuccess ? TDGL_OK : TDGL_ERR_CUDA;
+}
+
+void drop_poisson_graphs(tdgl_handle *h)
+{
+    for (int q = 0; q < 6; ++q)
+        if (h->pgraph[q]) {
+            cudaGraphExecDestroy(h->pgraph[q]);
+            h->pgraph[q] = nullptr;
+        }
 }
 
 }  // namespace tdgl
@@ -653,11 +671,7 @@ int tdgl_test_staged_waits(tdgl_handle *h, int64_t wait_ns, int32_t extra_tx_byt
     h->pa.wait_ns = h->dbg_wait_ns;
     h->pa.extra_tx = h->dbg_extra_tx;
     // the captured Poisson graphs hold the old kernel arguments: capture again on the next solve
-    for (int q = 0; q < 6; ++q)
-        if (h->pgraph[q]) {
-            cudaGraphExecDestroy(h->pgraph[q]);
-            h->pgraph[q] = nullptr;
-        }
+    drop_poisson_graphs(h);
     return TDGL_OK;
 }
 
@@ -717,6 +731,7 @@ int tdgl_get_mu_prev(tdgl_handle *h, float *out, int32_t out_on_host)
     if (!extrapolating(h) || !h->prev_valid) return 0;
     cudaStream_t s = h->stream;
     const size_t N = (size_t)h->g.N;
+    if (mu_materialize(h, 1 - h->mu_q) != TDGL_OK) return TDGL_ERR_CUDA;
     if (cudaMemcpyAsync(out, h->mu_buf[1 - h->mu_q], 4 * N, out_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
         return TDGL_ERR_CUDA;
@@ -738,6 +753,7 @@ int tdgl_set_mu_prev(tdgl_handle *h, const float *in, int32_t in_on_host)
     if (cudaMemcpyAsync(h->mu_buf[1 - h->mu_q], in, 4 * N, in_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
         return TDGL_ERR_CUDA;
+    if (cudaMemsetAsync(&h->ctl->mu_off[1 - h->mu_q], 0, sizeof(double), s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
     h->prev_valid = 1;
     return TDGL_OK;
@@ -759,6 +775,7 @@ int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double 
     if (!h) return TDGL_ERR_INVALID_ARG;
     const size_t N = (size_t)h->g.N;
     cudaStream_t s = h->stream;
+    if (mu_materialize(h, h->mu_q) != TDGL_OK) return TDGL_ERR_CUDA;
     if (host_psi && cudaMemcpyAsync(host_psi, h->psi[h->cur], 8 * N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TDGL_ERR_CUDA;
     if (host_mu && cudaMemcpyAsync(host_mu, h->mu, 4 * N, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
@@ -772,6 +789,7 @@ int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double 
 int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out)
 {
     if (!h || !out) return TDGL_ERR_INVALID_ARG;
+    if (mu_materialize(h, h->mu_q) != TDGL_OK) return TDGL_ERR_CUDA;
     out->psi = reinterpret_cast<float *>(h->psi[h->cur]);
     out->mu = h->mu;
     out->b = reinterpret_cast<float *>(h->b);
@@ -792,8 +810,10 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     a.src = h->psi[h->cur];
     a.dst = h->psi[ia];
     a.dst_index = ia;
+    a.mu_off = &h->ctl->mu_off[h->mu_q];   // the pending projection of mu
     if (extrapolating(h)) {
         // the init also writes the coming Poisson solve's guess over mu^(n-2)
+        a.mu_off_prev = &h->ctl->mu_off[1 - h->mu_q];
         a.mu_guess = h->mu_buf[1 - h->mu_q];
         a.ex_a = h->prev_valid ? 2.f : 1.f;
         a.ex_b = h->prev_valid ? -1.f : 0.f;
@@ -802,6 +822,7 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     ev_rec(h, 0);
     if (launch_init_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
     a.mu_guess = nullptr;
+    a.mu_off = a.mu_off_prev = nullptr;
     ev_rec(h, 1);
     h->prof.kernel_launches += 1;
     int launched = 1;   // sweeps enqueued (the init fuses the first)
@@ -910,6 +931,11 @@ static cudaError_t poisson_rhs(tdgl_handle *h, cudaStream_t s)
     return launch_poisson_rhs(h->pa, h->psi[h->cur], s);
 }
 
+static bool lazy_projection(const tdgl_handle *h, bool fm)
+{
+    return fm && !h->lk && !h->batch_owned && !h->in_adjoint;
+}
+
 static long long poisson_sequence(tdgl_handle *h, cudaStream_t s, cudaError_t *err)
 {
     long long nl = 1;
@@ -917,7 +943,8 @@ static long long poisson_sequence(tdgl_handle *h, cudaStream_t s, cudaError_t *e
     const bool fm = nc > 0 && vcycle_mean_fusable(h->pa);   // the last cycle leaves the mean of mu
     cudaError_t e = poisson_rhs(h, s);
     for (int q = 0; q < nc && e == cudaSuccess; ++q) e = launch_vcycle(h->pa, s, &nl, q > 0, fm && q == nc - 1);
-    if (e == cudaSuccess) e = launch_project_mu(h->pa, s, fm);
+    // with the mean summed by the cycle, the projection is left pending (applied where mu is read)
+    if (e == cudaSuccess) e = lazy_projection(h, fm) ? launch_commit_mean(h->pa, s) : launch_project_mu(h->pa, s, fm);
     *err = e;
     return nl + (fm ? 1 : 2);
 }
@@ -1011,7 +1038,8 @@ int tdgl_solve_mu(tdgl_handle *h)
             ++cycles;
         }
     }
-    if (launch_project_mu(h->pa, s, fm) != cudaSuccess) return TDGL_ERR_CUDA;
+    if ((lazy_projection(h, fm) ? launch_commit_mean(h->pa, s) : launch_project_mu(h->pa, s, fm)) != cudaSuccess)
+        return TDGL_ERR_CUDA;
     nl += fm ? 1 : 2;
     h->last_cycles = cycles;
     h->prof.vcycles += cycles;

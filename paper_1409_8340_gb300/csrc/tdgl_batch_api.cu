@@ -26,14 +26,14 @@ int batch_check(const tdgl_config *c)
     if (c->links_mode != TDGL_LINKS_LANDAU || (c->nx % 2) != 0 || c->d_insulating) return TDGL_ERR_INVALID_ARG;
     if ((long long)c->nx * c->ny * c->nz >= (1LL << 31)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_tol > 0) return TDGL_ERR_INVALID_ARG;
-    if (c->poisson_guess == 2) return TDGL_ERR_INVALID_ARG;   // members start from the previous mu
+
     return TDGL_OK;
 }
 
 struct BLayout {
     std::vector<size_t> inst;   // offset of each instance's workspace
     size_t table, act, bst, sweeps, bar, plog, save, total;
-    std::vector<size_t> save_psi, save_mu, save_ctl;
+    std::vector<size_t> save_psi, save_mu, save_mu2, save_ctl;
 };
 
 BLayout blayout(const tdgl_config *cfgs, int n)
@@ -57,6 +57,7 @@ BLayout blayout(const tdgl_config *cfgs, int n)
         const size_t N = (size_t)cfgs[i].nx * cfgs[i].ny * cfgs[i].nz;
         L.save_psi.push_back(take(8 * N));
         L.save_mu.push_back(take(4 * N));
+        L.save_mu2.push_back(take(4 * N));   // the second mu buffer (previous mu)
         L.save_ctl.push_back(take(sizeof(DevCtl)));
     }
     L.total = off;
@@ -147,6 +148,13 @@ void fill_instance(tdgl_batch *b, int i, int kz)
         for (int col = 0; col < 2; ++col) H.nlines[l][col] = mg_lines_of_colour(M.ny, M.nz, col);
     }
     I.pa = h->pa;
+    // Poisson guess: the linear extrapolation in time (tdgl_config.poisson_guess 0 or 2),
+    // solved in the second mu buffer; else the previous mu, solved in place
+    const bool ex = h->mu_buf[1] && !c.freeze_mu_K && (c.poisson_guess == 0 || c.poisson_guess == 2);
+    H.mu_solve = ex ? h->mu_buf[1] : h->mu;
+    I.pa.lev[0].u = I.pa.mu = H.mu_solve;
+    I.pa.mu_q = -1;
+    for (int l = 0; l < kMaxLevels; ++l) I.pa.umap_u[l] = nullptr;   // the batch smoother reads u directly
 }
 
 void fill_params(tdgl_batch *b)
@@ -275,6 +283,9 @@ int save_states(tdgl_batch *b, std::vector<int> &bst, std::vector<long long> &sw
             cudaMemcpyAsync(at<char>(b->ws, b->L.save_mu[i]), h->mu, 4 * N, cudaMemcpyDeviceToDevice, s) ||
             cudaMemcpyAsync(at<char>(b->ws, b->L.save_ctl[i]), h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s))
             return TDGL_ERR_CUDA;
+        if (h->mu_buf[1] &&
+            cudaMemcpyAsync(at<char>(b->ws, b->L.save_mu2[i]), h->mu_buf[1], 4 * N, cudaMemcpyDeviceToDevice, s))
+            return TDGL_ERR_CUDA;
     }
     bst.resize(b->n);
     sw.resize(b->n);
@@ -293,6 +304,9 @@ int restore_states(tdgl_batch *b, const std::vector<int> &bst, const std::vector
         if (cudaMemcpyAsync(h->psi[h->cur], at<char>(b->ws, b->L.save_psi[i]), 8 * N, cudaMemcpyDeviceToDevice, s) ||
             cudaMemcpyAsync(h->mu, at<char>(b->ws, b->L.save_mu[i]), 4 * N, cudaMemcpyDeviceToDevice, s) ||
             cudaMemcpyAsync(h->ctl, at<char>(b->ws, b->L.save_ctl[i]), sizeof(DevCtl), cudaMemcpyDeviceToDevice, s))
+            return TDGL_ERR_CUDA;
+        if (h->mu_buf[1] &&
+            cudaMemcpyAsync(h->mu_buf[1], at<char>(b->ws, b->L.save_mu2[i]), 4 * N, cudaMemcpyDeviceToDevice, s))
             return TDGL_ERR_CUDA;
     }
     if (cudaMemcpyAsync(b->P.bst, bst.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, s) ||

@@ -62,9 +62,14 @@ struct DevCtl {
     int result;                // buffer index holding the solve's result
     unsigned int ticket;       // last-block ticket (reset by the last block)
     int redo;                  // 1: the result is the first sweep of the last two-sweep pass (recompute it)
-    int pad[2];
+    int mu_prev_ok;            // batch member: the solve buffer holds the previous step's mu
+    int pad1;
     unsigned long long nstep;  // time steps initialised since creation or the last state load (noise counter)
     unsigned long long pad2;
+    // weighted mean not yet subtracted from each mu buffer: the state mu is mu_buf[q] -
+    // mu_off[q] (the zero-mode projection of a fixed-cycle solve is applied where mu is
+    // read, or when the state is handed out)
+    double mu_off[2];
 };
 
 // ----------------------------------------------------------------------------
@@ -219,11 +224,14 @@ struct SweepArgs {
     // previous-but-one mu: mu_guess = ex_a mu + ex_b mu_guess (nullptr: none)
     float *mu_guess;
     float ex_a, ex_b;
+    // init only: the pending mean of mu and of the previous-but-one mu (nullptr: none)
+    const double *mu_off, *mu_off_prev;
 };
 
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
 // the guess of launch_init_sweep on its own: P = a S + b P over N sites
-cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, float b, cudaStream_t s);
+cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, float b, const double *offS,
+                            const double *offP, cudaStream_t s);
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
 // one sweep src -> dst that neither tests nor touches the control block
 cudaError_t launch_sweep_redo(const SweepArgs &a, cudaStream_t s);
@@ -319,6 +327,7 @@ struct PoissonArgs {
     // falls back to the asynchronous-copy smoother)
     CUtensorMap umap[kMaxLevels];
     const float *umap_u[kMaxLevels];
+    int mu_q;                  // the handle's mu buffer that mu points at (-1: another array)
     // staged kernels' wait bound and extra expected bytes (as in SweepArgs; 0: normal use)
     unsigned long long wait_ns;
     unsigned int extra_tx;
@@ -337,6 +346,10 @@ cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launc
 bool vcycle_mean_fusable(const PoissonArgs &a);
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s, bool mean_done = false);
+// the projection left pending: ctl->mu_off[a.mu_q] = ctl->mu_mean (the fused mean of the cycle)
+cudaError_t launch_commit_mean(const PoissonArgs &a, cudaStream_t s);
+// subtract the pending mean from mu_buf (mu_off[q]) and clear it
+cudaError_t launch_mu_materialize(long long N, float *mu, DevCtl *ctl, int q, cudaStream_t s);
 cudaError_t launch_voltage(const PoissonArgs &a, cudaStream_t s);
 
 // Insulating inclusions (k_insulating.cu)
@@ -400,6 +413,10 @@ struct BatchHead {
     int nlev;                  // multigrid levels
     int lpb[kMaxLevels];       // lines per smoothing tile
     long long nlines[kMaxLevels][2];
+    // the Poisson solve's buffer: the state mu itself, or (extrapolated guess) the second
+    // mu buffer, which holds the previous step's mu until the init writes the guess there;
+    // the closing shift then writes the new state into mu and the old one into this buffer
+    float *mu_solve;
 };
 struct BatchInst {
     BatchHead h;               // staged in shared memory by every work item
@@ -464,6 +481,7 @@ struct tdgl_handle {
     uint8_t *lk;               // link bits when insulating sites are given, else nullptr
     int use_tma;               // 1: Jacobi sweeps by the shared-memory staged kernel
     int mu_solved;             // 1: a Poisson solve has run (f and mu hold its right-hand side and result)
+    int in_adjoint;            // 1: tdgl_adjoint is running (projections applied at once)
     unsigned long long dbg_wait_ns;   // tdgl_test_staged_waits: wait bound (0: default)
     unsigned int dbg_extra_tx;        // tdgl_test_staged_waits: extra expected bytes (0: none)
     // the Poisson solve of a step (right-hand side, V-cycles, projection) as CUDA graphs,
@@ -487,4 +505,6 @@ struct tdgl_handle {
 namespace tdgl {
 bool handle_extrapolates(const tdgl_handle *h);
 void use_mu_buffer(tdgl_handle *h, int q);
+int mu_materialize(tdgl_handle *h, int q);
+void drop_poisson_graphs(tdgl_handle *h);
 }  // namespace tdgl

@@ -54,8 +54,7 @@ MESOSCOPIC_CURRENTS = tuple(0.005 * n for n in range(11))
 
 def ensemble_member(m: inputs.EnsembleMember) -> Workload:
     nx, ny, nz = m.shape
-    # members of a batch start each Poisson solve from the previous mu: two V-cycles
-    p = Params(nx, ny, nz, bc=(OPEN, PERIODIC, PERIODIC), Bz=m.Bz, Jext=m.Jext, eps=1e-6, ht=0.1, poisson_cycles=2)
+    p = Params(nx, ny, nz, bc=(OPEN, PERIODIC, PERIODIC), Bz=m.Bz, Jext=m.Jext, eps=1e-6, ht=0.1)
     cand = inputs.spheres(800, (p.length(0), p.length(1), p.length(2)), 2.0, 4.0, seed=m.seed)
     return Workload(f"ensemble_member_{nx}x{ny}x{nz}", p, m.seed, 1000, cand, inputs.target_sites(m.fraction, p.N),
                     alpha_in=-m.alpha_scale, alpha_out=m.alpha_scale)

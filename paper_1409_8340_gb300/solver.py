@@ -42,7 +42,7 @@ class Params:
     poisson_cycles: int = 1
     poisson_max_cycles: int = 50
     poisson_tol: float = 0.0
-    poisson_guess: int = 0         # 1 previous mu, 2 linear extrapolation in time, 0 default (2; batches 1)
+    poisson_guess: int = 0         # 1 previous mu, 2 linear extrapolation in time, 0 default (2)
     general_links: bool = False
     xz_gauge: bool = False         # field (Bx, 0, Bz) in the Landau gauge of Eq. A_xz (By must be 0)
     Bx: float = 0.0

@@ -48,13 +48,13 @@ def inputs(ps, seed):
     return alphas, psi0s, mu0s
 
 
-def test_batch_matches_plain_handles():
-    ps = batch_cases()
+@pytest.mark.parametrize("guess", [1, 2], ids=["previous_mu", "extrapolated_mu"])
+def test_batch_matches_plain_handles(guess):
+    """Both Poisson starting guesses: the previous mu, and 2 mu^(n-1) - mu^(n-2)."""
+    ps = [dataclasses.replace(p, poisson_guess=guess) for p in batch_cases()]
     alphas, psi0s, mu0s = inputs(ps, 100)
     b = make_batch(ps, alphas, psi0s, mu0s)
-    # batch members start each Poisson solve from the previous mu; so do these handles
-    plain = [make_solver(dataclasses.replace(p, poisson_guess=1), a, psi, mu)
-             for p, a, psi, mu in zip(ps, alphas, psi0s, mu0s)]
+    plain = [make_solver(dataclasses.replace(p), a, psi, mu) for p, a, psi, mu in zip(ps, alphas, psi0s, mu0s)]
     for n in range(6):
         b.step(1)
         b.check()
@@ -171,7 +171,7 @@ def test_failed_instance_is_frozen_others_advance():
     alphas, psi0s, mu0s = inputs(ps, 500)
     b = make_batch(ps, alphas, psi0s, mu0s)
     frozen_before = gpu_state(b.instances[1])
-    plain = make_solver(dataclasses.replace(ps[0], poisson_guess=1), alphas[0], psi0s[0], mu0s[0])
+    plain = make_solver(dataclasses.replace(ps[0]), alphas[0], psi0s[0], mu0s[0])
     b.step(3)
     plain.step(3)
     rc, st = b.status()
@@ -234,7 +234,7 @@ def test_ensemble_64_full_size_sampled():
     sizes = sorted({p.shape for p in ps})
     picks = [next(i for i, p in enumerate(ps) if p.shape == sz) for sz in sizes][:3]
     for i in picks:
-        s = make_solver(dataclasses.replace(ps[i], poisson_guess=1), alphas[i].cpu().numpy(), psi0s[i])
+        s = make_solver(dataclasses.replace(ps[i]), alphas[i].cpu().numpy(), psi0s[i])
         s.step(2)
         x, y = gpu_state(b.instances[i]), gpu_state(s)
         assert np.max(np.abs(x[0] - y[0])) <= 1e-6, i

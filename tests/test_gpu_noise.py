@@ -92,7 +92,7 @@ def test_batch_with_noise_matches_plain_handles():
     b = Batch(ps, [torch.as_tensor(a).cuda() for a in alphas])
     for i, s in enumerate(b.instances):
         s.set_state(torch.as_tensor(psi0s[i]))
-    plain = [make_solver(dataclasses.replace(p, poisson_guess=1), a, x) for p, a, x in zip(ps, alphas, psi0s)]
+    plain = [make_solver(p, a, x) for p, a, x in zip(ps, alphas, psi0s)]
     b.step(4)
     b.check()
     for i, s in enumerate(plain):
