@@ -301,6 +301,65 @@ int tdgl_test_staged_waits(tdgl_handle *h, int64_t wait_ns, int32_t extra_tx_byt
 int tdgl_observables(tdgl_handle *h, tdgl_obs *out);
 
 /*
+ * z-slab decomposition (a grid split along z over several GPUs or processes; the
+ * paper names multi-GPU runs as future work, Sec. 5).  A slab handle holds the
+ * planes z0 .. z0 + nz_local - 1 of a grid described by global_cfg, between two halo
+ * planes: its arrays (psi, mu, alpha, f, as for tdgl_create) have nz_local + 2
+ * planes, plane 1 being global plane z0; the halo planes hold copies of the
+ * neighbouring slabs' edge planes, which the caller keeps current.  global_cfg must
+ * be periodic in z, open in x, with Landau links, even nx, no insulating sites, no
+ * thermal noise, one sweep per pass, check_every 1 and no fixed sweep count;
+ * global_cfg->d_alpha points at the slab's alpha with its halo planes (f32 of
+ * nx ny (nz_local + 2); the halo planes are not read).
+ *
+ * A step, driven by the caller over all slabs (Sec. 3.1 and 3.2 in the paper's order):
+ *   1. the halo planes of the state psi (tdgl_slab_planes, latest = 0) are exchanged;
+ *   2. tdgl_slab_sweep(first = 1) forms b and diag M (Eq. b) and runs the first
+ *      Jacobi sweep (Eq. final); *r2_local is max |b - M psi|^2 of the sweep's input
+ *      over the slab's own planes;
+ *   3. the caller takes the maximum of r2_local over all slabs; if it is below eps
+ *      (Eq. convergence) the output of that sweep is the result, else the halos of
+ *      the latest iterate (latest = 1) are exchanged and tdgl_slab_sweep(first = 0)
+ *      runs the next sweep (up to max_iter);
+ *   4. tdgl_slab_accept makes the result the state, whose halos are exchanged again;
+ *   5. tdgl_slab_rhs writes the Poisson right-hand side of the slab's planes into f
+ *      (tdgl_get_state: f, planes 1 .. nz_local);
+ *   6. the caller solves the potential of the whole grid's f (for instance on a
+ *      Poisson-only handle, below) and writes the slab's part into the slab's mu
+ *      (planes 1 .. nz_local), where the next init reads it.
+ * tdgl_slab_planes: planes[0], planes[1] = the slab's first and last plane (to send
+ * down and up), planes[2], planes[3] = the halo planes below and above (to receive),
+ * device pointers to complex64[nx ny] of the state (latest = 0) or of the latest
+ * iterate (latest = 1).  tdgl_slab_sweep synchronises; it returns the step's
+ * TDGL_ERR_NONFINITE like tdgl_step.  tdgl_step, tdgl_solve_psi, tdgl_solve_mu and
+ * tdgl_observables refuse slab handles.
+ */
+size_t tdgl_slab_workspace_bytes(const tdgl_config *global_cfg, int32_t z0, int32_t nz_local);
+int tdgl_slab_create(const tdgl_config *global_cfg, int32_t z0, int32_t nz_local, void *d_workspace, size_t ws_bytes,
+                     void *stream, tdgl_handle **out);
+int tdgl_slab_sweep(tdgl_handle *h, int32_t first, double *r2_local);
+int tdgl_slab_accept(tdgl_handle *h);
+int tdgl_slab_planes(tdgl_handle *h, int32_t latest, float **planes);
+int tdgl_slab_rhs(tdgl_handle *h);
+
+/*
+ * Poisson-only handle: the multigrid Poisson solve of Sec. 3.2 (the operator, the
+ * boundary conditions of cfg and the zero-mode projection of tdgl_step) for a
+ * right-hand side the caller writes into the handle's f (tdgl_get_state: f; mu is
+ * the result, psi NULL).  No psi arrays are allocated and cfg->d_alpha may be NULL;
+ * Landau links, no insulating sites.  tdgl_solve_mu_f runs poisson_cycles V-cycles
+ * (or to poisson_tol) from the starting guess of poisson_guess (the extrapolation
+ * of the last two solutions of this handle), projects out the weighted mean and,
+ * with open x, computes E_x from the face potentials; it works on single handles
+ * too (after a step: the f of that step).  tdgl_read_ctl_scalars returns E_x and the
+ * relative residual max|F - Lap mu| / max|F| of the last solve (synchronises).
+ */
+size_t tdgl_poisson_workspace_bytes(const tdgl_config *cfg);
+int tdgl_poisson_create(const tdgl_config *cfg, void *d_workspace, size_t ws_bytes, void *stream, tdgl_handle **out);
+int tdgl_solve_mu_f(tdgl_handle *h);
+int tdgl_read_ctl_scalars(tdgl_handle *h, double *Ex, double *poisson_res);
+
+/*
  * Inclusion pattern generator (Sec. 3.4), standalone.  Candidates (host array,
  * 10 doubles each: centre cx cy cz, semi-axes a b c, unit quaternion q0..q3 of
  * the body rotation) are consumed in order; a site r = (i hx, j hy, k hz) lies

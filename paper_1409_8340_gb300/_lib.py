@@ -174,6 +174,17 @@ _SIGS = {
     "tdgl_get_state": (ctypes.c_int, [_P, ctypes.POINTER(StatePtrs)]),
     "tdgl_set_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "tdgl_get_mu_prev": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "tdgl_slab_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int32, ctypes.c_int32]),
+    "tdgl_slab_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P,
+                                        ctypes.POINTER(_P)]),
+    "tdgl_slab_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "tdgl_slab_accept": (ctypes.c_int, [_P]),
+    "tdgl_slab_planes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "tdgl_slab_rhs": (ctypes.c_int, [_P]),
+    "tdgl_poisson_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config)]),
+    "tdgl_poisson_create": (ctypes.c_int, [ctypes.POINTER(Config), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "tdgl_solve_mu_f": (ctypes.c_int, [_P]),
+    "tdgl_read_ctl_scalars": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "tdgl_set_mu_prev": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "tdgl_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "tdgl_solve_psi": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),

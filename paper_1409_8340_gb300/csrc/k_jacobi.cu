@@ -29,7 +29,7 @@ __device__ __forceinline__ void finish_sweep(const SweepArgs &a, float bmax, boo
 static int zchunk(const DevGrid &g)
 {
     long long bxy = (long long)((g.nx + kBX - 1) / kBX) * ((g.ny + kBY - 1) / kBY);
-    long long kz = (bxy * g.nz) / 2432;
+    long long kz = (bxy * (zhi(g) - zlo(g))) / 2432;
     if (kz < 1) kz = 1;
     if (kz > 32) kz = 32;
     return (int)kz;
@@ -313,7 +313,7 @@ static dim3 sweep_grid(const DevGrid &g, int kz)
 
 static dim3 sweep2_grid(const DevGrid &g, int kz)
 {
-    return dim3((g.nx + kPX - 1) / kPX, (g.ny + kBY - 1) / kBY, (g.nz + kz - 1) / kz);
+    return dim3((g.nx + kPX - 1) / kPX, (g.ny + kBY - 1) / kBY, (zhi(g) - zlo(g) + kz - 1) / kz);
 }
 
 // the two-site tiled kernels: Landau links of either plane (tables), even nx

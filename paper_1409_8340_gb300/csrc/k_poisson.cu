@@ -1269,7 +1269,7 @@ cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s)
 // Zero mode of mu: subtract the weighted mean (FP64 sum).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGX) mu_mean_kernel(DevGrid g, const float *mu, DevCtl *ctl, double *blockred,
-                                                      double wsum)
+                                                      double wsum, int to_fmean)
 {
     const int i = blockIdx.x * kGX + threadIdx.x, j = blockIdx.y;
     float accf = 0.f;
@@ -1295,7 +1295,7 @@ __global__ void __launch_bounds__(kGX) mu_mean_kernel(DevGrid g, const float *mu
     t = block_sum(t, shd);
     if (threadIdx.x == 0) {
         ctl->ticket = 0u;
-        ctl->mu_mean = t / wsum;
+        (to_fmean ? ctl->fmean : ctl->mu_mean) = t / wsum;
     }
 }
 
@@ -1320,8 +1320,14 @@ __global__ void mu_shift_kernel(long long N, float *mu, DevCtl *ctl, int zero_q,
 
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s, bool mean_done)
 {
-    if (!mean_done) mu_mean_kernel<<<grid_xy(a.g.nx, a.g.ny), kGX, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum);
+    if (!mean_done) mu_mean_kernel<<<grid_xy(a.g.nx, a.g.ny), kGX, 0, s>>>(a.g, a.mu, a.ctl, a.blockred, a.wsum, 0);
     mu_shift_kernel<<<grid_blocks(a.g.N, 8), kThreads, 0, s>>>(a.g.N, a.mu, a.ctl, a.mu_q, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f_mean(const PoissonArgs &a, cudaStream_t s)
+{
+    mu_mean_kernel<<<grid_xy(a.g.nx, a.g.ny), kGX, 0, s>>>(a.g, a.f, a.ctl, a.blockred, a.wsum, 1);
     return cudaGetLastError();
 }
 

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     T.w = min(kTX, g.nx - T.x0);
     T.j0 = blockIdx.y * kTR;
     T.nr = min(kTR, g.ny - T.j0);
-    const int k0 = blockIdx.z * kz, k1 = min(k0 + kz, g.nz);
+    const int k0 = zlo(g) + blockIdx.z * kz, k1 = min(k0 + kz, zhi(g));
     const int nplanes = (k1 - k0) + 2;   // k0 - 1 .. k1
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -447,7 +447,7 @@ bool tma_encode_maps(const DevGrid &g, float2 *const psi[3], const float2 *b, co
 static int tma_kz(const DevGrid &g)
 {
     const long long bxy = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTR - 1) / kTR);
-    long long kz = (bxy * g.nz) / 1824;   // about 1824 blocks (four waves of three per SM) or more
+    long long kz = (bxy * (zhi(g) - zlo(g))) / 1824;   // about 1824 blocks (four waves of three per SM) or more
     if (kz < 2) kz = 2;
     if (kz > 32) kz = 32;
     return (int)kz;
@@ -465,7 +465,7 @@ static cudaError_t launch_variant(const SweepArgs &a, const CUtensorMap &map_psi
         attr = true;
     }
     const int kz = tma_kz(a.g);
-    const dim3 grid((a.g.nx + kTX - 1) / kTX, (a.g.ny + kTR - 1) / kTR, (a.g.nz + kz - 1) / kz);
+    const dim3 grid((a.g.nx + kTX - 1) / kTX, (a.g.ny + kTR - 1) / kTR, (zhi(a.g) - zlo(a.g) + kz - 1) / kz);
     sweep_tma_kernel<XZ, MASK, RHS><<<grid, kThreads, smem, s>>>(a, kz, map_psi, m.b, m.D);
     return cudaGetLastError();
 }

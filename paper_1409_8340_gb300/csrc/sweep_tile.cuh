@@ -128,8 +128,8 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
     const int tx = threadIdx.x;
     const int x = (bx * kBX + tx) * 2;
     const int j = by * kBY + threadIdx.y;
-    const int k0 = bz * kz;
-    const int k1 = min(k0 + kz, g.nz);
+    const int k0 = zlo(g) + bz * kz;
+    const int k1 = min(k0 + kz, zhi(g));
     const bool in = (x < g.nx) && (j < g.ny);
     const float2 Ux = ldx<CG>(&a.ctl->Ux);
     const unsigned long long nstep = INIT ? ldx<CG>(&a.ctl->nstep) : 0ull;

@@ -70,7 +70,8 @@ bool quantised(double B, double L1, double L2, long long *n)
     return fabs(q - r) <= 1e-9 * (1.0 + fabs(q));
 }
 
-int validate(const tdgl_config *c)
+// pon: a Poisson-only handle (tdgl_poisson_create), which has no psi and reads no alpha
+int validate(const tdgl_config *c, bool pon = false)
 {
     if (!c) return TDGL_ERR_INVALID_ARG;
     if (c->nx < 2 || c->ny < 2 || c->nz < 1) return TDGL_ERR_INVALID_ARG;
@@ -89,7 +90,7 @@ int validate(const tdgl_config *c)
     if (!(c->noise_T >= 0)) return TDGL_ERR_INVALID_ARG;
     if (c->fixed_sweeps == 0 && !(c->eps > 0)) return TDGL_ERR_INVALID_ARG;
     if (c->poisson_cycles < 1 || c->poisson_max_cycles < c->poisson_cycles) return TDGL_ERR_INVALID_ARG;
-    if (!c->d_alpha) return TDGL_ERR_INVALID_ARG;
+    if (!c->d_alpha && !pon) return TDGL_ERR_INVALID_ARG;
     if (c->links_mode != TDGL_LINKS_LANDAU && c->links_mode != TDGL_LINKS_GENERAL && c->links_mode != TDGL_LINKS_XZ)
         return TDGL_ERR_INVALID_ARG;
     if (c->links_mode == TDGL_LINKS_GENERAL && !c->d_link_phase) return TDGL_ERR_INVALID_ARG;
@@ -135,7 +136,7 @@ bool can_coarsen(int n, int bc)
 }
 int coarse_n(int n, int bc) { return bc == TDGL_PERIODIC ? n / 2 : (n - 1) / 2 + 1; }
 
-Layout layout(const tdgl_config *c)
+Layout layout(const tdgl_config *c, bool pon = false)
 {
     Layout L;
     memset(&L, 0, sizeof(L));
@@ -159,9 +160,10 @@ Layout layout(const tdgl_config *c)
     if (nb < 2 * pair_blocks(g)) nb = 2 * pair_blocks(g);
     L.nblockred = nb;
     L.blockred = take(sizeof(double) * nb);
-    for (int q = 0; q < 3; ++q) L.psi[q] = take(8 * (size_t)N);
-    L.b = take(8 * (size_t)N);
-    L.D = take(8 * (size_t)N);
+    const size_t npsi = pon ? 0 : (size_t)N;   // a Poisson-only handle holds no psi, b or diag M
+    for (int q = 0; q < 3; ++q) L.psi[q] = take(8 * npsi);
+    L.b = take(8 * npsi);
+    L.D = take(8 * npsi);
     L.mu = take(4 * (size_t)N);
     // the second mu buffer: the previous step's mu, over which the init writes the guess
     // that the next Poisson solve starts from (multigrid solves only)
@@ -350,13 +352,20 @@ size_t tdgl_workspace_bytes(const tdgl_config *cfg)
     return layout(cfg).total;
 }
 
+static int create_impl(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream, tdgl_handle **out, bool pon);
+
 int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream, tdgl_handle **out)
+{
+    return create_impl(cfg, ws, ws_bytes, stream, out, false);
+}
+
+static int create_impl(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream, tdgl_handle **out, bool pon)
 {
     if (!out) return TDGL_ERR_INVALID_ARG;
     *out = nullptr;
-    int v = validate(cfg);
+    int v = validate(cfg, pon);
     if (v != TDGL_OK) return v;
-    Layout L = layout(cfg);
+    Layout L = layout(cfg, pon);
     if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < L.total) return TDGL_ERR_WORKSPACE;
     tdgl_handle *h = new tdgl_handle();
     h->cfg = *cfg;
@@ -421,7 +430,8 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     // Jacobi sweep kernel: 1 register-tiled; 2 or 0 (default) staged in shared memory by the
     // tensor memory accelerator where it applies (Landau links of either plane, even nx),
     // measured faster at every size tried; the register-tiled kernel elsewhere
-    h->use_tma = (c.sweep_kernel != 1 && tma_sweep_supported(g)) ? 1 : 0;
+    h->poisson_only = pon ? 1 : 0;
+    h->use_tma = (!pon && c.sweep_kernel != 1 && tma_sweep_supported(g)) ? 1 : 0;
     if (h->use_tma && !tma_encode_maps(g, h->psi, h->b, h->D, &h->tmaps)) h->use_tma = 0;
     h->batch_owned = 0;
     {
@@ -522,7 +532,7 @@ int tdgl_create(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *stream,
     memset(&ctl0, 0, sizeof(ctl0));
     ctl0.Ux = make_float2(1.f, 0.f);
     chk(cudaMemcpyAsync(h->ctl, &ctl0, sizeof(DevCtl), cudaMemcpyHostToDevice, s));
-    chk(cudaMemsetAsync(h->psi[0], 0, 8 * (size_t)N, s));
+    if (!pon) chk(cudaMemsetAsync(h->psi[0], 0, 8 * (size_t)N, s));
     chk(cudaMemsetAsync(h->mu, 0, 4 * (size_t)N, s));
     if (h->mu_buf[1]) chk(cudaMemsetAsync(h->mu_buf[1], 0, 4 * (size_t)N, s));
     chk(cudaMemsetAsync(h->f, 0, 4 * (size_t)N, s));
@@ -687,6 +697,7 @@ int tdgl_profile_read(tdgl_handle *h, tdgl_profile *out)
 int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double K)
 {
     if (!h || !d_psi) return TDGL_ERR_INVALID_ARG;
+    if (h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const size_t N = (size_t)h->g.N;
     cudaStream_t s = h->stream;
     if (cudaMemcpyAsync(h->psi[h->cur], d_psi, 8 * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
@@ -708,6 +719,7 @@ int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double
 int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_mu, double K)
 {
     if (!h || !host_psi) return TDGL_ERR_INVALID_ARG;
+    if (h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const size_t N = (size_t)h->g.N;
     cudaStream_t s = h->stream;
     if (cudaMemcpyAsync(h->psi[h->cur], host_psi, 8 * N, cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
@@ -772,7 +784,7 @@ int tdgl_set_step(tdgl_handle *h, int64_t step)
 
 int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double *K)
 {
-    if (!h) return TDGL_ERR_INVALID_ARG;
+    if (!h || (h->poisson_only && host_psi)) return TDGL_ERR_INVALID_ARG;
     const size_t N = (size_t)h->g.N;
     cudaStream_t s = h->stream;
     if (mu_materialize(h, h->mu_q) != TDGL_OK) return TDGL_ERR_CUDA;
@@ -800,7 +812,7 @@ int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out)
 
 int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
 {
-    if (!h || h->batch_owned) return TDGL_ERR_INVALID_ARG;
+    if (!h || h->batch_owned || h->slab || h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     SweepArgs a = sweep_args(h);
@@ -980,7 +992,7 @@ static bool build_poisson_graph(tdgl_handle *h)
 
 int tdgl_solve_mu(tdgl_handle *h)
 {
-    if (!h || h->batch_owned) return TDGL_ERR_INVALID_ARG;
+    if (!h || h->batch_owned || h->slab || h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     h->mu_solved = 1;
@@ -1047,9 +1059,198 @@ int tdgl_solve_mu(tdgl_handle *h)
     return TDGL_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// z-slab decomposition: a handle for the planes z0 .. z0 + nz_local - 1 of a grid
+// periodic in z, with one halo plane on each side; sweeps one at a time, the
+// convergence decision and the halo exchange left to the caller.
+// ---------------------------------------------------------------------------------
+static int slab_config(const tdgl_config *gcfg, int32_t z0, int32_t nz_local, tdgl_config *lc)
+{
+    if (!gcfg || validate(gcfg) != TDGL_OK) return TDGL_ERR_INVALID_ARG;
+    const tdgl_config &c = *gcfg;
+    if (c.bc[2] != TDGL_PERIODIC || c.nz < 3 || c.bc[0] != TDGL_OPEN || c.links_mode != TDGL_LINKS_LANDAU ||
+        (c.nx % 2) != 0 || c.d_insulating || c.noise_T != 0.0 || c.sweeps_per_pass == 2 || c.fixed_sweeps > 0 ||
+        c.check_every != 1)
+        return TDGL_ERR_INVALID_ARG;
+    if (nz_local < 1 || z0 < 0 || (long long)z0 + nz_local > c.nz) return TDGL_ERR_INVALID_ARG;
+    *lc = c;
+    lc->nz = nz_local + 2;
+    return validate(lc);
+}
+
+size_t tdgl_slab_workspace_bytes(const tdgl_config *global_cfg, int32_t z0, int32_t nz_local)
+{
+    tdgl_config lc;
+    if (slab_config(global_cfg, z0, nz_local, &lc) != TDGL_OK) return 0;
+    return layout(&lc).total;
+}
+
+int tdgl_slab_create(const tdgl_config *global_cfg, int32_t z0, int32_t nz_local, void *d_workspace, size_t ws_bytes,
+                     void *stream, tdgl_handle **out)
+{
+    tdgl_config lc;
+    int rc = slab_config(global_cfg, z0, nz_local, &lc);
+    if (rc != TDGL_OK) return rc;
+    rc = create_impl(&lc, d_workspace, ws_bytes, stream, out, false);
+    if (rc != TDGL_OK) return rc;
+    tdgl_handle *h = *out;
+    h->slab = 1;
+    h->slab_z0 = z0;
+    h->slab_nz = nz_local;
+    h->g.kw0 = h->pa.g.kw0 = 1;
+    h->g.kw1 = h->pa.g.kw1 = nz_local + 1;
+    return TDGL_OK;
+}
+
+int tdgl_slab_sweep(tdgl_handle *h, int32_t first, double *r2_local)
+{
+    if (!h || !h->slab) return TDGL_ERR_INVALID_ARG;
+    if (!first && h->slab_n < 1) return TDGL_ERR_INVALID_ARG;
+    cudaStream_t s = h->stream;
+    SweepArgs a = sweep_args(h);
+    a.fixed_sweeps = 1 << 30;   // never decided on the device: the caller takes the global maximum
+    a.max_iter = 1 << 30;
+    a.check_every = 1;
+    const int ia = (h->cur + 1) % 3, ib = (h->cur + 2) % 3;
+    cudaError_t e;
+    if (first) {
+        a.src = h->psi[h->cur];
+        a.dst = h->psi[ia];
+        a.dst_index = ia;
+        e = launch_init_sweep(a, s);
+        h->slab_n = 1;
+    } else {
+        // sweep number slab_n reads the previous output: odd A -> B, even B -> A
+        const bool odd = (h->slab_n % 2) == 1;
+        a.src = odd ? h->psi[ia] : h->psi[ib];
+        a.dst = odd ? h->psi[ib] : h->psi[ia];
+        a.dst_index = odd ? ib : ia;
+        if (h->use_tma) {
+            int src = 0;
+            while (src < 2 && h->psi[src] != a.src) ++src;
+            e = launch_sweep_tma(a, h->tmaps.psi[src], h->tmaps, s);
+        } else {
+            e = launch_sweep(a, s);
+        }
+        h->slab_n += 1;
+    }
+    if (e != cudaSuccess) return TDGL_ERR_CUDA;
+    h->slab_last = a.dst_index;
+    h->prof.kernel_launches += 1;
+    DevCtl ctl;
+    int rc = read_ctl(h, &ctl);
+    if (rc != TDGL_OK) return rc;
+    if (r2_local) *r2_local = ctl.r2;
+    return ctl.status;
+}
+
+int tdgl_slab_accept(tdgl_handle *h)
+{
+    if (!h || !h->slab || h->slab_n < 1) return TDGL_ERR_INVALID_ARG;
+    h->cur = h->slab_last;
+    h->last_sweeps = h->slab_n;
+    h->prof.sweeps += h->slab_n;
+    h->slab_n = 0;
+    ++h->step;
+    return TDGL_OK;
+}
+
+int tdgl_slab_planes(tdgl_handle *h, int32_t latest, float **planes)
+{
+    if (!h || !h->slab || !planes || (latest && h->slab_n < 1)) return TDGL_ERR_INVALID_ARG;
+    float2 *buf = h->psi[latest ? h->slab_last : h->cur];
+    const long long pl = (long long)h->g.nx * h->g.ny;
+    planes[0] = reinterpret_cast<float *>(buf + pl);                        // first slab plane
+    planes[1] = reinterpret_cast<float *>(buf + pl * h->slab_nz);           // last slab plane
+    planes[2] = reinterpret_cast<float *>(buf);                             // halo below
+    planes[3] = reinterpret_cast<float *>(buf + pl * (h->slab_nz + 1));     // halo above
+    return TDGL_OK;
+}
+
+int tdgl_slab_rhs(tdgl_handle *h)
+{
+    if (!h || !h->slab) return TDGL_ERR_INVALID_ARG;
+    if (poisson_rhs(h, h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->prof.kernel_launches += 1;
+    return cuda_err(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------
+// Poisson-only handle: the potential of a right-hand side the caller writes into f
+// ---------------------------------------------------------------------------------
+size_t tdgl_poisson_workspace_bytes(const tdgl_config *cfg)
+{
+    if (validate(cfg, true) != TDGL_OK || cfg->d_insulating || cfg->links_mode != TDGL_LINKS_LANDAU) return 0;
+    return layout(cfg, true).total;
+}
+
+int tdgl_poisson_create(const tdgl_config *cfg, void *d_workspace, size_t ws_bytes, void *stream, tdgl_handle **out)
+{
+    if (!cfg || cfg->d_insulating || cfg->links_mode != TDGL_LINKS_LANDAU) return TDGL_ERR_INVALID_ARG;
+    return create_impl(cfg, d_workspace, ws_bytes, stream, out, true);
+}
+
+int tdgl_solve_mu_f(tdgl_handle *h)
+{
+    if (!h || h->batch_owned || h->slab || h->lk) return TDGL_ERR_INVALID_ARG;
+    const tdgl_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    h->mu_solved = 1;
+    long long nl = 1;
+    if (launch_f_mean(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (extrapolating(h)) {
+        // the guess 2 mu^(n-1) - mu^(n-2) over the previous mu, then solve there
+        const int q = h->mu_q;
+        if (launch_mu_guess(h->g.N, h->mu, h->mu_buf[1 - q], h->prev_valid ? 2.f : 1.f, h->prev_valid ? -1.f : 0.f,
+                            &h->ctl->mu_off[q], &h->ctl->mu_off[1 - q], s) != cudaSuccess)
+            return TDGL_ERR_CUDA;
+        use_mu_buffer(h, 1 - q);
+        h->prev_valid = 1;
+        nl += 1;
+    }
+    const bool fm = c.poisson_tol <= 0 && c.poisson_cycles > 0 && vcycle_mean_fusable(h->pa);
+    int cycles = 0;
+    for (; cycles < c.poisson_cycles; ++cycles)
+        if (launch_vcycle(h->pa, s, &nl, cycles > 0, fm && cycles == c.poisson_cycles - 1) != cudaSuccess)
+            return TDGL_ERR_CUDA;
+    if (c.poisson_tol > 0) {
+        for (;;) {
+            if (launch_poisson_residual(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
+            ++nl;
+            DevCtl ctl;
+            int rc = read_ctl(h, &ctl);
+            if (rc != TDGL_OK) return rc;
+            if (ctl.res <= c.poisson_tol || cycles >= c.poisson_max_cycles) break;
+            if (launch_vcycle(h->pa, s, &nl, true) != cudaSuccess) return TDGL_ERR_CUDA;
+            ++cycles;
+        }
+    }
+    if ((lazy_projection(h, fm) ? launch_commit_mean(h->pa, s) : launch_project_mu(h->pa, s, fm)) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    if (c.bc[0] == TDGL_OPEN && launch_voltage(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->last_cycles = cycles;
+    h->prof.vcycles += cycles;
+    h->prof.kernel_launches += nl + 2;
+    return cuda_err(cudaGetLastError());
+}
+
+int tdgl_read_ctl_scalars(tdgl_handle *h, double *Ex, double *poisson_res)
+{
+    if (!h) return TDGL_ERR_INVALID_ARG;
+    if (poisson_res && h->mu_solved && !h->lk && h->cfg.poisson_tol <= 0 &&
+        launch_poisson_residual(h->pa, h->stream) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    DevCtl ctl;
+    int rc = read_ctl(h, &ctl);
+    if (rc != TDGL_OK) return rc;
+    if (Ex) *Ex = ctl.Ex;
+    if (poisson_res) *poisson_res = ctl.res;
+    return TDGL_OK;
+}
+
 int tdgl_step(tdgl_handle *h, int n_steps)
 {
-    if (!h || h->batch_owned || n_steps < 0) return TDGL_ERR_INVALID_ARG;
+    if (!h || h->batch_owned || h->slab || h->poisson_only || n_steps < 0) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     for (int n = 0; n < n_steps; ++n) {
@@ -1091,7 +1292,7 @@ int tdgl_step(tdgl_handle *h, int n_steps)
 
 int tdgl_observables(tdgl_handle *h, tdgl_obs *out)
 {
-    if (!h || !out) return TDGL_ERR_INVALID_ARG;
+    if (!h || !out || h->slab || h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     double flux = c.hx * c.hy * c.Bz;
     // a solve with a fixed number of V-cycles never measured its residual: measure it now

@@ -34,7 +34,13 @@ struct DevGrid {
     const float2 *Wx;          // [nx] periodic-y wrap link, x part exp(-i i hx Ly Bz)
     const float2 *Wz;          // [nz] periodic-y wrap link, z part exp(+i k hz Ly Bx)
     const uint8_t *lk;         // [N] link bits (insulating inclusions), or nullptr: every link present
+    // z window: the planes kw0 .. kw1-1 are updated and reduced over (kw1 = 0: all planes).
+    // A z-slab of a larger grid holds its planes between two halo planes (window 1 .. nz-2)
+    // whose values come from the neighbouring slabs.
+    int kw0, kw1;
 };
+__host__ __device__ __forceinline__ int zlo(const DevGrid &g) { return g.kw1 ? g.kw0 : 0; }
+__host__ __device__ __forceinline__ int zhi(const DevGrid &g) { return g.kw1 ? g.kw1 : g.nz; }
 
 // Link bits of a site (insulating inclusions, Sec. 3.4 (ii)): the link to the +x,
 // -x, +y, -y, +z, -z neighbour exists and joins two conducting sites; kLkIns: the
@@ -346,6 +352,8 @@ cudaError_t launch_vcycle(const PoissonArgs &a, cudaStream_t s, long long *launc
 bool vcycle_mean_fusable(const PoissonArgs &a);
 cudaError_t launch_poisson_residual(const PoissonArgs &a, cudaStream_t s);
 cudaError_t launch_project_mu(const PoissonArgs &a, cudaStream_t s, bool mean_done = false);
+// ctl->fmean = the trapezoid-weighted mean of the level-0 right-hand side f
+cudaError_t launch_f_mean(const PoissonArgs &a, cudaStream_t s);
 // the projection left pending: ctl->mu_off[a.mu_q] = ctl->mu_mean (the fused mean of the cycle)
 cudaError_t launch_commit_mean(const PoissonArgs &a, cudaStream_t s);
 // subtract the pending mean from mu_buf (mu_off[q]) and clear it
@@ -482,6 +490,12 @@ struct tdgl_handle {
     int use_tma;               // 1: Jacobi sweeps by the shared-memory staged kernel
     int mu_solved;             // 1: a Poisson solve has run (f and mu hold its right-hand side and result)
     int in_adjoint;            // 1: tdgl_adjoint is running (projections applied at once)
+    // z-slab of a larger grid (tdgl_slab_create): planes 1 .. slab_nz of the arrays are the
+    // slab (global planes slab_z0 ..), planes 0 and slab_nz + 1 the halos
+    int slab, slab_z0, slab_nz;
+    int slab_n;                // sweeps of the current slab solve
+    int slab_last;             // buffer of the latest slab iterate
+    int poisson_only;          // 1: no psi arrays (tdgl_poisson_create)
     unsigned long long dbg_wait_ns;   // tdgl_test_staged_waits: wait bound (0: default)
     unsigned int dbg_extra_tx;        // tdgl_test_staged_waits: extra expected bytes (0: none)
     // the Poisson solve of a step (right-hand side, V-cycles, projection) as CUDA graphs,

@@ -132,3 +132,21 @@ def test_batch_validation_before_device_work(lib):
     b = ctypes.c_void_p()
     assert lib.tdgl_batch_create(arr, 2, ctypes.c_void_p(0x100001), n, None, ctypes.byref(b)) == -6
     assert lib.tdgl_batch_create(arr, 2, ctypes.c_void_p(0x100000), n - 1, None, ctypes.byref(b)) == -6
+
+
+def test_slab_and_poisson_only_workspaces_validate_on_the_host(lib):
+    """The z-slab handles need a grid periodic in z, open in x, Landau links, even nx, no
+    noise, and a slab inside the grid; the Poisson-only handle reads no alpha."""
+    good = _cfg(nx=32, ny=16, nz=12, bc=(1, 0, 0), Bz=0.1)
+    assert lib.tdgl_slab_workspace_bytes(ctypes.byref(good), 4, 4) > 0
+    assert lib.tdgl_slab_workspace_bytes(ctypes.byref(good), 8, 4) > 0
+    bad = [(good, 10, 4), (good, 0, 0), (good, -1, 4),
+           (_cfg(nx=32, ny=16, nz=12, bc=(1, 0, 1), Bz=0.1), 0, 4),      # open z
+           (_cfg(nx=33, ny=16, nz=12, bc=(1, 0, 0), Bz=0.1), 0, 4),      # odd nx
+           (_cfg(nx=32, ny=16, nz=12, bc=(1, 0, 0), Bz=0.1, noise_T=0.01), 0, 4)]
+    for c, z0, n in bad:
+        assert lib.tdgl_slab_workspace_bytes(ctypes.byref(c), z0, n) == 0, (z0, n)
+    pc = _cfg(nx=32, ny=16, nz=12, bc=(1, 0, 0), Bz=0.1)
+    pc.d_alpha = None
+    full = lib.tdgl_workspace_bytes(ctypes.byref(_cfg(nx=32, ny=16, nz=12, bc=(1, 0, 0), Bz=0.1)))
+    assert 0 < lib.tdgl_poisson_workspace_bytes(ctypes.byref(pc)) < full - 40 * 32 * 16 * 12 + 4096
