@@ -436,6 +436,7 @@ def insulating_mode(dev, steps: int = 20, relax: int = 20):
     from paper_1409_8340_gb300.solver import Solver, pattern_ex
     w = workload(0.025)
     p = w.params
+    p.poisson_cycles = 2          # two CG iterations per step, each preconditioned by a V-cycle
     cand = np.asarray(w.candidates)
     sh = np.zeros((cand.shape[0], 13))
     sh[:, 2:5] = cand[:, 0:3]

@@ -414,7 +414,26 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
                 if (i == g.nx - 1) accv -= (double)v;
             }
         };
-        if ((g.nx & 3) == 0) {
+        if ((g.nx & 3) == 0 && !oy && !oz) {
+            // periodic y and z: only the x faces carry a weight (1/2) and the face sums of E_x.
+            // Four sites of one row per thread and pass; the site's x index advances by the
+            // pass stride modulo nx instead of being divided out per site.
+            const unsigned int stride = 4u * kBT, dstep = stride % (unsigned int)g.nx;
+            unsigned int i = (m0 + 4u * tid) % (unsigned int)g.nx;
+            for (unsigned int q = m0 + 4u * tid; q < m1; q += stride) {
+                const float4 x = ld4<true>(mu + q);
+                float sum = (x.x + x.y) + (x.z + x.w);
+                if (ox && i == 0) sum -= 0.5f * x.x;
+                if (ox && i + 3 == (unsigned int)g.nx - 1) sum -= 0.5f * x.w;
+                accf += sum;
+                if (H.open_x) {
+                    if (i == 0) accv += (double)x.x;
+                    if (i + 3 == (unsigned int)g.nx - 1) accv -= (double)x.w;
+                }
+                i += dstep;
+                if (i >= (unsigned int)g.nx) i -= (unsigned int)g.nx;
+            }
+        } else if ((g.nx & 3) == 0) {
             // four sites of one row per thread and pass; the loads of all passes first
             constexpr int kMP = 8;
             float4 v[kMP];
