@@ -379,13 +379,13 @@ __device__ __forceinline__ int comp_of(const InsArgs &a, long long m)
 // island's by atomics into isl_acc (cleared before the launch).
 __global__ void ins_csum_kernel(InsArgs a, const float *v, int slot)
 {
-    double acc = 0.0;
+    float acc = 0.f;   // FP32 per thread, FP64 over the threads and blocks
     for_sites(a.g, [&](long long m, int, int, int, float w) {
         const int c = comp_of(a, m);
-        if (c == 0) acc += (double)(w * v[m]);
+        if (c == 0) acc += w * v[m];
         else if (c > 0) atomicAdd(a.isl_acc + (c - 1), (double)(w * v[m]));
     });
-    finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
+    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
 }
 
 // v -= its component's weighted mean, 0 on insulating sites.  dslot >= 0: also
@@ -394,7 +394,7 @@ __global__ void ins_csum_kernel(InsArgs a, const float *v, int slot)
 __global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int dslot, int fmax)
 {
     const float cm = (float)(a.ctl->sums[mslot] / a.wsum_c);
-    double acc = 0.0;
+    float acc = 0.f;   // FP32 per thread, FP64 over the threads and blocks
     float mx = 0.f;
     for_sites(a.g, [&](long long m, int, int, int, float w) {
         const int c = comp_of(a, m);
@@ -405,9 +405,9 @@ __global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int dslot, int
         const float x = v[m] - (c == 0 ? cm : (float)(a.isl_acc[c - 1] / a.isl_w[c - 1]));
         v[m] = x;
         mx = fmaxf(mx, fabsf(x));
-        if (dslot >= 0) acc += (double)(w * a.r[m] * x);
+        if (dslot >= 0) acc += w * a.r[m] * x;
     });
-    if (dslot >= 0) finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[dslot]);
+    if (dslot >= 0) finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[dslot]);
     if (!fmax) return;
     __shared__ float shf[32];
     __shared__ int flag;
@@ -424,6 +424,228 @@ __global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int dslot, int
         a.ctl->ticket = 0u;
         a.ctl->fmax = (double)tm;
         a.ctl->fmean = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same passes four sites at a time (nx a multiple of 4, no islands): 16-byte loads
+// of the site values and of the link bits, FP32 partial sums per thread.
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ void for_quads(const DevGrid &g, F &&fn)
+{
+    const long long nq = g.N >> 2;
+    const int qrow = g.nx >> 2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nq; t += (long long)gridDim.x * blockDim.x) {
+        const long long row = t / qrow;
+        const int i0 = (int)(t - row * qrow) * 4;
+        const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+        fn(row * g.nx + i0, i0, j, k, face_w(g.bcy, g.ny, j) * face_w(g.bcz, g.nz, k));
+    }
+}
+
+__device__ __forceinline__ float4 ld4f(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4f(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+// masked_lap of the four sites m .. m+3 (i0 = i of site m)
+__device__ __forceinline__ float4 masked_lap4(const DevGrid &g, const float *__restrict__ u, long long m, int i0, int j,
+                                              int k, uchar4 l4)
+{
+    const float4 c4 = ld4f(u + m);
+    const float c[4] = {c4.x, c4.y, c4.z, c4.w};
+    const unsigned l[4] = {l4.x, l4.y, l4.z, l4.w};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    // x: the quad's own values and one site beyond each end (wrapped; used only where the link exists)
+    const float xm = u[i0 == 0 ? m + g.nx - 1 : m - 1];
+    const float xp = u[i0 + 4 == g.nx ? m + 4 - g.nx : m + 4];
+    const float xs[6] = {xm, c[0], c[1], c[2], c[3], xp};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        float vp = (l[s] & kLkXp) ? xs[s + 2] - c[s] : 0.f;
+        float vm = (l[s] & kLkXm) ? xs[s] - c[s] : 0.f;
+        if (g.bcx == kOpen) {
+            if (i0 + s == 0) vm = vp;
+            if (i0 + s == g.nx - 1) vp = vm;
+        }
+        acc[s] = g.cx * (vp + vm);
+    }
+    // y and z: rows at the (wrapped) neighbour indices, whole quads
+    const int n[2] = {g.ny, g.nz}, bc[2] = {g.bcy, g.bcz}, idx[2] = {j, k};
+    const long long st[2] = {(long long)g.nx, (long long)g.nx * g.ny};
+    const float cc[2] = {g.cy, g.cz};
+    const unsigned bp[2] = {kLkYp, kLkZp}, bm[2] = {kLkYm, kLkZm};
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        if (n[ax] < 2) continue;
+        const long long mp = (idx[ax] == n[ax] - 1) ? m - (long long)(n[ax] - 1) * st[ax] : m + st[ax];
+        const long long mm = (idx[ax] == 0) ? m + (long long)(n[ax] - 1) * st[ax] : m - st[ax];
+        const float4 p4 = ld4f(u + mp), q4 = ld4f(u + mm);
+        const float ps[4] = {p4.x, p4.y, p4.z, p4.w}, qs[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            float vp = (l[s] & bp[ax]) ? ps[s] - c[s] : 0.f;
+            float vm = (l[s] & bm[ax]) ? qs[s] - c[s] : 0.f;
+            if (bc[ax] == kOpen) {
+                if (idx[ax] == 0) vm = vp;
+                if (idx[ax] == n[ax] - 1) vp = vm;
+            }
+            acc[s] += cc[ax] * (vp + vm);
+        }
+    }
+    return make_float4(acc[0], acc[1], acc[2], acc[3]);
+}
+
+// the components of four sites: -1 insulating, 0 the main one, c > 0 island c
+template <bool ISL>
+__device__ __forceinline__ void comps4(const InsArgs &a, long long m, int cs[4])
+{
+    if constexpr (ISL) {
+        const int4 c = *reinterpret_cast<const int4 *>(a.comp + m);
+        cs[0] = c.x, cs[1] = c.y, cs[2] = c.z, cs[3] = c.w;
+    } else {
+        const uchar4 l = *reinterpret_cast<const uchar4 *>(a.g.lk + m);
+        cs[0] = (l.x & kLkIns) ? -1 : 0, cs[1] = (l.y & kLkIns) ? -1 : 0;
+        cs[2] = (l.z & kLkIns) ? -1 : 0, cs[3] = (l.w & kLkIns) ? -1 : 0;
+    }
+}
+
+template <bool ISL>
+__global__ void ins_csum4_kernel(InsArgs a, const float *v, int slot)
+{
+    float acc = 0.f;
+    for_quads(a.g, [&](long long m, int i0, int, int, float wyz) {
+        const float4 x = ld4f(v + m);
+        int cs[4];
+        comps4<ISL>(a, m, cs);
+        const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float w = wyz * face_w(a.g.bcx, a.g.nx, i0 + s);
+            if (cs[s] == 0) acc += w * xs[s];
+            else if (ISL && cs[s] > 0) atomicAdd(a.isl_acc + (cs[s] - 1), (double)(w * xs[s]));
+        }
+    });
+    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
+}
+
+template <bool ISL>
+__global__ void ins_cshift4_kernel(InsArgs a, float *v, int mslot, int dslot, int fmax)
+{
+    const float cm = (float)(a.ctl->sums[mslot] / a.wsum_c);
+    float acc = 0.f, mx = 0.f;
+    for_quads(a.g, [&](long long m, int i0, int, int, float wyz) {
+        const float4 x = ld4f(v + m);
+        int cs[4];
+        comps4<ISL>(a, m, cs);
+        float xs[4] = {x.x, x.y, x.z, x.w};
+        float rs[4] = {0.f, 0.f, 0.f, 0.f};
+        if (dslot >= 0) {
+            const float4 r = ld4f(a.r + m);
+            rs[0] = r.x, rs[1] = r.y, rs[2] = r.z, rs[3] = r.w;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int c = cs[s];
+            xs[s] = (c < 0) ? 0.f : xs[s] - ((!ISL || c == 0) ? cm : (float)(a.isl_acc[c - 1] / a.isl_w[c - 1]));
+            mx = fmaxf(mx, fabsf(xs[s]));
+            if (dslot >= 0) acc += wyz * face_w(a.g.bcx, a.g.nx, i0 + s) * rs[s] * xs[s];
+        }
+        st4f(v + m, make_float4(xs[0], xs[1], xs[2], xs[3]));
+    });
+    if (dslot >= 0) finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[dslot]);
+    if (!fmax) return;
+    __shared__ float shf[32];
+    __shared__ int flag;
+    const float bmx = block_max(mx, shf);
+    if (threadIdx.x == 0) a.blockred[blockIdx.x] = (double)bmx;
+    if (!last_block(&a.ctl->ticket, gridDim.x, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+        const double w = ((volatile double *)a.blockred)[q];
+        t = w > t ? w : t;
+    }
+    const float tm = block_max((float)t, shf);
+    if (threadIdx.x == 0) {
+        a.ctl->ticket = 0u;
+        a.ctl->fmax = (double)tm;
+        a.ctl->fmean = 0.0;
+    }
+}
+
+__global__ void ins_resid4_kernel(InsArgs a)
+{
+    for_quads(a.g, [&](long long m, int i0, int j, int k, float) {
+        const uchar4 l = *reinterpret_cast<const uchar4 *>(a.g.lk + m);
+        const float4 L = masked_lap4(a.g, a.mu, m, i0, j, k, l);
+        const float4 f = ld4f(a.f + m);
+        st4f(a.r + m, make_float4((l.x & kLkIns) ? 0.f : f.x - L.x, (l.y & kLkIns) ? 0.f : f.y - L.y,
+                                  (l.z & kLkIns) ? 0.f : f.z - L.z, (l.w & kLkIns) ? 0.f : f.w - L.w));
+    });
+}
+
+__global__ void ins_apply4_kernel(InsArgs a, int slot)
+{
+    float acc = 0.f;
+    for_quads(a.g, [&](long long m, int i0, int j, int k, float wyz) {
+        const uchar4 l = *reinterpret_cast<const uchar4 *>(a.g.lk + m);
+        const float4 L = masked_lap4(a.g, a.p, m, i0, j, k, l);
+        const float4 pv = ld4f(a.p + m);
+        const float Ls[4] = {L.x, L.y, L.z, L.w}, ps[4] = {pv.x, pv.y, pv.z, pv.w};
+        const unsigned ls[4] = {l.x, l.y, l.z, l.w};
+        float qs[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            qs[s] = (ls[s] & kLkIns) ? 0.f : Ls[s];
+            acc += wyz * face_w(a.g.bcx, a.g.nx, i0 + s) * ps[s] * qs[s];
+        }
+        st4f(a.q + m, make_float4(qs[0], qs[1], qs[2], qs[3]));
+    });
+    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
+}
+
+__global__ void ins_dir4_kernel(InsArgs a, int num, int den, int first)
+{
+    const double d = a.ctl->sums[den];
+    const float beta = (first || d == 0.0) ? 0.f : (float)(a.ctl->sums[num] / d);
+    const long long nq = a.g.N >> 2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nq; t += (long long)gridDim.x * blockDim.x) {
+        const float4 z = ld4f(a.z + 4 * t), p = ld4f(a.p + 4 * t);
+        st4f(a.p + 4 * t, make_float4(z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, z.w + beta * p.w));
+    }
+}
+
+__global__ void ins_update4_kernel(InsArgs a, int rz, int pq)
+{
+    const double den = a.ctl->sums[pq];
+    const float al = den != 0.0 ? (float)(a.ctl->sums[rz] / den) : 0.f;
+    float mx = 0.f;
+    const long long nq = a.g.N >> 2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nq; t += (long long)gridDim.x * blockDim.x) {
+        float4 r = ld4f(a.r + 4 * t);
+        if (al != 0.f) {
+            const float4 p = ld4f(a.p + 4 * t), q = ld4f(a.q + 4 * t);
+            float4 u = ld4f(a.mu + 4 * t);
+            u = make_float4(u.x + al * p.x, u.y + al * p.y, u.z + al * p.z, u.w + al * p.w);
+            r = make_float4(r.x - al * q.x, r.y - al * q.y, r.z - al * q.z, r.w - al * q.w);
+            st4f(a.mu + 4 * t, u);
+            st4f(a.r + 4 * t, r);
+        }
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(r.x), fabsf(r.y)), fmaxf(fabsf(r.z), fabsf(r.w))));
+    }
+    __shared__ float shf[32];
+    __shared__ int flag;
+    const float bm = block_max(mx, shf);
+    if (threadIdx.x == 0) a.blockred[blockIdx.x] = (double)bm;
+    if (!last_block(&a.ctl->ticket, gridDim.x, &flag)) return;
+    double t = 0.0;
+    for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+        const double v = ((volatile double *)a.blockred)[q];
+        t = v > t ? v : t;
+    }
+    const float tm = block_max((float)t, shf);
+    if (threadIdx.x == 0) {
+        a.ctl->ticket = 0u;
+        a.ctl->res = a.ctl->fmax > 0.0 ? (double)tm / a.ctl->fmax : (double)tm;
     }
 }
 
@@ -449,7 +671,7 @@ __global__ void ins_dir_kernel(InsArgs a, int num, int den, int first)
 // q = A p, sums[slot] = sum_c w p q
 __global__ void ins_apply_kernel(InsArgs a, int slot)
 {
-    double acc = 0.0;
+    float acc = 0.f;   // FP32 per thread, FP64 over the threads and blocks
     for_sites(a.g, [&](long long m, int i, int j, int k, float w) {
         const unsigned l = a.g.lk[m];
         if (l & kLkIns) {
@@ -458,9 +680,9 @@ __global__ void ins_apply_kernel(InsArgs a, int slot)
         }
         const float v = masked_lap(a.g, a.p, m, i, j, k, l);
         a.q[m] = v;
-        acc += (double)(w * a.p[m] * v);
+        acc += w * a.p[m] * v;
     });
-    finish_sum(a.ctl, a.blockred, acc, &a.ctl->sums[slot]);
+    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
 }
 
 // alpha = sums[rz] / sums[pq] (the operator is negative semi-definite: both sums are
@@ -525,12 +747,22 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
     pz.mu = ip.z;
     pz.f = ip.r;
     long long nl = 0;
+    // four sites per thread where rows hold whole 16-byte quads
+    const bool quad = (a.g.nx % 4) == 0;
     // v -= the weighted mean of v's component (the constants of each component are the
     // operator's null space)
     auto project = [&](float *v, int dslot, int fmax) -> bool {
         if (ip.n_isl > 0 && cudaMemsetAsync(ip.isl_acc, 0, 8 * (size_t)ip.n_isl, s) != cudaSuccess) return false;
-        ins_csum_kernel<<<nb, kT, 0, s>>>(a, v, 4);
-        ins_cshift_kernel<<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
+        if (quad && a.islands) {
+            ins_csum4_kernel<true><<<nb, kT, 0, s>>>(a, v, 4);
+            ins_cshift4_kernel<true><<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
+        } else if (quad) {
+            ins_csum4_kernel<false><<<nb, kT, 0, s>>>(a, v, 4);
+            ins_cshift4_kernel<false><<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
+        } else {
+            ins_csum_kernel<<<nb, kT, 0, s>>>(a, v, 4);
+            ins_cshift_kernel<<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
+        }
         nl += 2;
         return cudaGetLastError() == cudaSuccess;
     };
@@ -540,17 +772,24 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
         return project(ip.z, rzslot, 0);
     };
     if (!project(a.f, -1, 1)) return TDGL_ERR_CUDA;   // compatible right-hand side on every component
-    ins_resid_kernel<<<nb, kT, 0, s>>>(a);
+    if (quad) ins_resid4_kernel<<<nb, kT, 0, s>>>(a);
+    else ins_resid_kernel<<<nb, kT, 0, s>>>(a);
     ++nl;
     if (!precondition(5)) return TDGL_ERR_CUDA;
-    ins_dir_kernel<<<nb, kT, 0, s>>>(a, 5, 5, 1);
+    if (quad) ins_dir4_kernel<<<nb, kT, 0, s>>>(a, 5, 5, 1);
+    else ins_dir_kernel<<<nb, kT, 0, s>>>(a, 5, 5, 1);
     ++nl;
     const int cap = iters > 0 ? iters : max_iters;
     int it = 0, rc = TDGL_OK;
     for (; it < cap; ++it) {
         const int rz = (it & 1) ? 6 : 5, rzn = (it & 1) ? 5 : 6;
-        ins_apply_kernel<<<nb, kT, 0, s>>>(a, 7);
-        ins_update_kernel<<<nb, kT, 0, s>>>(a, rz, 7);
+        if (quad) {
+            ins_apply4_kernel<<<nb, kT, 0, s>>>(a, 7);
+            ins_update4_kernel<<<nb, kT, 0, s>>>(a, rz, 7);
+        } else {
+            ins_apply_kernel<<<nb, kT, 0, s>>>(a, 7);
+            ins_update_kernel<<<nb, kT, 0, s>>>(a, rz, 7);
+        }
         nl += 2;
         if (cudaGetLastError() != cudaSuccess) return TDGL_ERR_CUDA;
         if (iters <= 0) {
@@ -573,7 +812,8 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
             break;
         }
         if (!precondition(rzn)) return TDGL_ERR_CUDA;
-        ins_dir_kernel<<<nb, kT, 0, s>>>(a, rzn, rz, 0);
+        if (quad) ins_dir4_kernel<<<nb, kT, 0, s>>>(a, rzn, rz, 0);
+        else ins_dir_kernel<<<nb, kT, 0, s>>>(a, rzn, rz, 0);
         ++nl;
     }
     // zero weighted mean on every component, mu = 0 on insulating sites
