@@ -205,7 +205,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
         if (INIT) {
             mu_n = ldx<CG>(mu2 + q0 + plq * k0);
             al_n = ldx<CG>(al2 + q0 + plq * k0);
-            if (guess) pg_n = ldx<CG>(guess2 + q0 + plq * k0);
+            if (guess && (!a.guess_odd_only || ((j + k0) & 1))) pg_n = ldx<CG>(guess2 + q0 + plq * k0);
         } else if (!RHS) {
             b_n = ldx<CG>(bq + q0 + plq * k0);
             D_n = ldx<CG>(Dq + q0 + plq * k0);
@@ -232,7 +232,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 if (INIT) {
                     mu_n = ldx<CG>(mu2 + q + plq);
                     al_n = ldx<CG>(al2 + q + plq);
-                    if (guess) pg_n = ldx<CG>(guess2 + q + plq);
+                    if (guess && (!a.guess_odd_only || ((j + k + 1) & 1))) pg_n = ldx<CG>(guess2 + q + plq);
                 } else if (!RHS) {
                     b_n = ldx<CG>(bq + q + plq);
                     D_n = ldx<CG>(Dq + q + plq);
@@ -418,7 +418,7 @@ __device__ __forceinline__ void sweep2_body(const SweepArgs &a, int kz, int bx, 
                 bout[q] = make_float4(b0.x, b0.y, b1.x, b1.y);
                 Dout[q] = make_float4(D0.x, D0.y, D1.x, D1.y);
                 // the coming Poisson solve starts from a mu^(n-1) + b mu^(n-2), written over the latter
-                if (guess)
+                if (guess && (!a.guess_odd_only || ((j + k) & 1)))
                     guess2[q] = make_float2(a.ex_a * muc.x + a.ex_b * (pgc.x - offP),
                                             a.ex_a * muc.y + a.ex_b * (pgc.y - offP));
             } else {

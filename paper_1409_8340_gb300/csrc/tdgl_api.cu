@@ -36,7 +36,8 @@ void use_mu_buffer(tdgl_handle *h, int q)
 // ctl->mu_off[q]; nothing to do without one)
 int mu_materialize(tdgl_handle *h, int q)
 {
-    if (h->lk || h->batch_owned || !h->mu_buf[q]) return TDGL_OK;
+    if (h->lk || h->batch_owned || !h->mu_buf[q] || !h->mu_pend[q]) return TDGL_OK;
+    h->mu_pend[q] = 0;
     return launch_mu_materialize(h->g.N, h->mu_buf[q], h->ctl, q, h->stream) == cudaSuccess ? TDGL_OK : TDGL_ERR_CUDA;
 }
 
@@ -713,6 +714,7 @@ int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double
     h->mu_solved = 0;   // f no longer belongs to mu
     h->prev_valid = 0;  // no mu of an earlier step to extrapolate from
     h->guess_ready = 0;
+    h->mu_pend[0] = h->mu_pend[1] = 0;   // the control block (and its pending means) was cleared
     return cuda_err(cudaStreamSynchronize(s));
 }
 
@@ -734,6 +736,7 @@ int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_m
     h->mu_solved = 0;   // f no longer belongs to mu
     h->prev_valid = 0;  // no mu of an earlier step to extrapolate from
     h->guess_ready = 0;
+    h->mu_pend[0] = h->mu_pend[1] = 0;   // the control block (and its pending means) was cleared
     return cuda_err(cudaStreamSynchronize(s));
 }
 
@@ -766,6 +769,7 @@ int tdgl_set_mu_prev(tdgl_handle *h, const float *in, int32_t in_on_host)
                         s) != cudaSuccess)
         return TDGL_ERR_CUDA;
     if (cudaMemsetAsync(&h->ctl->mu_off[1 - h->mu_q], 0, sizeof(double), s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->mu_pend[1 - h->mu_q] = 0;
     if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
     h->prev_valid = 1;
     return TDGL_OK;
@@ -829,6 +833,10 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
         a.mu_guess = h->mu_buf[1 - h->mu_q];
         a.ex_a = h->prev_valid ? 2.f : 1.f;
         a.ex_b = h->prev_valid ? -1.f : 0.f;
+        // the V-cycle's first pass reads only the colour-1 rows of the guess when the zebra
+        // colouring (j + k) % 2 is proper and the finest level is smoothed
+        const bool proper = (c.bc[1] == TDGL_OPEN || (c.ny % 2) == 0) && (c.bc[2] == TDGL_OPEN || c.nz == 1 || (c.nz % 2) == 0);
+        a.guess_odd_only = (proper && h->pa.nlevels > 1) ? 1 : 0;
         h->guess_ready = 1;
     }
     ev_rec(h, 0);
@@ -1013,6 +1021,7 @@ int tdgl_solve_mu(tdgl_handle *h)
         if (!h->pgraph[gk] && !build_poisson_graph(h)) h->pgraph_fail = 1;
         if (h->pgraph[gk]) {
             if (cudaGraphLaunch(h->pgraph[gk], s) != cudaSuccess) return TDGL_ERR_CUDA;
+            h->mu_pend[h->mu_q] = lazy_projection(h, vcycle_mean_fusable(h->pa) && c.poisson_cycles > 0) ? 1 : 0;
             h->last_cycles = c.poisson_cycles;
             h->prof.vcycles += c.poisson_cycles;
             h->prof.kernel_launches += h->pgraph_launches;
@@ -1052,6 +1061,7 @@ int tdgl_solve_mu(tdgl_handle *h)
     }
     if ((lazy_projection(h, fm) ? launch_commit_mean(h->pa, s) : launch_project_mu(h->pa, s, fm)) != cudaSuccess)
         return TDGL_ERR_CUDA;
+    h->mu_pend[h->mu_q] = lazy_projection(h, fm) ? 1 : 0;
     nl += fm ? 1 : 2;
     h->last_cycles = cycles;
     h->prof.vcycles += cycles;
@@ -1196,6 +1206,7 @@ int tdgl_solve_mu_f(tdgl_handle *h)
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
     h->mu_solved = 1;
+    h->guess_ready = 0;   // the guess is formed here, from the state and the previous mu
     long long nl = 1;
     if (launch_f_mean(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
     if (extrapolating(h)) {
@@ -1227,6 +1238,7 @@ int tdgl_solve_mu_f(tdgl_handle *h)
     }
     if ((lazy_projection(h, fm) ? launch_commit_mean(h->pa, s) : launch_project_mu(h->pa, s, fm)) != cudaSuccess)
         return TDGL_ERR_CUDA;
+    h->mu_pend[h->mu_q] = lazy_projection(h, fm) ? 1 : 0;
     if (c.bc[0] == TDGL_OPEN && launch_voltage(h->pa, s) != cudaSuccess) return TDGL_ERR_CUDA;
     h->last_cycles = cycles;
     h->prof.vcycles += cycles;

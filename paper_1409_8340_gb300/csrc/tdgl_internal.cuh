@@ -230,6 +230,10 @@ struct SweepArgs {
     // previous-but-one mu: mu_guess = ex_a mu + ex_b mu_guess (nullptr: none)
     float *mu_guess;
     float ex_a, ex_b;
+    // 1: write the guess on the rows of zebra colour 1 ((j + k) odd) only: the first pass
+    // of the coming V-cycle solves the colour-0 lines from their colour-1 neighbours and
+    // never reads colour-0 values (a proper colouring and a smoothed finest level)
+    int guess_odd_only;
     // init only: the pending mean of mu and of the previous-but-one mu (nullptr: none)
     const double *mu_off, *mu_off_prev;
 };
@@ -472,6 +476,7 @@ struct tdgl_handle {
     float *mu_buf[2];
     int mu_q;
     int prev_valid;            // 1: mu_buf[1 - mu_q] holds the state of the step before
+    int mu_pend[2];            // 1: a pending mean was recorded for the buffer (ctl->mu_off[q])
     int guess_ready;           // 1: the init of this step has written the guess
     CUtensorMap umap0[2];      // the finest level's smoother maps for each mu buffer
     const float *umap0_u[2];
