@@ -75,7 +75,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_sweep_tma.cu",):
+    for f in ("k_sweep_tma.cu", "sweep_tile.cuh", "tma_util.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1409_8340_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -610,6 +610,13 @@ def run_native(args, rank, world, local_rank):
     clk = clocks.stop()
     obs = s.observables()
 
+    # the same steps as one CUDA graph launch with conditional nodes (tdgl_step_resident):
+    # the graph is built by the untimed warm-up call (the loop decides convergence on the
+    # device, so a fixed sweep count is not run through it)
+    resident = None
+    if args.fixed_sweeps == 0:
+        resident = resident_mode(s, p, args, stream)
+
     site_iters = prof["sweeps"] * p.N
     t = torch.tensor([ms, float(site_iters)], dtype=torch.float64, device=dev)
     if dist:
@@ -690,6 +697,7 @@ def run_native(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": METRIC, "steps": args.e2e_steps,
                     "h2d_bytes_per_step": 12 * p.N, "d2h_bytes_per_step": 12 * p.N + 128},
             "gpu_launches": prof["kernel_launches"],
+            "resident_step": dict(resident, vs_host_step=resident["value"] / value) if resident else None,
             "clocks": clk,
             "observables": {"Ex": obs["Ex"], "psi2_mean": obs["psi2_mean"],
                             "vortex_unsigned_per_layer": obs["vortex_unsigned"], "last_sweeps": obs["last_sweeps"],
@@ -701,6 +709,27 @@ def run_native(args, rank, world, local_rank):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def resident_mode(s, p, args, stream):
+    """The timed steps again through tdgl_step_resident: one graph launch (conditional
+    nodes for the sweep loop and the buffer choices) and one synchronisation."""
+    import torch
+    s.step_resident(args.warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    s.profile_enable(True)      # counters only: the resident loop records no phase events
+    e0.record(stream)
+    s.step_resident(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pr = s.profile()
+    s.profile_enable(False)
+    return {"value": pr["sweeps"] * p.N / (ms * 1e-3) / 1e9, "unit": METRIC, "ms_per_step": ms / args.steps,
+            "sweeps_per_step": pr["sweeps"] / max(1, pr["steps"]), "gpu_launches": pr["kernel_launches"],
+            "graph_launches": 1, "host_syncs": 1}
 
 
 def main():

@@ -266,6 +266,23 @@ int tdgl_set_mu_prev(tdgl_handle *h, const float *in, int32_t in_on_host);
  * read the convergence status; returns the first error met. */
 int tdgl_step(tdgl_handle *h, int n_steps);
 
+/* Advance n_steps full time steps like tdgl_step, as ONE CUDA graph launch with a
+ * single synchronisation at the end (the kernel loop of Sec. 4.1 kept on the
+ * device).  A WHILE conditional node runs the steps; in each, IF nodes select the
+ * launch sequence of the state's psi and mu buffers, a nested WHILE node repeats
+ * two Jacobi sweeps until the sweep kernels' own convergence test (Eq. 11) has
+ * decided, and IF nodes select the Poisson solve of the buffer holding the result.
+ * Same kernels and arguments as tdgl_step, so the same results bit for bit.
+ *   The graph is built on the first call (tens of milliseconds) and kept with the
+ * handle.  The first step after creation or a state load (with the extrapolated
+ * Poisson guess: until a previous mu exists) runs launch by launch, as tdgl_step.
+ *   Returns TDGL_ERR_INVALID_ARG for handles the loop does not cover: insulating
+ * sites, poisson_tol > 0, fixed_sweeps > 0, two sweeps per pass, batch members,
+ * slabs and Poisson-only handles.  A step whose Jacobi solve fails (not converged
+ * within max_iter, non-finite, a wait that timed out) stops the loop with the state
+ * of the step before it and the error returned; the steps before it count. */
+int tdgl_step_resident(tdgl_handle *h, int32_t n_steps);
+
 /* Only the implicit psi solve of one step (init, Jacobi sweeps, residual
  * reductions), without the K and mu updates; *sweeps_out may be NULL. */
 int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out);

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtdgl_gb300.so")
-SOURCES = ["tdgl_api.cu", "k_jacobi.cu", "k_poisson.cu", "k_obs.cu", "k_pattern.cu", "tdgl_noalloc.cu", "k_adjoint.cu", "tdgl_adjoint_api.cu", "k_batch.cu", "tdgl_batch_api.cu", "k_pair.cu", "k_insulating.cu", "k_sweep_tma.cu"]
+SOURCES = ["tdgl_api.cu", "tdgl_resident.cu", "k_jacobi.cu", "k_poisson.cu", "k_obs.cu", "k_pattern.cu", "tdgl_noalloc.cu", "k_adjoint.cu", "tdgl_adjoint_api.cu", "k_batch.cu", "tdgl_batch_api.cu", "k_pair.cu", "k_insulating.cu", "k_sweep_tma.cu"]
 HEADERS = ["tdgl_internal.cuh", "sweep_tile.cuh", "mg_tile.cuh", os.path.join("..", "..", "include", "tdgl.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kBX *kBY) init_sweep_kernel(SweepArgs a, int k
 template <bool GEN>
 __global__ void __launch_bounds__(kBX *kBY) sweep_kernel(SweepArgs a, int kz)
 {
-    if (*(volatile int *)&a.ctl->done) return;
+    if (sweep_already_decided(a)) return;
     const DevGrid &g = a.g;
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
@@ -295,7 +295,7 @@ template <int MODE, bool XZ = false, bool MASK = false>
 __global__ void __launch_bounds__(kBX *kBY, 4) sweep2_kernel(SweepArgs a, int kz)
 {
     // MODE 5: a plain sweep that recomputes a known result (no test, no early exit)
-    if ((MODE == 0 || MODE == 3) && *(volatile int *)&a.ctl->done) return;
+    if ((MODE == 0 || MODE == 3) && sweep_already_decided(a)) return;
     float rmax = 0.f, facc = 0.f;
     sweep2_body<MODE, false, XZ, MASK>(a, kz, blockIdx.x, blockIdx.y, blockIdx.z, rmax, facc);
     if (MODE == 2) {

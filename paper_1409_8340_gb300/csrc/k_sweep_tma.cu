@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 {
     constexpr int NS = kStages<RHS>;
     using St = StageT<RHS>;
-    if (!RHS && *(volatile int *)&a.ctl->done) return;
+    if (!RHS && sweep_already_decided(a)) return;
     extern __shared__ __align__(128) unsigned char tma_smem[];
     St *ring = reinterpret_cast<St *>(tma_smem);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(tma_smem + NS * sizeof(St));

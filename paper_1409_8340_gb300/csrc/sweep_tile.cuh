@@ -14,7 +14,7 @@ constexpr int kBY = 8;
 
 // Convergence decision of one sweep (Sec. 3.1, Eq. convergence) on the grid
 // maximum gf of |r|^2 of the sweep's input iterate.  Run by one thread.
-__device__ __forceinline__ void sweep_decide(const SweepArgs &a, float gf, bool init)
+__device__ __forceinline__ void sweep_decide_ctl(const SweepArgs &a, float gf, bool init)
 {
     DevCtl *c = a.ctl;
     int it = init ? 1 : c->iter + 1;
@@ -46,6 +46,32 @@ __device__ __forceinline__ void sweep_decide(const SweepArgs &a, float gf, bool 
     } else {
         c->done = 0;
     }
+}
+
+// The decision, and in the device-resident loop the condition of its sweep loop: every
+// path above ends the solve by max_iter sweeps, so the loop ends.
+__device__ __forceinline__ void sweep_decide(const SweepArgs &a, float gf, bool init)
+{
+    sweep_decide_ctl(a, gf, init);
+    if (a.has_loop) {
+        DevCtl *c = a.ctl;
+        cudaGraphSetConditional(a.loop_cond, c->done ? 0u : 1u);
+        if (c->done) {
+            const bool ok = c->status == TDGL_OK;
+            c->rok = ok ? 1 : 0;
+            cudaGraphSetConditional(a.tail_cond, ok ? (unsigned int)(a.tail_base + c->result) : kNoBranch);
+        }
+    }
+}
+
+// Start of a sweep that the solve may no longer need: true when an earlier sweep has
+// decided (every block then returns); block (0, 0, 0) clears the loop condition.
+__device__ __forceinline__ bool sweep_already_decided(const SweepArgs &a)
+{
+    if (!*(volatile int *)&a.ctl->done) return false;
+    if (a.has_loop && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0)
+        cudaGraphSetConditional(a.loop_cond, 0u);
+    return true;
 }
 
 // Block maximum of |r|^2 into blockred[bid]; the last of nb blocks reduces the

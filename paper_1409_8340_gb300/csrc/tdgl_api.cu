@@ -48,6 +48,10 @@ void drop_poisson_graphs(tdgl_handle *h)
             cudaGraphExecDestroy(h->pgraph[q]);
             h->pgraph[q] = nullptr;
         }
+    if (h->rgraph) {
+        cudaGraphExecDestroy(h->rgraph);
+        h->rgraph = nullptr;
+    }
 }
 
 }  // namespace tdgl
@@ -286,6 +290,21 @@ SweepArgs sweep_args(tdgl_handle *h)
 }
 
 bool extrapolating(const tdgl_handle *h) { return handle_extrapolates(h); }
+
+// The init also writes the coming Poisson solve's guess over mu^(n-2), the buffer other than
+// the state's q: 2 mu^(n-1) - mu^(n-2) with a previous mu (prev), else mu^(n-1)
+void guess_args(const tdgl_handle *h, SweepArgs &a, int q, bool prev)
+{
+    const tdgl_config &c = h->cfg;
+    a.mu_off_prev = &h->ctl->mu_off[1 - q];
+    a.mu_guess = h->mu_buf[1 - q];
+    a.ex_a = prev ? 2.f : 1.f;
+    a.ex_b = prev ? -1.f : 0.f;
+    // the V-cycle's first pass reads only the colour-1 rows of the guess when the zebra
+    // colouring (j + k) % 2 is proper and the finest level is smoothed
+    const bool proper = (c.bc[1] == TDGL_OPEN || (c.ny % 2) == 0) && (c.bc[2] == TDGL_OPEN || c.nz == 1 || (c.nz % 2) == 0);
+    a.guess_odd_only = (proper && h->pa.nlevels > 1) ? 1 : 0;
+}
 
 void ev_rec(tdgl_handle *h, int i)
 {
@@ -649,8 +668,7 @@ static int create_impl(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *
 void tdgl_destroy(tdgl_handle *h)
 {
     if (!h) return;
-    for (int q = 0; q < 6; ++q)
-        if (h->pgraph[q]) cudaGraphExecDestroy(h->pgraph[q]);
+    drop_poisson_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->ev_made)
         for (int i = 0; i < tdgl_handle::kEvents; ++i) cudaEventDestroy(h->ev[i]);
@@ -828,15 +846,7 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     a.dst_index = ia;
     a.mu_off = &h->ctl->mu_off[h->mu_q];   // the pending projection of mu
     if (extrapolating(h)) {
-        // the init also writes the coming Poisson solve's guess over mu^(n-2)
-        a.mu_off_prev = &h->ctl->mu_off[1 - h->mu_q];
-        a.mu_guess = h->mu_buf[1 - h->mu_q];
-        a.ex_a = h->prev_valid ? 2.f : 1.f;
-        a.ex_b = h->prev_valid ? -1.f : 0.f;
-        // the V-cycle's first pass reads only the colour-1 rows of the guess when the zebra
-        // colouring (j + k) % 2 is proper and the finest level is smoothed
-        const bool proper = (c.bc[1] == TDGL_OPEN || (c.ny % 2) == 0) && (c.bc[2] == TDGL_OPEN || c.nz == 1 || (c.nz % 2) == 0);
-        a.guess_odd_only = (proper && h->pa.nlevels > 1) ? 1 : 0;
+        guess_args(h, a, h->mu_q, h->prev_valid != 0);
         h->guess_ready = 1;
     }
     ev_rec(h, 0);
@@ -920,8 +930,11 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
             batch = launched + 4;
         }
     }
-    if (ctl.status != TDGL_OK) return ctl.status;
-    if (!ctl.done) return TDGL_ERR_NOT_CONVERGED;
+    if (ctl.status != TDGL_OK || !ctl.done) {
+        // the init has written the Poisson guess over the previous mu: a retry starts afresh
+        if (extrapolating(h)) h->prev_valid = h->guess_ready = 0;
+        return ctl.status != TDGL_OK ? ctl.status : TDGL_ERR_NOT_CONVERGED;
+    }
     if (ctl.redo) {
         // the first sweep of the deciding pass is the result: recompute it from
         // the pass's input into the pass's output buffer
@@ -1298,6 +1311,7 @@ int tdgl_step(tdgl_handle *h, int n_steps)
         h->pend_P = h->prof_on;
         ++h->step;
         ++h->prof.steps;
+        h->stepped = 1;
     }
     return cuda_err(cudaGetLastError());
 }
@@ -1396,3 +1410,16 @@ int tdgl_pattern_ex(const tdgl_config *grid, const tdgl_shape *shapes, int64_t n
 }
 
 }  // extern "C"
+
+// Pieces of the host-driven step shared with the device-resident step loop
+namespace tdgl {
+SweepArgs step_sweep_args(tdgl_handle *h) { return sweep_args(h); }
+void step_guess_args(const tdgl_handle *h, SweepArgs &a, int q) { guess_args(h, a, q, true); }
+long long step_poisson_sequence(tdgl_handle *h, cudaStream_t s, cudaError_t *err) { return poisson_sequence(h, s, err); }
+bool step_lazy_projection(const tdgl_handle *h)
+{
+    return lazy_projection(h, h->cfg.poisson_cycles > 0 && vcycle_mean_fusable(h->pa));
+}
+bool step_pairs(const tdgl_handle *h) { return h->cfg.sweeps_per_pass == 2 && pair_supported(h->g); }
+int step_read_ctl(tdgl_handle *h, DevCtl *out) { return read_ctl(h, out); }
+}  // namespace tdgl

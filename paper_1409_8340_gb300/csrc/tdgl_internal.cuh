@@ -76,6 +76,13 @@ struct DevCtl {
     // mu_off[q] (the zero-mode projection of a fixed-cycle solve is applied where mu is
     // read, or when the state is handed out)
     double mu_off[2];
+    // the device-resident step loop (tdgl_step_resident)
+    int rcur, rq;              // psi buffer and mu buffer of the state
+    int rleft, rdone;          // steps still to run; steps run (their solves succeeded)
+    int rspare, rlast;         // (unused); sweeps of the last step run
+    int rok, rpad;             // 1: this step's Jacobi solve succeeded (its tail runs)
+    long long rsweeps;         // sweeps of the steps run
+    long long rloops;          // two-sweep loop iterations of all steps entered
 };
 
 // ----------------------------------------------------------------------------
@@ -236,7 +243,15 @@ struct SweepArgs {
     int guess_odd_only;
     // init only: the pending mean of mu and of the previous-but-one mu (nullptr: none)
     const double *mu_off, *mu_off_prev;
+    // device-resident step loop (has_loop 1): the condition of the WHILE graph node that
+    // repeats the sweeps, set by the block that decides a sweep (1 while the solve goes on)
+    // and by a sweep that finds the solve already decided (0); and, when the decision ends
+    // the solve, the value of the SWITCH node of the step's tail: tail_base + the result's
+    // buffer after a successful solve, else kNoBranch
+    cudaGraphConditionalHandle loop_cond, tail_cond;
+    int has_loop, tail_base;
 };
+constexpr unsigned int kNoBranch = 6;
 
 cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
 // the guess of launch_init_sweep on its own: P = a S + b P over N sites
@@ -510,6 +525,11 @@ struct tdgl_handle {
     int pgraph_fail;
     int poisson_calls;
     long long pgraph_launches;
+    // the device-resident step loop: one graph of conditional nodes for any number of steps
+    cudaGraphExec_t rgraph;
+    int rgraph_fail;
+    int stepped;                 // 1: a host-driven step has run on the handle
+    long long rgraph_launches;   // launches of one step outside the sweep loop
     tdgl::TmaMaps tmaps;       // its tensor maps
     tdgl::InsPoisson ip;
     // profiling
@@ -526,4 +546,11 @@ bool handle_extrapolates(const tdgl_handle *h);
 void use_mu_buffer(tdgl_handle *h, int q);
 int mu_materialize(tdgl_handle *h, int q);
 void drop_poisson_graphs(tdgl_handle *h);
+// pieces of the host-driven step (tdgl_api.cu) used by the device-resident loop
+SweepArgs step_sweep_args(tdgl_handle *h);
+void step_guess_args(const tdgl_handle *h, SweepArgs &a, int q);
+long long step_poisson_sequence(tdgl_handle *h, cudaStream_t s, cudaError_t *err);
+bool step_lazy_projection(const tdgl_handle *h);
+bool step_pairs(const tdgl_handle *h);
+int step_read_ctl(tdgl_handle *h, DevCtl *out);
 }  // namespace tdgl

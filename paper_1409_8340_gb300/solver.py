@@ -239,6 +239,10 @@ class Solver:
     def step(self, n: int = 1):
         check(self._L.tdgl_step(self._h, int(n)), "tdgl_step")
 
+    def step_resident(self, n: int = 1):
+        """n steps as one CUDA graph launch (conditional nodes), one synchronisation."""
+        check(self._L.tdgl_step_resident(self._h, int(n)), "tdgl_step_resident")
+
     def solve_psi(self) -> int:
         n = ctypes.c_int32()
         check(self._L.tdgl_solve_psi(self._h, ctypes.byref(n)), "tdgl_solve_psi")
