@@ -423,7 +423,7 @@ def xz_mode(dev, steps: int = 20, relax: int = 20, quanta_x: int = 600):
                             "vortex_unsigned_per_layer": obs["vortex_unsigned"]}}
 
 
-def insulating_mode(dev, steps: int = 20, relax: int = 20):
+def insulating_mode(dev, steps: int = 20, relax: int = 20, nz: int = 256):
     """The mesoscopic workload with insulating inclusions (Sec. 3.4 (ii)): the same
     ellipsoids as the metallic ones, every fourth marked insulating (links next to them
     removed), the rest eps = -1; the Poisson solve is 2 CG iterations preconditioned by
@@ -434,7 +434,7 @@ def insulating_mode(dev, steps: int = 20, relax: int = 20):
 
     from paper_1409_8340_gb300 import inputs
     from paper_1409_8340_gb300.solver import Solver, pattern_ex
-    w = workload(0.025)
+    w = workload(0.025, None if nz == 256 else nz)
     p = w.params
     p.poisson_cycles = 2          # two CG iterations per step, each preconditioned by a V-cycle
     cand = np.asarray(w.candidates)
@@ -469,7 +469,7 @@ def insulating_mode(dev, steps: int = 20, relax: int = 20):
     frac_ins = float(ins.float().mean())
     del s, alpha, ins
     torch.cuda.empty_cache()
-    return {"workload": "mesoscopic_512x512x256 with insulating inclusions (every 4th ellipsoid), J 0.025",
+    return {"workload": f"mesoscopic_512x512x{nz} with insulating inclusions (every 4th ellipsoid), J 0.025",
             "insulating_fraction": frac_ins, "inclusion_fraction": marked / p.N,
             "value": prof["sweeps"] * p.N / (ms * 1e-3) / 1e9, "unit": METRIC, "steps": steps,
             "ms_per_step": ms / steps, "sweeps_per_step": prof["sweeps"] / max(1, prof["steps"]),
@@ -753,7 +753,7 @@ def main():
         elif args.only == "pattern":
             out = pattern_mode(dev)
         elif args.only == "insulating":
-            out = insulating_mode(dev)
+            out = insulating_mode(dev, min(args.steps, 20), min(args.relax, 20), args.nz)
         else:
             out = adjoint_mode(dev)
         print(json.dumps({"mode": args.only, **out}), flush=True)

@@ -11,7 +11,7 @@
 // coefficients, so the constant-coefficient multigrid becomes a preconditioner:
 // conjugate gradients in the trapezoid-weighted inner product (in which the operator
 // is symmetric), each iteration preconditioned by one symmetric V-cycle of the plain
-// operator, the right-hand side and the iterates projected on every component; sums
+// operator, the right-hand side and the result projected on every component; sums
 // in FP64, bulk in FP32.
 #include <float.h>
 
@@ -57,14 +57,15 @@ __device__ __forceinline__ long long nbr(const DevGrid &g, long long m, int i, i
                      : (k == 0 ? m + (long long)(g.nz - 1) * sz : m - sz);
 }
 
-// Block sum of v into blockred[bid]; the last block writes the total to *out.
-__device__ __forceinline__ void finish_sum(DevCtl *ctl, double *blockred, double v, double *out)
+// Block sum of v into blockred[bid]; the last block writes the total to *out and
+// returns true (every other block false).
+__device__ __forceinline__ bool finish_sum(DevCtl *ctl, double *blockred, double v, double *out)
 {
     __shared__ double shd[32];
     __shared__ int flag;
     double s = block_sum(v, shd);
     if (threadIdx.x == 0) blockred[blockIdx.x] = s;
-    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return;
+    if (!last_block(&ctl->ticket, gridDim.x, &flag)) return false;
     double t = 0.0;
     for (unsigned int q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += ((volatile double *)blockred)[q];
     t = block_sum(t, shd);
@@ -72,6 +73,7 @@ __device__ __forceinline__ void finish_sum(DevCtl *ctl, double *blockred, double
         ctl->ticket = 0u;
         *out = t;
     }
+    return true;
 }
 
 }  // namespace
@@ -353,7 +355,16 @@ struct InsArgs {
     double *isl_acc;
     double wsum_c;
     int islands;               // 0: every conducting site is in the main component
+    int n_isl;
 };
+
+// After a component sum: the last block turns each island's sum into its weighted mean
+// (isl_acc, read by the shift that follows), the other blocks' atomics all done.
+__device__ __forceinline__ void island_means(const InsArgs &a)
+{
+    for (int c = threadIdx.x; c < a.n_isl; c += blockDim.x)
+        a.isl_acc[c] = ((volatile double *)a.isl_acc)[c] / a.isl_w[c];
+}
 
 // Rows (j, k) of the grid spread over the blocks, sites of a row over the threads:
 // (i, j, k) and the face weights without per-site division.
@@ -385,29 +396,26 @@ __global__ void ins_csum_kernel(InsArgs a, const float *v, int slot)
         if (c == 0) acc += w * v[m];
         else if (c > 0) atomicAdd(a.isl_acc + (c - 1), (double)(w * v[m]));
     });
-    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
+    if (finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]) && a.islands) island_means(a);
 }
 
-// v -= its component's weighted mean, 0 on insulating sites.  dslot >= 0: also
-// sums[dslot] = sum w r v.  fmax: also ctl->fmax = max|v| and ctl->fmean = 0 (the
-// level-0 multigrid kernels subtract ctl->fmean, which the preconditioner must not).
-__global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int dslot, int fmax)
+// v -= its component's weighted mean (the islands' from island_means), 0 on insulating
+// sites.  fmax: also ctl->fmax = max|v| and ctl->fmean = 0 (the level-0 multigrid kernels
+// subtract ctl->fmean, which the preconditioner must not).
+__global__ void ins_cshift_kernel(InsArgs a, float *v, int mslot, int fmax)
 {
     const float cm = (float)(a.ctl->sums[mslot] / a.wsum_c);
-    float acc = 0.f;   // FP32 per thread, FP64 over the threads and blocks
     float mx = 0.f;
-    for_sites(a.g, [&](long long m, int, int, int, float w) {
+    for_sites(a.g, [&](long long m, int, int, int, float) {
         const int c = comp_of(a, m);
         if (c < 0) {
             v[m] = 0.f;
             return;
         }
-        const float x = v[m] - (c == 0 ? cm : (float)(a.isl_acc[c - 1] / a.isl_w[c - 1]));
+        const float x = v[m] - (c == 0 ? cm : (float)a.isl_acc[c - 1]);
         v[m] = x;
         mx = fmaxf(mx, fabsf(x));
-        if (dslot >= 0) acc += w * a.r[m] * x;
     });
-    if (dslot >= 0) finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[dslot]);
     if (!fmax) return;
     __shared__ float shf[32];
     __shared__ int flag;
@@ -436,11 +444,27 @@ __device__ __forceinline__ void for_quads(const DevGrid &g, F &&fn)
 {
     const long long nq = g.N >> 2;
     const int qrow = g.nx >> 2;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nq; t += (long long)gridDim.x * blockDim.x) {
-        const long long row = t / qrow;
-        const int i0 = (int)(t - row * qrow) * 4;
-        const int j = (int)(row % g.ny), k = (int)(row / g.ny);
-        fn(row * g.nx + i0, i0, j, k, face_w(g.bcy, g.ny, j) * face_w(g.bcz, g.nz, k));
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nq) return;
+    // the quad's x index qi, row j and plane k, divided out once and then advanced by the
+    // stride's own (dq, dj, dk) with carries: no 64-bit division per quad
+    const long long row0 = t / qrow, srow = stride / qrow;
+    int qi = (int)(t - row0 * qrow), j = (int)(row0 % g.ny), k = (int)(row0 / g.ny);
+    const int dq = (int)(stride - srow * qrow), dj = (int)(srow % g.ny), dk = (int)(srow / g.ny);
+    for (; t < nq; t += stride) {
+        fn(((long long)k * g.ny + j) * g.nx + 4 * qi, 4 * qi, j, k, face_w(g.bcy, g.ny, j) * face_w(g.bcz, g.nz, k));
+        qi += dq;
+        j += dj;
+        k += dk;
+        if (qi >= qrow) {
+            qi -= qrow;
+            ++j;
+        }
+        if (j >= g.ny) {
+            j -= g.ny;
+            ++k;
+        }
     }
 }
 
@@ -525,34 +549,27 @@ __global__ void ins_csum4_kernel(InsArgs a, const float *v, int slot)
             else if (ISL && cs[s] > 0) atomicAdd(a.isl_acc + (cs[s] - 1), (double)(w * xs[s]));
         }
     });
-    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
+    if (finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]) && ISL) island_means(a);
 }
 
 template <bool ISL>
-__global__ void ins_cshift4_kernel(InsArgs a, float *v, int mslot, int dslot, int fmax)
+__global__ void ins_cshift4_kernel(InsArgs a, float *v, int mslot, int fmax)
 {
     const float cm = (float)(a.ctl->sums[mslot] / a.wsum_c);
-    float acc = 0.f, mx = 0.f;
-    for_quads(a.g, [&](long long m, int i0, int, int, float wyz) {
+    float mx = 0.f;
+    for_quads(a.g, [&](long long m, int, int, int, float) {
         const float4 x = ld4f(v + m);
         int cs[4];
         comps4<ISL>(a, m, cs);
         float xs[4] = {x.x, x.y, x.z, x.w};
-        float rs[4] = {0.f, 0.f, 0.f, 0.f};
-        if (dslot >= 0) {
-            const float4 r = ld4f(a.r + m);
-            rs[0] = r.x, rs[1] = r.y, rs[2] = r.z, rs[3] = r.w;
-        }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int c = cs[s];
-            xs[s] = (c < 0) ? 0.f : xs[s] - ((!ISL || c == 0) ? cm : (float)(a.isl_acc[c - 1] / a.isl_w[c - 1]));
+            xs[s] = (c < 0) ? 0.f : xs[s] - ((!ISL || c == 0) ? cm : (float)a.isl_acc[c - 1]);
             mx = fmaxf(mx, fabsf(xs[s]));
-            if (dslot >= 0) acc += wyz * face_w(a.g.bcx, a.g.nx, i0 + s) * rs[s] * xs[s];
         }
         st4f(v + m, make_float4(xs[0], xs[1], xs[2], xs[3]));
     });
-    if (dslot >= 0) finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[dslot]);
     if (!fmax) return;
     __shared__ float shf[32];
     __shared__ int flag;
@@ -570,6 +587,26 @@ __global__ void ins_cshift4_kernel(InsArgs a, float *v, int mslot, int dslot, in
         a.ctl->fmax = (double)tm;
         a.ctl->fmean = 0.0;
     }
+}
+
+// sums[slot] = sum w r v (r is zero on insulating sites)
+__global__ void ins_dot4_kernel(InsArgs a, const float *v, int slot)
+{
+    float acc = 0.f;
+    for_quads(a.g, [&](long long m, int i0, int, int, float wyz) {
+        const float4 x = ld4f(v + m), r = ld4f(a.r + m);
+        const float xs[4] = {x.x, x.y, x.z, x.w}, rs[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc += wyz * face_w(a.g.bcx, a.g.nx, i0 + s) * rs[s] * xs[s];
+    });
+    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
+}
+
+__global__ void ins_dot_kernel(InsArgs a, const float *v, int slot)
+{
+    float acc = 0.f;   // FP32 per thread, FP64 over the threads and blocks
+    for_sites(a.g, [&](long long m, int, int, int, float w) { acc += w * a.r[m] * v[m]; });
+    finish_sum(a.ctl, a.blockred, (double)acc, &a.ctl->sums[slot]);
 }
 
 __global__ void ins_resid4_kernel(InsArgs a)
@@ -609,7 +646,12 @@ __global__ void ins_dir4_kernel(InsArgs a, int num, int den, int first)
     const float beta = (first || d == 0.0) ? 0.f : (float)(a.ctl->sums[num] / d);
     const long long nq = a.g.N >> 2;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nq; t += (long long)gridDim.x * blockDim.x) {
-        const float4 z = ld4f(a.z + 4 * t), p = ld4f(a.p + 4 * t);
+        const float4 z = ld4f(a.z + 4 * t);
+        if (beta == 0.f) {   // the first direction (or a restart): p = z, the old p not read
+            st4f(a.p + 4 * t, z);
+            continue;
+        }
+        const float4 p = ld4f(a.p + 4 * t);
         st4f(a.p + 4 * t, make_float4(z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, z.w + beta * p.w));
     }
 }
@@ -719,6 +761,20 @@ __global__ void ins_update_kernel(InsArgs a, int rz, int pq)
     }
 }
 
+// Blocks of a quad pass: one resident wave.  Every block's grid-stride walk then moves
+// through the grid with the others, so the stencil's neighbours in the planes above and
+// below are still in L2 when they are read (with more blocks than fit, the late blocks
+// start far behind the early ones and those reads go to DRAM again).
+template <class K>
+static int wave_blocks(K kern)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 4096;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kT, 0) != cudaSuccess || per < 1) per = 1;
+    return per * sms < 4096 ? per * sms : 4096;
+}
+
 int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol, int iters, int max_iters,
                          cudaStream_t s, int *done, long long *launches)
 {
@@ -737,8 +793,15 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
     a.isl_acc = ip.isl_acc;
     a.wsum_c = ip.wsum_c;
     a.islands = ip.n_isl > 0 ? 1 : 0;
+    a.n_isl = ip.n_isl;
     // one block per row (up to 4096 blocks, grid-stride beyond): within the partial-sum slots
     const int nb = a.g.ny * a.g.nz < 4096 ? a.g.ny * a.g.nz : 4096;
+    // the quad passes: a resident wave each
+    const int w_sum = a.islands ? wave_blocks(ins_csum4_kernel<true>) : wave_blocks(ins_csum4_kernel<false>);
+    const int w_shift = a.islands ? wave_blocks(ins_cshift4_kernel<true>) : wave_blocks(ins_cshift4_kernel<false>);
+    const int w_res = wave_blocks(ins_resid4_kernel), w_dot = wave_blocks(ins_dot4_kernel);
+    const int w_app = wave_blocks(ins_apply4_kernel), w_upd = wave_blocks(ins_update4_kernel);
+    const int w_dir = wave_blocks(ins_dir4_kernel);
     const size_t bytes = 4 * (size_t)a.g.N;
     // the preconditioner: one V-cycle of the plain operator on r, from z = 0
     PoissonArgs pz = pa;
@@ -746,37 +809,52 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
     pz.lev[0].r = ip.r;
     pz.mu = ip.z;
     pz.f = ip.r;
+    pz.umap[0] = ip.zmap;
+    pz.umap_u[0] = ip.zmap_u;
     long long nl = 0;
     // four sites per thread where rows hold whole 16-byte quads
     const bool quad = (a.g.nx % 4) == 0;
     // v -= the weighted mean of v's component (the constants of each component are the
     // operator's null space)
-    auto project = [&](float *v, int dslot, int fmax) -> bool {
+    auto project = [&](float *v, int fmax) -> bool {
         if (ip.n_isl > 0 && cudaMemsetAsync(ip.isl_acc, 0, 8 * (size_t)ip.n_isl, s) != cudaSuccess) return false;
         if (quad && a.islands) {
-            ins_csum4_kernel<true><<<nb, kT, 0, s>>>(a, v, 4);
-            ins_cshift4_kernel<true><<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
+            ins_csum4_kernel<true><<<w_sum, kT, 0, s>>>(a, v, 4);
+            ins_cshift4_kernel<true><<<w_shift, kT, 0, s>>>(a, v, 4, fmax);
         } else if (quad) {
-            ins_csum4_kernel<false><<<nb, kT, 0, s>>>(a, v, 4);
-            ins_cshift4_kernel<false><<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
+            ins_csum4_kernel<false><<<w_sum, kT, 0, s>>>(a, v, 4);
+            ins_cshift4_kernel<false><<<w_shift, kT, 0, s>>>(a, v, 4, fmax);
         } else {
             ins_csum_kernel<<<nb, kT, 0, s>>>(a, v, 4);
-            ins_cshift_kernel<<<nb, kT, 0, s>>>(a, v, 4, dslot, fmax);
+            ins_cshift_kernel<<<nb, kT, 0, s>>>(a, v, 4, fmax);
         }
         nl += 2;
         return cudaGetLastError() == cudaSuccess;
     };
+    // z = M r by one V-cycle, and sums[rzslot] = (r, z).  z is not projected: its part in the
+    // operator's null space (a constant on each component, any value on insulating sites)
+    // is orthogonal to r and to every A p in the weighted inner product, so it changes no
+    // step length or direction's image; it only adds null-space parts to mu, which the
+    // closing projection removes.
+    // Where the cycle's closing finest-level passes can sum (r, z) as they write z, they do.
+    const bool fused_dot = vcycle_mean_fusable(pz);
+    pz.mean_dot = 1;
     auto precondition = [&](int rzslot) -> bool {
         if (cudaMemsetAsync(ip.z, 0, bytes, s) != cudaSuccess) return false;
-        if (launch_vcycle(pz, s, &nl) != cudaSuccess) return false;
-        return project(ip.z, rzslot, 0);
+        pz.dot_slot = rzslot;
+        if (launch_vcycle(pz, s, &nl, false, fused_dot) != cudaSuccess) return false;
+        if (fused_dot) return true;
+        if (quad) ins_dot4_kernel<<<w_dot, kT, 0, s>>>(a, ip.z, rzslot);
+        else ins_dot_kernel<<<nb, kT, 0, s>>>(a, ip.z, rzslot);
+        ++nl;
+        return cudaGetLastError() == cudaSuccess;
     };
-    if (!project(a.f, -1, 1)) return TDGL_ERR_CUDA;   // compatible right-hand side on every component
-    if (quad) ins_resid4_kernel<<<nb, kT, 0, s>>>(a);
+    if (!project(a.f, 1)) return TDGL_ERR_CUDA;   // compatible right-hand side on every component
+    if (quad) ins_resid4_kernel<<<w_res, kT, 0, s>>>(a);
     else ins_resid_kernel<<<nb, kT, 0, s>>>(a);
     ++nl;
     if (!precondition(5)) return TDGL_ERR_CUDA;
-    if (quad) ins_dir4_kernel<<<nb, kT, 0, s>>>(a, 5, 5, 1);
+    if (quad) ins_dir4_kernel<<<w_dir, kT, 0, s>>>(a, 5, 5, 1);
     else ins_dir_kernel<<<nb, kT, 0, s>>>(a, 5, 5, 1);
     ++nl;
     const int cap = iters > 0 ? iters : max_iters;
@@ -784,8 +862,8 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
     for (; it < cap; ++it) {
         const int rz = (it & 1) ? 6 : 5, rzn = (it & 1) ? 5 : 6;
         if (quad) {
-            ins_apply4_kernel<<<nb, kT, 0, s>>>(a, 7);
-            ins_update4_kernel<<<nb, kT, 0, s>>>(a, rz, 7);
+            ins_apply4_kernel<<<w_app, kT, 0, s>>>(a, 7);
+            ins_update4_kernel<<<w_upd, kT, 0, s>>>(a, rz, 7);
         } else {
             ins_apply_kernel<<<nb, kT, 0, s>>>(a, 7);
             ins_update_kernel<<<nb, kT, 0, s>>>(a, rz, 7);
@@ -812,12 +890,12 @@ int masked_poisson_solve(const PoissonArgs &pa, const InsPoisson &ip, double tol
             break;
         }
         if (!precondition(rzn)) return TDGL_ERR_CUDA;
-        if (quad) ins_dir4_kernel<<<nb, kT, 0, s>>>(a, rzn, rz, 0);
+        if (quad) ins_dir4_kernel<<<w_dir, kT, 0, s>>>(a, rzn, rz, 0);
         else ins_dir_kernel<<<nb, kT, 0, s>>>(a, rzn, rz, 0);
         ++nl;
     }
     // zero weighted mean on every component, mu = 0 on insulating sites
-    if (!project(a.mu, -1, 0)) return TDGL_ERR_CUDA;
+    if (!project(a.mu, 0)) return TDGL_ERR_CUDA;
     *done = it;
     *launches += nl;
     return rc;

@@ -115,6 +115,7 @@ struct LineArgs {
     // stage 2 (colour 0) adds its own at blockred[kMeanOff + b] and its last block writes
     // ctl->mu_mean.  0: off.
     int mean_stage, mean_nb1;
+    int mean_dot, dot_slot;   // the sum is of w r u, into ctlw->sums[dot_slot] (PoissonArgs)
     DevCtl *ctlw;
     double *blockred;
     double wsum;
@@ -844,7 +845,9 @@ __global__ void __launch_bounds__(kIirWarps * 32, 6)
 #pragma unroll
             for (int m = 0; m < C; ++m) {
                 const bool face = open && ((lane == 0 && m == 0) || (lane == 31 && m == C - 1));
-                ls += (face ? 0.5f : 1.f) * out[m];
+                const float4 r4 = rc[m / 4];
+                const float rm = (m % 4 == 0) ? r4.x : (m % 4 == 1) ? r4.y : (m % 4 == 2) ? r4.z : r4.w;
+                ls += (face ? 0.5f : 1.f) * (A.mean_dot ? rm * out[m] : out[m]);
             }
             float wyz = (A.bcy == kOpen && L.ny >= 2 && (j == 0 || j == L.ny - 1)) ? 0.5f : 1.f;
             if (A.bcz == kOpen && L.nz >= 2 && (k == 0 || k == L.nz - 1)) wyz *= 0.5f;
@@ -868,7 +871,8 @@ __global__ void __launch_bounds__(kIirWarps * 32, 6)
     t = block_sum(t, shd);
     if (threadIdx.x == 0) {
         A.ctlw->ticket = 0u;
-        A.ctlw->mu_mean = t / A.wsum;
+        if (A.mean_dot) A.ctlw->sums[A.dot_slot] = t;
+        else A.ctlw->mu_mean = t / A.wsum;
     }
 }
 
@@ -919,6 +923,8 @@ static cudaError_t smooth(const PoissonArgs &a, int l, int color, cudaStream_t s
     A.level0 = (l == 0);
     A.mean_stage = 0;
     A.mean_nb1 = 0;
+    A.mean_dot = a.mean_dot;
+    A.dot_slot = a.dot_slot;
     A.ctlw = a.ctl;
     A.blockred = a.blockred;
     A.wsum = a.wsum;

@@ -171,8 +171,8 @@ Layout layout(const tdgl_config *c, bool pon = false)
     L.D = take(8 * npsi);
     L.mu = take(4 * (size_t)N);
     // the second mu buffer: the previous step's mu, over which the init writes the guess
-    // that the next Poisson solve starts from (multigrid solves only)
-    L.mu2 = c->d_insulating ? 0 : take(4 * (size_t)N);
+    // that the next Poisson solve starts from (the multigrid solve and the masked CG)
+    L.mu2 = take(4 * (size_t)N);
     L.f = take(4 * (size_t)N);
     L.t = take(4 * (size_t)N);
     L.links = (c->links_mode != TDGL_LINKS_LANDAU) ? take(8 * 3 * (size_t)N) : 0;
@@ -301,9 +301,10 @@ void guess_args(const tdgl_handle *h, SweepArgs &a, int q, bool prev)
     a.ex_a = prev ? 2.f : 1.f;
     a.ex_b = prev ? -1.f : 0.f;
     // the V-cycle's first pass reads only the colour-1 rows of the guess when the zebra
-    // colouring (j + k) % 2 is proper and the finest level is smoothed
+    // colouring (j + k) % 2 is proper and the finest level is smoothed (the masked CG's
+    // first residual reads every site)
     const bool proper = (c.bc[1] == TDGL_OPEN || (c.ny % 2) == 0) && (c.bc[2] == TDGL_OPEN || c.nz == 1 || (c.nz % 2) == 0);
-    a.guess_odd_only = (proper && h->pa.nlevels > 1) ? 1 : 0;
+    a.guess_odd_only = (proper && h->pa.nlevels > 1 && !h->lk) ? 1 : 0;
 }
 
 void ev_rec(tdgl_handle *h, int i)
@@ -441,7 +442,7 @@ static int create_impl(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *
     h->b = at<float2>(ws, L.b);
     h->D = at<float2>(ws, L.D);
     h->mu_buf[0] = at<float>(ws, L.mu);
-    h->mu_buf[1] = c.d_insulating ? nullptr : at<float>(ws, L.mu2);
+    h->mu_buf[1] = at<float>(ws, L.mu2);
     h->mu_q = 0;
     h->mu = h->mu_buf[0];
     h->f = at<float>(ws, L.f);
@@ -649,6 +650,13 @@ static int create_impl(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *
     }
     // tensor maps for the recursive smoother's row staging (none: per-lane copies), for
     // each of the two mu buffers that the finest level can solve in
+    if (h->lk) {
+        // and of z, in which the masked solve's preconditioning V-cycle smooths
+        pa.lev[0].u = h->ip.z;
+        mg_encode_line_maps(pa);
+        h->ip.zmap = pa.umap[0];
+        h->ip.zmap_u = pa.umap_u[0];
+    }
     for (int q = 1; q >= 0; --q) {
         if (!h->mu_buf[q]) continue;
         pa.lev[0].u = pa.mu = h->mu_buf[q];

@@ -356,6 +356,10 @@ struct PoissonArgs {
     // staged kernels' wait bound and extra expected bytes (as in SweepArgs; 0: normal use)
     unsigned long long wait_ns;
     unsigned int extra_tx;
+    // mean_dot 1: a cycle's fused closing sum (mean_out) is the weighted inner product of
+    // the right-hand side and the result, sum w f u, into ctl->sums[dot_slot], instead of
+    // the mean of u
+    int mean_dot, dot_slot;
 };
 // tensor maps for the levels of pa that the recursive smoother handles (false: none made)
 bool mg_encode_line_maps(PoissonArgs &pa);
@@ -389,6 +393,8 @@ struct InsPoisson {
     int n_isl;                 // islands (conducting components enclosed by insulators)
     double wsum_c;             // sum of w over the largest component
     double n_face0, n_face1;   // its sites on the x = 0 and x = L faces
+    CUtensorMap zmap;          // the finest smoother's map of z for the preconditioning V-cycle
+    const float *zmap_u;       // z when zmap is valid, else nullptr
 };
 // Conducting components (labels by propagation in r..z as scratch), their compact ids,
 // and the weights of each; TDGL_ERR_INVALID_ARG beyond kMaxIslands islands.
