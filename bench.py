@@ -579,6 +579,12 @@ def run_native(args, rank, world, local_rank):
     s.set_state(torch.as_tensor(psi0))
     s.step(args.relax)
     s.step(args.warmup)
+    # the device-resident loop's graph is built here, untimed; the timed steps start from
+    # a checkpoint, so that the resident loop can repeat exactly the same steps below
+    ck = None
+    if args.fixed_sweeps == 0:
+        s.step_resident(args.warmup)
+        ck = s.checkpoint()
     torch.cuda.synchronize()
 
     uuid = None
@@ -614,8 +620,8 @@ def run_native(args, rank, world, local_rank):
     # the graph is built by the untimed warm-up call (the loop decides convergence on the
     # device, so a fixed sweep count is not run through it)
     resident = None
-    if args.fixed_sweeps == 0:
-        resident = resident_mode(s, p, args, stream)
+    if ck is not None:
+        resident = resident_mode(s, p, args, stream, ck)
 
     site_iters = prof["sweeps"] * p.N
     t = torch.tensor([ms, float(site_iters)], dtype=torch.float64, device=dev)
@@ -711,11 +717,12 @@ def run_native(args, rank, world, local_rank):
     return 0
 
 
-def resident_mode(s, p, args, stream):
-    """The timed steps again through tdgl_step_resident: one graph launch (conditional
-    nodes for the sweep loop and the buffer choices) and one synchronisation."""
+def resident_mode(s, p, args, stream, ck):
+    """The timed steps again, from the same checkpoint (so the same steps, bit for bit),
+    through tdgl_step_resident: one graph launch (conditional nodes for the sweep loop and
+    the buffer choices) and one synchronisation."""
     import torch
-    s.step_resident(args.warmup)
+    s.restore(ck)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -729,7 +736,7 @@ def resident_mode(s, p, args, stream):
     s.profile_enable(False)
     return {"value": pr["sweeps"] * p.N / (ms * 1e-3) / 1e9, "unit": METRIC, "ms_per_step": ms / args.steps,
             "sweeps_per_step": pr["sweeps"] / max(1, pr["steps"]), "gpu_launches": pr["kernel_launches"],
-            "graph_launches": 1, "host_syncs": 1}
+            "graph_launches": 1, "host_syncs": 1, "same_steps_as_host_timed": True}
 
 
 def main():

@@ -267,7 +267,7 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         float rmax = 0.f, facc = 0.f;
         if (op == OP_INIT) sweep2_body<1, true>(H.a, H.kz, bx, by, bz, rmax, facc);
         else sweep2_body<0, true>(H.a, H.kz, bx, by, bz, rmax, facc);
-        if (finish_sweep_at(H.a, rmax, op == OP_INIT, li, H.tiles) && tid == 0)
+        if (finish_sweep_at<false>(H.a, rmax, op == OP_INIT, li, H.tiles) && tid == 0)
             P.act[(parity & 1) * P.n + m] = H.a.ctl->done ? 0 : 1;
         break;
     }

@@ -49,11 +49,13 @@ __device__ __forceinline__ void sweep_decide_ctl(const SweepArgs &a, float gf, b
 }
 
 // The decision, and in the device-resident loop the condition of its sweep loop: every
-// path above ends the solve by max_iter sweeps, so the loop ends.
+// path above ends the solve by max_iter sweeps, so the loop ends.  LOOP false: a kernel
+// never launched inside that loop (the batched step), compiled without the graph calls.
+template <bool LOOP = true>
 __device__ __forceinline__ void sweep_decide(const SweepArgs &a, float gf, bool init)
 {
     sweep_decide_ctl(a, gf, init);
-    if (a.has_loop) {
+    if (LOOP && a.has_loop) {
         DevCtl *c = a.ctl;
         cudaGraphSetConditional(a.loop_cond, c->done ? 0u : 1u);
         if (c->done) {
@@ -76,6 +78,7 @@ __device__ __forceinline__ bool sweep_already_decided(const SweepArgs &a)
 
 // Block maximum of |r|^2 into blockred[bid]; the last of nb blocks reduces the
 // partials and decides.  Returns true in the block that decided.
+template <bool LOOP = true>
 __device__ __forceinline__ bool finish_sweep_at(const SweepArgs &a, float bmax, bool init, unsigned int bid,
                                                 unsigned int nb)
 {
@@ -93,7 +96,7 @@ __device__ __forceinline__ bool finish_sweep_at(const SweepArgs &a, float bmax, 
     float gf = block_max((float)g, shf);
     if (tid == 0) {
         a.ctl->ticket = 0u;
-        sweep_decide(a, gf, init);
+        sweep_decide<LOOP>(a, gf, init);
     }
     return true;
 }
