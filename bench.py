@@ -37,6 +37,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gsite-iter/s"
 BYTES_PER_SITE_ITER = 32          # read psi 8 + b 8 + D 8, write psi 8
+# the rest of a default time step, per site: the init (read psi 8, mu 4, alpha 4, the
+# previous mu on half the rows 2; write b 8, D 8, psi 8, the Poisson guess on half the
+# rows 2) and the Poisson solve (right-hand side 12; per multigrid level and site of it:
+# four smoothing passes of 6, residual and restriction 9, prolongation 5, summed over the
+# levels' 1 + 1/4 + 1/16 + ... = 4/3: 51)
+INIT_BYTES_PER_SITE = 44
+POISSON_BYTES_PER_SITE = 63
 SLAB_NZ = 8                       # CPU sample: full x-y extent, 8 z planes
 
 
@@ -696,6 +703,8 @@ def run_native(args, rank, world, local_rank):
                                   "sweeps": prof["ms_sweeps"] / args.steps, "K": prof["ms_K"] / args.steps,
                                   "poisson": prof["ms_poisson"] / args.steps},
             "implicit_step_gsite_iter_s": site_iters / (implicit_ms * 1e-3) / 1e9 if implicit_ms > 0 else None,
+            # the whole step against the bandwidth bound of all its algorithmic bytes
+            "step_roofline": step_roofline(p, prof, ms_max / args.steps, peak),
             "roofline": {"kernel": "sweep_tma_kernel" if p.sweep_kernel != 1 else "sweep2_kernel<0>", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_sweep_ms,
@@ -715,6 +724,16 @@ def run_native(args, rank, world, local_rank):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def step_roofline(p, prof, ms_step, peak):
+    """Algorithmic bytes of one default step (init, the sweeps after it, the Poisson
+    solve) over the step's time, against the measured copy bandwidth."""
+    sweeps = prof["sweeps"] / max(1, prof["steps"])
+    per_site = INIT_BYTES_PER_SITE + BYTES_PER_SITE_ITER * (sweeps - 1) + POISSON_BYTES_PER_SITE
+    gbs = per_site * p.N / (ms_step * 1e-3) / 1e9
+    return {"bound": "hbm", "bytes_per_site_step": per_site, "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak}
 
 
 def resident_mode(s, p, args, stream, ck):
