@@ -418,20 +418,33 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
             // periodic y and z: only the x faces carry a weight (1/2) and the face sums of E_x.
             // Four sites of one row per thread and pass; the site's x index advances by the
             // pass stride modulo nx instead of being divided out per site.
+            // The loads of kU passes are issued before their sums (one load in flight per
+            // thread left the pass latency-bound); the sums keep the pass order.
             const unsigned int stride = 4u * kBT, dstep = stride % (unsigned int)g.nx;
             unsigned int i = (m0 + 4u * tid) % (unsigned int)g.nx;
-            for (unsigned int q = m0 + 4u * tid; q < m1; q += stride) {
-                const float4 x = ld4<true>(mu + q);
-                float sum = (x.x + x.y) + (x.z + x.w);
-                if (ox && i == 0) sum -= 0.5f * x.x;
-                if (ox && i + 3 == (unsigned int)g.nx - 1) sum -= 0.5f * x.w;
-                accf += sum;
-                if (H.open_x) {
-                    if (i == 0) accv += (double)x.x;
-                    if (i + 3 == (unsigned int)g.nx - 1) accv -= (double)x.w;
+            constexpr int kU = 4;
+            for (unsigned int q0 = m0 + 4u * tid; q0 < m1; q0 += kU * stride) {
+                float4 xs[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const unsigned int q = q0 + u * stride;
+                    xs[u] = (q < m1) ? ld4<true>(mu + q) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                i += dstep;
-                if (i >= (unsigned int)g.nx) i -= (unsigned int)g.nx;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (q0 + u * stride >= m1) break;
+                    const float4 x = xs[u];
+                    float sum = (x.x + x.y) + (x.z + x.w);
+                    if (ox && i == 0) sum -= 0.5f * x.x;
+                    if (ox && i + 3 == (unsigned int)g.nx - 1) sum -= 0.5f * x.w;
+                    accf += sum;
+                    if (H.open_x) {
+                        if (i == 0) accv += (double)x.x;
+                        if (i + 3 == (unsigned int)g.nx - 1) accv -= (double)x.w;
+                    }
+                    i += dstep;
+                    if (i >= (unsigned int)g.nx) i -= (unsigned int)g.nx;
+                }
             }
         } else if ((g.nx & 3) == 0) {
             // four sites of one row per thread and pass; the loads of all passes first
@@ -499,10 +512,29 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
             // the next step's extrapolation
             float *sv = H.mu_solve;
             if ((H.a.g.N & 3) == 0) {
-                for (long long q = m0 + 4 * tid; q < m1; q += 4 * kBT) {
-                    const float4 v = ld4<true>(sv + q), o = ld4<true>(mu + q);
-                    *reinterpret_cast<float4 *>(mu + q) = make_float4(v.x - c, v.y - c, v.z - c, v.w - c);
-                    *reinterpret_cast<float4 *>(sv + q) = o;
+                // the loads of kU passes first (the two buffers are distinct, the passes'
+                // sites disjoint), then their stores
+                constexpr int kU = 4;
+                const long long stride = 4 * kBT;
+                for (long long q0 = m0 + 4 * tid; q0 < m1; q0 += kU * stride) {
+                    float4 vs[kU], os[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const long long q = q0 + u * stride;
+                        if (q < m1) {
+                            vs[u] = ld4<true>(sv + q);
+                            os[u] = ld4<true>(mu + q);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const long long q = q0 + u * stride;
+                        if (q < m1) {
+                            const float4 v = vs[u];
+                            *reinterpret_cast<float4 *>(mu + q) = make_float4(v.x - c, v.y - c, v.z - c, v.w - c);
+                            *reinterpret_cast<float4 *>(sv + q) = os[u];
+                        }
+                    }
                 }
             } else {
                 for (long long q = m0 + tid; q < m1; q += kBT) {
