@@ -274,7 +274,7 @@ int tdgl_step(tdgl_handle *h, int n_steps);
  * decided, and IF nodes select the Poisson solve of the buffer holding the result.
  * Same kernels and arguments as tdgl_step, so the same results bit for bit.
  *   The graph is built on the first call (tens of milliseconds) and kept with the
- * handle.  The first step after creation or a state load (with the extrapolated
+ * handle; where the driver cannot build it, the steps run as tdgl_step.  The first step after creation or a state load (with the extrapolated
  * Poisson guess: until a previous mu exists) runs launch by launch, as tdgl_step.
  *   Returns TDGL_ERR_INVALID_ARG for handles the loop does not cover: insulating
  * sites, poisson_tol > 0, fixed_sweeps > 0, two sweeps per pass, batch members,

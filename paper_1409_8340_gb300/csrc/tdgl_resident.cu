@@ -269,13 +269,9 @@ int tdgl_step_resident(tdgl_handle *h, int32_t n_steps)
         --n;
     }
     if (n == 0) return TDGL_OK;
-    if (!h->rgraph) {
-        if (h->rgraph_fail) return TDGL_ERR_CUDA;
-        if (build_resident(h) != TDGL_OK) {
-            h->rgraph_fail = 1;
-            return TDGL_ERR_CUDA;
-        }
-    }
+    // a driver that cannot build the graph runs the same launches from the host
+    if (!h->rgraph && !h->rgraph_fail && build_resident(h) != TDGL_OK) h->rgraph_fail = 1;
+    if (h->rgraph_fail) return tdgl_step(h, n);
     cudaStream_t s = h->stream;
     // the loop's part of the control block: state buffers, steps to run, counters cleared
     struct {
