@@ -856,6 +856,7 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
     if (extrapolating(h)) {
         guess_args(h, a, h->mu_q, h->prev_valid != 0);
         h->guess_ready = 1;
+        h->mu_pend[1 - h->mu_q] = 0;   // the guess over the previous mu carries no pending mean
     }
     ev_rec(h, 0);
     if (launch_init_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;

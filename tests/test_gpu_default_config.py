@@ -106,3 +106,27 @@ def test_default_configuration_long_run(O):
     assert abs(avg_g[0] - avg_o[0]) <= 0.01 * abs(avg_o[0]), (avg_g, avg_o)
     assert abs(avg_g[1] - avg_o[1]) <= 0.01 * max(abs(avg_o[1]), 1.0), (avg_g, avg_o)
     assert abs(avg_g[2] - avg_o[2]) <= max(0.01 * abs(avg_o[2]), 1e-4 * p.Jext), (avg_g, avg_o)
+
+
+def test_reading_the_state_between_the_sub_steps_changes_nothing():
+    """The init writes the Poisson guess over the previous mu, whose pending mean (the
+    projection left pending by the last solve) no longer applies: reading the state and the
+    previous mu between the psi solve and the Poisson solve must leave the step's result
+    unchanged, bit for bit."""
+    import torch
+    from _helpers import inclusion_alpha, make_solver
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(512, 32, 16, bc=(OP, P, P), Bz=0.2, Jext=0.025)
+    alpha = inclusion_alpha(p, 91)
+    psi0 = I.random_psi(p.nx, p.ny, p.nz, 92).astype(np.complex64)
+    a, b = make_solver(p, alpha, psi0), make_solver(p, alpha, psi0)
+    for s in (a, b):
+        s.step(5)
+        s.solve_psi()
+    ck = a.checkpoint()                   # reads psi, mu and the previous mu (now the guess)
+    assert ck["mu_prev"] is not None and torch.isfinite(ck["mu_prev"]).all()
+    for s in (a, b):
+        s.solve_mu()
+        s.step(2)
+    (pa, ma), (pb, mb) = gpu_state(a), gpu_state(b)
+    assert np.array_equal(pa, pb) and np.array_equal(ma, mb)
