@@ -311,8 +311,11 @@ int tdgl_step_resident(tdgl_handle *h, int32_t n_steps)
     h->prof.kernel_launches += 2 * ctl.rloops + (long long)done * h->rgraph_launches;
     if (ctl.status != TDGL_OK || done < n) {
         // a failed step's init has written the Poisson guess over the previous mu: a retry
-        // starts afresh (as after tdgl_step)
-        if (handle_extrapolates(h)) h->prev_valid = 0;
+        // starts afresh (as after tdgl_step), and that buffer holds no pending mean
+        if (handle_extrapolates(h)) {
+            h->prev_valid = 0;
+            h->mu_pend[1 - h->mu_q] = 0;
+        }
     }
     if (ctl.status != TDGL_OK) return ctl.status;
     return done == n ? TDGL_OK : TDGL_ERR_NOT_CONVERGED;
