@@ -283,6 +283,17 @@ int tdgl_step(tdgl_handle *h, int n_steps);
  * of the step before it and the error returned; the steps before it count. */
 int tdgl_step_resident(tdgl_handle *h, int32_t n_steps);
 
+/* The same steps as tdgl_step_resident, enqueued on the handle's stream without waiting
+ * for them: the call returns once the graph is launched (after the launch-by-launch first
+ * step, where one is due).  Steps enqueued while others are pending continue from their
+ * device state; a failure halts every step enqueued after it.  tdgl_sync waits for the
+ * enqueued steps and returns their status (the first error met; the state is then that of
+ * the last good step).  Every other call on the handle first does the same, and returns
+ * that error in place of its own work when the enqueued steps failed.  Handles the
+ * resident loop does not cover: TDGL_ERR_INVALID_ARG. */
+int tdgl_step_enqueue(tdgl_handle *h, int32_t n_steps);
+int tdgl_sync(tdgl_handle *h);
+
 /* Only the implicit psi solve of one step (init, Jacobi sweeps, residual
  * reductions), without the K and mu updates; *sweeps_out may be NULL. */
 int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out);

@@ -188,6 +188,8 @@ _SIGS = {
     "tdgl_set_mu_prev": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "tdgl_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "tdgl_step_resident": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "tdgl_step_enqueue": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "tdgl_sync": (ctypes.c_int, [_P]),
     "tdgl_solve_psi": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "tdgl_solve_mu": (ctypes.c_int, [_P]),
     "tdgl_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),

@@ -82,6 +82,10 @@ extern "C" size_t tdgl_adjoint_workspace_bytes(const tdgl_handle *h, const tdgl_
 extern "C" int tdgl_adjoint(tdgl_handle *h, const tdgl_adjoint_config *acfg, void *d_ws, size_t ws_bytes,
                             float *d_grad_alpha, double *objective, tdgl_adjoint_stats *stats)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     int rc = adj_validate(h, acfg);
     if (rc != TDGL_OK) return rc;
     // the reverse pass assumes a deterministic forward without noise

@@ -676,6 +676,7 @@ static int create_impl(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *
 void tdgl_destroy(tdgl_handle *h)
 {
     if (!h) return;
+    if (h->res_pending) resident_sync(h);   // the enqueued steps finish before the handle goes
     drop_poisson_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->ev_made)
@@ -685,6 +686,10 @@ void tdgl_destroy(tdgl_handle *h)
 
 int tdgl_profile_enable(tdgl_handle *h, int on)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h) return TDGL_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
     if (on && !h->ev_made) {
@@ -700,6 +705,10 @@ int tdgl_profile_enable(tdgl_handle *h, int on)
 
 int tdgl_test_staged_waits(tdgl_handle *h, int64_t wait_ns, int32_t extra_tx_bytes)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || wait_ns < 0 || wait_ns > 2000000000LL || extra_tx_bytes < 0 || extra_tx_bytes > 65536)
         return TDGL_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
@@ -714,6 +723,10 @@ int tdgl_test_staged_waits(tdgl_handle *h, int64_t wait_ns, int32_t extra_tx_byt
 
 int tdgl_profile_read(tdgl_handle *h, tdgl_profile *out)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || !out) return TDGL_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return TDGL_ERR_CUDA;
     ev_collect(h);
@@ -723,6 +736,10 @@ int tdgl_profile_read(tdgl_handle *h, tdgl_profile *out)
 
 int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double K)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || !d_psi) return TDGL_ERR_INVALID_ARG;
     if (h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const size_t N = (size_t)h->g.N;
@@ -746,6 +763,10 @@ int tdgl_set_state(tdgl_handle *h, const float *d_psi, const float *d_mu, double
 
 int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_mu, double K)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || !host_psi) return TDGL_ERR_INVALID_ARG;
     if (h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const size_t N = (size_t)h->g.N;
@@ -768,6 +789,10 @@ int tdgl_upload_state(tdgl_handle *h, const float *host_psi, const float *host_m
 
 int tdgl_get_mu_prev(tdgl_handle *h, float *out, int32_t out_on_host)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || !out) return TDGL_ERR_INVALID_ARG;
     if (!extrapolating(h) || !h->prev_valid) return 0;
     cudaStream_t s = h->stream;
@@ -782,6 +807,10 @@ int tdgl_get_mu_prev(tdgl_handle *h, float *out, int32_t out_on_host)
 
 int tdgl_set_mu_prev(tdgl_handle *h, const float *in, int32_t in_on_host)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h) return TDGL_ERR_INVALID_ARG;
     h->guess_ready = 0;
     if (!in) {
@@ -803,6 +832,10 @@ int tdgl_set_mu_prev(tdgl_handle *h, const float *in, int32_t in_on_host)
 
 int tdgl_set_step(tdgl_handle *h, int64_t step)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || step < 0) return TDGL_ERR_INVALID_ARG;
     cudaStream_t s = h->stream;
     const unsigned long long n = (unsigned long long)step;
@@ -814,6 +847,10 @@ int tdgl_set_step(tdgl_handle *h, int64_t step)
 
 int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double *K)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || (h->poisson_only && host_psi)) return TDGL_ERR_INVALID_ARG;
     const size_t N = (size_t)h->g.N;
     cudaStream_t s = h->stream;
@@ -830,6 +867,10 @@ int tdgl_download_state(tdgl_handle *h, float *host_psi, float *host_mu, double 
 
 int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || !out) return TDGL_ERR_INVALID_ARG;
     if (mu_materialize(h, h->mu_q) != TDGL_OK) return TDGL_ERR_CUDA;
     out->psi = reinterpret_cast<float *>(h->psi[h->cur]);
@@ -842,6 +883,10 @@ int tdgl_get_state(tdgl_handle *h, tdgl_state_ptrs *out)
 
 int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || h->batch_owned || h->slab || h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
@@ -1022,6 +1067,10 @@ static bool build_poisson_graph(tdgl_handle *h)
 
 int tdgl_solve_mu(tdgl_handle *h)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || h->batch_owned || h->slab || h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
@@ -1284,6 +1333,10 @@ int tdgl_read_ctl_scalars(tdgl_handle *h, double *Ex, double *poisson_res)
 
 int tdgl_step(tdgl_handle *h, int n_steps)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || h->batch_owned || h->slab || h->poisson_only || n_steps < 0) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     cudaStream_t s = h->stream;
@@ -1327,6 +1380,10 @@ int tdgl_step(tdgl_handle *h, int n_steps)
 
 int tdgl_observables(tdgl_handle *h, tdgl_obs *out)
 {
+    if (h && h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
     if (!h || !out || h->slab || h->poisson_only) return TDGL_ERR_INVALID_ARG;
     const tdgl_config &c = h->cfg;
     double flux = c.hx * c.hy * c.Bz;

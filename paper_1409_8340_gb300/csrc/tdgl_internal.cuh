@@ -80,7 +80,8 @@ struct DevCtl {
     int rcur, rq;              // psi buffer and mu buffer of the state
     int rleft, rdone;          // steps still to run; steps run (their solves succeeded)
     int rspare, rlast;         // (unused); sweeps of the last step run
-    int rok, rpad;             // 1: this step's Jacobi solve succeeded (its tail runs)
+    int rok;                   // 1: this step's Jacobi solve succeeded (its tail runs)
+    int rhalt;                 // 1: a failure stopped the enqueued steps (later ones do nothing)
     long long rsweeps;         // sweeps of the steps run
     long long rloops;          // two-sweep loop iterations of all steps entered
 };
@@ -535,6 +536,7 @@ struct tdgl_handle {
     cudaGraphExec_t rgraph;
     int rgraph_fail;
     int stepped;                 // 1: a host-driven step has run on the handle
+    int res_pending;             // 1: resident steps enqueued, not yet accounted on the host
     long long rgraph_launches;   // launches of one step outside the sweep loop
     tdgl::TmaMaps tmaps;       // its tensor maps
     tdgl::InsPoisson ip;
@@ -559,4 +561,7 @@ long long step_poisson_sequence(tdgl_handle *h, cudaStream_t s, cudaError_t *err
 bool step_lazy_projection(const tdgl_handle *h);
 bool step_pairs(const tdgl_handle *h);
 int step_read_ctl(tdgl_handle *h, DevCtl *out);
+// wait for the resident steps enqueued on the handle and account for them on the host;
+// returns their status (TDGL_OK when none are pending)
+int resident_sync(tdgl_handle *h);
 }  // namespace tdgl

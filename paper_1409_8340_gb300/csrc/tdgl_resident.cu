@@ -33,10 +33,12 @@ using namespace tdgl;
 namespace {
 
 // the SWITCH node of the step's solve: the branch of the state's psi buffer and mu buffer
-// (b + 3 q when the mu buffers swap every step, else b)
-__global__ void res_select_state(DevCtl *c, cudaGraphConditionalHandle hs, int flip)
+// (b + 3 q when the mu buffers swap every step, else b), none once a failure has halted
+// the enqueued steps; the tail's SWITCH runs nothing until a solve ends successfully
+__global__ void res_select_state(DevCtl *c, cudaGraphConditionalHandle hs, cudaGraphConditionalHandle ht, int flip)
 {
-    cudaGraphSetConditional(hs, (unsigned int)(c->rcur + (flip ? 3 * c->rq : 0)));
+    cudaGraphSetConditional(hs, c->rhalt ? kNoBranch : (unsigned int)(c->rcur + (flip ? 3 * c->rq : 0)));
+    cudaGraphSetConditional(ht, kNoBranch);
     c->rok = 0;
 }
 
@@ -45,6 +47,10 @@ __global__ void res_step_end(DevCtl *c, cudaGraphConditionalHandle ho, int flip)
     // a failed Jacobi solve leaves the state as it was (the tail did not run); a failure in
     // the tail (a Poisson wait that timed out) ends the loop after the step
     bool go = false;
+    if (c->rhalt) {
+        cudaGraphSetConditional(ho, 0u);
+        return;
+    }
     c->rloops += c->iter / 2;   // passes of the sweep loop after the init's sweep
     if (c->rok) {
         c->rcur = c->result;
@@ -55,6 +61,7 @@ __global__ void res_step_end(DevCtl *c, cudaGraphConditionalHandle ho, int flip)
         c->rleft -= 1;
         go = c->rleft > 0 && c->status == TDGL_OK;
     }
+    if (!c->rok || c->status != TDGL_OK) c->rhalt = 1;
     cudaGraphSetConditional(ho, go ? 1u : 0u);
 }
 
@@ -202,7 +209,7 @@ struct Builder {
         e = cudaGraphConditionalHandleCreate(&hsel, ob, 0, 0);
         if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&htail, ob, 0, 0);
         if (e == cudaSuccess) {
-            res_select_state<<<1, 1, 0, so>>>(h->ctl, hsel, flip ? 1 : 0);
+            res_select_state<<<1, 1, 0, so>>>(h->ctl, hsel, htail, flip ? 1 : 0);
             e = cudaGetLastError();
         }
         cudaGraph_t body[6] = {};
@@ -253,17 +260,14 @@ int build_resident(tdgl_handle *h)
 
 }  // namespace
 
-extern "C" {
-
-int tdgl_step_resident(tdgl_handle *h, int32_t n_steps)
+// Enqueue n resident steps (n >= 1) on the handle's stream; the first step after creation
+// or a state load runs launch by launch first.  Steps enqueued while others are pending
+// continue from their device state (the host has not accounted for them yet).
+static int resident_enqueue(tdgl_handle *h, int n)
 {
-    if (!h || h->batch_owned || h->slab || h->poisson_only || n_steps < 0) return TDGL_ERR_INVALID_ARG;
-    const tdgl_config &c = h->cfg;
-    if (h->lk || c.poisson_tol > 0 || c.fixed_sweeps > 0 || step_pairs(h)) return TDGL_ERR_INVALID_ARG;
-    int n = n_steps;
     // the first step after creation or a state load runs launch by launch: it sets the
     // kernels' one-time attributes outside a capture and leaves a previous mu to extrapolate from
-    while (n > 0 && (!h->stepped || (handle_extrapolates(h) && !h->prev_valid))) {
+    while (n > 0 && !h->res_pending && (!h->stepped || (handle_extrapolates(h) && !h->prev_valid))) {
         const int rc = tdgl_step(h, 1);
         if (rc != TDGL_OK) return rc;
         --n;
@@ -271,17 +275,40 @@ int tdgl_step_resident(tdgl_handle *h, int32_t n_steps)
     if (n == 0) return TDGL_OK;
     // a driver that cannot build the graph runs the same launches from the host
     if (!h->rgraph && !h->rgraph_fail && build_resident(h) != TDGL_OK) h->rgraph_fail = 1;
-    if (h->rgraph_fail) return tdgl_step(h, n);
+    if (h->rgraph_fail) {
+        const int rc = resident_sync(h);
+        return rc != TDGL_OK ? rc : tdgl_step(h, n);
+    }
     cudaStream_t s = h->stream;
-    // the loop's part of the control block: state buffers, steps to run, counters cleared
-    struct {
-        int rcur, rq, rleft, rdone, rspare, rlast, rok, rpad;
-        long long rsweeps, rloops;
-    } r = {h->cur, h->mu_q, n, 0, 0, h->last_sweeps, 0, 0, 0, 0};
-    static_assert(sizeof(r) == offsetof(DevCtl, rloops) + sizeof(long long) - offsetof(DevCtl, rcur), "layout");
-    if (cudaMemcpyAsync(&h->ctl->rcur, &r, sizeof(r), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (h->res_pending) {
+        // after the pending steps (stream order): n more; the counters keep accumulating
+        if (cudaMemcpyAsync(&h->ctl->rleft, &n, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return TDGL_ERR_CUDA;
+    } else {
+        // the loop's part of the control block: state buffers, steps to run, counters cleared
+        struct {
+            int rcur, rq, rleft, rdone, rspare, rlast, rok, rhalt;
+            long long rsweeps, rloops;
+        } r = {h->cur, h->mu_q, n, 0, 0, h->last_sweeps, 0, 0, 0, 0};
+        static_assert(sizeof(r) == offsetof(DevCtl, rloops) + sizeof(long long) - offsetof(DevCtl, rcur), "layout");
+        if (cudaMemcpyAsync(&h->ctl->rcur, &r, sizeof(r), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return TDGL_ERR_CUDA;
+    }
+    // (a copy from pageable host memory is staged before the call returns: the stack values
+    // above may go)
     if (cudaGraphLaunch(h->rgraph, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->res_pending = 1;
     h->guess_ready = 0;
+    return TDGL_OK;
+}
+
+namespace tdgl {
+
+int resident_sync(tdgl_handle *h)
+{
+    if (!h->res_pending) return TDGL_OK;
+    h->res_pending = 0;
+    const tdgl_config &c = h->cfg;
     DevCtl ctl;
     const int rc = step_read_ctl(h, &ctl);
     if (rc != TDGL_OK) return rc;
@@ -309,16 +336,49 @@ int tdgl_step_resident(tdgl_handle *h, int32_t n_steps)
     h->prof.sweeps += ctl.rsweeps;
     h->prof.sweep_launches += 2 * ctl.rloops + done;
     h->prof.kernel_launches += 2 * ctl.rloops + (long long)done * h->rgraph_launches;
-    if (ctl.status != TDGL_OK || done < n) {
+    if (!ctl.rhalt) return TDGL_OK;
+    if (handle_extrapolates(h)) {
         // a failed step's init has written the Poisson guess over the previous mu: a retry
         // starts afresh (as after tdgl_step), and that buffer holds no pending mean
-        if (handle_extrapolates(h)) {
-            h->prev_valid = 0;
-            h->mu_pend[1 - h->mu_q] = 0;
-        }
+        h->prev_valid = 0;
+        h->mu_pend[1 - h->mu_q] = 0;
     }
-    if (ctl.status != TDGL_OK) return ctl.status;
-    return done == n ? TDGL_OK : TDGL_ERR_NOT_CONVERGED;
+    return ctl.status != TDGL_OK ? ctl.status : TDGL_ERR_NOT_CONVERGED;
+}
+
+}  // namespace tdgl
+
+extern "C" {
+
+static bool resident_covers(const tdgl_handle *h)
+{
+    const tdgl_config &c = h->cfg;
+    return !h->batch_owned && !h->slab && !h->poisson_only && !h->lk && c.poisson_tol <= 0 && c.fixed_sweeps <= 0 &&
+           !step_pairs(h);
+}
+
+int tdgl_step_resident(tdgl_handle *h, int32_t n_steps)
+{
+    if (!h || n_steps < 0 || !resident_covers(h)) return TDGL_ERR_INVALID_ARG;
+    if (n_steps > 0) {
+        const int rc = resident_enqueue(h, n_steps);
+        if (rc != TDGL_OK) return rc;
+    }
+    return resident_sync(h);
+}
+
+int tdgl_step_enqueue(tdgl_handle *h, int32_t n_steps)
+{
+    if (!h || n_steps < 0 || !resident_covers(h)) return TDGL_ERR_INVALID_ARG;
+    return n_steps > 0 ? resident_enqueue(h, n_steps) : TDGL_OK;
+}
+
+int tdgl_sync(tdgl_handle *h)
+{
+    if (!h) return TDGL_ERR_INVALID_ARG;
+    const int rc = resident_sync(h);
+    if (rc != TDGL_OK) return rc;
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? TDGL_OK : TDGL_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -243,6 +243,15 @@ class Solver:
         """n steps as one CUDA graph launch (conditional nodes), one synchronisation."""
         check(self._L.tdgl_step_resident(self._h, int(n)), "tdgl_step_resident")
 
+    def step_enqueue(self, n: int = 1):
+        """n resident steps enqueued without waiting; errors surface at sync() or at the
+        next call on the solver."""
+        check(self._L.tdgl_step_enqueue(self._h, int(n)), "tdgl_step_enqueue")
+
+    def sync(self):
+        """Wait for the enqueued steps; raises their error."""
+        check(self._L.tdgl_sync(self._h), "tdgl_sync")
+
     def solve_psi(self) -> int:
         n = ctypes.c_int32()
         check(self._L.tdgl_solve_psi(self._h, ctypes.byref(n)), "tdgl_solve_psi")

@@ -168,3 +168,71 @@ def test_resident_default_configuration_against_the_oracle(O):
         assert np.max(np.abs(mu - mu_ex)) <= 0.1 * lag + 1e-4 * np.max(np.abs(mu_ex)), n
         ex_ex = O.voltage_open_x(G, mu_ex)
         assert abs(o["Ex"] - ex_ex) <= 1e-3 * abs(ex_ex), (n, o["Ex"], ex_ex)
+
+
+def test_enqueued_steps_equal_host_steps():
+    """tdgl_step_enqueue: chained enqueues without waiting, then tdgl_sync (or any other
+    call, which accounts for the pending steps first) -- the same bits as tdgl_step."""
+    p = cases()["openx_512x32x16"]
+    a, b = twins(p, seed=51)
+    a.step(12)
+    b.step_enqueue(3)
+    b.step_enqueue(4)
+    b.step_enqueue(5)
+    b.sync()
+    assert_same(a, b, "chained enqueues")
+    a.step(6)
+    b.step_enqueue(6)
+    assert_same(a, b, "implicit sync")        # gpu_state reads the state: the pending steps first
+    a.step(2)
+    b.step_enqueue(1)
+    b.step(1)                                 # a host-driven step after pending resident ones
+    assert_same(a, b, "host step after enqueue")
+
+
+def test_enqueued_failure_halts_the_later_steps():
+    """A failure inside the graph halts every step enqueued after it: sync raises the error
+    and the state is that of the host-driven path's last good step.  The failure is a staged
+    sweep's bounded wait made to run out (the test hook of the timeout tests)."""
+    from paper_1409_8340_gb300._lib import TDGL_ERR_TIMEOUT, TdglError
+    p = cases()["openx_512x32x16"]
+    a, b = twins(p, seed=61)
+    a.step(2)
+    b.step(2)
+    for s in (a, b):
+        s.test_staged_waits(20_000_000, 64)
+    with pytest.raises(TdglError) as ea:
+        a.step(5)
+    b.step_enqueue(3)
+    b.step_enqueue(3)
+    with pytest.raises(TdglError) as eb:
+        b.sync()
+    assert ea.value.code == eb.value.code == TDGL_ERR_TIMEOUT
+    b.sync()                                  # the error is reported once
+    for s in (a, b):
+        s.test_staged_waits(0, 0)
+    pa, ma = gpu_state(a)
+    pb, mb = gpu_state(b)
+    assert a.observables()["step"] == b.observables()["step"] == 2
+    assert np.array_equal(pa, pb) and np.array_equal(ma, mb)
+
+
+def test_enqueued_not_converged_matches_the_host_path():
+    """A solve that cannot converge within max_iter: the error comes from the enqueue (its
+    first, launch-by-launch step) or from sync, and the state is the host path's."""
+    from paper_1409_8340_gb300 import _lib
+    from paper_1409_8340_gb300._lib import TdglError
+    from paper_1409_8340_gb300.solver import Params
+    p = Params(64, 32, 8, bc=(OP, P, P), Bz=0.2, Jext=0.02, eps=1e-6, max_iter=6)
+    a, b = twins(p, seed=62)
+    with pytest.raises(TdglError) as ea:
+        a.step(60)
+    with pytest.raises(TdglError) as eb:
+        b.step_enqueue(30)
+        b.step_enqueue(30)
+        b.sync()
+    assert ea.value.code == eb.value.code == _lib.TDGL_ERR_NOT_CONVERGED
+    pa, ma = gpu_state(a)
+    pb, mb = gpu_state(b)
+    assert a.observables()["step"] == b.observables()["step"] < 60
+    assert np.array_equal(pa, pb) and np.array_equal(ma, mb)
