@@ -287,6 +287,10 @@ def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5, autotune:
     b.phase_log(True)
     b.step(1)
     phases = {k: {"ms": round(v[0], 4), "phases": v[1]} for k, v in b.phase_profile().items() if v[1]}
+    plist = b.phase_list()
+    by_kind = {}
+    for kind, pms in plist:
+        by_kind.setdefault(kind, []).append(round(pms, 4))
     b.phase_log(False)
     site_iters = st1["site_iters"] - st0["site_iters"]
     value = site_iters / (ms * 1e-3) / 1e9
@@ -319,6 +323,8 @@ def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5, autotune:
         "sweep_bytes_gbs": BYTES_PER_SITE_ITER * site_iters / (ms * 1e-3) / 1e9,
         "launches_per_step": 1, "graph": st1["graph"], "grid_blocks": st1["grid_blocks"],
         "blocks_per_sm": st1["blocks_per_sm"], "autotune": rep, "phase_ms_one_step": phases,
+        "phase_ms_in_order": {k: by_kind[k] for k in ("sweep", "smooth", "residual", "restrict", "prolong")
+                              if k in by_kind},
         "sequential_plain": {"value": seq_iters / seq_s / 1e9, "unit": METRIC, "steps": seq_steps,
                              "ms_per_batch_step": 1e3 * seq_s / seq_steps,
                              "launches_per_batch_step": launches / seq_steps},

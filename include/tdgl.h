@@ -667,6 +667,9 @@ int tdgl_batch_set_tuning(tdgl_batch *b, const tdgl_batch_tuning *in);
 #define TDGL_BATCH_OPS 13
 int tdgl_batch_phase_log(tdgl_batch *b, int32_t on);
 int tdgl_batch_phase_read(tdgl_batch *b, double *ms_by_op, int32_t *phases_by_op, int32_t nops);
+/* The last launch's phases one by one, in order: ms[i] and ops[i] (the kinds above) for
+ * the first cap of them; *n_out = the number of phases.  Synchronises. */
+int tdgl_batch_phase_list(tdgl_batch *b, double *ms, int32_t *ops, int32_t cap, int32_t *n_out);
 
 /* Time trial_steps steps (after one warm-up step) for each candidate launch
  * shape and per-size-class sweep tile depth, restoring the states before every

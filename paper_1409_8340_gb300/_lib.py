@@ -216,6 +216,8 @@ _SIGS = {
     "tdgl_batch_phase_log": (ctypes.c_int, [_P, ctypes.c_int32]),
     "tdgl_batch_phase_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                              ctypes.c_int32]),
+    "tdgl_batch_phase_list": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "tdgl_pattern_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64]),
     "tdgl_pattern_ex_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(Config), ctypes.c_int64, _P, ctypes.c_int32,
                                                         ctypes.POINTER(Background)]),

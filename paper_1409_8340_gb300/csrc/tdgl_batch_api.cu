@@ -498,6 +498,33 @@ int tdgl_batch_phase_read(tdgl_batch *b, double *ms_by_op, int32_t *phases_by_op
     return TDGL_OK;
 }
 
+int tdgl_batch_phase_list(tdgl_batch *b, double *ms, int32_t *ops, int32_t cap, int32_t *n_out)
+{
+    if (!b || !ms || !ops || !n_out || cap < 0) return TDGL_ERR_INVALID_ARG;
+    if (!b->log_on) return TDGL_ERR_INVALID_ARG;
+    std::vector<unsigned long long> log(2 * (size_t)kPhaseLogCap);
+    if (cudaMemcpyAsync(log.data(), at<char>(b->ws, b->L.plog), sizeof(unsigned long long) * log.size(),
+                        cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    int n = 0;
+    unsigned long long t_prev = log[0];
+    for (int i = 1; i < kPhaseLogCap; ++i) {
+        const unsigned long long tag = log[2 * i + 1];
+        if (tag == 0xffffull) break;
+        const int op = (int)(tag >> 8);
+        if (op < 0 || op >= TDGL_BATCH_OPS) break;
+        if (n < cap) {
+            ms[n] = (double)(log[2 * i] - t_prev) * 1e-6;
+            ops[n] = op;
+        }
+        ++n;
+        t_prev = log[2 * i];
+    }
+    *n_out = n;
+    return TDGL_OK;
+}
+
 int tdgl_batch_autotune(tdgl_batch *b, int32_t trial_steps, tdgl_batch_tune_report *report)
 {
     if (!b || trial_steps < 1) return TDGL_ERR_INVALID_ARG;

@@ -403,6 +403,14 @@ class Batch:
         check(self._L.tdgl_batch_phase_read(self._b, ms, cnt, n), "tdgl_batch_phase_read")
         return {name: (ms[q], cnt[q]) for q, name in enumerate(_lib.BATCH_OPS)}
 
+    def phase_list(self, cap: int = 512) -> list[tuple[str, float]]:
+        """The last launch's phases in order: (kind, ms)."""
+        ms = (ctypes.c_double * cap)()
+        ops = (ctypes.c_int32 * cap)()
+        n = ctypes.c_int32()
+        check(self._L.tdgl_batch_phase_list(self._b, ms, ops, cap, ctypes.byref(n)), "tdgl_batch_phase_list")
+        return [(_lib.BATCH_OPS[ops[q]], ms[q]) for q in range(min(n.value, cap))]
+
     def autotune(self, trial_steps: int = 3) -> dict:
         r = _lib.BatchTuneReport()
         check(self._L.tdgl_batch_autotune(self._b, int(trial_steps), ctypes.byref(r)), "tdgl_batch_autotune")
