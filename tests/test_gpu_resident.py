@@ -59,6 +59,10 @@ def cases():
         "frozen_48x24x8": quantised(Params(48, 24, 8, bc=(P, P, P), freeze_mu_K=True), 6),
         # a sweep decision every third sweep
         "check3_64x32x8": Params(64, 32, 8, bc=(OP, P, P), Bz=0.2, Jext=0.02, check_every=3),
+        # the xz-plane field (Eq. A_xz): staged sweeps with the j-indexed link tables
+        "xz_gauge_128x32x16": Params(128, 32, 16, bc=(OP, P, OP), Bz=0.2, Bx=0.15, xz_gauge=True, Jext=0.01),
+        # a tighter tolerance: more passes of the sweep loop per step
+        "tight_eps_64x32x16": Params(64, 32, 16, bc=(OP, P, P), Bz=0.2, Jext=0.02, eps=1e-9, max_iter=400),
     }
 
 
