@@ -48,6 +48,8 @@ struct BatchSmem {
     MGLevel L0, L1;
     int cached;                 // instance whose head is in H (-1: none)
     int flag;
+    int cw;                     // barrier count word of this launch: bar[0] (psi solve), bar[2] (mu solve)
+    unsigned int log0;          // phase-log index of this launch's start
 };
 
 __device__ __forceinline__ int btid() { return threadIdx.x + kBX * threadIdx.y; }
@@ -66,20 +68,20 @@ __device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes
     for (int w = btid(); w < bytes / 4; w += kBT) d[w] = s[w];
 }
 
-// Grid barrier with a bounded wait.  Arrivals accumulate in bar[0] over the
+// Grid barrier with a bounded wait.  Arrivals accumulate in *count over the
 // launch (zeroed before it); barrier number nb completes at nb * (grid + extra)
-// arrivals.  A wait that passes timeout_ns, or sees the error flag, sets the
+// arrivals.  A wait that passes timeout_ns, or sees the error flag bar[1], sets the
 // flag and returns false in every thread of the block.
-__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int extra, unsigned long long timeout_ns,
-                                             unsigned int nb, int *flag)
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int *count, unsigned int extra,
+                                             unsigned long long timeout_ns, unsigned int nb, int *flag)
 {
     __syncthreads();
     if (btid() == 0) {
         const unsigned int target = nb * (gridDim.x + extra);
-        volatile unsigned int *cnt = bar;
+        volatile unsigned int *cnt = count;
         volatile unsigned int *err = bar + 1;
         __threadfence();
-        atomicAdd(bar, 1u);
+        atomicAdd(count, 1u);
         const unsigned long long t0 = gtimer();
         int good = 1;
         unsigned int back = 32;
@@ -583,21 +585,28 @@ __device__ __forceinline__ bool phase(const BatchParams &P, BatchSmem &S, float 
                                       int l, int parity)
 {
     run_items(P, S, dsm, op, l, parity, build_phase(P, S, op, l));
-    if (!grid_barrier(P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag)) return false;
-    log_phase(P, nbar, op, l);
+    if (!grid_barrier(P.bar, P.bar + S.cw, P.extra, P.timeout_ns, ++nbar, &S.flag)) return false;
+    log_phase(P, S.log0 + nbar, op, l);
     return true;
 }
 
+// A time step is two cooperative launches: the implicit psi solve, then K, the Poisson
+// solve and the projection.  Each is compiled alone, so each gets the registers its own
+// phases need (one kernel with every phase spilled more in the Jacobi sweeps).
 // MINB: resident blocks per SM the register budget is sized for (2: no spills;
 // 3: a few spilled registers, more warps to cover memory latency).
 template <int MINB>
-__global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
+__global__ void __launch_bounds__(kBT, MINB) batch_psi_kernel(BatchParams P)
 {
     extern __shared__ __align__(16) float dsm[];
     __shared__ BatchSmem S;
     if (*(volatile unsigned int *)(P.bar + 1) != 0u) return;   // sticky error from an earlier launch
     const int tid = btid();
     unsigned int nbar = 0;
+    if (tid == 0) {
+        S.cw = 0;
+        S.log0 = 0;
+    }
     log_phase(P, 0, 255, 0);   // launch start
     for (int t = tid; t < P.n; t += kBT) {
         S.alive[t] = (ldx<true>(P.bst + t) == 0) ? 1 : 0;
@@ -618,19 +627,42 @@ __global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
         const int total = build_phase(P, S, OP_SWEEP, 0);
         if (total == 0) break;
         run_items(P, S, dsm, OP_SWEEP, 0, p & 1, total);
-        if (!grid_barrier(P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag)) return;
+        if (!grid_barrier(P.bar, P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag)) return;
         log_phase(P, nbar, OP_SWEEP, 0);
     }
+    // block 0 records each instance's sweeps and failure (which the second launch reads)
+    // and where the second launch's phase log continues
     __syncthreads();
-    for (int t = tid; t < P.n; t += kBT) {
-        const DevCtl *c = P.inst[t].h.a.ctl;
-        const int st = ldx<true>(&c->status);
-        S.ok[t] = S.alive[t] && st == TDGL_OK;
-        if (blockIdx.x == 0 && S.alive[t]) {
+    if (blockIdx.x == 0) {
+        for (int t = tid; t < P.n; t += kBT) {
+            if (!S.alive[t]) continue;
+            const DevCtl *c = P.inst[t].h.a.ctl;
+            const int st = ldx<true>(&c->status);
             P.sweeps[t] += ldx<true>(&c->iter);
             if (st != TDGL_OK) P.bst[t] = st;
         }
+        if (tid == 0) P.bar[3] = nbar;
     }
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kBT, MINB) batch_mu_kernel(BatchParams P)
+{
+    extern __shared__ __align__(16) float dsm[];
+    __shared__ BatchSmem S;
+    if (*(volatile unsigned int *)(P.bar + 1) != 0u) return;   // sticky error (either launch)
+    const int tid = btid();
+    unsigned int nbar = 0;
+    if (tid == 0) {
+        S.cw = 2;
+        S.log0 = ldx<true>(P.bar + 3);
+    }
+    // the instances whose psi solve succeeded: no failure recorded
+    for (int t = tid; t < P.n; t += kBT) {
+        S.ok[t] = (ldx<true>(P.bst + t) == 0) ? 1 : 0;
+        S.alive[t] = S.active[t] = 0;
+    }
+    __syncthreads();
     if (P.any_px && !phase(P, S, dsm, nbar, OP_JAVG, 0, 0)) return;
     if (!phase(P, S, dsm, nbar, OP_RHS, 0, 0)) return;
     for (int cyc = 0; cyc < P.cycles_max; ++cyc) {
@@ -651,8 +683,9 @@ __global__ void __launch_bounds__(kBT, MINB) batch_step_kernel(BatchParams P)
     }
     if (!phase(P, S, dsm, nbar, OP_MEAN, 0, 0)) return;
     run_items(P, S, dsm, OP_SHIFT, 0, 0, build_phase(P, S, OP_SHIFT, 0));
-    log_phase(P, nbar + 1, OP_SHIFT, 0);   // block 0's own end (no barrier follows)
-    if (P.plog && blockIdx.x == 0 && tid == 0 && (int)(nbar + 2) < P.plog_cap) P.plog[2 * (nbar + 2) + 1] = 0xffffull;
+    log_phase(P, S.log0 + nbar + 1, OP_SHIFT, 0);   // block 0's own end (no barrier follows)
+    if (P.plog && blockIdx.x == 0 && tid == 0 && (int)(S.log0 + nbar + 2) < P.plog_cap)
+        P.plog[2 * (S.log0 + nbar + 2) + 1] = 0xffffull;
 }
 
 // ---------------------------------------------------------------------------
@@ -697,22 +730,33 @@ size_t batch_smem_bytes(const BatchInst &I)
 }
 
 // Kernel variant for a target of bps resident blocks per SM.
-static const void *batch_kernel(int bps)
+// the two launches of a step for a target of bps resident blocks per SM
+static const void *batch_kernel(int which, int bps)
 {
-    return bps >= 3 ? (const void *)batch_step_kernel<3> : (const void *)batch_step_kernel<2>;
+    if (which == 0) return bps >= 3 ? (const void *)batch_psi_kernel<3> : (const void *)batch_psi_kernel<2>;
+    return bps >= 3 ? (const void *)batch_mu_kernel<3> : (const void *)batch_mu_kernel<2>;
 }
 
+// resident blocks per SM of the step's launches at this shared memory (the smaller of the two)
 cudaError_t batch_max_blocks_per_sm(size_t smem, int bps, int *out)
 {
-    const void *k = batch_kernel(bps);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, kBT, smem);
+    int occ[2] = {0, 0};
+    for (int w = 0; w < 2; ++w) {
+        const void *k = batch_kernel(w, bps);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[w], k, kBT, smem);
+        if (e != cudaSuccess) return e;
+    }
+    *out = occ[0] < occ[1] ? occ[0] : occ[1];
+    return cudaSuccess;
 }
 
 cudaError_t launch_batch_step(const BatchParams &p, int grid, int bps, size_t smem, cudaStream_t s)
 {
+    // the two launches' barrier counts and the log index; the error flag (bar[1]) stays
     cudaError_t e = cudaMemsetAsync(p.bar, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.bar + 2, 0, 2 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
@@ -725,8 +769,9 @@ cudaError_t launch_batch_step(const BatchParams &p, int grid, int bps, size_t sm
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (bps >= 3) return cudaLaunchKernelEx(&cfg, batch_step_kernel<3>, p);
-    return cudaLaunchKernelEx(&cfg, batch_step_kernel<2>, p);
+    e = bps >= 3 ? cudaLaunchKernelEx(&cfg, batch_psi_kernel<3>, p) : cudaLaunchKernelEx(&cfg, batch_psi_kernel<2>, p);
+    if (e != cudaSuccess) return e;
+    return bps >= 3 ? cudaLaunchKernelEx(&cfg, batch_mu_kernel<3>, p) : cudaLaunchKernelEx(&cfg, batch_mu_kernel<2>, p);
 }
 
 }  // namespace tdgl
