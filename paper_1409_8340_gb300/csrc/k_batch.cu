@@ -50,6 +50,7 @@ struct BatchSmem {
     int flag;
     int cw;                     // barrier count word of this launch: bar[0] (psi solve), bar[2] (mu solve)
     unsigned int log0;          // phase-log index of this launch's start
+    int grab;                   // the item this block took last (dynamic phases)
 };
 
 __device__ __forceinline__ int btid() { return threadIdx.x + kBX * threadIdx.y; }
@@ -561,13 +562,33 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
     }
 }
 
-// This block's share of a phase's items (total from build_phase).
-__device__ void run_items(const BatchParams &P, BatchSmem &S, float *dsm, int op, int l, int parity, int total)
+// This block's share of a phase's items (total from build_phase); ph: the phase's index in
+// the launch.  Items are dealt on demand from a counter, tiles one at a time and the other
+// items in runs of ch (about eight runs per block), so that blocks whose items ran faster
+// take more and the phase ends together.  Two counters per launch alternate between phases: at the start of every phase
+// block 0 clears the one the phase before used (the next phase's; every block has passed
+// the barrier that ended the one before).
+__device__ void run_items(const BatchParams &P, BatchSmem &S, float *dsm, int op, int l, int parity, int total,
+                          unsigned int ph)
 {
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int m = find_instance(S, P.n, it);
-        stage(P, S, m, op, l, parity);
-        run_item(P, S, dsm, op, l, parity, m, it - S.start[m]);
+    const int tid = btid();
+    unsigned int *ctr = P.bar + 4 + (S.cw ? 2 : 0);
+    if (blockIdx.x == 0 && tid == 0) atomicExch(ctr + ((ph + 1) & 1), 0u);
+    // tiles (init, sweeps, right-hand side) one at a time: they are few and long
+    const bool tiles = op == OP_INIT || op == OP_SWEEP || op == OP_RHS;
+    const int ch = tiles ? 1 : max(1, total / (int)(8 * gridDim.x));
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) S.grab = (int)atomicAdd(ctr + (ph & 1), (unsigned int)ch);
+        __syncthreads();
+        const int i0 = S.grab;
+        if (i0 >= total) break;
+        const int i1 = min(i0 + ch, total);
+        for (int it = i0; it < i1; ++it) {
+            const int m = find_instance(S, P.n, it);
+            stage(P, S, m, op, l, parity);
+            run_item(P, S, dsm, op, l, parity, m, it - S.start[m]);
+        }
     }
 }
 
@@ -584,7 +605,7 @@ __device__ __forceinline__ void log_phase(const BatchParams &P, unsigned int nb,
 __device__ __forceinline__ bool phase(const BatchParams &P, BatchSmem &S, float *dsm, unsigned int &nbar, int op,
                                       int l, int parity)
 {
-    run_items(P, S, dsm, op, l, parity, build_phase(P, S, op, l));
+    run_items(P, S, dsm, op, l, parity, build_phase(P, S, op, l), nbar);
     if (!grid_barrier(P.bar, P.bar + S.cw, P.extra, P.timeout_ns, ++nbar, &S.flag)) return false;
     log_phase(P, S.log0 + nbar, op, l);
     return true;
@@ -626,7 +647,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_psi_kernel(BatchParams P)
         }
         const int total = build_phase(P, S, OP_SWEEP, 0);
         if (total == 0) break;
-        run_items(P, S, dsm, OP_SWEEP, 0, p & 1, total);
+        run_items(P, S, dsm, OP_SWEEP, 0, p & 1, total, nbar);
         if (!grid_barrier(P.bar, P.bar, P.extra, P.timeout_ns, ++nbar, &S.flag)) return;
         log_phase(P, nbar, OP_SWEEP, 0);
     }
@@ -682,7 +703,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_mu_kernel(BatchParams P)
         }
     }
     if (!phase(P, S, dsm, nbar, OP_MEAN, 0, 0)) return;
-    run_items(P, S, dsm, OP_SHIFT, 0, 0, build_phase(P, S, OP_SHIFT, 0));
+    run_items(P, S, dsm, OP_SHIFT, 0, 0, build_phase(P, S, OP_SHIFT, 0), nbar);
     log_phase(P, S.log0 + nbar + 1, OP_SHIFT, 0);   // block 0's own end (no barrier follows)
     if (P.plog && blockIdx.x == 0 && tid == 0 && (int)(S.log0 + nbar + 2) < P.plog_cap)
         P.plog[2 * (S.log0 + nbar + 2) + 1] = 0xffffull;
@@ -754,9 +775,10 @@ cudaError_t batch_max_blocks_per_sm(size_t smem, int bps, int *out)
 
 cudaError_t launch_batch_step(const BatchParams &p, int grid, int bps, size_t smem, cudaStream_t s)
 {
-    // the two launches' barrier counts and the log index; the error flag (bar[1]) stays
+    // the two launches' barrier counts, the log index and the item counters; the error flag
+    // (bar[1]) stays
     cudaError_t e = cudaMemsetAsync(p.bar, 0, sizeof(unsigned int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.bar + 2, 0, 2 * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.bar + 2, 0, 6 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));

@@ -50,7 +50,8 @@ BLayout blayout(const tdgl_config *cfgs, int n)
     L.act = take(sizeof(int) * 2 * (size_t)n);
     L.bst = take(sizeof(int) * (size_t)n);
     L.sweeps = take(sizeof(long long) * (size_t)n);
-    L.bar = take(4 * sizeof(unsigned int));   // psi-solve count, error flag, mu-solve count, log index
+    // psi-solve count, error flag, mu-solve count, log index, two item counters per launch
+    L.bar = take(8 * sizeof(unsigned int));
     L.plog = take(2 * sizeof(unsigned long long) * kPhaseLogCap);
     L.save = off;
     for (int i = 0; i < n; ++i) {
