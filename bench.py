@@ -591,6 +591,9 @@ def run_native(args, rank, world, local_rank):
     s = Solver(p, alpha)
     s.set_state(torch.as_tensor(psi0))
     s.step(args.relax)
+    # the sweep kernel by timing (staged, register-tiled, two sweeps per pass), from this
+    # state and restored after each trial; the timed steps use the choice
+    tune = s.autotune(3) if args.fixed_sweeps == 0 else None
     s.step(args.warmup)
     # the device-resident loop's graph is built here, untimed; the timed steps start from
     # a checkpoint, so that the resident loop can repeat exactly the same steps below
@@ -719,6 +722,7 @@ def run_native(args, rank, world, local_rank):
                     "h2d_bytes_per_step": 12 * p.N, "d2h_bytes_per_step": 12 * p.N + 128},
             "gpu_launches": prof["kernel_launches"],
             "resident_step": dict(resident, vs_host_step=resident["value"] / value) if resident else None,
+            "sweep_autotune": tune,
             "clocks": clk,
             "observables": {"Ex": obs["Ex"], "psi2_mean": obs["psi2_mean"],
                             "vortex_unsigned_per_layer": obs["vortex_unsigned"], "last_sweeps": obs["last_sweeps"],

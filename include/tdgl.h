@@ -294,6 +294,24 @@ int tdgl_step_resident(tdgl_handle *h, int32_t n_steps);
 int tdgl_step_enqueue(tdgl_handle *h, int32_t n_steps);
 int tdgl_sync(tdgl_handle *h);
 
+/* Choose the Jacobi sweep of this handle by timing (Sec. 3.1; the two-sweep pass is
+ * temporal blocking, not in the paper): the staged sweep (sweep_kernel 2), the
+ * register-tiled one (1), and two sweeps per pass (sweeps_per_pass 2), as far as the
+ * grid supports each.  Every candidate takes one warm-up step and trial_steps timed
+ * steps from the current state; the state (psi, mu, the previous mu, K, the step and
+ * noise counters, the profile counters) is restored before every trial and at the end,
+ * so the run continues as if the call had not been made, with the fastest candidate.
+ * Host memory holds the saved state (12 N + 4 N bytes); the device gets no allocation.
+ * ms[c]: ms per step of candidate c (0 staged, 1 register-tiled, 2 two sweeps per pass;
+ * 0 where not supported); chosen: the one kept.  Synchronises.  Handles the step does
+ * not cover (batch members, slabs, Poisson-only): TDGL_ERR_INVALID_ARG. */
+typedef struct tdgl_tune_report {
+    double ms[3];
+    int32_t chosen;
+    int32_t candidates;
+} tdgl_tune_report;
+int tdgl_autotune(tdgl_handle *h, int32_t trial_steps, tdgl_tune_report *report);
+
 /* Only the implicit psi solve of one step (init, Jacobi sweeps, residual
  * reductions), without the K and mu updates; *sweeps_out may be NULL. */
 int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out);

@@ -156,9 +156,13 @@ class Background(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("host_seeds", ctypes.c_void_p), ("n_seeds", ctypes.c_int64)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 3), ("chosen", ctypes.c_int32), ("candidates", ctypes.c_int32)]
+
+
 # order of tdgl_abi_struct_size's argument
 ABI_STRUCTS = (Config, Obs, StatePtrs, Profile, AdjointConfig, AdjointStats, BatchTuning, BatchStats,
-               BatchTuneReport, Shape, Lattice, Background)
+               BatchTuneReport, Shape, Lattice, Background, TuneReport)
 
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -190,6 +194,7 @@ _SIGS = {
     "tdgl_step_resident": (ctypes.c_int, [_P, ctypes.c_int32]),
     "tdgl_step_enqueue": (ctypes.c_int, [_P, ctypes.c_int32]),
     "tdgl_sync": (ctypes.c_int, [_P]),
+    "tdgl_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(TuneReport)]),
     "tdgl_solve_psi": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "tdgl_solve_mu": (ctypes.c_int, [_P]),
     "tdgl_observables": (ctypes.c_int, [_P, ctypes.POINTER(Obs)]),

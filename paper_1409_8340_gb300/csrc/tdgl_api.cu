@@ -363,6 +363,7 @@ size_t tdgl_abi_struct_size(int32_t which)
     case 9: return sizeof(tdgl_shape);
     case 10: return sizeof(tdgl_lattice);
     case 11: return sizeof(tdgl_background);
+    case 12: return sizeof(tdgl_tune_report);
     default: return 0;
     }
 }
@@ -1376,6 +1377,132 @@ int tdgl_step(tdgl_handle *h, int n_steps)
         h->stepped = 1;
     }
     return cuda_err(cudaGetLastError());
+}
+
+// The state a trial of tdgl_autotune changes, saved in host memory and put back.
+struct TuneSave {
+    std::vector<float2> psi;
+    std::vector<float> mu[2];
+    DevCtl ctl;
+    int cur, mu_q, prev_valid, guess_ready, last_sweeps, last_cycles, stepped;
+    int mu_pend[2];
+    int64_t step;
+    tdgl_profile prof;
+};
+
+static int tune_save(tdgl_handle *h, TuneSave &t)
+{
+    const size_t N = (size_t)h->g.N;
+    cudaStream_t s = h->stream;
+    t.psi.resize(N);
+    if (cudaMemcpyAsync(t.psi.data(), h->psi[h->cur], 8 * N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    for (int q = 0; q < 2; ++q) {
+        if (!h->mu_buf[q]) continue;
+        t.mu[q].resize(N);
+        if (cudaMemcpyAsync(t.mu[q].data(), h->mu_buf[q], 4 * N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return TDGL_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(&t.ctl, h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    t.cur = h->cur;
+    t.mu_q = h->mu_q;
+    t.prev_valid = h->prev_valid;
+    t.guess_ready = h->guess_ready;
+    t.last_sweeps = h->last_sweeps;
+    t.last_cycles = h->last_cycles;
+    t.stepped = h->stepped;
+    t.mu_pend[0] = h->mu_pend[0];
+    t.mu_pend[1] = h->mu_pend[1];
+    t.step = h->step;
+    t.prof = h->prof;
+    return TDGL_OK;
+}
+
+static int tune_restore(tdgl_handle *h, const TuneSave &t)
+{
+    const size_t N = (size_t)h->g.N;
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->psi[t.cur], t.psi.data(), 8 * N, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return TDGL_ERR_CUDA;
+    for (int q = 0; q < 2; ++q)
+        if (h->mu_buf[q] &&
+            cudaMemcpyAsync(h->mu_buf[q], t.mu[q].data(), 4 * N, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return TDGL_ERR_CUDA;
+    if (cudaMemcpyAsync(h->ctl, &t.ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDGL_ERR_CUDA;
+    h->cur = t.cur;
+    use_mu_buffer(h, t.mu_q);
+    h->mu_solved = 0;   // f holds a trial's right-hand side: the saved residual stands
+    h->prev_valid = t.prev_valid;
+    h->guess_ready = t.guess_ready;
+    h->last_sweeps = t.last_sweeps;
+    h->last_cycles = t.last_cycles;
+    h->stepped = t.stepped;
+    h->mu_pend[0] = t.mu_pend[0];
+    h->mu_pend[1] = t.mu_pend[1];
+    h->step = t.step;
+    h->prof = t.prof;
+    return TDGL_OK;
+}
+
+// candidate c: 0 the staged sweep, 1 the register-tiled sweep, 2 two sweeps per pass
+static void tune_apply(tdgl_handle *h, int c)
+{
+    h->use_tma = (c == 0) ? 1 : 0;
+    h->cfg.sweeps_per_pass = (c == 2) ? 2 : 1;
+    drop_poisson_graphs(h);   // captured with the previous kernels (and the resident loop's graph)
+    h->pgraph_fail = 0;
+    h->rgraph_fail = 0;
+}
+
+int tdgl_autotune(tdgl_handle *h, int32_t trial_steps, tdgl_tune_report *report)
+{
+    if (!h || !report || trial_steps < 1 || h->batch_owned || h->slab || h->poisson_only) return TDGL_ERR_INVALID_ARG;
+    if (h->res_pending) {   // resident steps enqueued: finish and account for them first
+        const int rs = resident_sync(h);
+        if (rs != TDGL_OK) return rs;
+    }
+    memset(report, 0, sizeof(*report));
+    bool ok[3];
+    ok[0] = tma_sweep_supported(h->g) && (h->use_tma || tma_encode_maps(h->g, h->psi, h->b, h->D, &h->tmaps));
+    ok[1] = true;
+    ok[2] = pair_supported(h->g) && h->cfg.fixed_sweeps <= 0;
+    const int start = h->cfg.sweeps_per_pass == 2 && ok[2] ? 2 : (h->use_tma ? 0 : 1);
+    TuneSave t;
+    int rc = tune_save(h, t);
+    if (rc != TDGL_OK) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return TDGL_ERR_CUDA;
+    }
+    int best = start;
+    for (int c = 0; c < 3 && rc == TDGL_OK; ++c) {
+        if (!ok[c]) continue;
+        tune_apply(h, c);
+        rc = tdgl_step(h, 1);   // warm-up (and the first replay-captured Poisson sequence)
+        if (rc == TDGL_OK && cudaEventRecord(e0, h->stream) != cudaSuccess) rc = TDGL_ERR_CUDA;
+        if (rc == TDGL_OK) rc = tdgl_step(h, trial_steps);
+        if (rc == TDGL_OK && (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            rc = TDGL_ERR_CUDA;
+        float ms = 0.f;
+        if (rc == TDGL_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = TDGL_ERR_CUDA;
+        if (rc == TDGL_OK) {
+            report->ms[c] = ms / trial_steps;
+            report->candidates += 1;
+            if (report->ms[c] < report->ms[best] || !ok[best] || report->ms[best] == 0.0) best = c;
+        }
+        const int rr = tune_restore(h, t);
+        if (rc == TDGL_OK) rc = rr;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // a failed trial leaves the starting configuration
+    tune_apply(h, rc == TDGL_OK ? best : start);
+    report->chosen = rc == TDGL_OK ? best : start;
+    return rc;
 }
 
 int tdgl_observables(tdgl_handle *h, tdgl_obs *out)

@@ -252,6 +252,15 @@ class Solver:
         """Wait for the enqueued steps; raises their error."""
         check(self._L.tdgl_sync(self._h), "tdgl_sync")
 
+    def autotune(self, trial_steps: int = 3) -> dict:
+        """Time the staged sweep, the register-tiled sweep and two sweeps per pass from the
+        current state (restored after every trial) and keep the fastest."""
+        r = _lib.TuneReport()
+        check(self._L.tdgl_autotune(self._h, int(trial_steps), ctypes.byref(r)), "tdgl_autotune")
+        names = ("staged", "register_tiled", "two_sweeps_per_pass")
+        return {"ms_per_step": {names[c]: r.ms[c] for c in range(3) if r.ms[c] > 0}, "chosen": names[r.chosen],
+                "candidates": r.candidates}
+
     def solve_psi(self) -> int:
         n = ctypes.c_int32()
         check(self._L.tdgl_solve_psi(self._h, ctypes.byref(n)), "tdgl_solve_psi")
