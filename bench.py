@@ -270,6 +270,8 @@ def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5, autotune:
     b.step(relax)
     b.check()
     rep = b.autotune(trial_steps=3) if autotune else None
+    tun = b.tuning()
+    kz_by_size = {f"{p.nx}x{p.ny}x{p.nz}": kz for p, kz in zip(ps, tun["kz"])}
     b.step(3)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
@@ -322,7 +324,9 @@ def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5, autotune:
         "value": value, "unit": METRIC, "status": rc,
         "sweep_bytes_gbs": BYTES_PER_SITE_ITER * site_iters / (ms * 1e-3) / 1e9,
         "launches_per_step": 1, "graph": st1["graph"], "grid_blocks": st1["grid_blocks"],
-        "blocks_per_sm": st1["blocks_per_sm"], "autotune": rep, "phase_ms_one_step": phases,
+        "blocks_per_sm": st1["blocks_per_sm"], "autotune": rep,
+        "sweep_tiles": "staged" if tun["sweep_kernel"] == 0 else "register_tiled", "kz_by_size": kz_by_size,
+        "phase_ms_one_step": phases,
         "phase_ms_in_order": {k: by_kind[k] for k in ("sweep", "smooth", "residual", "restrict", "prolong")
                               if k in by_kind},
         "sequential_plain": {"value": seq_iters / seq_s / 1e9, "unit": METRIC, "steps": seq_steps,

@@ -633,6 +633,8 @@ typedef struct tdgl_batch_tuning {
     int32_t timeout_ms;           /* bound of every grid-barrier wait                                  */
     int32_t test_extra_arrivals;  /* 0.  > 0 makes every barrier wait for blocks that do not exist,    */
                                   /* so that the timeout path can be tested                            */
+    int32_t sweep_kernel;         /* Jacobi sweep tiles: 0 staged in shared memory by asynchronous     */
+                                  /* copies (default), 1 register-tiled                                */
     int32_t kz[TDGL_BATCH_MAX];   /* z planes per sweep tile, per instance (0: default rule)           */
 } tdgl_batch_tuning;
 
@@ -690,7 +692,8 @@ int tdgl_batch_phase_read(tdgl_batch *b, double *ms_by_op, int32_t *phases_by_op
 int tdgl_batch_phase_list(tdgl_batch *b, double *ms, int32_t *ops, int32_t cap, int32_t *n_out);
 
 /* Time trial_steps steps (after one warm-up step) for each candidate launch
- * shape and per-size-class sweep tile depth, restoring the states before every
+ * shape, sweep tile kind (staged or register-tiled) and per-size-class sweep
+ * tile depth, restoring the states before every
  * trial and at the end; keeps the fastest.  The states are left unchanged. */
 int tdgl_batch_autotune(tdgl_batch *b, int32_t trial_steps, tdgl_batch_tune_report *report);
 

@@ -111,7 +111,8 @@ BATCH_OPS = ("init", "sweep", "javg", "rhs", "smooth", "residual", "restrict", "
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
-                ("test_extra_arrivals", ctypes.c_int32), ("kz", ctypes.c_int32 * BATCH_MAX)]
+                ("test_extra_arrivals", ctypes.c_int32), ("sweep_kernel", ctypes.c_int32),
+                ("kz", ctypes.c_int32 * BATCH_MAX)]
 
 
 class BatchStats(ctypes.Structure):

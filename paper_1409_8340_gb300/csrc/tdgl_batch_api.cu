@@ -1,7 +1,7 @@
 // C ABI of batched ensembles: instance creation in one caller-owned workspace,
 // the instance table of the persistent kernel, CUDA-graph replay of its
-// launches, per-instance status, and the autotuner (launch shape and sweep
-// tile depth per grid-size class, timed on the batch itself).
+// launches, per-instance status, and the autotuner (launch shape, sweep tile kind
+// and sweep tile depth per grid-size class, timed on the batch itself).
 #include <math.h>
 #include <string.h>
 
@@ -169,6 +169,7 @@ void fill_params(tdgl_batch *b)
     P.sweeps = at<long long>(b->ws, b->L.sweeps);
     P.bar = at<unsigned int>(b->ws, b->L.bar);
     P.extra = (unsigned int)std::max(0, b->tune.test_extra_arrivals);
+    P.staged = b->tune.sweep_kernel == 0 ? 1 : 0;
     P.timeout_ns = (unsigned long long)std::max(1, b->tune.timeout_ms) * 1000000ull;
     P.plog = b->log_on ? at<unsigned long long>(b->ws, b->L.plog) : nullptr;
     P.plog_cap = b->log_on ? kPhaseLogCap : 0;
@@ -458,7 +459,7 @@ int tdgl_batch_set_tuning(tdgl_batch *b, const tdgl_batch_tuning *in)
 {
     if (!b || !in) return TDGL_ERR_INVALID_ARG;
     if (in->blocks_per_sm < 0 || in->blocks_per_sm > 3 || in->graph_steps < 0 || in->timeout_ms < 1 ||
-        in->test_extra_arrivals < 0)
+        in->test_extra_arrivals < 0 || in->sweep_kernel < 0 || in->sweep_kernel > 1)
         return TDGL_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TDGL_ERR_CUDA;
     b->tune = *in;
@@ -572,6 +573,18 @@ int tdgl_batch_autotune(tdgl_batch *b, int32_t trial_steps, tdgl_batch_tune_repo
         if ((bps == 3 && b->occ3 < 3) || (bps < 3 && b->occ2 < bps)) continue;
         tdgl_batch_tuning t = best;
         t.blocks_per_sm = bps;
+        b->tune = t;
+        double ms = 0.0;
+        rc = trial(&ms);
+        if (rc == TDGL_OK && ms < ms_best) {
+            ms_best = ms;
+            best = b->tune;
+        }
+    }
+    // sweep tiles staged in shared memory or register-tiled
+    if (rc == TDGL_OK) {
+        tdgl_batch_tuning t = best;
+        t.sweep_kernel = 1 - best.sweep_kernel;
         b->tune = t;
         double ms = 0.0;
         rc = trial(&ms);

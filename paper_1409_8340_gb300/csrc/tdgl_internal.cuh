@@ -463,6 +463,7 @@ struct BatchParams {
     int cycles_max;
     int any_px;                // some instance has a periodic x axis
     int max_phases;            // bound on Jacobi phases per launch
+    int staged;                // 1: Jacobi sweep tiles staged in shared memory; 0: register-tiled
     int *act;                  // [2][n]: instance still iterating after a phase of that parity
     int *bst;                  // [n]: 0, or the error that stopped the instance
     long long *sweeps;         // [n]: cumulative Jacobi sweeps

@@ -387,7 +387,8 @@ class Batch:
         t = _lib.BatchTuning()
         check(self._L.tdgl_batch_get_tuning(self._b, ctypes.byref(t)), "tdgl_batch_get_tuning")
         return {"blocks_per_sm": t.blocks_per_sm, "graph_steps": t.graph_steps, "timeout_ms": t.timeout_ms,
-                "test_extra_arrivals": t.test_extra_arrivals, "kz": list(t.kz)[:self.n]}
+                "test_extra_arrivals": t.test_extra_arrivals, "sweep_kernel": t.sweep_kernel,
+                "kz": list(t.kz)[:self.n]}
 
     def set_tuning(self, **kw):
         t = _lib.BatchTuning()

@@ -116,6 +116,38 @@ def test_batch_against_oracle(O):
     assert mism <= 2
 
 
+def test_staged_and_register_tiled_tiles_agree():
+    """The tiles staged in shared memory and the register-tiled ones compute every
+    site with the same arithmetic in the same order.  After one step (the sweeps
+    alone decide psi) psi agrees bit for bit, with the same sweep counts; over five
+    steps, where the right-hand side feeds mu back (its products may be contracted
+    into fused multiply-adds differently in the two code paths, an ulp apart), psi
+    and mu agree to 1e-6 like any two launch shapes."""
+    from paper_1409_8340_gb300.solver import Params
+    # and two grids wider than one tile (x halo pairs from the neighbouring tiles, a
+    # ragged last tile), open and periodic in x
+    ps = batch_cases() + [Params(132, 10, 7, bc=(OP, P, P), Bz=0.2, Jext=0.02, eps=1e-6, poisson_cycles=2),
+                          Params(136, 12, 6, bc=(P, OP, OP), Bz=0.12, Jext=0.015, eps=1e-6, poisson_cycles=2)]
+    alphas, psi0s, mu0s = inputs(ps, 310)
+    one, five = {}, {}
+    for kind in (0, 1):
+        b = make_batch(ps, alphas, psi0s, mu0s)
+        b.set_tuning(sweep_kernel=kind, kz=[1, 2, 3, 16, 5, 7, 4])
+        assert b.tuning()["sweep_kernel"] == kind
+        b.step(1)
+        b.check()
+        one[kind] = ([gpu_state(s)[0] for s in b.instances], b.stats()["instance_sweeps"])
+        b.step(4)
+        b.check()
+        five[kind] = [gpu_state(s) for s in b.instances]
+    assert one[0][1] == one[1][1]
+    for i in range(len(ps)):
+        assert np.array_equal(one[0][0][i], one[1][0][i]), i
+        (p0, m0), (p1, m1) = five[0][i], five[1][i]
+        assert np.max(np.abs(p0 - p1)) <= 1e-6, (i, np.max(np.abs(p0 - p1)))
+        assert np.max(np.abs(m0 - m1)) <= 1e-6 * max(1.0, np.max(np.abs(m1))), i
+
+
 def test_graph_replay_and_launch_shapes_agree():
     """Plain launches and graph replays, 1..3 blocks per SM and any sweep tile
     depth give identical psi (every site is computed the same way)."""
@@ -123,7 +155,8 @@ def test_graph_replay_and_launch_shapes_agree():
     alphas, psi0s, mu0s = inputs(ps, 300)
     ref = None
     for tune in ({"graph_steps": 0}, {"graph_steps": 3}, {"graph_steps": 2, "blocks_per_sm": 1},
-                 {"graph_steps": 0, "blocks_per_sm": 3, "kz": [1, 2, 3, 16]}):
+                 {"graph_steps": 0, "blocks_per_sm": 3, "kz": [1, 2, 3, 16]},
+                 {"graph_steps": 2, "sweep_kernel": 1, "kz": [4, 1, 5, 2]}):
         b = make_batch(ps, alphas, psi0s, mu0s)
         b.set_tuning(**tune)
         b.step(5)
