@@ -21,6 +21,8 @@ namespace tdgl {
 
 constexpr int kBT = kBX * kBY;   // threads per block
 constexpr int kFlat = 1024;      // sites per flat work item (4 per thread)
+constexpr int kQ = 4;            // site quads per thread in a residual or prolongation item
+constexpr int kFlatQ = 4 * kQ * kBX * kBY;   // sites per residual or prolongation item
 
 enum BatchOp {
     OP_INIT,
@@ -130,7 +132,7 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
         return (int)((I.h.nlines[lev][c] + I.h.lpb[lev] - 1) / I.h.lpb[lev]);
     }
     case OP_RESID:
-    case OP_PROLONG: return (l < top) ? (int)((I.pa.lev[l].N + kFlat - 1) / kFlat) : 0;
+    case OP_PROLONG: return (l < top) ? (int)((I.pa.lev[l].N + kFlatQ - 1) / kFlatQ) : 0;
     case OP_RESTRICT: return (l < top) ? (int)((I.pa.lev[l + 1].N + kFlat - 1) / kFlat) : 0;
     case OP_CFWD:
     case OP_CINV: return (int)(((long long)I.pa.lev[top].M * I.pa.lev[top].nx + kFlat - 1) / kFlat);
@@ -581,17 +583,26 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const DevGrid &g = H.a.g;
         const float fsub = (l == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
         if ((L.nx & 3) == 0) {
-            const long long m0 = (long long)li * kFlat + 4 * tid;
-            if (m0 < L.N) {
+            // kQ quads per thread, every quad's loads before any store (lanes past the end
+            // compute a valid quad and store nothing)
+            float4 res[kQ];
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                const long long mc = min((long long)li * kFlatQ + 4 * (tid + u * kBT), L.N - 4);
                 int i, j, k;
-                flat_ijk((unsigned int)m0, L.nx, L.ny, i, j, k);
-                *reinterpret_cast<float4 *>(L.t + m0) = residual4_at<true>(L, g.bcx, g.bcy, g.bcz, fsub, i, j, k);
+                flat_ijk((unsigned int)mc, L.nx, L.ny, i, j, k);
+                res[u] = residual4_at<true>(L, g.bcx, g.bcy, g.bcz, fsub, i, j, k);
+            }
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                const long long m0 = (long long)li * kFlatQ + 4 * (tid + u * kBT);
+                if (m0 < L.N) *reinterpret_cast<float4 *>(L.t + m0) = res[u];
             }
             break;
         }
-#pragma unroll
-        for (int r = 0; r < kFlat / kBT; ++r) {
-            const long long mm = (long long)li * kFlat + r * kBT + tid;
+#pragma unroll 4
+        for (int r = 0; r < kFlatQ / kBT; ++r) {
+            const long long mm = (long long)li * kFlatQ + r * kBT + tid;
             if (mm >= L.N) break;
             int i, j, k;
             flat_ijk((unsigned int)mm, L.nx, L.ny, i, j, k);
@@ -627,19 +638,26 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const MGLevel &F = S.L0, &C = S.L1;
         const DevGrid &g = H.a.g;
         if ((F.nx & 3) == 0) {
-            const long long m0 = (long long)li * kFlat + 4 * tid;
-            if (m0 < F.N) {
+            float4 res[kQ];
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                const long long mc = min((long long)li * kFlatQ + 4 * (tid + u * kBT), F.N - 4);
                 int i, j, k;
-                flat_ijk((unsigned int)m0, F.nx, F.ny, i, j, k);
+                flat_ijk((unsigned int)mc, F.nx, F.ny, i, j, k);
                 const float4 v = prolong4_at<true>(F, C, g.bcy, g.bcz, i, j, k);
-                const float4 o = ld4<true>(F.u + m0);
-                *reinterpret_cast<float4 *>(F.u + m0) = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+                const float4 o = ld4<true>(F.u + mc);
+                res[u] = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+            }
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                const long long m0 = (long long)li * kFlatQ + 4 * (tid + u * kBT);
+                if (m0 < F.N) *reinterpret_cast<float4 *>(F.u + m0) = res[u];
             }
             break;
         }
-#pragma unroll
-        for (int r = 0; r < kFlat / kBT; ++r) {
-            const long long mm = (long long)li * kFlat + r * kBT + tid;
+#pragma unroll 4
+        for (int r = 0; r < kFlatQ / kBT; ++r) {
+            const long long mm = (long long)li * kFlatQ + r * kBT + tid;
             if (mm >= F.N) break;
             int i, j, k;
             flat_ijk((unsigned int)mm, F.nx, F.ny, i, j, k);
