@@ -261,11 +261,12 @@ __device__ __forceinline__ double javg_site(const DevGrid &g, float2 Ux, const f
 }
 
 // ---------------------------------------------------------------------------
-// Sweep tiles staged in shared memory (Sec. 3.1, Eq. final and Eq. convergence; and
-// the Poisson right-hand side of Sec. 3.3).
+// Sweep tiles staged in shared memory (Sec. 3.1, Eq. b, Eq. final and Eq. convergence;
+// and the Poisson right-hand side of Sec. 3.3).
 //
 // A tile is 64 x-sites by 8 rows, marching along z.  Every thread streams, per z
-// plane, its own site pair of psi (and of b and diag M for a sweep) into a ring of
+// plane, its own site pair of psi (and of b and diag M for a sweep; the first half
+// warp the row's mu, alpha and previous-but-one mu for the init) into a ring of
 // plane stages with 16-byte asynchronous copies through L2 (cp.async.cg), the edge
 // warps and lanes also the tile's y halo rows and x halo pairs.  Planes stay in flight
 // ahead of the plane being updated, held in shared memory instead of registers.  Copies
@@ -287,17 +288,31 @@ struct RStage {
     float4 psi[kBY + 2][kRowQ];
 };
 constexpr size_t kRingRBytes = kRingR * sizeof(RStage);
-template <bool RHS>
+// init + first sweep: psi, and the tile's mu, alpha and previous-but-one mu (the Poisson
+// guess's source) as rows of 64 floats
+struct IStage {
+    float4 psi[kBY + 2][kRowQ];
+    float mu[kBY][kPX];
+    float al[kBY][kPX];
+    float pg[kBY][kPX];
+};
+static_assert(kRing * sizeof(IStage) <= kRingBytes, "the init ring fits the sweep ring's shared memory");
+// stage kind and ring depth of a tile mode (0 sweep, 1 init + first sweep, 4 right-hand side)
+template <int MODE>
 struct StageOf {
     using T = BStage;
     static constexpr int n = kRing;
 };
 template <>
-struct StageOf<true> {
+struct StageOf<1> {
+    using T = IStage;
+    static constexpr int n = kRing;
+};
+template <>
+struct StageOf<4> {
     using T = RStage;
     static constexpr int n = kRingR;
 };
-
 // b and diag M of a stage (the right-hand side's stages hold none)
 __device__ __forceinline__ float4 *stage_b_ptr(BStage &S, int r, int tx) { return &S.b[r][tx]; }
 __device__ __forceinline__ float4 *stage_D_ptr(BStage &S, int r, int tx) { return &S.D[r][tx]; }
@@ -307,6 +322,24 @@ __device__ __forceinline__ float4 stage_b(const BStage &S, int r, int tx) { retu
 __device__ __forceinline__ float4 stage_D(const BStage &S, int r, int tx) { return S.D[r][tx]; }
 __device__ __forceinline__ float4 stage_b(const RStage &, int, int) { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ float4 stage_D(const RStage &, int, int) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 *stage_b_ptr(IStage &, int, int) { return nullptr; }
+__device__ __forceinline__ float4 *stage_D_ptr(IStage &, int, int) { return nullptr; }
+__device__ __forceinline__ float4 stage_b(const IStage &, int, int) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 stage_D(const IStage &, int, int) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// mu, alpha and previous-but-one mu rows of an init stage (other stages hold none)
+__device__ __forceinline__ float *stage_row(IStage &S, int w, int r)
+{
+    return w == 0 ? &S.mu[r][0] : (w == 1 ? &S.al[r][0] : &S.pg[r][0]);
+}
+template <class St>
+__device__ __forceinline__ float *stage_row(St &, int, int) { return nullptr; }
+__device__ __forceinline__ float2 stage_pair(const IStage &S, int w, int r, int tx)
+{
+    const float *row = w == 0 ? &S.mu[r][0] : (w == 1 ? &S.al[r][0] : &S.pg[r][0]);
+    return *reinterpret_cast<const float2 *>(row + 2 * tx);
+}
+template <class St>
+__device__ __forceinline__ float2 stage_pair(const St &, int, int, int) { return make_float2(0.f, 0.f); }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
@@ -346,18 +379,21 @@ __device__ __forceinline__ int batch_plane(const DevGrid &g, int z)
 // each later plane's lower neighbour is carried in a register, so the step of plane t
 // reads the stages of planes t and t + 1 and the one of plane t - 1 takes plane t + NS - 1.
 //
-// RHS: the Poisson right-hand side (sweep2_body's MODE 4, Sec. 3.3): psi alone is staged;
-// each site pair writes f = Im[conj(psi) NS(psi)] / (ht/2) plus the injected current on
-// the open x faces, copies psi to a.dst, and adds its trapezoid-weighted f to facc.
-// Otherwise the Jacobi sweep (MODE 0).  Per site the arithmetic is sweep2_body's, in the
+// MODE 4, the Poisson right-hand side (Sec. 3.3): psi alone is staged; each site pair
+// writes f = Im[conj(psi) NS(psi)] / (ht/2) plus the injected current on the open x
+// faces, copies psi to a.dst, and adds its trapezoid-weighted f to facc.  MODE 1, the
+// init (Sec. 3.1, Eq. b; nx % 4 == 0): b and diag M from psi^n, mu and alpha (with the
+// thermal noise), written out, then the first sweep; and the Poisson guess.  MODE 0, the
+// Jacobi sweep.  Per site the arithmetic is sweep2_body's (without insulating sites), in the
 // same order; each stage element maps to a grid site with the periodic wraps applied (open
 // faces clamp to the face; the boundary rules zero or double those terms), so every x and
 // y neighbour, the wrap neighbours included, is a plain read of the stage.
-template <bool RHS>
+template <int MODE>
 __device__ void sweep_staged_tile(const SweepArgs &a, int kz, int bx, int by, int bz, float &rmax, float &facc,
-                                  typename StageOf<RHS>::T *ring)
+                                  typename StageOf<MODE>::T *ring)
 {
-    constexpr int NS = StageOf<RHS>::n;
+    constexpr bool RHS = (MODE == 4), INIT = (MODE == 1);
+    constexpr int NS = StageOf<MODE>::n;
     const DevGrid &g = a.g;
     const int tx = threadIdx.x, r = threadIdx.y;
     const int x0 = bx * kPX, j0 = by * kBY;
@@ -387,6 +423,8 @@ __device__ void sweep_staged_tile(const SweepArgs &a, int kz, int bx, int by, in
     const int xh = wrap_or_clamp(j, g.ny, yper) * rowq +
                    wrap_or_clamp(tx == 0 ? x0 / 2 - 1 : x0 / 2 + kBX, rowq, xper);
     const bool need = (x <= g.nx) && (j <= g.ny);
+    const long long sz = (long long)g.nx * g.ny;   // sites per plane
+    const bool guess = INIT && a.mu_guess != nullptr;
     auto issue = [&](int t) {
         if (t < nplanes) {
             auto &S = ring[t % NS];
@@ -396,9 +434,18 @@ __device__ void sweep_staged_tile(const SweepArgs &a, int kz, int bx, int by, in
             if (r == kBY - 1) cp_async16(&S.psi[kBY + 1][tx + 1], src + base + yh);
             if (tx == 0) cp_async16(&S.psi[r + 1][0], src + base + xh);
             if (tx == kBX - 1) cp_async16(&S.psi[r + 1][kBX + 1], src + base + xh);
-            if (!RHS && in && t + 1 < nplanes) {   // b and diag M of the updated planes only
+            if (!RHS && !INIT && in && t + 1 < nplanes) {   // b and diag M of the updated planes only
                 cp_async16(stage_b_ptr(S, r, tx), bq + base + own);
                 cp_async16(stage_D_ptr(S, r, tx), Dq + base + own);
+            }
+            // init: the updated planes' mu, alpha and (on the rows that take the guess)
+            // previous-but-one mu, 16 bytes per lane of the first half warp (nx % 4 == 0)
+            if (INIT && t + 1 < nplanes && j < g.ny && tx < kPX / 4 && x0 + 4 * tx < g.nx) {
+                const int k = k0 - 1 + t;
+                const long long fb = sz * k + (long long)g.nx * j + x0 + 4 * tx;
+                cp_async16(stage_row(S, 0, r) + 4 * tx, a.mu + fb);
+                cp_async16(stage_row(S, 1, r) + 4 * tx, a.alpha + fb);
+                if (guess && (!a.guess_odd_only || ((j + k) & 1))) cp_async16(stage_row(S, 2, r) + 4 * tx, a.mu_guess + fb);
             }
         }
         cp_async_commit();
@@ -425,6 +472,10 @@ __device__ void sweep_staged_tile(const SweepArgs &a, int kz, int bx, int by, in
     const float wxy0 = wy * ((g.bcx == kOpen && x == 0) ? 0.5f : 1.f);
     const float wxy1 = wy * ((g.bcx == kOpen && x + 1 == g.nx - 1) ? 0.5f : 1.f);
     const float inv_ht2 = 1.0f / g.ht2;
+    // init: the noise counter and the pending means of mu and of the previous-but-one mu
+    const unsigned long long nstep = INIT ? ldx<true>(&a.ctl->nstep) : 0ull;
+    const float offS = (INIT && a.mu_off) ? (float)ldx<true>(a.mu_off) : 0.f;
+    const float offP = (INIT && a.mu_off_prev) ? (float)ldx<true>(a.mu_off_prev) : 0.f;
 
     float4 pzm = make_float4(0.f, 0.f, 0.f, 0.f);
     if (in && zact) pzm = ldx<true>(src + plq * batch_plane(g, k0 - 1) + own);
@@ -508,8 +559,50 @@ __device__ void sweep_staged_tile(const SweepArgs &a, int kz, int bx, int by, in
             facc += wz * (wxy0 * f0 + wxy1 * f1);
             continue;
         }
-        const float4 bc = stage_b(Pc, r, tx), Dc = stage_D(Pc, r, tx);
-        const float2 b0 = lo2(bc), b1 = hi2(bc), D0 = lo2(Dc), D1 = hi2(Dc);
+        float2 b0, b1, D0, D1;
+        if (INIT) {
+            // b and diag M of the pair from psi^n, mu and alpha (sweep2_body's MODE 1 order)
+            const float2 mu_n = stage_pair(Pc, 0, r, tx);
+            const float2 muc = make_float2(mu_n.x - offS, mu_n.y - offS), alc = stage_pair(Pc, 1, r, tx);
+            const float2 cs[2] = {c0, c1};
+            const float2 nss[2] = {ns0, ns1};
+            const float mus[2] = {muc.x, muc.y}, als[2] = {alc.x, alc.y};
+            const float S2 = 2.f * g.S;
+            const long long m = (long long)x + (long long)g.nx * jc + sz * k;
+            float2 bo[2], Do[2];
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const float a2 = cabs2(cs[s2]);
+                Do[s2] = cmk(1.f + g.ht2 * (g.beta * a2 + S2 - als[s2]), g.ht2 * g.u * mus[s2]);
+                const float cr = als[s2] - g.beta * a2 - S2;
+                const float ci = -g.u * mus[s2];
+                const float2 lin = cmk(cr * cs[s2].x - ci * cs[s2].y, cr * cs[s2].y + ci * cs[s2].x);
+                bo[s2] = cadd(cadd(cs[s2], cscale(g.ht2, lin)), nss[s2]);
+                if (a.noise_amp != 0.f) {
+                    // thermal noise h_t zeta_m (Sec. 3.1.2), counter (site, step)
+                    const float2 v = noise_uv(a.noise_seed, m + s2, nstep);
+                    bo[s2] = cmk(bo[s2].x + a.noise_amp * v.x, bo[s2].y + a.noise_amp * v.y);
+                }
+            }
+            b0 = bo[0];
+            b1 = bo[1];
+            D0 = Do[0];
+            D1 = Do[1];
+            reinterpret_cast<float4 *>(a.b)[q0 + plq * k] = make_float4(b0.x, b0.y, b1.x, b1.y);
+            reinterpret_cast<float4 *>(a.D)[q0 + plq * k] = make_float4(D0.x, D0.y, D1.x, D1.y);
+            // the coming Poisson solve starts from a mu^(n-1) + b mu^(n-2), written over the latter
+            if (guess && (!a.guess_odd_only || ((j + k) & 1))) {
+                const float2 pgc = stage_pair(Pc, 2, r, tx);
+                reinterpret_cast<float2 *>(a.mu_guess)[q0 + plq * k] =
+                    make_float2(a.ex_a * muc.x + a.ex_b * (pgc.x - offP), a.ex_a * muc.y + a.ex_b * (pgc.y - offP));
+            }
+        } else {
+            const float4 bc = stage_b(Pc, r, tx), Dc = stage_D(Pc, r, tx);
+            b0 = lo2(bc);
+            b1 = hi2(bc);
+            D0 = lo2(Dc);
+            D1 = hi2(Dc);
+        }
         const float2 s0 = cadd(b0, ns0), s1 = cadd(b1, ns1);
         const float2 r0 = csub(s0, cmul(D0, c0)), r1 = csub(s1, cmul(D1, c1));
         const float2 n0 = cscale(__frcp_rn(cabs2(D0)), cmulc(D0, s0));
@@ -534,8 +627,14 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const int bx = li % H.gx, r = li / H.gx;
         const int by = r % H.gy, bz = r / H.gy;
         float rmax = 0.f, facc = 0.f;
-        if (op == OP_INIT) sweep2_body<1, true>(H.a, H.kz, bx, by, bz, rmax, facc);
-        else if (P.staged) sweep_staged_tile<false>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<BStage *>(dsm));
+        if (op == OP_INIT) {
+            // staged init where mu's rows sit on 16-byte boundaries
+            if (P.staged && (H.a.g.nx & 3) == 0)
+                sweep_staged_tile<1>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<IStage *>(dsm));
+            else
+                sweep2_body<1, true>(H.a, H.kz, bx, by, bz, rmax, facc);
+        }
+        else if (P.staged) sweep_staged_tile<0>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<BStage *>(dsm));
         else sweep2_body<0, true>(H.a, H.kz, bx, by, bz, rmax, facc);
         if (finish_sweep_at<false>(H.a, rmax, op == OP_INIT, li, H.tiles) && tid == 0)
             P.act[(parity & 1) * P.n + m] = H.a.ctl->done ? 0 : 1;
@@ -545,7 +644,7 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const int bx = li % H.gx, r = li / H.gx;
         const int by = r % H.gy, bz = r / H.gy;
         float rmax = 0.f, facc = 0.f;
-        if (P.staged) sweep_staged_tile<true>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<RStage *>(dsm));
+        if (P.staged) sweep_staged_tile<4>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<RStage *>(dsm));
         else sweep2_body<4, true>(H.a, H.kz, bx, by, bz, rmax, facc);
         finish_rhs_sum_at(H.a.ctl, H.a.blockred, (double)facc, H.a.wsum, li, H.tiles);
         break;
