@@ -109,6 +109,23 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int *co
     return *flag != 0;
 }
 
+// A proper zebra colouring of a level: no two lines of one colour are neighbours across a
+// periodic wrap (y and z extents even, or open, or a single line).  Then the
+// post-smoothing's first pass (colour 1) solves its lines from F and the colour-0 lines
+// alone, and the prolongation needs to correct the colour-0 lines only.
+__device__ __forceinline__ bool proper_zebra(const MGLevel &L, int bcy, int bcz)
+{
+    return (bcy == kOpen || L.ny == 1 || (L.ny & 1) == 0) && (bcz == kOpen || L.nz == 1 || (L.nz & 1) == 0);
+}
+
+// Sites the prolongation of level l corrects: the colour-0 lines' under a proper zebra
+// colouring, else every site.
+__device__ __forceinline__ long long prolong_sites(const BatchInst &I, int l)
+{
+    const MGLevel &L = I.pa.lev[l];
+    return proper_zebra(L, I.h.a.g.bcy, I.h.a.g.bcz) ? I.h.nlines[l][0] * L.nx : L.N;
+}
+
 // Work items of instance t in a phase (0: not taking part).
 __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op, int l)
 {
@@ -131,8 +148,8 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
         if (lev >= top) return 0;
         return (int)((I.h.nlines[lev][c] + I.h.lpb[lev] - 1) / I.h.lpb[lev]);
     }
-    case OP_RESID:
-    case OP_PROLONG: return (l < top) ? (int)((I.pa.lev[l].N + kFlatQ - 1) / kFlatQ) : 0;
+    case OP_RESID: return (l < top) ? (int)((I.pa.lev[l].N + kFlatQ - 1) / kFlatQ) : 0;
+    case OP_PROLONG: return (l < top) ? (int)((prolong_sites(I, l) + kFlatQ - 1) / kFlatQ) : 0;
     case OP_RESTRICT: return (l < top) ? (int)((I.pa.lev[l + 1].N + kFlat - 1) / kFlat) : 0;
     case OP_CFWD:
     case OP_CINV: return (int)(((long long)I.pa.lev[top].M * I.pa.lev[top].nx + kFlat - 1) / kFlat);
@@ -734,32 +751,51 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         break;
     }
     case OP_PROLONG: {
+        // u += P e on the colour-0 lines (a proper zebra colouring: the colour-1 lines are
+        // solved next without reading their old values), else on every site; sites are
+        // enumerated line by line
         const MGLevel &F = S.L0, &C = S.L1;
         const DevGrid &g = H.a.g;
+        const bool zeb = proper_zebra(F, g.bcy, g.bcz);
+        const unsigned int ns = (unsigned int)(zeb ? H.nlines[l][0] * F.nx : F.N);
+        const unsigned int nxu = (unsigned int)F.nx;
+        // site s of the enumeration: (i, j, k) and its index
+        auto site = [&](unsigned int sc, int &i, int &j, int &k) -> long long {
+            if (zeb) {
+                const unsigned int q = sc / nxu;
+                i = (int)(sc - q * nxu);
+                line_jk(q, 0, F.ny, F.nz, j, k);
+                return (long long)F.nx * (j + (long long)F.ny * k) + i;
+            }
+            flat_ijk(sc, F.nx, F.ny, i, j, k);
+            return (long long)sc;
+        };
         if ((F.nx & 3) == 0) {
+            // kQ quads per thread, every quad's loads before any store (lanes past the end
+            // compute a valid quad and store nothing)
             float4 res[kQ];
+            long long mq[kQ];
 #pragma unroll
             for (int u = 0; u < kQ; ++u) {
-                const long long mc = min((long long)li * kFlatQ + 4 * (tid + u * kBT), F.N - 4);
+                const unsigned int sq = (unsigned int)li * kFlatQ + 4u * (tid + u * kBT);
                 int i, j, k;
-                flat_ijk((unsigned int)mc, F.nx, F.ny, i, j, k);
+                const long long mc = site(min(sq, ns - 4u), i, j, k);
+                mq[u] = (sq < ns) ? mc : -1;
                 const float4 v = prolong4_at<true>(F, C, g.bcy, g.bcz, i, j, k);
                 const float4 o = ld4<true>(F.u + mc);
                 res[u] = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
             }
 #pragma unroll
-            for (int u = 0; u < kQ; ++u) {
-                const long long m0 = (long long)li * kFlatQ + 4 * (tid + u * kBT);
-                if (m0 < F.N) *reinterpret_cast<float4 *>(F.u + m0) = res[u];
-            }
+            for (int u = 0; u < kQ; ++u)
+                if (mq[u] >= 0) *reinterpret_cast<float4 *>(F.u + mq[u]) = res[u];
             break;
         }
 #pragma unroll 4
         for (int r = 0; r < kFlatQ / kBT; ++r) {
-            const long long mm = (long long)li * kFlatQ + r * kBT + tid;
-            if (mm >= F.N) break;
+            const unsigned int sc = (unsigned int)li * kFlatQ + r * kBT + tid;
+            if (sc >= ns) break;
             int i, j, k;
-            flat_ijk((unsigned int)mm, F.nx, F.ny, i, j, k);
+            const long long mm = site(sc, i, j, k);
             const float v = prolong_at<true>(F, C, g.bcy, g.bcz, i, j, k);
             F.u[mm] = ldx<true>(F.u + mm) + v;
         }
