@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include "philox.cuh"
+#include "staged_tile.cuh"
 #include "sweep_tile.cuh"
 
 namespace tdgl {
@@ -359,10 +360,42 @@ cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, floa
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s)
+// Init + first sweep with the tile staged in shared memory (b, diag M, the first sweep and
+// the Poisson guess; yz links, no insulating sites, nx % 4 == 0): the same per-site
+// arithmetic as sweep2_kernel<1>, planes of psi and rows of mu, alpha and the previous-but-one
+// mu copied ahead through a ring of plane stages.
+constexpr size_t kInitRingBytes = kRing * sizeof(IStage);
+__global__ void __launch_bounds__(kBX *kBY, 3) init_staged_kernel(SweepArgs a, int kz)
+{
+    extern __shared__ __align__(16) float init_ring[];
+    float rmax = 0.f, facc = 0.f;
+    sweep_staged_tile<1>(a, kz, blockIdx.x, blockIdx.y, blockIdx.z, rmax, facc,
+                         reinterpret_cast<IStage *>(init_ring));
+    finish_sweep(a, rmax, true);
+}
+
+bool init_staged_supported(const DevGrid &g)
+{
+    return use_sweep2(g) && g.Xj == nullptr && g.lk == nullptr && (g.nx & 3) == 0;
+}
+
+cudaError_t init_staged_setup()
+{
+    static const cudaError_t e =
+        cudaFuncSetAttribute(init_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInitRingBytes);
+    return e;
+}
+
+cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s, bool staged)
 {
     int kz = zchunk(a.g);
     dim3 block(kBX, kBY);
+    if (staged && init_staged_supported(a.g)) {
+        const cudaError_t e = init_staged_setup();
+        if (e != cudaSuccess) return e;
+        init_staged_kernel<<<sweep2_grid(a.g, kz), block, kInitRingBytes, s>>>(a, kz);
+        return cudaGetLastError();
+    }
     if (use_sweep2(a.g)) {
         launch_sweep2<1>(a, kz, s);   // forms the Poisson guess too
         return cudaGetLastError();

@@ -665,6 +665,8 @@ static int create_impl(const tdgl_config *cfg, void *ws, size_t ws_bytes, void *
         h->umap0[q] = pa.umap[0];
         h->umap0_u[q] = pa.umap_u[0];
     }
+    // with the staged sweep, the init's tile is staged too (asynchronous copies) where it applies
+    if (h->use_tma && init_staged_supported(g)) chk(init_staged_setup());
     chk(cudaStreamSynchronize(s));
     if (rc != TDGL_OK) {
         delete h;
@@ -905,7 +907,7 @@ int tdgl_solve_psi(tdgl_handle *h, int32_t *sweeps_out)
         h->mu_pend[1 - h->mu_q] = 0;   // the guess over the previous mu carries no pending mean
     }
     ev_rec(h, 0);
-    if (launch_init_sweep(a, s) != cudaSuccess) return TDGL_ERR_CUDA;
+    if (launch_init_sweep(a, s, h->use_tma != 0) != cudaSuccess) return TDGL_ERR_CUDA;
     a.mu_guess = nullptr;
     a.mu_off = a.mu_off_prev = nullptr;
     ev_rec(h, 1);
@@ -1199,7 +1201,7 @@ int tdgl_slab_sweep(tdgl_handle *h, int32_t first, double *r2_local)
         a.src = h->psi[h->cur];
         a.dst = h->psi[ia];
         a.dst_index = ia;
-        e = launch_init_sweep(a, s);
+        e = launch_init_sweep(a, s, h->use_tma != 0);
         h->slab_n = 1;
     } else {
         // sweep number slab_n reads the previous output: odd A -> B, even B -> A

@@ -254,7 +254,10 @@ struct SweepArgs {
 };
 constexpr unsigned int kNoBranch = 6;
 
-cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s);
+// staged: the tile staged in shared memory where init_staged_supported (else register-tiled)
+cudaError_t launch_init_sweep(const SweepArgs &a, cudaStream_t s, bool staged = false);
+bool init_staged_supported(const DevGrid &g);
+cudaError_t init_staged_setup();   // the staged init's shared-memory attribute (set once per process)
 // the guess of launch_init_sweep on its own: P = a S + b P over N sites
 cudaError_t launch_mu_guess(long long N, const float *S, float *P, float a, float b, const double *offS,
                             const double *offP, cudaStream_t s);

@@ -124,7 +124,7 @@ struct Builder {
         a.has_loop = 1;
         a.tail_cond = htail;
         a.tail_base = tail_base;
-        if (e == cudaSuccess) e = launch_init_sweep(a, st);
+        if (e == cudaSuccess) e = launch_init_sweep(a, st, h->use_tma != 0);
         a.mu_guess = nullptr;
         a.mu_off = a.mu_off_prev = nullptr;
         cudaGraph_t wb = nullptr;
