@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-modes", action="store_true", help="skip the batched and adjoint measurements")
     ap.add_argument("--batch-steps", type=int, default=30)
     ap.add_argument("--batch-relax", type=int, default=20)
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernels (no sweep or batch autotuning); for profiling captures")
     ap.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "xz", "pattern", "insulating"],
                     help="run one mode alone and print its dictionary (profiling captures)")
     # profiling captures only (a number printed with these changed is not a bench value)
@@ -597,12 +598,13 @@ def run_native(args, rank, world, local_rank):
     s.step(args.relax)
     # the sweep kernel by timing (staged, register-tiled, two sweeps per pass), from this
     # state and restored after each trial; the timed steps use the choice
-    tune = s.autotune(3) if args.fixed_sweeps == 0 else None
+    tune = s.autotune(3) if args.fixed_sweeps == 0 and not args.no_autotune else None
     s.step(args.warmup)
     # the device-resident loop's graph is built here, untimed; the timed steps start from
-    # a checkpoint, so that the resident loop can repeat exactly the same steps below
+    # a checkpoint, so that the resident loop can repeat exactly the same steps below (the
+    # loop runs one sweep per pass: not with two sweeps per pass, nor a fixed sweep count)
     ck = None
-    if args.fixed_sweeps == 0:
+    if args.fixed_sweeps == 0 and (tune is None or tune["chosen"] != "two_sweeps_per_pass"):
         s.step_resident(args.warmup)
         ck = s.checkpoint()
     torch.cuda.synchronize()
