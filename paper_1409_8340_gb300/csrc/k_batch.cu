@@ -54,6 +54,7 @@ struct BatchSmem {
     int cw;                     // barrier count word of this launch: bar[0] (psi solve), bar[2] (mu solve)
     unsigned int log0;          // phase-log index of this launch's start
     int grab;                   // the item this block took last (dynamic phases)
+    unsigned short order[kBatchMax];   // instances in dealing order (copied from P.order)
 };
 
 __device__ __forceinline__ int btid() { return threadIdx.x + kBX * threadIdx.y; }
@@ -159,11 +160,12 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
     }
 }
 
-// Item counts and their exclusive prefix for a phase; returns the total.
+// Item counts and their exclusive prefix for a phase, by dealing position (instance
+// S.order[t] at position t); returns the total.
 __device__ int build_phase(const BatchParams &P, BatchSmem &S, int op, int l)
 {
     __syncthreads();
-    for (int t = btid(); t < P.n; t += kBT) S.cnt[t] = items_of(P, S, t, op, l);
+    for (int t = btid(); t < P.n; t += kBT) S.cnt[t] = items_of(P, S, S.order[t], op, l);
     __syncthreads();
     if (btid() < 32) {
         const int lane = btid();
@@ -194,7 +196,7 @@ __device__ int build_phase(const BatchParams &P, BatchSmem &S, int op, int l)
     return S.start[P.n];
 }
 
-// Instance holding item `it` (the last t with start[t] <= it; it < total).
+// Dealing position holding item `it` (the last t with start[t] <= it; it < total).
 __device__ __forceinline__ int find_instance(const BatchSmem &S, int n, int it)
 {
     int lo = 0, hi = n - 1;
@@ -649,9 +651,10 @@ __device__ void run_items(const BatchParams &P, BatchSmem &S, float *dsm, int op
         if (i0 >= total) break;
         const int i1 = min(i0 + ch, total);
         for (int it = i0; it < i1; ++it) {
-            const int m = find_instance(S, P.n, it);
+            const int pos = find_instance(S, P.n, it);
+            const int m = S.order[pos];
             stage(P, S, m, op, l, parity);
-            run_item(P, S, dsm, op, l, parity, m, it - S.start[m]);
+            run_item(P, S, dsm, op, l, parity, m, it - S.start[pos]);
         }
     }
 }
@@ -694,6 +697,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_psi_kernel(BatchParams P)
     }
     log_phase(P, 0, 255, 0);   // launch start
     for (int t = tid; t < P.n; t += kBT) {
+        S.order[t] = (unsigned short)P.order[t];
         S.alive[t] = (ldx<true>(P.bst + t) == 0) ? 1 : 0;
         S.active[t] = S.alive[t];
         S.ok[t] = 0;
@@ -744,6 +748,7 @@ __global__ void __launch_bounds__(kBT, MINB) batch_mu_kernel(BatchParams P)
     }
     // the instances whose psi solve succeeded: no failure recorded
     for (int t = tid; t < P.n; t += kBT) {
+        S.order[t] = (unsigned short)P.order[t];
         S.ok[t] = (ldx<true>(P.bst + t) == 0) ? 1 : 0;
         S.alive[t] = S.active[t] = 0;
     }

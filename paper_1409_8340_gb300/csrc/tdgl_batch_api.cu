@@ -32,7 +32,7 @@ int batch_check(const tdgl_config *c)
 
 struct BLayout {
     std::vector<size_t> inst;   // offset of each instance's workspace
-    size_t table, act, bst, sweeps, bar, plog, save, total;
+    size_t table, order, act, bst, sweeps, bar, plog, save, total;
     std::vector<size_t> save_psi, save_mu, save_mu2, save_ctl;
 };
 
@@ -47,6 +47,7 @@ BLayout blayout(const tdgl_config *cfgs, int n)
     };
     for (int i = 0; i < n; ++i) L.inst.push_back(take(tdgl_workspace_bytes(&cfgs[i])));
     L.table = take(sizeof(BatchInst) * (size_t)n);
+    L.order = take(sizeof(int) * (size_t)n);
     L.act = take(sizeof(int) * 2 * (size_t)n);
     L.bst = take(sizeof(int) * (size_t)n);
     L.sweeps = take(sizeof(long long) * (size_t)n);
@@ -87,6 +88,7 @@ struct tdgl_batch {
     int bps, grid;
     size_t smem;
     tdgl_batch_tuning tune;
+    std::vector<int> order;     // dealing order of the instances (device copy at L.order)
     cudaGraphExec_t gexec;
     int graph_built;            // gexec matches the current table and launch shape
     int graph_ok;               // capture worked (0: plain launches)
@@ -182,6 +184,15 @@ void fill_params(tdgl_batch *b)
         phases = std::max(phases, H.a.fixed_sweeps > 0 ? H.a.fixed_sweeps : H.a.max_iter);
     }
     P.max_phases = phases + 1;
+    // dealing order: sites per sweep tile, largest first (ties by index)
+    std::vector<int> ord(b->n);
+    for (int i = 0; i < b->n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+        const BatchHead &X = b->inst[x].h, &Y = b->inst[y].h;
+        return (double)X.a.g.N / X.tiles > (double)Y.a.g.N / Y.tiles;
+    });
+    b->order = ord;
+    P.order = at<int>(b->ws, b->L.order);
 }
 
 // Push the table and launch shape of the current tuning to the device.
@@ -206,7 +217,9 @@ int apply_tuning(tdgl_batch *b)
     b->grid = b->sms * want;
     fill_params(b);
     if (cudaMemcpyAsync(at<BatchInst>(b->ws, b->L.table), b->inst.data(), sizeof(BatchInst) * b->n,
-                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(at<int>(b->ws, b->L.order), b->order.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess)
         return TDGL_ERR_CUDA;
     b->graph_built = 0;
     return cudaStreamSynchronize(b->stream) == cudaSuccess ? TDGL_OK : TDGL_ERR_CUDA;

@@ -467,6 +467,9 @@ struct BatchParams {
     int any_px;                // some instance has a periodic x axis
     int max_phases;            // bound on Jacobi phases per launch
     int staged;                // 1: Jacobi sweep tiles staged in shared memory; 0: register-tiled
+    // [n]: the instances in the order their items are dealt, the largest sweep tiles first, so
+    // that a phase ends on small items
+    const int *order;
     int *act;                  // [2][n]: instance still iterating after a phase of that parity
     int *bst;                  // [n]: 0, or the error that stopped the instance
     long long *sweeps;         // [n]: cumulative Jacobi sweeps
