@@ -104,8 +104,13 @@ extern "C" {
  *                   memory by the tensor memory accelerator (a producer thread
  *                   keeps three planes of boxes in flight; Landau links of either
  *                   plane, with or without insulating sites, even nx, else the
- *                   register-tiled kernel runs); 0 the default, which is 2.  Both
- *                   give the same iterates (same arithmetic, same order).
+ *                   register-tiled kernel runs); 0 the default, which is 2.  With 2,
+ *                   the init + first sweep is staged too (16-byte asynchronous
+ *                   copies of psi, mu, alpha and the previous mu; yz links without
+ *                   insulating sites and nx % 4 == 0, else register-tiled).  The
+ *                   kernels do the same arithmetic in the same order (the staged
+ *                   sweep's 1 / |diag M|^2 is the hardware reciprocal, about one
+ *                   ulp from the correctly rounded one).
  *   poisson_guess   starting guess of each Poisson solve: 1 the previous step's mu;
  *                   2 its linear extrapolation in time, 2 mu^(n-1) - mu^(n-2) (the
  *                   previous mu on the first step after creation or a state load);
@@ -633,8 +638,9 @@ typedef struct tdgl_batch_tuning {
     int32_t timeout_ms;           /* bound of every grid-barrier wait                                  */
     int32_t test_extra_arrivals;  /* 0.  > 0 makes every barrier wait for blocks that do not exist,    */
                                   /* so that the timeout path can be tested                            */
-    int32_t sweep_kernel;         /* Jacobi sweep tiles: 0 staged in shared memory by asynchronous     */
-                                  /* copies (default), 1 register-tiled                                */
+    int32_t sweep_kernel;         /* init, Jacobi sweep and Poisson right-hand-side tiles: 0 staged in */
+                                  /* shared memory by asynchronous copies (default; the init where     */
+                                  /* nx % 4 == 0), 1 register-tiled                                    */
     int32_t kz[TDGL_BATCH_MAX];   /* z planes per sweep tile, per instance (0: default rule)           */
 } tdgl_batch_tuning;
 
