@@ -270,7 +270,7 @@ def batched_mode(dev, steps: int, relax: int = 20, seq_steps: int = 5, autotune:
                                     .astype(np.complex64)))
     b.step(relax)
     b.check()
-    rep = b.autotune(trial_steps=3) if autotune else None
+    rep = b.autotune(trial_steps=8) if autotune else None
     tun = b.tuning()
     kz_by_size = {f"{p.nx}x{p.ny}x{p.nz}": kz for p, kz in zip(ps, tun["kz"])}
     b.step(3)
