@@ -55,6 +55,7 @@ struct BatchSmem {
     unsigned int log0;          // phase-log index of this launch's start
     int grab;                   // the item this block took last (dynamic phases)
     unsigned short order[kBatchMax];   // instances in dealing order (copied from P.order)
+    int split;                  // sweep phases: z parts per tile (1, or 2 or 4 when the phase has few tiles)
 };
 
 __device__ __forceinline__ int btid() { return threadIdx.x + kBX * threadIdx.y; }
@@ -134,7 +135,7 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
     const BatchInst &I = P.inst[t];
     switch (op) {
     case OP_INIT: return S.alive[t] ? I.h.tiles : 0;
-    case OP_SWEEP: return S.active[t] ? I.h.tiles : 0;
+    case OP_SWEEP: return S.active[t] ? I.h.tiles * min(S.split, I.h.split_max) : 0;
     case OP_JAVG: return (S.ok[t] && I.h.periodic_x) ? I.h.red_items : 0;
     case OP_RHS: return S.ok[t] ? I.h.tiles : 0;
     case OP_MEAN: return (S.ok[t] && (!I.h.freeze || I.h.open_x)) ? I.h.red_items : 0;
@@ -165,6 +166,9 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
 __device__ int build_phase(const BatchParams &P, BatchSmem &S, int op, int l)
 {
     __syncthreads();
+    if (btid() == 0) S.split = 1;
+    __syncthreads();
+    for (int pass = 0;; ++pass) {
     for (int t = btid(); t < P.n; t += kBT) S.cnt[t] = items_of(P, S, S.order[t], op, l);
     __syncthreads();
     if (btid() < 32) {
@@ -190,6 +194,15 @@ __device__ int build_phase(const BatchParams &P, BatchSmem &S, int op, int l)
             }
         }
         if (lane == 31) S.start[P.n] = incl;
+    }
+    __syncthreads();
+    // A sweep phase with fewer tiles than twice the blocks (the members still iterating at
+    // the end of a solve) splits each tile into 2 or 4 parts along z, so that its last
+    // items are short: the phase is counted again with the parts.
+    const int total = S.start[P.n];
+    if (pass > 0 || op != OP_SWEEP || total >= 2 * (int)gridDim.x || total == 0) break;
+    if (btid() == 0) S.split = (2 * total < (int)gridDim.x) ? 4 : 2;
+    __syncthreads();
     }
     if (btid() == 0) S.cached = -1;
     __syncthreads();
@@ -288,19 +301,25 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
     switch (op) {
     case OP_INIT:
     case OP_SWEEP: {
-        const int bx = li % H.gx, r = li / H.gx;
-        const int by = r % H.gy, bz = r / H.gy;
+        // a sweep phase's item is part `part` of `spl` along z of a tile
+        const int spl = (op == OP_SWEEP) ? min(S.split, H.split_max) : 1;
+        const int tile = li / spl, part = li - tile * spl;
+        const int bx = tile % H.gx, r = tile / H.gx;
+        const int by = r % H.gy, bz = r / H.gy * spl + part;
+        const int kz = H.kz / spl;
         float rmax = 0.f, facc = 0.f;
-        if (op == OP_INIT) {
+        if (zlo(H.a.g) + bz * kz >= zhi(H.a.g)) {
+            // an empty part of the last z tile
+        } else if (op == OP_INIT) {
             // staged init where mu's rows sit on 16-byte boundaries
             if (P.staged && (H.a.g.nx & 3) == 0)
-                sweep_staged_tile<1>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<IStage *>(dsm));
+                sweep_staged_tile<1>(H.a, kz, bx, by, bz, rmax, facc, reinterpret_cast<IStage *>(dsm));
             else
-                sweep2_body<1, true>(H.a, H.kz, bx, by, bz, rmax, facc);
+                sweep2_body<1, true>(H.a, kz, bx, by, bz, rmax, facc);
         }
-        else if (P.staged) sweep_staged_tile<0>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<BStage *>(dsm));
-        else sweep2_body<0, true>(H.a, H.kz, bx, by, bz, rmax, facc);
-        if (finish_sweep_at<false>(H.a, rmax, op == OP_INIT, li, H.tiles) && tid == 0)
+        else if (P.staged) sweep_staged_tile<0>(H.a, kz, bx, by, bz, rmax, facc, reinterpret_cast<BStage *>(dsm));
+        else sweep2_body<0, true>(H.a, kz, bx, by, bz, rmax, facc);
+        if (finish_sweep_at<false>(H.a, rmax, op == OP_INIT, li, H.tiles * spl) && tid == 0)
             P.act[(parity & 1) * P.n + m] = H.a.ctl->done ? 0 : 1;
         break;
     }

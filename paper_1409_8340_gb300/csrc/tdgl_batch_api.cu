@@ -131,6 +131,9 @@ void fill_instance(tdgl_batch *b, int i, int kz)
     if (kz <= 0) kz = batch_default_kz(h->g);
     batch_tiling(I, kz);
     while ((size_t)H.tiles > h->nblockred && H.kz < c.nz) batch_tiling(I, H.kz * 2);
+    H.split_max = 1;
+    for (int sp = 2; sp <= 4; sp *= 2)
+        if (H.kz % sp == 0 && (size_t)H.tiles * sp <= h->nblockred) H.split_max = sp;
     const long long N = h->g.N;
     const long long half = (long long)(h->nblockred / 2);
     long long chunk = std::max<long long>(32768, (N + half - 1) / half);

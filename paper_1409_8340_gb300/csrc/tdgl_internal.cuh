@@ -444,6 +444,7 @@ struct BatchHead {
     int iS, iA, iB;            // state buffer and the two Jacobi buffers
     int kz, gx, gy, gz;        // sweep tiling: tiles = gx gy gz
     int tiles;
+    int split_max;             // z parts a sweep tile may be split into (1, 2 or 4: divides kz, fits the partial slots)
     int red_chunk, red_items;  // sites per reduction item, items (<= half the partial slots)
     int periodic_x, open_x, freeze, cycles;
     double hx, dtK, Jext;
