@@ -138,7 +138,7 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
     case OP_SWEEP: return S.active[t] ? I.h.tiles * min(S.split, I.h.split_max) : 0;
     case OP_JAVG: return (S.ok[t] && I.h.periodic_x) ? I.h.red_items : 0;
     case OP_RHS: return S.ok[t] ? I.h.tiles : 0;
-    case OP_MEAN: return (S.ok[t] && (!I.h.freeze || I.h.open_x)) ? I.h.red_items : 0;
+    case OP_MEAN: return (S.ok[t] && (I.h.freeze ? I.h.open_x : !I.h.mean_fused)) ? I.h.red_items : 0;
     case OP_SHIFT: return (S.ok[t] && !I.h.freeze) ? I.h.red_items : 0;
     default: break;
     }
@@ -329,7 +329,11 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         float rmax = 0.f, facc = 0.f;
         if (P.staged) sweep_staged_tile<4>(H.a, H.kz, bx, by, bz, rmax, facc, reinterpret_cast<RStage *>(dsm));
         else sweep2_body<4, true>(H.a, H.kz, bx, by, bz, rmax, facc);
-        finish_rhs_sum_at(H.a.ctl, H.a.blockred, (double)facc, H.a.wsum, li, H.tiles);
+        // the deciding block also clears the sums the finest smoothing passes will accumulate
+        if (finish_rhs_sum_at(H.a.ctl, H.a.blockred, (double)facc, H.a.wsum, li, H.tiles) && tid == 0) {
+            H.a.ctl->bmean[0] = 0.0;
+            H.a.ctl->bmean[1] = 0.0;
+        }
         break;
     }
     case OP_JAVG: {
@@ -357,6 +361,23 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         const float fsub = (lev == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
         const DevGrid &g = H.a.g;
         const LineShape sh = line_shape(S.L0.nx, S.L0.kmin, S.L0.kmax, kBT);
+        if (parity && lev == 0 && H.mean_fused) {
+            // the last cycle's finest passes: each line's new values are final, so their
+            // weighted sum and x-face difference (the zero mode, the voltage) are summed here
+            float sw = 0.f, sv = 0.f;
+            line_smooth_lines<true, true>(S.L0, sh, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], fsub, li, tid, kBT,
+                                          dsm, &sw, &sv);
+            // per warp, without a block barrier: the warp's sums added to the instance's
+            for (int o = 16; o > 0; o >>= 1) {
+                sw += __shfl_xor_sync(0xffffffffu, sw, o);
+                sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            }
+            if ((tid & 31) == 0) {
+                atomicAdd(&H.a.ctl->bmean[0], (double)sw);
+                atomicAdd(&H.a.ctl->bmean[1], (double)sv);
+            }
+            break;
+        }
         line_smooth_lines<true>(S.L0, sh, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], fsub, li, tid, kBT, dsm);
         break;
     }
@@ -591,7 +612,20 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         break;
     }
     case OP_SHIFT: {
-        const float c = (float)ldx<true>(&H.a.ctl->mu_mean);
+        if (H.mean_fused) {
+            // the sums of the finest smoothing passes: the mean, the voltage and the guess flag
+            // (what the mean phase records otherwise), written by the first item
+            DevCtl *cc = H.a.ctl;
+            const double t0 = ldx<true>(&cc->bmean[0]), t1 = ldx<true>(&cc->bmean[1]);
+            if (li == 0 && tid == 0) {
+                const DevGrid &g = H.a.g;
+                cc->mu_mean = t0 / H.a.wsum;
+                if (H.open_x) cc->Ex = t1 / (double)((long long)g.ny * g.nz) / ((g.nx - 1) * H.hx);
+                if (H.mu_solve != H.a.mu) cc->mu_prev_ok = 1;
+            }
+        }
+        const float c = H.mean_fused ? (float)(ldx<true>(&H.a.ctl->bmean[0]) / H.a.wsum)
+                                     : (float)ldx<true>(&H.a.ctl->mu_mean);
         float *mu = const_cast<float *>(H.a.mu);
         const long long m0 = (long long)li * H.red_chunk;
         const long long m1 = min(m0 + H.red_chunk, H.a.g.N);
@@ -784,13 +818,16 @@ __global__ void __launch_bounds__(kBT, MINB) batch_mu_kernel(BatchParams P)
         if (!phase(P, S, dsm, nbar, OP_CFWD, 0, 0)) return;
         if (!phase(P, S, dsm, nbar, OP_CCONV, 0, 0)) return;
         if (!phase(P, S, dsm, nbar, OP_CINV, 0, 0)) return;
+        // (the finest level's passes of the last cycle sum the zero mode and the voltage:
+        // parity 1 of a smoothing phase)
+        const int last = (cyc == P.cycles_max - 1) ? 1 : 0;
         for (int l = P.lmax - 1; l >= 0; --l) {
             if (!phase(P, S, dsm, nbar, OP_PROLONG, l, 0)) return;
-            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l + 1, 0)) return;
-            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l, 0)) return;
+            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l + 1, l == 0 ? last : 0)) return;
+            if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l, l == 0 ? last : 0)) return;
         }
     }
-    if (!phase(P, S, dsm, nbar, OP_MEAN, 0, 0)) return;
+    if (P.any_mean && !phase(P, S, dsm, nbar, OP_MEAN, 0, 0)) return;
     run_items(P, S, dsm, OP_SHIFT, 0, 0, build_phase(P, S, OP_SHIFT, 0), nbar);
     log_phase(P, S.log0 + nbar + 1, OP_SHIFT, 0);   // block 0's own end (no barrier follows)
     if (P.plog && blockIdx.x == 0 && tid == 0 && (int)(S.log0 + nbar + 2) < P.plog_cap)

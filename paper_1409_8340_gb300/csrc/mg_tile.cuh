@@ -86,10 +86,13 @@ __host__ __device__ inline long long line_tile_floats(const LineShape &s) { retu
 // each line solves T u_line = -(F - fsub) + cy (u_{j+1} + u_{j-1}) + cz (u_{k+1} + u_{k-1})
 // exactly by convolution with the line Green's function G_k, k = kmin..kmax:
 // u_i = sum_k G_k v_ext(i + k), v_ext the periodic or mirrored extension of the line.
-template <bool CG>
+// SUM: also this thread's part of the weighted sum of the new values (trapezoid weights 1/2
+// per open face, the zero mode of Sec. 3.3.2) in *sw and of their x-face difference (open x:
+// values at i = 0 minus those at i = nx - 1) in *sv.
+template <bool CG, bool SUM = false>
 __device__ __forceinline__ void line_smooth_lines(const MGLevel &L, const LineShape &sh, int bcx, int bcy, int bcz,
                                                   int color, long long nlines, float fsub, long long blk, int tid,
-                                                  int nthr, float *sm)
+                                                  int nthr, float *sm, float *sw = nullptr, float *sv = nullptr)
 {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
     const int nG = L.kmax - L.kmin + 1, lead = L.kmin - sh.koff;
@@ -194,6 +197,27 @@ __device__ __forceinline__ void line_smooth_lines(const MGLevel &L, const LineSh
 #pragma unroll
             for (int c = 0; c < kLR; ++c)
                 if (i0 + c < nx) dst[c] = out[c];
+        }
+        if constexpr (SUM) {
+            const long long plane = (long long)nx * ny;
+            const int k = (int)(base / plane), j = (int)((base - plane * k) / nx);
+            const bool ox = bcx == kOpen, oy = bcy == kOpen, oz = bcz == kOpen && nz >= 2;
+            const float wyz = ((oy && (j == 0 || j == ny - 1)) ? 0.5f : 1.f) * ((oz && (k == 0 || k == nz - 1)) ? 0.5f : 1.f);
+            float acc = 0.f;
+#pragma unroll
+            for (int c = 0; c < kLR; ++c) {
+                const int i = i0 + c;
+                if (i < nx) acc += ((ox && (i == 0 || i == nx - 1)) ? 0.5f : 1.f) * out[c];
+            }
+            *sw += wyz * acc;
+            if (ox) {
+                if (i0 == 0) *sv += out[0];
+                if (i0 <= nx - 1 && nx - 1 < i0 + kLR) {
+#pragma unroll
+                    for (int c = 0; c < kLR; ++c)
+                        if (i0 + c == nx - 1) *sv -= out[c];
+                }
+            }
         }
     }
 }

@@ -148,6 +148,7 @@ void fill_instance(tdgl_batch *b, int i, int kz)
     H.dtK = h->dtK;
     H.Jext = c.Jext;
     H.nlev = h->pa.nlevels;
+    H.mean_fused = (!H.freeze && H.nlev >= 2) ? 1 : 0;
     for (int l = 0; l < H.nlev; ++l) {
         const MGLevel &M = h->pa.lev[l];
         H.lpb[l] = line_shape(M.nx, M.kmin, M.kmax, 256).lpb;
@@ -184,6 +185,7 @@ void fill_params(tdgl_batch *b)
         P.lmax = std::max(P.lmax, H.nlev - 1);
         if (!H.freeze) P.cycles_max = std::max(P.cycles_max, H.cycles);
         P.any_px |= H.periodic_x;
+        if (H.freeze ? H.open_x : !H.mean_fused) P.any_mean = 1;
         phases = std::max(phases, H.a.fixed_sweeps > 0 ? H.a.fixed_sweeps : H.a.max_iter);
     }
     P.max_phases = phases + 1;

@@ -84,6 +84,9 @@ struct DevCtl {
     int rhalt;                 // 1: a failure stopped the enqueued steps (later ones do nothing)
     long long rsweeps;         // sweeps of the steps run
     long long rloops;          // two-sweep loop iterations of all steps entered
+    // batch member: sum of w mu and the x-face difference of mu (open x), accumulated by the
+    // finest level's last two smoothing passes (cleared when the right-hand side is formed)
+    double bmean[2];
 };
 
 // ----------------------------------------------------------------------------
@@ -445,6 +448,7 @@ struct BatchHead {
     int kz, gx, gy, gz;        // sweep tiling: tiles = gx gy gz
     int tiles;
     int split_max;             // z parts a sweep tile may be split into (1, 2 or 4: divides kz, fits the partial slots)
+    int mean_fused;            // 1: the zero mode and the voltage are summed by the finest smoothing passes
     int red_chunk, red_items;  // sites per reduction item, items (<= half the partial slots)
     int periodic_x, open_x, freeze, cycles;
     double hx, dtK, Jext;
@@ -468,6 +472,7 @@ struct BatchParams {
     int any_px;                // some instance has a periodic x axis
     int max_phases;            // bound on Jacobi phases per launch
     int staged;                // 1: Jacobi sweep tiles staged in shared memory; 0: register-tiled
+    int any_mean;              // 1: some instance needs the separate mean phase (no fused sums)
     // [n]: the instances in the order their items are dealt, the largest sweep tiles first, so
     // that a phase ends on small items
     const int *order;
