@@ -687,7 +687,8 @@ int tdgl_batch_set_tuning(tdgl_batch *b, const tdgl_batch_tuning *in);
  * tdgl_batch_phase_read sums the last launch's phase durations by kind into
  * ms_by_op[TDGL_BATCH_OPS] and counts the phases into phases_by_op; the kinds are
  * 0 init + first sweep, 1 Jacobi sweep, 2 J_av and K, 3 Poisson right-hand side,
- * 4 line smoothing, 5 residual, 6 restriction, 7-9 coarsest-level transform,
+ * 4 line smoothing, 5 residual (no phase: formed inside the restriction), 6 restriction
+ * with the residual, 7-9 coarsest-level transform,
  * line solve and inverse transform, 10 prolongation, 11 zero mode and voltage,
  * 12 projection.  Synchronises. */
 #define TDGL_BATCH_OPS 13

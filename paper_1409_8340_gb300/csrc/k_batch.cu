@@ -22,8 +22,8 @@ namespace tdgl {
 
 constexpr int kBT = kBX * kBY;   // threads per block
 constexpr int kFlat = 1024;      // sites per flat work item (4 per thread)
-constexpr int kQ = 4;            // site quads per thread in a residual or prolongation item
-constexpr int kFlatQ = 4 * kQ * kBX * kBY;   // sites per residual or prolongation item
+constexpr int kQ = 4;            // site quads per thread in a prolongation item
+constexpr int kFlatQ = 4 * kQ * kBX * kBY;   // sites per prolongation item
 
 enum BatchOp {
     OP_INIT,
@@ -31,7 +31,7 @@ enum BatchOp {
     OP_JAVG,
     OP_RHS,
     OP_SMOOTH,
-    OP_RESID,
+    OP_RESID,      // (a phase-log kind no phase has: the residual is formed inside the restriction)
     OP_RESTRICT,
     OP_CFWD,
     OP_CCONV,
@@ -151,7 +151,6 @@ __device__ int items_of(const BatchParams &P, const BatchSmem &S, int t, int op,
         if (lev >= top) return 0;
         return (int)((I.h.nlines[lev][c] + I.h.lpb[lev] - 1) / I.h.lpb[lev]);
     }
-    case OP_RESID: return (l < top) ? (int)((I.pa.lev[l].N + kFlatQ - 1) / kFlatQ) : 0;
     case OP_PROLONG: return (l < top) ? (int)((prolong_sites(I, l) + kFlatQ - 1) / kFlatQ) : 0;
     case OP_RESTRICT: return (l < top) ? (int)((I.pa.lev[l + 1].N + kFlat - 1) / kFlat) : 0;
     case OP_CFWD:
@@ -232,7 +231,6 @@ __device__ void stage(const BatchParams &P, BatchSmem &S, int m, int op, int l, 
     int la = -1, lb = -1;
     const int top = I.h.nlev - 1;
     if (op == OP_SMOOTH) la = l >> 1;
-    else if (op == OP_RESID) la = l;
     else if (op == OP_RESTRICT || op == OP_PROLONG) {
         la = l;
         lb = l + 1;
@@ -381,58 +379,60 @@ __device__ void run_item(const BatchParams &P, BatchSmem &S, float *dsm, int op,
         line_smooth_lines<true>(S.L0, sh, g.bcx, g.bcy, g.bcz, c, H.nlines[lev][c], fsub, li, tid, kBT, dsm);
         break;
     }
-    case OP_RESID: {
-        const MGLevel &L = S.L0;
-        const DevGrid &g = H.a.g;
-        const float fsub = (l == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
-        if ((L.nx & 3) == 0) {
-            // kQ quads per thread, every quad's loads before any store (lanes past the end
-            // compute a valid quad and store nothing)
-            float4 res[kQ];
-#pragma unroll
-            for (int u = 0; u < kQ; ++u) {
-                const long long mc = min((long long)li * kFlatQ + 4 * (tid + u * kBT), L.N - 4);
-                int i, j, k;
-                flat_ijk((unsigned int)mc, L.nx, L.ny, i, j, k);
-                res[u] = residual4_at<true>(L, g.bcx, g.bcy, g.bcz, fsub, i, j, k);
-            }
-#pragma unroll
-            for (int u = 0; u < kQ; ++u) {
-                const long long m0 = (long long)li * kFlatQ + 4 * (tid + u * kBT);
-                if (m0 < L.N) *reinterpret_cast<float4 *>(L.t + m0) = res[u];
-            }
-            break;
-        }
-#pragma unroll 4
-        for (int r = 0; r < kFlatQ / kBT; ++r) {
-            const long long mm = (long long)li * kFlatQ + r * kBT + tid;
-            if (mm >= L.N) break;
-            int i, j, k;
-            flat_ijk((unsigned int)mm, L.nx, L.ny, i, j, k);
-            L.t[mm] = residual_at<true>(L, g.bcx, g.bcy, g.bcz, fsub, i, j, k, mm);
-        }
-        break;
-    }
     case OP_RESTRICT: {
+        // full weighting in (y, z) of the fine residual, formed on the fly (never stored):
+        // each coarse site weights the residuals of its fine rows and planes as restrict4_at
+        // weights the stored ones, in the same order
         const MGLevel &F = S.L0, &C = S.L1;
         const DevGrid &g = H.a.g;
+        const float fsub = (l == 0) ? (float)ldx<true>(&H.a.ctl->fmean) : 0.f;
+        const int nk = (F.fz == 2) ? 3 : 1, nj = (F.fy == 2) ? 3 : 1;
         if ((C.nx & 3) == 0) {
             const long long m0 = (long long)li * kFlat + 4 * tid;
             if (m0 < C.N) {
                 int i, J, K;
                 flat_ijk((unsigned int)m0, C.nx, C.ny, i, J, K);
-                *reinterpret_cast<float4 *>(C.r + m0) = restrict4_at<true>(F, g.bcy, g.bcz, i, J, K);
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int a2 = 0; a2 < nk; ++a2) {
+                    const int dk = (nk == 3) ? a2 - 1 : 0;
+                    const float wk = (nk == 3) ? (dk == 0 ? 0.5f : 0.25f) : 1.f;
+                    const int kf = (F.nz >= 2) ? nb_idx(F.fz * K, dk, F.nz, g.bcz) : 0;
+                    for (int b2 = 0; b2 < nj; ++b2) {
+                        const int dj = (nj == 3) ? b2 - 1 : 0;
+                        const float wj = (nj == 3) ? (dj == 0 ? 0.5f : 0.25f) : 1.f;
+                        const int jf = nb_idx(F.fy * J, dj, F.ny, g.bcy);
+                        const float4 t = residual4_at<true>(F, g.bcx, g.bcy, g.bcz, fsub, i, jf, kf);
+                        acc.x += wk * wj * t.x;
+                        acc.y += wk * wj * t.y;
+                        acc.z += wk * wj * t.z;
+                        acc.w += wk * wj * t.w;
+                    }
+                }
+                *reinterpret_cast<float4 *>(C.r + m0) = acc;
                 *reinterpret_cast<float4 *>(C.u + m0) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             break;
         }
-#pragma unroll
+#pragma unroll 1
         for (int r = 0; r < kFlat / kBT; ++r) {
             const long long mm = (long long)li * kFlat + r * kBT + tid;
             if (mm >= C.N) break;
             int i, J, K;
             flat_ijk((unsigned int)mm, C.nx, C.ny, i, J, K);
-            C.r[mm] = restrict_at<true>(F, g.bcy, g.bcz, i, J, K);
+            float acc = 0.f;
+            for (int a2 = 0; a2 < nk; ++a2) {
+                const int dk = (nk == 3) ? a2 - 1 : 0;
+                const float wk = (nk == 3) ? (dk == 0 ? 0.5f : 0.25f) : 1.f;
+                const int kf = (F.nz >= 2) ? nb_idx(F.fz * K, dk, F.nz, g.bcz) : 0;
+                for (int b2 = 0; b2 < nj; ++b2) {
+                    const int dj = (nj == 3) ? b2 - 1 : 0;
+                    const float wj = (nj == 3) ? (dj == 0 ? 0.5f : 0.25f) : 1.f;
+                    const int jf = nb_idx(F.fy * J, dj, F.ny, g.bcy);
+                    const long long mf = (long long)F.nx * (jf + (long long)F.ny * kf) + i;
+                    acc += wk * wj * residual_at<true>(F, g.bcx, g.bcy, g.bcz, fsub, i, jf, kf, mf);
+                }
+            }
+            C.r[mm] = acc;
             C.u[mm] = 0.f;
         }
         break;
@@ -812,7 +812,6 @@ __global__ void __launch_bounds__(kBT, MINB) batch_mu_kernel(BatchParams P)
         for (int l = 0; l < P.lmax; ++l) {
             if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l, 0)) return;
             if (!phase(P, S, dsm, nbar, OP_SMOOTH, 2 * l + 1, 0)) return;
-            if (!phase(P, S, dsm, nbar, OP_RESID, l, 0)) return;
             if (!phase(P, S, dsm, nbar, OP_RESTRICT, l, 0)) return;
         }
         if (!phase(P, S, dsm, nbar, OP_CFWD, 0, 0)) return;
