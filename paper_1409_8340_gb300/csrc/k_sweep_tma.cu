@@ -239,6 +239,9 @@ __global__ void __launch_bounds__(kThreads, 3)
             int sm = 0, sc = 1, sp = 2;
             unsigned php = 0u;
             float4 *dp = dst + q0 + plq * k0;   // plane k0 - 1 + t of this lane's site pair
+            // MASK: the link bits of the pair, read one plane ahead (their load overlaps a plane)
+            uchar2 lk_next = make_uchar2(0x3f, 0x3f);
+            if (MASK && in) lk_next = lk2[q0 + plq * k0];
             for (int t = 1; t + 1 < nplanes; ++t) {
                 const int k = k0 - 1 + t;
                 if (t == 1) {
@@ -251,7 +254,8 @@ __global__ void __launch_bounds__(kThreads, 3)
                 }
                 const St &Pm = ring[sm], &Pc = ring[sc], &Pp = ring[sp];
                 if (in) {
-                    const uchar2 lkc = MASK ? lk2[q0 + plq * k] : make_uchar2(0x3f, 0x3f);
+                    const uchar2 lkc = lk_next;
+                    if (MASK && t + 2 < nplanes) lk_next = lk2[q0 + plq * (k + 1)];
                     const int cx = 2 + 2 * lane;
                     const float4 pc = *reinterpret_cast<const float4 *>(&Pc.psi[r + 1][cx]);
                     const float2 c0 = lo2(pc), c1 = hi2(pc);
